@@ -1,0 +1,512 @@
+"""Pins for the FP64 CPU oracle: every check compares it with something other
+than itself -- closed-form eigenpairs, dense direct solves and products done
+by numpy/scipy, brute-force graph enumeration, finite differences and the
+paper's worked examples (Sec. 3.1, 3.2).  CPU only."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import oracle as O
+from paper_2606_09001_b300 import matrices as M
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_examples.json")
+
+
+def to_sp(A):
+    return sp.csr_matrix((A.values, A.col_idx, A.row_ptr), shape=(A.n, A.n))
+
+
+def lvl_sp(m, ncols):
+    return sp.csr_matrix((m.values, m.col_idx, m.row_ptr), shape=(m.n, ncols))
+
+
+# --------------------------------------------------------------------------
+# SpMV against closed-form eigenpairs
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,d", [(50, 2.0), (33, 4.0)])
+def test_spmv_1d_eigenpairs(n, d):
+    A = M.tridiagonal_matrix(n, d)
+    for k in (1, 7, n):
+        v = np.sin(k * np.pi * np.arange(1, n + 1) / (n + 1))
+        lam = d - 2.0 * np.cos(k * np.pi / (n + 1))
+        assert np.linalg.norm(O.spmv(A, v) - lam * v) <= 1e-13 * np.linalg.norm(v)
+
+
+def test_spmv_2d_eigenpairs():
+    s = 24
+    A = M.poisson2d(s)
+    t = np.arange(1, s + 1)
+    for j, k in [(1, 1), (3, 5), (24, 2)]:
+        v = np.outer(np.sin(k * np.pi * t / (s + 1)), np.sin(j * np.pi * t / (s + 1))).reshape(-1)
+        lam = 4 - 2 * np.cos(j * np.pi / (s + 1)) - 2 * np.cos(k * np.pi / (s + 1))
+        assert np.linalg.norm(O.spmv(A, v) - lam * v) <= 1e-13 * np.linalg.norm(v)
+
+
+def test_transpose_matches_scipy():
+    rng = np.random.default_rng(0)
+    S = sp.random(40, 27, density=0.2, random_state=1, format="csr")
+    S.sort_indices()
+    rp, ci, v = O.transpose(S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data, 27)
+    T = S.T.tocsr()
+    T.sort_indices()
+    assert np.array_equal(rp, T.indptr) and np.array_equal(ci, T.indices)
+    assert np.array_equal(v, T.data)
+    del rng
+
+
+# --------------------------------------------------------------------------
+# Validation
+# --------------------------------------------------------------------------
+
+def test_validate_codes():
+    A = M.poisson2d(4)
+    assert O.validate(A) == O.OK
+    bad = M.CSR(A.row_ptr.copy(), A.col_idx.copy(), A.values.copy())
+    bad.col_idx[1], bad.col_idx[0] = bad.col_idx[0], bad.col_idx[1]
+    assert O.validate(bad) == O.ERR_BAD_CSR
+    bad = M.CSR(A.row_ptr.copy(), A.col_idx.copy(), A.values.copy())
+    bad.col_idx[-1] = A.n
+    assert O.validate(bad) == O.ERR_BAD_CSR
+    bad = M.CSR(A.row_ptr.copy(), A.col_idx.copy(), A.values.copy())
+    bad.values[0] = 0.0  # row 0 stores its diagonal first
+    assert O.validate(bad) == O.ERR_ZERO_DIAG
+    bad = M.CSR(A.row_ptr.copy(), A.col_idx.copy(), A.values.copy())
+    bad.row_ptr[2] = bad.row_ptr[1] - 1
+    assert O.validate(bad) == O.ERR_BAD_CSR
+
+
+# --------------------------------------------------------------------------
+# Strength of connection
+# --------------------------------------------------------------------------
+
+def test_strength_poisson_all_links_strong():
+    A = M.poisson2d(9)
+    srp, sci = O.strength(A, 0.08)
+    D = A.to_dense()
+    off = (D != 0) & ~np.eye(A.n, dtype=bool)
+    S = np.zeros_like(off)
+    S[np.repeat(np.arange(A.n), np.diff(srp)), sci] = True
+    assert np.array_equal(S, off)
+
+
+def test_strength_anisotropic_keeps_strong_direction():
+    # -u_xx - eps u_yy with eps = 1e-3: y-links |a| = eps fail the test
+    # (eps^2 < 0.08^2 (2+2eps)^2), x-links pass -> S is the union of x-lines.
+    s, eps = 8, 1e-3
+    n = s * s
+    D = np.zeros((n, n))
+    for i in range(n):
+        x, y = i % s, i // s
+        D[i, i] = 2 + 2 * eps
+        if x > 0: D[i, i - 1] = -1
+        if x < s - 1: D[i, i + 1] = -1
+        if y > 0: D[i, i - s] = -eps
+        if y < s - 1: D[i, i + s] = -eps
+    A = M.CSR(*_dense_to_csr(D))
+    srp, sci = O.strength(A, 0.08)
+    rows = np.repeat(np.arange(n), np.diff(srp))
+    assert np.all(np.abs(rows - sci) == 1) and np.all(rows // s == sci // s)
+    assert sci.size == 2 * s * (s - 1)
+
+
+def test_strength_threshold_equality_is_strong_and_union_symmetric():
+    # theta = 0.5: a_01^2 = 1 = 0.25 * |2 * 2| -> strong by equality.
+    D = np.array([[2.0, -1.0, 0.0], [-1.0, 2.0, -0.1], [0.0, -3.0, 4.0]])
+    A = M.CSR(*_dense_to_csr(D))
+    srp, sci = O.strength(A, 0.5)
+    S = {(i, j) for i in range(3) for j in sci[srp[i]:srp[i + 1]]}
+    # (1,2): 0.01 < 0.25*8 weak; (2,1): 9 >= 0.25*8 strong -> union keeps both
+    assert S == {(0, 1), (1, 0), (1, 2), (2, 1)}
+
+
+def _dense_to_csr(D):
+    Ssp = sp.csr_matrix(D)
+    Ssp.sort_indices()
+    # keep explicit diagonal even when zero is impossible here
+    return Ssp.indptr.astype(np.int32), Ssp.indices.astype(np.int32), Ssp.data.astype(np.float64)
+
+
+# --------------------------------------------------------------------------
+# MIS-2 and aggregation
+# --------------------------------------------------------------------------
+
+def _dist2_sets(srp, sci):
+    import networkx as nx
+    n = srp.shape[0] - 1
+    G = nx.Graph()
+    G.add_nodes_from(range(n))
+    for i in range(n):
+        for j in sci[srp[i]:srp[i + 1]]:
+            G.add_edge(i, int(j))
+    return G, {i: set(nx.single_source_shortest_path_length(G, i, cutoff=2)) for i in range(n)}
+
+
+def _check_mis2(srp, sci, root):
+    _, ball = _dist2_sets(srp, sci)
+    R = np.flatnonzero(root)
+    for i in R:  # independence: no other root within distance 2
+        assert not (ball[i] - {i}) & set(R.tolist())
+    for i in range(len(root)):  # maximality: every node within distance 2 of a root
+        assert ball[i] & set(R.tolist())
+
+
+def _random_graph(n, p, seed):
+    rng = np.random.default_rng(seed)
+    U = np.triu(rng.random((n, n)) < p, 1)
+    Adj = U | U.T
+    srp = np.zeros(n + 1, np.int32)
+    srp[1:] = np.cumsum(Adj.sum(1))
+    sci = np.concatenate([np.flatnonzero(Adj[i]) for i in range(n)]).astype(np.int32) if Adj.any() else np.zeros(0, np.int32)
+    return srp, sci
+
+
+def test_fmix32_is_murmur3_finaliser_and_bijective():
+    # Appleby's MurmurHash3 fmix32: xor-shift 16, * 0x85ebca6b, xor-shift 13,
+    # * 0xc2b2ae35, xor-shift 16 (mod 2^32).
+    def ref(h):
+        h ^= h >> 16; h = (h * 0x85EBCA6B) & 0xFFFFFFFF
+        h ^= h >> 13; h = (h * 0xC2B2AE35) & 0xFFFFFFFF
+        return h ^ (h >> 16)
+    for v in (0, 1, 2, 12345, 2**31 - 1, 2**32 - 1):
+        assert O.fmix32(v) == ref(v)
+    vals = {O.fmix32(i) for i in range(20000)}
+    assert len(vals) == 20000 and O.fmix32(0) == 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_mis2_tiny_graphs_lexicographically_first(seed):
+    n = 10 + seed % 3
+    srp, sci = _random_graph(n, 0.25, seed)
+    root, _ = O.mis2(srp, sci, "greedy")
+    root_r, _ = O.mis2(srp, sci, "rounds")
+    assert np.array_equal(root, root_r)
+    _, ball = _dist2_sets(srp, sci)
+    # enumerate every distance-2 independent, maximal set; the greedy set is
+    # the one that is lexicographically first in decreasing-priority order
+    order = sorted(range(n), key=lambda i: (O.fmix32(i), i), reverse=True)
+    best = None
+    for mask in range(1 << n):
+        R = [i for i in range(n) if mask >> i & 1]
+        if any((ball[i] - {i}) & set(R) for i in R):
+            continue
+        if not all(ball[i] & set(R) for i in range(n)):
+            continue
+        key = tuple(1 if (mask >> i & 1) else 0 for i in order)
+        if best is None or key > best[0]:
+            best = (key, R)
+    assert sorted(np.flatnonzero(root).tolist()) == sorted(best[1])
+
+
+@pytest.mark.parametrize("maker", [lambda: M.poisson2d(20), lambda: M.poisson3d(7),
+                                   lambda: M.convection_diffusion_upwind(6)])
+def test_mis2_grid_independent_maximal_and_rounds_equal(maker):
+    A = maker()
+    srp, sci = O.strength(A, 0.08)
+    root, _ = O.mis2(srp, sci, "greedy")
+    root_r, nr = O.mis2(srp, sci, "rounds")
+    assert np.array_equal(root, root_r) and nr < 40
+    _check_mis2(srp, sci, root)
+
+
+def test_mis2_rounds_equal_greedy_random_graphs():
+    for seed in range(5):
+        srp, sci = _random_graph(300, 0.01 + 0.01 * seed, seed + 10)
+        a, _ = O.mis2(srp, sci, "greedy")
+        b, _ = O.mis2(srp, sci, "rounds")
+        assert np.array_equal(a, b)
+        _check_mis2(srp, sci, a)
+
+
+@pytest.mark.parametrize("maker", [lambda: M.poisson2d(17), lambda: M.poisson3d(6),
+                                   lambda: M.convection_diffusion_upwind(6),
+                                   lambda: M.diffusion_fv(np.exp(np.random.default_rng(3).normal(size=(12, 12))))])
+def test_aggregates_partition_and_connected(maker):
+    import networkx as nx
+    A = maker()
+    srp, sci = O.strength(A, 0.08)
+    root, _ = O.mis2(srp, sci)
+    agg, nc = O.aggregate(A, srp, sci, root.astype(np.int32))
+    assert agg.min() == 0 and agg.max() == nc - 1
+    R = np.flatnonzero(root)
+    assert nc == R.size and np.array_equal(agg[R], np.arange(nc))  # ids by node index
+    G, ball = _dist2_sets(srp, sci)
+    for J in range(nc):
+        members = np.flatnonzero(agg == J)
+        assert nx.is_connected(G.subgraph(members.tolist()))
+        assert set(members.tolist()) <= ball[R[J]]  # radius 2 around its root
+
+
+# --------------------------------------------------------------------------
+# Prolongator, Galerkin, hierarchy
+# --------------------------------------------------------------------------
+
+def test_gershgorin_rho_poisson_closed_form():
+    s = 64
+    h = O.Hierarchy(M.poisson2d(s))
+    rho = h.level(0).rho
+    assert rho == 2.0  # interior rows: (4 + 4) / 4
+    assert 1 + np.cos(np.pi / (s + 1)) <= rho  # true rho(D^-1 A)
+
+
+@pytest.mark.parametrize("maker", [lambda: M.poisson2d(16), lambda: M.poisson3d(8),
+                                   lambda: M.convection_diffusion_upwind(8),
+                                   lambda: M.diffusion_fv(np.exp(np.random.default_rng(5).normal(size=(16, 16))))])
+def test_prolongator_and_galerkin_against_dense(maker):
+    A = maker()
+    h = O.Hierarchy(A, {"coarse_max": 8})
+    assert h.nlevels >= 2
+    for l in range(h.nlevels - 1):
+        lv, nx_ = h.level(l), h.level(l + 1)
+        n, nc = lv.A.n, nx_.A.n
+        Ad = lvl_sp(lv.A, n).toarray()
+        T = np.zeros((n, nc))
+        T[np.arange(n), lv.agg] = 1.0
+        assert np.array_equal(T.sum(1), np.ones(n))
+        d = np.diag(Ad)
+        rho = np.max(np.abs(Ad).sum(1) / np.abs(d))
+        assert lv.rho == pytest.approx(rho, rel=1e-15)
+        Pd = (np.eye(n) - (4.0 / 3.0) / rho * (Ad / d[:, None])) @ T
+        P = lvl_sp(lv.P, nc).toarray()
+        assert np.allclose(P, Pd, rtol=0, atol=1e-14)
+        # structural pattern: columns of P = aggregates touched by the row of A
+        pat = (np.abs(Ad) > 0).astype(float) @ T > 0
+        assert np.array_equal(lvl_sp(lv.P, nc).toarray() != 0, pat & (P != 0))
+        assert np.array_equal(np.diff(lv.P.row_ptr), pat.sum(1))
+        # P 1 = 1 on rows with zero row sum
+        zero_rows = np.abs(Ad.sum(1)) < 1e-12 * np.abs(d)
+        assert np.allclose((P @ np.ones(nc))[zero_rows], 1.0, atol=1e-14)
+        # R = P^T exactly
+        assert np.array_equal(lvl_sp(lv.R, n).toarray(), P.T)
+        Ac_dense = P.T @ Ad @ P
+        Ac = lvl_sp(nx_.A, nc).toarray()
+        scale = np.abs(Ac_dense).max()
+        assert np.abs(Ac - Ac_dense).max() <= 1e-14 * scale * max(1, l + 1) * 4
+        if h.symmetric:
+            assert np.abs(Ac - Ac.T).max() <= 1e-14 * scale
+            np.linalg.cholesky(Ac)  # SPD
+
+
+def test_c1_hierarchy_shape():
+    h = O.Hierarchy(M.poisson2d(64))
+    dims = [h.dims(l) for l in range(h.nlevels)]
+    assert dims[0][:2] == (4096, 20224)
+    assert dims[-1][0] <= 64 and all(d[0] > 64 for d in dims[:-1])
+
+
+# --------------------------------------------------------------------------
+# V-cycle
+# --------------------------------------------------------------------------
+
+def _dense_Minv(h, n):
+    return np.stack([h.vcycle(e) for e in np.eye(n)], axis=1)
+
+
+def test_vcycle_symmetric_and_convergent():
+    A = M.poisson2d(12)
+    h = O.Hierarchy(A, {"coarse_max": 10})
+    assert h.nlevels >= 3
+    Mi = _dense_Minv(h, A.n)
+    assert np.abs(Mi - Mi.T).max() <= 1e-13 * np.abs(Mi).max()
+    E = np.eye(A.n) - Mi @ A.to_dense()
+    assert np.max(np.abs(np.linalg.eigvals(E))) < 1.0
+    np.linalg.cholesky((Mi + Mi.T) / 2)
+
+
+def test_two_level_cycle_algebraic_formula():
+    A = M.poisson2d(10)
+    h = O.Hierarchy(A, {"coarse_max": 40})
+    assert h.nlevels == 2
+    lv = h.level(0)
+    n = A.n
+    nc = lv.P.row_ptr.shape[0] and h.level(1).A.n
+    Ad = A.to_dense()
+    P = lvl_sp(lv.P, nc).toarray()
+    W = np.diag((2.0 / 3.0) / np.diag(Ad))
+    Ac = P.T @ Ad @ P
+    S = np.eye(n) - W @ Ad
+    E = S @ (np.eye(n) - P @ np.linalg.solve(Ac, P.T @ Ad)) @ S
+    Minv_formula = (np.eye(n) - E) @ np.linalg.inv(Ad)
+    assert np.allclose(_dense_Minv(h, n), Minv_formula, atol=1e-12)
+
+
+def test_l1_jacobi_cycle_formula():
+    A = M.poisson2d(8)
+    h = O.Hierarchy(A, {"coarse_max": 40, "smoother": 1})
+    lv = h.level(0)
+    nc = h.level(1).A.n
+    Ad = A.to_dense()
+    P = lvl_sp(lv.P, nc).toarray()
+    W = np.diag(1.0 / np.abs(Ad).sum(1))
+    S = np.eye(A.n) - W @ Ad
+    E = S @ (np.eye(A.n) - P @ np.linalg.solve(P.T @ Ad @ P, P.T @ Ad)) @ S
+    assert np.allclose(_dense_Minv(h, A.n), (np.eye(A.n) - E) @ np.linalg.inv(Ad), atol=1e-12)
+
+
+def test_coarse_direct_solve_single_level():
+    A = M.poisson2d(7)  # 49 rows <= 64: one level, dense Cholesky
+    h = O.Hierarchy(A)
+    assert h.nlevels == 1
+    b = np.random.default_rng(1).uniform(-1, 1, A.n)
+    assert np.allclose(h.vcycle(b), np.linalg.solve(A.to_dense(), b), rtol=1e-13, atol=1e-14)
+    C = M.convection_diffusion_upwind(3)  # 27 rows, LU with pivoting
+    h = O.Hierarchy(C)
+    b = b[:C.n]
+    assert not h.symmetric
+    assert np.allclose(h.vcycle(b), np.linalg.solve(C.to_dense(), b), rtol=1e-13, atol=1e-14)
+
+
+def test_not_spd_detected():
+    D = np.array([[1.0, 2.0], [2.0, 1.0]])  # symmetric indefinite
+    A = M.CSR(*_dense_to_csr(D))
+    with pytest.raises(O.OracleError) as e:
+        O.Hierarchy(A, {"symmetric": 1})
+    assert e.value.status == O.NOT_SPD
+
+
+# --------------------------------------------------------------------------
+# Krylov solvers
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("solver,maker", [
+    (O.PCG, lambda: M.poisson2d(32)),
+    (O.PCG, lambda: M.diffusion_fv(np.exp(np.random.default_rng(2).normal(size=(24, 24))))),
+    (O.BICGSTAB, lambda: M.convection_diffusion_upwind(10)),
+    (O.CG, lambda: M.poisson2d(20)),
+    (O.BICGSTAB_NOPREC, lambda: M.convection_diffusion_upwind(8)),
+])
+def test_krylov_against_dense_solve(solver, maker):
+    A = maker()
+    b = np.random.default_rng(7).uniform(-1, 1, A.n)
+    x, info = O.solve(A, b, {"solver": solver, "rtol": 1e-10})
+    assert info.status == O.OK and info.rel_res_true <= 1e-10
+    Ad = A.to_dense()
+    xs = np.linalg.solve(Ad, b)
+    kappa = np.linalg.cond(Ad)
+    assert np.linalg.norm(x - xs) <= kappa * 1e-10 * np.linalg.norm(xs)
+    assert np.linalg.norm(Ad @ x - b) <= 1.0001e-10 * np.linalg.norm(b)
+
+
+def test_cg_eigenvector_rhs_one_iteration():
+    s = 16
+    A = M.poisson2d(s)
+    t = np.arange(1, s + 1)
+    v = np.outer(np.sin(2 * np.pi * t / (s + 1)), np.sin(3 * np.pi * t / (s + 1))).reshape(-1)
+    lam = 4 - 2 * np.cos(3 * np.pi / (s + 1)) - 2 * np.cos(2 * np.pi / (s + 1))
+    x, info = O.solve(A, v, {"solver": O.CG, "rtol": 1e-12})
+    assert info.iters == 1
+    assert np.allclose(x, v / lam, rtol=1e-13, atol=1e-15)
+
+
+def test_zero_rhs_and_maxit_and_nan():
+    A = M.poisson2d(16)
+    x, info = O.solve(A, np.zeros(A.n))
+    assert info.status == O.OK and info.iters == 0 and not x.any()
+    b = np.random.default_rng(0).uniform(-1, 1, A.n)
+    x, info = O.solve(A, b, {"max_iter": 2, "max_restarts": 0})
+    assert info.status == O.MAXIT and info.iters == 2
+    b[3] = np.nan
+    x, info = O.solve(A, b)
+    assert info.status == O.NAN
+
+
+def test_paper_example1_iteration_band():
+    g = json.load(open(GOLDEN))["ex1_poisson"]
+    A = M.poisson_matrix(g["grid"])
+    b = M.rhs_ones(A.n)
+    _, info = O.solve(A, b, {"solver": O.BICGSTAB, "rtol": g["tolerance"]})
+    assert info.status == O.OK and info.iters <= g["band_amg_max"]
+    _, info0 = O.solve(A, b, {"solver": O.BICGSTAB_NOPREC, "rtol": g["tolerance"]})
+    lo, hi = g["band_unpreconditioned"]
+    assert lo <= info0.iters <= hi
+    assert info.iters < info0.iters
+
+
+# --------------------------------------------------------------------------
+# Adjoint (Eq. 1-2)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("maker", [lambda: M.poisson2d(12), lambda: M.convection_diffusion_upwind(6)])
+def test_adjoint_against_dense(maker):
+    A = maker()
+    rng = np.random.default_rng(11)
+    b = rng.uniform(-1, 1, A.n)
+    g = rng.uniform(-1, 1, A.n)
+    cfg = {"solver": O.PCG if A.n == 144 else O.BICGSTAB, "rtol": 1e-13}
+    h = O.Hierarchy(A, cfg)
+    x, _ = h.solve(b)
+    lam, dA, info = h.adjoint(x, g, A.nnz)
+    Ad = A.to_dense()
+    lam_ref = np.linalg.solve(Ad.T, g)
+    assert np.allclose(lam, lam_ref, rtol=1e-10, atol=1e-12)
+    rows = A.row_of()
+    assert np.allclose(dA, -lam_ref[rows] * np.linalg.solve(Ad, b)[A.col_idx], rtol=1e-9, atol=1e-12)
+
+
+def test_adjoint_central_fd_on_values():
+    A = M.convection_diffusion_upwind(5)
+    rng = np.random.default_rng(4)
+    b = rng.uniform(-1, 1, A.n)
+    xt = rng.uniform(-1, 1, A.n)
+    cfg = {"solver": O.BICGSTAB, "rtol": 1e-13}
+
+    def loss(vals, bb):
+        x, info = O.solve(M.CSR(A.row_ptr, A.col_idx, vals), bb, cfg)
+        return np.sum((x - xt) ** 2), x
+
+    L0, x = loss(A.values, b)
+    h = O.Hierarchy(A, cfg)
+    lam, dA, _ = h.adjoint(x, 2 * (x - xt), A.nnz)
+    eps = 1e-5
+    for _ in range(3):
+        v = rng.normal(size=A.nnz)
+        fd = (loss(A.values + eps * v, b)[0] - loss(A.values - eps * v, b)[0]) / (2 * eps)
+        assert dA @ v == pytest.approx(fd, rel=1e-5)
+        u = rng.normal(size=A.n)
+        fdb = (loss(A.values, b + eps * u)[0] - loss(A.values, b - eps * u)[0]) / (2 * eps)
+        assert lam @ u == pytest.approx(fdb, rel=1e-5)
+
+
+def test_paper_example2_gradient_descent():
+    g = json.load(open(GOLDEN))["ex2_tridiagonal_inverse"]
+    n = g["n"]
+    b = M.rhs_ones(n)
+    cfg = {"solver": O.PCG, "rtol": 1e-12}
+    x_t, _ = O.solve(M.tridiagonal_matrix(n, g["true_diag"]), b, cfg)
+    x_t_dense = np.linalg.solve(M.tridiagonal_matrix(n, g["true_diag"]).to_dense(), b)
+    d = d_ref = g["init_diag"]
+    d_at_bound = None
+    for step in range(g["max_iters"]):
+        A = M.tridiagonal_matrix(n, d)
+        h = O.Hierarchy(A, cfg)
+        x, _ = h.solve(b)
+        lam, dA, _ = h.adjoint(x, 2 * (x - x_t), A.nnz)
+        grad = dA[A.row_of() == A.col_idx].sum()  # d enters every diagonal entry
+        # closed form on the exact (dense) trajectory: dL/dd = -lam . x
+        Ad = M.tridiagonal_matrix(n, d_ref).to_dense()
+        xr = np.linalg.solve(Ad, b)
+        grad_ref = -np.linalg.solve(Ad.T, 2 * (xr - x_t_dense)) @ xr
+        assert grad == pytest.approx(grad_ref, rel=1e-7, abs=1e-12)
+        d -= g["lr"] * grad
+        d_ref -= g["lr"] * grad_ref
+        if step + 1 == g["steps_upper_bound"]:
+            d_at_bound = d
+        if abs(grad) < g["grad_tol"]:
+            assert abs(grad_ref) < 1.01 * g["grad_tol"]
+            break
+    assert abs(d_at_bound - g["true_diag"]) < g["recover_abs_tol"]
+    assert d == pytest.approx(g["true_diag"], abs=1e-3)
+
+
+def test_symmetric_detection():
+    assert O.Hierarchy(M.poisson2d(10)).symmetric
+    assert not O.Hierarchy(M.convection_diffusion_upwind(5)).symmetric
+    A = M.poisson2d(10)
+    v = A.values.copy()
+    v[1] = np.nextafter(v[1], 0)  # break bitwise symmetry of one pair
+    assert not O.Hierarchy(M.CSR(A.row_ptr, A.col_idx, v)).symmetric
