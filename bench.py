@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Benchmark of the AMG-preconditioned solve + adjoint.
+
+One step = one AMG-PCG solve of A x = b to rtol 1e-8 plus its adjoint solve
+A^T lambda = g with dL/db = lambda and dL/dA on the pattern, through the
+cached hierarchy (setup excluded, as in the paper's fixed-hierarchy runs).
+The default workload is the 3D variable-coefficient diffusion problem on
+128^3 cells (log k a Gaussian random field), timed in the mixed form (FP32
+V-cycle inside FP64 PCG); the FP64 form is timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves an
+independent replica of the workload; the step time is the maximum over
+ranks and ``value`` is per whole-job step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2606_09001_b300 import matrices as M  # noqa: E402
+
+METRIC = "AMG-PCG solve+adjoint ms at rtol 1e-8 (mixed vs FP64 form); V-cycle HBM GB/s"
+FALLBACK_HBM_GBS = 6400.0
+
+WORKLOADS = {
+    # name: (generator, solver, description)
+    "diffusion3d_grf_128": (lambda: M.diffusion3d_grf(N=128), "PCG",
+                            "3D 7-point variable-coefficient diffusion, 128^3 cells, log k GRF (sigma 1, ell 0.1)"),
+    "poisson2d_64": (lambda: M.poisson2d_64(), "PCG", "2D 5-point Poisson, 64x64"),
+    "diffusion2d_logk_512": (lambda: M.diffusion2d_logk(N=512), "PCG", "2D diffusion, 512x512 cells, log k ~ N(0,1)"),
+    "convdiff3d_upwind_160": (lambda: M.convdiff3d_upwind(N=160), "BICGSTAB",
+                              "3D upwind convection-diffusion, 160^3, cell Peclet 10"),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=list(WORKLOADS), default="diffusion3d_grf_128")
+    p.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.samples = []
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        if not self.samples:
+            return None
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_step_time(w, solver: str, budget_s: float, max_steps: int):
+    """Times the oracle's solve + adjoint on the workload (setup excluded);
+    runs as many whole steps as fit in budget_s (at least one)."""
+    import oracle as O
+    cfg = {"solver": O.BICGSTAB if solver == "BICGSTAB" else O.PCG}
+    h = O.Hierarchy(w.A, cfg)
+    g = np.random.default_rng(7).uniform(-1, 1, w.A.n)
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < max_steps:
+        t0 = time.perf_counter()
+        x, info = h.solve(w.b)
+        h.adjoint(x, g, w.A.nnz)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start + times[-1] > budget_s:
+            break
+    h.close()
+    return statistics.mean(times) * 1e3, len(times), info
+
+
+def run_reference(args):
+    world, rank, _ = dist_init()
+    if rank != 0:
+        return
+    gen, solver, desc = WORKLOADS[args.workload]
+    w = gen()
+    budget = max(30.0, 150.0)
+    total = args.steps + args.warmup
+    ms, nsteps, info = oracle_step_time(w, solver, budget, total)
+    sample = (f"{nsteps} of {total} solve+adjoint steps on the full workload (setup excluded), "
+              f"single-threaded FP64 oracle, {info.iters} iterations per solve")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+        "config": {"workload": args.workload, "description": desc, "n": w.A.n, "nnz": w.A.nnz, "rtol": 1e-8,
+                   "solver": solver},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def load_traffic(kernel: str):
+    """DRAM traffic per launch of `kernel` from the committed ncu summary, if
+    it was taken on the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2606_09001_b300", "csrc", "solve.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = d.get(kernel)
+    if not ent or ent.get("solve_cu_sha256_16") != digest:
+        return None
+    return ent.get("bytes_per_launch_full")
+
+
+def run_ours(args):
+    import torch
+    from paper_2606_09001_b300 import api
+
+    world, rank, local = dist_init()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    gen, solver, desc = WORKLOADS[args.workload]
+    w = gen()
+    A = w.A
+    n, nnz = A.n, A.nnz
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    rp, ci, vals = t(A.row_ptr), t(A.col_idx), t(A.values)
+    b = t(w.b)
+    g = t(np.random.default_rng(7).uniform(-1, 1, n))  # a seeded dL/dx
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    lam = torch.empty_like(x)
+    dA = torch.empty(nnz, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    forms = {}
+    solvers = {}
+    for form in ("mixed", "fp64"):
+        s = api.Solver(rp, ci, vals, {"solver": solver, "precision": form.upper() if form == "mixed" else "FP64"})
+        solvers[form] = s
+
+        def step():
+            _, si = s.solve(b, x, info=False)
+            _, _, ai = s.adjoint(x, g, lam, dA, info=False)
+            if si < 0 or ai < 0:
+                raise RuntimeError("solve failed")
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        s.profile(False)  # restart the launch count
+        sampler = None
+        if form == "mixed":
+            uuid = None
+            try:
+                uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+            except Exception:
+                pass
+            sampler = ClockSampler(uuid)
+            sampler.start()
+            time.sleep(0.25)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = e0.elapsed_time(e1) / args.steps
+        clocks = sampler.stop() if sampler else None
+        launches, _ = s.profile_records()
+        if world > 1:
+            tt = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = tt.item()
+        _, sinfo = s.solve(b, x)
+        _, _, ainfo = s.adjoint(x, g, lam, dA)
+        forms[form] = {"ms_per_step": ms, "solve_iters": sinfo.iters, "adjoint_iters": ainfo.iters,
+                       "rel_res_true": sinfo.rel_res_true, "adjoint_rel_res_true": ainfo.rel_res_true,
+                       "gpu_launches": launches,
+                       "launches_per_step": launches / args.steps}
+        if clocks:
+            forms[form]["clocks"] = clocks
+
+    # per-kernel trace of the mixed form (a separate pass of the same steps)
+    s = solvers["mixed"]
+    s.profile(True)
+    prof_steps = max(1, min(args.steps, 3))
+    for _ in range(prof_steps):
+        s.solve(b, x, info=False)
+        s.adjoint(x, g, lam, dA, info=False)
+    torch.cuda.synchronize(dev)
+    _, recs = s.profile_records()
+    s.profile(False)
+    tot_ms = sum(r["ms"] for r in recs) or 1.0
+    top = max(recs, key=lambda r: r["ms"])
+    vc_names = {"presmooth", "restrict", "coarse", "prolong", "postsmooth"}
+    vc = [r for r in recs if r["name"] in vc_names]
+    vc_bytes, vc_ms = sum(r["bytes"] for r in vc), sum(r["ms"] for r in vc)
+    peak, peak_kind = measured_peaks()
+    top_name = f"{top['name']}[L{top['level']}]"
+    achieved = top["bytes"] / top["launches"] / (top["ms"] / top["launches"] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "bytes_per_launch": top["bytes"] / top["launches"], "ms_per_launch": top["ms"] / top["launches"],
+                "share_of_traced_time": top["ms"] / tot_ms, "traffic": load_traffic(top_name)}
+    kernels = sorted(({"kernel": f"{r['name']}[L{r['level']}]", "launches": r["launches"],
+                       "ms_per_launch": r["ms"] / r["launches"], "share": r["ms"] / tot_ms,
+                       "gbs": r["bytes"] / (r["ms"] * 1e-3) / 1e9 if r["ms"] > 0 else None}
+                      for r in recs), key=lambda d: -d["share"])[:12]
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        s = solvers["mixed"]
+        hb = torch.from_numpy(np.ascontiguousarray(w.b)).pin_memory()
+        hg = g.cpu().pin_memory()
+        hx = torch.empty(n, dtype=torch.float64).pin_memory()
+        hl = torch.empty(n, dtype=torch.float64).pin_memory()
+        hd = torch.empty(nnz, dtype=torch.float64).pin_memory()
+
+        def hstep():
+            s.solve(hb, hx, info=False)
+            s.adjoint(hx, hg, hl, hd, info=False)
+
+        for _ in range(max(1, args.warmup)):
+            hstep()
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        torch.cuda.synchronize(dev)
+        barrier()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        if world > 1:
+            tt = torch.tensor([e2e_ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = tt.item()
+        e2e = {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": 8 * 3 * n,
+               "d2h_bytes_per_step": 8 * (2 * n + nnz)}
+
+    # CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ms_cpu, nsteps, info = oracle_step_time(w, solver, args.cpu_budget, 4)
+        cpu = {"value": ms_cpu, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"{nsteps} solve+adjoint step(s) of the full workload, setup excluded, "
+                         f"single-threaded FP64 ({info.iters} iterations per solve)"}
+
+    info = solvers["mixed"].info()
+    for s in solvers.values():
+        s.close()
+    if rank == 0:
+        mixed = forms["mixed"]
+        value = mixed["ms_per_step"] / world
+        out = {
+            "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic (seeded)",
+            "config": {"workload": args.workload, "description": desc, "n": n, "nnz": nnz, "rtol": 1e-8,
+                       "solver": solver, "precision": "mixed (FP32 V-cycle, FP64 Krylov)",
+                       "levels": info.nlevels, "rows": info.rows, "operator_complexity": info.operator_complexity,
+                       "setup_ms": info.setup_ms,
+                       "l2": "inputs larger than L2: level-0 operator alone is "
+                             f"{nnz * 12 / 1e6:.0f} MB FP64 / {nnz * 8 / 1e6:.0f} MB FP32",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "forms": forms,
+            "vcycle_gbs": vc_bytes / (vc_ms * 1e-3) / 1e9 if vc_ms > 0 else None,
+            "roofline": roofline,
+            "kernels": kernels,
+            "gpu_launches": mixed["gpu_launches"],
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": mixed.get("clocks"),
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

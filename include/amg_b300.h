@@ -1,0 +1,191 @@
+/*
+ * amg_b300.h -- C ABI of libamgb300.so: an algebraic-multigrid-preconditioned
+ * Krylov solver for sparse CSR systems with a reverse-mode adjoint, for one
+ * NVIDIA B300 GPU (sm_103a).
+ *
+ * What the paper defines and this library provides:
+ *   - a single solve entry on a CSR matrix with a configurable Krylov solver
+ *     and AMG preconditioner (JAX-AMG paper, Sec. 2.1 "Python API": inputs are
+ *     normalised to CSR; default BiCGSTAB + AMG);
+ *   - setup caching: the hierarchy built once by amg_setup is reused by every
+ *     amg_solve / amg_adjoint on the handle (Sec. 2.1 "C++/CUDA backend":
+ *     solver handles are cached and reused across solves; Sec. 3.5 runs with a
+ *     fixed hierarchy, reuse_setup=True);
+ *   - the adjoint of the solve (Sec. 2.1 "JAX integration", Eq. 1-2):
+ *     A^T lambda = dL/dx, dL/dA = -lambda x^T (on the stored pattern),
+ *     dL/db = lambda; for symmetric A the forward hierarchy is reused, for a
+ *     nonsymmetric A a hierarchy is built on A^T;
+ *   - diagnostics: iteration count, final residual, convergence status and
+ *     hierarchy statistics (Sec. 2.2, last paragraph).
+ * The AMG method itself is not specified by the paper; this library builds a
+ * smoothed-aggregation hierarchy (strength of connection, distance-2 MIS
+ * aggregation, Jacobi-smoothed prolongator, Galerkin P^T A P) entirely on the
+ * GPU, deterministically.
+ *
+ * Conventions for every entry point:
+ *   - Index arrays are int32, values FP64.  A CSR matrix is square n x n with
+ *     row_ptr[n+1] (row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz < 2^31)
+ *     and col_idx[nnz] strictly ascending within each row; every row stores a
+ *     nonzero diagonal.
+ *   - Array arguments may be device pointers or host pointers (pageable or
+ *     pinned); the library looks up each pointer's memory type and stages host
+ *     arrays through device memory it owns.  The caller owns every array it
+ *     passes; the library never keeps a caller pointer after a call returns.
+ *   - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  All
+ *     GPU work of a call is ordered on that stream; calls that return results
+ *     in amg_info, or that read host arrays, synchronise the stream before
+ *     returning.
+ *   - A handle may be used by one host thread at a time.
+ *   - Return value: AMG_OK (0); a positive soft status (AMG_MAXIT,
+ *     AMG_BREAKDOWN, AMG_NAN) after which the outputs hold the last iterate
+ *     and info->status repeats the code; or a negative hard error, after which
+ *     the outputs are unspecified and amg_last_error() describes the failure.
+ */
+#ifndef AMG_B300_H
+#define AMG_B300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define AMG_OK 0
+#define AMG_MAXIT 1          /* max_iter reached before the tolerance */
+#define AMG_BREAKDOWN 2      /* Krylov breakdown (p.q <= 0 in PCG; rho, r^.v, t.t or omega = 0 twice in BiCGStab) */
+#define AMG_NOT_SPD 3        /* coarsest Cholesky met a pivot <= 0 (or LU a zero pivot) */
+#define AMG_NAN 4            /* non-finite value in the right-hand side or an iterate */
+#define AMG_ERR_ARG (-1)     /* bad argument (NULL handle/pointer, n <= 0, ...) */
+#define AMG_ERR_BAD_CSR (-2) /* row_ptr not monotone / out of range, column out of range or not ascending */
+#define AMG_ERR_ZERO_DIAG (-3) /* a row without a stored diagonal, or a zero diagonal */
+#define AMG_ERR_CUDA (-4)    /* a CUDA runtime error */
+#define AMG_ERR_STALL (-5)   /* coarsening stopped with more than AMG_DENSE_MAX rows on the last level */
+#define AMG_ERR_OOM (-6)     /* device allocation failed */
+#define AMG_ERR_UNSUPPORTED (-7) /* a size beyond a documented limit */
+
+#define AMG_MAX_LEVELS 32
+#define AMG_DENSE_MAX 256    /* largest coarsest level solved densely */
+
+/* Solvers. */
+#define AMG_SOLVER_PCG 0            /* AMG-preconditioned CG (SPD A) */
+#define AMG_SOLVER_BICGSTAB 1       /* AMG right-preconditioned BiCGStab */
+#define AMG_SOLVER_CG 2             /* CG without preconditioner */
+#define AMG_SOLVER_BICGSTAB_NOPREC 3 /* BiCGStab without preconditioner */
+
+/* Smoothers. */
+#define AMG_SMOOTHER_JACOBI 0    /* x <- x + omega D^-1 (b - A x) */
+#define AMG_SMOOTHER_L1_JACOBI 1 /* x <- x + D_l1^-1 (b - A x), d_i = sum_j |a_ij| */
+
+/* Precision of the V-cycle. */
+#define AMG_PRECISION_FP64 0
+#define AMG_PRECISION_MIXED 1 /* FP32 hierarchy values and V-cycle arithmetic inside FP64 Krylov;
+                                 FP64 true residual, dot products and coarsest solve */
+
+typedef struct amg_handle_s *amg_handle; /* opaque, owned by the library until amg_free */
+
+typedef struct {
+    int solver;       /* AMG_SOLVER_*; default AMG_SOLVER_PCG */
+    int smoother;     /* AMG_SMOOTHER_*; default weighted Jacobi */
+    double omega;     /* Jacobi weight; default 2/3 */
+    double theta;     /* finest-level strength threshold; level l uses theta * 2^-l; default 0.08 */
+    int coarse_max;   /* coarsening stops at <= coarse_max rows; default 64 */
+    int max_levels;   /* default 20 (at most AMG_MAX_LEVELS) */
+    double rtol;      /* stop when ||b - A x||_2 <= rtol ||b||_2; default 1e-8 */
+    int max_iter;     /* Krylov iterations (products with A in CG; pairs in BiCGStab); default 500 */
+    int max_restarts; /* restarts from x while the true residual is above rtol; default 3 */
+    int precision;    /* AMG_PRECISION_*; default FP64 */
+    int symmetric;    /* -1 detect (pattern symmetric and values bitwise equal), 0 no, 1 yes; default -1 */
+} amg_config;
+
+typedef struct {
+    int status;        /* same code as the call's return value */
+    int iters;         /* Krylov iterations of the last solve */
+    int restarts;      /* true-residual restarts of the last solve */
+    int nlevels;       /* levels in the hierarchy (the last is solved densely) */
+    double rel_res_true;  /* ||b - A x||_2 / ||b||_2, recomputed in FP64 at the end */
+    double rel_res_rec;   /* recursive residual estimate at the end */
+    int rows[AMG_MAX_LEVELS];
+    long long nnz[AMG_MAX_LEVELS];
+    double operator_complexity; /* sum_l nnz(A_l) / nnz(A_0) */
+    double setup_ms;   /* wall time of amg_setup */
+    double solve_ms;   /* wall time of the last solve (or adjoint solve) */
+} amg_info;
+
+/* Fills *cfg with the defaults listed above.  Returns AMG_OK or AMG_ERR_ARG. */
+int amg_config_default(amg_config *cfg);
+
+/* Builds the AMG hierarchy of A on the GPU and returns it in *out.
+ * Copies row_ptr/col_idx/values; the caller may free them afterwards.
+ * Errors: AMG_ERR_ARG, AMG_ERR_BAD_CSR, AMG_ERR_ZERO_DIAG, AMG_NOT_SPD (the
+ * coarsest level of a matrix declared or detected symmetric is not SPD),
+ * AMG_ERR_STALL, AMG_ERR_OOM, AMG_ERR_UNSUPPORTED, AMG_ERR_CUDA; on error
+ * *out is set to NULL and nothing is leaked. */
+int amg_setup(const amg_config *cfg, int n, long long nnz, const int *row_ptr, const int *col_idx,
+              const double *values, void *cuda_stream, amg_handle *out);
+
+/* Solves A x = b from x0 = 0 with the handle's solver; b and x have n entries.
+ * info may be NULL.  Returns AMG_OK or a soft/hard status (see above). */
+int amg_solve(amg_handle h, const double *b, double *x, void *cuda_stream, amg_info *info);
+
+/* Reverse-mode adjoint of x = A^-1 b (Eq. 1-2).  Given the forward solution x
+ * and g = dL/dx (n entries each), solves A^T lambda = g with the handle's
+ * configuration and writes lambda = dL/db (n entries) and
+ * dA[k] = -lambda[row(k)] * x[col_idx[k]] for every stored entry k (nnz
+ * entries, the order of the setup's col_idx).  Either output may be NULL to
+ * skip it.  For a nonsymmetric A the first call builds and caches a hierarchy
+ * of A^T.  Returns like amg_solve. */
+int amg_adjoint(amg_handle h, const double *x, const double *g, double *lambda, double *dA,
+                void *cuda_stream, amg_info *info);
+
+/* Applies the AMG preconditioner once: z = M^-1 r (one V(1,1) cycle from
+ * z = 0), the operator the Krylov solvers use (Sec. 2.2, preconditioner
+ * export).  r and z have n entries. */
+int amg_vcycle(amg_handle h, const double *r, double *z, void *cuda_stream);
+
+/* Hierarchy statistics (nlevels, rows, nnz, operator_complexity, setup_ms).
+ * The iteration fields are those of the handle's last solve. */
+int amg_get_info(amg_handle h, amg_info *info);
+
+/* Copies level data out of the hierarchy (inspection and testing).
+ * which = 0: A_l (rows n_l); 1: P_l (n_l x n_{l+1}); 2: R_l = P_l^T.
+ * dims[0] = rows, dims[1] = cols, dims[2] = nnz are written when dims != NULL;
+ * row_ptr/col_idx/values may be NULL to query the sizes only. */
+int amg_get_level(amg_handle h, int level, int which, long long *dims, int *row_ptr, int *col_idx,
+                  double *values);
+
+/* Copies the aggregate index of every row of level l (l < nlevels - 1). */
+int amg_get_aggregates(amg_handle h, int level, int *agg);
+
+/* Per-kernel tracing of the solve phase.  The paper reports wall-clock times
+ * only; this is the library's own instrumentation.  amg_profile(h, 1) clears
+ * the records and brackets every later solve-phase kernel launch of the
+ * handle with CUDA events on the handle's stream; amg_profile(h, 0) stops
+ * bracketing and keeps the records.  Kernel launches are counted in both
+ * modes (the count restarts at every amg_profile call). */
+int amg_profile(amg_handle h, int enable);
+
+/* Kernel launches since the last amg_profile call, and the number of
+ * (kernel, level) records.  Either pointer may be NULL. */
+int amg_profile_summary(amg_handle h, long long *launches, int *nrecords);
+
+/* Record i (0 <= i < nrecords): kernel name (NUL-terminated, truncated to
+ * name_len bytes), hierarchy level, launches, total device time in ms and
+ * total algorithmic bytes (compulsory DRAM traffic of the launches: operator
+ * values, indices and row pointers once, each vector once).  Output pointers
+ * may be NULL. */
+int amg_profile_record(amg_handle h, int i, char *name, int name_len, int *level, long long *launches,
+                       double *total_ms, double *total_bytes);
+
+/* Releases every resource of the handle.  amg_free(NULL) is a no-op. */
+int amg_free(amg_handle h);
+
+/* Static description of a status code. */
+const char *amg_status_string(int code);
+
+/* Description of the last hard error raised on the calling host thread. */
+const char *amg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMG_B300_H */

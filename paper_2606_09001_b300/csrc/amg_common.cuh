@@ -1,0 +1,179 @@
+// amg_common.cuh -- internal types and helpers of libamgb300 (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+#include <vector>
+
+#include "amg_b300.h"
+
+namespace amg {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+
+void set_last_error(const char *fmt, ...);
+
+#define AMG_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t _e = (expr);                                                        \
+        if (_e != cudaSuccess) {                                                        \
+            ::amg::set_last_error("%s:%d: %s -> %s", __FILE__, __LINE__, #expr,          \
+                                  cudaGetErrorString(_e));                              \
+            return _e == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA;        \
+        }                                                                               \
+    } while (0)
+
+#define AMG_TRY(expr)                 \
+    do {                              \
+        int _s = (expr);              \
+        if (_s < 0) return _s;        \
+    } while (0)
+
+#define AMG_LAUNCH_CHECK() AMG_CUDA_TRY(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// Device memory owned by a handle
+// ---------------------------------------------------------------------------
+
+// Records every allocation so a handle frees all of it at once.  Allocations
+// are rounded up and padded by 64 bytes so that vector loads that run up to
+// 16 bytes past the last element of an array stay inside the allocation.
+struct DevArena {
+    std::vector<void *> ptrs;
+    size_t bytes = 0;
+    template <typename T>
+    int alloc(T **p, size_t count) {
+        size_t b = (count * sizeof(T) + 64 + 255) & ~size_t(255);
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, b);
+        if (e != cudaSuccess) {
+            set_last_error("cudaMalloc(%zu) failed: %s", b, cudaGetErrorString(e));
+            *p = nullptr;
+            return e == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA;
+        }
+        ptrs.push_back(q);
+        bytes += b;
+        *p = static_cast<T *>(q);
+        return AMG_OK;
+    }
+    void release(void *p) {
+        for (auto &q : ptrs)
+            if (q == p) {
+                cudaFree(q);
+                q = nullptr;
+            }
+    }
+    void free_all() {
+        for (void *q : ptrs)
+            if (q) cudaFree(q);
+        ptrs.clear();
+        bytes = 0;
+    }
+};
+
+// Scratch buffers freed at the end of a setup phase.
+struct Scratch {
+    DevArena arena;
+    ~Scratch() { arena.free_all(); }
+    template <typename T>
+    int alloc(T **p, size_t count) { return arena.alloc(p, count); }
+};
+
+// ---------------------------------------------------------------------------
+// Sparse matrices
+// ---------------------------------------------------------------------------
+
+struct DevCSR {
+    int nrows = 0, ncols = 0;
+    long long nnz = 0;
+    int *rp = nullptr;
+    int *ci = nullptr;
+    double *v = nullptr;
+    float *v32 = nullptr;  // FP32 copy (mixed precision), or null
+};
+
+// ---------------------------------------------------------------------------
+// Device-side Krylov state
+// ---------------------------------------------------------------------------
+
+struct DevScalars {
+    double bn2;       // ||b||^2
+    double tol2;      // (rtol ||b||)^2
+    double rz;        // PCG: r.z of the current iteration
+    double rz_new;
+    double pq;
+    double alpha, beta;
+    double rr;        // ||r||^2 (recursive)
+    double rho, rho_old, omega, rv, ts, tt, ss;  // BiCGStab
+    double tr;        // true residual ||b - A x||^2
+    int done;         // 1: stop launching work (converged, failed or max_iter)
+    int status;       // AMG_OK / AMG_MAXIT / AMG_BREAKDOWN / AMG_NAN while running
+    int iters;
+    int flexible;     // PCG uses the Polak-Ribiere beta (mixed-precision V-cycle)
+    int max_iter;
+    int first;        // PCG: the next beta starts a new recursion (beta = 0)
+    int pad[2];
+};
+
+// ---------------------------------------------------------------------------
+// Hierarchy
+// ---------------------------------------------------------------------------
+
+struct Level {
+    DevCSR A, P, R;     // P: n x nc, R = P^T: nc x n (P, R unused on the last level)
+    double *w = nullptr;    // smoother weight per row (omega / a_ii, or 1 / sum |a_ij|)
+    float *w32 = nullptr;
+    int *agg = nullptr;     // aggregate of each row (levels < last)
+    double rho = 0.0;       // Gershgorin estimate used for P
+    // V-cycle work vectors: b (right-hand side, levels > 0), t (residual, then
+    // prolonged iterate), x (smoothed iterate, levels > 0).
+    double *b = nullptr, *t = nullptr, *x = nullptr;
+    float *b32 = nullptr, *t32 = nullptr, *x32 = nullptr;
+    int vec_a = 8, vec_p = 8, vec_r = 8;  // threads per row chosen per operator
+};
+
+struct Hierarchy {
+    amg_config cfg;
+    int n = 0;
+    long long nnz = 0;
+    int symmetric = 0;
+    int nlevels = 0;
+    Level L[AMG_MAX_LEVELS];
+    int nc = 0;                 // rows of the coarsest level
+    double *cinv = nullptr;     // dense inverse of the coarsest operator, nc x nc row-major
+    DevArena arena;
+    double setup_ms = 0.0;
+};
+
+// ---------------------------------------------------------------------------
+// Small device helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int W, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, W);
+    return v;
+}
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Host utilities implemented in setup.cu.
+int exclusive_scan_int(const int *in, int *out, int n, int *total_host, cudaStream_t s);
+int transpose_csr(const DevCSR &a, DevCSR &t, DevArena &arena, cudaStream_t s);
+int build_hierarchy(Hierarchy *h, const int *rp, const int *ci, const double *v, cudaStream_t s);
+void free_hierarchy(Hierarchy *h);
+int num_sms();
+
+}  // namespace amg

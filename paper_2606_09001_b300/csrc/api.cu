@@ -1,0 +1,343 @@
+// api.cu -- the C ABI of libamgb300 (declared in include/amg_b300.h).
+#include <chrono>
+#include <cstring>
+#include <new>
+
+#include "solve.cuh"
+
+namespace amg {
+const char *last_error();
+}
+
+using namespace amg;
+
+struct amg_handle_s {
+    Hierarchy H;              // hierarchy of A
+    Hierarchy *HT = nullptr;  // hierarchy of A^T (nonsymmetric adjoint), built on first use
+    Workspace W;
+    cudaStream_t s = nullptr; // private stream; ordered after/before the caller's stream by events
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    double *dA_stage = nullptr;  // device staging of dL/dA for host outputs
+    DevArena extra;
+    SolveResult last;
+    double last_solve_ms = 0.0;
+};
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+int check_config(const amg_config &c) {
+    if (c.solver < 0 || c.solver > 3 || (c.smoother != 0 && c.smoother != 1) || !(c.omega > 0.0) ||
+        !(c.theta >= 0.0) || c.coarse_max < 1 || c.max_levels < 1 || c.max_levels > AMG_MAX_LEVELS ||
+        !(c.rtol > 0.0) || c.max_iter < 1 || c.max_restarts < 0 || (c.precision != 0 && c.precision != 1) ||
+        c.symmetric < -1 || c.symmetric > 1) {
+        set_last_error("invalid amg_config");
+        return AMG_ERR_ARG;
+    }
+    return AMG_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Orders the private stream after the caller's stream.
+int enter(amg_handle h, void *cuda_stream) {
+    cudaStream_t us = (cudaStream_t)cuda_stream;
+    AMG_CUDA_TRY(cudaEventRecord(h->ev_in, us));
+    AMG_CUDA_TRY(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+    return AMG_OK;
+}
+
+// Orders the caller's stream after the private stream.
+int leave(amg_handle h, void *cuda_stream, bool sync) {
+    cudaStream_t us = (cudaStream_t)cuda_stream;
+    AMG_CUDA_TRY(cudaEventRecord(h->ev_out, h->s));
+    AMG_CUDA_TRY(cudaStreamWaitEvent(us, h->ev_out, 0));
+    if (sync) AMG_CUDA_TRY(cudaStreamSynchronize(h->s));
+    return AMG_OK;
+}
+
+void fill_info(amg_handle h, const Hierarchy &H, amg_info *info) {
+    memset(info, 0, sizeof(*info));
+    info->status = h->last.status;
+    info->iters = h->last.iters;
+    info->restarts = h->last.restarts;
+    info->rel_res_true = h->last.rel_res_true;
+    info->rel_res_rec = h->last.rel_res_rec;
+    info->nlevels = H.nlevels;
+    long long tot = 0;
+    for (int l = 0; l < H.nlevels; ++l) {
+        info->rows[l] = H.L[l].A.nrows;
+        info->nnz[l] = H.L[l].A.nnz;
+        tot += H.L[l].A.nnz;
+    }
+    info->operator_complexity = H.nnz ? (double)tot / (double)H.nnz : 0.0;
+    info->setup_ms = H.setup_ms;
+    info->solve_ms = h->last_solve_ms;
+}
+
+void destroy(amg_handle h) {
+    if (!h) return;
+    if (h->s) cudaStreamSynchronize(h->s);
+    free_hierarchy(&h->H);
+    if (h->HT) {
+        free_hierarchy(h->HT);
+        delete h->HT;
+    }
+    workspace_free(h->W);
+    h->extra.free_all();
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->s) cudaStreamDestroy(h->s);
+    delete h;
+}
+
+int run_solve(amg_handle h, Hierarchy *H, cudaStream_t s) {
+    const auto t0 = clk::now();
+    SolveResult r;
+    int rc = krylov_solve(H, h->W, s, &r);
+    h->last_solve_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    if (rc < 0) return rc;
+    h->last = r;
+    return r.status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int amg_config_default(amg_config *c) {
+    if (!c) return AMG_ERR_ARG;
+    c->solver = AMG_SOLVER_PCG;
+    c->smoother = AMG_SMOOTHER_JACOBI;
+    c->omega = 2.0 / 3.0;
+    c->theta = 0.08;
+    c->coarse_max = 64;
+    c->max_levels = 20;
+    c->rtol = 1e-8;
+    c->max_iter = 500;
+    c->max_restarts = 3;
+    c->precision = AMG_PRECISION_FP64;
+    c->symmetric = -1;
+    return AMG_OK;
+}
+
+int amg_setup(const amg_config *cfg, int n, long long nnz, const int *row_ptr, const int *col_idx,
+              const double *values, void *cuda_stream, amg_handle *out) {
+    if (!out) return AMG_ERR_ARG;
+    *out = nullptr;
+    if (n <= 0 || nnz < n || nnz >= (1LL << 31) - 1 || !row_ptr || !col_idx || !values) {
+        set_last_error("amg_setup: invalid sizes or null array (n=%d, nnz=%lld)", n, nnz);
+        return AMG_ERR_ARG;
+    }
+    amg_config c;
+    if (cfg) c = *cfg;
+    else amg_config_default(&c);
+    AMG_TRY(check_config(c));
+    amg_handle h = new (std::nothrow) amg_handle_s();
+    if (!h) return AMG_ERR_OOM;
+    const auto t0 = clk::now();
+    int rc = AMG_OK;
+    do {
+        if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+            set_last_error("amg_setup: stream/event creation failed: %s", cudaGetErrorString(cudaGetLastError()));
+            rc = AMG_ERR_CUDA;
+            break;
+        }
+        if ((rc = enter(h, cuda_stream)) < 0) break;
+        h->H.cfg = c;
+        h->H.n = n;
+        h->H.nnz = nnz;
+        if ((rc = build_hierarchy(&h->H, row_ptr, col_idx, values, h->s)) != AMG_OK) break;
+        if ((rc = workspace_init(h->W, n)) < 0) break;
+        if ((rc = leave(h, cuda_stream, true)) < 0) break;
+    } while (0);
+    if (rc != AMG_OK) {
+        destroy(h);
+        return rc;
+    }
+    h->H.setup_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    *out = h;
+    return AMG_OK;
+}
+
+int amg_solve(amg_handle h, const double *b, double *x, void *cuda_stream, amg_info *info) {
+    if (!h || !b || !x) return AMG_ERR_ARG;
+    const int n = h->H.n;
+    AMG_TRY(enter(h, cuda_stream));
+    AMG_CUDA_TRY(cudaMemcpyAsync(h->W.b, b, sizeof(double) * n, cudaMemcpyDefault, h->s));
+    int rc = run_solve(h, &h->H, h->s);
+    if (rc < 0) return rc;
+    AMG_CUDA_TRY(cudaMemcpyAsync(x, h->W.x, sizeof(double) * n, cudaMemcpyDefault, h->s));
+    AMG_TRY(leave(h, cuda_stream, info != nullptr || !is_device_ptr(x)));
+    if (info) fill_info(h, h->H, info);
+    return rc;
+}
+
+int amg_adjoint(amg_handle h, const double *x, const double *g, double *lambda, double *dA, void *cuda_stream,
+                amg_info *info) {
+    if (!h || !x || !g) return AMG_ERR_ARG;
+    const int n = h->H.n;
+    const long long nnz = h->H.nnz;
+    AMG_TRY(enter(h, cuda_stream));
+    Hierarchy *H = &h->H;
+    if (!h->H.symmetric) {
+        if (!h->HT) {
+            // A^T: transpose on the device, then a full setup of its own
+            Hierarchy *HT = new (std::nothrow) Hierarchy();
+            if (!HT) return AMG_ERR_OOM;
+            DevArena tmp;
+            DevCSR At;
+            int rc = transpose_csr(h->H.L[0].A, At, tmp, h->s);
+            if (rc == AMG_OK) {
+                HT->cfg = h->H.cfg;
+                HT->cfg.symmetric = 0;
+                HT->n = n;
+                HT->nnz = nnz;
+                const auto t0 = clk::now();
+                rc = build_hierarchy(HT, At.rp, At.ci, At.v, h->s);
+                HT->setup_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+            }
+            cudaStreamSynchronize(h->s);
+            tmp.free_all();
+            if (rc != AMG_OK) {
+                free_hierarchy(HT);
+                delete HT;
+                return rc;
+            }
+            h->HT = HT;
+        }
+        H = h->HT;
+    }
+    AMG_CUDA_TRY(cudaMemcpyAsync(h->W.aux, x, sizeof(double) * n, cudaMemcpyDefault, h->s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(h->W.b, g, sizeof(double) * n, cudaMemcpyDefault, h->s));
+    int rc = run_solve(h, H, h->s);
+    if (rc < 0) return rc;
+    // W.x = lambda
+    bool host_out = false;
+    if (lambda) {
+        AMG_CUDA_TRY(cudaMemcpyAsync(lambda, h->W.x, sizeof(double) * n, cudaMemcpyDefault, h->s));
+        host_out |= !is_device_ptr(lambda);
+    }
+    if (dA) {
+        if (is_device_ptr(dA)) {
+            AMG_TRY(grad_values(&h->H, h->W, h->W.x, h->W.aux, dA, h->s));
+        } else {
+            if (!h->dA_stage) AMG_TRY(h->extra.alloc(&h->dA_stage, (size_t)nnz));
+            AMG_TRY(grad_values(&h->H, h->W, h->W.x, h->W.aux, h->dA_stage, h->s));
+            AMG_CUDA_TRY(cudaMemcpyAsync(dA, h->dA_stage, sizeof(double) * nnz, cudaMemcpyDefault, h->s));
+            host_out = true;
+        }
+    }
+    AMG_TRY(leave(h, cuda_stream, info != nullptr || host_out));
+    if (info) fill_info(h, *H, info);
+    return rc;
+}
+
+int amg_vcycle(amg_handle h, const double *r, double *z, void *cuda_stream) {
+    if (!h || !r || !z) return AMG_ERR_ARG;
+    const int n = h->H.n;
+    AMG_TRY(enter(h, cuda_stream));
+    AMG_CUDA_TRY(cudaMemcpyAsync(h->W.b, r, sizeof(double) * n, cudaMemcpyDefault, h->s));
+    AMG_TRY(vcycle_apply(&h->H, h->W, h->W.b, h->W.z, h->s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(z, h->W.z, sizeof(double) * n, cudaMemcpyDefault, h->s));
+    AMG_TRY(leave(h, cuda_stream, !is_device_ptr(z)));
+    return AMG_OK;
+}
+
+int amg_get_info(amg_handle h, amg_info *info) {
+    if (!h || !info) return AMG_ERR_ARG;
+    fill_info(h, h->H, info);
+    return AMG_OK;
+}
+
+int amg_get_level(amg_handle h, int level, int which, long long *dims, int *row_ptr, int *col_idx,
+                  double *values) {
+    if (!h || level < 0 || level >= h->H.nlevels || which < 0 || which > 2) return AMG_ERR_ARG;
+    if (which > 0 && level >= h->H.nlevels - 1) return AMG_ERR_ARG;
+    const Level &lv = h->H.L[level];
+    const DevCSR &m = which == 0 ? lv.A : which == 1 ? lv.P : lv.R;
+    if (dims) {
+        dims[0] = m.nrows;
+        dims[1] = m.ncols;
+        dims[2] = m.nnz;
+    }
+    if (row_ptr) AMG_CUDA_TRY(cudaMemcpy(row_ptr, m.rp, sizeof(int) * ((size_t)m.nrows + 1), cudaMemcpyDefault));
+    if (col_idx) AMG_CUDA_TRY(cudaMemcpy(col_idx, m.ci, sizeof(int) * (size_t)m.nnz, cudaMemcpyDefault));
+    if (values) AMG_CUDA_TRY(cudaMemcpy(values, m.v, sizeof(double) * (size_t)m.nnz, cudaMemcpyDefault));
+    return AMG_OK;
+}
+
+int amg_get_aggregates(amg_handle h, int level, int *agg) {
+    if (!h || !agg || level < 0 || level >= h->H.nlevels - 1) return AMG_ERR_ARG;
+    AMG_CUDA_TRY(cudaMemcpy(agg, h->H.L[level].agg, sizeof(int) * (size_t)h->H.L[level].A.nrows, cudaMemcpyDefault));
+    return AMG_OK;
+}
+
+int amg_profile(amg_handle h, int enable) {
+    if (!h) return AMG_ERR_ARG;
+    AMG_CUDA_TRY(cudaStreamSynchronize(h->s));
+    h->W.prof.reset();
+    h->W.prof.on = enable != 0;
+    return AMG_OK;
+}
+
+int amg_profile_summary(amg_handle h, long long *launches, int *nrecords) {
+    if (!h) return AMG_ERR_ARG;
+    AMG_CUDA_TRY(cudaStreamSynchronize(h->s));
+    h->W.prof.collect();
+    if (launches) *launches = h->W.prof.launches;
+    if (nrecords) *nrecords = (int)h->W.prof.recs.size();
+    return AMG_OK;
+}
+
+int amg_profile_record(amg_handle h, int i, char *name, int name_len, int *level, long long *launches,
+                       double *total_ms, double *total_bytes) {
+    if (!h || i < 0 || i >= (int)h->W.prof.recs.size()) return AMG_ERR_ARG;
+    const Profiler::Rec &r = h->W.prof.recs[i];
+    if (name && name_len > 0) {
+        strncpy(name, r.name, (size_t)name_len - 1);
+        name[name_len - 1] = 0;
+    }
+    if (level) *level = r.level;
+    if (launches) *launches = r.launches;
+    if (total_ms) *total_ms = r.ms;
+    if (total_bytes) *total_bytes = r.bytes;
+    return AMG_OK;
+}
+
+int amg_free(amg_handle h) {
+    destroy(h);
+    return AMG_OK;
+}
+
+const char *amg_status_string(int code) {
+    switch (code) {
+        case AMG_OK: return "ok";
+        case AMG_MAXIT: return "maximum iterations reached";
+        case AMG_BREAKDOWN: return "Krylov breakdown";
+        case AMG_NOT_SPD: return "coarsest operator not SPD / singular";
+        case AMG_NAN: return "non-finite value";
+        case AMG_ERR_ARG: return "invalid argument";
+        case AMG_ERR_BAD_CSR: return "invalid CSR structure";
+        case AMG_ERR_ZERO_DIAG: return "zero or missing diagonal";
+        case AMG_ERR_CUDA: return "CUDA error";
+        case AMG_ERR_STALL: return "coarsening stalled";
+        case AMG_ERR_OOM: return "out of device memory";
+        case AMG_ERR_UNSUPPORTED: return "size beyond a supported limit";
+        default: return "unknown status";
+    }
+}
+
+const char *amg_last_error(void) { return amg::last_error(); }
+
+}  // extern "C"

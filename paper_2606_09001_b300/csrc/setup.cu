@@ -1,0 +1,1088 @@
+// setup.cu -- construction of the smoothed-aggregation AMG hierarchy on the GPU.
+//
+// Every integer decision (strength, independent set, aggregates, sparsity
+// patterns) is deterministic, and every floating-point value that feeds a
+// later decision is computed in a fixed order with each multiply and add
+// rounded separately (__dmul_rn / __dadd_rn / __ddiv_rn; this file is also
+// built with -fmad=false), so the hierarchy does not depend on thread
+// scheduling.  The steps are:
+//   validation of the CSR input               (CSR normalisation, Sec. 2.1)
+//   strength of connection S = S1 or S1^T      a_ij^2 >= theta_l^2 |a_ii a_jj|
+//   distance-2 maximal independent set         synchronous rounds of max-tuple propagation
+//   aggregates                                 roots, their neighbours, then best strong neighbour
+//   prolongator P = (I - omega_P D^-1 A) T     omega_P = (4/3) / Gershgorin bound
+//   R = P^T                                    CSR transpose
+//   Galerkin A_c = R (A P)                     row-wise SpGEMM, fixed summation order
+//   coarsest level                             dense Cholesky / LU, explicit inverse
+#include <cstdarg>
+#include <cstring>
+#include <algorithm>
+
+#include "amg_common.cuh"
+
+namespace amg {
+
+static thread_local char g_last_error[1024] = "";
+
+void set_last_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+}
+
+const char *last_error() { return g_last_error; }
+
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 148;
+    }
+    return sms;
+}
+
+// ===========================================================================
+// Exclusive scan of int counts (out has n + 1 entries; out[n] = total)
+// ===========================================================================
+
+constexpr int SCAN_T = 256, SCAN_I = 8, SCAN_TILE = SCAN_T * SCAN_I;
+
+template <typename TIn, typename TOut>
+__global__ void k_scan_tile(const TIn *in, TOut *out, long long *sums, int n) {
+    __shared__ long long sh[SCAN_T];
+    const int tid = threadIdx.x;
+    const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)tid * SCAN_I;
+    long long v[SCAN_I];
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_I; ++i) {
+        v[i] = (base + i < n) ? (long long)in[base + i] : 0;
+        s += v[i];
+    }
+    sh[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < SCAN_T; off <<= 1) {
+        long long add = tid >= off ? sh[tid - off] : 0;
+        __syncthreads();
+        sh[tid] += add;
+        __syncthreads();
+    }
+    long long run = tid ? sh[tid - 1] : 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_I; ++i) {
+        if (base + i < n) out[base + i] = (TOut)run;
+        run += v[i];
+    }
+    if (tid == SCAN_T - 1) sums[blockIdx.x] = sh[SCAN_T - 1];
+}
+
+template <typename TOut>
+__global__ void k_scan_add(TOut *out, const long long *sums, int n) {
+    long long i = (long long)blockIdx.x * SCAN_TILE + threadIdx.x;
+    long long add = sums[blockIdx.x];
+    for (int k = 0; k < SCAN_I; ++k, i += SCAN_T)
+        if (i < n) out[i] = (TOut)((long long)out[i] + add);
+}
+
+// Exclusive scan of long long in place; returns the total.
+static int scan_ll_inplace(long long *a, int n, long long *total, cudaStream_t s) {
+    int nb = ceil_div(n, SCAN_TILE);
+    long long *sums = nullptr;
+    Scratch sc;
+    AMG_TRY(sc.alloc(&sums, nb + 1));
+    k_scan_tile<long long, long long><<<nb, SCAN_T, 0, s>>>(a, a, sums, n);
+    AMG_LAUNCH_CHECK();
+    if (nb > 1) {
+        long long t = 0;
+        AMG_TRY(scan_ll_inplace(sums, nb, &t, s));
+        k_scan_add<long long><<<nb, SCAN_T, 0, s>>>(a, sums, n);
+        AMG_LAUNCH_CHECK();
+        *total = t;
+    } else {
+        AMG_CUDA_TRY(cudaMemcpyAsync(total, sums, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return AMG_OK;
+}
+
+int exclusive_scan_int(const int *in, int *out, int n, int *total_host, cudaStream_t s) {
+    if (n <= 0) {
+        AMG_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int), s));
+        if (total_host) *total_host = 0;
+        return AMG_OK;
+    }
+    int nb = ceil_div(n, SCAN_TILE);
+    long long *sums = nullptr;
+    Scratch sc;
+    AMG_TRY(sc.alloc(&sums, nb + 1));
+    k_scan_tile<int, int><<<nb, SCAN_T, 0, s>>>(in, out, sums, n);
+    AMG_LAUNCH_CHECK();
+    long long total = 0;
+    if (nb > 1) {
+        AMG_TRY(scan_ll_inplace(sums, nb, &total, s));
+        k_scan_add<int><<<nb, SCAN_T, 0, s>>>(out, sums, n);
+        AMG_LAUNCH_CHECK();
+    } else {
+        AMG_CUDA_TRY(cudaMemcpyAsync(&total, sums, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (total >= (1LL << 31) - 1) {
+        set_last_error("scan total %lld exceeds the int32 index range", total);
+        return AMG_ERR_UNSUPPORTED;
+    }
+    int t32 = (int)total;
+    AMG_CUDA_TRY(cudaMemcpyAsync(out + n, &t32, sizeof(int), cudaMemcpyHostToDevice, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));  // t32 lives on this stack frame
+    if (total_host) *total_host = t32;
+    return AMG_OK;
+}
+
+// ===========================================================================
+// Generic small kernels
+// ===========================================================================
+
+__global__ void k_fill_int(int *a, int n, int v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+__global__ void k_iota(int *a, int n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a[i] = (int)i;
+}
+
+__global__ void k_fill_double(double *a, long long n, double v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+__global__ void k_to_f32(const double *in, float *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = __double2float_rn(in[i]);
+}
+
+static int grid_for(long long n, int threads = 256) {
+    long long g = (n + threads - 1) / threads;
+    long long cap = (long long)num_sms() * 16;
+    return (int)std::max(1LL, std::min(g, cap));
+}
+
+// ===========================================================================
+// CSR transpose (deterministic: each output row lists its columns ascending)
+// ===========================================================================
+
+__global__ void k_count_cols(const int *ci, long long nnz, int *cnt) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[ci[k]], 1);
+}
+
+__global__ void k_transpose_scatter(int nrows, const int *rp, const int *ci, const double *v, int *next,
+                                    int *tci, double *tv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x)
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            int pos = atomicAdd(&next[ci[k]], 1);
+            tci[pos] = i;
+            if (v) tv[pos] = v[k];
+        }
+}
+
+// One warp per segment: stable order by key (keys in a segment are unique),
+// by rank counting.  Writes the sorted segment to (out_k, out_v).
+__global__ void k_sort_segments(int nseg, const int *seg_ptr, const int *in_k, const double *in_v, int *out_k,
+                                double *out_v) {
+    const int lane = threadIdx.x & 31;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int sgm = wid; sgm < nseg; sgm += nw) {
+        const int s = seg_ptr[sgm], e = seg_ptr[sgm + 1];
+        const int len = e - s;
+        for (int a = lane; a < len; a += 32) {
+            int key = in_k[s + a];
+            int rank = 0;
+            for (int b = 0; b < len; ++b) rank += in_k[s + b] < key;
+            out_k[s + rank] = key;
+            if (in_v) out_v[s + rank] = in_v[s + a];
+        }
+    }
+}
+
+int transpose_csr(const DevCSR &a, DevCSR &t, DevArena &arena, cudaStream_t s) {
+    t.nrows = a.ncols;
+    t.ncols = a.nrows;
+    t.nnz = a.nnz;
+    AMG_TRY(arena.alloc(&t.rp, (size_t)t.nrows + 1));
+    AMG_TRY(arena.alloc(&t.ci, (size_t)std::max(1LL, a.nnz)));
+    t.v = nullptr;
+    if (a.v) AMG_TRY(arena.alloc(&t.v, (size_t)std::max(1LL, a.nnz)));
+    Scratch sc;
+    int *cnt, *next, *tmp_k;
+    double *tmp_v = nullptr;
+    AMG_TRY(sc.alloc(&cnt, (size_t)t.nrows + 1));
+    AMG_TRY(sc.alloc(&next, (size_t)t.nrows + 1));
+    AMG_TRY(sc.alloc(&tmp_k, (size_t)std::max(1LL, a.nnz)));
+    if (a.v) AMG_TRY(sc.alloc(&tmp_v, (size_t)std::max(1LL, a.nnz)));
+    AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)t.nrows + 1), s));
+    if (a.nnz > 0) {
+        k_count_cols<<<grid_for(a.nnz), 256, 0, s>>>(a.ci, a.nnz, cnt);
+        AMG_LAUNCH_CHECK();
+    }
+    int total = 0;
+    AMG_TRY(exclusive_scan_int(cnt, t.rp, t.nrows, &total, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(next, t.rp, sizeof(int) * ((size_t)t.nrows + 1), cudaMemcpyDeviceToDevice, s));
+    if (a.nnz > 0) {
+        k_transpose_scatter<<<grid_for(a.nrows), 256, 0, s>>>(a.nrows, a.rp, a.ci, a.v, next, tmp_k, tmp_v);
+        AMG_LAUNCH_CHECK();
+        k_sort_segments<<<grid_for((long long)t.nrows * 32), 256, 0, s>>>(t.nrows, t.rp, tmp_k, tmp_v, t.ci, t.v);
+        AMG_LAUNCH_CHECK();
+    }
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));  // scratch is freed on return
+    return AMG_OK;
+}
+
+// ===========================================================================
+// Validation and diagonal
+// ===========================================================================
+
+// Per row, the first violation in storage order: code 1 = bad CSR, 2 = zero
+// or missing diagonal.  The lowest failing row wins (key = row * 4 + code).
+__global__ void k_validate(int n, long long nnz, const int *rp, const int *ci, const double *v, int *diag_pos,
+                           unsigned long long *first_err) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int code = 0;
+        const int s = rp[i], e = rp[i + 1];
+        int dpos = -1;
+        if (e < s || s < 0 || (long long)e > nnz) {
+            code = 1;
+        } else {
+            for (int k = s; k < e; ++k) {
+                const int c = ci[k];
+                if (c < 0 || c >= n || (k > s && c <= ci[k - 1])) { code = 1; break; }
+                if (c == i) {
+                    dpos = k;
+                    if (v[k] == 0.0) { code = 2; break; }
+                }
+            }
+            if (!code && dpos < 0) code = 2;
+        }
+        diag_pos[i] = dpos;
+        if (code) atomicMin(first_err, (unsigned long long)i * 4ull + (unsigned long long)code);
+    }
+}
+
+__global__ void k_find_diag(int n, const int *rp, const int *ci, const double *v, double *diag, int *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k)
+            if (ci[k] == i) { d = v[k]; break; }
+        diag[i] = d;
+        if (d == 0.0) atomicExch(bad, 1);
+    }
+}
+
+// Bitwise comparison of A and its transpose (symmetry detection).
+__global__ void k_compare_csr(int n, long long nnz, const int *rp1, const int *ci1, const double *v1,
+                              const int *rp2, const int *ci2, const double *v2, int *differ) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz + n + 1;
+         k += (long long)gridDim.x * blockDim.x) {
+        bool d;
+        if (k < nnz)
+            d = ci1[k] != ci2[k] || __double_as_longlong(v1[k]) != __double_as_longlong(v2[k]);
+        else
+            d = rp1[k - nnz] != rp2[k - nnz];
+        if (d) atomicExch(differ, 1);
+    }
+}
+
+// ===========================================================================
+// Strength of connection
+// ===========================================================================
+
+__device__ __forceinline__ bool strong_link(double aij, double aii, double ajj, double t2) {
+    const double lhs = __dmul_rn(aij, aij);
+    const double prod = __dmul_rn(aii, ajj);
+    const double rhs = __dmul_rn(t2, fabs(prod));
+    return lhs >= rhs;
+}
+
+template <bool FILL>
+__global__ void k_strength(int n, const int *rp, const int *ci, const double *v, const double *diag, double t2,
+                           int *cnt, const int *srp, int *sci) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double aii = diag[i];
+        int c = 0;
+        int pos = FILL ? srp[i] : 0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const int j = ci[k];
+            if (j == i) continue;
+            if (strong_link(v[k], aii, diag[j], t2)) {
+                if (FILL) sci[pos++] = j;
+                else c++;
+            }
+        }
+        if (!FILL) cnt[i] = c;
+    }
+}
+
+// Union of two ascending column lists per row.
+template <bool FILL>
+__global__ void k_union(int n, const int *arp, const int *aci, const int *brp, const int *bci, int *cnt,
+                        const int *orp, int *oci) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int p = arp[i], pe = arp[i + 1], q = brp[i], qe = brp[i + 1];
+        int pos = FILL ? orp[i] : 0, c = 0;
+        while (p < pe || q < qe) {
+            int col;
+            if (q >= qe || (p < pe && aci[p] < bci[q])) col = aci[p++];
+            else if (p >= pe || bci[q] < aci[p]) col = bci[q++];
+            else { col = aci[p]; ++p; ++q; }
+            if (FILL) oci[pos++] = col;
+            else c++;
+        }
+        if (!FILL) cnt[i] = c;
+    }
+}
+
+// ===========================================================================
+// Distance-2 maximal independent set by synchronous rounds
+// ===========================================================================
+// Node tuple = (state << 32) | fmix32(local index), state IN = 2 > UNDECIDED = 1
+// > OUT = 0.  fmix32 (MurmurHash3's finaliser) is a bijection of 32-bit words,
+// and two nodes within distance 2 always belong to the same system, so tuples
+// within any neighbourhood are distinct.
+
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__global__ void k_mis_init(int n, const int *row_start, unsigned long long *t) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int local = row_start ? i - row_start[i] : i;
+        t[i] = (1ull << 32) | (unsigned long long)fmix32((uint32_t)local);
+    }
+}
+
+__global__ void k_mis_max(int n, const int *srp, const int *sci, const unsigned long long *in,
+                          unsigned long long *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned long long m = in[i];
+        for (int p = srp[i]; p < srp[i + 1]; ++p) m = max(m, in[sci[p]]);
+        out[i] = m;
+    }
+}
+
+__global__ void k_mis_update(int n, const int *srp, const int *sci, const unsigned long long *m1,
+                             unsigned long long *t, int *undecided) {
+    int und = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long ti = t[i];
+        if ((ti >> 32) != 1ull) continue;
+        unsigned long long m = m1[i];
+        for (int p = srp[i]; p < srp[i + 1]; ++p) m = max(m, m1[sci[p]]);
+        if (m == ti) t[i] = (2ull << 32) | (ti & 0xffffffffull);
+        else if ((m >> 32) == 2ull) t[i] = ti & 0xffffffffull;
+        else und++;
+    }
+    und = __reduce_add_sync(0xffffffffu, und);
+    if ((threadIdx.x & 31) == 0 && und) atomicAdd(undecided, und);
+}
+
+// ===========================================================================
+// Aggregation
+// ===========================================================================
+
+__global__ void k_root_flags(int n, const unsigned long long *t, int *flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flag[i] = (t[i] >> 32) == 2ull;
+}
+
+// Phases 1-2: roots take their id; a non-root adjacent to a root takes that
+// root's aggregate (unique: roots are at least 3 apart).
+__global__ void k_agg_phase12(int n, const int *srp, const int *sci, const unsigned long long *t,
+                              const int *root_id, int *snap) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int a = -1;
+        if ((t[i] >> 32) == 2ull) {
+            a = root_id[i];
+        } else {
+            for (int p = srp[i]; p < srp[i + 1]; ++p) {
+                const int j = sci[p];
+                if ((t[j] >> 32) == 2ull) { a = root_id[j]; break; }
+            }
+        }
+        snap[i] = a;
+    }
+}
+
+// Phase 3: an unassigned node joins the aggregate of the phase-2-assigned
+// strong neighbour j with the largest |a_ij| (0 when (i,j) is not stored);
+// ties go to the smallest j.  Reads only the phase-2 snapshot.
+__global__ void k_agg_phase3(int n, const int *rp, const int *ci, const double *v, const int *srp,
+                             const int *sci, const int *snap, int *agg, int *unassigned) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int a = snap[i];
+        if (a < 0) {
+            int best = -1;
+            double bw = -1.0;
+            int k = rp[i];
+            const int ke = rp[i + 1];
+            for (int p = srp[i]; p < srp[i + 1]; ++p) {
+                const int j = sci[p];
+                while (k < ke && ci[k] < j) ++k;  // both lists ascend
+                if (snap[j] < 0) continue;
+                const double w = (k < ke && ci[k] == j) ? fabs(v[k]) : 0.0;
+                if (w > bw) { bw = w; best = j; }
+            }
+            a = best >= 0 ? snap[best] : -1;
+        }
+        agg[i] = a;
+        unassigned[i] = a < 0;
+    }
+}
+
+__global__ void k_agg_singletons(int n, const int *rank, int base, int *agg) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (agg[i] < 0) agg[i] = base + rank[i];
+}
+
+// ===========================================================================
+// Prolongator pieces
+// ===========================================================================
+
+// rho_i = (sum_j |a_ij| in storage order) / |a_ii|; the maximum is taken over
+// the bit patterns (non-negative doubles order like their bits).
+__global__ void k_gershgorin(int n, const int *rp, const double *v, const double *diag,
+                             unsigned long long *rho_bits) {
+    unsigned long long m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) s = __dadd_rn(s, fabs(v[k]));
+        const double q = __ddiv_rn(s, fabs(diag[i]));
+        m = max(m, (unsigned long long)__double_as_longlong(q));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(rho_bits, m);
+}
+
+__global__ void k_smoother_weights(int n, const int *rp, const double *v, const double *diag, double omega,
+                                   int l1, double *w) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (l1) {
+            double s = 0.0;
+            for (int k = rp[i]; k < rp[i + 1]; ++k) s = __dadd_rn(s, fabs(v[k]));
+            w[i] = __ddiv_rn(1.0, s);
+        } else {
+            w[i] = __ddiv_rn(omega, diag[i]);
+        }
+    }
+}
+
+// ===========================================================================
+// Row-wise SpGEMM C = X Y with a per-warp hash accumulator in shared memory
+// ===========================================================================
+// One warp builds one row of C.  The entries of row i of X are taken one at a
+// time in storage (ascending column) order; the lanes spread over the
+// matching row of Y, whose columns are distinct, so within a step no two
+// lanes touch the same accumulator.  Hence for each (i, J) the products
+// x_ik y_kJ are added in increasing k, starting from +0.0, each product and
+// sum rounded separately: the order the FP64 reference computes in.
+// Symbolic pass: counts distinct columns.  Numeric pass: values, then the row
+// is compacted and sorted by column (rank counting) and written.
+// A row whose distinct count does not fit the table is listed in `overflow`
+// and redone by a second launch with one larger table per block.
+
+constexpr int SPG_EMPTY = -1;
+
+enum { EPI_NONE = 0, EPI_PROLONG = 1 };
+
+struct ProlongEpi {
+    const int *agg;      // aggregate of each fine row
+    const double *diag;  // a_ii
+    double omega_p;      // (4/3) / rho
+};
+
+template <bool NUMERIC, int EPI>
+__global__ void k_spgemm(int nrows, const int *xrp, const int *xci, const double *xv, const int *yrp,
+                         const int *yci, const double *yv, int hcap, const int *row_list, int nlist,
+                         int *cnt_out, const int *crp, int *cci, double *cv, ProlongEpi epi, int *overflow_rows,
+                         int *overflow_count) {
+    extern __shared__ unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    int *keys = reinterpret_cast<int *>(smem_raw) + (size_t)wib * hcap;
+    double *vals = reinterpret_cast<double *>(smem_raw + (size_t)wpb * hcap * sizeof(int)) + (size_t)wib * hcap;
+    const int mask = hcap - 1;
+    const int nwork = row_list ? nlist : nrows;
+    for (int w = blockIdx.x * wpb + wib; w < nwork; w += gridDim.x * wpb) {
+        const int i = row_list ? row_list[w] : w;
+        for (int s = lane; s < hcap; s += 32) {
+            keys[s] = SPG_EMPTY;
+            if (NUMERIC) vals[s] = 0.0;
+        }
+        __syncwarp();
+        bool ovf = false;
+        const int pe = xrp[i + 1];
+        for (int p = xrp[i]; p < pe && !ovf; ++p) {
+            const int k = xci[p];
+            const double xk = NUMERIC ? (xv ? xv[p] : 1.0) : 0.0;
+            const int qe = yrp[k + 1];
+            for (int q0 = yrp[k]; q0 < qe; q0 += 32) {
+                const int q = q0 + lane;
+                bool lane_ovf = false;
+                if (q < qe) {
+                    const int J = yci[q];
+                    unsigned h = ((unsigned)J * 2654435761u) & (unsigned)mask;
+                    int probes = 0;
+                    int slot = -1;
+                    while (probes < hcap) {
+                        int cur = keys[h];
+                        if (cur == J) { slot = (int)h; break; }
+                        if (cur == SPG_EMPTY) {
+                            int prev = atomicCAS(&keys[h], SPG_EMPTY, J);
+                            if (prev == SPG_EMPTY || prev == J) { slot = (int)h; break; }
+                        }
+                        h = (h + 1) & (unsigned)mask;
+                        ++probes;
+                    }
+                    if (slot < 0) lane_ovf = true;
+                    else if (NUMERIC) {
+                        const double yJ = yv ? yv[q] : 1.0;
+                        vals[slot] = __dadd_rn(vals[slot], __dmul_rn(xk, yJ));
+                    }
+                }
+                __syncwarp();
+                if (__any_sync(0xffffffffu, lane_ovf)) { ovf = true; break; }
+            }
+        }
+        // count (and compact in place, preserving slot order)
+        int count = 0;
+        if (!ovf) {
+            for (int base = 0; base < hcap; base += 32) {
+                const int s = base + lane;
+                const int key = keys[s];
+                double val = NUMERIC ? vals[s] : 0.0;
+                const unsigned ball = __ballot_sync(0xffffffffu, key != SPG_EMPTY);
+                const int pos = count + __popc(ball & ((1u << lane) - 1u));
+                __syncwarp();
+                if (key != SPG_EMPTY) {
+                    keys[pos] = key;
+                    if (NUMERIC) vals[pos] = val;
+                }
+                __syncwarp();
+                count += __popc(ball);
+            }
+            // A table filled beyond 3/4 is treated as an overflow so that probing stays short.
+            if (count > (hcap * 3) / 4) ovf = true;
+        }
+        if (ovf) {
+            if (lane == 0) {
+                int slot_o = atomicAdd(overflow_count, 1);
+                overflow_rows[slot_o] = i;
+            }
+            __syncwarp();
+            continue;
+        }
+        if (!NUMERIC) {
+            if (lane == 0) cnt_out[i] = count;
+        } else {
+            const int out0 = crp[i];
+            for (int a = lane; a < count; a += 32) {
+                const int key = keys[a];
+                int rank = 0;
+                for (int b = 0; b < count; ++b) rank += keys[b] < key;
+                double val = vals[a];
+                if (EPI == EPI_PROLONG) {
+                    const double t = __ddiv_rn(val, epi.diag[i]);
+                    const double delta = (key == epi.agg[i]) ? 1.0 : 0.0;
+                    val = __dsub_rn(delta, __dmul_rn(epi.omega_p, t));
+                }
+                cci[out0 + rank] = key;
+                cv[out0 + rank] = val;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// C = X Y (X: nrows x *, Y: * x ncols).  xv/yv may be null (all ones).
+template <int EPI>
+static int spgemm(int nrows, int ncols, const int *xrp, const int *xci, const double *xv, const int *yrp,
+                  const int *yci, const double *yv, ProlongEpi epi, DevCSR &C, DevArena &arena, cudaStream_t s) {
+    C.nrows = nrows;
+    C.ncols = ncols;
+    Scratch sc;
+    int *cnt, *ovf_rows, *ovf_cnt;
+    AMG_TRY(sc.alloc(&cnt, (size_t)nrows + 1));
+    AMG_TRY(sc.alloc(&ovf_rows, (size_t)nrows + 1));
+    AMG_TRY(sc.alloc(&ovf_cnt, 2));
+    AMG_TRY(arena.alloc(&C.rp, (size_t)nrows + 1));
+    const int small_cap = 512, warps = 8;
+    const size_t small_smem = (size_t)warps * small_cap * (sizeof(int) + sizeof(double));
+    int big_cap = 8192;
+    size_t big_smem = (size_t)big_cap * (sizeof(int) + sizeof(double));
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    while (big_smem > (size_t)optin && big_cap > 1024) {
+        big_cap >>= 1;
+        big_smem = (size_t)big_cap * (sizeof(int) + sizeof(double));
+    }
+    AMG_CUDA_TRY(cudaFuncSetAttribute(k_spgemm<false, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem));
+    AMG_CUDA_TRY(cudaFuncSetAttribute(k_spgemm<true, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem));
+
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool numeric = pass == 1;
+        AMG_CUDA_TRY(cudaMemsetAsync(ovf_cnt, 0, sizeof(int), s));
+        const int blocks = (int)std::min<long long>((nrows + warps - 1) / warps, (long long)num_sms() * 8);
+        if (!numeric)
+            k_spgemm<false, EPI><<<std::max(blocks, 1), warps * 32, small_smem, s>>>(
+                nrows, xrp, xci, xv, yrp, yci, yv, small_cap, nullptr, 0, cnt, nullptr, nullptr, nullptr, epi,
+                ovf_rows, ovf_cnt);
+        else
+            k_spgemm<true, EPI><<<std::max(blocks, 1), warps * 32, small_smem, s>>>(
+                nrows, xrp, xci, xv, yrp, yci, yv, small_cap, nullptr, 0, nullptr, C.rp, C.ci, C.v, epi, ovf_rows,
+                ovf_cnt);
+        AMG_LAUNCH_CHECK();
+        int novf = 0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&novf, ovf_cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (novf > 0) {
+            AMG_CUDA_TRY(cudaMemsetAsync(ovf_cnt, 0, sizeof(int), s));
+            int *ovf2;
+            AMG_TRY(sc.alloc(&ovf2, (size_t)novf + 1));
+            const int blocks2 = std::min(novf, num_sms() * 2);
+            if (!numeric)
+                k_spgemm<false, EPI><<<blocks2, 32, big_smem, s>>>(nrows, xrp, xci, xv, yrp, yci, yv, big_cap,
+                                                                   ovf_rows, novf, cnt, nullptr, nullptr, nullptr,
+                                                                   epi, ovf2, ovf_cnt);
+            else
+                k_spgemm<true, EPI><<<blocks2, 32, big_smem, s>>>(nrows, xrp, xci, xv, yrp, yci, yv, big_cap,
+                                                                  ovf_rows, novf, nullptr, C.rp, C.ci, C.v, epi,
+                                                                  ovf2, ovf_cnt);
+            AMG_LAUNCH_CHECK();
+            int novf2 = 0;
+            AMG_CUDA_TRY(cudaMemcpyAsync(&novf2, ovf_cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+            AMG_CUDA_TRY(cudaStreamSynchronize(s));
+            if (novf2 > 0) {
+                set_last_error("a product row has more than %d distinct columns", (big_cap * 3) / 4);
+                return AMG_ERR_UNSUPPORTED;
+            }
+        }
+        if (!numeric) {
+            int total = 0;
+            AMG_TRY(exclusive_scan_int(cnt, C.rp, nrows, &total, s));
+            C.nnz = total;
+            AMG_TRY(arena.alloc(&C.ci, (size_t)std::max(1, total)));
+            AMG_TRY(arena.alloc(&C.v, (size_t)std::max(1, total)));
+        }
+    }
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+// ===========================================================================
+// Dense coarsest level: factor (Cholesky if symmetric, else LU with partial
+// pivoting) and explicit inverse, one thread block, FP64.
+// ===========================================================================
+
+__global__ void k_csr_to_dense(int n, const int *rp, const int *ci, const double *v, double *d) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * n; i += gridDim.x * blockDim.x) d[i] = 0.0;
+    __syncthreads();
+    // one block
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int k = rp[i]; k < rp[i + 1]; ++k) d[(size_t)i * n + ci[k]] = v[k];
+}
+
+__global__ void k_dense_factor_inverse(int n, int symmetric, double *a, int *piv, double *inv, int *status) {
+    __shared__ int s_piv;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    if (symmetric) {
+        for (int j = 0; j < n; ++j) {
+            if (tid == 0) {
+                double d = a[(size_t)j * n + j];
+                for (int k = 0; k < j; ++k) d -= a[(size_t)j * n + k] * a[(size_t)j * n + k];
+                if (!(d > 0.0)) s_fail = 1;
+                else a[(size_t)j * n + j] = sqrt(d);
+            }
+            __syncthreads();
+            if (s_fail) break;
+            const double ljj = a[(size_t)j * n + j];
+            for (int i = j + 1 + tid; i < n; i += nt) {
+                double s = a[(size_t)i * n + j];
+                for (int k = 0; k < j; ++k) s -= a[(size_t)i * n + k] * a[(size_t)j * n + k];
+                a[(size_t)i * n + j] = s / ljj;
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int k = 0; k < n; ++k) {
+            if (tid == 0) {
+                int p = k;
+                double best = fabs(a[(size_t)k * n + k]);
+                for (int i = k + 1; i < n; ++i) {
+                    const double c = fabs(a[(size_t)i * n + k]);
+                    if (c > best) { best = c; p = i; }
+                }
+                s_piv = p;
+                piv[k] = p;
+                if (best == 0.0) s_fail = 1;
+            }
+            __syncthreads();
+            if (s_fail) break;
+            const int p = s_piv;
+            if (p != k)
+                for (int j = tid; j < n; j += nt) {
+                    const double t = a[(size_t)k * n + j];
+                    a[(size_t)k * n + j] = a[(size_t)p * n + j];
+                    a[(size_t)p * n + j] = t;
+                }
+            __syncthreads();
+            for (int i = k + 1 + tid; i < n; i += nt) a[(size_t)i * n + k] /= a[(size_t)k * n + k];
+            __syncthreads();
+            for (int idx = tid; idx < (n - k - 1) * (n - k - 1); idx += nt) {
+                const int i = k + 1 + idx / (n - k - 1), j = k + 1 + idx % (n - k - 1);
+                a[(size_t)i * n + j] -= a[(size_t)i * n + k] * a[(size_t)k * n + j];
+            }
+            __syncthreads();
+        }
+    }
+    if (s_fail) {
+        if (tid == 0) *status = AMG_NOT_SPD;
+        return;
+    }
+    // inverse: column c of inv solves A x = e_c (one thread per column)
+    for (int c = tid; c < n; c += nt) {
+        double *x = inv + (size_t)c;  // column c, stride n
+        for (int i = 0; i < n; ++i) x[(size_t)i * n] = (i == c) ? 1.0 : 0.0;
+        if (symmetric) {
+            for (int i = 0; i < n; ++i) {
+                double s = x[(size_t)i * n];
+                for (int k = 0; k < i; ++k) s -= a[(size_t)i * n + k] * x[(size_t)k * n];
+                x[(size_t)i * n] = s / a[(size_t)i * n + i];
+            }
+            for (int i = n - 1; i >= 0; --i) {
+                double s = x[(size_t)i * n];
+                for (int k = i + 1; k < n; ++k) s -= a[(size_t)k * n + i] * x[(size_t)k * n];
+                x[(size_t)i * n] = s / a[(size_t)i * n + i];
+            }
+        } else {
+            for (int k = 0; k < n; ++k) {
+                const int p = piv[k];
+                if (p != k) {
+                    const double t = x[(size_t)k * n];
+                    x[(size_t)k * n] = x[(size_t)p * n];
+                    x[(size_t)p * n] = t;
+                }
+            }
+            for (int i = 0; i < n; ++i) {
+                double s = x[(size_t)i * n];
+                for (int k = 0; k < i; ++k) s -= a[(size_t)i * n + k] * x[(size_t)k * n];
+                x[(size_t)i * n] = s;
+            }
+            for (int i = n - 1; i >= 0; --i) {
+                double s = x[(size_t)i * n];
+                for (int k = i + 1; k < n; ++k) s -= a[(size_t)i * n + k] * x[(size_t)k * n];
+                x[(size_t)i * n] = s / a[(size_t)i * n + i];
+            }
+        }
+    }
+    if (tid == 0) *status = AMG_OK;
+}
+
+// ===========================================================================
+// Hierarchy construction
+// ===========================================================================
+
+static int choose_vec(long long nnz, int nrows) {
+    const double mean = nrows > 0 ? (double)nnz / nrows : 1.0;
+    int v = 2;
+    while (v < 32 && v < mean) v <<= 1;
+    return v;
+}
+
+int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const double *v_in, cudaStream_t s) {
+    const amg_config &cfg = h->cfg;
+    const int n = h->n;
+    const long long nnz = h->nnz;
+    DevArena &ar = h->arena;
+
+    // ---- level 0: copy and validate ----
+    Level &L0 = h->L[0];
+    L0.A.nrows = L0.A.ncols = n;
+    L0.A.nnz = nnz;
+    AMG_TRY(ar.alloc(&L0.A.rp, (size_t)n + 1));
+    AMG_TRY(ar.alloc(&L0.A.ci, (size_t)nnz));
+    AMG_TRY(ar.alloc(&L0.A.v, (size_t)nnz));
+    AMG_CUDA_TRY(cudaMemcpyAsync(L0.A.rp, rp_in, sizeof(int) * ((size_t)n + 1), cudaMemcpyDefault, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(L0.A.ci, ci_in, sizeof(int) * (size_t)nnz, cudaMemcpyDefault, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(L0.A.v, v_in, sizeof(double) * (size_t)nnz, cudaMemcpyDefault, s));
+    int ends[2] = {0, 0};
+    AMG_CUDA_TRY(cudaMemcpyAsync(&ends[0], L0.A.rp, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(&ends[1], L0.A.rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (ends[0] != 0 || (long long)ends[1] != nnz) {
+        set_last_error("row_ptr[0] = %d, row_ptr[n] = %d, nnz = %lld", ends[0], ends[1], nnz);
+        return AMG_ERR_BAD_CSR;
+    }
+    {
+        Scratch sc;
+        int *dpos;
+        unsigned long long *err;
+        AMG_TRY(sc.alloc(&dpos, (size_t)n));
+        AMG_TRY(sc.alloc(&err, 1));
+        unsigned long long init = ~0ull;
+        AMG_CUDA_TRY(cudaMemcpyAsync(err, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+        k_validate<<<grid_for(n), 256, 0, s>>>(n, nnz, L0.A.rp, L0.A.ci, L0.A.v, dpos, err);
+        AMG_LAUNCH_CHECK();
+        unsigned long long first = 0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&first, err, sizeof(first), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (first != ~0ull) {
+            const int row = (int)(first >> 2), code = (int)(first & 3);
+            set_last_error("invalid CSR at row %d (%s)", row, code == 1 ? "bad structure" : "zero or missing diagonal");
+            return code == 1 ? AMG_ERR_BAD_CSR : AMG_ERR_ZERO_DIAG;
+        }
+    }
+
+    // ---- symmetry ----
+    if (cfg.symmetric >= 0) {
+        h->symmetric = cfg.symmetric;
+    } else {
+        DevArena tmp;
+        DevCSR At;
+        int rc = transpose_csr(L0.A, At, tmp, s);
+        if (rc < 0) { tmp.free_all(); return rc; }
+        int *differ = nullptr;
+        rc = tmp.alloc(&differ, 1);
+        if (rc < 0) { tmp.free_all(); return rc; }
+        cudaMemsetAsync(differ, 0, sizeof(int), s);
+        k_compare_csr<<<grid_for(nnz + n + 1), 256, 0, s>>>(n, nnz, L0.A.rp, L0.A.ci, L0.A.v, At.rp, At.ci, At.v,
+                                                             differ);
+        int d = 1;
+        cudaMemcpyAsync(&d, differ, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        tmp.free_all();
+        AMG_CUDA_TRY(e);
+        h->symmetric = d ? 0 : 1;
+    }
+
+    // ---- levels ----
+    int l = 0;
+    for (;;) {
+        Level &Lv = h->L[l];
+        DevCSR &A = Lv.A;
+        const int nl = A.nrows;
+        Scratch sc;
+        double *diag;
+        int *bad;
+        AMG_TRY(sc.alloc(&diag, (size_t)nl));
+        AMG_TRY(sc.alloc(&bad, 1));
+        AMG_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        k_find_diag<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, diag, bad);
+        AMG_LAUNCH_CHECK();
+        int hbad = 0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hbad) {
+            set_last_error("level %d has a zero diagonal", l);
+            return AMG_ERR_ZERO_DIAG;
+        }
+        AMG_TRY(ar.alloc(&Lv.w, (size_t)nl));
+        k_smoother_weights<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.v, diag, cfg.omega,
+                                                        cfg.smoother == AMG_SMOOTHER_L1_JACOBI, Lv.w);
+        AMG_LAUNCH_CHECK();
+        if (nl <= cfg.coarse_max || l + 1 >= cfg.max_levels || l + 1 >= AMG_MAX_LEVELS) break;
+
+        // strength
+        const double theta_l = ldexp(cfg.theta, -l);
+        const double t2 = theta_l * theta_l;
+        int *cnt, *s1rp, *s1ci, *srp, *sci;
+        AMG_TRY(sc.alloc(&cnt, (size_t)nl + 1));
+        AMG_TRY(sc.alloc(&s1rp, (size_t)nl + 1));
+        k_strength<false><<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, diag, t2, cnt, nullptr, nullptr);
+        AMG_LAUNCH_CHECK();
+        int s1nnz = 0;
+        AMG_TRY(exclusive_scan_int(cnt, s1rp, nl, &s1nnz, s));
+        AMG_TRY(sc.alloc(&s1ci, (size_t)std::max(1, s1nnz)));
+        k_strength<true><<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, diag, t2, nullptr, s1rp, s1ci);
+        AMG_LAUNCH_CHECK();
+        DevCSR S1;
+        S1.nrows = S1.ncols = nl;
+        S1.nnz = s1nnz;
+        S1.rp = s1rp;
+        S1.ci = s1ci;
+        DevCSR S1t;
+        AMG_TRY(transpose_csr(S1, S1t, sc.arena, s));
+        AMG_TRY(sc.alloc(&srp, (size_t)nl + 1));
+        k_union<false><<<grid_for(nl), 256, 0, s>>>(nl, s1rp, s1ci, S1t.rp, S1t.ci, cnt, nullptr, nullptr);
+        AMG_LAUNCH_CHECK();
+        int snnz = 0;
+        AMG_TRY(exclusive_scan_int(cnt, srp, nl, &snnz, s));
+        AMG_TRY(sc.alloc(&sci, (size_t)std::max(1, snnz)));
+        k_union<true><<<grid_for(nl), 256, 0, s>>>(nl, s1rp, s1ci, S1t.rp, S1t.ci, nullptr, srp, sci);
+        AMG_LAUNCH_CHECK();
+
+        // distance-2 MIS
+        unsigned long long *t, *m1;
+        int *und;
+        AMG_TRY(sc.alloc(&t, (size_t)nl));
+        AMG_TRY(sc.alloc(&m1, (size_t)nl));
+        AMG_TRY(sc.alloc(&und, 1));
+        k_mis_init<<<grid_for(nl), 256, 0, s>>>(nl, nullptr, t);
+        AMG_LAUNCH_CHECK();
+        int rounds = 0, hund = 1;
+        while (hund > 0) {
+            if (++rounds > 100000) {
+                set_last_error("independent-set rounds did not terminate at level %d", l);
+                return AMG_ERR_STALL;
+            }
+            AMG_CUDA_TRY(cudaMemsetAsync(und, 0, sizeof(int), s));
+            k_mis_max<<<grid_for(nl), 256, 0, s>>>(nl, srp, sci, t, m1);
+            k_mis_update<<<grid_for(nl), 256, 0, s>>>(nl, srp, sci, m1, t, und);
+            AMG_LAUNCH_CHECK();
+            AMG_CUDA_TRY(cudaMemcpyAsync(&hund, und, sizeof(int), cudaMemcpyDeviceToHost, s));
+            AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+
+        // aggregates
+        int *flag, *root_id, *snap, *rank;
+        AMG_TRY(sc.alloc(&flag, (size_t)nl + 1));
+        AMG_TRY(sc.alloc(&root_id, (size_t)nl + 1));
+        AMG_TRY(sc.alloc(&snap, (size_t)nl));
+        AMG_TRY(sc.alloc(&rank, (size_t)nl + 1));
+        AMG_TRY(ar.alloc(&Lv.agg, (size_t)nl));
+        k_root_flags<<<grid_for(nl), 256, 0, s>>>(nl, t, flag);
+        AMG_LAUNCH_CHECK();
+        int nroots = 0;
+        AMG_TRY(exclusive_scan_int(flag, root_id, nl, &nroots, s));
+        k_agg_phase12<<<grid_for(nl), 256, 0, s>>>(nl, srp, sci, t, root_id, snap);
+        k_agg_phase3<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, srp, sci, snap, Lv.agg, flag);
+        AMG_LAUNCH_CHECK();
+        int nsingle = 0;
+        AMG_TRY(exclusive_scan_int(flag, rank, nl, &nsingle, s));
+        if (nsingle > 0) {
+            k_agg_singletons<<<grid_for(nl), 256, 0, s>>>(nl, rank, nroots, Lv.agg);
+            AMG_LAUNCH_CHECK();
+        }
+        const int nc = nroots + nsingle;
+        if (nc >= nl) {  // coarsening stalled: this level is the last
+            ar.release(Lv.agg);
+            Lv.agg = nullptr;
+            break;
+        }
+
+        // prolongator P = (I - omega_P D^-1 A) T
+        unsigned long long *rho_bits;
+        AMG_TRY(sc.alloc(&rho_bits, 1));
+        AMG_CUDA_TRY(cudaMemsetAsync(rho_bits, 0, sizeof(unsigned long long), s));
+        k_gershgorin<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.v, diag, rho_bits);
+        AMG_LAUNCH_CHECK();
+        unsigned long long hb = 0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&hb, rho_bits, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        double rho;
+        memcpy(&rho, &hb, sizeof(rho));
+        Lv.rho = rho;
+        const double c43 = 4.0 / 3.0;
+        ProlongEpi epi{Lv.agg, diag, c43 / rho};
+        int *trp;
+        AMG_TRY(sc.alloc(&trp, (size_t)nl + 1));
+        k_iota<<<grid_for(nl + 1), 256, 0, s>>>(trp, nl + 1);
+        AMG_LAUNCH_CHECK();
+        AMG_TRY((spgemm<EPI_PROLONG>(nl, nc, A.rp, A.ci, A.v, trp, Lv.agg, nullptr, epi, Lv.P, ar, s)));
+        AMG_TRY(transpose_csr(Lv.P, Lv.R, ar, s));
+        // Galerkin A_c = R (A P)
+        DevCSR AP;
+        AMG_TRY((spgemm<EPI_NONE>(nl, nc, A.rp, A.ci, A.v, Lv.P.rp, Lv.P.ci, Lv.P.v, ProlongEpi{}, AP, sc.arena, s)));
+        Level &Ln = h->L[l + 1];
+        AMG_TRY((spgemm<EPI_NONE>(nc, nc, Lv.R.rp, Lv.R.ci, Lv.R.v, AP.rp, AP.ci, AP.v, ProlongEpi{}, Ln.A, ar, s)));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        ++l;
+    }
+    h->nlevels = l + 1;
+
+    // ---- coarsest level: dense factor + inverse ----
+    Level &Lc = h->L[l];
+    h->nc = Lc.A.nrows;
+    if (h->nc > AMG_DENSE_MAX) {
+        set_last_error("coarsening stopped at level %d with %d rows (> %d)", l, h->nc, AMG_DENSE_MAX);
+        return AMG_ERR_STALL;
+    }
+    {
+        Scratch sc;
+        double *dense;
+        int *piv, *st;
+        const int m = h->nc;
+        AMG_TRY(sc.alloc(&dense, (size_t)m * m));
+        AMG_TRY(sc.alloc(&piv, (size_t)m));
+        AMG_TRY(sc.alloc(&st, 1));
+        AMG_TRY(ar.alloc(&h->cinv, (size_t)m * m));
+        k_csr_to_dense<<<1, 256, 0, s>>>(m, Lc.A.rp, Lc.A.ci, Lc.A.v, dense);
+        k_dense_factor_inverse<<<1, 256, 0, s>>>(m, h->symmetric, dense, piv, h->cinv, st);
+        AMG_LAUNCH_CHECK();
+        int hst = -1;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hst != AMG_OK) {
+            set_last_error("coarsest level (%d rows) is not %s", m, h->symmetric ? "SPD" : "invertible");
+            return AMG_NOT_SPD;
+        }
+    }
+
+    // ---- FP32 copies, work vectors, launch shapes ----
+    const bool mixed = cfg.precision == AMG_PRECISION_MIXED;
+    for (int k = 0; k < h->nlevels; ++k) {
+        Level &Lv = h->L[k];
+        const int nl = Lv.A.nrows;
+        const bool last = k == h->nlevels - 1;
+        Lv.vec_a = choose_vec(Lv.A.nnz, nl);
+        if (!last) {
+            Lv.vec_p = choose_vec(Lv.P.nnz, nl);
+            Lv.vec_r = choose_vec(Lv.R.nnz, Lv.R.nrows);
+        }
+        AMG_TRY(ar.alloc(&Lv.t, (size_t)nl));
+        if (k > 0) {
+            AMG_TRY(ar.alloc(&Lv.b, (size_t)nl));
+            AMG_TRY(ar.alloc(&Lv.x, (size_t)nl));
+        }
+        if (mixed) {
+            AMG_TRY(ar.alloc(&Lv.A.v32, (size_t)std::max(1LL, Lv.A.nnz)));
+            k_to_f32<<<grid_for(Lv.A.nnz), 256, 0, s>>>(Lv.A.v, Lv.A.v32, Lv.A.nnz);
+            AMG_TRY(ar.alloc(&Lv.w32, (size_t)nl));
+            k_to_f32<<<grid_for(nl), 256, 0, s>>>(Lv.w, Lv.w32, nl);
+            if (!last) {
+                AMG_TRY(ar.alloc(&Lv.P.v32, (size_t)std::max(1LL, Lv.P.nnz)));
+                k_to_f32<<<grid_for(Lv.P.nnz), 256, 0, s>>>(Lv.P.v, Lv.P.v32, Lv.P.nnz);
+                AMG_TRY(ar.alloc(&Lv.R.v32, (size_t)std::max(1LL, Lv.R.nnz)));
+                k_to_f32<<<grid_for(Lv.R.nnz), 256, 0, s>>>(Lv.R.v, Lv.R.v32, Lv.R.nnz);
+            }
+            AMG_LAUNCH_CHECK();
+            AMG_TRY(ar.alloc(&Lv.t32, (size_t)nl));
+            if (k > 0) {
+                AMG_TRY(ar.alloc(&Lv.b32, (size_t)nl));
+                AMG_TRY(ar.alloc(&Lv.x32, (size_t)nl));
+            }
+        }
+    }
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+void free_hierarchy(Hierarchy *h) {
+    if (!h) return;
+    h->arena.free_all();
+}
+
+}  // namespace amg

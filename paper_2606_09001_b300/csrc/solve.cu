@@ -1,0 +1,944 @@
+// solve.cu -- solve phase: V(1,1) cycle, preconditioned CG and BiCGStab.
+//
+// Every kernel reads scal->done first and returns at once when the solve has
+// finished, so the host may launch iterations ahead of the convergence check.
+// Dot products are reduced deterministically: each block writes one partial
+// sum, and the last block to finish (ticket counter) adds the partials in
+// block order and updates the Krylov scalars on the device.
+#include <algorithm>
+#include <cstring>
+
+#include "solve.cuh"
+
+namespace amg {
+
+constexpr int BLOCK = 256;
+
+static int grid_rows(int n, int vec, int cap) {
+    const int rpb = BLOCK / vec;
+    return std::max(1, std::min((n + rpb - 1) / rpb, cap));
+}
+
+#define VEC_DISPATCH(vec, ...)                          \
+    switch (vec) {                                      \
+        case 2: { constexpr int V = 2; __VA_ARGS__; } break;   \
+        case 4: { constexpr int V = 4; __VA_ARGS__; } break;   \
+        case 8: { constexpr int V = 8; __VA_ARGS__; } break;   \
+        case 16: { constexpr int V = 16; __VA_ARGS__; } break; \
+        default: { constexpr int V = 32; __VA_ARGS__; } break; \
+    }
+
+// ---------------------------------------------------------------------------
+// Deterministic block reduction + last-block finisher
+// ---------------------------------------------------------------------------
+
+// Reduces NV values over the block, stores the block's partials, and returns
+// true in the last block to arrive, with tot[] = sum over blocks in block order
+// (valid in every thread of that block).
+template <int NV>
+__device__ bool reduce_last(double (&v)[NV], double *part, int cap, unsigned *counter, double (&tot)[NV]) {
+    __shared__ double sh[NV][BLOCK / 32];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double a = warp_sum(v[k]);
+        if (lane == 0) sh[k][wid] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double a = 0.0;
+            for (int w = 0; w < BLOCK / 32; ++w) a += sh[k][w];
+            part[k * cap + blockIdx.x] = a;
+        }
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += BLOCK) a += __ldcg(&part[k * cap + b]);
+        a = warp_sum(a);
+        __syncthreads();
+        if (lane == 0) sh[k][wid] = a;
+        __syncthreads();
+        double t = 0.0;
+        for (int w = 0; w < BLOCK / 32; ++w) t += sh[k][w];
+        tot[k] = t;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+__device__ __forceinline__ bool finite(double a) { return isfinite(a); }
+
+__device__ __forceinline__ void fail(DevScalars *sc, int status) {
+    sc->status = status;
+    sc->done = 1;
+}
+
+// ---------------------------------------------------------------------------
+// Loads (the V-cycle may read FP64 inputs into FP32 arithmetic)
+// ---------------------------------------------------------------------------
+
+template <typename TM, typename T>
+__device__ __forceinline__ TM ld(const T *p, int i) { return (TM)__ldg(p + i); }
+
+// ---------------------------------------------------------------------------
+// V-cycle kernels: VEC threads per row, grid-stride over warps so that every
+// lane of a warp runs the same number of iterations (shuffles are warp-wide).
+// ---------------------------------------------------------------------------
+
+#define ROW_LOOP(VEC, n)                                                                     \
+    const int lane_ = threadIdx.x & (VEC - 1);                                               \
+    const int rows_per_warp_ = 32 / VEC;                                                     \
+    const int warp_ = (blockIdx.x * BLOCK + threadIdx.x) >> 5;                               \
+    const int nwarps_ = (gridDim.x * BLOCK) >> 5;                                            \
+    const int sub_ = (threadIdx.x & 31) / VEC;                                               \
+    for (int base_ = warp_ * rows_per_warp_; base_ < (n); base_ += nwarps_ * rows_per_warp_) { \
+        const int i = base_ + sub_;                                                          \
+        const bool valid = i < (n);
+
+#define ROW_LOOP_END }
+
+// r = b - A (W b): pre-smoothing from x = 0 fused with the residual.
+template <int VEC, typename TB, typename TM>
+__global__ void __launch_bounds__(BLOCK) k_presmooth(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                     const TM *__restrict__ v, const TM *__restrict__ w,
+                                                     const TB *__restrict__ b, TM *__restrict__ r, const int *done) {
+    if (*done) return;
+    ROW_LOOP(VEC, n)
+    TM s = 0;
+    if (valid) {
+        const int e = rp[i + 1];
+        for (int k = rp[i] + lane_; k < e; k += VEC) {
+            const int j = ci[k];
+            s += v[k] * (ld<TM>(w, j) * ld<TM>(b, j));
+        }
+    }
+    s = group_sum<VEC>(s);
+    if (valid && lane_ == 0) r[i] = ld<TM>(b, i) - s;
+    ROW_LOOP_END
+}
+
+// y = M x (restriction by R = P^T, or any plain CSR product).
+template <int VEC, typename TX, typename TM, typename TY>
+__global__ void __launch_bounds__(BLOCK) k_spmv(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                const TM *__restrict__ v, const TX *__restrict__ x,
+                                                TY *__restrict__ y, const int *done) {
+    if (*done) return;
+    ROW_LOOP(VEC, n)
+    TM s = 0;
+    if (valid) {
+        const int e = rp[i + 1];
+        for (int k = rp[i] + lane_; k < e; k += VEC) s += v[k] * ld<TM>(x, ci[k]);
+    }
+    s = group_sum<VEC>(s);
+    if (valid && lane_ == 0) y[i] = (TY)s;
+    ROW_LOOP_END
+}
+
+// t = W b + P x_c: the pre-smoothed iterate (recomputed) plus the coarse correction.
+template <int VEC, typename TB, typename TM>
+__global__ void __launch_bounds__(BLOCK) k_prolong(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                   const TM *__restrict__ v, const TM *__restrict__ w,
+                                                   const TB *__restrict__ b, const TM *__restrict__ xc,
+                                                   TM *__restrict__ t, const int *done) {
+    if (*done) return;
+    ROW_LOOP(VEC, n)
+    TM s = 0;
+    if (valid) {
+        const int e = rp[i + 1];
+        for (int k = rp[i] + lane_; k < e; k += VEC) s += v[k] * xc[ci[k]];
+    }
+    s = group_sum<VEC>(s);
+    if (valid && lane_ == 0) t[i] = ld<TM>(w, i) * ld<TM>(b, i) + s;
+    ROW_LOOP_END
+}
+
+enum Fin { FIN_NONE = 0, FIN_PCG_BETA = 1 };
+
+// Finisher of the PCG preconditioner application: rz_new = r.z (and, for the
+// flexible form, z.r_old); beta = rz_new / rz (or (rz_new - z.r_old) / rz);
+// the first iteration after a (re)start uses beta = 0.
+__device__ void finish_pcg_beta(DevScalars *sc, const double *tot) {
+    const double rz_new = tot[0];
+    if (!finite(rz_new)) { fail(sc, AMG_NAN); return; }
+    double beta = 0.0;
+    if (!sc->first) {
+        const double num = sc->flexible ? rz_new - tot[1] : rz_new;
+        beta = num / sc->rz;
+    }
+    sc->first = 0;
+    sc->beta = beta;
+    sc->rz = rz_new;
+}
+
+// x = t + W (b - A t): post-smoothing.  FIN_PCG_BETA also reduces r.z (r = b,
+// the V-cycle input) and z.r_old, and finishes beta.
+template <int VEC, typename TB, typename TM, typename TO, int FIN>
+__global__ void __launch_bounds__(BLOCK) k_postsmooth(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                      const TM *__restrict__ v, const TM *__restrict__ w,
+                                                      const TB *__restrict__ b, const TM *__restrict__ t,
+                                                      TO *__restrict__ out, const double *__restrict__ rold,
+                                                      DevScalars *sc, double *part, int cap, unsigned *counter) {
+    if (sc->done) return;
+    double acc[2] = {0.0, 0.0};
+    ROW_LOOP(VEC, n)
+    TM s = 0;
+    if (valid) {
+        const int e = rp[i + 1];
+        for (int k = rp[i] + lane_; k < e; k += VEC) s += v[k] * t[ci[k]];
+    }
+    s = group_sum<VEC>(s);
+    if (valid && lane_ == 0) {
+        const TM bi = ld<TM>(b, i);
+        const TM xi = t[i] + ld<TM>(w, i) * (bi - s);
+        const TO o = (TO)xi;
+        out[i] = o;
+        if (FIN == FIN_PCG_BETA) {
+            acc[0] += (double)ld<double>(b, i) * (double)o;
+            if (rold) acc[1] += rold[i] * (double)o;
+        }
+    }
+    ROW_LOOP_END
+    if (FIN == FIN_PCG_BETA) {
+        double tot[2];
+        if (reduce_last<2>(acc, part, cap, counter, tot) && threadIdx.x == 0) finish_pcg_beta(sc, tot);
+    }
+}
+
+// Coarsest level: x = A_c^-1 b in FP64 with the stored dense inverse (one block).
+template <typename TI, typename TO, int FIN>
+__global__ void __launch_bounds__(BLOCK) k_coarse(int m, const double *__restrict__ cinv, const TI *__restrict__ b,
+                                                  TO *__restrict__ x, const double *__restrict__ rold,
+                                                  DevScalars *sc, double *part, int cap, unsigned *counter) {
+    if (sc->done) return;
+    __shared__ double sb[AMG_DENSE_MAX];
+    for (int i = threadIdx.x; i < m; i += BLOCK) sb[i] = (double)b[i];
+    __syncthreads();
+    double acc[2] = {0.0, 0.0};
+    for (int i = threadIdx.x; i < m; i += BLOCK) {
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s += cinv[(size_t)i * m + j] * sb[j];
+        const TO o = (TO)s;
+        x[i] = o;
+        if (FIN == FIN_PCG_BETA) {
+            acc[0] += sb[i] * (double)o;
+            if (rold) acc[1] += rold[i] * (double)o;
+        }
+    }
+    if (FIN == FIN_PCG_BETA) {
+        double tot[2];
+        if (reduce_last<2>(acc, part, cap, counter, tot) && threadIdx.x == 0) finish_pcg_beta(sc, tot);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Krylov kernels (FP64)
+// ---------------------------------------------------------------------------
+
+// PCG start: x = 0, r = b, p = 0, ||b||^2.
+__global__ void __launch_bounds__(BLOCK) k_pcg_init(int n, const double *__restrict__ b, double *x, double *r,
+                                                    double *p, double *rold, DevScalars *sc, double rtol,
+                                                    double *part, int cap, unsigned *counter) {
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+        const double bi = b[i];
+        x[i] = 0.0;
+        r[i] = bi;
+        p[i] = 0.0;
+        if (rold) rold[i] = 0.0;
+        acc[0] += bi * bi;
+    }
+    double tot[1];
+    if (reduce_last<1>(acc, part, cap, counter, tot) && threadIdx.x == 0) {
+        sc->bn2 = tot[0];
+        sc->tol2 = rtol * rtol * tot[0];
+        sc->rr = tot[0];
+        sc->iters = 0;
+        sc->beta = 0.0;
+        sc->first = 1;
+        sc->status = AMG_OK;
+        sc->done = 0;
+        if (!finite(tot[0])) fail(sc, AMG_NAN);
+        else if (tot[0] == 0.0) sc->done = 1;
+    }
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(BLOCK) k_pcg_p(int n, const double *__restrict__ z, double *p, const DevScalars *sc) {
+    if (sc->done) return;
+    const double beta = sc->beta;
+    if (beta == 0.0) {  // first step after a (re)start: p = z exactly
+        for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) p[i] = z[i];
+    } else {
+        for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) p[i] = z[i] + beta * p[i];
+    }
+}
+
+enum SpmvFin { SF_PCG_ALPHA = 0, SF_BICG_ALPHA = 1, SF_BICG_OMEGA = 2, SF_TRUE_RES = 3 };
+
+// y = A x fused with a finisher:
+//   SF_PCG_ALPHA : p.q           -> alpha = rz / p.q     (dvec = x)
+//   SF_BICG_ALPHA: r^.v          -> alpha = rho / r^.v  (dvec = r^)
+//   SF_BICG_OMEGA: t.s, t.t      -> omega = t.s / t.t   (dvec = s)
+//   SF_TRUE_RES  : y = b - A x,  ||y||^2 -> tr          (dvec = b)
+template <int VEC, int SF>
+__global__ void __launch_bounds__(BLOCK) k_spmv_fin(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                    const double *__restrict__ v, const double *__restrict__ x,
+                                                    double *__restrict__ y, const double *__restrict__ dvec,
+                                                    DevScalars *sc, double *part, int cap, unsigned *counter) {
+    if (SF != SF_TRUE_RES && sc->done) return;
+    double acc[2] = {0.0, 0.0};
+    ROW_LOOP(VEC, n)
+    double s = 0.0;
+    if (valid) {
+        const int e = rp[i + 1];
+        for (int k = rp[i] + lane_; k < e; k += VEC) s += v[k] * __ldg(x + ci[k]);
+    }
+    s = group_sum<VEC>(s);
+    if (valid && lane_ == 0) {
+        if (SF == SF_TRUE_RES) {
+            const double ri = dvec[i] - s;
+            y[i] = ri;
+            acc[0] += ri * ri;
+        } else {
+            y[i] = s;
+            if (SF == SF_PCG_ALPHA) acc[0] += x[i] * s;
+            if (SF == SF_BICG_ALPHA) acc[0] += dvec[i] * s;
+            if (SF == SF_BICG_OMEGA) { acc[0] += s * dvec[i]; acc[1] += s * s; }
+        }
+    }
+    ROW_LOOP_END
+    double tot[2];
+    if (reduce_last<2>(acc, part, cap, counter, tot) && threadIdx.x == 0) {
+        if (SF == SF_PCG_ALPHA) {
+            const double pq = tot[0];
+            if (!finite(pq)) fail(sc, AMG_NAN);
+            else if (pq <= 0.0) fail(sc, AMG_BREAKDOWN);
+            else { sc->pq = pq; sc->alpha = sc->rz / pq; }
+        } else if (SF == SF_BICG_ALPHA) {
+            const double rv = tot[0];
+            if (!finite(rv)) fail(sc, AMG_NAN);
+            else if (rv == 0.0) fail(sc, AMG_BREAKDOWN);
+            else { sc->rv = rv; sc->alpha = sc->rho / rv; }
+        } else if (SF == SF_BICG_OMEGA) {
+            const double ts = tot[0], tt = tot[1];
+            if (!finite(ts) || !finite(tt)) fail(sc, AMG_NAN);
+            else if (tt == 0.0) fail(sc, AMG_BREAKDOWN);
+            else { sc->ts = ts; sc->tt = tt; sc->omega = ts / tt; }
+        } else {
+            sc->tr = tot[0];
+        }
+    }
+}
+
+// x += alpha p; (r_old = r;) r -= alpha q; ||r||^2; convergence / iteration cap.
+__global__ void __launch_bounds__(BLOCK) k_pcg_update(int n, double *x, double *r, const double *__restrict__ p,
+                                                      const double *__restrict__ q, double *rold, DevScalars *sc,
+                                                      double *part, int cap, unsigned *counter) {
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+        x[i] += alpha * p[i];
+        const double ri = r[i];
+        if (rold) rold[i] = ri;
+        const double rn = ri - alpha * q[i];
+        r[i] = rn;
+        acc[0] += rn * rn;
+    }
+    double tot[1];
+    if (reduce_last<1>(acc, part, cap, counter, tot) && threadIdx.x == 0) {
+        sc->iters += 1;
+        sc->rr = tot[0];
+        if (!finite(tot[0])) fail(sc, AMG_NAN);
+        else if (tot[0] <= sc->tol2) sc->done = 1;
+        else if (sc->iters >= sc->max_iter) fail(sc, AMG_MAXIT);
+    }
+}
+
+// BiCGStab start: x = 0, r = r^ = b, p = v = 0, rho = b.b, rho_old = alpha = omega = 1.
+__global__ void __launch_bounds__(BLOCK) k_bicg_init(int n, const double *__restrict__ b, double *x, double *r,
+                                                     double *rh, double *p, double *v, DevScalars *sc, double rtol,
+                                                     double *part, int cap, unsigned *counter) {
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+        const double bi = b[i];
+        x[i] = 0.0;
+        r[i] = bi;
+        rh[i] = bi;
+        p[i] = 0.0;
+        v[i] = 0.0;
+        acc[0] += bi * bi;
+    }
+    double tot[1];
+    if (reduce_last<1>(acc, part, cap, counter, tot) && threadIdx.x == 0) {
+        sc->bn2 = tot[0];
+        sc->tol2 = rtol * rtol * tot[0];
+        sc->rr = tot[0];
+        sc->rho = tot[0];
+        sc->rho_old = 1.0;
+        sc->alpha = 1.0;
+        sc->omega = 1.0;
+        sc->iters = 0;
+        sc->status = AMG_OK;
+        sc->done = 0;
+        if (!finite(tot[0])) fail(sc, AMG_NAN);
+        else if (tot[0] == 0.0) sc->done = 1;
+    }
+}
+
+// Restart from the current x with r = r^ = b - A x (r already holds it).
+__global__ void __launch_bounds__(BLOCK) k_bicg_restart(int n, const double *__restrict__ r, double *rh, double *p,
+                                                        double *v, DevScalars *sc, double *part, int cap,
+                                                        unsigned *counter) {
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+        const double ri = r[i];
+        rh[i] = ri;
+        p[i] = 0.0;
+        v[i] = 0.0;
+        acc[0] += ri * ri;
+    }
+    double tot[1];
+    if (reduce_last<1>(acc, part, cap, counter, tot) && threadIdx.x == 0) {
+        sc->rr = tot[0];
+        sc->rho = tot[0];
+        sc->rho_old = 1.0;
+        sc->alpha = 1.0;
+        sc->omega = 1.0;
+        sc->status = AMG_OK;
+        sc->done = 0;
+        if (!finite(tot[0])) fail(sc, AMG_NAN);
+        else if (tot[0] == 0.0) sc->done = 1;
+    }
+}
+
+// p = r + beta (p - omega v), beta = (rho / rho_old)(alpha / omega); counts the iteration.
+__global__ void __launch_bounds__(BLOCK) k_bicg_p(int n, const double *__restrict__ r, double *p,
+                                                  const double *__restrict__ v, DevScalars *sc) {
+    if (sc->done) return;
+    const double beta = (sc->rho / sc->rho_old) * (sc->alpha / sc->omega);
+    const double omega = sc->omega;
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK)
+        p[i] = r[i] + beta * (p[i] - omega * v[i]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->iters += 1;
+}
+
+// s = r - alpha v; x += alpha p^; ||s||^2 (early exit when small).
+__global__ void __launch_bounds__(BLOCK) k_bicg_s(int n, const double *__restrict__ r, const double *__restrict__ v,
+                                                  double *s, double *x, const double *__restrict__ ph,
+                                                  DevScalars *sc, double *part, int cap, unsigned *counter) {
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+        const double si = r[i] - alpha * v[i];
+        s[i] = si;
+        x[i] += alpha * ph[i];
+        acc[0] += si * si;
+    }
+    double tot[1];
+    if (reduce_last<1>(acc, part, cap, counter, tot) && threadIdx.x == 0) {
+        sc->ss = tot[0];
+        sc->rr = tot[0];
+        if (!finite(tot[0])) fail(sc, AMG_NAN);
+        else if (tot[0] <= sc->tol2) sc->done = 1;
+    }
+}
+
+// x += omega s^; r = s - omega t; ||r||^2 and the next rho = r^.r.
+__global__ void __launch_bounds__(BLOCK) k_bicg_update(int n, double *x, const double *__restrict__ sh, double *r,
+                                                       const double *__restrict__ s, const double *__restrict__ t,
+                                                       const double *__restrict__ rh, DevScalars *sc, double *part,
+                                                       int cap, unsigned *counter) {
+    if (sc->done) return;
+    const double omega = sc->omega;
+    double acc[2] = {0.0, 0.0};
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+        x[i] += omega * sh[i];
+        const double ri = s[i] - omega * t[i];
+        r[i] = ri;
+        acc[0] += ri * ri;
+        acc[1] += rh[i] * ri;
+    }
+    double tot[2];
+    if (reduce_last<2>(acc, part, cap, counter, tot) && threadIdx.x == 0) {
+        sc->rr = tot[0];
+        if (!finite(tot[0]) || !finite(tot[1])) fail(sc, AMG_NAN);
+        else if (tot[0] <= sc->tol2) sc->done = 1;
+        else if (omega == 0.0 || tot[1] == 0.0) fail(sc, AMG_BREAKDOWN);
+        else if (sc->iters >= sc->max_iter) fail(sc, AMG_MAXIT);
+        else { sc->rho_old = sc->rho; sc->rho = tot[1]; }
+    }
+}
+
+__global__ void k_copy(int n, const double *__restrict__ a, double *b) {
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) b[i] = a[i];
+}
+
+// dA[k] = -lambda_i x_{col(k)} for every stored entry of row i.
+template <int VEC>
+__global__ void __launch_bounds__(BLOCK) k_grad_values(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                       const double *__restrict__ lambda,
+                                                       const double *__restrict__ x, double *__restrict__ dA) {
+    ROW_LOOP(VEC, n)
+    if (valid) {
+        const double li = -lambda[i];
+        const int e = rp[i + 1];
+        for (int k = rp[i] + lane_; k < e; k += VEC) dA[k] = li * __ldg(x + ci[k]);
+    }
+    ROW_LOOP_END
+}
+
+// Unpreconditioned CG: z is r itself; beta comes from r.r.
+__global__ void __launch_bounds__(BLOCK) k_cg_beta(int n, const double *__restrict__ r, DevScalars *sc, double *part,
+                                                   int cap, unsigned *counter) {
+    if (sc->done) return;
+    double acc[2] = {0.0, 0.0};
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) acc[0] += r[i] * r[i];
+    double tot[2];
+    if (reduce_last<2>(acc, part, cap, counter, tot) && threadIdx.x == 0) finish_pcg_beta(sc, tot);
+}
+
+// Host-chosen control fields of the device scalars.
+__global__ void k_set_control(DevScalars *sc, int done, int status, int flexible, int max_iter, int reset_iters) {
+    sc->done = done;
+    sc->status = status;
+    sc->flexible = flexible;
+    sc->max_iter = max_iter;
+    if (reset_iters) sc->iters = 0;
+}
+
+// The next preconditioner application starts a new recursion (beta = 0, p = z).
+__global__ void k_pcg_restart(DevScalars *sc) { sc->first = 1; }
+
+// ---------------------------------------------------------------------------
+// Tracing
+// ---------------------------------------------------------------------------
+
+int Profiler::find(const char *name, int level) {
+    for (size_t i = 0; i < recs.size(); ++i)
+        if (recs[i].level == level && strncmp(recs[i].name, name, sizeof(recs[i].name)) == 0) return (int)i;
+    Rec r;
+    memset(&r, 0, sizeof(r));
+    strncpy(r.name, name, sizeof(r.name) - 1);
+    r.level = level;
+    recs.push_back(r);
+    return (int)recs.size() - 1;
+}
+
+cudaEvent_t Profiler::event() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int Profiler::collect() {
+    for (const Pending &q : pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) recs[q.rec].ms += ms;
+        pool.push_back(q.a);
+        pool.push_back(q.b);
+    }
+    pending.clear();
+    return AMG_OK;
+}
+
+void Profiler::reset() {
+    collect();
+    recs.clear();
+    launches = 0;
+}
+
+void Profiler::destroy() {
+    collect();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+}
+
+ProfScope::ProfScope(Profiler *p_, cudaStream_t s_, const char *name, int level, double bytes) : p(p_), s(s_) {
+    if (!p) return;
+    p->launches++;
+    if (!p->on) return;
+    rec = p->find(name, level);
+    p->recs[rec].launches++;
+    p->recs[rec].bytes += bytes;
+    a = p->event();
+    cudaEventRecord(a, s);
+}
+
+ProfScope::~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = p->event();
+    cudaEventRecord(b, s);
+    p->pending.push_back({rec, a, b});
+}
+
+#define TRACE(name, level, bytes) ProfScope prof_scope_(&W.prof, s, name, level, (double)(bytes))
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+int workspace_init(Workspace &W, int n) {
+    W.n = n;
+    DevArena &a = W.arena;
+    double **vecs[] = {&W.b, &W.x, &W.r, &W.z, &W.p, &W.q, &W.rold, &W.rh, &W.v, &W.ph, &W.s, &W.sh, &W.t, &W.aux};
+    for (double **pp : vecs) AMG_TRY(a.alloc(pp, (size_t)n));
+    AMG_TRY(a.alloc(&W.scal, 1));
+    W.part_cap = num_sms() * 8;
+    AMG_TRY(a.alloc(&W.part, (size_t)3 * W.part_cap));
+    AMG_TRY(a.alloc(&W.counter, 4));
+    AMG_CUDA_TRY(cudaMemset(W.counter, 0, 4 * sizeof(unsigned)));
+    AMG_CUDA_TRY(cudaMemset(W.scal, 0, sizeof(DevScalars)));
+    AMG_CUDA_TRY(cudaMallocHost(&W.scal_h, sizeof(DevScalars)));
+    memset(W.scal_h, 0, sizeof(DevScalars));
+    AMG_CUDA_TRY(cudaStreamSynchronize(0));  // the memsets above ran on the legacy stream
+    return AMG_OK;
+}
+
+void workspace_free(Workspace &W) {
+    W.prof.destroy();
+    W.arena.free_all();
+    if (W.scal_h) cudaFreeHost(W.scal_h);
+    W.scal_h = nullptr;
+}
+
+// Algorithmic bytes of a CSR operator pass: values + column indices + row pointers.
+static double csr_bytes(const DevCSR &m, int vb) {
+    return (double)m.nnz * (4.0 + vb) + 4.0 * ((double)m.nrows + 1.0);
+}
+
+// One V-cycle: z0 = M^-1 b0.  TM = float for the mixed form.
+template <typename TM>
+static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z0, int fin, cudaStream_t s) {
+    const int L = h->nlevels;
+    const int cap = W.part_cap;
+    const int *done = &W.scal->done;
+    const bool mixed = sizeof(TM) == 4;
+    const int vb = sizeof(TM);
+    auto Av = [&](const DevCSR &m) -> const TM * { return (const TM *)(mixed ? (const void *)m.v32 : (const void *)m.v); };
+    auto Wv = [&](const Level &lv) -> const TM * { return (const TM *)(mixed ? (const void *)lv.w32 : (const void *)lv.w); };
+    auto Tv = [&](const Level &lv) -> TM * { return (TM *)(mixed ? (void *)lv.t32 : (void *)lv.t); };
+    auto Bv = [&](const Level &lv) -> TM * { return (TM *)(mixed ? (void *)lv.b32 : (void *)lv.b); };
+    auto Xv = [&](const Level &lv) -> TM * { return (TM *)(mixed ? (void *)lv.x32 : (void *)lv.x); };
+    const double *rold = (fin == FIN_PCG_BETA && h->cfg.precision == AMG_PRECISION_MIXED) ? W.rold : nullptr;
+
+    if (L == 1) {
+        const double m = h->nc;
+        TRACE("coarse", 0, m * m * 8.0 + 16.0 * m + (fin == FIN_PCG_BETA ? 8.0 * m : 0.0));
+        if (fin == FIN_PCG_BETA)
+            k_coarse<double, double, FIN_PCG_BETA><<<1, BLOCK, 0, s>>>(h->nc, h->cinv, b0, z0, rold, W.scal, W.part, cap, W.counter);
+        else
+            k_coarse<double, double, FIN_NONE><<<1, BLOCK, 0, s>>>(h->nc, h->cinv, b0, z0, rold, W.scal, W.part, cap, W.counter);
+        AMG_LAUNCH_CHECK();
+        return AMG_OK;
+    }
+    // down
+    for (int l = 0; l < L - 1; ++l) {
+        Level &lv = h->L[l];
+        Level &nx = h->L[l + 1];
+        const int n = lv.A.nrows;
+        const double bb = l == 0 ? 8.0 : vb;
+        {
+            TRACE("presmooth", l, csr_bytes(lv.A, vb) + n * (bb + 2.0 * vb));
+            if (l == 0) {
+                VEC_DISPATCH(lv.vec_a, (k_presmooth<V, double, TM><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                                           n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), b0, Tv(lv), done)));
+            } else {
+                VEC_DISPATCH(lv.vec_a, (k_presmooth<V, TM, TM><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                                           n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), Bv(lv), Tv(lv), done)));
+            }
+        }
+        const int nc = lv.R.nrows;
+        {
+            TRACE("restrict", l, csr_bytes(lv.R, vb) + (double)vb * (n + nc));
+            VEC_DISPATCH(lv.vec_r, (k_spmv<V, TM, TM, TM><<<grid_rows(nc, V, cap), BLOCK, 0, s>>>(
+                                       nc, lv.R.rp, lv.R.ci, Av(lv.R), Tv(lv), Bv(nx), done)));
+        }
+        AMG_LAUNCH_CHECK();
+    }
+    // coarsest
+    {
+        Level &lc = h->L[L - 1];
+        const double m = h->nc;
+        TRACE("coarse", L - 1, m * m * 8.0 + 2.0 * vb * m);
+        k_coarse<TM, TM, FIN_NONE><<<1, BLOCK, 0, s>>>(h->nc, h->cinv, Bv(lc), Xv(lc), nullptr, W.scal, W.part, cap, W.counter);
+        AMG_LAUNCH_CHECK();
+    }
+    // up
+    for (int l = L - 2; l >= 0; --l) {
+        Level &lv = h->L[l];
+        Level &nx = h->L[l + 1];
+        const int n = lv.A.nrows;
+        const int nc = nx.A.nrows;
+        const double bb = l == 0 ? 8.0 : vb;
+        {
+            TRACE("prolong", l, csr_bytes(lv.P, vb) + (double)vb * nc + n * (bb + 2.0 * vb));
+            if (l == 0) {
+                VEC_DISPATCH(lv.vec_p, (k_prolong<V, double, TM><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                                           n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), b0, Xv(nx), Tv(lv), done)));
+            } else {
+                VEC_DISPATCH(lv.vec_p, (k_prolong<V, TM, TM><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                                           n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), Bv(lv), Xv(nx), Tv(lv), done)));
+            }
+        }
+        {
+            const double ob = l == 0 ? 8.0 : vb;
+            TRACE("postsmooth", l, csr_bytes(lv.A, vb) + n * (2.0 * vb + bb + ob) + (rold && l == 0 ? 8.0 * n : 0.0));
+            if (l == 0) {
+                if (fin == FIN_PCG_BETA) {
+                    VEC_DISPATCH(lv.vec_a, (k_postsmooth<V, double, TM, double, FIN_PCG_BETA><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                                               n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), b0, Tv(lv), z0, rold, W.scal, W.part, cap, W.counter)));
+                } else {
+                    VEC_DISPATCH(lv.vec_a, (k_postsmooth<V, double, TM, double, FIN_NONE><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                                               n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), b0, Tv(lv), z0, nullptr, W.scal, W.part, cap, W.counter)));
+                }
+            } else {
+                VEC_DISPATCH(lv.vec_a, (k_postsmooth<V, TM, TM, TM, FIN_NONE><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                                           n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), Bv(lv), Tv(lv), Xv(lv), nullptr, W.scal, W.part, cap, W.counter)));
+            }
+        }
+        AMG_LAUNCH_CHECK();
+    }
+    return AMG_OK;
+}
+
+static int vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z0, int fin, cudaStream_t s) {
+    if (h->cfg.precision == AMG_PRECISION_MIXED) return launch_vcycle<float>(h, W, b0, z0, fin, s);
+    return launch_vcycle<double>(h, W, b0, z0, fin, s);
+}
+
+static int stream_grid(int n, int cap) { return std::max(1, std::min((n + BLOCK - 1) / BLOCK, cap)); }
+
+// q = A x with a finisher (the outer, FP64 operator).
+template <int SF>
+static int spmv_fin(Hierarchy *h, Workspace &W, const char *name, const double *x, double *y, const double *dvec,
+                    cudaStream_t s) {
+    const int n = h->n, cap = W.part_cap;
+    const Level &l0 = h->L[0];
+    TRACE(name, 0, csr_bytes(l0.A, 8) + 16.0 * n + (SF == SF_PCG_ALPHA ? 0.0 : 8.0 * n));
+    VEC_DISPATCH(l0.vec_a, (k_spmv_fin<V, SF><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                               n, l0.A.rp, l0.A.ci, l0.A.v, x, y, dvec, W.scal, W.part, cap, W.counter)));
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+// One PCG iteration: z = M r (with beta), p = z + beta p, q = A p (alpha), update.
+static int pcg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
+    const int n = h->n, cap = W.part_cap;
+    const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
+    AMG_TRY(vcycle(h, W, W.r, W.z, FIN_PCG_BETA, s));
+    {
+        TRACE("pcg_p", 0, 24.0 * n);
+        k_pcg_p<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.z, W.p, W.scal);
+    }
+    AMG_TRY(spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s));
+    {
+        TRACE("pcg_update", 0, (mixed ? 56.0 : 48.0) * n);
+        k_pcg_update<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.x, W.r, W.p, W.q, mixed ? W.rold : nullptr, W.scal,
+                                                           W.part, cap, W.counter);
+    }
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+static int cg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
+    const int n = h->n, cap = W.part_cap;
+    {
+        TRACE("cg_beta", 0, 8.0 * n);
+        k_cg_beta<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.r, W.scal, W.part, cap, W.counter);
+    }
+    {
+        TRACE("pcg_p", 0, 24.0 * n);
+        k_pcg_p<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.r, W.p, W.scal);
+    }
+    AMG_TRY(spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s));
+    {
+        TRACE("pcg_update", 0, 48.0 * n);
+        k_pcg_update<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.x, W.r, W.p, W.q, nullptr, W.scal, W.part, cap, W.counter);
+    }
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+static int bicg_iteration(Hierarchy *h, Workspace &W, bool precond, cudaStream_t s) {
+    const int n = h->n, cap = W.part_cap;
+    {
+        TRACE("bicg_p", 0, 32.0 * n);
+        k_bicg_p<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.r, W.p, W.v, W.scal);
+    }
+    const double *ph = W.p;
+    if (precond) {
+        AMG_TRY(vcycle(h, W, W.p, W.ph, FIN_NONE, s));
+        ph = W.ph;
+    }
+    AMG_TRY(spmv_fin<SF_BICG_ALPHA>(h, W, "spmv_rv", ph, W.v, W.rh, s));
+    {
+        TRACE("bicg_s", 0, 48.0 * n);
+        k_bicg_s<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.r, W.v, W.s, W.x, ph, W.scal, W.part, cap, W.counter);
+    }
+    const double *sh = W.s;
+    if (precond) {
+        AMG_TRY(vcycle(h, W, W.s, W.sh, FIN_NONE, s));
+        sh = W.sh;
+    }
+    AMG_TRY(spmv_fin<SF_BICG_OMEGA>(h, W, "spmv_ts", sh, W.t, W.s, s));
+    {
+        TRACE("bicg_update", 0, 64.0 * n);
+        k_bicg_update<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.x, sh, W.r, W.s, W.t, W.rh, W.scal, W.part, cap, W.counter);
+    }
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+static int read_scalars(Workspace &W, cudaStream_t s) {
+    AMG_CUDA_TRY(cudaMemcpyAsync(W.scal_h, W.scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+// r = b - A x and ||r||^2 into scal->tr; the host reads the scalars.
+static int true_residual(Hierarchy *h, Workspace &W, cudaStream_t s) {
+    AMG_TRY(spmv_fin<SF_TRUE_RES>(h, W, "true_residual", W.x, W.r, W.b, s));
+    return read_scalars(W, s);
+}
+
+static int set_control(Workspace &W, cudaStream_t s, int done, int status, int flexible, int max_iter, int reset) {
+    TRACE("control", 0, 0.0);
+    k_set_control<<<1, 1, 0, s>>>(W.scal, done, status, flexible, max_iter, reset);
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+static int bicg_restart(Hierarchy *h, Workspace &W, cudaStream_t s) {
+    const int n = h->n, cap = W.part_cap;
+    TRACE("bicg_restart", 0, 32.0 * n);
+    k_bicg_restart<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.r, W.rh, W.p, W.v, W.scal, W.part, cap, W.counter);
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
+    const amg_config &c = h->cfg;
+    const int n = h->n, cap = W.part_cap;
+    const bool bicg = c.solver == AMG_SOLVER_BICGSTAB || c.solver == AMG_SOLVER_BICGSTAB_NOPREC;
+    const bool precond = c.solver == AMG_SOLVER_PCG || c.solver == AMG_SOLVER_BICGSTAB;
+    const int flexible = c.precision == AMG_PRECISION_MIXED ? 1 : 0;
+
+    AMG_TRY(set_control(W, s, 0, AMG_OK, flexible, c.max_iter, 1));
+    {
+        TRACE(bicg ? "bicg_init" : "pcg_init", 0, (bicg ? 48.0 : 40.0) * n);
+        if (bicg)
+            k_bicg_init<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.b, W.x, W.r, W.rh, W.p, W.v, W.scal, c.rtol, W.part,
+                                                              cap, W.counter);
+        else
+            k_pcg_init<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.b, W.x, W.r, W.p, W.rold, W.scal, c.rtol, W.part,
+                                                             cap, W.counter);
+    }
+    AMG_LAUNCH_CHECK();
+    AMG_TRY(read_scalars(W, s));
+    int status = W.scal_h->status;
+    int restarts = 0, bd_restarts = 0;
+    const double bn2 = W.scal_h->bn2;
+    if (bn2 == 0.0 && status == AMG_OK) {
+        res->status = AMG_OK;
+        res->iters = 0;
+        res->restarts = 0;
+        res->rel_res_true = res->rel_res_rec = 0.0;
+        W.prof.collect();
+        return AMG_OK;
+    }
+    const int chunk = 4;
+    long long launched = 0;
+    const long long launch_cap = (long long)c.max_iter * (c.max_restarts + 2) + 4 * chunk;
+    while (status == AMG_OK) {
+        // iterate until the device marks the solve done; the device sets done
+        // at max_iter at the latest, launch_cap only guards the host loop
+        for (;;) {
+            for (int k = 0; k < chunk; ++k) {
+                if (bicg) AMG_TRY(bicg_iteration(h, W, precond, s));
+                else if (precond) AMG_TRY(pcg_iteration(h, W, s));
+                else AMG_TRY(cg_iteration(h, W, s));
+            }
+            launched += chunk;
+            AMG_TRY(read_scalars(W, s));
+            if (W.scal_h->done) break;
+            if (launched > launch_cap) {
+                set_last_error("solver loop exceeded %lld iterations without finishing", launch_cap);
+                return AMG_ERR_CUDA;
+            }
+        }
+        status = W.scal_h->status;
+        if (bicg && status == AMG_BREAKDOWN && bd_restarts < 1) {
+            // restart once from the current x with r^ = r = b - A x
+            bd_restarts++;
+            AMG_TRY(true_residual(h, W, s));
+            AMG_TRY(bicg_restart(h, W, s));
+            AMG_TRY(read_scalars(W, s));
+            status = W.scal_h->status;
+            if (W.scal_h->done) break;
+            continue;
+        }
+        if (status != AMG_OK) break;
+        // converged on the recursive residual: check the true residual
+        AMG_TRY(true_residual(h, W, s));
+        const double tr = W.scal_h->tr;
+        if (tr <= W.scal_h->tol2) break;
+        if (restarts >= c.max_restarts || W.scal_h->iters >= c.max_iter) {
+            status = AMG_MAXIT;
+            break;
+        }
+        restarts++;
+        // r already holds b - A x; restart the recursion from the current x
+        if (bicg) {
+            AMG_TRY(bicg_restart(h, W, s));
+        } else {
+            AMG_TRY(set_control(W, s, 0, AMG_OK, flexible, c.max_iter, 0));
+            TRACE("control", 0, 0.0);
+            k_pcg_restart<<<1, 1, 0, s>>>(W.scal);
+            AMG_LAUNCH_CHECK();
+        }
+    }
+    AMG_TRY(read_scalars(W, s));
+    const double rec = W.scal_h->rr;
+    res->iters = W.scal_h->iters;
+    AMG_TRY(true_residual(h, W, s));
+    res->status = status;
+    res->restarts = restarts;
+    res->rel_res_true = sqrt(W.scal_h->tr / bn2);
+    res->rel_res_rec = sqrt(rec / bn2);
+    if (status == AMG_OK && !(res->rel_res_true <= c.rtol)) res->status = AMG_MAXIT;
+    W.prof.collect();
+    return AMG_OK;
+}
+
+int vcycle_apply(Hierarchy *h, Workspace &W, const double *r, double *z, cudaStream_t s) {
+    AMG_TRY(set_control(W, s, 0, AMG_OK, 0, h->cfg.max_iter, 1));
+    return vcycle(h, W, r, z, FIN_NONE, s);
+}
+
+int grad_values(Hierarchy *h, Workspace &W, const double *lambda, const double *x, double *dA, cudaStream_t s) {
+    const Level &l0 = h->L[0];
+    const int n = h->n;
+    TRACE("grad_values", 0, csr_bytes(l0.A, 0) + 16.0 * n + 8.0 * l0.A.nnz);
+    VEC_DISPATCH(l0.vec_a, (k_grad_values<V><<<grid_rows(n, V, num_sms() * 8), BLOCK, 0, s>>>(
+                               n, l0.A.rp, l0.A.ci, lambda, x, dA)));
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+}  // namespace amg

@@ -1,0 +1,77 @@
+// solve.cuh -- internal interface of the solve phase (V-cycle, Krylov drivers).
+#pragma once
+
+#include "amg_common.cuh"
+
+namespace amg {
+
+// Per-kernel tracing: when on, every solve-phase launch is bracketed by CUDA
+// events on the launching stream; durations and algorithmic bytes accumulate
+// per (kernel, level).  Launches are counted whether or not tracing is on.
+struct Profiler {
+    struct Rec {
+        char name[32];
+        int level;
+        long long launches;
+        double ms;
+        double bytes;
+    };
+    struct Pending {
+        int rec;
+        cudaEvent_t a, b;
+    };
+    bool on = false;
+    long long launches = 0;
+    std::vector<Rec> recs;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    int find(const char *name, int level);
+    cudaEvent_t event();
+    int collect();  // call after the stream has been synchronised
+    void reset();
+    void destroy();
+};
+
+struct ProfScope {
+    Profiler *p;
+    cudaStream_t s;
+    int rec = -1;
+    cudaEvent_t a = nullptr;
+    ProfScope(Profiler *p_, cudaStream_t s_, const char *name, int level, double bytes);
+    ~ProfScope();
+};
+
+// Krylov state shared by all hierarchies of a handle (vectors of length n).
+struct Workspace {
+    int n = 0;
+    double *b = nullptr, *x = nullptr;                     // right-hand side / solution (handle-owned)
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *rold = nullptr;
+    double *rh = nullptr, *v = nullptr, *ph = nullptr, *s = nullptr, *sh = nullptr, *t = nullptr;
+    double *aux = nullptr;                                 // adjoint: forward solution x
+    DevScalars *scal = nullptr;                            // device
+    DevScalars *scal_h = nullptr;                          // pinned host mirror
+    double *part = nullptr;                                // per-block partial sums (3 x part_cap)
+    unsigned *counter = nullptr;                           // last-block ticket
+    int part_cap = 0;
+    DevArena arena;
+    Profiler prof;
+};
+
+int workspace_init(Workspace &W, int n);
+void workspace_free(Workspace &W);
+
+struct SolveResult {
+    int status = AMG_OK, iters = 0, restarts = 0;
+    double rel_res_true = 0.0, rel_res_rec = 0.0;
+};
+
+// Solves A x = W.b (A = h's finest operator) into W.x with h's configuration.
+int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res);
+
+// z = M^-1 r with one V-cycle of h (r, z: device vectors of length n).
+int vcycle_apply(Hierarchy *h, Workspace &W, const double *r, double *z, cudaStream_t s);
+
+// dA[k] = -lambda[row(k)] * x[col(k)] on h's finest pattern.
+int grad_values(Hierarchy *h, Workspace &W, const double *lambda, const double *x, double *dA, cudaStream_t s);
+
+}  // namespace amg
