@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--forms", default="mixed,fp64", help="comma list of precision forms to time (first = headline)")
+    p.add_argument("--no-trace", action="store_true", help="skip the per-kernel traced pass (profiler captures)")
     return p.parse_args()
 
 
@@ -195,6 +197,37 @@ def load_traffic(kernel: str):
     return ent.get("bytes_per_launch_full")
 
 
+def trace_pass(s, b, x, g, lam, dA, steps, dev):
+    """Per-kernel CUDA-event trace of solve + adjoint steps (separate from the
+    timed region); returns (roofline, kernel table, V-cycle bytes, V-cycle ms)."""
+    import torch
+    s.profile(True)
+    prof_steps = max(1, min(steps, 3))
+    for _ in range(prof_steps):
+        s.solve(b, x, info=False)
+        s.adjoint(x, g, lam, dA, info=False)
+    torch.cuda.synchronize(dev)
+    _, recs = s.profile_records()
+    s.profile(False)
+    tot_ms = sum(r["ms"] for r in recs) or 1.0
+    top = max(recs, key=lambda r: r["ms"])
+    vc_names = {"presmooth", "restrict", "coarse", "prolong", "postsmooth"}
+    vc = [r for r in recs if r["name"] in vc_names]
+    vc_bytes, vc_ms = sum(r["bytes"] for r in vc), sum(r["ms"] for r in vc)
+    peak, peak_kind = measured_peaks()
+    top_name = f"{top['name']}[L{top['level']}]"
+    achieved = top["bytes"] / top["launches"] / (top["ms"] / top["launches"] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "bytes_per_launch": top["bytes"] / top["launches"], "ms_per_launch": top["ms"] / top["launches"],
+                "share_of_traced_time": top["ms"] / tot_ms, "traffic": load_traffic(top_name)}
+    kernels = sorted(({"kernel": f"{r['name']}[L{r['level']}]", "launches": r["launches"],
+                       "ms_per_launch": r["ms"] / r["launches"], "share": r["ms"] / tot_ms,
+                       "gbs": r["bytes"] / (r["ms"] * 1e-3) / 1e9 if r["ms"] > 0 else None}
+                      for r in recs), key=lambda d: -d["share"])[:12]
+    return roofline, kernels, vc_bytes, vc_ms
+
+
 def run_ours(args):
     import torch
     from paper_2606_09001_b300 import api
@@ -226,7 +259,9 @@ def run_ours(args):
 
     forms = {}
     solvers = {}
-    for form in ("mixed", "fp64"):
+    form_list = [f.strip() for f in args.forms.split(",") if f.strip()]
+    primary = form_list[0]
+    for form in form_list:
         s = api.Solver(rp, ci, vals, {"solver": solver, "precision": form.upper() if form == "mixed" else "FP64"})
         solvers[form] = s
 
@@ -241,7 +276,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         s.profile(False)  # restart the launch count
         sampler = None
-        if form == "mixed":
+        if form == primary:
             uuid = None
             try:
                 uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -275,37 +310,15 @@ def run_ours(args):
         if clocks:
             forms[form]["clocks"] = clocks
 
-    # per-kernel trace of the mixed form (a separate pass of the same steps)
-    s = solvers["mixed"]
-    s.profile(True)
-    prof_steps = max(1, min(args.steps, 3))
-    for _ in range(prof_steps):
-        s.solve(b, x, info=False)
-        s.adjoint(x, g, lam, dA, info=False)
-    torch.cuda.synchronize(dev)
-    _, recs = s.profile_records()
-    s.profile(False)
-    tot_ms = sum(r["ms"] for r in recs) or 1.0
-    top = max(recs, key=lambda r: r["ms"])
-    vc_names = {"presmooth", "restrict", "coarse", "prolong", "postsmooth"}
-    vc = [r for r in recs if r["name"] in vc_names]
-    vc_bytes, vc_ms = sum(r["bytes"] for r in vc), sum(r["ms"] for r in vc)
-    peak, peak_kind = measured_peaks()
-    top_name = f"{top['name']}[L{top['level']}]"
-    achieved = top["bytes"] / top["launches"] / (top["ms"] / top["launches"] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind,
-                "bytes_per_launch": top["bytes"] / top["launches"], "ms_per_launch": top["ms"] / top["launches"],
-                "share_of_traced_time": top["ms"] / tot_ms, "traffic": load_traffic(top_name)}
-    kernels = sorted(({"kernel": f"{r['name']}[L{r['level']}]", "launches": r["launches"],
-                       "ms_per_launch": r["ms"] / r["launches"], "share": r["ms"] / tot_ms,
-                       "gbs": r["bytes"] / (r["ms"] * 1e-3) / 1e9 if r["ms"] > 0 else None}
-                      for r in recs), key=lambda d: -d["share"])[:12]
+    # per-kernel trace of the headline form (a separate pass of the same steps)
+    roofline, kernels, vc_bytes, vc_ms = None, None, 0.0, 0.0
+    if not args.no_trace:
+        roofline, kernels, vc_bytes, vc_ms = trace_pass(solvers[primary], b, x, g, lam, dA, args.steps, dev)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        s = solvers["mixed"]
+        s = solvers[primary]
         hb = torch.from_numpy(np.ascontiguousarray(w.b)).pin_memory()
         hg = g.cpu().pin_memory()
         hx = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -341,18 +354,18 @@ def run_ours(args):
                "sample": f"{nsteps} solve+adjoint step(s) of the full workload, setup excluded, "
                          f"single-threaded FP64 ({info.iters} iterations per solve)"}
 
-    info = solvers["mixed"].info()
+    info = solvers[primary].info()
     for s in solvers.values():
         s.close()
     if rank == 0:
-        mixed = forms["mixed"]
+        mixed = forms[primary]
         value = mixed["ms_per_step"] / world
         out = {
             "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"], "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic (seeded)",
             "config": {"workload": args.workload, "description": desc, "n": n, "nnz": nnz, "rtol": 1e-8,
-                       "solver": solver, "precision": "mixed (FP32 V-cycle, FP64 Krylov)",
+                       "solver": solver, "precision": {"mixed": "mixed (FP32 V-cycle, FP64 Krylov)", "fp64": "FP64"}[primary],
                        "levels": info.nlevels, "rows": info.rows, "operator_complexity": info.operator_complexity,
                        "setup_ms": info.setup_ms,
                        "l2": "inputs larger than L2: level-0 operator alone is "
