@@ -175,6 +175,41 @@ int amg_profile_summary(amg_handle h, long long *launches, int *nrecords);
 int amg_profile_record(amg_handle h, int i, char *name, int name_len, int *level, long long *launches,
                        double *total_ms, double *total_bytes);
 
+/* Largest system amg_cg_solve_noalloc accepts (rows). */
+#define AMG_NOALLOC_MAX_N (1 << 18)
+
+/* Unpreconditioned conjugate gradients on a caller's CSR matrix that
+ * allocates no device memory.  The paper has no counterpart; this entry
+ * point exists for callers that cannot allocate at the moment they solve:
+ * code that runs inside a framework owning all device memory (one that only
+ * hands an operator the buffers it planned, and forbids cudaMalloc while it
+ * executes), or a latency-critical loop in which an allocation would stall
+ * every stream.  amg_setup allocates a whole hierarchy, so such callers
+ * cannot hold a handle; this call needs none.
+ *
+ * Computes the same iteration as amg_solve with AMG_SOLVER_CG (x0 = 0; stop at
+ * ||b - A x||_2 <= rtol ||b||_2, at most 3 restarts from x while the true
+ * residual is above it).  n rows, nnz stored entries; row_ptr/col_idx/values,
+ * b and x must be DEVICE memory (host arrays return AMG_ERR_ARG, since
+ * staging them would need an allocation); the CSR must satisfy the
+ * conventions above and is not validated.  info may be NULL (its hierarchy
+ * fields are left zero).
+ *
+ * Work space: the vectors r, p, q, the per-block partial sums and the Krylov
+ * scalars live in one fixed __device__ array of about 6.3 MB that every GPU
+ * which loads the library keeps until the process exits.  n above
+ * AMG_NOALLOC_MAX_N returns AMG_ERR_UNSUPPORTED before any GPU work.  Every
+ * call on a device shares that array and it keeps the last call's contents
+ * (the call clears what must start at zero), so calls whose GPU work
+ * overlaps -- on two streams, or from two host threads -- race and corrupt
+ * each other: serialise them.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.
+ * Returns AMG_OK, AMG_MAXIT, AMG_BREAKDOWN, AMG_NAN or a hard error. */
+int amg_cg_solve_noalloc(int n, long long nnz, const int *row_ptr, const int *col_idx, const double *values,
+                         const double *b, double *x, double rtol, int max_iter, void *cuda_stream,
+                         amg_info *info);
+
 /* Releases every resource of the handle.  amg_free(NULL) is a no-op. */
 int amg_free(amg_handle h);
 

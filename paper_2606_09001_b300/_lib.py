@@ -15,6 +15,7 @@ AMG_ERR_ARG, AMG_ERR_BAD_CSR, AMG_ERR_ZERO_DIAG, AMG_ERR_CUDA = -1, -2, -3, -4
 AMG_ERR_STALL, AMG_ERR_OOM, AMG_ERR_UNSUPPORTED = -5, -6, -7
 AMG_MAX_LEVELS = 32
 AMG_DENSE_MAX = 256
+AMG_NOALLOC_MAX_N = 1 << 18
 
 SOLVERS = {"PCG": 0, "BICGSTAB": 1, "CG": 2, "BICGSTAB_NOPREC": 3}
 SMOOTHERS = {"JACOBI": 0, "L1_JACOBI": 1}
@@ -23,7 +24,7 @@ PRECISIONS = {"FP64": 0, "MIXED": 1}
 # Every symbol the header declares.
 EXPORTS = ("amg_config_default", "amg_setup", "amg_solve", "amg_adjoint", "amg_vcycle", "amg_get_info",
            "amg_get_level", "amg_get_aggregates", "amg_profile", "amg_profile_summary", "amg_profile_record",
-           "amg_free", "amg_status_string", "amg_last_error")
+           "amg_cg_solve_noalloc", "amg_free", "amg_status_string", "amg_last_error")
 
 
 class AmgConfig(C.Structure):
@@ -67,6 +68,7 @@ def load() -> C.CDLL:
         L.amg_profile_summary.argtypes = [vp, C.POINTER(ll), C.POINTER(i)]
         L.amg_profile_record.argtypes = [vp, i, C.c_char_p, i, C.POINTER(i), C.POINTER(ll), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]
+        L.amg_cg_solve_noalloc.argtypes = [i, ll, vp, vp, vp, vp, vp, C.c_double, i, vp, C.POINTER(AmgInfo)]
         L.amg_free.argtypes = [vp]
         L.amg_status_string.argtypes = [i]
         L.amg_status_string.restype = C.c_char_p

@@ -317,3 +317,24 @@ def solve(A, b, config: dict | None = None, cache: SetupCache | None = default_c
     cfg = make_config(config)
     s = cache.get(rp, ci, v, cfg) if cache is not None else Solver(rp, ci, v, cfg)
     return s.solve(b)
+
+
+def cg_solve_noalloc(row_ptr, col_idx, values, b, x=None, rtol: float = 1e-8, max_iter: int = 500,
+                     stream: int | None = None):
+    """Unpreconditioned CG through amg_cg_solve_noalloc: the library allocates
+    no device memory for this call (it works in a fixed device array), for
+    callers that may not allocate while they run.  All arrays must be CUDA
+    tensors; ``x`` is allocated here only when the caller does not pass one.
+    Returns (x, Info)."""
+    L = _lib.load()
+    for a, k in ((row_ptr, "i32"), (col_idx, "i32"), (values, "f64"), (b, "f64")):
+        _check_dtype(a, k)
+    if x is None:
+        x = torch.empty_like(b)
+    ci = AmgInfo()
+    s = _stream_of(b, x) if stream is None else stream
+    rc = L.amg_cg_solve_noalloc(int(row_ptr.shape[0]) - 1, int(col_idx.shape[0]), _ptr(row_ptr), _ptr(col_idx),
+                                _ptr(values), _ptr(b), _ptr(x), rtol, max_iter, s, C.byref(ci))
+    if rc < 0:
+        raise AMGError(rc, "amg_cg_solve_noalloc")
+    return x, Info.from_c(ci)
