@@ -17,6 +17,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <algorithm>
+#include <vector>
 
 #include "amg_common.cuh"
 
@@ -805,6 +806,40 @@ __global__ void k_dense_factor_inverse(int n, int symmetric, double *a, int *piv
 // Hierarchy construction
 // ===========================================================================
 
+// a_ij w_j for every stored entry (the pre-smoother applies A W to b).
+__global__ void k_scale_cols(int n, const int *rp, const int *ci, const double *v, const double *w, double *out,
+                             float *out32) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const double a = v[k] * w[ci[k]];
+            out[k] = a;
+            if (out32) out32[k] = __double2float_rn(a);
+        }
+}
+
+// Largest tile (rows, a power of two <= 512) whose every tile holds at most
+// CAP - 8 stored entries; operators below 16384 rows keep the row-vector kernels.
+static int plan_stream(const DevCSR &m, StreamPlan &pl, cudaStream_t s) {
+    pl = StreamPlan();
+    const int n = m.nrows;
+    if (n < 16384) return AMG_OK;
+    std::vector<int> rp((size_t)n + 1);
+    AMG_CUDA_TRY(cudaMemcpyAsync(rp.data(), m.rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    const int cap = 4096 - 8;
+    for (int rt = 512; rt >= 16; rt >>= 1) {
+        int worst = 0;
+        for (int r0 = 0; r0 < n; r0 += rt) worst = std::max(worst, rp[std::min(r0 + rt, n)] - rp[r0]);
+        if (worst <= cap) {
+            pl.rt = rt;
+            pl.vec = 512 / rt;
+            pl.ntiles = (n + rt - 1) / rt;
+            return AMG_OK;
+        }
+    }
+    return AMG_OK;
+}
+
 static int choose_vec(long long nnz, int nrows) {
     const double mean = nrows > 0 ? (double)nnz / nrows : 1.0;
     int v = 2;
@@ -1056,6 +1091,17 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
         if (k > 0) {
             AMG_TRY(ar.alloc(&Lv.b, (size_t)nl));
             AMG_TRY(ar.alloc(&Lv.x, (size_t)nl));
+        }
+        if (!last) {
+            AMG_TRY(plan_stream(Lv.A, Lv.sa, s));
+            AMG_TRY(plan_stream(Lv.P, Lv.sp, s));
+            AMG_TRY(plan_stream(Lv.R, Lv.sr, s));
+            AMG_TRY(ar.alloc(&Lv.ahat, (size_t)std::max(1LL, Lv.A.nnz)));
+            if (mixed) AMG_TRY(ar.alloc(&Lv.ahat32, (size_t)std::max(1LL, Lv.A.nnz)));
+            k_scale_cols<<<grid_for(nl), 256, 0, s>>>(nl, Lv.A.rp, Lv.A.ci, Lv.A.v, Lv.w, Lv.ahat, Lv.ahat32);
+            AMG_LAUNCH_CHECK();
+        } else {
+            AMG_TRY(plan_stream(Lv.A, Lv.sa, s));
         }
         if (mixed) {
             AMG_TRY(ar.alloc(&Lv.A.v32, (size_t)std::max(1LL, Lv.A.nnz)));

@@ -9,6 +9,7 @@
 #include <cstring>
 
 #include "solve.cuh"
+#include "stream.cuh"
 
 namespace amg {
 
@@ -35,9 +36,9 @@ static int grid_rows(int n, int vec, int cap) {
 // Reduces NV values over the block, stores the block's partials, and returns
 // true in the last block to arrive, with tot[] = sum over blocks in block order
 // (valid in every thread of that block).
-template <int NV>
+template <int NV, int NT = BLOCK>
 __device__ bool reduce_last(double (&v)[NV], double *part, int cap, unsigned *counter, double (&tot)[NV]) {
-    __shared__ double sh[NV][BLOCK / 32];
+    __shared__ double sh[NV][NT / 32];
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -50,7 +51,7 @@ __device__ bool reduce_last(double (&v)[NV], double *part, int cap, unsigned *co
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             double a = 0.0;
-            for (int w = 0; w < BLOCK / 32; ++w) a += sh[k][w];
+            for (int w = 0; w < NT / 32; ++w) a += sh[k][w];
             part[k * cap + blockIdx.x] = a;
         }
         __threadfence();
@@ -62,13 +63,13 @@ __device__ bool reduce_last(double (&v)[NV], double *part, int cap, unsigned *co
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         double a = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += BLOCK) a += __ldcg(&part[k * cap + b]);
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) a += __ldcg(&part[k * cap + b]);
         a = warp_sum(a);
         __syncthreads();
         if (lane == 0) sh[k][wid] = a;
         __syncthreads();
         double t = 0.0;
-        for (int w = 0; w < BLOCK / 32; ++w) t += sh[k][w];
+        for (int w = 0; w < NT / 32; ++w) t += sh[k][w];
         tot[k] = t;
     }
     if (threadIdx.x == 0) *counter = 0u;
@@ -289,6 +290,29 @@ enum SpmvFin { SF_PCG_ALPHA = 0, SF_BICG_ALPHA = 1, SF_BICG_OMEGA = 2, SF_TRUE_R
 //   SF_BICG_ALPHA: r^.v          -> alpha = rho / r^.v  (dvec = r^)
 //   SF_BICG_OMEGA: t.s, t.t      -> omega = t.s / t.t   (dvec = s)
 //   SF_TRUE_RES  : y = b - A x,  ||y||^2 -> tr          (dvec = b)
+// Finisher of the outer products (one thread of the last block).
+template <int SF>
+__device__ void finish_spmv(DevScalars *sc, const double (&tot)[2]) {
+    if (SF == SF_PCG_ALPHA) {
+        const double pq = tot[0];
+        if (!finite(pq)) fail(sc, AMG_NAN);
+        else if (pq <= 0.0) fail(sc, AMG_BREAKDOWN);
+        else { sc->pq = pq; sc->alpha = sc->rz / pq; }
+    } else if (SF == SF_BICG_ALPHA) {
+        const double rv = tot[0];
+        if (!finite(rv)) fail(sc, AMG_NAN);
+        else if (rv == 0.0) fail(sc, AMG_BREAKDOWN);
+        else { sc->rv = rv; sc->alpha = sc->rho / rv; }
+    } else if (SF == SF_BICG_OMEGA) {
+        const double ts = tot[0], tt = tot[1];
+        if (!finite(ts) || !finite(tt)) fail(sc, AMG_NAN);
+        else if (tt == 0.0) fail(sc, AMG_BREAKDOWN);
+        else { sc->ts = ts; sc->tt = tt; sc->omega = ts / tt; }
+    } else {
+        sc->tr = tot[0];
+    }
+}
+
 template <int VEC, int SF>
 __global__ void __launch_bounds__(BLOCK) k_spmv_fin(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                     const double *__restrict__ v, const double *__restrict__ x,
@@ -317,26 +341,7 @@ __global__ void __launch_bounds__(BLOCK) k_spmv_fin(int n, const int *__restrict
     }
     ROW_LOOP_END
     double tot[2];
-    if (reduce_last<2>(acc, part, cap, counter, tot) && threadIdx.x == 0) {
-        if (SF == SF_PCG_ALPHA) {
-            const double pq = tot[0];
-            if (!finite(pq)) fail(sc, AMG_NAN);
-            else if (pq <= 0.0) fail(sc, AMG_BREAKDOWN);
-            else { sc->pq = pq; sc->alpha = sc->rz / pq; }
-        } else if (SF == SF_BICG_ALPHA) {
-            const double rv = tot[0];
-            if (!finite(rv)) fail(sc, AMG_NAN);
-            else if (rv == 0.0) fail(sc, AMG_BREAKDOWN);
-            else { sc->rv = rv; sc->alpha = sc->rho / rv; }
-        } else if (SF == SF_BICG_OMEGA) {
-            const double ts = tot[0], tt = tot[1];
-            if (!finite(ts) || !finite(tt)) fail(sc, AMG_NAN);
-            else if (tt == 0.0) fail(sc, AMG_BREAKDOWN);
-            else { sc->ts = ts; sc->tt = tt; sc->omega = ts / tt; }
-        } else {
-            sc->tr = tot[0];
-        }
-    }
+    if (reduce_last<2>(acc, part, cap, counter, tot) && threadIdx.x == 0) finish_spmv<SF>(sc, tot);
 }
 
 // x += alpha p; (r_old = r;) r -= alpha q; ||r||^2; convergence / iteration cap.
@@ -514,7 +519,10 @@ __global__ void k_set_control(DevScalars *sc, int done, int status, int flexible
     sc->status = status;
     sc->flexible = flexible;
     sc->max_iter = max_iter;
-    if (reset_iters) sc->iters = 0;
+    if (reset_iters) {
+        sc->iters = 0;
+        sc->copy_timeout = 0;
+    }
 }
 
 // The next preconditioner application starts a new recursion (beta = 0, p = z).
@@ -617,6 +625,139 @@ void workspace_free(Workspace &W) {
     W.scal_h = nullptr;
 }
 
+// ---------------------------------------------------------------------------
+// Epilogues of the bulk-copy streaming kernel (stream.cuh)
+// ---------------------------------------------------------------------------
+
+// r = b - (A W) b
+template <typename TB, typename TM>
+struct OpPre {
+    const int *dn;
+    const TB *b;
+    TM *r;
+    __device__ bool done() const { return *dn != 0; }
+    __device__ TM gather(int j) const { return (TM)__ldg(b + j); }
+    __device__ void finish(int i, TM s, double (&)[2]) const { r[i] = (TM)__ldg(b + i) - s; }
+    __device__ void reduce(double (&)[2]) const {}
+};
+
+// y = M x
+template <typename TM>
+struct OpSpmv {
+    const int *dn;
+    const TM *x;
+    TM *y;
+    __device__ bool done() const { return *dn != 0; }
+    __device__ TM gather(int j) const { return __ldg(x + j); }
+    __device__ void finish(int i, TM s, double (&)[2]) const { y[i] = s; }
+    __device__ void reduce(double (&)[2]) const {}
+};
+
+// t = W b + P x_c
+template <typename TB, typename TM>
+struct OpProlong {
+    const int *dn;
+    const TM *w;
+    const TB *b;
+    const TM *xc;
+    TM *t;
+    __device__ bool done() const { return *dn != 0; }
+    __device__ TM gather(int j) const { return __ldg(xc + j); }
+    __device__ void finish(int i, TM s, double (&)[2]) const { t[i] = __ldg(w + i) * (TM)__ldg(b + i) + s; }
+    __device__ void reduce(double (&)[2]) const {}
+};
+
+// out = t + W (b - A t), with the PCG beta finisher on level 0
+template <typename TB, typename TM, typename TO, int FIN>
+struct OpPost {
+    DevScalars *sc;
+    const TM *w;
+    const TB *b;
+    const TM *t;
+    TO *out;
+    const double *rold;
+    double *part;
+    int cap;
+    unsigned *counter;
+    __device__ bool done() const { return sc->done != 0; }
+    __device__ TM gather(int j) const { return __ldg(t + j); }
+    __device__ void finish(int i, TM s, double (&acc)[2]) const {
+        const TB bi = __ldg(b + i);
+        const TO o = (TO)(__ldg(t + i) + __ldg(w + i) * ((TM)bi - s));
+        out[i] = o;
+        if (FIN == FIN_PCG_BETA) {
+            acc[0] += (double)bi * (double)o;
+            if (rold) acc[1] += rold[i] * (double)o;
+        }
+    }
+    __device__ void reduce(double (&acc)[2]) const {
+        if (FIN == FIN_PCG_BETA) {
+            double tot[2];
+            if (reduce_last<2, stream::THREADS>(acc, part, cap, counter, tot) && threadIdx.x == 0)
+                finish_pcg_beta(sc, tot);
+        }
+    }
+};
+
+// the outer FP64 products with their finishers (see k_spmv_fin)
+template <int SF>
+struct OpFin {
+    DevScalars *sc;
+    const double *x;
+    double *y;
+    const double *dvec;
+    double *part;
+    int cap;
+    unsigned *counter;
+    __device__ bool done() const { return SF != SF_TRUE_RES && sc->done != 0; }
+    __device__ double gather(int j) const { return __ldg(x + j); }
+    __device__ void finish(int i, double s, double (&acc)[2]) const {
+        if (SF == SF_TRUE_RES) {
+            const double ri = dvec[i] - s;
+            y[i] = ri;
+            acc[0] += ri * ri;
+        } else {
+            y[i] = s;
+            if (SF == SF_PCG_ALPHA) acc[0] += x[i] * s;
+            if (SF == SF_BICG_ALPHA) acc[0] += dvec[i] * s;
+            if (SF == SF_BICG_OMEGA) { acc[0] += s * dvec[i]; acc[1] += s * s; }
+        }
+    }
+    __device__ void reduce(double (&acc)[2]) const {
+        double tot[2];
+        if (reduce_last<2, stream::THREADS>(acc, part, cap, counter, tot) && threadIdx.x == 0) finish_spmv<SF>(sc, tot);
+    }
+};
+
+template <typename TM, int VEC, class Op>
+static int stream_launch_vec(const StreamPlan &pl, int n, const int *rp, const int *ci, const TM *v, const Op &op,
+                             int *err, cudaStream_t s) {
+    constexpr int SM = stream::smem_bytes<TM>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        AMG_CUDA_TRY(cudaFuncSetAttribute(stream::k_stream<TM, VEC, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM));
+        attr_set = true;
+    }
+    const int grid = std::max(1, std::min(pl.ntiles, 2 * num_sms()));
+    stream::k_stream<TM, VEC, Op><<<grid, stream::THREADS, SM, s>>>(n, pl.rt, pl.ntiles, rp, ci, v, op, err);
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+// One streaming pass of a CSR operator whose plan is usable (pl.rt > 0).
+template <typename TM, class Op>
+static int stream_launch(const StreamPlan &pl, int n, const int *rp, const int *ci, const TM *v, const Op &op,
+                         int *err, cudaStream_t s) {
+    switch (pl.vec) {
+        case 1: return stream_launch_vec<TM, 1, Op>(pl, n, rp, ci, v, op, err, s);
+        case 2: return stream_launch_vec<TM, 2, Op>(pl, n, rp, ci, v, op, err, s);
+        case 4: return stream_launch_vec<TM, 4, Op>(pl, n, rp, ci, v, op, err, s);
+        case 8: return stream_launch_vec<TM, 8, Op>(pl, n, rp, ci, v, op, err, s);
+        case 16: return stream_launch_vec<TM, 16, Op>(pl, n, rp, ci, v, op, err, s);
+        default: return stream_launch_vec<TM, 32, Op>(pl, n, rp, ci, v, op, err, s);
+    }
+}
+
 // Algorithmic bytes of a CSR operator pass: values + column indices + row pointers.
 static double csr_bytes(const DevCSR &m, int vb) {
     return (double)m.nnz * (4.0 + vb) + 4.0 * ((double)m.nrows + 1.0);
@@ -653,7 +794,15 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         Level &nx = h->L[l + 1];
         const int n = lv.A.nrows;
         const double bb = l == 0 ? 8.0 : vb;
-        {
+        int *err = &W.scal->copy_timeout;
+        if (lv.sa.rt) {
+            TRACE("presmooth", l, csr_bytes(lv.A, vb) + n * (bb + vb));
+            const TM *ah = (const TM *)(mixed ? (const void *)lv.ahat32 : (const void *)lv.ahat);
+            if (l == 0)
+                AMG_TRY(stream_launch<TM>(lv.sa, n, lv.A.rp, lv.A.ci, ah, OpPre<double, TM>{done, b0, Tv(lv)}, err, s));
+            else
+                AMG_TRY(stream_launch<TM>(lv.sa, n, lv.A.rp, lv.A.ci, ah, OpPre<TM, TM>{done, Bv(lv), Tv(lv)}, err, s));
+        } else {
             TRACE("presmooth", l, csr_bytes(lv.A, vb) + n * (bb + 2.0 * vb));
             if (l == 0) {
                 VEC_DISPATCH(lv.vec_a, (k_presmooth<V, double, TM><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
@@ -666,8 +815,11 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         const int nc = lv.R.nrows;
         {
             TRACE("restrict", l, csr_bytes(lv.R, vb) + (double)vb * (n + nc));
-            VEC_DISPATCH(lv.vec_r, (k_spmv<V, TM, TM, TM><<<grid_rows(nc, V, cap), BLOCK, 0, s>>>(
-                                       nc, lv.R.rp, lv.R.ci, Av(lv.R), Tv(lv), Bv(nx), done)));
+            if (lv.sr.rt)
+                AMG_TRY(stream_launch<TM>(lv.sr, nc, lv.R.rp, lv.R.ci, Av(lv.R), OpSpmv<TM>{done, Tv(lv), Bv(nx)}, err, s));
+            else
+                VEC_DISPATCH(lv.vec_r, (k_spmv<V, TM, TM, TM><<<grid_rows(nc, V, cap), BLOCK, 0, s>>>(
+                                           nc, lv.R.rp, lv.R.ci, Av(lv.R), Tv(lv), Bv(nx), done)));
         }
         AMG_LAUNCH_CHECK();
     }
@@ -686,7 +838,16 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         const int n = lv.A.nrows;
         const int nc = nx.A.nrows;
         const double bb = l == 0 ? 8.0 : vb;
-        {
+        int *err = &W.scal->copy_timeout;
+        if (lv.sp.rt) {
+            TRACE("prolong", l, csr_bytes(lv.P, vb) + (double)vb * nc + n * (bb + 2.0 * vb));
+            if (l == 0)
+                AMG_TRY(stream_launch<TM>(lv.sp, n, lv.P.rp, lv.P.ci, Av(lv.P),
+                                          OpProlong<double, TM>{done, Wv(lv), b0, Xv(nx), Tv(lv)}, err, s));
+            else
+                AMG_TRY(stream_launch<TM>(lv.sp, n, lv.P.rp, lv.P.ci, Av(lv.P),
+                                          OpProlong<TM, TM>{done, Wv(lv), Bv(lv), Xv(nx), Tv(lv)}, err, s));
+        } else {
             TRACE("prolong", l, csr_bytes(lv.P, vb) + (double)vb * nc + n * (bb + 2.0 * vb));
             if (l == 0) {
                 VEC_DISPATCH(lv.vec_p, (k_prolong<V, double, TM><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
@@ -699,7 +860,24 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         {
             const double ob = l == 0 ? 8.0 : vb;
             TRACE("postsmooth", l, csr_bytes(lv.A, vb) + n * (2.0 * vb + bb + ob) + (rold && l == 0 ? 8.0 * n : 0.0));
-            if (l == 0) {
+            if (lv.sa.rt) {
+                const int *rp_ = lv.A.rp, *ci_ = lv.A.ci;
+                if (l == 0 && fin == FIN_PCG_BETA)
+                    AMG_TRY(stream_launch<TM>(lv.sa, n, rp_, ci_, Av(lv.A),
+                                              OpPost<double, TM, double, FIN_PCG_BETA>{W.scal, Wv(lv), b0, Tv(lv), z0, rold,
+                                                                                         W.part, cap, W.counter},
+                                              err, s));
+                else if (l == 0)
+                    AMG_TRY(stream_launch<TM>(lv.sa, n, rp_, ci_, Av(lv.A),
+                                              OpPost<double, TM, double, FIN_NONE>{W.scal, Wv(lv), b0, Tv(lv), z0, nullptr,
+                                                                                     W.part, cap, W.counter},
+                                              err, s));
+                else
+                    AMG_TRY(stream_launch<TM>(lv.sa, n, rp_, ci_, Av(lv.A),
+                                              OpPost<TM, TM, TM, FIN_NONE>{W.scal, Wv(lv), Bv(lv), Tv(lv), Xv(lv), nullptr,
+                                                                             W.part, cap, W.counter},
+                                              err, s));
+            } else if (l == 0) {
                 if (fin == FIN_PCG_BETA) {
                     VEC_DISPATCH(lv.vec_a, (k_postsmooth<V, double, TM, double, FIN_PCG_BETA><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
                                                n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), b0, Tv(lv), z0, rold, W.scal, W.part, cap, W.counter)));
@@ -731,6 +909,11 @@ static int spmv_fin(Hierarchy *h, Workspace &W, const char *name, const double *
     const int n = h->n, cap = W.part_cap;
     const Level &l0 = h->L[0];
     TRACE(name, 0, csr_bytes(l0.A, 8) + 16.0 * n + (SF == SF_PCG_ALPHA ? 0.0 : 8.0 * n));
+    if (l0.sa.rt) {
+        AMG_TRY(stream_launch<double>(l0.sa, n, l0.A.rp, l0.A.ci, l0.A.v,
+                                      OpFin<SF>{W.scal, x, y, dvec, W.part, cap, W.counter}, &W.scal->copy_timeout, s));
+        return AMG_OK;
+    }
     VEC_DISPATCH(l0.vec_a, (k_spmv_fin<V, SF><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
                                n, l0.A.rp, l0.A.ci, l0.A.v, x, y, dvec, W.scal, W.part, cap, W.counter)));
     AMG_LAUNCH_CHECK();
@@ -923,6 +1106,10 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
     res->rel_res_rec = sqrt(rec / bn2);
     if (status == AMG_OK && !(res->rel_res_true <= c.rtol)) res->status = AMG_MAXIT;
     W.prof.collect();
+    if (W.scal_h->copy_timeout) {
+        set_last_error("a bulk-copy wait in a streaming kernel timed out");
+        return AMG_ERR_CUDA;
+    }
     return AMG_OK;
 }
 

@@ -50,6 +50,16 @@ SMALL_CASES = {
     "tridiag_1000": lambda: M.tridiagonal_matrix(1000, 2.5),
 }
 
+# Large enough (>= 16384 rows) for the bulk-copy streaming kernels, with a
+# ragged last tile; grf3d_61 also streams on level 1 (20,619 rows).
+STREAM_CASES = {
+    "grf3d_33": lambda: M.diffusion3d_grf(N=33).A,
+    "poisson2d_181": lambda: M.poisson2d(181),
+    "convdiff_29": lambda: M.convdiff3d_upwind(N=29).A,
+    "grf3d_61": lambda: M.diffusion3d_grf(N=61).A,
+}
+SMALL_CASES.update(STREAM_CASES)
+
 
 def compare_hierarchy(A, cfg=None):
     h = O.Hierarchy(A, ocfg(cfg))
@@ -90,6 +100,11 @@ def test_hierarchy_bit_exact_l1_and_small_coarse():
     ("convdiff_14", {"solver": "BICGSTAB"}),
     ("tridiag_1000", {"solver": "CG"}),
     ("convdiff_14", {"solver": "BICGSTAB_NOPREC", "max_iter": 2000}),
+    ("grf3d_33", {}),
+    ("poisson2d_181", {}),
+    ("convdiff_29", {"solver": "BICGSTAB"}),
+    ("grf3d_61", {}),
+    ("poisson2d_181", {"solver": "CG", "max_iter": 5000}),
 ])
 def test_solve_parity(name, cfg):
     A = SMALL_CASES[name]()
@@ -109,7 +124,8 @@ def test_solve_parity(name, cfg):
     assert np.linalg.norm(x - xt) <= 1e-6 * np.linalg.norm(xt)
 
 
-@pytest.mark.parametrize("name", ["poisson2d_64", "grf3d_24", "convdiff_14"])
+@pytest.mark.parametrize("name", ["poisson2d_64", "grf3d_24", "convdiff_14", "grf3d_33", "poisson2d_181",
+                                  "convdiff_29", "grf3d_61"])
 def test_vcycle_parity(name):
     A = SMALL_CASES[name]()
     r = np.random.default_rng(1).uniform(-1, 1, A.n)
@@ -118,7 +134,7 @@ def test_vcycle_parity(name):
     assert np.linalg.norm(z - zo) <= 1e-12 * np.linalg.norm(zo)
 
 
-@pytest.mark.parametrize("name", ["poisson2d_64", "grf3d_24"])
+@pytest.mark.parametrize("name", ["poisson2d_64", "grf3d_24", "grf3d_33", "grf3d_61"])
 def test_vcycle_mixed_close_to_fp64(name):
     A = SMALL_CASES[name]()
     r = np.random.default_rng(1).uniform(-1, 1, A.n)
@@ -128,7 +144,8 @@ def test_vcycle_mixed_close_to_fp64(name):
 
 
 @pytest.mark.parametrize("name,cfg", [("poisson2d_64", {}), ("grf3d_24", {}), ("logk2d_48", {}),
-                                      ("convdiff_14", {"solver": "BICGSTAB"})])
+                                      ("convdiff_14", {"solver": "BICGSTAB"}), ("grf3d_61", {}),
+                                      ("convdiff_29", {"solver": "BICGSTAB"})])
 def test_mixed_precision_solve(name, cfg):
     A = SMALL_CASES[name]()
     b = np.random.default_rng(9).uniform(-1, 1, A.n)
@@ -144,7 +161,9 @@ def test_mixed_precision_solve(name, cfg):
 
 @pytest.mark.parametrize("name,cfg", [("poisson2d_64", {}), ("logk2d_48", {}),
                                       ("convdiff_14", {"solver": "BICGSTAB"}),
-                                      ("grf3d_24", {"precision": "MIXED"})])
+                                      ("grf3d_24", {"precision": "MIXED"}),
+                                      ("grf3d_33", {"precision": "MIXED"}),
+                                      ("convdiff_29", {"solver": "BICGSTAB", "precision": "MIXED"})])
 def test_adjoint_parity(name, cfg):
     A = SMALL_CASES[name]()
     rng = np.random.default_rng(3)
@@ -279,3 +298,47 @@ def test_symmetry_detection_and_nonsymmetric_adjoint_reuse():
     assert torch.equal(lam1, lam2)
     At = A.to_dense().T
     assert np.allclose(lam1.cpu().numpy(), np.linalg.solve(At, np.ones(A.n)), rtol=1e-7, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads in the launch configuration bench.py times
+# ---------------------------------------------------------------------------
+
+@pytest.mark.slow
+@pytest.mark.parametrize("gen,cfg", [
+    (lambda: M.diffusion3d_grf(N=128), {"solver": "PCG"}),
+    (lambda: M.convdiff3d_upwind(N=160), {"solver": "BICGSTAB"}),
+])
+def test_full_size_parity(gen, cfg):
+    """128^3 GRF diffusion and 160^3 convection-diffusion: level-0 and level-1
+    aggregates and coarse patterns bit-exact, iteration counts within 2 of the
+    oracle, both precision forms at true residual <= 1e-8 and within 1e-6 of
+    the oracle's solution; the adjoint's lambda within 1e-6."""
+    w = gen()
+    A = w.A
+    h = O.Hierarchy(A, ocfg(cfg))
+    xo, io = h.solve(w.b)
+    for prec in ("FP64", "MIXED"):
+        s = gpu_solver(A, dict(cfg, precision=prec))
+        info = s.info()
+        assert info.nlevels == h.nlevels
+        for l in range(2):
+            lv = h.level(l)
+            assert np.array_equal(s.aggregates(l), lv.agg)
+            rp, ci, v, _ = s.level(l + 1, "A")
+            nxt = h.level(l + 1).A
+            assert np.array_equal(rp, nxt.row_ptr) and np.array_equal(ci, nxt.col_idx)
+            assert np.array_equal(v.view(np.int64), nxt.values.view(np.int64))
+        x, gi = s.solve(dev(w.b))
+        x = x.cpu().numpy()
+        assert gi.status == 0 and gi.rel_res_true <= 1e-8, gi
+        assert abs(gi.iters - io.iters) <= 2, (prec, gi.iters, io.iters)
+        assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
+        if prec == "MIXED":
+            g = np.random.default_rng(7).uniform(-1, 1, A.n)
+            lam, dA, ai = s.adjoint(dev(x), dev(g))
+            assert ai.status == 0 and ai.rel_res_true <= 1e-8
+            lam_o, _, _ = h.adjoint(x, g, A.nnz)
+            lam = lam.cpu().numpy()
+            assert np.linalg.norm(lam - lam_o) <= 1e-6 * np.linalg.norm(lam_o)
+        s.close()
