@@ -221,10 +221,16 @@ def trace_pass(s, b, x, g, lam, dA, steps, dev):
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "bytes_per_launch": top["bytes"] / top["launches"], "ms_per_launch": top["ms"] / top["launches"],
                 "share_of_traced_time": top["ms"] / tot_ms, "traffic": load_traffic(top_name)}
+    by_level = {}
+    for r in recs:
+        key = r["level"] if r["name"] in vc_names else "outer"
+        by_level[key] = by_level.get(key, 0.0) + r["ms"]
+    level_ms = {str(k): v / prof_steps for k, v in sorted(by_level.items(), key=lambda kv: str(kv[0]))}
     kernels = sorted(({"kernel": f"{r['name']}[L{r['level']}]", "launches": r["launches"],
                        "ms_per_launch": r["ms"] / r["launches"], "share": r["ms"] / tot_ms,
                        "gbs": r["bytes"] / (r["ms"] * 1e-3) / 1e9 if r["ms"] > 0 else None}
                       for r in recs), key=lambda d: -d["share"])[:12]
+    roofline["traced_ms_per_step_by_level"] = level_ms
     return roofline, kernels, vc_bytes, vc_ms
 
 

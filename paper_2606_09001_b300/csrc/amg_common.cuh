@@ -126,17 +126,19 @@ struct DevScalars {
 // ---------------------------------------------------------------------------
 
 // Tiling of one operator for the bulk-copy streaming kernels: rt rows per
-// tile (a power of two, 16..512), vec = 512 / rt threads per row.  rt = 0:
-// the operator is too small or too irregular and uses the row-vector kernels.
+// tile (a multiple of 16, at most 1024), each tile holding at most cap - 8
+// stored entries, vec threads per row.  rt = 0: the operator is too small or
+// too irregular and uses the row-vector kernels.
 struct StreamPlan {
-    int rt = 0, vec = 0, ntiles = 0;
+    int rt = 0, vec = 0, cap = 0, ntiles = 0;
 };
 
 struct Level {
     DevCSR A, P, R;     // P: n x nc, R = P^T: nc x n (P, R unused on the last level)
     double *ahat = nullptr;  // A W: values a_ij w_j (the pre-smoother's operator), FP64
     float *ahat32 = nullptr; // and FP32
-    StreamPlan sa, sp, sr;   // streaming plans of A (and A W), P, R
+    StreamPlan sa, sp, sr;   // streaming plans of A (and A W), P, R at the V-cycle's precision
+    StreamPlan sa64;         // plan of A for the outer FP64 products (level 0)
     double *w = nullptr;    // smoother weight per row (omega / a_ii, or 1 / sum |a_ij|)
     float *w32 = nullptr;
     int *agg = nullptr;     // aggregate of each row (levels < last)

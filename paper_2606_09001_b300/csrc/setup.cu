@@ -817,26 +817,48 @@ __global__ void k_scale_cols(int n, const int *rp, const int *ci, const double *
         }
 }
 
-// Largest tile (rows, a power of two <= 512) whose every tile holds at most
-// CAP - 8 stored entries; operators below 16384 rows keep the row-vector kernels.
-static int plan_stream(const DevCSR &m, StreamPlan &pl, cudaStream_t s) {
+// Tiling for the streaming kernels: the largest rt (multiple of 16, <= 1024)
+// whose every tile holds at most cap - 8 stored entries, and vec threads per
+// row from the mean row length.  Operators below 16384 rows keep the
+// row-vector kernels.
+static int plan_stream(const DevCSR &m, int cap, StreamPlan &pl, cudaStream_t s) {
     pl = StreamPlan();
     const int n = m.nrows;
     if (n < 16384) return AMG_OK;
     std::vector<int> rp((size_t)n + 1);
     AMG_CUDA_TRY(cudaMemcpyAsync(rp.data(), m.rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
-    const int cap = 4096 - 8;
-    for (int rt = 512; rt >= 16; rt >>= 1) {
-        int worst = 0;
-        for (int r0 = 0; r0 < n; r0 += rt) worst = std::max(worst, rp[std::min(r0 + rt, n)] - rp[r0]);
-        if (worst <= cap) {
-            pl.rt = rt;
-            pl.vec = 512 / rt;
-            pl.ntiles = (n + rt - 1) / rt;
-            return AMG_OK;
+    auto worst = [&](int rt) {
+        int w = 0;
+        for (int r0 = 0; r0 < n; r0 += rt) w = std::max(w, rp[std::min(r0 + rt, n)] - rp[r0]);
+        return w;
+    };
+    const double mean = (double)m.nnz / n;
+    int v = 1;
+    while (v < 32 && mean > 12.0 * v) v <<= 1;
+    // 480 consumer threads take a tile in passes of 480 / v rows: prefer tile
+    // heights that are whole passes (and multiples of 16), else any multiple of 16
+    const int pass = 480 / v;
+    int unit = 16;
+    while (unit % pass != 0) unit += 16;
+    int best = 0;
+    for (int u : {unit, 16}) {
+        int lo = 0, hi = 1024 / u;  // search rt = u k
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (worst(u * mid) <= cap - 8) lo = mid;
+            else hi = mid - 1;
+        }
+        if (lo > 0) {
+            best = u * lo;
+            break;
         }
     }
+    if (best == 0) return AMG_OK;
+    pl.rt = best;
+    pl.cap = cap;
+    pl.vec = v;
+    pl.ntiles = (n + pl.rt - 1) / pl.rt;
     return AMG_OK;
 }
 
@@ -1092,16 +1114,16 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
             AMG_TRY(ar.alloc(&Lv.b, (size_t)nl));
             AMG_TRY(ar.alloc(&Lv.x, (size_t)nl));
         }
+        const int cap = 4096;  // stage capacity (stream::CAP)
+        if (k == 0) AMG_TRY(plan_stream(Lv.A, cap, Lv.sa64, s));
         if (!last) {
-            AMG_TRY(plan_stream(Lv.A, Lv.sa, s));
-            AMG_TRY(plan_stream(Lv.P, Lv.sp, s));
-            AMG_TRY(plan_stream(Lv.R, Lv.sr, s));
+            AMG_TRY(plan_stream(Lv.A, cap, Lv.sa, s));
+            AMG_TRY(plan_stream(Lv.P, cap, Lv.sp, s));
+            AMG_TRY(plan_stream(Lv.R, cap, Lv.sr, s));
             AMG_TRY(ar.alloc(&Lv.ahat, (size_t)std::max(1LL, Lv.A.nnz)));
             if (mixed) AMG_TRY(ar.alloc(&Lv.ahat32, (size_t)std::max(1LL, Lv.A.nnz)));
             k_scale_cols<<<grid_for(nl), 256, 0, s>>>(nl, Lv.A.rp, Lv.A.ci, Lv.A.v, Lv.w, Lv.ahat, Lv.ahat32);
             AMG_LAUNCH_CHECK();
-        } else {
-            AMG_TRY(plan_stream(Lv.A, Lv.sa, s));
         }
         if (mixed) {
             AMG_TRY(ar.alloc(&Lv.A.v32, (size_t)std::max(1LL, Lv.A.nnz)));

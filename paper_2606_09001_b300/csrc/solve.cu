@@ -635,9 +635,13 @@ struct OpPre {
     const int *dn;
     const TB *b;
     TM *r;
+    struct Pre {
+        TB b;
+    };
     __device__ bool done() const { return *dn != 0; }
     __device__ TM gather(int j) const { return (TM)__ldg(b + j); }
-    __device__ void finish(int i, TM s, double (&)[2]) const { r[i] = (TM)__ldg(b + i) - s; }
+    __device__ Pre load(int i) const { return Pre{__ldg(b + i)}; }
+    __device__ void finish(int i, TM s, const Pre &p, double (&)[2]) const { r[i] = (TM)p.b - s; }
     __device__ void reduce(double (&)[2]) const {}
 };
 
@@ -647,9 +651,11 @@ struct OpSpmv {
     const int *dn;
     const TM *x;
     TM *y;
+    struct Pre {};
     __device__ bool done() const { return *dn != 0; }
     __device__ TM gather(int j) const { return __ldg(x + j); }
-    __device__ void finish(int i, TM s, double (&)[2]) const { y[i] = s; }
+    __device__ Pre load(int) const { return Pre{}; }
+    __device__ void finish(int i, TM s, const Pre &, double (&)[2]) const { y[i] = s; }
     __device__ void reduce(double (&)[2]) const {}
 };
 
@@ -661,9 +667,14 @@ struct OpProlong {
     const TB *b;
     const TM *xc;
     TM *t;
+    struct Pre {
+        TM w;
+        TB b;
+    };
     __device__ bool done() const { return *dn != 0; }
     __device__ TM gather(int j) const { return __ldg(xc + j); }
-    __device__ void finish(int i, TM s, double (&)[2]) const { t[i] = __ldg(w + i) * (TM)__ldg(b + i) + s; }
+    __device__ Pre load(int i) const { return Pre{__ldg(w + i), __ldg(b + i)}; }
+    __device__ void finish(int i, TM s, const Pre &p, double (&)[2]) const { t[i] = p.w * (TM)p.b + s; }
     __device__ void reduce(double (&)[2]) const {}
 };
 
@@ -679,15 +690,22 @@ struct OpPost {
     double *part;
     int cap;
     unsigned *counter;
+    struct Pre {
+        TM t, w;
+        TB b;
+        double ro;
+    };
     __device__ bool done() const { return sc->done != 0; }
     __device__ TM gather(int j) const { return __ldg(t + j); }
-    __device__ void finish(int i, TM s, double (&acc)[2]) const {
-        const TB bi = __ldg(b + i);
-        const TO o = (TO)(__ldg(t + i) + __ldg(w + i) * ((TM)bi - s));
+    __device__ Pre load(int i) const {
+        return Pre{__ldg(t + i), __ldg(w + i), __ldg(b + i), (FIN == FIN_PCG_BETA && rold) ? __ldg(rold + i) : 0.0};
+    }
+    __device__ void finish(int i, TM s, const Pre &p, double (&acc)[2]) const {
+        const TO o = (TO)(p.t + p.w * ((TM)p.b - s));
         out[i] = o;
         if (FIN == FIN_PCG_BETA) {
-            acc[0] += (double)bi * (double)o;
-            if (rold) acc[1] += rold[i] * (double)o;
+            acc[0] += (double)p.b * (double)o;
+            acc[1] += p.ro * (double)o;
         }
     }
     __device__ void reduce(double (&acc)[2]) const {
@@ -709,18 +727,25 @@ struct OpFin {
     double *part;
     int cap;
     unsigned *counter;
+    struct Pre {
+        double d;
+    };
     __device__ bool done() const { return SF != SF_TRUE_RES && sc->done != 0; }
     __device__ double gather(int j) const { return __ldg(x + j); }
-    __device__ void finish(int i, double s, double (&acc)[2]) const {
+    __device__ Pre load(int i) const { return Pre{SF == SF_PCG_ALPHA ? __ldg(x + i) : __ldg(dvec + i)}; }
+    __device__ void finish(int i, double s, const Pre &p, double (&acc)[2]) const {
         if (SF == SF_TRUE_RES) {
-            const double ri = dvec[i] - s;
+            const double ri = p.d - s;
             y[i] = ri;
             acc[0] += ri * ri;
         } else {
             y[i] = s;
-            if (SF == SF_PCG_ALPHA) acc[0] += x[i] * s;
-            if (SF == SF_BICG_ALPHA) acc[0] += dvec[i] * s;
-            if (SF == SF_BICG_OMEGA) { acc[0] += s * dvec[i]; acc[1] += s * s; }
+            if (SF == SF_BICG_OMEGA) {
+                acc[0] += s * p.d;
+                acc[1] += s * s;
+            } else {
+                acc[0] += p.d * s;
+            }
         }
     }
     __device__ void reduce(double (&acc)[2]) const {
@@ -732,14 +757,17 @@ struct OpFin {
 template <typename TM, int VEC, class Op>
 static int stream_launch_vec(const StreamPlan &pl, int n, const int *rp, const int *ci, const TM *v, const Op &op,
                              int *err, cudaStream_t s) {
-    constexpr int SM = stream::smem_bytes<TM>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        AMG_CUDA_TRY(cudaFuncSetAttribute(stream::k_stream<TM, VEC, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM));
-        attr_set = true;
+    const int smem = stream::smem_bytes<TM>(pl.rt, pl.cap);
+    static int attr_set = 0;  // largest dynamic shared memory enabled for this instantiation
+    if (smem > attr_set) {
+        AMG_CUDA_TRY(cudaFuncSetAttribute(stream::k_stream<TM, VEC, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          smem));
+        attr_set = smem;
     }
-    const int grid = std::max(1, std::min(pl.ntiles, 2 * num_sms()));
-    stream::k_stream<TM, VEC, Op><<<grid, stream::THREADS, SM, s>>>(n, pl.rt, pl.ntiles, rp, ci, v, op, err);
+    // CTAs per SM that fit the SM's 228 KB of shared memory (1 KB reserved per CTA)
+    const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 2048)));
+    const int grid = std::max(1, std::min(pl.ntiles, per_sm * num_sms()));
+    stream::k_stream<TM, VEC, Op><<<grid, stream::THREADS, smem, s>>>(n, pl.rt, pl.cap, pl.ntiles, rp, ci, v, op, err);
     AMG_LAUNCH_CHECK();
     return AMG_OK;
 }
@@ -909,8 +937,8 @@ static int spmv_fin(Hierarchy *h, Workspace &W, const char *name, const double *
     const int n = h->n, cap = W.part_cap;
     const Level &l0 = h->L[0];
     TRACE(name, 0, csr_bytes(l0.A, 8) + 16.0 * n + (SF == SF_PCG_ALPHA ? 0.0 : 8.0 * n));
-    if (l0.sa.rt) {
-        AMG_TRY(stream_launch<double>(l0.sa, n, l0.A.rp, l0.A.ci, l0.A.v,
+    if (l0.sa64.rt) {
+        AMG_TRY(stream_launch<double>(l0.sa64, n, l0.A.rp, l0.A.ci, l0.A.v,
                                       OpFin<SF>{W.scal, x, y, dvec, W.part, cap, W.counter}, &W.scal->copy_timeout, s));
         return AMG_OK;
     }

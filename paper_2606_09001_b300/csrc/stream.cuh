@@ -2,17 +2,22 @@
 // copies (cp.async.bulk + mbarrier), used for every large operator of the
 // V-cycle and the outer Krylov products.
 //
-// A persistent CTA walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
-// of RT consecutive rows.  For each tile one thread issues three bulk copies
-// into a pipeline stage: the tile's row pointers, column indices and values
-// (each range rounded out to 16-byte boundaries; every array the library
-// owns is padded so the rounded range stays inside its allocation).  STAGES
-// tiles are in flight per CTA, so the copy engine keeps enough bytes moving to
-// saturate HBM with few threads.  Consumers wait on the stage's mbarrier (a
-// bounded wait), then VEC threads per row reduce the row from shared memory,
-// gathering the input vector from global memory (L2), and an epilogue functor
-// finishes the row.  Optional dot products end in the deterministic
-// last-block reduction.
+// Warp-specialised persistent CTAs of 512 threads walk the tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ... of rt consecutive rows.
+//   * Warp 0, lane 0 is the producer: for each tile it issues three bulk copies
+//     into a pipeline stage -- the tile's row pointers, column indices and
+//     values, each range rounded out to 16-byte boundaries (every array the
+//     library owns is padded so the rounded range stays inside it) -- and
+//     arms the stage's "full" mbarrier with the byte count.
+//   * Warps 1..15 consume: wait on "full", reduce the tile's rows from shared
+//     memory (VEC threads per row, UNR entries in flight per thread, the input
+//     vector gathered from global memory), hand each row to an epilogue
+//     functor, then arrive on the stage's "empty" mbarrier.  The producer
+//     waits on "empty" before refilling the stage.
+// No block-wide barrier runs inside the loop, so consumer warps drift freely
+// across STAGES tiles.  Every wait is bounded; a timeout sets an error flag
+// and the CTA leaves the loop.  Optional dot products end in the
+// deterministic last-block reduction (the one __syncthreads of the kernel).
 #pragma once
 
 #include "amg_common.cuh"
@@ -21,23 +26,29 @@ namespace amg {
 namespace stream {
 
 constexpr int THREADS = 512;
-constexpr int CAP = 4096;   // entries per stage (values and column indices)
-constexpr int RT_MAX = 512;
+constexpr int CONSUMER_WARPS = THREADS / 32 - 1;
+constexpr int MAX_STAGES = 3;
+constexpr int RT_MAX = 1024;
+constexpr int CAP = 4096;  // stage capacity in stored entries
+
+// Pipeline depth per value type: 3 stages of 4-byte values or 2 of 8-byte
+// values keep two 512-thread CTAs resident per SM (about 104 KB each).
+template <typename TM>
+__host__ __device__ constexpr int stages() { return sizeof(TM) == 4 ? 3 : 2; }
+
+__host__ __device__ constexpr int align16(int b) { return (b + 15) & ~15; }
+
+// Stage layout (bytes): [row pointers | column indices | values | header]
+template <typename TM>
+struct Layout {
+    int rpb, cib, vab, stb;
+    __host__ __device__ Layout(int rt, int cap)
+        : rpb(align16((rt + 8) * 4)), cib(align16((cap + 8) * 4)), vab(align16((cap + 8) * (int)sizeof(TM))),
+          stb(rpb + cib + vab + 16) {}
+};
 
 template <typename TM>
-struct Stages;
-template <>
-struct Stages<float> { static constexpr int N = 3; };
-template <>
-struct Stages<double> { static constexpr int N = 2; };
-
-// Shared-memory layout of one stage (bytes, 16-byte multiples).
-constexpr int RP_BYTES = (RT_MAX + 8) * 4;
-constexpr int CI_BYTES = (CAP + 8) * 4;
-template <typename TM>
-constexpr int stage_bytes() { return RP_BYTES + CI_BYTES + (CAP + 8) * (int)sizeof(TM) + 16; }
-template <typename TM>
-constexpr int smem_bytes() { return Stages<TM>::N * stage_bytes<TM>(); }
+inline int smem_bytes(int rt, int cap) { return stages<TM>() * Layout<TM>(rt, cap).stb; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -48,6 +59,9 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -72,90 +86,127 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
     return false;
 }
 
-// Issues the copies of tile t into stage buffers; called by one thread.
-template <typename TM>
-__device__ __forceinline__ void issue_tile(int t, int rt, int n, const int *__restrict__ rp,
-                                           const int *__restrict__ ci, const TM *__restrict__ v,
-                                           unsigned char *stage, uint64_t *bar) {
-    const int r0 = t * rt;
-    const int r1 = min(r0 + rt, n);
-    const int s = __ldg(rp + r0), e = __ldg(rp + r1);
-    const int rp_cnt = (r1 - r0 + 1 + 3) & ~3;                  // r0 is a multiple of 4
-    const int cs = s & ~3, ce = (e + 3) & ~3;                   // int32: 4 per 16 bytes
-    constexpr int PER = 16 / sizeof(TM);
-    const int vs = s & ~(PER - 1), ve = (e + PER - 1) & ~(PER - 1);
-    int *hdr = reinterpret_cast<int *>(stage + RP_BYTES + CI_BYTES + (CAP + 8) * sizeof(TM));
-    hdr[0] = cs;
-    hdr[1] = vs;
-    const uint32_t b_rp = rp_cnt * 4, b_ci = (ce - cs) * 4, b_v = (ve - vs) * (uint32_t)sizeof(TM);
-    mbar_expect_tx(bar, b_rp + b_ci + b_v);
-    bulk_g2s(stage, rp + r0, b_rp, bar);
-    if (b_ci) bulk_g2s(stage + RP_BYTES, ci + cs, b_ci, bar);
-    if (b_v) bulk_g2s(stage + RP_BYTES + CI_BYTES, v + vs, b_v, bar);
-}
-
-// The row pass.  Op provides: bool done() const; TM gather(int j) const;
-// void finish(int i, TM s, double* acc) const; void reduce(double* acc) const
-// (called by every thread of every CTA at the end).
+// The row pass.  Op provides: bool done(); TM gather(int j); Pre load(int i)
+// (the row's epilogue operands, loaded before the gathers so the latencies
+// overlap); finish(int i, TM s, const Pre&, double (&acc)[2]);
+// reduce(double (&acc)[2]) (called by every thread of every CTA at the end).
 template <typename TM, int VEC, class Op>
-__global__ void __launch_bounds__(THREADS) k_stream(int n, int rt, int ntiles, const int *__restrict__ rp,
+__global__ void __launch_bounds__(THREADS) k_stream(int n, int rt, int cap, int ntiles, const int *__restrict__ rp,
                                                     const int *__restrict__ ci, const TM *__restrict__ v, Op op,
                                                     int *err) {
-    constexpr int S = Stages<TM>::N;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bars[S];
+    constexpr int STAGES = stages<TM>();
+    __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES];
     if (op.done()) return;
-    const int tid = threadIdx.x;
+    const Layout<TM> L(rt, cap);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+        for (int k = 0; k < STAGES; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], CONSUMER_WARPS);
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0)
-        for (int k = 0; k < S; ++k) {
-            const int t = blockIdx.x + k * gridDim.x;
-            if (t < ntiles) issue_tile<TM>(t, rt, n, rp, ci, v, smem + k * stage_bytes<TM>(), &bars[k]);
-        }
     double acc[2] = {0.0, 0.0};
-    const int row_local = tid / VEC, lane = tid % VEC;
     bool ok = true;
-    for (int j = 0;; ++j) {
-        const int t = blockIdx.x + j * gridDim.x;
-        if (t >= ntiles) break;
-        const int st = j % S;
-        unsigned char *stage = smem + st * stage_bytes<TM>();
-        const bool got = mbar_wait(&bars[st], (uint32_t)((j / S) & 1));
-        if (__syncthreads_or(!got)) {  // block-uniform decision
-            ok = false;
-            break;
-        }
-        const int *rps = reinterpret_cast<const int *>(stage);
-        const int *cis = reinterpret_cast<const int *>(stage + RP_BYTES);
-        const TM *vs_ = reinterpret_cast<const TM *>(stage + RP_BYTES + CI_BYTES);
-        const int *hdr = reinterpret_cast<const int *>(stage + RP_BYTES + CI_BYTES + (CAP + 8) * sizeof(TM));
-        const int cs = hdr[0], vsb = hdr[1];
-        const int r0 = t * rt;
-        const int rows = min(rt, n - r0);
-        TM sum = 0;
-        if (row_local < rows) {
-            const int k1 = rps[row_local + 1];
-            for (int k = rps[row_local] + lane; k < k1; k += VEC) sum += vs_[k - vsb] * op.gather(cis[k - cs]);
-        }
-        if (VEC > 1) sum = group_sum<VEC>(sum);
-        if (lane == 0 && row_local < rows) op.finish(r0 + row_local, sum, acc);
-        __syncthreads();  // every read of this stage is done
-        if (tid == 0) {
-            const int tn = t + S * gridDim.x;
-            if (tn < ntiles) {
-                fence_proxy_async();
-                issue_tile<TM>(tn, rt, n, rp, ci, v, stage, &bars[st]);
+    if (warp == 0) {
+        if (lane == 0) {
+            int s = 0, e = 0;
+            if ((int)blockIdx.x < ntiles) {
+                s = __ldg(rp + blockIdx.x * rt);
+                e = __ldg(rp + min((int)blockIdx.x * rt + rt, n));
             }
+            for (int j = 0;; ++j) {
+                const int t = blockIdx.x + j * gridDim.x;
+                if (t >= ntiles) break;
+                const int st = j % STAGES;
+                // bounds of the following tile, loaded while this one is issued
+                const int tn = t + gridDim.x;
+                int ns = 0, ne = 0;
+                if (tn < ntiles) {
+                    ns = __ldg(rp + tn * rt);
+                    ne = __ldg(rp + min(tn * rt + rt, n));
+                }
+                if (j >= STAGES && !mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *stage = smem + st * L.stb;
+                const int r0 = t * rt, r1 = min(r0 + rt, n);
+                const int rp_cnt = (r1 - r0 + 1 + 3) & ~3;  // r0 is a multiple of 4
+                const int cs = s & ~3, ce = (e + 3) & ~3;
+                constexpr int PER = 16 / sizeof(TM);
+                const int vs = s & ~(PER - 1), ve = (e + PER - 1) & ~(PER - 1);
+                int *hdr = reinterpret_cast<int *>(stage + L.rpb + L.cib + L.vab);
+                hdr[0] = cs;
+                hdr[1] = vs;
+                const uint32_t b_rp = rp_cnt * 4, b_ci = (ce - cs) * 4, b_v = (ve - vs) * (uint32_t)sizeof(TM);
+                if (j >= STAGES) fence_proxy_async();
+                mbar_expect_tx(&full[st], b_rp + b_ci + b_v);
+                bulk_g2s(stage, rp + r0, b_rp, &full[st]);
+                if (b_ci) bulk_g2s(stage + L.rpb, ci + cs, b_ci, &full[st]);
+                if (b_v) bulk_g2s(stage + L.rpb + L.cib, v + vs, b_v, &full[st]);
+                s = ns;
+                e = ne;
+            }
+        }
+    } else {
+        constexpr int UNR = VEC == 1 ? 8 : 4;
+        const int ct = tid - 32;
+        constexpr int ROWS_PER_PASS = CONSUMER_WARPS * 32 / VEC;
+        const int rsub = ct / VEC, vl = ct % VEC;
+        for (int j = 0;; ++j) {
+            const int t = blockIdx.x + j * gridDim.x;
+            if (t >= ntiles) break;
+            const int st = j % STAGES;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / STAGES) & 1)))) {  // warp-uniform
+                ok = false;
+                break;
+            }
+            const unsigned char *stage = smem + st * L.stb;
+            const int *rps = reinterpret_cast<const int *>(stage);
+            const int *cis = reinterpret_cast<const int *>(stage + L.rpb);
+            const TM *vals = reinterpret_cast<const TM *>(stage + L.rpb + L.cib);
+            const int *hdr = reinterpret_cast<const int *>(stage + L.rpb + L.cib + L.vab);
+            const int cs = hdr[0], vsb = hdr[1];
+            const int r0 = t * rt;
+            const int rows = min(rt, n - r0);
+            for (int base = 0; base < rows; base += ROWS_PER_PASS) {
+                const int rl = base + rsub;
+                TM sum = 0;
+                typename Op::Pre pre{};
+                if (rl < rows) {
+                    if (vl == 0) pre = op.load(r0 + rl);
+                    const int k1 = rps[rl + 1];
+                    for (int kb = rps[rl] + vl; kb < k1; kb += UNR * VEC) {
+                        TM av[UNR], xv[UNR];
+#pragma unroll
+                        for (int u = 0; u < UNR; ++u) {
+                            const int k = kb + u * VEC;
+                            if (k < k1) {
+                                av[u] = vals[k - vsb];
+                                xv[u] = op.gather(cis[k - cs]);
+                            } else {
+                                av[u] = 0;
+                                xv[u] = 0;
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < UNR; ++u) sum += av[u] * xv[u];
+                    }
+                }
+                if (VEC > 1) sum = group_sum<VEC>(sum);
+                if (vl == 0 && rl < rows) op.finish(r0 + rl, sum, pre, acc);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
         }
     }
     if (!ok) {
-        if (tid == 0) atomicExch(err, 1);
-        // give the copies in flight a bounded chance to land before the CTA exits
-        for (int k = 0; k < S; ++k) mbar_try_wait(&bars[k], 0);
+        atomicExch(err, 1);
+        // a bounded chance for copies still in flight to land before exit
+        for (int k = 0; k < STAGES; ++k) mbar_try_wait(&full[k], 0);
     }
     op.reduce(acc);
 }
