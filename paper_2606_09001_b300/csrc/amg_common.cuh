@@ -159,6 +159,17 @@ struct Hierarchy {
     Level L[AMG_MAX_LEVELS];
     int nc = 0;                 // rows of the coarsest level
     double *cinv = nullptr;     // dense inverse of the coarsest operator, nc x nc row-major
+    // Fused coarse levels: levels tail_start..nlevels-1 run in one cluster launch
+    // (tail_start = -1: not used); device tables for FP64 and FP32 cycles.
+    int tail_start = -1;
+    int tail_cluster = 0;
+    void *tail_args64 = nullptr;
+    void *tail_args32 = nullptr;
+    // One Krylov iteration captured as a CUDA graph (replayed per iteration);
+    // iter_kind: which iteration it holds, iter_kernels: launches it contains.
+    cudaGraphExec_t iter_exec = nullptr;
+    int iter_kind = -1;
+    int iter_kernels = 0;
     DevArena arena;
     double setup_ms = 0.0;
 };
@@ -186,6 +197,7 @@ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 int exclusive_scan_int(const int *in, int *out, int n, int *total_host, cudaStream_t s);
 int transpose_csr(const DevCSR &a, DevCSR &t, DevArena &arena, cudaStream_t s);
 int build_hierarchy(Hierarchy *h, const int *rp, const int *ci, const double *v, cudaStream_t s);
+int tail_prepare(Hierarchy *h, cudaStream_t s);
 void free_hierarchy(Hierarchy *h);
 int num_sms();
 

@@ -159,6 +159,7 @@ int amg_setup(const amg_config *cfg, int n, long long nnz, const int *row_ptr, c
         h->H.nnz = nnz;
         if ((rc = build_hierarchy(&h->H, row_ptr, col_idx, values, h->s)) != AMG_OK) break;
         if ((rc = workspace_init(h->W, n)) < 0) break;
+        if ((rc = autotune_plans(&h->H, h->W.scal, h->s)) < 0) break;
         if ((rc = leave(h, cuda_stream, true)) < 0) break;
     } while (0);
     if (rc != AMG_OK) {
@@ -205,6 +206,7 @@ int amg_adjoint(amg_handle h, const double *x, const double *g, double *lambda, 
                 HT->nnz = nnz;
                 const auto t0 = clk::now();
                 rc = build_hierarchy(HT, At.rp, At.ci, At.v, h->s);
+                if (rc == AMG_OK) rc = autotune_plans(HT, h->W.scal, h->s);
                 HT->setup_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
             }
             cudaStreamSynchronize(h->s);

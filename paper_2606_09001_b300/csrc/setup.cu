@@ -1145,11 +1145,13 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
         }
     }
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
-    return AMG_OK;
+    return tail_prepare(h, s);
 }
 
 void free_hierarchy(Hierarchy *h) {
     if (!h) return;
+    if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
+    h->iter_exec = nullptr;
     h->arena.free_all();
 }
 

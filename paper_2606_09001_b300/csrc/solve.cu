@@ -10,6 +10,7 @@
 
 #include "solve.cuh"
 #include "stream.cuh"
+#include "tail.cuh"
 
 namespace amg {
 
@@ -791,6 +792,241 @@ static double csr_bytes(const DevCSR &m, int vb) {
     return (double)m.nnz * (4.0 + vb) + 4.0 * ((double)m.nrows + 1.0);
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: timed trial of streaming plans at setup
+// ---------------------------------------------------------------------------
+
+// Candidate tilings of one operator: rows per tile (multiples of 16, whole
+// consumer passes when possible, capped so that there are at least four
+// tiles per resident CTA) and threads per row (the mean-length choice and
+// twice it).  Every candidate keeps each tile within cap - 8 stored entries.
+static std::vector<StreamPlan> plan_candidates(const DevCSR &m, const StreamPlan &base, cudaStream_t s) {
+    std::vector<StreamPlan> out;
+    if (base.rt == 0) return out;
+    const int n = m.nrows;
+    std::vector<int> rp((size_t)n + 1);
+    if (cudaMemcpyAsync(rp.data(), m.rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        out.push_back(base);
+        return out;
+    }
+    auto worst = [&](int rt) {
+        int w = 0;
+        for (int r0 = 0; r0 < n; r0 += rt) w = std::max(w, rp[std::min(r0 + rt, n)] - rp[r0]);
+        return w;
+    };
+    const int resident = 2 * num_sms();
+    std::vector<int> rts = {base.rt};
+    int rt4 = (n / (4 * resident)) / 16 * 16;  // >= 4 tiles per resident CTA
+    if (rt4 >= 16 && rt4 < base.rt) rts.push_back(rt4);
+    if (base.rt / 2 >= 16) rts.push_back(base.rt / 2 / 16 * 16);
+    for (int vec : {base.vec, base.vec * 2}) {
+        if (vec > 32) continue;
+        for (int rt : rts) {
+            if (rt < 16 || worst(rt) > base.cap - 8) continue;
+            StreamPlan p = base;
+            p.rt = rt;
+            p.vec = vec;
+            p.ntiles = (n + rt - 1) / rt;
+            bool dup = false;
+            for (const StreamPlan &q : out) dup |= q.rt == p.rt && q.vec == p.vec;
+            if (!dup) out.push_back(p);
+        }
+    }
+    return out;
+}
+
+// Times y = M x with each candidate (three runs after one warm-up) and keeps
+// the fastest plan.  x and y are scratch vectors of the operator's sizes.
+template <typename TM>
+static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevScalars *sc, cudaStream_t s) {
+    std::vector<StreamPlan> cands = plan_candidates(m, pl, s);
+    if (cands.size() <= 1) return AMG_OK;
+    Scratch scr;
+    TM *x = nullptr, *y = nullptr;
+    int *err = nullptr;
+    AMG_TRY(scr.alloc(&x, (size_t)m.ncols));
+    AMG_TRY(scr.alloc(&y, (size_t)m.nrows));
+    AMG_TRY(scr.alloc(&err, 1));
+    AMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(TM) * (size_t)m.ncols, s));
+    AMG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    int *dn = &sc->done;  // 0 between solves
+    cudaEvent_t e0, e1;
+    AMG_CUDA_TRY(cudaEventCreate(&e0));
+    AMG_CUDA_TRY(cudaEventCreate(&e1));
+    // cands[0] is the heuristic plan; another candidate must beat it by 3 %
+    float base_ms = 0.f, best = 1e30f;
+    StreamPlan chosen = pl;
+    int rc = AMG_OK;
+    for (size_t ci_ = 0; ci_ < cands.size(); ++ci_) {
+        const StreamPlan &c = cands[ci_];
+        OpSpmv<TM> op{dn, x, y};
+        if ((rc = stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals, op, err, s)) < 0) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 5; ++r)
+            if ((rc = stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals, op, err, s)) < 0) break;
+        cudaEventRecord(e1, s);
+        if (rc < 0 || cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ci_ == 0) base_ms = ms;
+        if (ms < best && (ci_ == 0 || ms < 0.97f * base_ms)) {
+            best = ms;
+            chosen = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (rc < 0) return rc;
+    pl = chosen;
+    return AMG_OK;
+}
+
+// Refines every streaming plan of the hierarchy by timed trial (the autotuner).
+int autotune_plans(Hierarchy *h, DevScalars *sc, cudaStream_t s) {
+    const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
+    for (int l = 0; l < h->nlevels - 1; ++l) {
+        Level &lv = h->L[l];
+        if (mixed) {
+            AMG_TRY(tune_plan<float>(lv.A, lv.A.v32, lv.sa, sc, s));
+            AMG_TRY(tune_plan<float>(lv.P, lv.P.v32, lv.sp, sc, s));
+            AMG_TRY(tune_plan<float>(lv.R, lv.R.v32, lv.sr, sc, s));
+        } else {
+            AMG_TRY(tune_plan<double>(lv.A, lv.A.v, lv.sa, sc, s));
+            AMG_TRY(tune_plan<double>(lv.P, lv.P.v, lv.sp, sc, s));
+            AMG_TRY(tune_plan<double>(lv.R, lv.R.v, lv.sr, sc, s));
+        }
+    }
+    if (mixed) AMG_TRY(tune_plan<double>(h->L[0].A, h->L[0].A.v, h->L[0].sa64, sc, s));
+    else h->L[0].sa64 = h->L[0].sa;
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Fused coarse levels (tail.cuh)
+// ---------------------------------------------------------------------------
+
+template <typename TM>
+static int build_tail_table(Hierarchy *h, int t, void **out) {
+    const bool mixed = sizeof(TM) == 4;
+    tail::TArgs<TM> a;
+    memset(&a, 0, sizeof(a));
+    a.nlev = h->nlevels - t;
+    a.level0 = t == 0;
+    a.nc = h->nc;
+    a.cinv = h->cinv;
+    for (int k = 0; k < a.nlev; ++k) {
+        const Level &lv = h->L[t + k];
+        tail::TLevel<TM> &d = a.L[k];
+        d.n = lv.A.nrows;
+        // lanes per row: the row-vector choice, widened while the cluster's
+        // threads outnumber the level's rows
+        const int threads = h->tail_cluster * tail::THREADS;
+        auto widen = [&](int vec, int rows) {
+            while (vec < 32 && (long long)rows * vec * 2 <= threads) vec <<= 1;
+            return vec;
+        };
+        d.vec_a = widen(lv.vec_a, lv.A.nrows);
+        d.vec_p = widen(lv.vec_p, lv.A.nrows);
+        d.vec_r = widen(lv.vec_r, lv.R.nrows);
+        d.arp = lv.A.rp;
+        d.aci = lv.A.ci;
+        d.av = (const TM *)(mixed ? (const void *)lv.A.v32 : (const void *)lv.A.v);
+        d.ahat = (const TM *)(mixed ? (const void *)lv.ahat32 : (const void *)lv.ahat);
+        d.w = (const TM *)(mixed ? (const void *)lv.w32 : (const void *)lv.w);
+        d.prp = lv.P.rp;
+        d.pci = lv.P.ci;
+        d.pv = (const TM *)(mixed ? (const void *)lv.P.v32 : (const void *)lv.P.v);
+        d.rrp = lv.R.rp;
+        d.rci = lv.R.ci;
+        d.rv = (const TM *)(mixed ? (const void *)lv.R.v32 : (const void *)lv.R.v);
+        d.b = (TM *)(mixed ? (void *)lv.b32 : (void *)lv.b);
+        d.t = (TM *)(mixed ? (void *)lv.t32 : (void *)lv.t);
+        d.x = (TM *)(mixed ? (void *)lv.x32 : (void *)lv.x);
+    }
+    tail::TArgs<TM> *dev = nullptr;
+    AMG_TRY(h->arena.alloc(&dev, 1));
+    AMG_CUDA_TRY(cudaMemcpy(dev, &a, sizeof(a), cudaMemcpyHostToDevice));
+    *out = dev;
+    return AMG_OK;
+}
+
+template <typename TM>
+static int tail_cluster_size() {
+    const void *fn = (const void *)tail::k_tail<TM>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
+    for (int cs : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(tail::THREADS);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) == cudaSuccess && nclusters > 0) return cs;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+// Chooses the first level of the fused tail: every level from it down is
+// small -- no streaming plan, fewer than 16384 rows and at most 400K stored
+// entries, a few MB that one cluster of 16 SMs reads faster than a
+// full-GPU launch can start -- and at least one of them is smoothed.  Builds
+// the device tables and picks the cluster size.
+int tail_prepare(Hierarchy *h, cudaStream_t) {
+    h->tail_start = -1;
+    const int L = h->nlevels;
+    if (L < 2) return AMG_OK;
+    int t = L - 1;
+    while (t > 0 && h->L[t - 1].sa.rt == 0 && h->L[t - 1].A.nrows < 16384 && h->L[t - 1].A.nnz <= 400000) --t;
+    if (t > L - 2 || L - t > tail::MAX_LEVELS) return AMG_OK;
+    const int cs = h->cfg.precision == AMG_PRECISION_MIXED ? tail_cluster_size<float>() : tail_cluster_size<double>();
+    if (cs == 0) return AMG_OK;
+    h->tail_cluster = cs;
+    AMG_TRY(build_tail_table<double>(h, t, &h->tail_args64));
+    if (h->cfg.precision == AMG_PRECISION_MIXED) AMG_TRY(build_tail_table<float>(h, t, &h->tail_args32));
+    h->tail_start = t;
+    return AMG_OK;
+}
+
+template <typename TM>
+static int launch_tail(Hierarchy *h, Workspace &W, const double *b0, double *z0, const double *rold, int fin,
+                       cudaStream_t s) {
+    const bool mixed = sizeof(TM) == 4;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->tail_cluster);
+    cfg.blockDim = dim3(tail::THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = h->tail_cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const tail::TArgs<TM> *args = (const tail::TArgs<TM> *)(mixed ? h->tail_args32 : h->tail_args64);
+    AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, tail::k_tail<TM>, args, b0, z0, rold, fin, W.scal));
+    return AMG_OK;
+}
+
+// Algorithmic bytes of the fused tail (levels t.. of one V-cycle).
+static double tail_bytes(const Hierarchy *h, int vb) {
+    double by = 0.0;
+    for (int l = h->tail_start; l < h->nlevels - 1; ++l) {
+        const Level &lv = h->L[l];
+        by += 2.0 * (lv.A.nnz * (4.0 + vb) + 4.0 * (lv.A.nrows + 1.0)) + 2.0 * (lv.P.nnz * (4.0 + vb)) +
+              4.0 * (lv.A.nrows + lv.R.nrows + 2.0) + 8.0 * vb * lv.A.nrows;
+    }
+    return by + 8.0 * h->nc * h->nc + 2.0 * vb * h->nc;
+}
+
 // One V-cycle: z0 = M^-1 b0.  TM = float for the mixed form.
 template <typename TM>
 static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z0, int fin, cudaStream_t s) {
@@ -816,8 +1052,13 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         AMG_LAUNCH_CHECK();
         return AMG_OK;
     }
+    const int tl = h->tail_start >= 0 ? h->tail_start : L - 1;  // first level handled by the fused tail
+    if (h->tail_start == 0) {
+        TRACE("tail", 0, tail_bytes(h, vb));
+        return launch_tail<TM>(h, W, b0, z0, rold, fin == FIN_PCG_BETA, s);
+    }
     // down
-    for (int l = 0; l < L - 1; ++l) {
+    for (int l = 0; l < tl; ++l) {
         Level &lv = h->L[l];
         Level &nx = h->L[l + 1];
         const int n = lv.A.nrows;
@@ -851,8 +1092,10 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         }
         AMG_LAUNCH_CHECK();
     }
-    // coarsest
-    {
+    if (h->tail_start > 0) {
+        TRACE("tail", tl, tail_bytes(h, vb));
+        AMG_TRY(launch_tail<TM>(h, W, nullptr, nullptr, nullptr, 0, s));
+    } else {
         Level &lc = h->L[L - 1];
         const double m = h->nc;
         TRACE("coarse", L - 1, m * m * 8.0 + 2.0 * vb * m);
@@ -860,7 +1103,7 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         AMG_LAUNCH_CHECK();
     }
     // up
-    for (int l = L - 2; l >= 0; --l) {
+    for (int l = tl - 1; l >= 0; --l) {
         Level &lv = h->L[l];
         Level &nx = h->L[l + 1];
         const int n = lv.A.nrows;
@@ -1016,6 +1259,47 @@ static int bicg_iteration(Hierarchy *h, Workspace &W, bool precond, cudaStream_t
     return AMG_OK;
 }
 
+static int iterate(Hierarchy *h, Workspace &W, int kind, cudaStream_t s) {
+    switch (kind) {
+        case 0: return cg_iteration(h, W, s);
+        case 1: return pcg_iteration(h, W, s);
+        case 2: return bicg_iteration(h, W, false, s);
+        default: return bicg_iteration(h, W, true, s);
+    }
+}
+
+// One Krylov iteration (kind: 0 CG, 1 PCG, 2 BiCGStab, 3 AMG-BiCGStab).  The
+// iteration's kernels are captured once per hierarchy as a CUDA graph and
+// replayed, which removes most of the per-launch cost of the ~25 kernels; the
+// launch count still advances by the kernels the graph holds.  With
+// per-kernel tracing on, the kernels are launched directly.
+static int run_iteration(Hierarchy *h, Workspace &W, int kind, cudaStream_t s) {
+    if (W.prof.on) return iterate(h, W, kind, s);
+    if (!h->iter_exec || h->iter_kind != kind) {
+        if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
+        h->iter_exec = nullptr;
+        const long long before = W.prof.launches;
+        AMG_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const int rc = iterate(h, W, kind, s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(s, &g);
+        if (rc < 0) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        AMG_CUDA_TRY(ce);
+        const cudaError_t ie = cudaGraphInstantiate(&h->iter_exec, g, 0);
+        cudaGraphDestroy(g);
+        AMG_CUDA_TRY(ie);
+        h->iter_kind = kind;
+        h->iter_kernels = (int)(W.prof.launches - before);
+        W.prof.launches = before;
+    }
+    AMG_CUDA_TRY(cudaGraphLaunch(h->iter_exec, s));
+    W.prof.launches += h->iter_kernels;
+    return AMG_OK;
+}
+
 static int read_scalars(Workspace &W, cudaStream_t s) {
     AMG_CUDA_TRY(cudaMemcpyAsync(W.scal_h, W.scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1081,9 +1365,7 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
         // at max_iter at the latest, launch_cap only guards the host loop
         for (;;) {
             for (int k = 0; k < chunk; ++k) {
-                if (bicg) AMG_TRY(bicg_iteration(h, W, precond, s));
-                else if (precond) AMG_TRY(pcg_iteration(h, W, s));
-                else AMG_TRY(cg_iteration(h, W, s));
+                AMG_TRY(run_iteration(h, W, bicg ? (precond ? 3 : 2) : (precond ? 1 : 0), s));
             }
             launched += chunk;
             AMG_TRY(read_scalars(W, s));

@@ -58,6 +58,10 @@ struct Workspace {
 };
 
 int workspace_init(Workspace &W, int n);
+
+// Refines the hierarchy's streaming plans by timed trial (needs the workspace's
+// device scalars for the kernels' done flag).
+int autotune_plans(Hierarchy *h, DevScalars *sc, cudaStream_t s);
 void workspace_free(Workspace &W);
 
 struct SolveResult {
