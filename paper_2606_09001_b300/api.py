@@ -270,22 +270,45 @@ class SetupCache:
     """LRU cache of Solver handles keyed by a hash of the full sparsity
     pattern, the dimensions, the precision and the configuration (the key
     the paper's backend uses).  A hit whose values differ rebuilds the
-    hierarchy for the new values."""
+    hierarchy for the new values.  The pattern hash is memoised per tensor
+    (identity and version counter); values are compared exactly against a
+    stored copy on their own device."""
 
     def __init__(self, capacity: int = 8):
         self.capacity = capacity
         self._d: OrderedDict = OrderedDict()
+        self._pattern_memo: dict = {}
         self.hits = self.misses = 0
 
+    def _pattern_digest(self, row_ptr, col_idx) -> str:
+        if isinstance(row_ptr, torch.Tensor) and isinstance(col_idx, torch.Tensor):
+            mk = (row_ptr.data_ptr(), row_ptr._version, tuple(row_ptr.shape), str(row_ptr.device),
+                  col_idx.data_ptr(), col_idx._version, tuple(col_idx.shape))
+            d = self._pattern_memo.get(mk)
+            if d is None:
+                d = _digest(row_ptr, col_idx)
+                if len(self._pattern_memo) > 64:
+                    self._pattern_memo.clear()
+                self._pattern_memo[mk] = d
+            return d
+        return _digest(row_ptr, col_idx)
+
     def key(self, row_ptr, col_idx, cfg: AmgConfig):
-        return (_digest(row_ptr, col_idx), int(row_ptr.shape[0]) - 1, int(col_idx.shape[0]),
+        return (self._pattern_digest(row_ptr, col_idx), int(row_ptr.shape[0]) - 1, int(col_idx.shape[0]),
                 tuple(sorted(config_dict(cfg).items())))
+
+    @staticmethod
+    def _same(a, b) -> bool:
+        if isinstance(a, torch.Tensor) and isinstance(b, torch.Tensor):
+            return a.device == b.device and a.shape == b.shape and bool(torch.equal(a, b))
+        if isinstance(a, np.ndarray) and isinstance(b, np.ndarray):
+            return a.shape == b.shape and np.array_equal(a, b)
+        return False
 
     def get(self, row_ptr, col_idx, values, cfg: AmgConfig) -> Solver:
         k = self.key(row_ptr, col_idx, cfg)
-        vd = _digest(values)
         ent = self._d.get(k)
-        if ent is not None and ent[1] == vd:
+        if ent is not None and self._same(ent[1], values):
             self._d.move_to_end(k)
             self.hits += 1
             return ent[0]
@@ -293,7 +316,8 @@ class SetupCache:
         if ent is not None:
             ent[0].close()
         s = Solver(row_ptr, col_idx, values, cfg)
-        self._d[k] = (s, vd)
+        kept = values.detach().clone() if isinstance(values, torch.Tensor) else np.array(values, copy=True)
+        self._d[k] = (s, kept)
         self._d.move_to_end(k)
         while len(self._d) > self.capacity:
             _, (old, _) = self._d.popitem(last=False)
