@@ -160,6 +160,12 @@ __global__ void __launch_bounds__(THREADS) k_stream(int n, int rt, int cap, int 
             const int t = blockIdx.x + j * gridDim.x;
             if (t >= ntiles) break;
             const int st = j % STAGES;
+            const int r0 = t * rt;
+            const int rows = min(rt, n - r0);
+            // the first pass's epilogue operands are loaded before the stage
+            // wait, so their latency overlaps the bulk copy's
+            typename Op::Pre pre0{};
+            if (rsub < rows && vl == 0) pre0 = op.load(r0 + rsub);
             if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / STAGES) & 1)))) {  // warp-uniform
                 ok = false;
                 break;
@@ -170,14 +176,12 @@ __global__ void __launch_bounds__(THREADS) k_stream(int n, int rt, int cap, int 
             const TM *vals = reinterpret_cast<const TM *>(stage + L.rpb + L.cib);
             const int *hdr = reinterpret_cast<const int *>(stage + L.rpb + L.cib + L.vab);
             const int cs = hdr[0], vsb = hdr[1];
-            const int r0 = t * rt;
-            const int rows = min(rt, n - r0);
             for (int base = 0; base < rows; base += ROWS_PER_PASS) {
                 const int rl = base + rsub;
                 TM sum = 0;
-                typename Op::Pre pre{};
+                typename Op::Pre pre = pre0;
                 if (rl < rows) {
-                    if (vl == 0) pre = op.load(r0 + rl);
+                    if (vl == 0 && base > 0) pre = op.load(r0 + rl);
                     const int k1 = rps[rl + 1];
                     for (int kb = rps[rl] + vl; kb < k1; kb += UNR * VEC) {
                         TM av[UNR], xv[UNR];
