@@ -175,6 +175,51 @@ int amg_profile_summary(amg_handle h, long long *launches, int *nrecords);
 int amg_profile_record(amg_handle h, int i, char *name, int name_len, int *level, long long *launches,
                        double *total_ms, double *total_bytes);
 
+/* Right-hand sides per system that one batched solve carries. */
+#define AMG_BATCH_MAX_RHS 8
+
+/* Batched systems and right-hand sides (the paper's Sec. 2.2 applies the
+ * solver over a batch of right-hand sides with one cached setup; here many
+ * independent systems, each with up to AMG_BATCH_MAX_RHS right-hand sides,
+ * are solved concurrently).  The caller passes nsys independent square
+ * systems as ONE block-diagonal CSR of n rows: system k owns rows and
+ * columns sys_off[k] .. sys_off[k+1]-1 (sys_off has nsys + 1 entries, host
+ * or device, sys_off[0] = 0, sys_off[nsys] = n, every system non-empty), and
+ * a row of system k may store columns of system k only (AMG_ERR_BAD_CSR
+ * otherwise).  Each system gets the hierarchy amg_setup would build for it
+ * alone -- the same strength graph, aggregates, prolongators and Galerkin
+ * operators, bit for bit -- built for all systems at once; a system whose
+ * coarsening ends (at most coarse_max rows, or max_levels) is solved densely
+ * on that level while the others continue.  cfg->solver must be
+ * AMG_SOLVER_PCG (AMG_ERR_UNSUPPORTED otherwise); precision FP64 or MIXED.
+ * The handle serves amg_solve_batched, amg_batch_level, amg_get_level,
+ * amg_get_aggregates, amg_get_info, the amg_profile* calls and amg_free;
+ * amg_solve, amg_adjoint and amg_vcycle return AMG_ERR_ARG on it.
+ * Errors as amg_setup. */
+int amg_setup_batched(const amg_config *cfg, int nsys, const int *sys_off, int n, long long nnz,
+                      const int *row_ptr, const int *col_idx, const double *values, void *cuda_stream,
+                      amg_handle *out);
+
+/* Solves A_k X_k = B_k for every system k of a batched handle, each column
+ * (right-hand side) on its own: preconditioned CG from x0 = 0 with one
+ * V-cycle per iteration, its own step sizes, and its own stop at
+ * ||b - A x||_2 <= rtol ||b||_2 (true-residual restarts as amg_solve).
+ * B and X: n x nrhs, row-major ([row][rhs]), 1 <= nrhs <= AMG_BATCH_MAX_RHS,
+ * host or device.  iters (int) and rel_res (double, true relative
+ * residual): nsys x nrhs row-major, host or device, may be NULL.  info may be
+ * NULL; its status is the worst status of any pair, iters the largest count,
+ * rel_res_true the largest relative residual.  Returns that worst status or
+ * a hard error. */
+int amg_solve_batched(amg_handle h, int nrhs, const double *B, double *X, int *iters, double *rel_res,
+                      void *cuda_stream, amg_info *info);
+
+/* Layout of level `level` of a batched handle: *nsys_level systems live on
+ * it; if the arrays are non-NULL (host, sized for the batch's nsys and
+ * nsys + 1 entries), sys[j] is the j-th of them (ascending ids), row_off[j]
+ * its first row on this level (row_off[*nsys_level] = the level's rows) and
+ * final[j] 1 if its coarsening ends here (solved densely on this level). */
+int amg_batch_level(amg_handle h, int level, int *nsys_level, int *sys, int *row_off, int *final_flags);
+
 /* Largest system amg_cg_solve_noalloc accepts (rows). */
 #define AMG_NOALLOC_MAX_N (1 << 18)
 

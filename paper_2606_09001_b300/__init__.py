@@ -6,13 +6,13 @@ sm_103a CUDA kernels behind a C ABI, include/amg_b300.h).
 """
 from __future__ import annotations
 
-__all__ = ["Solver", "solve", "amg_solve", "SetupCache", "Info", "AMGError", "make_config"]
+__all__ = ["Solver", "BatchedSolver", "solve", "amg_solve", "SetupCache", "Info", "AMGError", "make_config"]
 
 
 def __getattr__(name):
     # The CUDA-facing modules import torch; load them on first use so that
     # the input generators (matrices) import without it.
-    if name in ("Solver", "solve", "SetupCache", "Info", "AMGError", "make_config"):
+    if name in ("Solver", "BatchedSolver", "solve", "SetupCache", "Info", "AMGError", "make_config"):
         from . import api
         return getattr(api, name)
     if name == "amg_solve":

@@ -16,6 +16,7 @@ AMG_ERR_STALL, AMG_ERR_OOM, AMG_ERR_UNSUPPORTED = -5, -6, -7
 AMG_MAX_LEVELS = 32
 AMG_DENSE_MAX = 256
 AMG_NOALLOC_MAX_N = 1 << 18
+AMG_BATCH_MAX_RHS = 8
 
 SOLVERS = {"PCG": 0, "BICGSTAB": 1, "CG": 2, "BICGSTAB_NOPREC": 3}
 SMOOTHERS = {"JACOBI": 0, "L1_JACOBI": 1}
@@ -24,7 +25,7 @@ PRECISIONS = {"FP64": 0, "MIXED": 1}
 # Every symbol the header declares.
 EXPORTS = ("amg_config_default", "amg_setup", "amg_solve", "amg_adjoint", "amg_vcycle", "amg_get_info",
            "amg_get_level", "amg_get_aggregates", "amg_profile", "amg_profile_summary", "amg_profile_record",
-           "amg_cg_solve_noalloc", "amg_free", "amg_status_string", "amg_last_error")
+           "amg_setup_batched", "amg_solve_batched", "amg_batch_level", "amg_cg_solve_noalloc", "amg_free", "amg_status_string", "amg_last_error")
 
 
 class AmgConfig(C.Structure):
@@ -68,6 +69,9 @@ def load() -> C.CDLL:
         L.amg_profile_summary.argtypes = [vp, C.POINTER(ll), C.POINTER(i)]
         L.amg_profile_record.argtypes = [vp, i, C.c_char_p, i, C.POINTER(i), C.POINTER(ll), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]
+        L.amg_setup_batched.argtypes = [C.POINTER(AmgConfig), i, vp, i, ll, vp, vp, vp, vp, C.POINTER(vp)]
+        L.amg_solve_batched.argtypes = [vp, i, vp, vp, vp, vp, vp, C.POINTER(AmgInfo)]
+        L.amg_batch_level.argtypes = [vp, i, C.POINTER(i), vp, vp, vp]
         L.amg_cg_solve_noalloc.argtypes = [i, ll, vp, vp, vp, vp, vp, C.c_double, i, vp, C.POINTER(AmgInfo)]
         L.amg_free.argtypes = [vp]
         L.amg_status_string.argtypes = [i]

@@ -250,6 +250,69 @@ class Solver:
         return agg
 
 
+class BatchedSolver(Solver):
+    """Many independent systems, each with up to 8 right-hand sides, solved
+    concurrently with one cached setup (amg_setup_batched ...
+    amg_solve_batched).  The systems are passed as one block-diagonal CSR
+    whose system k owns rows sys_off[k] .. sys_off[k+1]-1."""
+
+    def __init__(self, sys_off, row_ptr, col_idx, values, config: dict | AmgConfig | None = None,
+                 stream: int | None = None):
+        L = _lib.load()
+        for a, k in ((sys_off, "i32"), (row_ptr, "i32"), (col_idx, "i32"), (values, "f64")):
+            _check_dtype(a, k)
+        self.n = int(row_ptr.shape[0]) - 1
+        self.nnz = int(col_idx.shape[0])
+        self.nsys = int(sys_off.shape[0]) - 1
+        self.config = config if isinstance(config, AmgConfig) else make_config(config)
+        h = C.c_void_p()
+        s = _stream_of(row_ptr, col_idx, values) if stream is None else stream
+        rc = L.amg_setup_batched(C.byref(self.config), self.nsys, _ptr(sys_off), self.n, self.nnz, _ptr(row_ptr),
+                                 _ptr(col_idx), _ptr(values), s, C.byref(h))
+        if rc != _lib.AMG_OK:
+            raise AMGError(rc, "amg_setup_batched")
+        self._h = h
+        self._L = L
+
+    def solve(self, B, X=None, stream: int | None = None, info: bool = True, check: bool = False):
+        """X[:, r] = A^-1 B[:, r] for every column of B (n x nrhs, nrhs <= 8)
+        on every system.  Returns (X, iters [nsys, nrhs], rel_res [nsys, nrhs],
+        Info)."""
+        _check_dtype(B, "f64")
+        if B.ndim == 1:
+            B = B.reshape(-1, 1)
+        nrhs = int(B.shape[1])
+        if X is None:
+            X = torch.empty_like(B) if isinstance(B, torch.Tensor) else np.empty_like(B)
+        its = np.empty((self.nsys, nrhs), np.int32)
+        rel = np.empty((self.nsys, nrhs))
+        ci = AmgInfo()
+        s = _stream_of(B, X) if stream is None else stream
+        rc = self._L.amg_solve_batched(self._h, nrhs, _ptr(B), _ptr(X), its.ctypes.data, rel.ctypes.data, s,
+                                       C.byref(ci) if info else None)
+        if rc < 0 or (check and rc != 0):
+            raise AMGError(rc, "amg_solve_batched")
+        return X, its, rel, (Info.from_c(ci) if info else rc)
+
+    def adjoint(self, *a, **k):
+        raise AMGError(_lib.AMG_ERR_ARG, "BatchedSolver.adjoint (not provided for batches)")
+
+    def vcycle(self, *a, **k):
+        raise AMGError(_lib.AMG_ERR_ARG, "BatchedSolver.vcycle (not provided for batches)")
+
+    def batch_level(self, l: int):
+        """(system ids, row offsets, final flags) of level l."""
+        ns = C.c_int()
+        sys_ = np.empty(self.nsys, np.int32)
+        off = np.empty(self.nsys + 1, np.int32)
+        fin = np.empty(self.nsys, np.int32)
+        rc = self._L.amg_batch_level(self._h, l, C.byref(ns), sys_.ctypes.data, off.ctypes.data, fin.ctypes.data)
+        if rc < 0:
+            raise AMGError(rc, "amg_batch_level")
+        k = ns.value
+        return sys_[:k], off[:k + 1], fin[:k].astype(bool)
+
+
 # ---------------------------------------------------------------------------
 # Setup cache and the solve entry point
 # ---------------------------------------------------------------------------

@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
                  "--expt-relaxed-constexpr"]
 PER_FILE = {"setup.cu": ["-fmad=false"]}
-SOURCES = ["setup.cu", "solve.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["setup.cu", "solve.cu", "batched.cu", "api.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

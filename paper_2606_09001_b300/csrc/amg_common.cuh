@@ -150,6 +150,18 @@ struct Level {
     int vec_a = 8, vec_p = 8, vec_r = 8;  // threads per row chosen per operator
 };
 
+// One level of a block-diagonal batch: which systems are present, where their
+// rows start, and which of them end here (solved densely on this level).
+struct BatchLevel {
+    std::vector<int> sys;            // system ids present on this level, ascending
+    std::vector<int> off;            // row offsets of those systems (size + 1)
+    std::vector<unsigned char> fin;  // 1: the system's last level is this one
+    int nfin = 0, max_m = 0;
+    int *fin_r0 = nullptr, *fin_m = nullptr;  // device: first row and size of each final system
+    long long *fin_off2 = nullptr;            // device: offset of its dense inverse in binv
+    double *binv = nullptr;                   // device: the final systems' dense inverses, FP64
+};
+
 struct Hierarchy {
     amg_config cfg;
     int n = 0;
@@ -161,6 +173,8 @@ struct Hierarchy {
     double *cinv = nullptr;     // dense inverse of the coarsest operator, nc x nc row-major
     // Fused coarse levels: levels tail_start..nlevels-1 run in one cluster launch
     // (tail_start = -1: not used); device tables for FP64 and FP32 cycles.
+    int nsys = 0;                  // > 0: a block-diagonal batch of nsys independent systems
+    std::vector<BatchLevel> bl;    // per level (batches only)
     int tail_start = -1;
     int tail_cluster = 0;
     void *tail_args64 = nullptr;
@@ -198,6 +212,8 @@ int exclusive_scan_int(const int *in, int *out, int n, int *total_host, cudaStre
 int transpose_csr(const DevCSR &a, DevCSR &t, DevArena &arena, cudaStream_t s);
 int build_hierarchy(Hierarchy *h, const int *rp, const int *ci, const double *v, cudaStream_t s);
 int tail_prepare(Hierarchy *h, cudaStream_t s);
+int build_hierarchy_batched(Hierarchy *h, const int *rp, const int *ci, const double *v, const int *sys_off_host,
+                            int nsys, cudaStream_t s);
 void free_hierarchy(Hierarchy *h);
 int num_sms();
 

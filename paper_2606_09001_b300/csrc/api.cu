@@ -15,6 +15,7 @@ struct amg_handle_s {
     Hierarchy H;              // hierarchy of A
     Hierarchy *HT = nullptr;  // hierarchy of A^T (nonsymmetric adjoint), built on first use
     Workspace W;
+    amg_batch_ws *BW = nullptr;  // batched handles only
     cudaStream_t s = nullptr; // private stream; ordered after/before the caller's stream by events
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     double *dA_stage = nullptr;  // device staging of dL/dA for host outputs
@@ -92,11 +93,39 @@ void destroy(amg_handle h) {
         delete h->HT;
     }
     workspace_free(h->W);
+    batch_destroy(h->BW);
     h->extra.free_all();
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->s) cudaStreamDestroy(h->s);
     delete h;
+}
+
+int single_only(amg_handle h, const char *fn) {
+    if (h->H.nsys > 0) {
+        set_last_error("%s: the handle holds a batch of systems (use amg_solve_batched)", fn);
+        return AMG_ERR_ARG;
+    }
+    return AMG_OK;
+}
+
+int make_handle(amg_handle *out, void *cuda_stream) {
+    amg_handle h = new (std::nothrow) amg_handle_s();
+    if (!h) return AMG_ERR_OOM;
+    if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        set_last_error("stream/event creation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        destroy(h);
+        return AMG_ERR_CUDA;
+    }
+    const int rc = enter(h, cuda_stream);
+    if (rc < 0) {
+        destroy(h);
+        return rc;
+    }
+    *out = h;
+    return AMG_OK;
 }
 
 int run_solve(amg_handle h, Hierarchy *H, cudaStream_t s) {
@@ -173,6 +202,7 @@ int amg_setup(const amg_config *cfg, int n, long long nnz, const int *row_ptr, c
 
 int amg_solve(amg_handle h, const double *b, double *x, void *cuda_stream, amg_info *info) {
     if (!h || !b || !x) return AMG_ERR_ARG;
+    AMG_TRY(single_only(h, "amg_solve"));
     const int n = h->H.n;
     AMG_TRY(enter(h, cuda_stream));
     AMG_CUDA_TRY(cudaMemcpyAsync(h->W.b, b, sizeof(double) * n, cudaMemcpyDefault, h->s));
@@ -187,6 +217,7 @@ int amg_solve(amg_handle h, const double *b, double *x, void *cuda_stream, amg_i
 int amg_adjoint(amg_handle h, const double *x, const double *g, double *lambda, double *dA, void *cuda_stream,
                 amg_info *info) {
     if (!h || !x || !g) return AMG_ERR_ARG;
+    AMG_TRY(single_only(h, "amg_adjoint"));
     const int n = h->H.n;
     const long long nnz = h->H.nnz;
     AMG_TRY(enter(h, cuda_stream));
@@ -247,6 +278,7 @@ int amg_adjoint(amg_handle h, const double *x, const double *g, double *lambda, 
 
 int amg_vcycle(amg_handle h, const double *r, double *z, void *cuda_stream) {
     if (!h || !r || !z) return AMG_ERR_ARG;
+    AMG_TRY(single_only(h, "amg_vcycle"));
     const int n = h->H.n;
     AMG_TRY(enter(h, cuda_stream));
     AMG_CUDA_TRY(cudaMemcpyAsync(h->W.b, r, sizeof(double) * n, cudaMemcpyDefault, h->s));
@@ -314,6 +346,80 @@ int amg_profile_record(amg_handle h, int i, char *name, int name_len, int *level
     if (launches) *launches = r.launches;
     if (total_ms) *total_ms = r.ms;
     if (total_bytes) *total_bytes = r.bytes;
+    return AMG_OK;
+}
+
+int amg_setup_batched(const amg_config *cfg, int nsys, const int *sys_off, int n, long long nnz,
+                      const int *row_ptr, const int *col_idx, const double *values, void *cuda_stream,
+                      amg_handle *out) {
+    if (!out) return AMG_ERR_ARG;
+    *out = nullptr;
+    if (nsys <= 0 || nsys > n || n <= 0 || nnz < n || nnz >= (1LL << 31) - 1 || !sys_off || !row_ptr || !col_idx ||
+        !values) {
+        set_last_error("amg_setup_batched: invalid sizes or null array (nsys=%d, n=%d, nnz=%lld)", nsys, n, nnz);
+        return AMG_ERR_ARG;
+    }
+    amg_config c;
+    if (cfg) c = *cfg;
+    else amg_config_default(&c);
+    AMG_TRY(check_config(c));
+    if (c.solver != AMG_SOLVER_PCG) {
+        set_last_error("amg_setup_batched: only AMG_SOLVER_PCG is supported for batches");
+        return AMG_ERR_UNSUPPORTED;
+    }
+    std::vector<int> off((size_t)nsys + 1);
+    AMG_CUDA_TRY(cudaMemcpy(off.data(), sys_off, sizeof(int) * off.size(), cudaMemcpyDefault));
+    const auto t0 = clk::now();
+    amg_handle h = nullptr;
+    AMG_TRY(make_handle(&h, cuda_stream));
+    int rc = AMG_OK;
+    do {
+        h->H.cfg = c;
+        h->H.n = n;
+        h->H.nnz = nnz;
+        if ((rc = build_hierarchy_batched(&h->H, row_ptr, col_idx, values, off.data(), nsys, h->s)) != AMG_OK) break;
+        if ((rc = batch_create(&h->H, &h->BW)) < 0) break;
+        if ((rc = leave(h, cuda_stream, true)) < 0) break;
+    } while (0);
+    if (rc != AMG_OK) {
+        destroy(h);
+        return rc;
+    }
+    h->H.setup_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    *out = h;
+    return AMG_OK;
+}
+
+int amg_solve_batched(amg_handle h, int nrhs, const double *B, double *X, int *iters, double *rel_res,
+                      void *cuda_stream, amg_info *info) {
+    if (!h || !B || !X || nrhs < 1 || nrhs > AMG_BATCH_MAX_RHS) return AMG_ERR_ARG;
+    if (!h->BW) {
+        set_last_error("amg_solve_batched: the handle was not made by amg_setup_batched");
+        return AMG_ERR_ARG;
+    }
+    AMG_TRY(enter(h, cuda_stream));
+    const auto t0 = clk::now();
+    SolveResult r;
+    const int rc = batch_solve(&h->H, h->BW, h->W.prof, nrhs, B, X, iters, rel_res, h->s, &r);
+    h->last_solve_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    if (rc < 0) return rc;
+    h->last = r;
+    AMG_TRY(leave(h, cuda_stream, true));
+    if (info) fill_info(h, h->H, info);
+    return r.status;
+}
+
+int amg_batch_level(amg_handle h, int level, int *nsys_level, int *sys, int *row_off, int *final_flags) {
+    if (!h || !nsys_level || h->H.nsys <= 0 || level < 0 || level >= h->H.nlevels) return AMG_ERR_ARG;
+    const BatchLevel &b = h->H.bl[level];
+    const int ns = (int)b.sys.size();
+    *nsys_level = ns;
+    for (int j = 0; j < ns; ++j) {
+        if (sys) sys[j] = b.sys[j];
+        if (final_flags) final_flags[j] = b.fin[j];
+    }
+    if (row_off)
+        for (int j = 0; j <= ns; ++j) row_off[j] = b.off[j];
     return AMG_OK;
 }
 

@@ -1,0 +1,688 @@
+// batched.cu -- many independent systems with several right-hand sides each.
+//
+// The systems form one block-diagonal CSR (hierarchy: build_hierarchy_batched)
+// and every right-hand side of every system is its own preconditioned CG
+// problem (the paper's sequential vmap over right-hand sides, Sec. 2.2, run
+// concurrently): vectors are stored row-interleaved [row][K] with K = 8, so
+// each stored matrix entry is read once for all K right-hand sides, and every
+// (system, right-hand side) pair carries its own Krylov scalars and stops on
+// its own (a per-pair convergence mask).  The V-cycle runs in FP32 or FP64
+// (the handle's precision); the Krylov vectors, dot products and the
+// coarsest solves are FP64.
+//
+// Finest-level row passes run over "chunks" (at most CH consecutive rows of
+// one system) so that dot products reduce per system deterministically: each
+// chunk writes its partial sums, and the last chunk of a system to finish
+// (per-system ticket) adds them in chunk order and updates that system's
+// scalars.  Rows of a system whose last level is level l (smoother weight
+// 0) are written only by the dense solve of that level.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "solve.cuh"
+
+namespace amg {
+
+constexpr int K = 8;          // right-hand sides per system, interleaved
+constexpr int BT = 256;       // threads per block: 32 rows x K
+constexpr int CH = 512;       // rows per finest-level chunk
+
+struct BDev {
+    int n = 0, nsys = 0, npairs = 0, nchunks = 0;
+    // finest-level chunks: system, first row, row count; per system: first chunk, chunks
+    int *ch_sys = nullptr, *ch_r0 = nullptr, *ch_rows = nullptr;
+    int *sys_ch0 = nullptr, *sys_nch = nullptr;
+    unsigned *ticket = nullptr;   // per system
+    double *part = nullptr;       // [chunk][K][2]
+    // outer vectors [n][K], FP64
+    double *B = nullptr, *X = nullptr, *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr, *Rold = nullptr;
+    // per pair (system * K + rhs)
+    double *bn2 = nullptr, *tol2 = nullptr, *rz = nullptr, *alpha = nullptr, *beta = nullptr, *rr = nullptr,
+           *tr = nullptr;
+    int *act = nullptr, *first = nullptr, *iters = nullptr, *status = nullptr;
+    int *nact = nullptr;          // active pairs (device), polled by the host
+    // Active pairs per system.  A chunked kernel exits early on its own
+    // system's count: that count changes only in the system's last chunk,
+    // after every chunk of the system has read it, so all chunks of a system
+    // take the same branch (the global count may drop mid-kernel).
+    int *sys_nact = nullptr;
+};
+
+}  // namespace amg
+
+struct amg_batch_ws {
+    amg::BDev d;
+    // level vectors [n_l][K] at the V-cycle's precision
+    void *lb[AMG_MAX_LEVELS] = {}, *lt[AMG_MAX_LEVELS] = {}, *lx[AMG_MAX_LEVELS] = {};
+    cudaGraphExec_t iter_exec = nullptr;
+    int iter_kernels = 0;
+    amg::DevArena arena;
+};
+
+namespace amg {
+
+using BatchWorkspace = amg_batch_ws;
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+template <typename TA, typename TX>
+__device__ __forceinline__ TA spmm_row(const int *__restrict__ rp, const int *__restrict__ ci,
+                                       const TA *__restrict__ v, const TX *__restrict__ x, int i, int r) {
+    TA s = 0;
+    const int e = rp[i + 1];
+    int k = rp[i];
+    for (; k + 3 < e; k += 4) {
+        const int j0 = ci[k], j1 = ci[k + 1], j2 = ci[k + 2], j3 = ci[k + 3];
+        const TA a0 = v[k], a1 = v[k + 1], a2 = v[k + 2], a3 = v[k + 3];
+        const TA x0 = (TA)x[(size_t)j0 * K + r], x1 = (TA)x[(size_t)j1 * K + r];
+        const TA x2 = (TA)x[(size_t)j2 * K + r], x3 = (TA)x[(size_t)j3 * K + r];
+        s += a0 * x0 + a1 * x1 + a2 * x2 + a3 * x3;
+    }
+    for (; k < e; ++k) s += v[k] * (TA)x[(size_t)ci[k] * K + r];
+    return s;
+}
+
+#define ROWS_K(n)                                                                                   \
+    for (long long e_ = (long long)blockIdx.x * BT + threadIdx.x; e_ < (long long)(n) * K;         \
+         e_ += (long long)gridDim.x * BT) {                                                        \
+        const int i = (int)(e_ / K), r = (int)(e_ % K);
+
+// t = b - (A W) b
+template <typename TB, typename TM>
+__global__ void __launch_bounds__(BT) kb_presmooth(int n, const int *rp, const int *ci, const TM *ahat,
+                                                   const TB *b, TM *t, const int *nact) {
+    if (*nact == 0) return;
+    ROWS_K(n)
+    t[(size_t)i * K + r] = (TM)b[(size_t)i * K + r] - spmm_row<TM, TB>(rp, ci, ahat, b, i, r);
+}
+}
+
+// y = M x (restriction)
+template <typename TM>
+__global__ void __launch_bounds__(BT) kb_spmm(int n, const int *rp, const int *ci, const TM *v, const TM *x, TM *y,
+                                              const int *nact) {
+    if (*nact == 0) return;
+    ROWS_K(n)
+    y[(size_t)i * K + r] = spmm_row<TM, TM>(rp, ci, v, x, i, r);
+}
+}
+
+// t = W b + P x_c
+template <typename TB, typename TM>
+__global__ void __launch_bounds__(BT) kb_prolong(int n, const int *rp, const int *ci, const TM *pv, const TM *w,
+                                                 const TB *b, const TM *xc, TM *t, const int *nact) {
+    if (*nact == 0) return;
+    ROWS_K(n)
+    t[(size_t)i * K + r] = w[i] * (TM)b[(size_t)i * K + r] + spmm_row<TM, TM>(rp, ci, pv, xc, i, r);
+}
+}
+
+// x = t + W (b - A t) on rows with w > 0 (rows with w = 0 belong to a dense solve)
+template <typename TB, typename TM, typename TO>
+__global__ void __launch_bounds__(BT) kb_postsmooth(int n, const int *rp, const int *ci, const TM *av, const TM *w,
+                                                    const TB *b, const TM *t, TO *x, const int *nact) {
+    if (*nact == 0) return;
+    ROWS_K(n)
+    const TM wi = w[i];
+    if (wi != (TM)0) {
+        const TM s = spmm_row<TM, TM>(rp, ci, av, t, i, r);
+        x[(size_t)i * K + r] = (TO)(t[(size_t)i * K + r] + wi * ((TM)b[(size_t)i * K + r] - s));
+    }
+}
+}
+
+// Dense solves of the systems whose last level this is: block per system.
+template <typename TB, typename TO>
+__global__ void __launch_bounds__(BT) kb_dense(const int *r0s, const int *ms, const long long *off2,
+                                               const double *binv, const TB *b, TO *x, const int *nact) {
+    if (*nact == 0) return;
+    const int f = blockIdx.x, r0 = r0s[f], m = ms[f];
+    const double *inv = binv + off2[f];
+    for (int e = threadIdx.x; e < m * K; e += BT) {
+        const int i = e / K, r = e % K;
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s += inv[(size_t)i * m + j] * (double)b[(size_t)(r0 + j) * K + r];
+        x[(size_t)(r0 + i) * K + r] = (TO)s;
+    }
+}
+
+// Block reduction of acc[NV] per right-hand side (thread r = tid % K), the
+// chunk's partials, and in the last chunk of the system the per-system totals
+// (returned in tot[q], valid in threads tid < K for right-hand side tid).
+template <int NV>
+__device__ bool chunk_reduce(double (&acc)[NV], int chunk, int sys, const BDev &W, double (&tot)[NV]) {
+    __shared__ double sh[NV][BT];
+    __shared__ bool s_last;
+    for (int q = 0; q < NV; ++q) sh[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        for (int q = 0; q < NV; ++q) {
+            double a = 0.0;
+            for (int t = threadIdx.x; t < BT; t += K) a += sh[q][t];
+            W.part[((size_t)chunk * K + threadIdx.x) * 2 + q] = a;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&W.ticket[sys], 1u) == (unsigned)W.sys_nch[sys] - 1;
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    if (threadIdx.x < K) {
+        const int c0 = W.sys_ch0[sys], nc = W.sys_nch[sys];
+        for (int q = 0; q < NV; ++q) {
+            double a = 0.0;
+            for (int c = c0; c < c0 + nc; ++c) a += __ldcg(&W.part[((size_t)c * K + threadIdx.x) * 2 + q]);
+            tot[q] = a;
+        }
+    }
+    if (threadIdx.x == 0) W.ticket[sys] = 0u;
+    return true;
+}
+
+__device__ __forceinline__ void deactivate(const BDev &W, int p, int status) {
+    W.status[p] = status;
+    W.act[p] = 0;
+    atomicSub(&W.sys_nact[p / K], 1);
+    atomicSub(W.nact, 1);
+}
+
+// Finest level, chunked: z = t + W (b - A t) (rows with w = 0 keep the dense
+// solve's z), r.z and r_old.z per pair -> beta.
+template <typename TM>
+__global__ void __launch_bounds__(BT) kb_post0(BDev W, const int *rp, const int *ci, const TM *av,
+                                               const TM *w, const TM *t, int flexible) {
+    const int chunk = blockIdx.x, sys = W.ch_sys[chunk], r0 = W.ch_r0[chunk], rows = W.ch_rows[chunk];
+    if (W.sys_nact[sys] == 0) return;
+    const int r = threadIdx.x % K;
+    double acc[2] = {0.0, 0.0};
+    for (int il = threadIdx.x / K; il < rows; il += BT / K) {
+        const int i = r0 + il;
+        const size_t e = (size_t)i * K + r;
+        const TM wi = w[i];
+        double o;
+        if (wi != (TM)0) {
+            const TM s = spmm_row<TM, TM>(rp, ci, av, t, i, r);
+            o = (double)(t[e] + wi * ((TM)W.R[e] - s));
+            W.Z[e] = o;
+        } else {
+            o = W.Z[e];
+        }
+        acc[0] += W.R[e] * o;
+        if (flexible) acc[1] += W.Rold[e] * o;
+    }
+    double tot[2];
+    if (chunk_reduce<2>(acc, chunk, sys, W, tot) && threadIdx.x < K) {
+        const int p = sys * K + threadIdx.x;
+        if (W.act[p]) {
+            if (!isfinite(tot[0])) {
+                deactivate(W, p, AMG_NAN);
+            } else {
+                W.beta[p] = W.first[p] ? 0.0 : (flexible ? tot[0] - tot[1] : tot[0]) / W.rz[p];
+                W.first[p] = 0;
+                W.rz[p] = tot[0];
+            }
+        }
+    }
+}
+
+// p = z + beta p (active pairs)
+__global__ void __launch_bounds__(BT) kb_p(BDev W) {
+    const int chunk = blockIdx.x, sys = W.ch_sys[chunk], r0 = W.ch_r0[chunk], rows = W.ch_rows[chunk];
+    const int r = threadIdx.x % K, p = sys * K + r;
+    if (!W.act[p]) return;
+    const double beta = W.beta[p];
+    for (int il = threadIdx.x / K; il < rows; il += BT / K) {
+        const size_t e = (size_t)(r0 + il) * K + r;
+        W.P[e] = beta == 0.0 ? W.Z[e] : W.Z[e] + beta * W.P[e];
+    }
+}
+
+// q = A p, p.q per pair -> alpha; or (TRUE_RES) r = b - A x, ||r||^2 per pair
+template <bool TRUE_RES>
+__global__ void __launch_bounds__(BT) kb_spmv0(BDev W, const int *rp, const int *ci, const double *av) {
+    const int chunk = blockIdx.x, sys = W.ch_sys[chunk], r0 = W.ch_r0[chunk], rows = W.ch_rows[chunk];
+    if (!TRUE_RES && W.sys_nact[sys] == 0) return;
+    const int r = threadIdx.x % K;
+    double acc[1] = {0.0};
+    for (int il = threadIdx.x / K; il < rows; il += BT / K) {
+        const int i = r0 + il;
+        const size_t e = (size_t)i * K + r;
+        if (TRUE_RES) {
+            const double ri = W.B[e] - spmm_row<double, double>(rp, ci, av, W.X, i, r);
+            W.R[e] = ri;
+            acc[0] += ri * ri;
+        } else {
+            const double q = spmm_row<double, double>(rp, ci, av, W.P, i, r);
+            W.Q[e] = q;
+            acc[0] += W.P[e] * q;
+        }
+    }
+    double tot[1];
+    if (chunk_reduce<1>(acc, chunk, sys, W, tot) && threadIdx.x < K) {
+        const int p = sys * K + threadIdx.x;
+        if (TRUE_RES) {
+            W.tr[p] = tot[0];
+        } else if (W.act[p]) {
+            if (!isfinite(tot[0])) deactivate(W, p, AMG_NAN);
+            else if (tot[0] <= 0.0) deactivate(W, p, AMG_BREAKDOWN);
+            else W.alpha[p] = W.rz[p] / tot[0];
+        }
+    }
+}
+
+// x += alpha p, r_old = r, r -= alpha q (active pairs), ||r||^2 -> convergence
+__global__ void __launch_bounds__(BT) kb_update(BDev W, int max_iter, int flexible) {
+    const int chunk = blockIdx.x, sys = W.ch_sys[chunk], r0 = W.ch_r0[chunk], rows = W.ch_rows[chunk];
+    if (W.sys_nact[sys] == 0) return;
+    const int r = threadIdx.x % K, p = sys * K + r;
+    const bool a = W.act[p] != 0;
+    const double alpha = a ? W.alpha[p] : 0.0;
+    double acc[1] = {0.0};
+    for (int il = threadIdx.x / K; il < rows; il += BT / K) {
+        const size_t e = (size_t)(r0 + il) * K + r;
+        if (a) {
+            W.X[e] += alpha * W.P[e];
+            const double ri = W.R[e];
+            if (flexible) W.Rold[e] = ri;
+            const double rn = ri - alpha * W.Q[e];
+            W.R[e] = rn;
+            acc[0] += rn * rn;
+        }
+    }
+    double tot[1];
+    if (chunk_reduce<1>(acc, chunk, sys, W, tot) && threadIdx.x < K) {
+        const int q = sys * K + threadIdx.x;
+        if (W.act[q]) {
+            W.iters[q] += 1;
+            W.rr[q] = tot[0];
+            if (!isfinite(tot[0])) deactivate(W, q, AMG_NAN);
+            else if (tot[0] <= W.tol2[q]) deactivate(W, q, AMG_OK);
+            else if (W.iters[q] >= max_iter) deactivate(W, q, AMG_MAXIT);
+        }
+    }
+}
+
+// x = 0, r = b, p = r_old = 0; ||b||^2 per pair; pairs with b = 0 are done at once.
+__global__ void __launch_bounds__(BT) kb_init(BDev W, double rtol) {
+    const int chunk = blockIdx.x, sys = W.ch_sys[chunk], r0 = W.ch_r0[chunk], rows = W.ch_rows[chunk];
+    const int r = threadIdx.x % K;
+    double acc[1] = {0.0};
+    for (int il = threadIdx.x / K; il < rows; il += BT / K) {
+        const size_t e = (size_t)(r0 + il) * K + r;
+        const double bi = W.B[e];
+        W.X[e] = 0.0;
+        W.R[e] = bi;
+        W.P[e] = 0.0;
+        W.Rold[e] = 0.0;
+        W.Z[e] = 0.0;
+        acc[0] += bi * bi;
+    }
+    double tot[1];
+    if (chunk_reduce<1>(acc, chunk, sys, W, tot) && threadIdx.x < K) {
+        const int p = sys * K + threadIdx.x;
+        W.bn2[p] = tot[0];
+        W.tol2[p] = rtol * rtol * tot[0];
+        W.rr[p] = tot[0];
+        W.iters[p] = 0;
+        W.first[p] = 1;
+        W.rz[p] = 0.0;
+        W.status[p] = AMG_OK;
+        const bool live = tot[0] > 0.0 && isfinite(tot[0]);
+        W.act[p] = live;
+        if (!isfinite(tot[0])) W.status[p] = AMG_NAN;
+        if (live) {
+            atomicAdd(&W.sys_nact[sys], 1);
+            atomicAdd(W.nact, 1);
+        }
+    }
+}
+
+// Restart the pairs whose true residual is still above the tolerance (r holds it).
+__global__ void kb_restart(BDev W, int max_iter) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < W.npairs; p += gridDim.x * blockDim.x) {
+        if (W.status[p] == AMG_OK && W.bn2[p] > 0.0 && W.tr[p] > W.tol2[p] && W.iters[p] < max_iter) {
+            W.act[p] = 1;
+            W.first[p] = 1;
+            atomicAdd(&W.sys_nact[p / K], 1);
+            atomicAdd(W.nact, 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+static int workspace_build(Hierarchy *h, BatchWorkspace &W) {
+    DevArena &a = W.arena;
+    BDev &d = W.d;
+    const int n = h->n, ns = h->nsys;
+    d.n = n;
+    d.nsys = ns;
+    d.npairs = ns * K;
+    const BatchLevel &B0 = h->bl[0];
+    std::vector<int> ch_sys, ch_r0, ch_rows, sys_ch0(ns), sys_nch(ns);
+    for (int s = 0; s < ns; ++s) {
+        sys_ch0[s] = (int)ch_sys.size();
+        for (int r0 = B0.off[s]; r0 < B0.off[s + 1]; r0 += CH) {
+            ch_sys.push_back(s);
+            ch_r0.push_back(r0);
+            ch_rows.push_back(std::min(CH, B0.off[s + 1] - r0));
+        }
+        sys_nch[s] = (int)ch_sys.size() - sys_ch0[s];
+    }
+    d.nchunks = (int)ch_sys.size();
+    AMG_TRY(a.alloc(&d.ch_sys, d.nchunks));
+    AMG_TRY(a.alloc(&d.ch_r0, d.nchunks));
+    AMG_TRY(a.alloc(&d.ch_rows, d.nchunks));
+    AMG_TRY(a.alloc(&d.sys_ch0, ns));
+    AMG_TRY(a.alloc(&d.sys_nch, ns));
+    AMG_TRY(a.alloc(&d.ticket, ns));
+    AMG_TRY(a.alloc(&d.part, (size_t)d.nchunks * K * 2));
+    AMG_CUDA_TRY(cudaMemcpy(d.ch_sys, ch_sys.data(), sizeof(int) * d.nchunks, cudaMemcpyHostToDevice));
+    AMG_CUDA_TRY(cudaMemcpy(d.ch_r0, ch_r0.data(), sizeof(int) * d.nchunks, cudaMemcpyHostToDevice));
+    AMG_CUDA_TRY(cudaMemcpy(d.ch_rows, ch_rows.data(), sizeof(int) * d.nchunks, cudaMemcpyHostToDevice));
+    AMG_CUDA_TRY(cudaMemcpy(d.sys_ch0, sys_ch0.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+    AMG_CUDA_TRY(cudaMemcpy(d.sys_nch, sys_nch.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+    AMG_CUDA_TRY(cudaMemset(d.ticket, 0, sizeof(unsigned) * ns));
+    const size_t nk = (size_t)n * K;
+    double **vecs[] = {&d.B, &d.X, &d.R, &d.Z, &d.P, &d.Q, &d.Rold};
+    for (double **v : vecs) AMG_TRY(a.alloc(v, nk));
+    double **pv[] = {&d.bn2, &d.tol2, &d.rz, &d.alpha, &d.beta, &d.rr, &d.tr};
+    for (double **v : pv) AMG_TRY(a.alloc(v, (size_t)d.npairs));
+    int **pi[] = {&d.act, &d.first, &d.iters, &d.status};
+    for (int **v : pi) AMG_TRY(a.alloc(v, (size_t)d.npairs));
+    AMG_TRY(a.alloc(&d.nact, 1));
+    AMG_CUDA_TRY(cudaMemset(d.nact, 0, sizeof(int)));
+    AMG_TRY(a.alloc(&d.sys_nact, ns));
+    const size_t vb = h->cfg.precision == AMG_PRECISION_MIXED ? 4 : 8;
+    for (int l = 0; l < h->nlevels; ++l) {
+        const size_t nl = (size_t)h->L[l].A.nrows * K;
+        unsigned char *p;
+        AMG_TRY(a.alloc(&p, nl * vb));
+        W.lt[l] = p;
+        if (l > 0) {
+            AMG_TRY(a.alloc(&p, nl * vb));
+            W.lb[l] = p;
+            AMG_TRY(a.alloc(&p, nl * vb));
+            W.lx[l] = p;
+        }
+    }
+    AMG_CUDA_TRY(cudaDeviceSynchronize());
+    return AMG_OK;
+}
+
+int batch_create(Hierarchy *h, BatchWorkspace **out) {
+    *out = nullptr;
+    BatchWorkspace *W = new (std::nothrow) BatchWorkspace();
+    if (!W) return AMG_ERR_OOM;
+    const int rc = workspace_build(h, *W);
+    if (rc < 0) {
+        batch_destroy(W);
+        return rc;
+    }
+    *out = W;
+    return AMG_OK;
+}
+
+void batch_destroy(BatchWorkspace *W) {
+    if (!W) return;
+    if (W->iter_exec) cudaGraphExecDestroy(W->iter_exec);
+    W->arena.free_all();
+    delete W;
+}
+
+static int rows_grid(long long n) {
+    const long long g = (n * K + BT - 1) / BT;
+    return (int)std::max(1LL, std::min(g, (long long)num_sms() * 16));
+}
+
+template <typename TM>
+static int batch_vcycle(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cudaStream_t s) {
+    const int L = h->nlevels;
+    constexpr bool mixed = sizeof(TM) == 4;
+    const BDev &d = W.d;
+    const int *na = d.nact;
+    auto Av = [&](const DevCSR &m) -> const TM * { return (const TM *)(mixed ? (const void *)m.v32 : (const void *)m.v); };
+    auto Ah = [&](const Level &lv) -> const TM * { return (const TM *)(mixed ? (const void *)lv.ahat32 : (const void *)lv.ahat); };
+    auto Wv = [&](const Level &lv) -> const TM * { return (const TM *)(mixed ? (const void *)lv.w32 : (const void *)lv.w); };
+    auto T = [&](int l) { return (TM *)W.lt[l]; };
+    auto Bv = [&](int l) { return (TM *)W.lb[l]; };
+    auto Xv = [&](int l) { return (TM *)W.lx[l]; };
+    auto dense = [&](int l) -> int {
+        const BatchLevel &bl = h->bl[l];
+        if (bl.nfin == 0) return AMG_OK;
+        ProfScope ps(&prof, s, "b_dense", l, 0.0);
+        if (l == 0)
+            kb_dense<double, double><<<bl.nfin, BT, 0, s>>>(bl.fin_r0, bl.fin_m, bl.fin_off2, bl.binv, d.R, d.Z, na);
+        else
+            kb_dense<TM, TM><<<bl.nfin, BT, 0, s>>>(bl.fin_r0, bl.fin_m, bl.fin_off2, bl.binv, Bv(l), Xv(l), na);
+        AMG_LAUNCH_CHECK();
+        return AMG_OK;
+    };
+    const double vb = (double)sizeof(TM);
+    // down: the systems ending on level l are solved there first
+    AMG_TRY(dense(0));
+    for (int l = 0; l < L - 1; ++l) {
+        const Level &lv = h->L[l];
+        const int n = lv.A.nrows, nc = lv.R.nrows;
+        {
+            ProfScope ps(&prof, s, "b_presmooth", l,
+                         lv.A.nnz * (4.0 + vb) + (double)n * K * (l == 0 ? 8.0 + vb : 2.0 * vb));
+            if (l == 0)
+                kb_presmooth<double, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Ah(lv), d.R, T(0), na);
+            else
+                kb_presmooth<TM, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Ah(lv), Bv(l), T(l), na);
+        }
+        {
+            ProfScope ps(&prof, s, "b_restrict", l, lv.R.nnz * (4.0 + vb) + (double)(n + nc) * K * vb);
+            kb_spmm<TM><<<rows_grid(nc), BT, 0, s>>>(nc, lv.R.rp, lv.R.ci, Av(lv.R), T(l), Bv(l + 1), na);
+        }
+        AMG_LAUNCH_CHECK();
+        AMG_TRY(dense(l + 1));
+    }
+    // up
+    for (int l = L - 2; l >= 0; --l) {
+        const Level &lv = h->L[l];
+        const int n = lv.A.nrows, nc = lv.P.ncols;
+        {
+            ProfScope ps(&prof, s, "b_prolong", l, lv.P.nnz * (4.0 + vb) + (double)n * vb + (double)(2 * n + nc) * K * vb);
+            if (l == 0)
+                kb_prolong<double, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), d.R, Xv(1),
+                                                                   T(0), na);
+            else
+                kb_prolong<TM, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), Bv(l),
+                                                               Xv(l + 1), T(l), na);
+        }
+        AMG_LAUNCH_CHECK();
+        if (l > 0) {
+            ProfScope ps(&prof, s, "b_postsmooth", l, lv.A.nnz * (4.0 + vb) + (double)n * vb + (double)n * K * 3.0 * vb);
+            kb_postsmooth<TM, TM, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), Bv(l), T(l),
+                                                                  Xv(l), na);
+            AMG_LAUNCH_CHECK();
+        }
+    }
+    // finest post-smoothing with r.z (systems ending on level 0 keep the dense z)
+    {
+        const Level &l0 = h->L[0];
+        const double nk = (double)l0.A.nrows * K;
+        ProfScope ps(&prof, s, "b_postsmooth_rz", 0,
+                     L > 1 ? l0.A.nnz * (4.0 + vb) + l0.A.nrows * vb + nk * (vb + 8.0 * (mixed ? 4.0 : 3.0)) : nk * 16.0);
+        kb_post0<TM><<<d.nchunks, BT, 0, s>>>(d, l0.A.rp, l0.A.ci, Av(l0.A), Wv(l0), T(0), mixed ? 1 : 0);
+        AMG_LAUNCH_CHECK();
+    }
+    return AMG_OK;
+}
+
+static int batch_iteration(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cudaStream_t s) {
+    const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
+    if (mixed) AMG_TRY(batch_vcycle<float>(h, W, prof, s));
+    else AMG_TRY(batch_vcycle<double>(h, W, prof, s));
+    const Level &l0 = h->L[0];
+    const BDev &d = W.d;
+    const double nk = (double)d.n * K;
+    {
+        ProfScope ps(&prof, s, "b_p", 0, 24.0 * nk);
+        kb_p<<<d.nchunks, BT, 0, s>>>(d);
+    }
+    {
+        ProfScope ps(&prof, s, "b_spmv_pq", 0, l0.A.nnz * 12.0 + 4.0 * (d.n + 1) + 24.0 * nk);
+        kb_spmv0<false><<<d.nchunks, BT, 0, s>>>(d, l0.A.rp, l0.A.ci, l0.A.v);
+    }
+    {
+        ProfScope ps(&prof, s, "b_update", 0, (mixed ? 64.0 : 56.0) * nk);
+        kb_update<<<d.nchunks, BT, 0, s>>>(d, h->cfg.max_iter, mixed ? 1 : 0);
+    }
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+// Copies B ([n][nrhs], device) into the K-wide workspace (zero padding), and
+// the result back.
+__global__ void kb_pack(int n, int nrhs, const double *src, double *dst) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * K;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / K), r = (int)(e % K);
+        dst[e] = r < nrhs ? src[(size_t)i * nrhs + r] : 0.0;
+    }
+}
+__global__ void kb_unpack(int n, int nrhs, const double *src, double *dst) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * nrhs;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / nrhs), r = (int)(e % nrhs);
+        dst[e] = src[(size_t)i * K + r];
+    }
+}
+
+static bool on_device(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int batch_solve(Hierarchy *h, BatchWorkspace *Wp, Profiler &prof, int nrhs, const double *Bin, double *Xout,
+                int *iters_out, double *rel_out, cudaStream_t s, SolveResult *res) {
+    BatchWorkspace &W = *Wp;
+    const BDev &d = W.d;
+    const amg_config &c = h->cfg;
+    const Level &l0 = h->L[0];
+    const int grid = std::max(1, std::min((int)(((long long)d.n * K + 255) / 256), num_sms() * 16));
+    // stage: host arrays go through Q (free before the solve starts)
+    const double *Bd = Bin;
+    if (!on_device(Bin)) {
+        AMG_CUDA_TRY(cudaMemcpyAsync(d.Q, Bin, sizeof(double) * (size_t)d.n * nrhs, cudaMemcpyDefault, s));
+        Bd = d.Q;
+    }
+    kb_pack<<<grid, 256, 0, s>>>(d.n, nrhs, Bd, d.B);
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA_TRY(cudaMemsetAsync(d.nact, 0, sizeof(int), s));
+    AMG_CUDA_TRY(cudaMemsetAsync(d.sys_nact, 0, sizeof(int) * d.nsys, s));
+    {
+        ProfScope ps(&prof, s, "b_init", 0, 48.0 * d.n * K);
+        kb_init<<<d.nchunks, BT, 0, s>>>(d, c.rtol);
+    }
+    AMG_LAUNCH_CHECK();
+    int nact = 0;
+    const long long cap = (long long)c.max_iter * (c.max_restarts + 1) + 16;
+    long long launched = 0;
+    int restarts = 0;
+    for (;;) {
+        AMG_CUDA_TRY(cudaMemcpyAsync(&nact, d.nact, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        while (nact > 0) {
+            // iterations of finished pairs are no-ops; the host polls every 4
+            for (int k = 0; k < 4; ++k) {
+                if (prof.on) {
+                    AMG_TRY(batch_iteration(h, W, prof, s));
+                    continue;
+                }
+                if (!W.iter_exec) {
+                    const long long before = prof.launches;
+                    AMG_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                    const int rc = batch_iteration(h, W, prof, s);
+                    cudaGraph_t g = nullptr;
+                    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+                    if (rc < 0) {
+                        if (g) cudaGraphDestroy(g);
+                        return rc;
+                    }
+                    AMG_CUDA_TRY(ce);
+                    const cudaError_t ie = cudaGraphInstantiate(&W.iter_exec, g, 0);
+                    cudaGraphDestroy(g);
+                    AMG_CUDA_TRY(ie);
+                    W.iter_kernels = (int)(prof.launches - before);
+                    prof.launches = before;
+                }
+                AMG_CUDA_TRY(cudaGraphLaunch(W.iter_exec, s));
+                prof.launches += W.iter_kernels;
+            }
+            launched += 4;
+            AMG_CUDA_TRY(cudaMemcpyAsync(&nact, d.nact, sizeof(int), cudaMemcpyDeviceToHost, s));
+            AMG_CUDA_TRY(cudaStreamSynchronize(s));
+            if (launched > cap) {
+                set_last_error("batched solve: %lld iterations launched without every pair stopping", launched);
+                return AMG_ERR_CUDA;
+            }
+        }
+        // true residuals; restart the pairs still above the tolerance
+        {
+            ProfScope ps(&prof, s, "b_true_residual", 0, l0.A.nnz * 12.0 + 4.0 * (d.n + 1) + 24.0 * d.n * K);
+            kb_spmv0<true><<<d.nchunks, BT, 0, s>>>(d, l0.A.rp, l0.A.ci, l0.A.v);
+        }
+        AMG_LAUNCH_CHECK();
+        if (restarts >= c.max_restarts) break;
+        kb_restart<<<std::max(1, (d.npairs + 255) / 256), 256, 0, s>>>(d, c.max_iter);
+        AMG_LAUNCH_CHECK();
+        AMG_CUDA_TRY(cudaMemcpyAsync(&nact, d.nact, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (nact == 0) break;
+        ++restarts;
+    }
+    // outputs
+    double *Xd = Xout;
+    const bool host_x = !on_device(Xout);
+    if (host_x) Xd = d.Q;
+    kb_unpack<<<grid, 256, 0, s>>>(d.n, nrhs, d.X, Xd);
+    AMG_LAUNCH_CHECK();
+    if (host_x) AMG_CUDA_TRY(cudaMemcpyAsync(Xout, d.Q, sizeof(double) * (size_t)d.n * nrhs, cudaMemcpyDefault, s));
+    const int np = d.npairs;
+    std::vector<int> st(np), it(np);
+    std::vector<double> tr(np), bn(np), rr(np);
+    AMG_CUDA_TRY(cudaMemcpyAsync(st.data(), d.status, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(it.data(), d.iters, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(tr.data(), d.tr, sizeof(double) * np, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(bn.data(), d.bn2, sizeof(double) * np, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(rr.data(), d.rr, sizeof(double) * np, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    SolveResult out;
+    out.restarts = restarts;
+    std::vector<int> io((size_t)d.nsys * nrhs);
+    std::vector<double> ro((size_t)d.nsys * nrhs);
+    for (int sy = 0; sy < d.nsys; ++sy)
+        for (int r = 0; r < nrhs; ++r) {
+            const int p = sy * K + r;
+            int sp = st[p];
+            const double rel = bn[p] > 0.0 ? sqrt(tr[p] / bn[p]) : 0.0;
+            if (sp == AMG_OK && bn[p] > 0.0 && !(tr[p] <= c.rtol * c.rtol * bn[p])) sp = AMG_MAXIT;
+            out.status = std::max(out.status, sp);
+            out.iters = std::max(out.iters, it[p]);
+            out.rel_res_true = std::max(out.rel_res_true, rel);
+            out.rel_res_rec = std::max(out.rel_res_rec, bn[p] > 0.0 ? sqrt(rr[p] / bn[p]) : 0.0);
+            io[(size_t)sy * nrhs + r] = it[p];
+            ro[(size_t)sy * nrhs + r] = rel;
+        }
+    if (iters_out) AMG_CUDA_TRY(cudaMemcpy(iters_out, io.data(), sizeof(int) * io.size(), cudaMemcpyDefault));
+    if (rel_out) AMG_CUDA_TRY(cudaMemcpy(rel_out, ro.data(), sizeof(double) * ro.size(), cudaMemcpyDefault));
+    prof.collect();
+    *res = out;
+    return AMG_OK;
+}
+
+}  // namespace amg

@@ -399,18 +399,22 @@ __global__ void k_mis_update(int n, const int *srp, const int *sci, const unsign
 // Aggregation
 // ===========================================================================
 
-__global__ void k_root_flags(int n, const unsigned long long *t, int *flag) {
+// active (may be null): rows of systems still coarsening in a batch.
+__global__ void k_root_flags(int n, const unsigned long long *t, int *flag, const unsigned char *active = nullptr) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        flag[i] = (t[i] >> 32) == 2ull;
+        flag[i] = (t[i] >> 32) == 2ull && (!active || active[i]);
 }
 
 // Phases 1-2: roots take their id; a non-root adjacent to a root takes that
 // root's aggregate (unique: roots are at least 3 apart).
 __global__ void k_agg_phase12(int n, const int *srp, const int *sci, const unsigned long long *t,
-                              const int *root_id, int *snap) {
+                              const int *root_id, int *snap,
+                              const unsigned char *active = nullptr) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int a = -1;
-        if ((t[i] >> 32) == 2ull) {
+        if (active && !active[i]) {
+            a = -1;
+        } else if ((t[i] >> 32) == 2ull) {
             a = root_id[i];
         } else {
             for (int p = srp[i]; p < srp[i + 1]; ++p) {
@@ -426,9 +430,15 @@ __global__ void k_agg_phase12(int n, const int *srp, const int *sci, const unsig
 // strong neighbour j with the largest |a_ij| (0 when (i,j) is not stored);
 // ties go to the smallest j.  Reads only the phase-2 snapshot.
 __global__ void k_agg_phase3(int n, const int *rp, const int *ci, const double *v, const int *srp,
-                             const int *sci, const int *snap, int *agg, int *unassigned) {
+                             const int *sci, const int *snap, int *agg, int *unassigned,
+                             const unsigned char *active = nullptr) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int a = snap[i];
+        if (active && !active[i]) {
+            agg[i] = -1;
+            unassigned[i] = 0;
+            continue;
+        }
         if (a < 0) {
             int best = -1;
             double bw = -1.0;
@@ -508,6 +518,7 @@ struct ProlongEpi {
     const int *agg;      // aggregate of each fine row
     const double *diag;  // a_ii
     double omega_p;      // (4/3) / rho
+    const double *omega_row = nullptr;  // per-row omega_P (block-diagonal batches: per system), or null
 };
 
 template <bool NUMERIC, int EPI>
@@ -604,7 +615,8 @@ __global__ void k_spgemm(int nrows, const int *xrp, const int *xci, const double
                 if (EPI == EPI_PROLONG) {
                     const double t = __ddiv_rn(val, epi.diag[i]);
                     const double delta = (key == epi.agg[i]) ? 1.0 : 0.0;
-                    val = __dsub_rn(delta, __dmul_rn(epi.omega_p, t));
+                    const double om = epi.omega_row ? epi.omega_row[i] : epi.omega_p;
+                    val = __dsub_rn(delta, __dmul_rn(om, t));
                 }
                 cci[out0 + rank] = key;
                 cv[out0 + rank] = val;
@@ -703,7 +715,8 @@ __global__ void k_csr_to_dense(int n, const int *rp, const int *ci, const double
         for (int k = rp[i]; k < rp[i + 1]; ++k) d[(size_t)i * n + ci[k]] = v[k];
 }
 
-__global__ void k_dense_factor_inverse(int n, int symmetric, double *a, int *piv, double *inv, int *status) {
+// One thread block factors an n x n dense matrix in place and writes its inverse.
+__device__ void dense_factor_inverse_block(int n, int symmetric, double *a, int *piv, double *inv, int *status) {
     __shared__ int s_piv;
     __shared__ int s_fail;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -800,6 +813,30 @@ __global__ void k_dense_factor_inverse(int n, int symmetric, double *a, int *piv
         }
     }
     if (tid == 0) *status = AMG_OK;
+}
+
+__global__ void k_dense_factor_inverse(int n, int symmetric, double *a, int *piv, double *inv, int *status) {
+    dense_factor_inverse_block(n, symmetric, a, piv, inv, status);
+}
+
+// Batched: block b factors system b's m[b] x m[b] block (dense at off2[b],
+// pivots at off1[b], inverse at off2[b] of inv).
+__global__ void k_dense_factor_inverse_batch(const int *m, const long long *off2, const int *off1, int symmetric,
+                                             double *a, int *piv, double *inv, int *status) {
+    const int b = blockIdx.x;
+    dense_factor_inverse_block(m[b], symmetric, a + off2[b], piv + off1[b], inv + off2[b], status + b);
+}
+
+// Batched dense extraction: block b copies rows [r0, r0 + m) of the CSR into
+// an m x m block with columns shifted by r0.
+__global__ void k_csr_to_dense_batch(const int *r0s, const int *m, const long long *off2, const int *rp,
+                                     const int *ci, const double *v, double *d) {
+    const int b = blockIdx.x, r0 = r0s[b], mb = m[b];
+    double *db = d + off2[b];
+    for (int i = threadIdx.x; i < mb * mb; i += blockDim.x) db[i] = 0.0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < mb; i += blockDim.x)
+        for (int k = rp[r0 + i]; k < rp[r0 + i + 1]; ++k) db[(size_t)i * mb + (ci[k] - r0)] = v[k];
 }
 
 // ===========================================================================
@@ -1146,6 +1183,446 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
     }
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
     return tail_prepare(h, s);
+}
+
+
+// ===========================================================================
+// Block-diagonal batches of independent systems
+// ===========================================================================
+// The hierarchy of a batch is, system by system, the hierarchy each system
+// would have alone: independent-set priorities use the row's index within its
+// system, the Gershgorin estimate and omega_P are per system, and a system
+// stops coarsening on its own (<= coarse_max rows, the level cap, or no
+// shrink).  A system that stops on level l is "final" there: its rows keep
+// zero smoother weights (the smoothing kernels leave zeros), get no
+// prolongator rows (it is absent from level l + 1), and a per-system dense
+// inverse solves it on level l.
+
+__global__ void k_rows_of_sys(int n, int nsys, const int *off, int *row_sys, int *row_start) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int lo = 0, hi = nsys - 1;
+        while (lo < hi) {  // last system with off <= i
+            const int mid = (lo + hi + 1) / 2;
+            if (off[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        row_sys[i] = lo;
+        row_start[i] = off[lo];
+    }
+}
+
+__global__ void k_active_rows(int n, const int *row_sys, const unsigned char *fin, unsigned char *active, double *w) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const bool a = !fin[row_sys[i]];
+        active[i] = a;
+        if (!a) w[i] = 0.0;
+    }
+}
+
+__global__ void k_gershgorin_sys(int n, const int *rp, const double *v, const double *diag, const int *row_sys,
+                                 const unsigned char *active, unsigned long long *rho_bits) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!active[i]) continue;
+        double s = 0.0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) s = __dadd_rn(s, fabs(v[k]));
+        const double q = __ddiv_rn(s, fabs(diag[i]));
+        atomicMax(rho_bits + row_sys[i], (unsigned long long)__double_as_longlong(q));
+    }
+}
+
+__global__ void k_omega_rows(int n, const int *row_sys, const unsigned char *active, const double *om_sys,
+                             double *om_row) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        om_row[i] = active[i] ? om_sys[row_sys[i]] : 0.0;
+}
+
+__global__ void k_assigned(int n, const int *agg, int *flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) flag[i] = agg[i] >= 0;
+}
+
+__global__ void k_t_fill(int n, const int *agg, const int *trp, int *tci) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (agg[i] >= 0) tci[trp[i]] = agg[i];
+}
+
+// Dense inverses of the systems final on this level (each <= AMG_DENSE_MAX rows).
+static int batch_dense(Hierarchy *h, int l, cudaStream_t s) {
+    BatchLevel &B = h->bl[l];
+    const DevCSR &A = h->L[l].A;
+    std::vector<int> r0, m, off1;
+    std::vector<long long> off2;
+    long long tot2 = 0;
+    int tot1 = 0;
+    for (size_t k = 0; k < B.sys.size(); ++k) {
+        if (!B.fin[k]) continue;
+        const int mk = B.off[k + 1] - B.off[k];
+        if (mk > AMG_DENSE_MAX) {
+            set_last_error("system %d stopped coarsening on level %d with %d rows (> %d)", B.sys[k], l, mk,
+                           AMG_DENSE_MAX);
+            return AMG_ERR_STALL;
+        }
+        r0.push_back(B.off[k]);
+        m.push_back(mk);
+        off1.push_back(tot1);
+        off2.push_back(tot2);
+        tot1 += mk;
+        tot2 += (long long)mk * mk;
+        B.max_m = std::max(B.max_m, mk);
+    }
+    B.nfin = (int)r0.size();
+    if (B.nfin == 0) return AMG_OK;
+    DevArena &ar = h->arena;
+    Scratch sc;
+    int *d_r0s, *d_m, *d_off1, *piv, *st;
+    long long *d_off2;
+    double *dense;
+    AMG_TRY(ar.alloc(&B.fin_r0, r0.size()));
+    AMG_TRY(ar.alloc(&B.fin_m, m.size()));
+    AMG_TRY(ar.alloc(&B.fin_off2, off2.size()));
+    AMG_TRY(ar.alloc(&B.binv, (size_t)tot2));
+    AMG_TRY(sc.alloc(&d_off1, off1.size()));
+    AMG_TRY(sc.alloc(&piv, (size_t)tot1));
+    AMG_TRY(sc.alloc(&st, r0.size()));
+    AMG_TRY(sc.alloc(&dense, (size_t)tot2));
+    d_r0s = B.fin_r0;
+    d_m = B.fin_m;
+    d_off2 = B.fin_off2;
+    AMG_CUDA_TRY(cudaMemcpyAsync(d_r0s, r0.data(), sizeof(int) * r0.size(), cudaMemcpyHostToDevice, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(d_m, m.data(), sizeof(int) * m.size(), cudaMemcpyHostToDevice, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(d_off2, off2.data(), sizeof(long long) * off2.size(), cudaMemcpyHostToDevice, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(d_off1, off1.data(), sizeof(int) * off1.size(), cudaMemcpyHostToDevice, s));
+    k_csr_to_dense_batch<<<B.nfin, 256, 0, s>>>(d_r0s, d_m, d_off2, A.rp, A.ci, A.v, dense);
+    k_dense_factor_inverse_batch<<<B.nfin, 256, 0, s>>>(d_m, d_off2, d_off1, h->symmetric, dense, piv, B.binv, st);
+    AMG_LAUNCH_CHECK();
+    std::vector<int> hst(r0.size());
+    AMG_CUDA_TRY(cudaMemcpyAsync(hst.data(), st, sizeof(int) * hst.size(), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    for (size_t k = 0; k < hst.size(); ++k)
+        if (hst[k] != AMG_OK) {
+            set_last_error("the last level of a system of the batch (level %d) is not %s", l,
+                           h->symmetric ? "SPD" : "invertible");
+            return AMG_NOT_SPD;
+        }
+    return AMG_OK;
+}
+
+int build_hierarchy_batched(Hierarchy *h, const int *rp_in, const int *ci_in, const double *v_in,
+                            const int *sys_off_host, int nsys, cudaStream_t s) {
+    const amg_config &cfg = h->cfg;
+    const int n = h->n;
+    const long long nnz = h->nnz;
+    DevArena &ar = h->arena;
+    h->nsys = nsys;
+    if (sys_off_host[0] != 0 || sys_off_host[nsys] != n) {
+        set_last_error("system offsets must start at 0 and end at n");
+        return AMG_ERR_ARG;
+    }
+    for (int k = 0; k < nsys; ++k)
+        if (sys_off_host[k + 1] <= sys_off_host[k]) {
+            set_last_error("system %d is empty", k);
+            return AMG_ERR_ARG;
+        }
+    // level 0: copy and validate, then check the matrix is block diagonal
+    Level &L0 = h->L[0];
+    L0.A.nrows = L0.A.ncols = n;
+    L0.A.nnz = nnz;
+    AMG_TRY(ar.alloc(&L0.A.rp, (size_t)n + 1));
+    AMG_TRY(ar.alloc(&L0.A.ci, (size_t)nnz));
+    AMG_TRY(ar.alloc(&L0.A.v, (size_t)nnz));
+    AMG_CUDA_TRY(cudaMemcpyAsync(L0.A.rp, rp_in, sizeof(int) * ((size_t)n + 1), cudaMemcpyDefault, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(L0.A.ci, ci_in, sizeof(int) * (size_t)nnz, cudaMemcpyDefault, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(L0.A.v, v_in, sizeof(double) * (size_t)nnz, cudaMemcpyDefault, s));
+    {
+        std::vector<int> hrp((size_t)n + 1), hci((size_t)nnz);
+        AMG_CUDA_TRY(cudaMemcpyAsync(hrp.data(), L0.A.rp, sizeof(int) * hrp.size(), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaMemcpyAsync(hci.data(), L0.A.ci, sizeof(int) * hci.size(), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hrp[0] != 0 || (long long)hrp[n] != nnz) {
+            set_last_error("row_ptr[0] = %d, row_ptr[n] = %d, nnz = %lld", hrp[0], hrp[n], nnz);
+            return AMG_ERR_BAD_CSR;
+        }
+        for (int k = 0; k < nsys; ++k)
+            for (int i = sys_off_host[k]; i < sys_off_host[k + 1]; ++i) {
+                if (hrp[i + 1] < hrp[i] || hrp[i] < 0 || (long long)hrp[i + 1] > nnz) {
+                    set_last_error("invalid CSR at row %d", i);
+                    return AMG_ERR_BAD_CSR;
+                }
+                for (int q = hrp[i]; q < hrp[i + 1]; ++q)
+                    if (hci[q] < sys_off_host[k] || hci[q] >= sys_off_host[k + 1]) {
+                        set_last_error("row %d of system %d couples to column %d outside its block", i, k, hci[q]);
+                        return AMG_ERR_BAD_CSR;
+                    }
+            }
+    }
+    {
+        Scratch sc;
+        int *dpos;
+        unsigned long long *err;
+        AMG_TRY(sc.alloc(&dpos, (size_t)n));
+        AMG_TRY(sc.alloc(&err, 1));
+        unsigned long long init = ~0ull;
+        AMG_CUDA_TRY(cudaMemcpyAsync(err, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+        k_validate<<<grid_for(n), 256, 0, s>>>(n, nnz, L0.A.rp, L0.A.ci, L0.A.v, dpos, err);
+        AMG_LAUNCH_CHECK();
+        unsigned long long first = 0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&first, err, sizeof(first), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (first != ~0ull) {
+            const int code = (int)(first & 3);
+            set_last_error("invalid CSR at row %d", (int)(first >> 2));
+            return code == 1 ? AMG_ERR_BAD_CSR : AMG_ERR_ZERO_DIAG;
+        }
+    }
+    if (cfg.symmetric >= 0) {
+        h->symmetric = cfg.symmetric;
+    } else {
+        DevArena tmp;
+        DevCSR At;
+        int rc = transpose_csr(L0.A, At, tmp, s);
+        int *differ = nullptr;
+        if (rc == AMG_OK) rc = tmp.alloc(&differ, 1);
+        if (rc < 0) { tmp.free_all(); return rc; }
+        cudaMemsetAsync(differ, 0, sizeof(int), s);
+        k_compare_csr<<<grid_for(nnz + n + 1), 256, 0, s>>>(n, nnz, L0.A.rp, L0.A.ci, L0.A.v, At.rp, At.ci, At.v,
+                                                             differ);
+        int d = 1;
+        cudaMemcpyAsync(&d, differ, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        tmp.free_all();
+        AMG_CUDA_TRY(e);
+        h->symmetric = d ? 0 : 1;
+    }
+
+    h->bl.assign(AMG_MAX_LEVELS, BatchLevel());
+    h->bl[0].sys.resize(nsys);
+    h->bl[0].off.assign(sys_off_host, sys_off_host + nsys + 1);
+    for (int k = 0; k < nsys; ++k) h->bl[0].sys[k] = k;
+    int l = 0;
+    for (;;) {
+        Level &Lv = h->L[l];
+        BatchLevel &B = h->bl[l];
+        DevCSR &A = Lv.A;
+        const int nl = A.nrows;
+        const int ns = (int)B.sys.size();
+        Scratch sc;
+        double *diag;
+        int *bad, *d_off, *row_sys, *row_start;
+        unsigned char *d_fin, *active;
+        AMG_TRY(sc.alloc(&diag, (size_t)nl));
+        AMG_TRY(sc.alloc(&bad, 1));
+        AMG_TRY(sc.alloc(&d_off, (size_t)ns + 1));
+        AMG_TRY(sc.alloc(&row_sys, (size_t)nl));
+        AMG_TRY(sc.alloc(&row_start, (size_t)nl));
+        AMG_TRY(sc.alloc(&d_fin, (size_t)ns));
+        AMG_TRY(sc.alloc(&active, (size_t)nl));
+        AMG_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        AMG_CUDA_TRY(cudaMemcpyAsync(d_off, B.off.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice, s));
+        k_rows_of_sys<<<grid_for(nl), 256, 0, s>>>(nl, ns, d_off, row_sys, row_start);
+        k_find_diag<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, diag, bad);
+        AMG_LAUNCH_CHECK();
+        int hbad = 0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hbad) {
+            set_last_error("level %d has a zero diagonal", l);
+            return AMG_ERR_ZERO_DIAG;
+        }
+        AMG_TRY(ar.alloc(&Lv.w, (size_t)nl));
+        B.fin.assign(ns, 0);
+        for (int k = 0; k < ns; ++k) {
+            const int m = B.off[k + 1] - B.off[k];
+            B.fin[k] = !(m > cfg.coarse_max && l + 1 < cfg.max_levels && l + 1 < AMG_MAX_LEVELS);
+        }
+        const double theta_l = ldexp(cfg.theta, -l);
+        const double t2 = theta_l * theta_l;
+        std::vector<int> nc_sys(ns, 0);
+        int nc = 0;
+        for (int attempt = 0;; ++attempt) {
+            k_smoother_weights<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.v, diag, cfg.omega,
+                                                            cfg.smoother == AMG_SMOOTHER_L1_JACOBI, Lv.w);
+            AMG_CUDA_TRY(cudaMemcpyAsync(d_fin, B.fin.data(), ns, cudaMemcpyHostToDevice, s));
+            k_active_rows<<<grid_for(nl), 256, 0, s>>>(nl, row_sys, d_fin, active, Lv.w);
+            AMG_LAUNCH_CHECK();
+            bool any_active = false;
+            for (int k = 0; k < ns; ++k) any_active |= !B.fin[k];
+            if (!any_active) break;
+            Scratch sa;
+            int *cnt, *s1rp, *s1ci, *srp, *sci;
+            AMG_TRY(sa.alloc(&cnt, (size_t)nl + 1));
+            AMG_TRY(sa.alloc(&s1rp, (size_t)nl + 1));
+            k_strength<false><<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, diag, t2, cnt, nullptr, nullptr);
+            AMG_LAUNCH_CHECK();
+            int s1nnz = 0;
+            AMG_TRY(exclusive_scan_int(cnt, s1rp, nl, &s1nnz, s));
+            AMG_TRY(sa.alloc(&s1ci, (size_t)std::max(1, s1nnz)));
+            k_strength<true><<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, diag, t2, nullptr, s1rp, s1ci);
+            AMG_LAUNCH_CHECK();
+            DevCSR S1;
+            S1.nrows = S1.ncols = nl;
+            S1.nnz = s1nnz;
+            S1.rp = s1rp;
+            S1.ci = s1ci;
+            DevCSR S1t;
+            AMG_TRY(transpose_csr(S1, S1t, sa.arena, s));
+            AMG_TRY(sa.alloc(&srp, (size_t)nl + 1));
+            k_union<false><<<grid_for(nl), 256, 0, s>>>(nl, s1rp, s1ci, S1t.rp, S1t.ci, cnt, nullptr, nullptr);
+            AMG_LAUNCH_CHECK();
+            int snnz = 0;
+            AMG_TRY(exclusive_scan_int(cnt, srp, nl, &snnz, s));
+            AMG_TRY(sa.alloc(&sci, (size_t)std::max(1, snnz)));
+            k_union<true><<<grid_for(nl), 256, 0, s>>>(nl, s1rp, s1ci, S1t.rp, S1t.ci, nullptr, srp, sci);
+            AMG_LAUNCH_CHECK();
+            unsigned long long *t, *m1;
+            int *und;
+            AMG_TRY(sa.alloc(&t, (size_t)nl));
+            AMG_TRY(sa.alloc(&m1, (size_t)nl));
+            AMG_TRY(sa.alloc(&und, 1));
+            k_mis_init<<<grid_for(nl), 256, 0, s>>>(nl, row_start, t);
+            AMG_LAUNCH_CHECK();
+            int rounds = 0, hund = 1;
+            while (hund > 0) {
+                if (++rounds > 100000) {
+                    set_last_error("independent-set rounds did not terminate at level %d", l);
+                    return AMG_ERR_STALL;
+                }
+                AMG_CUDA_TRY(cudaMemsetAsync(und, 0, sizeof(int), s));
+                k_mis_max<<<grid_for(nl), 256, 0, s>>>(nl, srp, sci, t, m1);
+                k_mis_update<<<grid_for(nl), 256, 0, s>>>(nl, srp, sci, m1, t, und);
+                AMG_LAUNCH_CHECK();
+                AMG_CUDA_TRY(cudaMemcpyAsync(&hund, und, sizeof(int), cudaMemcpyDeviceToHost, s));
+                AMG_CUDA_TRY(cudaStreamSynchronize(s));
+            }
+            int *flag, *root_id, *snap;
+            AMG_TRY(sa.alloc(&flag, (size_t)nl + 1));
+            AMG_TRY(sa.alloc(&root_id, (size_t)nl + 1));
+            AMG_TRY(sa.alloc(&snap, (size_t)nl));
+            if (!Lv.agg) AMG_TRY(ar.alloc(&Lv.agg, (size_t)nl));
+            k_root_flags<<<grid_for(nl), 256, 0, s>>>(nl, t, flag, active);
+            AMG_LAUNCH_CHECK();
+            int nroots = 0;
+            AMG_TRY(exclusive_scan_int(flag, root_id, nl, &nroots, s));
+            k_agg_phase12<<<grid_for(nl), 256, 0, s>>>(nl, srp, sci, t, root_id, snap, active);
+            k_agg_phase3<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, srp, sci, snap, Lv.agg, flag, active);
+            AMG_LAUNCH_CHECK();
+            int nsingle = 0;
+            AMG_TRY(exclusive_scan_int(flag, snap, nl, &nsingle, s));  // snap reused as scratch
+            if (nsingle > 0) {
+                set_last_error("aggregation left %d nodes unassigned at level %d", nsingle, l);
+                return AMG_ERR_UNSUPPORTED;
+            }
+            // aggregates per system: the roots inside each system's row range
+            std::vector<int> hroot((size_t)nl + 1);
+            AMG_CUDA_TRY(cudaMemcpyAsync(hroot.data(), root_id, sizeof(int) * ((size_t)nl + 1), cudaMemcpyDeviceToHost, s));
+            AMG_CUDA_TRY(cudaStreamSynchronize(s));
+            bool stalled = false;
+            for (int k = 0; k < ns; ++k) {
+                nc_sys[k] = B.fin[k] ? 0 : hroot[B.off[k + 1]] - hroot[B.off[k]];
+                const int m = B.off[k + 1] - B.off[k];
+                if (!B.fin[k] && nc_sys[k] >= m) {
+                    B.fin[k] = 1;  // no shrink: this system ends here
+                    stalled = true;
+                }
+            }
+            nc = nroots;
+            if (!stalled) break;
+            if (attempt > ns) {
+                set_last_error("batched coarsening did not settle at level %d", l);
+                return AMG_ERR_STALL;
+            }
+        }
+        Lv.A.v32 = nullptr;
+        AMG_TRY(batch_dense(h, l, s));
+        bool any_active = false;
+        for (int k = 0; k < ns; ++k) any_active |= !B.fin[k];
+        if (!any_active) break;
+
+        // prolongator with per-system omega_P
+        unsigned long long *rho_bits;
+        double *om_sys, *om_row;
+        AMG_TRY(sc.alloc(&rho_bits, (size_t)ns));
+        AMG_TRY(sc.alloc(&om_sys, (size_t)ns));
+        AMG_TRY(sc.alloc(&om_row, (size_t)nl));
+        AMG_CUDA_TRY(cudaMemsetAsync(rho_bits, 0, sizeof(unsigned long long) * ns, s));
+        k_gershgorin_sys<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.v, diag, row_sys, active, rho_bits);
+        AMG_LAUNCH_CHECK();
+        std::vector<unsigned long long> hb(ns);
+        AMG_CUDA_TRY(cudaMemcpyAsync(hb.data(), rho_bits, sizeof(unsigned long long) * ns, cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        std::vector<double> hom(ns, 0.0);
+        double rho_max = 0.0;
+        for (int k = 0; k < ns; ++k) {
+            if (B.fin[k]) continue;
+            double rho;
+            memcpy(&rho, &hb[k], sizeof(rho));
+            const double c43 = 4.0 / 3.0;
+            hom[k] = c43 / rho;
+            rho_max = std::max(rho_max, rho);
+        }
+        Lv.rho = rho_max;
+        AMG_CUDA_TRY(cudaMemcpyAsync(om_sys, hom.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+        k_omega_rows<<<grid_for(nl), 256, 0, s>>>(nl, row_sys, active, om_sys, om_row);
+        int *tflag, *trp, *tci;
+        AMG_TRY(sc.alloc(&tflag, (size_t)nl + 1));
+        AMG_TRY(sc.alloc(&trp, (size_t)nl + 1));
+        k_assigned<<<grid_for(nl), 256, 0, s>>>(nl, Lv.agg, tflag);
+        AMG_LAUNCH_CHECK();
+        int tnnz = 0;
+        AMG_TRY(exclusive_scan_int(tflag, trp, nl, &tnnz, s));
+        AMG_TRY(sc.alloc(&tci, (size_t)std::max(1, tnnz)));
+        k_t_fill<<<grid_for(nl), 256, 0, s>>>(nl, Lv.agg, trp, tci);
+        AMG_LAUNCH_CHECK();
+        ProlongEpi epi{Lv.agg, diag, 0.0, om_row};
+        AMG_TRY((spgemm<EPI_PROLONG>(nl, nc, A.rp, A.ci, A.v, trp, tci, nullptr, epi, Lv.P, ar, s)));
+        AMG_TRY(transpose_csr(Lv.P, Lv.R, ar, s));
+        DevCSR AP;
+        AMG_TRY((spgemm<EPI_NONE>(nl, nc, A.rp, A.ci, A.v, Lv.P.rp, Lv.P.ci, Lv.P.v, ProlongEpi{}, AP, sc.arena, s)));
+        Level &Ln = h->L[l + 1];
+        AMG_TRY((spgemm<EPI_NONE>(nc, nc, Lv.R.rp, Lv.R.ci, Lv.R.v, AP.rp, AP.ci, AP.v, ProlongEpi{}, Ln.A, ar, s)));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        // the next level holds the systems still coarsening
+        BatchLevel &Bn = h->bl[l + 1];
+        Bn.sys.clear();
+        Bn.off.assign(1, 0);
+        for (int k = 0; k < ns; ++k)
+            if (!B.fin[k]) {
+                Bn.sys.push_back(B.sys[k]);
+                Bn.off.push_back(Bn.off.back() + nc_sys[k]);
+            }
+        ++l;
+    }
+    h->nlevels = l + 1;
+    h->nc = 0;
+    h->cinv = nullptr;
+    // Ahat = A W, FP32 copies; work vectors are allocated by the batched workspace
+    const bool mixed = cfg.precision == AMG_PRECISION_MIXED;
+    for (int k = 0; k < h->nlevels; ++k) {
+        Level &Lv = h->L[k];
+        const int nl = Lv.A.nrows;
+        const bool last = k == h->nlevels - 1;
+        Lv.vec_a = choose_vec(Lv.A.nnz, nl);
+        AMG_TRY(ar.alloc(&Lv.ahat, (size_t)std::max(1LL, Lv.A.nnz)));
+        if (mixed) AMG_TRY(ar.alloc(&Lv.ahat32, (size_t)std::max(1LL, Lv.A.nnz)));
+        k_scale_cols<<<grid_for(nl), 256, 0, s>>>(nl, Lv.A.rp, Lv.A.ci, Lv.A.v, Lv.w, Lv.ahat, Lv.ahat32);
+        if (!last) {
+            Lv.vec_p = choose_vec(Lv.P.nnz, nl);
+            Lv.vec_r = choose_vec(Lv.R.nnz, Lv.R.nrows);
+        }
+        if (mixed) {
+            AMG_TRY(ar.alloc(&Lv.A.v32, (size_t)std::max(1LL, Lv.A.nnz)));
+            k_to_f32<<<grid_for(Lv.A.nnz), 256, 0, s>>>(Lv.A.v, Lv.A.v32, Lv.A.nnz);
+            AMG_TRY(ar.alloc(&Lv.w32, (size_t)nl));
+            k_to_f32<<<grid_for(nl), 256, 0, s>>>(Lv.w, Lv.w32, nl);
+            if (!last) {
+                AMG_TRY(ar.alloc(&Lv.P.v32, (size_t)std::max(1LL, Lv.P.nnz)));
+                k_to_f32<<<grid_for(Lv.P.nnz), 256, 0, s>>>(Lv.P.v, Lv.P.v32, Lv.P.nnz);
+                AMG_TRY(ar.alloc(&Lv.R.v32, (size_t)std::max(1LL, Lv.R.nnz)));
+                k_to_f32<<<grid_for(Lv.R.nnz), 256, 0, s>>>(Lv.R.v, Lv.R.v32, Lv.R.nnz);
+            }
+        }
+        AMG_LAUNCH_CHECK();
+    }
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return AMG_OK;
 }
 
 void free_hierarchy(Hierarchy *h) {

@@ -3,6 +3,8 @@
 
 #include "amg_common.cuh"
 
+struct amg_batch_ws;  // batched-solve work space (batched.cu)
+
 namespace amg {
 
 // Per-kernel tracing: when on, every solve-phase launch is bracketed by CUDA
@@ -77,5 +79,15 @@ int vcycle_apply(Hierarchy *h, Workspace &W, const double *r, double *z, cudaStr
 
 // dA[k] = -lambda[row(k)] * x[col(k)] on h's finest pattern.
 int grad_values(Hierarchy *h, Workspace &W, const double *lambda, const double *x, double *dA, cudaStream_t s);
+
+// Block-diagonal batches (h->nsys > 0): work space for up to 8 right-hand
+// sides per system, and the solve of every (system, right-hand side) pair.
+// B: [n][nrhs] (host or device), X likewise; iters / rel_res: [nsys][nrhs]
+// (host or device, may be null); res: worst status, largest iteration count
+// and largest relative residuals over the pairs.
+int batch_create(Hierarchy *h, amg_batch_ws **out);
+void batch_destroy(amg_batch_ws *W);
+int batch_solve(Hierarchy *h, amg_batch_ws *W, Profiler &prof, int nrhs, const double *B, double *X, int *iters,
+                double *rel_res, cudaStream_t s, SolveResult *res);
 
 }  // namespace amg
