@@ -169,16 +169,28 @@ struct Hierarchy {
     int symmetric = 0;
     int nlevels = 0;
     Level L[AMG_MAX_LEVELS];
-    int nc = 0;                 // rows of the coarsest level
-    double *cinv = nullptr;     // dense inverse of the coarsest operator, nc x nc row-major
+    // The solve runs levels 0 .. nsolve-1; on level nsolve-1 the rest of the
+    // cycle is applied as one dense nc x nc matrix (row-major): the coarsest
+    // inverse when nsolve == nlevels, else the exact operator of the cycle
+    // from that level down (collapsed at setup); cinv32 is its FP32 copy for
+    // the mixed cycle (collapsed operators only).
+    int nsolve = 0;
+    int nc = 0;
+    double *cinv = nullptr;
+    float *cinv32 = nullptr;
+    // copies of the dense operator with rows padded to nc_ld entries (a
+    // multiple of 4, zero-filled) for 16-byte vector loads
+    int nc_ld = 0;
+    double *cpad64 = nullptr;
+    float *cpad32 = nullptr;
     // Fused coarse levels: levels tail_start..nlevels-1 run in one cluster launch
     // (tail_start = -1: not used); device tables for FP64 and FP32 cycles.
     int nsys = 0;                  // > 0: a block-diagonal batch of nsys independent systems
     std::vector<BatchLevel> bl;    // per level (batches only)
     int tail_start = -1;
     int tail_cluster = 0;
-    void *tail_args64 = nullptr;
-    void *tail_args32 = nullptr;
+    std::vector<unsigned char> tail_args64, tail_args32;  // host copies of the kernel's parameter tables
+    int tail_smem64 = 0, tail_smem32 = 0;  // dynamic shared memory of each table's launch
     // One Krylov iteration captured as a CUDA graph (replayed per iteration);
     // iter_kind: which iteration it holds, iter_kernels: launches it contains.
     cudaGraphExec_t iter_exec = nullptr;

@@ -906,6 +906,8 @@ static int choose_vec(long long nnz, int nrows) {
     return v;
 }
 
+static int collapse_coarse(Hierarchy *h, cudaStream_t s);
+
 int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const double *v_in, cudaStream_t s) {
     const amg_config &cfg = h->cfg;
     const int n = h->n;
@@ -1182,6 +1184,7 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
         }
     }
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    AMG_TRY(collapse_coarse(h, s));
     return tail_prepare(h, s);
 }
 
@@ -1304,6 +1307,150 @@ static int batch_dense(Hierarchy *h, int l, cudaStream_t s) {
             return AMG_NOT_SPD;
         }
     return AMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Collapsing the coarse end of the cycle into one dense operator
+// ---------------------------------------------------------------------------
+//
+// With a fixed hierarchy and a zero initial iterate, the V(1,1) cycle from
+// level l down is a fixed linear map x_l = M_l b_l.  From the cycle's steps
+// (pre-smoothing x = W b, residual, restriction, the coarser cycle,
+// prolongation, post-smoothing):
+//   T   = W + P_l M_{l+1} R_l (I - A_l W)     (the iterate after the correction)
+//   M_l = W + T - W (A_l T)                   (after post-smoothing)
+// with M_{L-1} the coarsest inverse.  Every product below is a plain sum in
+// a fixed order (CSR order, then increasing index), separately rounded.
+
+// E = I - A W (dense n x n, zero-filled beforehand)
+__global__ void k_dense_i_minus_aw(int n, const int *rp, const int *ci, const double *v, const double *w, double *E) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        E[(size_t)i * n + i] = 1.0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const int j = ci[k];
+            E[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - v[k] * w[j];
+        }
+    }
+}
+
+// C = S B: S sparse (rows), B dense row-major with nb columns
+__global__ void k_spmm_dense(int rows, int nb, const int *rp, const int *ci, const double *v, const double *B, double *C) {
+    const long long total = (long long)rows * nb;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / nb), j = (int)(e % nb);
+        double s = 0.0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) s = s + v[k] * B[(size_t)ci[k] * nb + j];
+        C[e] = s;
+    }
+}
+
+// C = M B: M dense m x m, B dense m x nb
+__global__ void k_gemm_dense(int m, int nb, const double *M, const double *B, double *C) {
+    const long long total = (long long)m * nb;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / nb), j = (int)(e % nb);
+        double s = 0.0;
+        for (int q = 0; q < m; ++q) s = s + M[(size_t)i * m + q] * B[(size_t)q * nb + j];
+        C[e] = s;
+    }
+}
+
+// T += W (diagonal)
+__global__ void k_add_diag(int n, double *T, const double *w) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) T[(size_t)i * n + i] += w[i];
+}
+
+// M = W + T - W U
+__global__ void k_collapse_combine(int n, const double *T, const double *U, const double *w, double *M) {
+    const long long total = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        M[e] = ((i == j ? w[i] : 0.0) + T[e]) - w[i] * U[e];
+    }
+}
+
+// padded row-major copies of a dense m x m operator: rows of ld entries, zero beyond m
+__global__ void k_pad_dense(int m, int ld, const double *in, double *out64, float *out32) {
+    const long long total = (long long)m * ld;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ld), j = (int)(e % ld);
+        const double v = j < m ? in[(size_t)i * m + j] : 0.0;
+        out64[e] = v;
+        if (out32) out32[e] = (float)v;
+    }
+}
+
+__global__ void k_to_f32_ll(const double *in, float *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+static int grid_ll(long long n);
+
+// The padded copies of the dense operator the solve applies (h->cinv).
+static int pad_dense(Hierarchy *h, cudaStream_t s) {
+    const int m = h->nc;
+    const int ld = (m + 3) / 4 * 4;
+    const long long tot = (long long)m * ld;
+    h->nc_ld = ld;
+    AMG_TRY(h->arena.alloc(&h->cpad64, (size_t)tot));
+    if (h->cfg.precision == AMG_PRECISION_MIXED) AMG_TRY(h->arena.alloc(&h->cpad32, (size_t)tot));
+    k_pad_dense<<<grid_ll(tot), 256, 0, s>>>(m, ld, h->cinv, h->cpad64, h->cpad32);
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+static int grid_ll(long long n) { return (int)std::max(1LL, std::min((n + 255) / 256, (long long)num_sms() * 32)); }
+
+// Chooses the first level below the finest with at most COLLAPSE_MAX rows and,
+// if coarser levels follow it, replaces the rest of the cycle from there by
+// its dense operator (h->nsolve, h->nc, h->cinv, h->cinv32).
+constexpr int COLLAPSE_MAX = 2048;
+
+static int collapse_coarse(Hierarchy *h, cudaStream_t s) {
+    const int L = h->nlevels;
+    h->nsolve = L;
+    int tc = 1;
+    while (tc < L && h->L[tc].A.nrows > COLLAPSE_MAX) ++tc;
+    if (tc >= L - 1) return pad_dense(h, s);
+    DevArena &ar = h->arena;
+    Scratch sc;
+    const int nmax = h->L[tc].A.nrows;
+    const size_t sq = (size_t)nmax * nmax;
+    double *E, *Y, *Z, *T, *U, *Mnext = h->cinv, *Mcur = nullptr;
+    AMG_TRY(sc.alloc(&E, sq));
+    AMG_TRY(sc.alloc(&Y, sq));
+    AMG_TRY(sc.alloc(&Z, sq));
+    AMG_TRY(sc.alloc(&T, sq));
+    AMG_TRY(sc.alloc(&U, sq));
+    for (int l = L - 2; l >= tc; --l) {
+        const Level &lv = h->L[l];
+        const int n = lv.A.nrows, m = lv.R.nrows;
+        const long long nn = (long long)n * n, mn = (long long)m * n;
+        if (l == tc) AMG_TRY(ar.alloc(&Mcur, (size_t)nn));
+        else AMG_TRY(sc.alloc(&Mcur, (size_t)nn));
+        AMG_CUDA_TRY(cudaMemsetAsync(E, 0, sizeof(double) * nn, s));
+        k_dense_i_minus_aw<<<grid_for(n), 256, 0, s>>>(n, lv.A.rp, lv.A.ci, lv.A.v, lv.w, E);
+        k_spmm_dense<<<grid_ll(mn), 256, 0, s>>>(m, n, lv.R.rp, lv.R.ci, lv.R.v, E, Y);   // Y = R (I - A W)
+        k_gemm_dense<<<grid_ll(mn), 256, 0, s>>>(m, n, Mnext, Y, Z);                      // Z = M_{l+1} Y
+        k_spmm_dense<<<grid_ll(nn), 256, 0, s>>>(n, n, lv.P.rp, lv.P.ci, lv.P.v, Z, T);   // T = P Z
+        k_add_diag<<<grid_for(n), 256, 0, s>>>(n, T, lv.w);                                // T += W
+        k_spmm_dense<<<grid_ll(nn), 256, 0, s>>>(n, n, lv.A.rp, lv.A.ci, lv.A.v, T, U);   // U = A T
+        k_collapse_combine<<<grid_ll(nn), 256, 0, s>>>(n, T, U, lv.w, Mcur);
+        AMG_LAUNCH_CHECK();
+        Mnext = Mcur;
+    }
+    h->nsolve = tc + 1;
+    h->nc = nmax;
+    h->cinv = Mcur;
+    if (h->cfg.precision == AMG_PRECISION_MIXED) {
+        AMG_TRY(ar.alloc(&h->cinv32, sq));
+        k_to_f32_ll<<<grid_ll((long long)sq), 256, 0, s>>>(Mcur, h->cinv32, (long long)sq);
+        AMG_LAUNCH_CHECK();
+    }
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return pad_dense(h, s);
 }
 
 int build_hierarchy_batched(Hierarchy *h, const int *rp_in, const int *ci_in, const double *v_in,
@@ -1591,6 +1738,7 @@ int build_hierarchy_batched(Hierarchy *h, const int *rp_in, const int *ci_in, co
         ++l;
     }
     h->nlevels = l + 1;
+    h->nsolve = h->nlevels;
     h->nc = 0;
     h->cinv = nullptr;
     // Ahat = A W, FP32 copies; work vectors are allocated by the batched workspace

@@ -6,6 +6,7 @@
 // sum, and the last block to finish (ticket counter) adds the partials in
 // block order and updates the Krylov scalars on the device.
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 
 #include "solve.cuh"
@@ -238,6 +239,52 @@ __global__ void __launch_bounds__(BLOCK) k_coarse(int m, const double *__restric
     if (FIN == FIN_PCG_BETA) {
         double tot[2];
         if (reduce_last<2>(acc, part, cap, counter, tot) && threadIdx.x == 0) finish_pcg_beta(sc, tot);
+    }
+}
+
+// The dense operator of the coarse end of the cycle: x = M b (M m x m, rows
+// padded to ld entries with zeros), one warp per row reading 16-byte vectors
+// with all of a lane's loads of the row in flight together; b is staged into
+// shared memory (zero beyond m); FP64 accumulation.
+constexpr int DENSE_MAX_LD = 2048;
+
+template <typename TMAT, typename TV>
+__global__ void __launch_bounds__(BLOCK) k_dense_apply(int m, int ld, const TMAT *__restrict__ M,
+                                                       const TV *__restrict__ b, TV *__restrict__ x, const int *done) {
+    if (*done) return;
+    __shared__ __align__(16) TMAT sb[DENSE_MAX_LD];
+    for (int j = threadIdx.x; j < ld; j += BLOCK) sb[j] = j < m ? (TMAT)b[j] : (TMAT)0;
+    __syncthreads();
+    using V = typename std::conditional<sizeof(TMAT) == 4, float4, double2>::type;
+    constexpr int VW = sizeof(V) / sizeof(TMAT);
+    const int lane = threadIdx.x & 31;
+    const int nv = ld / VW;
+    for (int i = (blockIdx.x * BLOCK + threadIdx.x) >> 5; i < m; i += (gridDim.x * BLOCK) >> 5) {
+        const V *row = reinterpret_cast<const V *>(M + (size_t)i * ld);
+        const V *bv = reinterpret_cast<const V *>(sb);
+        double s = 0.0;
+        constexpr int U = 8;
+        for (int q0 = lane; q0 < nv; q0 += 32 * U) {
+            V a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + 32 * u;
+                if (q < nv) a[u] = __ldg(row + q);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + 32 * u;
+                if (q < nv) {
+                    const V c = bv[q];
+                    if constexpr (VW == 4)
+                        s += (double)a[u].x * c.x + (double)a[u].y * c.y + (double)a[u].z * c.z + (double)a[u].w * c.w;
+                    else
+                        s += a[u].x * c.x + a[u].y * c.y;
+                }
+            }
+        }
+        s = warp_sum(s);
+        if (lane == 0) x[i] = (TV)s;
     }
 }
 
@@ -887,7 +934,7 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevScalars
 // Refines every streaming plan of the hierarchy by timed trial (the autotuner).
 int autotune_plans(Hierarchy *h, DevScalars *sc, cudaStream_t s) {
     const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
-    for (int l = 0; l < h->nlevels - 1; ++l) {
+    for (int l = 0; l < h->nsolve - 1; ++l) {
         Level &lv = h->L[l];
         if (mixed) {
             AMG_TRY(tune_plan<float>(lv.A, lv.A.v32, lv.sa, sc, s));
@@ -908,59 +955,198 @@ int autotune_plans(Hierarchy *h, DevScalars *sc, cudaStream_t s) {
 // Fused coarse levels (tail.cuh)
 // ---------------------------------------------------------------------------
 
+// Shared memory one tail CTA may use (the SM's 228 KB less the static part).
+constexpr int TAIL_SMEM_MAX = 220 * 1024;
+
+// Splits an operator's rows into `cta` contiguous slices of about equal
+// stored entries (dense: equal rows) and picks the lanes per row.
+template <typename TV>
+static void tail_partition(tail::TOp<TV> &op, const std::vector<int> &rp, int cta) {
+    const int n = op.n;
+    const long long nnz = op.ci ? rp[n] : (long long)n * op.ncols;
+    op.r0[0] = 0;
+    for (int c = 1; c < cta; ++c) {
+        if (op.ci) {
+            const long long target = nnz * c / cta;
+            op.r0[c] = (int)(std::lower_bound(rp.begin(), rp.begin() + n + 1, (int)target) - rp.begin());
+        } else {
+            op.r0[c] = (int)((long long)n * c / cta);
+        }
+        op.r0[c] = std::max(op.r0[c], op.r0[c - 1]);
+    }
+    for (int c = cta; c <= tail::MAX_CTAS; ++c) op.r0[c] = n;
+    for (int c = 0; c <= tail::MAX_CTAS; ++c) op.e0[c] = op.ci ? rp[op.r0[c]] : 0;
+    int rows_max = 1;
+    for (int c = 0; c < cta; ++c) rows_max = std::max(rows_max, op.r0[c + 1] - op.r0[c]);
+    const double mean = n > 0 ? (double)nnz / n : 1.0;
+    int by_rows = 1;
+    while (by_rows < 32 && (long long)(by_rows * 2) * rows_max <= tail::THREADS) by_rows <<= 1;
+    int by_nnz = 1;
+    while (by_nnz < 32 && by_nnz < mean) by_nnz <<= 1;
+    op.vec = std::max(1, std::min(by_rows, by_nnz));
+}
+
+// Largest shared-memory slice (bytes, 16-aligned) of an operator over the CTAs.
+template <typename TV>
+static void tail_slice_bytes(const tail::TOp<TV> &op, const std::vector<int> &rp, int cta, long long &rpb,
+                             long long &cib, long long &vb) {
+    rpb = cib = vb = 0;
+    for (int c = 0; c < cta; ++c) {
+        const int r0 = op.r0[c], r1 = op.r0[c + 1];
+        if (r0 >= r1) continue;
+        long long e0, e1;
+        if (op.ci) {
+            rpb = std::max(rpb, (tail::align_hi<int>(r1 + 1) - tail::align_lo<int>(r0)) * 4);
+            e0 = rp[r0];
+            e1 = rp[r1];
+            if (e1 > e0) cib = std::max(cib, (tail::align_hi<int>(e1) - tail::align_lo<int>(e0)) * 4);
+        } else {
+            e0 = (long long)r0 * op.ncols;
+            e1 = (long long)r1 * op.ncols;
+        }
+        if (e1 > e0) vb = std::max(vb, (tail::align_hi<TV>(e1) - tail::align_lo<TV>(e0)) * (long long)sizeof(TV));
+    }
+}
+
+static int host_rp(const DevCSR &m, std::vector<int> &rp) {
+    rp.resize((size_t)m.nrows + 1);
+    AMG_CUDA_TRY(cudaMemcpy(rp.data(), m.rp, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost));
+    return AMG_OK;
+}
+
+// Bytes CTA c bulk-copies for one preloaded operator (the same rounding as
+// the kernel's preload()).
+template <typename TV>
+static long long tail_cta_bytes(const tail::TOp<TV> &op, int c) {
+    if (!op.res) return 0;
+    const int r0 = op.r0[c], r1 = op.r0[c + 1];
+    if (r0 >= r1) return 0;
+    long long by = 0, e0, e1;
+    if (op.ci) {
+        by += (tail::align_hi<int>(r1 + 1) - tail::align_lo<int>(r0)) * 4;
+        e0 = op.e0[c];
+        e1 = op.e0[c + 1];
+        if (e1 > e0) by += (tail::align_hi<int>(e1) - tail::align_lo<int>(e0)) * 4;
+    } else {
+        e0 = (long long)r0 * op.ncols;
+        e1 = (long long)r1 * op.ncols;
+    }
+    if (e1 > e0) by += (tail::align_hi<TV>(e1) - tail::align_lo<TV>(e0)) * (long long)sizeof(TV);
+    return by;
+}
+
+// Builds the kernel's parameter table for the fused tail from level t: row
+// slices, lanes per row, and the shared-memory layout -- the staged vector,
+// every smoothed level's w and b, then the slices of the finest tail level's
+// A, P, R, the next level's, ..., the coarsest inverse, each preloaded while
+// the budget lasts.
 template <typename TM>
-static int build_tail_table(Hierarchy *h, int t, void **out) {
+static int build_tail_table(Hierarchy *h, int t, int cta, std::vector<unsigned char> &out, int *smem_bytes) {
     const bool mixed = sizeof(TM) == 4;
     tail::TArgs<TM> a;
     memset(&a, 0, sizeof(a));
-    a.nlev = h->nlevels - t;
+    a.nlev = h->nsolve - t;
     a.level0 = t == 0;
     a.nc = h->nc;
-    a.cinv = h->cinv;
+    // operators and their row slices
+    std::vector<std::vector<int>> rps;  // host row pointers, in placement order
+    std::vector<tail::TOp<TM> *> order;
     for (int k = 0; k < a.nlev; ++k) {
         const Level &lv = h->L[t + k];
         tail::TLevel<TM> &d = a.L[k];
         d.n = lv.A.nrows;
-        // lanes per row: the row-vector choice, widened while the cluster's
-        // threads outnumber the level's rows
-        const int threads = h->tail_cluster * tail::THREADS;
-        auto widen = [&](int vec, int rows) {
-            while (vec < 32 && (long long)rows * vec * 2 <= threads) vec <<= 1;
-            return vec;
-        };
-        d.vec_a = widen(lv.vec_a, lv.A.nrows);
-        d.vec_p = widen(lv.vec_p, lv.A.nrows);
-        d.vec_r = widen(lv.vec_r, lv.R.nrows);
-        d.arp = lv.A.rp;
-        d.aci = lv.A.ci;
-        d.av = (const TM *)(mixed ? (const void *)lv.A.v32 : (const void *)lv.A.v);
-        d.ahat = (const TM *)(mixed ? (const void *)lv.ahat32 : (const void *)lv.ahat);
         d.w = (const TM *)(mixed ? (const void *)lv.w32 : (const void *)lv.w);
-        d.prp = lv.P.rp;
-        d.pci = lv.P.ci;
-        d.pv = (const TM *)(mixed ? (const void *)lv.P.v32 : (const void *)lv.P.v);
-        d.rrp = lv.R.rp;
-        d.rci = lv.R.ci;
-        d.rv = (const TM *)(mixed ? (const void *)lv.R.v32 : (const void *)lv.R.v);
         d.b = (TM *)(mixed ? (void *)lv.b32 : (void *)lv.b);
         d.t = (TM *)(mixed ? (void *)lv.t32 : (void *)lv.t);
         d.x = (TM *)(mixed ? (void *)lv.x32 : (void *)lv.x);
+        d.ws_off = d.bs_off = -1;
+        if (k == a.nlev - 1) break;  // the coarsest level is solved with its dense inverse
+        struct {
+            tail::TOp<TM> *op;
+            const DevCSR *m;
+        } ops[3] = {{&d.A, &lv.A}, {&d.P, &lv.P}, {&d.R, &lv.R}};
+        for (auto &o : ops) {
+            o.op->rp = o.m->rp;
+            o.op->ci = o.m->ci;
+            o.op->v = (const TM *)(mixed ? (const void *)o.m->v32 : (const void *)o.m->v);
+            o.op->n = o.m->nrows;
+            o.op->ncols = o.m->ncols;
+            rps.emplace_back();
+            AMG_TRY(host_rp(*o.m, rps.back()));
+            tail_partition(*o.op, rps.back(), cta);
+            order.push_back(o.op);
+        }
     }
-    tail::TArgs<TM> *dev = nullptr;
-    AMG_TRY(h->arena.alloc(&dev, 1));
-    AMG_CUDA_TRY(cudaMemcpy(dev, &a, sizeof(a), cudaMemcpyHostToDevice));
-    *out = dev;
+    const std::vector<int> none;
+    a.C.rp = nullptr;
+    a.C.ci = nullptr;
+    a.C.v = h->cinv;
+    a.C.n = a.nc;
+    a.C.ncols = a.nc;
+    tail_partition(a.C, none, cta);
+    // shared memory: the staged vector, every smoothed level's w and b, then
+    // operator slices
+    long long stage = a.nc;
+    for (int k = 0; k < a.nlev; ++k) stage = std::max<long long>(stage, h->L[t + k].A.nrows);
+    long long off = (stage * sizeof(TM) + 127) / 128 * 128;
+    a.stage_off = 0;
+    if (off > TAIL_SMEM_MAX) {
+        *smem_bytes = -1;  // does not fit: no fused tail
+        return AMG_OK;
+    }
+    for (int k = 0; k < a.nlev - 1; ++k) {
+        tail::TLevel<TM> &d = a.L[k];
+        const long long vb = (tail::align_hi<TM>(d.n)) * (long long)sizeof(TM);
+        if (off + 2 * vb <= TAIL_SMEM_MAX) {
+            d.ws_off = (int)off;
+            d.bs_off = (int)(off + vb);
+            off += 2 * vb;
+        }
+    }
+    auto place = [&](auto &op, const std::vector<int> &rp) {
+        long long rpb, cib, vb;
+        tail_slice_bytes(op, rp, cta, rpb, cib, vb);
+        const long long need = rpb + cib + vb;
+        if (off + need > TAIL_SMEM_MAX) {
+            op.res = 0;
+            return;
+        }
+        op.res = 1;
+        op.rp_off = (int)off;
+        op.ci_off = (int)(off + rpb);
+        op.v_off = (int)(off + rpb + cib);
+        off += need;
+    };
+    for (size_t q = 0; q < order.size(); ++q) place(*order[q], rps[q]);
+    place(a.C, none);
+    for (int c = 0; c < cta; ++c) {
+        long long tx = tail_cta_bytes(a.C, c);
+        for (int k = 0; k < a.nlev - 1; ++k) {
+            const tail::TLevel<TM> &d = a.L[k];
+            tx += tail_cta_bytes(d.A, c) + tail_cta_bytes(d.P, c) + tail_cta_bytes(d.R, c);
+            if (d.ws_off >= 0) tx += tail::align_hi<TM>(d.n) * (long long)sizeof(TM);
+        }
+        a.tx[c] = (unsigned)tx;
+    }
+    out.resize(sizeof(a));
+    memcpy(out.data(), &a, sizeof(a));
+    *smem_bytes = (int)off;
     return AMG_OK;
 }
 
 template <typename TM>
-static int tail_cluster_size() {
+static int tail_cluster_size(int smem) {
     const void *fn = (const void *)tail::k_tail<TM>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     for (int cs : {16, 8}) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cs);
         cfg.blockDim = dim3(tail::THREADS);
+        cfg.dynamicSmemBytes = smem;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = cs;
@@ -979,20 +1165,34 @@ static int tail_cluster_size() {
 // small -- no streaming plan, fewer than 16384 rows and at most 400K stored
 // entries, a few MB that one cluster of 16 SMs reads faster than a
 // full-GPU launch can start -- and at least one of them is smoothed.  Builds
-// the device tables and picks the cluster size.
+// the device tables (the cluster size is the largest of 16 and 8 that the
+// device schedules with the tables' shared memory).
 int tail_prepare(Hierarchy *h, cudaStream_t) {
     h->tail_start = -1;
-    const int L = h->nlevels;
+    const int L = h->nsolve;
     if (L < 2) return AMG_OK;
     int t = L - 1;
     while (t > 0 && h->L[t - 1].sa.rt == 0 && h->L[t - 1].A.nrows < 16384 && h->L[t - 1].A.nnz <= 400000) --t;
     if (t > L - 2 || L - t > tail::MAX_LEVELS) return AMG_OK;
-    const int cs = h->cfg.precision == AMG_PRECISION_MIXED ? tail_cluster_size<float>() : tail_cluster_size<double>();
-    if (cs == 0) return AMG_OK;
-    h->tail_cluster = cs;
-    AMG_TRY(build_tail_table<double>(h, t, &h->tail_args64));
-    if (h->cfg.precision == AMG_PRECISION_MIXED) AMG_TRY(build_tail_table<float>(h, t, &h->tail_args32));
-    h->tail_start = t;
+    const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
+    for (int cs : {16, 8}) {
+        int s64 = 0, s32 = 0;
+        std::vector<unsigned char> a64, a32;
+        AMG_TRY(build_tail_table<double>(h, t, cs, a64, &s64));
+        if (mixed) AMG_TRY(build_tail_table<float>(h, t, cs, a32, &s32));
+        if (s64 < 0 || s32 < 0) continue;
+        const int got = tail_cluster_size<double>(s64);
+        const int got32 = mixed ? tail_cluster_size<float>(s32) : got;
+        if (got >= cs && got32 >= cs) {
+            h->tail_cluster = cs;
+            h->tail_args64 = a64;
+            h->tail_args32 = a32;
+            h->tail_smem64 = s64;
+            h->tail_smem32 = s32;
+            h->tail_start = t;
+            return AMG_OK;
+        }
+    }
     return AMG_OK;
 }
 
@@ -1003,6 +1203,7 @@ static int launch_tail(Hierarchy *h, Workspace &W, const double *b0, double *z0,
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(h->tail_cluster);
     cfg.blockDim = dim3(tail::THREADS);
+    cfg.dynamicSmemBytes = mixed ? h->tail_smem32 : h->tail_smem64;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1011,7 +1212,7 @@ static int launch_tail(Hierarchy *h, Workspace &W, const double *b0, double *z0,
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    const tail::TArgs<TM> *args = (const tail::TArgs<TM> *)(mixed ? h->tail_args32 : h->tail_args64);
+    const tail::TArgs<TM> &args = *(const tail::TArgs<TM> *)(mixed ? h->tail_args32.data() : h->tail_args64.data());
     AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, tail::k_tail<TM>, args, b0, z0, rold, fin, W.scal));
     return AMG_OK;
 }
@@ -1019,7 +1220,7 @@ static int launch_tail(Hierarchy *h, Workspace &W, const double *b0, double *z0,
 // Algorithmic bytes of the fused tail (levels t.. of one V-cycle).
 static double tail_bytes(const Hierarchy *h, int vb) {
     double by = 0.0;
-    for (int l = h->tail_start; l < h->nlevels - 1; ++l) {
+    for (int l = h->tail_start; l < h->nsolve - 1; ++l) {
         const Level &lv = h->L[l];
         by += 2.0 * (lv.A.nnz * (4.0 + vb) + 4.0 * (lv.A.nrows + 1.0)) + 2.0 * (lv.P.nnz * (4.0 + vb)) +
               4.0 * (lv.A.nrows + lv.R.nrows + 2.0) + 8.0 * vb * lv.A.nrows;
@@ -1030,7 +1231,7 @@ static double tail_bytes(const Hierarchy *h, int vb) {
 // One V-cycle: z0 = M^-1 b0.  TM = float for the mixed form.
 template <typename TM>
 static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z0, int fin, cudaStream_t s) {
-    const int L = h->nlevels;
+    const int L = h->nsolve;
     const int cap = W.part_cap;
     const int *done = &W.scal->done;
     const bool mixed = sizeof(TM) == 4;
@@ -1098,8 +1299,13 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
     } else {
         Level &lc = h->L[L - 1];
         const double m = h->nc;
-        TRACE("coarse", L - 1, m * m * 8.0 + 2.0 * vb * m);
-        k_coarse<TM, TM, FIN_NONE><<<1, BLOCK, 0, s>>>(h->nc, h->cinv, Bv(lc), Xv(lc), nullptr, W.scal, W.part, cap, W.counter);
+        const bool m32 = mixed && h->cpad32;
+        TRACE("coarse", L - 1, m * m * (m32 ? 4.0 : 8.0) + 2.0 * vb * m);
+        const int grid = std::max(1, std::min((h->nc + BLOCK / 32 - 1) / (BLOCK / 32), 4 * num_sms()));
+        if (m32)
+            k_dense_apply<float, TM><<<grid, BLOCK, 0, s>>>(h->nc, h->nc_ld, h->cpad32, Bv(lc), Xv(lc), done);
+        else
+            k_dense_apply<double, TM><<<grid, BLOCK, 0, s>>>(h->nc, h->nc_ld, h->cpad64, Bv(lc), Xv(lc), done);
         AMG_LAUNCH_CHECK();
     }
     // up
