@@ -131,13 +131,22 @@ struct DevScalars {
 // too irregular and uses the row-vector kernels.
 struct StreamPlan {
     int rt = 0, vec = 0, cap = 0, ntiles = 0;
+    int nt = 512;  // threads per CTA (768: the wide variant, 4-byte values only)
+    // windowed plans (c16 != null): per tile up to 4 windows of the gathered
+    // vector (start, length pairs; ntiles x 8 ints), 16-bit local column
+    // indices, and the window capacity per stage in elements
+    int xw = 0;
+    const int *wtab = nullptr;
+    const uint16_t *c16 = nullptr;
 };
 
 struct Level {
     DevCSR A, P, R;     // P: n x nc, R = P^T: nc x n (P, R unused on the last level)
     double *ahat = nullptr;  // A W: values a_ij w_j (the pre-smoother's operator), FP64
     float *ahat32 = nullptr; // and FP32
-    StreamPlan sa, sp, sr;   // streaming plans of A (and A W), P, R at the V-cycle's precision
+    StreamPlan sa, sp, sr;   // streaming plans of A W (pre-smoothing), P, R at the V-cycle's precision
+    StreamPlan sa_post;      // streaming plan of A for post-smoothing (tuned apart on the finest
+                             // level of the mixed cycle, where the two passes gather different types)
     StreamPlan sa64;         // plan of A for the outer FP64 products (level 0)
     double *w = nullptr;    // smoother weight per row (omega / a_ii, or 1 / sum |a_ij|)
     float *w32 = nullptr;

@@ -1157,6 +1157,7 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
         if (k == 0) AMG_TRY(plan_stream(Lv.A, cap, Lv.sa64, s));
         if (!last) {
             AMG_TRY(plan_stream(Lv.A, cap, Lv.sa, s));
+            Lv.sa_post = Lv.sa;
             AMG_TRY(plan_stream(Lv.P, cap, Lv.sp, s));
             AMG_TRY(plan_stream(Lv.R, cap, Lv.sr, s));
             AMG_TRY(ar.alloc(&Lv.ahat, (size_t)std::max(1LL, Lv.A.nnz)));

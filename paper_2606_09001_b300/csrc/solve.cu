@@ -6,6 +6,7 @@
 // sum, and the last block to finish (ticket counter) adds the partials in
 // block order and updates the Krylov scalars on the device.
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 #include <cstring>
 
@@ -688,8 +689,14 @@ struct OpPre {
     };
     __device__ bool done() const { return *dn != 0; }
     __device__ TM gather(int j) const { return (TM)__ldg(b + j); }
+    using GX = TB;
+    __device__ const GX *gsrc() const { return b; }
     __device__ Pre load(int i) const { return Pre{__ldg(b + i)}; }
+    static constexpr bool SELF = true;  // the epilogue needs the gathered vector's own entry
+    __device__ Pre load_rest(int) const { return Pre{}; }
+    __device__ void put_self(Pre &p, GX v) const { p.b = v; }
     __device__ void finish(int i, TM s, const Pre &p, double (&)[2]) const { r[i] = (TM)p.b - s; }
+    template <int NT>
     __device__ void reduce(double (&)[2]) const {}
 };
 
@@ -702,8 +709,35 @@ struct OpSpmv {
     struct Pre {};
     __device__ bool done() const { return *dn != 0; }
     __device__ TM gather(int j) const { return __ldg(x + j); }
+    using GX = TM;
+    __device__ const GX *gsrc() const { return x; }
     __device__ Pre load(int) const { return Pre{}; }
+    static constexpr bool SELF = false;
+    __device__ Pre load_rest(int i) const { return load(i); }
+    __device__ void put_self(Pre &, GX) const {}
     __device__ void finish(int i, TM s, const Pre &, double (&)[2]) const { y[i] = s; }
+    template <int NT>
+    __device__ void reduce(double (&)[2]) const {}
+};
+
+// y = M x with x of type TG (the autotuner's probe of a plan: gathers the type
+// the plan's heaviest use gathers)
+template <typename TM, typename TG>
+struct OpTune {
+    const int *dn;
+    const TG *x;
+    TM *y;
+    struct Pre {};
+    __device__ bool done() const { return *dn != 0; }
+    __device__ TM gather(int j) const { return (TM)__ldg(x + j); }
+    using GX = TG;
+    __device__ const GX *gsrc() const { return x; }
+    __device__ Pre load(int) const { return Pre{}; }
+    static constexpr bool SELF = false;
+    __device__ Pre load_rest(int i) const { return load(i); }
+    __device__ void put_self(Pre &, GX) const {}
+    __device__ void finish(int i, TM s, const Pre &, double (&)[2]) const { y[i] = s; }
+    template <int NT>
     __device__ void reduce(double (&)[2]) const {}
 };
 
@@ -721,8 +755,14 @@ struct OpProlong {
     };
     __device__ bool done() const { return *dn != 0; }
     __device__ TM gather(int j) const { return __ldg(xc + j); }
+    using GX = TM;
+    __device__ const GX *gsrc() const { return xc; }
     __device__ Pre load(int i) const { return Pre{__ldg(w + i), __ldg(b + i)}; }
+    static constexpr bool SELF = false;
+    __device__ Pre load_rest(int i) const { return load(i); }
+    __device__ void put_self(Pre &, GX) const {}
     __device__ void finish(int i, TM s, const Pre &p, double (&)[2]) const { t[i] = p.w * (TM)p.b + s; }
+    template <int NT>
     __device__ void reduce(double (&)[2]) const {}
 };
 
@@ -745,9 +785,16 @@ struct OpPost {
     };
     __device__ bool done() const { return sc->done != 0; }
     __device__ TM gather(int j) const { return __ldg(t + j); }
+    using GX = TM;
+    __device__ const GX *gsrc() const { return t; }
     __device__ Pre load(int i) const {
         return Pre{__ldg(t + i), __ldg(w + i), __ldg(b + i), (FIN == FIN_PCG_BETA && rold) ? __ldg(rold + i) : 0.0};
     }
+    static constexpr bool SELF = true;
+    __device__ Pre load_rest(int i) const {
+        return Pre{(TM)0, __ldg(w + i), __ldg(b + i), (FIN == FIN_PCG_BETA && rold) ? __ldg(rold + i) : 0.0};
+    }
+    __device__ void put_self(Pre &p, GX v) const { p.t = v; }
     __device__ void finish(int i, TM s, const Pre &p, double (&acc)[2]) const {
         const TO o = (TO)(p.t + p.w * ((TM)p.b - s));
         out[i] = o;
@@ -756,10 +803,11 @@ struct OpPost {
             acc[1] += p.ro * (double)o;
         }
     }
+    template <int NT>
     __device__ void reduce(double (&acc)[2]) const {
         if (FIN == FIN_PCG_BETA) {
             double tot[2];
-            if (reduce_last<2, stream::THREADS>(acc, part, cap, counter, tot) && threadIdx.x == 0)
+            if (reduce_last<2, NT>(acc, part, cap, counter, tot) && threadIdx.x == 0)
                 finish_pcg_beta(sc, tot);
         }
     }
@@ -780,7 +828,14 @@ struct OpFin {
     };
     __device__ bool done() const { return SF != SF_TRUE_RES && sc->done != 0; }
     __device__ double gather(int j) const { return __ldg(x + j); }
+    using GX = double;
+    __device__ const GX *gsrc() const { return x; }
     __device__ Pre load(int i) const { return Pre{SF == SF_PCG_ALPHA ? __ldg(x + i) : __ldg(dvec + i)}; }
+    static constexpr bool SELF = SF == SF_PCG_ALPHA;
+    __device__ Pre load_rest(int i) const { return SELF ? Pre{} : load(i); }
+    __device__ void put_self(Pre &p, GX v) const {
+        if (SELF) p.d = v;
+    }
     __device__ void finish(int i, double s, const Pre &p, double (&acc)[2]) const {
         if (SF == SF_TRUE_RES) {
             const double ri = p.d - s;
@@ -796,28 +851,56 @@ struct OpFin {
             }
         }
     }
+    template <int NT>
     __device__ void reduce(double (&acc)[2]) const {
         double tot[2];
-        if (reduce_last<2, stream::THREADS>(acc, part, cap, counter, tot) && threadIdx.x == 0) finish_spmv<SF>(sc, tot);
+        if (reduce_last<2, NT>(acc, part, cap, counter, tot) && threadIdx.x == 0) finish_spmv<SF>(sc, tot);
     }
 };
 
-template <typename TM, int VEC, class Op>
-static int stream_launch_vec(const StreamPlan &pl, int n, const int *rp, const int *ci, const TM *v, const Op &op,
-                             int *err, cudaStream_t s) {
-    const int smem = stream::smem_bytes<TM>(pl.rt, pl.cap);
+template <typename TM, int VEC, class Op, int NT>
+static int stream_launch_nt(const StreamPlan &pl, int n, const int *rp, const int *ci, const TM *v, const Op &op,
+                            int *err, cudaStream_t s) {
+    if constexpr (NT == 512) {
+        if (pl.c16) {
+        using GX = typename Op::GX;
+        const int smem = stream::smem_bytes_win<TM, GX, NT>(pl.rt, pl.cap, pl.xw);
+        static int attr_set = 0;
+        if (smem > attr_set) {
+            AMG_CUDA_TRY(cudaFuncSetAttribute(stream::k_stream_win<TM, VEC, Op, NT>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            attr_set = smem;
+        }
+        const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 2048)));
+        const int grid = std::max(1, std::min(pl.ntiles, per_sm * num_sms()));
+        stream::k_stream_win<TM, VEC, Op, NT><<<grid, NT, smem, s>>>(n, pl.rt, pl.cap, pl.xw, pl.ntiles, rp, pl.c16,
+                                                                      v, pl.wtab, op, err);
+        AMG_LAUNCH_CHECK();
+        return AMG_OK;
+        }
+    }
+    const int smem = stream::smem_bytes<TM, NT>(pl.rt, pl.cap);
     static int attr_set = 0;  // largest dynamic shared memory enabled for this instantiation
     if (smem > attr_set) {
-        AMG_CUDA_TRY(cudaFuncSetAttribute(stream::k_stream<TM, VEC, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          smem));
+        AMG_CUDA_TRY(cudaFuncSetAttribute(stream::k_stream<TM, VEC, Op, NT>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr_set = smem;
     }
     // CTAs per SM that fit the SM's 228 KB of shared memory (1 KB reserved per CTA)
     const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 2048)));
     const int grid = std::max(1, std::min(pl.ntiles, per_sm * num_sms()));
-    stream::k_stream<TM, VEC, Op><<<grid, stream::THREADS, smem, s>>>(n, pl.rt, pl.cap, pl.ntiles, rp, ci, v, op, err);
+    stream::k_stream<TM, VEC, Op, NT><<<grid, NT, smem, s>>>(n, pl.rt, pl.cap, pl.ntiles, rp, ci, v, op, err);
     AMG_LAUNCH_CHECK();
     return AMG_OK;
+}
+
+template <typename TM, int VEC, class Op>
+static int stream_launch_vec(const StreamPlan &pl, int n, const int *rp, const int *ci, const TM *v, const Op &op,
+                             int *err, cudaStream_t s) {
+    if constexpr (sizeof(TM) == 4) {
+        if (pl.nt == 768) return stream_launch_nt<TM, VEC, Op, 768>(pl, n, rp, ci, v, op, err, s);
+    }
+    return stream_launch_nt<TM, VEC, Op, 512>(pl, n, rp, ci, v, op, err, s);
 }
 
 // One streaming pass of a CSR operator whose plan is usable (pl.rt > 0).
@@ -847,7 +930,7 @@ static double csr_bytes(const DevCSR &m, int vb) {
 // consumer passes when possible, capped so that there are at least four
 // tiles per resident CTA) and threads per row (the mean-length choice and
 // twice it).  Every candidate keeps each tile within cap - 8 stored entries.
-static std::vector<StreamPlan> plan_candidates(const DevCSR &m, const StreamPlan &base, cudaStream_t s) {
+static std::vector<StreamPlan> plan_candidates(const DevCSR &m, const StreamPlan &base, bool wide, cudaStream_t s) {
     std::vector<StreamPlan> out;
     if (base.rt == 0) return out;
     const int n = m.nrows;
@@ -877,26 +960,250 @@ static std::vector<StreamPlan> plan_candidates(const DevCSR &m, const StreamPlan
             p.vec = vec;
             p.ntiles = (n + rt - 1) / rt;
             bool dup = false;
-            for (const StreamPlan &q : out) dup |= q.rt == p.rt && q.vec == p.vec;
+            for (const StreamPlan &q : out) dup |= q.rt == p.rt && q.vec == p.vec && q.nt == p.nt;
             if (!dup) out.push_back(p);
+        }
+    }
+    if (wide) {
+        // 768-thread CTAs (23 consumer warps, two stages of 6144 entries):
+        // tiles of one or two whole consumer passes
+        for (int vec : {base.vec, base.vec * 2}) {
+            if (vec > 32) continue;
+            const int pass = 23 * 32 / vec;
+            for (int rt : {pass, 2 * pass}) {
+                if (rt > stream::RT_MAX || worst(rt) > 6144 - 8) continue;
+                StreamPlan p = base;
+                p.nt = 768;
+                p.cap = 6144;
+                p.rt = rt;
+                p.vec = vec;
+                p.ntiles = (n + rt - 1) / rt;
+                out.push_back(p);
+            }
         }
     }
     return out;
 }
 
-// Times y = M x with each candidate (three runs after one warm-up) and keeps
-// the fastest plan.  x and y are scratch vectors of the operator's sizes.
+// ---------------------------------------------------------------------------
+// Windowed plans: per-tile windows of the gathered vector
+// ---------------------------------------------------------------------------
+
+constexpr int WIN_SPAN_CH = 16384;  // largest column span of a tile, in 4-element chunks
+constexpr int WIN_GAP_CH = 8;       // runs of touched chunks closer than this share a window
+constexpr int WIN_RUNS = 1024;      // most runs a tile may have before they are grouped
+
+// One block per tile (grid-stride): the windows covering every column the
+// tile touches -- the runs of touched 4-element chunks (runs closer than
+// WIN_GAP_CH chunks joined), grouped into at most WIN_NW windows by breaking
+// at the WIN_NW - 1 widest gaps -- and each entry's offset into them.  Tiles
+// whose windows exceed xw_max elements (or that span too many columns or
+// runs) set *bad.
+__global__ void __launch_bounds__(256) k_tile_windows(int n, int rt, int ntiles, const int *__restrict__ rp,
+                                                      const int *__restrict__ ci, int xw_max, int *wtab,
+                                                      uint16_t *c16, int *bad, int *xw_used) {
+    constexpr int NW = stream::WIN_NW;
+    __shared__ unsigned char ch[WIN_SPAN_CH];
+    __shared__ int rs[WIN_RUNS], re[WIN_RUNS], gap[WIN_RUNS];
+    __shared__ int s_min, s_max, s_ok, s_nr, s_nw;
+    __shared__ int s_ws[NW], s_wl[NW], s_off[NW];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int r0 = t * rt, r1 = min(r0 + rt, n);
+        const int s = rp[r0], e = rp[r1];
+        if (threadIdx.x == 0) {
+            s_min = INT_MAX;
+            s_max = -1;
+            s_ok = 1;
+            s_nr = 0;
+            s_nw = 0;
+        }
+        __syncthreads();
+        int lmin = INT_MAX, lmax = -1;
+        for (int k = s + threadIdx.x; k < e; k += blockDim.x) {
+            const int c = ci[k];
+            lmin = min(lmin, c);
+            lmax = max(lmax, c);
+        }
+        atomicMin(&s_min, lmin);
+        atomicMax(&s_max, lmax);
+        __syncthreads();
+        const int base = s_max >= 0 ? (s_min & ~3) : 0;
+        const int nch = s_max >= 0 ? ((s_max - base) >> 2) + 1 : 0;
+        if (nch <= WIN_SPAN_CH) {
+            for (int q = threadIdx.x; q < nch; q += blockDim.x) ch[q] = 0;
+            __syncthreads();
+            for (int k = s + threadIdx.x; k < e; k += blockDim.x) ch[(ci[k] - base) >> 2] = 1;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                // warp 0 lists the runs in order (every lane keeps the same state)
+                int nr = 0, ws = -1, we = -1;
+                for (int q0 = 0; q0 < nch; q0 += 32) {
+                    const int q = q0 + threadIdx.x;
+                    unsigned msk = __ballot_sync(0xffffffffu, q < nch && ch[q]);
+                    while (msk) {
+                        const int c = q0 + __ffs(msk) - 1;
+                        msk &= msk - 1;
+                        if (ws >= 0 && c - we < WIN_GAP_CH) {
+                            we = c + 1;
+                        } else {
+                            if (ws >= 0) {
+                                if (nr < WIN_RUNS && threadIdx.x == 0) {
+                                    rs[nr] = ws;
+                                    re[nr] = we;
+                                }
+                                ++nr;
+                            }
+                            ws = c;
+                            we = c + 1;
+                        }
+                    }
+                }
+                if (ws >= 0) {
+                    if (nr < WIN_RUNS && threadIdx.x == 0) {
+                        rs[nr] = ws;
+                        re[nr] = we;
+                    }
+                    ++nr;
+                }
+                if (threadIdx.x == 0) {
+                    s_nr = nr;
+                    if (nr > WIN_RUNS) s_ok = 0;
+                }
+            }
+        } else if (threadIdx.x == 0) {
+            s_ok = 0;
+        }
+        __syncthreads();
+        const int nr = s_nr;
+        if (s_ok && nr > NW) {
+            // break at the NW - 1 widest gaps (the narrowest index on ties):
+            // gap[i] between runs i and i+1, marked -1 once chosen
+            for (int i = threadIdx.x; i < nr - 1; i += blockDim.x) gap[i] = rs[i + 1] - re[i];
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                for (int pick = 0; pick < NW - 1; ++pick) {
+                    int best = -1, bi = -1;
+                    for (int i = threadIdx.x; i < nr - 1; i += 32)
+                        if (gap[i] > best) {
+                            best = gap[i];
+                            bi = i;
+                        }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const int ob = __shfl_xor_sync(0xffffffffu, best, o), oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                        if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) {
+                            best = ob;
+                            bi = oi;
+                        }
+                    }
+                    if (threadIdx.x == 0 && bi >= 0) gap[bi] = -1;
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+        }
+        if (s_ok && threadIdx.x == 0) {
+            int nw = 0, tot = 0, ws = nr > 0 ? rs[0] : 0;
+            for (int i = 0; i < nr; ++i) {
+                const bool last = i == nr - 1;
+                const bool brk = last || nr <= NW || gap[i] < 0;
+                if (brk) {
+                    s_ws[nw] = base + 4 * ws;
+                    s_wl[nw] = 4 * (re[i] - ws);
+                    s_off[nw] = tot;
+                    tot += 4 * (re[i] - ws);
+                    ++nw;
+                    if (!last) ws = rs[i + 1];
+                }
+            }
+            s_nw = nw;
+            if (tot > xw_max) s_ok = 0;
+            else atomicMax(xw_used, tot);
+        }
+        __syncthreads();
+        if (!s_ok) {
+            if (threadIdx.x == 0) atomicExch(bad, 1);
+        } else {
+            const int nw = s_nw;
+            if (threadIdx.x < 2 * NW) {
+                const int w = threadIdx.x >> 1;
+                wtab[(size_t)t * 2 * NW + threadIdx.x] = w < nw ? ((threadIdx.x & 1) ? s_wl[w] : s_ws[w]) : 0;
+            }
+            for (int k = s + threadIdx.x; k < e; k += blockDim.x) {
+                const int c = ci[k];
+                int w = 0;
+                while (w + 1 < nw && c >= s_ws[w + 1]) ++w;
+                c16[k] = (uint16_t)(s_off[w] + (c - s_ws[w]));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Turns plan p (512 threads) into a windowed plan for operator m: tightens
+// the stage capacity to the tiles' entries, budgets the windows for FP64
+// gathers at two CTAs per SM, and builds the window table and local indices
+// in `scr`.  Returns false when some tile does not fit.
 template <typename TM>
-static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevScalars *sc, cudaStream_t s) {
-    std::vector<StreamPlan> cands = plan_candidates(m, pl, s);
-    if (cands.size() <= 1) return AMG_OK;
+static bool build_windows(const DevCSR &m, StreamPlan &p, int worst_tile, int gx_bytes, Scratch &scr, cudaStream_t s) {
+    p.cap = (worst_tile + 8 + 255) / 256 * 256;
+    const stream::WLayout<TM, double> lay(p.rt, p.cap, 0);
+    const int per_cta = (228 * 1024) / 2 - 2048;
+    const int budget = per_cta / stream::WIN_STAGES - lay.stb;
+    const int xw_max = std::min(65532, budget / gx_bytes / 4 * 4);
+    if (xw_max < 64) return false;
+    int *wtab = nullptr, *bad = nullptr, *used = nullptr;
+    uint16_t *c16 = nullptr;
+    if (scr.alloc(&wtab, (size_t)p.ntiles * 2 * stream::WIN_NW) < 0 || scr.alloc(&c16, (size_t)std::max(1LL, m.nnz)) < 0 ||
+        scr.alloc(&bad, 2) < 0) {
+        cudaGetLastError();
+        return false;
+    }
+    used = bad + 1;
+    if (cudaMemsetAsync(bad, 0, 2 * sizeof(int), s) != cudaSuccess) return false;
+    k_tile_windows<<<std::min(p.ntiles, 8 * num_sms()), 256, 0, s>>>(m.nrows, p.rt, p.ntiles, m.rp, m.ci, xw_max, wtab,
+                                                                       c16, bad, used);
+    int h[2] = {1, 0};
+    if (cudaMemcpyAsync(h, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (h[0]) return false;
+    p.xw = std::max(4, h[1]);
+    p.wtab = wtab;
+    p.c16 = c16;
+    return true;
+}
+
+// Times y = M x with each candidate (the best of three trials of ten launches,
+// after one warm-up) and keeps the fastest plan.  x and y are scratch vectors
+// of the operator's sizes.
+template <typename TM, typename TG>
+static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &ar, DevScalars *sc, cudaStream_t s) {
+    const int gx_bytes = sizeof(TG);
+    std::vector<StreamPlan> cands = plan_candidates(m, pl, sizeof(TM) == 4, s);
     Scratch scr;
-    TM *x = nullptr, *y = nullptr;
+    // windowed variants of the 512-thread candidates
+    if (pl.rt > 0) {
+        std::vector<int> rp((size_t)m.nrows + 1);
+        AMG_CUDA_TRY(cudaMemcpy(rp.data(), m.rp, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost));
+        const size_t nbase = cands.size();
+        for (size_t q = 0; q < nbase; ++q) {
+            if (cands[q].nt != 512) continue;
+            StreamPlan w = cands[q];
+            int worst = 0;
+            for (int r0 = 0; r0 < m.nrows; r0 += w.rt) worst = std::max(worst, rp[std::min(r0 + w.rt, m.nrows)] - rp[r0]);
+            if (build_windows<TM>(m, w, worst, gx_bytes, scr, s)) cands.push_back(w);
+        }
+    }
+    if (cands.size() <= 1) return AMG_OK;
+    TG *x = nullptr;
+    TM *y = nullptr;
     int *err = nullptr;
     AMG_TRY(scr.alloc(&x, (size_t)m.ncols));
     AMG_TRY(scr.alloc(&y, (size_t)m.nrows));
     AMG_TRY(scr.alloc(&err, 1));
-    AMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(TM) * (size_t)m.ncols, s));
+    AMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(TG) * (size_t)m.ncols, s));
     AMG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
     int *dn = &sc->done;  // 0 between solves
     cudaEvent_t e0, e1;
@@ -908,15 +1215,24 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevScalars
     int rc = AMG_OK;
     for (size_t ci_ = 0; ci_ < cands.size(); ++ci_) {
         const StreamPlan &c = cands[ci_];
-        OpSpmv<TM> op{dn, x, y};
+        OpTune<TM, TG> op{dn, x, y};
         if ((rc = stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals, op, err, s)) < 0) break;
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < 5; ++r)
-            if ((rc = stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals, op, err, s)) < 0) break;
-        cudaEventRecord(e1, s);
-        if (rc < 0 || cudaEventSynchronize(e1) != cudaSuccess) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        // best of three trials of ten launches
+        float ms = 1e30f;
+        for (int trial = 0; trial < 3 && rc >= 0; ++trial) {
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 10; ++r)
+                if ((rc = stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals, op, err, s)) < 0) break;
+            cudaEventRecord(e1, s);
+            if (rc < 0 || cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = rc < 0 ? rc : AMG_ERR_CUDA;
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = std::min(ms, t);
+        }
+        if (rc < 0) break;
         if (ci_ == 0) base_ms = ms;
         if (ms < best && (ci_ == 0 || ms < 0.97f * base_ms)) {
             best = ms;
@@ -927,6 +1243,19 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevScalars
     cudaEventDestroy(e1);
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
     if (rc < 0) return rc;
+    if (chosen.c16) {
+        // keep the chosen windows (the candidates live in scratch memory)
+        int *wtab = nullptr;
+        uint16_t *c16 = nullptr;
+        AMG_TRY(ar.alloc(&wtab, (size_t)chosen.ntiles * 2 * stream::WIN_NW));
+        AMG_TRY(ar.alloc(&c16, (size_t)std::max(1LL, m.nnz)));
+        AMG_CUDA_TRY(cudaMemcpyAsync(wtab, chosen.wtab, sizeof(int) * (size_t)chosen.ntiles * 2 * stream::WIN_NW,
+                                     cudaMemcpyDeviceToDevice, s));
+        AMG_CUDA_TRY(cudaMemcpyAsync(c16, chosen.c16, sizeof(uint16_t) * (size_t)m.nnz, cudaMemcpyDeviceToDevice, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        chosen.wtab = wtab;
+        chosen.c16 = c16;
+    }
     pl = chosen;
     return AMG_OK;
 }
@@ -937,16 +1266,26 @@ int autotune_plans(Hierarchy *h, DevScalars *sc, cudaStream_t s) {
     for (int l = 0; l < h->nsolve - 1; ++l) {
         Level &lv = h->L[l];
         if (mixed) {
-            AMG_TRY(tune_plan<float>(lv.A, lv.A.v32, lv.sa, sc, s));
-            AMG_TRY(tune_plan<float>(lv.P, lv.P.v32, lv.sp, sc, s));
-            AMG_TRY(tune_plan<float>(lv.R, lv.R.v32, lv.sr, sc, s));
+            // level 0's pre-smoothing gathers the FP64 Krylov vector, its
+            // post-smoothing the FP32 iterate: two plans tuned apart
+            if (l == 0) {
+                lv.sa_post = lv.sa;
+                AMG_TRY((tune_plan<float, double>(lv.A, lv.A.v32, lv.sa, h->arena, sc, s)));
+                AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa_post, h->arena, sc, s)));
+            } else {
+                AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa, h->arena, sc, s)));
+                lv.sa_post = lv.sa;
+            }
+            AMG_TRY((tune_plan<float, float>(lv.P, lv.P.v32, lv.sp, h->arena, sc, s)));
+            AMG_TRY((tune_plan<float, float>(lv.R, lv.R.v32, lv.sr, h->arena, sc, s)));
         } else {
-            AMG_TRY(tune_plan<double>(lv.A, lv.A.v, lv.sa, sc, s));
-            AMG_TRY(tune_plan<double>(lv.P, lv.P.v, lv.sp, sc, s));
-            AMG_TRY(tune_plan<double>(lv.R, lv.R.v, lv.sr, sc, s));
+            AMG_TRY((tune_plan<double, double>(lv.A, lv.A.v, lv.sa, h->arena, sc, s)));
+            lv.sa_post = lv.sa;
+            AMG_TRY((tune_plan<double, double>(lv.P, lv.P.v, lv.sp, h->arena, sc, s)));
+            AMG_TRY((tune_plan<double, double>(lv.R, lv.R.v, lv.sr, h->arena, sc, s)));
         }
     }
-    if (mixed) AMG_TRY(tune_plan<double>(h->L[0].A, h->L[0].A.v, h->L[0].sa64, sc, s));
+    if (mixed) AMG_TRY((tune_plan<double, double>(h->L[0].A, h->L[0].A.v, h->L[0].sa64, h->arena, sc, s)));
     else h->L[0].sa64 = h->L[0].sa;
     return AMG_OK;
 }
@@ -1337,20 +1676,20 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         {
             const double ob = l == 0 ? 8.0 : vb;
             TRACE("postsmooth", l, csr_bytes(lv.A, vb) + n * (2.0 * vb + bb + ob) + (rold && l == 0 ? 8.0 * n : 0.0));
-            if (lv.sa.rt) {
+            if (lv.sa_post.rt) {
                 const int *rp_ = lv.A.rp, *ci_ = lv.A.ci;
                 if (l == 0 && fin == FIN_PCG_BETA)
-                    AMG_TRY(stream_launch<TM>(lv.sa, n, rp_, ci_, Av(lv.A),
+                    AMG_TRY(stream_launch<TM>(lv.sa_post, n, rp_, ci_, Av(lv.A),
                                               OpPost<double, TM, double, FIN_PCG_BETA>{W.scal, Wv(lv), b0, Tv(lv), z0, rold,
                                                                                          W.part, cap, W.counter},
                                               err, s));
                 else if (l == 0)
-                    AMG_TRY(stream_launch<TM>(lv.sa, n, rp_, ci_, Av(lv.A),
+                    AMG_TRY(stream_launch<TM>(lv.sa_post, n, rp_, ci_, Av(lv.A),
                                               OpPost<double, TM, double, FIN_NONE>{W.scal, Wv(lv), b0, Tv(lv), z0, nullptr,
                                                                                      W.part, cap, W.counter},
                                               err, s));
                 else
-                    AMG_TRY(stream_launch<TM>(lv.sa, n, rp_, ci_, Av(lv.A),
+                    AMG_TRY(stream_launch<TM>(lv.sa_post, n, rp_, ci_, Av(lv.A),
                                               OpPost<TM, TM, TM, FIN_NONE>{W.scal, Wv(lv), Bv(lv), Tv(lv), Xv(lv), nullptr,
                                                                              W.part, cap, W.counter},
                                               err, s));

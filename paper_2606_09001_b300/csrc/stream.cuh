@@ -2,7 +2,8 @@
 // copies (cp.async.bulk + mbarrier), used for every large operator of the
 // V-cycle and the outer Krylov products.
 //
-// Warp-specialised persistent CTAs of 512 threads walk the tiles
+// Warp-specialised persistent CTAs of NT threads (512, or 768 for 4-byte
+// values) walk the tiles
 // t = blockIdx.x, blockIdx.x + gridDim.x, ... of rt consecutive rows.
 //   * Warp 0, lane 0 is the producer: for each tile it issues three bulk copies
 //     into a pipeline stage -- the tile's row pointers, column indices and
@@ -15,7 +16,8 @@
 //     functor, then arrive on the stage's "empty" mbarrier.  The producer
 //     waits on "empty" before refilling the stage.
 // No block-wide barrier runs inside the loop, so consumer warps drift freely
-// across STAGES tiles.  Every wait is bounded; a timeout sets an error flag
+// across STAGES tiles.  The wider CTA keeps more gathers in flight per SM (two
+// CTAs of 23 consumer warps instead of 15) with two pipeline stages.  Every wait is bounded; a timeout sets an error flag
 // and the CTA leaves the loop.  Optional dot products end in the
 // deterministic last-block reduction (the one __syncthreads of the kernel).
 #pragma once
@@ -25,16 +27,16 @@
 namespace amg {
 namespace stream {
 
-constexpr int THREADS = 512;
-constexpr int CONSUMER_WARPS = THREADS / 32 - 1;
+constexpr int THREADS = 512;  // the default CTA width
 constexpr int MAX_STAGES = 3;
 constexpr int RT_MAX = 1024;
 constexpr int CAP = 4096;  // stage capacity in stored entries
 
-// Pipeline depth per value type: 3 stages of 4-byte values or 2 of 8-byte
-// values keep two 512-thread CTAs resident per SM (about 104 KB each).
-template <typename TM>
-__host__ __device__ constexpr int stages() { return sizeof(TM) == 4 ? 3 : 2; }
+// Pipeline depth per value type and CTA width: 3 stages of 4-byte values or
+// 2 of 8-byte values keep two 512-thread CTAs resident per SM (about 104 KB
+// each); 768-thread CTAs use 2 stages.
+template <typename TM, int NT = THREADS>
+__host__ __device__ constexpr int stages() { return NT == 512 && sizeof(TM) == 4 ? 3 : 2; }
 
 __host__ __device__ constexpr int align16(int b) { return (b + 15) & ~15; }
 
@@ -47,8 +49,8 @@ struct Layout {
           stb(rpb + cib + vab + 16) {}
 };
 
-template <typename TM>
-inline int smem_bytes(int rt, int cap) { return stages<TM>() * Layout<TM>(rt, cap).stb; }
+template <typename TM, int NT = THREADS>
+inline int smem_bytes(int rt, int cap) { return stages<TM, NT>() * Layout<TM>(rt, cap).stb; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -89,13 +91,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
 // The row pass.  Op provides: bool done(); TM gather(int j); Pre load(int i)
 // (the row's epilogue operands, loaded before the gathers so the latencies
 // overlap); finish(int i, TM s, const Pre&, double (&acc)[2]);
-// reduce(double (&acc)[2]) (called by every thread of every CTA at the end).
-template <typename TM, int VEC, class Op>
-__global__ void __launch_bounds__(THREADS) k_stream(int n, int rt, int cap, int ntiles, const int *__restrict__ rp,
-                                                    const int *__restrict__ ci, const TM *__restrict__ v, Op op,
-                                                    int *err) {
+// reduce<NT>(double (&acc)[2]) (called by every thread of every CTA at the end).
+template <typename TM, int VEC, class Op, int NT = THREADS>
+__global__ void __launch_bounds__(NT, 2) k_stream(int n, int rt, int cap, int ntiles, const int *__restrict__ rp,
+                                                  const int *__restrict__ ci, const TM *__restrict__ v, Op op,
+                                                  int *err) {
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int STAGES = stages<TM>();
+    constexpr int STAGES = stages<TM, NT>();
+    constexpr int CONSUMER_WARPS = NT / 32 - 1;
     __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES];
     if (op.done()) return;
     const Layout<TM> L(rt, cap);
@@ -212,7 +215,183 @@ __global__ void __launch_bounds__(THREADS) k_stream(int n, int rt, int cap, int 
         // a bounded chance for copies still in flight to land before exit
         for (int k = 0; k < STAGES; ++k) mbar_try_wait(&full[k], 0);
     }
-    op.reduce(acc);
+    op.template reduce<NT>(acc);
+}
+
+// ---------------------------------------------------------------------------
+// Windowed variant: the gathered vector staged too
+// ---------------------------------------------------------------------------
+//
+// For operators whose tiles each touch only a few short ranges of columns
+// (the stencil structure of PDE matrices), setup finds, per tile, up to
+// WIN_NW windows of the gathered vector -- 4-element aligned ranges that
+// cover every column the tile touches, split at the tile's largest gaps --
+// and rewrites each stored column
+// index as a 16-bit offset into the tile's windows laid end to end.  The
+// producer then bulk-copies those windows of the vector into the stage with
+// the tile, and consumers gather from shared memory: no global load waits
+// inside the row loop, and the index stream shrinks from 4 to 2 bytes per
+// entry.  Op additionally provides GX (the gathered vector's type),
+// const GX *gsrc(), and for epilogues that need the gathered vector's entry
+// of their own row (SELF: square operators, where every row stores its
+// diagonal, so a tile's own rows lie in one window) load_rest() and
+// put_self(): that entry is then read from the staged window.
+
+constexpr int WIN_NW = 16;
+
+template <typename TM, typename GX>
+struct WLayout {
+    int rpb, cib, vab, xwb, stb;
+    __host__ __device__ WLayout(int rt, int cap, int xw)
+        : rpb(align16((rt + 8) * 4)), cib(align16((cap + 8) * 2)), vab(align16((cap + 8) * (int)sizeof(TM))),
+          xwb(align16(xw * (int)sizeof(GX))), stb(rpb + cib + vab + xwb + 16) {}
+};
+
+// Two pipeline stages: consumers no longer wait on gathers, so two tiles in
+// flight per CTA (four per SM) cover the bulk copies' latency.
+constexpr int WIN_STAGES = 2;
+
+template <typename TM, typename GX, int NT = THREADS>
+inline int smem_bytes_win(int rt, int cap, int xw) { return WIN_STAGES * WLayout<TM, GX>(rt, cap, xw).stb; }
+
+template <typename TM, int VEC, class Op, int NT = THREADS>
+__global__ void __launch_bounds__(NT, 2) k_stream_win(int n, int rt, int cap, int xw, int ntiles,
+                                                      const int *__restrict__ rp, const uint16_t *__restrict__ c16,
+                                                      const TM *__restrict__ v, const int *__restrict__ wtab, Op op,
+                                                      int *err) {
+    using GX = typename Op::GX;
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int STAGES = WIN_STAGES;
+    constexpr int CONSUMER_WARPS = NT / 32 - 1;
+    __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES];
+    if (op.done()) return;
+    const WLayout<TM, GX> L(rt, cap, xw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int k = 0; k < STAGES; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], CONSUMER_WARPS);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    double acc[2] = {0.0, 0.0};
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {
+            const GX *gx = op.gsrc();
+            for (int j = 0;; ++j) {
+                const int t = blockIdx.x + j * gridDim.x;
+                if (t >= ntiles) break;
+                const int st = j % STAGES;
+                const int r0 = t * rt, r1 = min(r0 + rt, n);
+                const int s = __ldg(rp + r0), e = __ldg(rp + r1);
+                // window table row: WIN_NW (start, length) pairs
+                const int4 *wrow = reinterpret_cast<const int4 *>(wtab) + (size_t)t * (WIN_NW / 2);
+                int4 wq[WIN_NW / 2];
+#pragma unroll
+                for (int q = 0; q < WIN_NW / 2; ++q) wq[q] = __ldg(wrow + q);
+                if (j >= STAGES && !mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *stage = smem + st * L.stb;
+                const int rp_cnt = (r1 - r0 + 1 + 3) & ~3;  // r0 is a multiple of 4
+                const int cs = s & ~7, ce = (e + 7) & ~7;
+                constexpr int PER = 16 / sizeof(TM);
+                const int vs = s & ~(PER - 1), ve = (e + PER - 1) & ~(PER - 1);
+                int *hdr = reinterpret_cast<int *>(stage + L.rpb + L.cib + L.vab + L.xwb);
+                hdr[0] = cs;
+                hdr[1] = vs;
+                // offset of column r0 in the windows when one window holds columns r0 .. r1-1
+                int dl0 = -1;
+                {
+                    int woff = 0;
+#pragma unroll
+                    for (int q = 0; q < WIN_NW / 2; ++q) {
+                        if (dl0 < 0 && wq[q].y > 0 && r0 >= wq[q].x && r1 <= wq[q].x + wq[q].y) dl0 = woff + r0 - wq[q].x;
+                        woff += wq[q].y;
+                        if (dl0 < 0 && wq[q].w > 0 && r0 >= wq[q].z && r1 <= wq[q].z + wq[q].w) dl0 = woff + r0 - wq[q].z;
+                        woff += wq[q].w;
+                    }
+                }
+                hdr[2] = dl0;
+                const uint32_t b_rp = rp_cnt * 4, b_ci = (ce - cs) * 2, b_v = (ve - vs) * (uint32_t)sizeof(TM);
+                uint32_t b_x = 0;
+#pragma unroll
+                for (int q = 0; q < WIN_NW / 2; ++q) b_x += (uint32_t)(wq[q].y + wq[q].w) * (uint32_t)sizeof(GX);
+                if (j >= STAGES) fence_proxy_async();
+                mbar_expect_tx(&full[st], b_rp + b_ci + b_v + b_x);
+                bulk_g2s(stage, rp + r0, b_rp, &full[st]);
+                if (b_ci) bulk_g2s(stage + L.rpb, c16 + cs, b_ci, &full[st]);
+                if (b_v) bulk_g2s(stage + L.rpb + L.cib, v + vs, b_v, &full[st]);
+                unsigned char *xs = stage + L.rpb + L.cib + L.vab;
+                uint32_t off = 0;
+#pragma unroll
+                for (int q = 0; q < WIN_NW / 2; ++q) {
+                    if (wq[q].y > 0) {
+                        bulk_g2s(xs + off, gx + wq[q].x, (uint32_t)wq[q].y * (uint32_t)sizeof(GX), &full[st]);
+                        off += (uint32_t)wq[q].y * (uint32_t)sizeof(GX);
+                    }
+                    if (wq[q].w > 0) {
+                        bulk_g2s(xs + off, gx + wq[q].z, (uint32_t)wq[q].w * (uint32_t)sizeof(GX), &full[st]);
+                        off += (uint32_t)wq[q].w * (uint32_t)sizeof(GX);
+                    }
+                }
+            }
+        }
+    } else {
+        constexpr int UNR = VEC == 1 ? 8 : 4;
+        const int ct = tid - 32;
+        constexpr int ROWS_PER_PASS = CONSUMER_WARPS * 32 / VEC;
+        const int rsub = ct / VEC, vl = ct % VEC;
+        for (int j = 0;; ++j) {
+            const int t = blockIdx.x + j * gridDim.x;
+            if (t >= ntiles) break;
+            const int st = j % STAGES;
+            const int r0 = t * rt;
+            const int rows = min(rt, n - r0);
+            typename Op::Pre pre0{};
+            if (rsub < rows && vl == 0) pre0 = op.load_rest(r0 + rsub);
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / STAGES) & 1)))) {  // warp-uniform
+                ok = false;
+                break;
+            }
+            const unsigned char *stage = smem + st * L.stb;
+            const int *rps = reinterpret_cast<const int *>(stage);
+            const uint16_t *cis = reinterpret_cast<const uint16_t *>(stage + L.rpb);
+            const TM *vals = reinterpret_cast<const TM *>(stage + L.rpb + L.cib);
+            const GX *xs = reinterpret_cast<const GX *>(stage + L.rpb + L.cib + L.vab);
+            const int *hdr = reinterpret_cast<const int *>(stage + L.rpb + L.cib + L.vab + L.xwb);
+            const int cs = hdr[0], vsb = hdr[1], dl0 = hdr[2];
+            for (int base = 0; base < rows; base += ROWS_PER_PASS) {
+                const int rl = base + rsub;
+                TM sum = 0;
+                typename Op::Pre pre = pre0;
+                if (rl < rows) {
+                    if (vl == 0 && base > 0) pre = op.load_rest(r0 + rl);
+                    if (Op::SELF && vl == 0) op.put_self(pre, dl0 >= 0 ? xs[dl0 + rl] : __ldg(op.gsrc() + r0 + rl));
+                    const int k1 = rps[rl + 1];
+                    for (int kb = rps[rl] + vl; kb < k1; kb += UNR * VEC) {
+#pragma unroll
+                        for (int u = 0; u < UNR; ++u) {
+                            const int k = kb + u * VEC;
+                            if (k < k1) sum += vals[k - vsb] * (TM)xs[cis[k - cs]];
+                        }
+                    }
+                }
+                if (VEC > 1) sum = group_sum<VEC>(sum);
+                if (vl == 0 && rl < rows) op.finish(r0 + rl, sum, pre, acc);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+        }
+    }
+    if (!ok) {
+        atomicExch(err, 1);
+        for (int k = 0; k < STAGES; ++k) mbar_try_wait(&full[k], 0);
+    }
+    op.template reduce<NT>(acc);
 }
 
 }  // namespace stream
