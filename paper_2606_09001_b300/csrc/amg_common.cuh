@@ -213,6 +213,15 @@ struct Hierarchy {
 // Small device helpers
 // ---------------------------------------------------------------------------
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor drains; pdl_wait() blocks
+// until the predecessor grid has completed and its writes are visible (a
+// no-op for kernels launched without the attribute), pdl_trigger() lets this
+// kernel's own successor begin launching.  Every solve-phase kernel calls
+// pdl_wait() before it reads anything a predecessor may have written.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -23,6 +23,25 @@ static int grid_rows(int n, int vec, int cap) {
     return std::max(1, std::min((n + rpb - 1) / rpb, cap));
 }
 
+// Launches a solve-phase kernel with programmatic stream serialization, so
+// that it starts while its predecessor drains (each such kernel waits on the
+// dependency before reading what the predecessor wrote; see pdl_wait()).
+template <typename... KArgs, typename... Args>
+static int launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+    return AMG_OK;
+}
+
 #define VEC_DISPATCH(vec, ...)                          \
     switch (vec) {                                      \
         case 2: { constexpr int V = 2; __VA_ARGS__; } break;   \
@@ -115,6 +134,8 @@ template <int VEC, typename TB, typename TM>
 __global__ void __launch_bounds__(BLOCK) k_presmooth(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                      const TM *__restrict__ v, const TM *__restrict__ w,
                                                      const TB *__restrict__ b, TM *__restrict__ r, const int *done) {
+    pdl_wait();
+    pdl_trigger();
     if (*done) return;
     ROW_LOOP(VEC, n)
     TM s = 0;
@@ -135,6 +156,8 @@ template <int VEC, typename TX, typename TM, typename TY>
 __global__ void __launch_bounds__(BLOCK) k_spmv(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                 const TM *__restrict__ v, const TX *__restrict__ x,
                                                 TY *__restrict__ y, const int *done) {
+    pdl_wait();
+    pdl_trigger();
     if (*done) return;
     ROW_LOOP(VEC, n)
     TM s = 0;
@@ -153,6 +176,8 @@ __global__ void __launch_bounds__(BLOCK) k_prolong(int n, const int *__restrict_
                                                    const TM *__restrict__ v, const TM *__restrict__ w,
                                                    const TB *__restrict__ b, const TM *__restrict__ xc,
                                                    TM *__restrict__ t, const int *done) {
+    pdl_wait();
+    pdl_trigger();
     if (*done) return;
     ROW_LOOP(VEC, n)
     TM s = 0;
@@ -191,6 +216,8 @@ __global__ void __launch_bounds__(BLOCK) k_postsmooth(int n, const int *__restri
                                                       const TB *__restrict__ b, const TM *__restrict__ t,
                                                       TO *__restrict__ out, const double *__restrict__ rold,
                                                       DevScalars *sc, double *part, int cap, unsigned *counter) {
+    pdl_wait();
+    pdl_trigger();
     if (sc->done) return;
     double acc[2] = {0.0, 0.0};
     ROW_LOOP(VEC, n)
@@ -222,6 +249,8 @@ template <typename TI, typename TO, int FIN>
 __global__ void __launch_bounds__(BLOCK) k_coarse(int m, const double *__restrict__ cinv, const TI *__restrict__ b,
                                                   TO *__restrict__ x, const double *__restrict__ rold,
                                                   DevScalars *sc, double *part, int cap, unsigned *counter) {
+    pdl_wait();
+    pdl_trigger();
     if (sc->done) return;
     __shared__ double sb[AMG_DENSE_MAX];
     for (int i = threadIdx.x; i < m; i += BLOCK) sb[i] = (double)b[i];
@@ -252,6 +281,8 @@ constexpr int DENSE_MAX_LD = 2048;
 template <typename TMAT, typename TV>
 __global__ void __launch_bounds__(BLOCK) k_dense_apply(int m, int ld, const TMAT *__restrict__ M,
                                                        const TV *__restrict__ b, TV *__restrict__ x, const int *done) {
+    pdl_wait();
+    pdl_trigger();
     if (*done) return;
     __shared__ __align__(16) TMAT sb[DENSE_MAX_LD];
     for (int j = threadIdx.x; j < ld; j += BLOCK) sb[j] = j < m ? (TMAT)b[j] : (TMAT)0;
@@ -297,6 +328,8 @@ __global__ void __launch_bounds__(BLOCK) k_dense_apply(int m, int ld, const TMAT
 __global__ void __launch_bounds__(BLOCK) k_pcg_init(int n, const double *__restrict__ b, double *x, double *r,
                                                     double *p, double *rold, DevScalars *sc, double rtol,
                                                     double *part, int cap, unsigned *counter) {
+    pdl_wait();
+    pdl_trigger();
     double acc[1] = {0.0};
     for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
         const double bi = b[i];
@@ -323,6 +356,8 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(int n, const double *__restr
 
 // p = z + beta p
 __global__ void __launch_bounds__(BLOCK) k_pcg_p(int n, const double *__restrict__ z, double *p, const DevScalars *sc) {
+    pdl_wait();
+    pdl_trigger();
     if (sc->done) return;
     const double beta = sc->beta;
     if (beta == 0.0) {  // first step after a (re)start: p = z exactly
@@ -367,6 +402,8 @@ __global__ void __launch_bounds__(BLOCK) k_spmv_fin(int n, const int *__restrict
                                                     const double *__restrict__ v, const double *__restrict__ x,
                                                     double *__restrict__ y, const double *__restrict__ dvec,
                                                     DevScalars *sc, double *part, int cap, unsigned *counter) {
+    pdl_wait();
+    pdl_trigger();
     if (SF != SF_TRUE_RES && sc->done) return;
     double acc[2] = {0.0, 0.0};
     ROW_LOOP(VEC, n)
@@ -397,6 +434,8 @@ __global__ void __launch_bounds__(BLOCK) k_spmv_fin(int n, const int *__restrict
 __global__ void __launch_bounds__(BLOCK) k_pcg_update(int n, double *x, double *r, const double *__restrict__ p,
                                                       const double *__restrict__ q, double *rold, DevScalars *sc,
                                                       double *part, int cap, unsigned *counter) {
+    pdl_wait();
+    pdl_trigger();
     if (sc->done) return;
     const double alpha = sc->alpha;
     double acc[1] = {0.0};
@@ -422,6 +461,8 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(int n, double *x, double *
 __global__ void __launch_bounds__(BLOCK) k_bicg_init(int n, const double *__restrict__ b, double *x, double *r,
                                                      double *rh, double *p, double *v, DevScalars *sc, double rtol,
                                                      double *part, int cap, unsigned *counter) {
+    pdl_wait();
+    pdl_trigger();
     double acc[1] = {0.0};
     for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
         const double bi = b[i];
@@ -453,6 +494,8 @@ __global__ void __launch_bounds__(BLOCK) k_bicg_init(int n, const double *__rest
 __global__ void __launch_bounds__(BLOCK) k_bicg_restart(int n, const double *__restrict__ r, double *rh, double *p,
                                                         double *v, DevScalars *sc, double *part, int cap,
                                                         unsigned *counter) {
+    pdl_wait();
+    pdl_trigger();
     double acc[1] = {0.0};
     for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
         const double ri = r[i];
@@ -478,6 +521,8 @@ __global__ void __launch_bounds__(BLOCK) k_bicg_restart(int n, const double *__r
 // p = r + beta (p - omega v), beta = (rho / rho_old)(alpha / omega); counts the iteration.
 __global__ void __launch_bounds__(BLOCK) k_bicg_p(int n, const double *__restrict__ r, double *p,
                                                   const double *__restrict__ v, DevScalars *sc) {
+    pdl_wait();
+    pdl_trigger();
     if (sc->done) return;
     const double beta = (sc->rho / sc->rho_old) * (sc->alpha / sc->omega);
     const double omega = sc->omega;
@@ -490,6 +535,8 @@ __global__ void __launch_bounds__(BLOCK) k_bicg_p(int n, const double *__restric
 __global__ void __launch_bounds__(BLOCK) k_bicg_s(int n, const double *__restrict__ r, const double *__restrict__ v,
                                                   double *s, double *x, const double *__restrict__ ph,
                                                   DevScalars *sc, double *part, int cap, unsigned *counter) {
+    pdl_wait();
+    pdl_trigger();
     if (sc->done) return;
     const double alpha = sc->alpha;
     double acc[1] = {0.0};
@@ -513,6 +560,8 @@ __global__ void __launch_bounds__(BLOCK) k_bicg_update(int n, double *x, const d
                                                        const double *__restrict__ s, const double *__restrict__ t,
                                                        const double *__restrict__ rh, DevScalars *sc, double *part,
                                                        int cap, unsigned *counter) {
+    pdl_wait();
+    pdl_trigger();
     if (sc->done) return;
     const double omega = sc->omega;
     double acc[2] = {0.0, 0.0};
@@ -535,6 +584,8 @@ __global__ void __launch_bounds__(BLOCK) k_bicg_update(int n, double *x, const d
 }
 
 __global__ void k_copy(int n, const double *__restrict__ a, double *b) {
+    pdl_wait();
+    pdl_trigger();
     for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) b[i] = a[i];
 }
 
@@ -543,6 +594,8 @@ template <int VEC>
 __global__ void __launch_bounds__(BLOCK) k_grad_values(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                        const double *__restrict__ lambda,
                                                        const double *__restrict__ x, double *__restrict__ dA) {
+    pdl_wait();
+    pdl_trigger();
     ROW_LOOP(VEC, n)
     if (valid) {
         const double li = -lambda[i];
@@ -555,6 +608,8 @@ __global__ void __launch_bounds__(BLOCK) k_grad_values(int n, const int *__restr
 // Unpreconditioned CG: z is r itself; beta comes from r.r.
 __global__ void __launch_bounds__(BLOCK) k_cg_beta(int n, const double *__restrict__ r, DevScalars *sc, double *part,
                                                    int cap, unsigned *counter) {
+    pdl_wait();
+    pdl_trigger();
     if (sc->done) return;
     double acc[2] = {0.0, 0.0};
     for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) acc[0] += r[i] * r[i];
@@ -564,6 +619,8 @@ __global__ void __launch_bounds__(BLOCK) k_cg_beta(int n, const double *__restri
 
 // Host-chosen control fields of the device scalars.
 __global__ void k_set_control(DevScalars *sc, int done, int status, int flexible, int max_iter, int reset_iters) {
+    pdl_wait();
+    pdl_trigger();
     sc->done = done;
     sc->status = status;
     sc->flexible = flexible;
@@ -575,7 +632,9 @@ __global__ void k_set_control(DevScalars *sc, int done, int status, int flexible
 }
 
 // The next preconditioner application starts a new recursion (beta = 0, p = z).
-__global__ void k_pcg_restart(DevScalars *sc) { sc->first = 1; }
+__global__ void k_pcg_restart(DevScalars *sc) {
+    pdl_wait();
+    pdl_trigger(); sc->first = 1; }
 
 // ---------------------------------------------------------------------------
 // Tracing
@@ -871,10 +930,10 @@ static int stream_launch_nt(const StreamPlan &pl, int n, const int *rp, const in
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             attr_set = smem;
         }
-        const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 2048)));
+        const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 11 * 1024)));
         const int grid = std::max(1, std::min(pl.ntiles, per_sm * num_sms()));
-        stream::k_stream_win<TM, VEC, Op, NT><<<grid, NT, smem, s>>>(n, pl.rt, pl.cap, pl.xw, pl.ntiles, rp, pl.c16,
-                                                                      v, pl.wtab, op, err);
+        AMG_TRY(launch_k(stream::k_stream_win<TM, VEC, Op, NT>, grid, NT, smem, s, n, pl.rt, pl.cap, pl.xw, pl.ntiles, rp, pl.c16,
+                                                                      v, pl.wtab, op, err));
         AMG_LAUNCH_CHECK();
         return AMG_OK;
         }
@@ -889,7 +948,7 @@ static int stream_launch_nt(const StreamPlan &pl, int n, const int *rp, const in
     // CTAs per SM that fit the SM's 228 KB of shared memory (1 KB reserved per CTA)
     const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 2048)));
     const int grid = std::max(1, std::min(pl.ntiles, per_sm * num_sms()));
-    stream::k_stream<TM, VEC, Op, NT><<<grid, NT, smem, s>>>(n, pl.rt, pl.cap, pl.ntiles, rp, ci, v, op, err);
+    AMG_TRY(launch_k(stream::k_stream<TM, VEC, Op, NT>, grid, NT, smem, s, n, pl.rt, pl.cap, pl.ntiles, rp, ci, v, op, err));
     AMG_LAUNCH_CHECK();
     return AMG_OK;
 }
@@ -1147,7 +1206,9 @@ template <typename TM>
 static bool build_windows(const DevCSR &m, StreamPlan &p, int worst_tile, int gx_bytes, Scratch &scr, cudaStream_t s) {
     p.cap = (worst_tile + 8 + 255) / 256 * 256;
     const stream::WLayout<TM, double> lay(p.rt, p.cap, 0);
-    const int per_cta = (228 * 1024) / 2 - 2048;
+    // two CTAs per SM: 228 KB less 1 KB reserved per CTA and the descriptors'
+    // static shared memory (about 9 KB)
+    const int per_cta = (228 * 1024) / 2 - 1024 - 10 * 1024;
     const int budget = per_cta / stream::WIN_STAGES - lay.stb;
     const int xw_max = std::min(65532, budget / gx_bytes / 4 * 4);
     if (xw_max < 64) return false;
@@ -1586,9 +1647,9 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         const double m = h->nc;
         TRACE("coarse", 0, m * m * 8.0 + 16.0 * m + (fin == FIN_PCG_BETA ? 8.0 * m : 0.0));
         if (fin == FIN_PCG_BETA)
-            k_coarse<double, double, FIN_PCG_BETA><<<1, BLOCK, 0, s>>>(h->nc, h->cinv, b0, z0, rold, W.scal, W.part, cap, W.counter);
+            AMG_TRY(launch_k(k_coarse<double, double, FIN_PCG_BETA>, 1, BLOCK, 0, s, h->nc, h->cinv, b0, z0, rold, W.scal, W.part, cap, W.counter));
         else
-            k_coarse<double, double, FIN_NONE><<<1, BLOCK, 0, s>>>(h->nc, h->cinv, b0, z0, rold, W.scal, W.part, cap, W.counter);
+            AMG_TRY(launch_k(k_coarse<double, double, FIN_NONE>, 1, BLOCK, 0, s, h->nc, h->cinv, b0, z0, rold, W.scal, W.part, cap, W.counter));
         AMG_LAUNCH_CHECK();
         return AMG_OK;
     }
@@ -1614,10 +1675,10 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         } else {
             TRACE("presmooth", l, csr_bytes(lv.A, vb) + n * (bb + 2.0 * vb));
             if (l == 0) {
-                VEC_DISPATCH(lv.vec_a, (k_presmooth<V, double, TM><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                VEC_DISPATCH(lv.vec_a, AMG_TRY(launch_k(k_presmooth<V, double, TM>, grid_rows(n, V, cap), BLOCK, 0, s, 
                                            n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), b0, Tv(lv), done)));
             } else {
-                VEC_DISPATCH(lv.vec_a, (k_presmooth<V, TM, TM><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                VEC_DISPATCH(lv.vec_a, AMG_TRY(launch_k(k_presmooth<V, TM, TM>, grid_rows(n, V, cap), BLOCK, 0, s, 
                                            n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), Bv(lv), Tv(lv), done)));
             }
         }
@@ -1627,7 +1688,7 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
             if (lv.sr.rt)
                 AMG_TRY(stream_launch<TM>(lv.sr, nc, lv.R.rp, lv.R.ci, Av(lv.R), OpSpmv<TM>{done, Tv(lv), Bv(nx)}, err, s));
             else
-                VEC_DISPATCH(lv.vec_r, (k_spmv<V, TM, TM, TM><<<grid_rows(nc, V, cap), BLOCK, 0, s>>>(
+                VEC_DISPATCH(lv.vec_r, AMG_TRY(launch_k(k_spmv<V, TM, TM, TM>, grid_rows(nc, V, cap), BLOCK, 0, s, 
                                            nc, lv.R.rp, lv.R.ci, Av(lv.R), Tv(lv), Bv(nx), done)));
         }
         AMG_LAUNCH_CHECK();
@@ -1642,9 +1703,9 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         TRACE("coarse", L - 1, m * m * (m32 ? 4.0 : 8.0) + 2.0 * vb * m);
         const int grid = std::max(1, std::min((h->nc + BLOCK / 32 - 1) / (BLOCK / 32), 4 * num_sms()));
         if (m32)
-            k_dense_apply<float, TM><<<grid, BLOCK, 0, s>>>(h->nc, h->nc_ld, h->cpad32, Bv(lc), Xv(lc), done);
+            AMG_TRY(launch_k(k_dense_apply<float, TM>, grid, BLOCK, 0, s, h->nc, h->nc_ld, h->cpad32, Bv(lc), Xv(lc), done));
         else
-            k_dense_apply<double, TM><<<grid, BLOCK, 0, s>>>(h->nc, h->nc_ld, h->cpad64, Bv(lc), Xv(lc), done);
+            AMG_TRY(launch_k(k_dense_apply<double, TM>, grid, BLOCK, 0, s, h->nc, h->nc_ld, h->cpad64, Bv(lc), Xv(lc), done));
         AMG_LAUNCH_CHECK();
     }
     // up
@@ -1666,10 +1727,10 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         } else {
             TRACE("prolong", l, csr_bytes(lv.P, vb) + (double)vb * nc + n * (bb + 2.0 * vb));
             if (l == 0) {
-                VEC_DISPATCH(lv.vec_p, (k_prolong<V, double, TM><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                VEC_DISPATCH(lv.vec_p, AMG_TRY(launch_k(k_prolong<V, double, TM>, grid_rows(n, V, cap), BLOCK, 0, s, 
                                            n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), b0, Xv(nx), Tv(lv), done)));
             } else {
-                VEC_DISPATCH(lv.vec_p, (k_prolong<V, TM, TM><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                VEC_DISPATCH(lv.vec_p, AMG_TRY(launch_k(k_prolong<V, TM, TM>, grid_rows(n, V, cap), BLOCK, 0, s, 
                                            n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), Bv(lv), Xv(nx), Tv(lv), done)));
             }
         }
@@ -1695,14 +1756,14 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
                                               err, s));
             } else if (l == 0) {
                 if (fin == FIN_PCG_BETA) {
-                    VEC_DISPATCH(lv.vec_a, (k_postsmooth<V, double, TM, double, FIN_PCG_BETA><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                    VEC_DISPATCH(lv.vec_a, AMG_TRY(launch_k(k_postsmooth<V, double, TM, double, FIN_PCG_BETA>, grid_rows(n, V, cap), BLOCK, 0, s, 
                                                n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), b0, Tv(lv), z0, rold, W.scal, W.part, cap, W.counter)));
                 } else {
-                    VEC_DISPATCH(lv.vec_a, (k_postsmooth<V, double, TM, double, FIN_NONE><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                    VEC_DISPATCH(lv.vec_a, AMG_TRY(launch_k(k_postsmooth<V, double, TM, double, FIN_NONE>, grid_rows(n, V, cap), BLOCK, 0, s, 
                                                n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), b0, Tv(lv), z0, nullptr, W.scal, W.part, cap, W.counter)));
                 }
             } else {
-                VEC_DISPATCH(lv.vec_a, (k_postsmooth<V, TM, TM, TM, FIN_NONE><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+                VEC_DISPATCH(lv.vec_a, AMG_TRY(launch_k(k_postsmooth<V, TM, TM, TM, FIN_NONE>, grid_rows(n, V, cap), BLOCK, 0, s, 
                                            n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), Bv(lv), Tv(lv), Xv(lv), nullptr, W.scal, W.part, cap, W.counter)));
             }
         }
@@ -1730,7 +1791,7 @@ static int spmv_fin(Hierarchy *h, Workspace &W, const char *name, const double *
                                       OpFin<SF>{W.scal, x, y, dvec, W.part, cap, W.counter}, &W.scal->copy_timeout, s));
         return AMG_OK;
     }
-    VEC_DISPATCH(l0.vec_a, (k_spmv_fin<V, SF><<<grid_rows(n, V, cap), BLOCK, 0, s>>>(
+    VEC_DISPATCH(l0.vec_a, AMG_TRY(launch_k(k_spmv_fin<V, SF>, grid_rows(n, V, cap), BLOCK, 0, s, 
                                n, l0.A.rp, l0.A.ci, l0.A.v, x, y, dvec, W.scal, W.part, cap, W.counter)));
     AMG_LAUNCH_CHECK();
     return AMG_OK;
@@ -1743,13 +1804,13 @@ static int pcg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
     AMG_TRY(vcycle(h, W, W.r, W.z, FIN_PCG_BETA, s));
     {
         TRACE("pcg_p", 0, 24.0 * n);
-        k_pcg_p<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.z, W.p, W.scal);
+        AMG_TRY(launch_k(k_pcg_p, stream_grid(n, cap), BLOCK, 0, s, n, W.z, W.p, W.scal));
     }
     AMG_TRY(spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s));
     {
         TRACE("pcg_update", 0, (mixed ? 56.0 : 48.0) * n);
-        k_pcg_update<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.x, W.r, W.p, W.q, mixed ? W.rold : nullptr, W.scal,
-                                                           W.part, cap, W.counter);
+        AMG_TRY(launch_k(k_pcg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, W.r, W.p, W.q, mixed ? W.rold : nullptr, W.scal,
+                                                           W.part, cap, W.counter));
     }
     AMG_LAUNCH_CHECK();
     return AMG_OK;
@@ -1759,16 +1820,16 @@ static int cg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
     const int n = h->n, cap = W.part_cap;
     {
         TRACE("cg_beta", 0, 8.0 * n);
-        k_cg_beta<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.r, W.scal, W.part, cap, W.counter);
+        AMG_TRY(launch_k(k_cg_beta, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.scal, W.part, cap, W.counter));
     }
     {
         TRACE("pcg_p", 0, 24.0 * n);
-        k_pcg_p<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.r, W.p, W.scal);
+        AMG_TRY(launch_k(k_pcg_p, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.p, W.scal));
     }
     AMG_TRY(spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s));
     {
         TRACE("pcg_update", 0, 48.0 * n);
-        k_pcg_update<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.x, W.r, W.p, W.q, nullptr, W.scal, W.part, cap, W.counter);
+        AMG_TRY(launch_k(k_pcg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, W.r, W.p, W.q, nullptr, W.scal, W.part, cap, W.counter));
     }
     AMG_LAUNCH_CHECK();
     return AMG_OK;
@@ -1778,7 +1839,7 @@ static int bicg_iteration(Hierarchy *h, Workspace &W, bool precond, cudaStream_t
     const int n = h->n, cap = W.part_cap;
     {
         TRACE("bicg_p", 0, 32.0 * n);
-        k_bicg_p<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.r, W.p, W.v, W.scal);
+        AMG_TRY(launch_k(k_bicg_p, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.p, W.v, W.scal));
     }
     const double *ph = W.p;
     if (precond) {
@@ -1788,7 +1849,7 @@ static int bicg_iteration(Hierarchy *h, Workspace &W, bool precond, cudaStream_t
     AMG_TRY(spmv_fin<SF_BICG_ALPHA>(h, W, "spmv_rv", ph, W.v, W.rh, s));
     {
         TRACE("bicg_s", 0, 48.0 * n);
-        k_bicg_s<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.r, W.v, W.s, W.x, ph, W.scal, W.part, cap, W.counter);
+        AMG_TRY(launch_k(k_bicg_s, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.v, W.s, W.x, ph, W.scal, W.part, cap, W.counter));
     }
     const double *sh = W.s;
     if (precond) {
@@ -1798,7 +1859,7 @@ static int bicg_iteration(Hierarchy *h, Workspace &W, bool precond, cudaStream_t
     AMG_TRY(spmv_fin<SF_BICG_OMEGA>(h, W, "spmv_ts", sh, W.t, W.s, s));
     {
         TRACE("bicg_update", 0, 64.0 * n);
-        k_bicg_update<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.x, sh, W.r, W.s, W.t, W.rh, W.scal, W.part, cap, W.counter);
+        AMG_TRY(launch_k(k_bicg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, sh, W.r, W.s, W.t, W.rh, W.scal, W.part, cap, W.counter));
     }
     AMG_LAUNCH_CHECK();
     return AMG_OK;
@@ -1859,7 +1920,7 @@ static int true_residual(Hierarchy *h, Workspace &W, cudaStream_t s) {
 
 static int set_control(Workspace &W, cudaStream_t s, int done, int status, int flexible, int max_iter, int reset) {
     TRACE("control", 0, 0.0);
-    k_set_control<<<1, 1, 0, s>>>(W.scal, done, status, flexible, max_iter, reset);
+    AMG_TRY(launch_k(k_set_control, 1, 1, 0, s, W.scal, done, status, flexible, max_iter, reset));
     AMG_LAUNCH_CHECK();
     return AMG_OK;
 }
@@ -1867,7 +1928,7 @@ static int set_control(Workspace &W, cudaStream_t s, int done, int status, int f
 static int bicg_restart(Hierarchy *h, Workspace &W, cudaStream_t s) {
     const int n = h->n, cap = W.part_cap;
     TRACE("bicg_restart", 0, 32.0 * n);
-    k_bicg_restart<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.r, W.rh, W.p, W.v, W.scal, W.part, cap, W.counter);
+    AMG_TRY(launch_k(k_bicg_restart, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.rh, W.p, W.v, W.scal, W.part, cap, W.counter));
     AMG_LAUNCH_CHECK();
     return AMG_OK;
 }
@@ -1883,11 +1944,11 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
     {
         TRACE(bicg ? "bicg_init" : "pcg_init", 0, (bicg ? 48.0 : 40.0) * n);
         if (bicg)
-            k_bicg_init<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.b, W.x, W.r, W.rh, W.p, W.v, W.scal, c.rtol, W.part,
-                                                              cap, W.counter);
+            AMG_TRY(launch_k(k_bicg_init, stream_grid(n, cap), BLOCK, 0, s, n, W.b, W.x, W.r, W.rh, W.p, W.v, W.scal, c.rtol, W.part,
+                                                              cap, W.counter));
         else
-            k_pcg_init<<<stream_grid(n, cap), BLOCK, 0, s>>>(n, W.b, W.x, W.r, W.p, W.rold, W.scal, c.rtol, W.part,
-                                                             cap, W.counter);
+            AMG_TRY(launch_k(k_pcg_init, stream_grid(n, cap), BLOCK, 0, s, n, W.b, W.x, W.r, W.p, W.rold, W.scal, c.rtol, W.part,
+                                                             cap, W.counter));
     }
     AMG_LAUNCH_CHECK();
     AMG_TRY(read_scalars(W, s));
@@ -1947,7 +2008,7 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
         } else {
             AMG_TRY(set_control(W, s, 0, AMG_OK, flexible, c.max_iter, 0));
             TRACE("control", 0, 0.0);
-            k_pcg_restart<<<1, 1, 0, s>>>(W.scal);
+            AMG_TRY(launch_k(k_pcg_restart, 1, 1, 0, s, W.scal));
             AMG_LAUNCH_CHECK();
         }
     }
@@ -1977,7 +2038,7 @@ int grad_values(Hierarchy *h, Workspace &W, const double *lambda, const double *
     const Level &l0 = h->L[0];
     const int n = h->n;
     TRACE("grad_values", 0, csr_bytes(l0.A, 0) + 16.0 * n + 8.0 * l0.A.nnz);
-    VEC_DISPATCH(l0.vec_a, (k_grad_values<V><<<grid_rows(n, V, num_sms() * 8), BLOCK, 0, s>>>(
+    VEC_DISPATCH(l0.vec_a, AMG_TRY(launch_k(k_grad_values<V>, grid_rows(n, V, num_sms() * 8), BLOCK, 0, s, 
                                n, l0.A.rp, l0.A.ci, lambda, x, dA)));
     AMG_LAUNCH_CHECK();
     return AMG_OK;

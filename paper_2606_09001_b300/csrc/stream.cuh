@@ -31,6 +31,10 @@ constexpr int THREADS = 512;  // the default CTA width
 constexpr int MAX_STAGES = 3;
 constexpr int RT_MAX = 1024;
 constexpr int CAP = 4096;  // stage capacity in stored entries
+// Tile descriptors (entry range, window table row) of a CTA's first META_T
+// tiles are loaded into shared memory at launch, in one round trip by all
+// threads, so the producer never waits on a global load before a refill.
+constexpr int META_T = 64;
 
 // Pipeline depth per value type and CTA width: 3 stages of 4-byte values or
 // 2 of 8-byte values keep two 512-thread CTAs resident per SM (about 104 KB
@@ -61,6 +65,10 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+// Adds to the current phase's expected transaction bytes without arriving.
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
@@ -100,7 +108,6 @@ __global__ void __launch_bounds__(NT, 2) k_stream(int n, int rt, int cap, int nt
     constexpr int STAGES = stages<TM, NT>();
     constexpr int CONSUMER_WARPS = NT / 32 - 1;
     __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES];
-    if (op.done()) return;
     const Layout<TM> L(rt, cap);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -111,47 +118,69 @@ __global__ void __launch_bounds__(NT, 2) k_stream(int n, int rt, int cap, int nt
         fence_mbar_init();
     }
     __syncthreads();
+    __shared__ int2 m_se[META_T];
+    const int my_tiles = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    for (int j = tid; j < min(my_tiles, META_T); j += NT) {
+        const int t = blockIdx.x + j * gridDim.x;
+        m_se[j] = make_int2(__ldg(rp + t * rt), __ldg(rp + min(t * rt + rt, n)));
+    }
+    __syncthreads();
+    // Issues tile t (the CTA's j-th) into stage st: the expected bytes are
+    // added without arriving when `pre` (the first tiles, copied before the
+    // dependency wait: the operator is constant), else with the producer's
+    // arrival.
+    auto issue = [&](int t, int j, int st, bool pre) {
+        unsigned char *stage = smem + st * L.stb;
+        const int r0 = t * rt, r1 = min(r0 + rt, n);
+        const int2 se = j < META_T ? m_se[j] : make_int2(__ldg(rp + r0), __ldg(rp + r1));
+        const int s = se.x, e = se.y;
+        const int rp_cnt = (r1 - r0 + 1 + 3) & ~3;  // r0 is a multiple of 4
+        const int cs = s & ~3, ce = (e + 3) & ~3;
+        constexpr int PER = 16 / sizeof(TM);
+        const int vs = s & ~(PER - 1), ve = (e + PER - 1) & ~(PER - 1);
+        int *hdr = reinterpret_cast<int *>(stage + L.rpb + L.cib + L.vab);
+        hdr[0] = cs;
+        hdr[1] = vs;
+        const uint32_t b_rp = rp_cnt * 4, b_ci = (ce - cs) * 4, b_v = (ve - vs) * (uint32_t)sizeof(TM);
+        if (pre) mbar_expect_tx_only(&full[st], b_rp + b_ci + b_v);
+        else mbar_expect_tx(&full[st], b_rp + b_ci + b_v);
+        bulk_g2s(stage, rp + r0, b_rp, &full[st]);
+        if (b_ci) bulk_g2s(stage + L.rpb, ci + cs, b_ci, &full[st]);
+        if (b_v) bulk_g2s(stage + L.rpb + L.cib, v + vs, b_v, &full[st]);
+    };
+    int npre = 0;
+    if (tid == 0)
+        for (; npre < STAGES && (int)blockIdx.x + npre * (int)gridDim.x < ntiles; ++npre)
+            issue(blockIdx.x + npre * gridDim.x, npre, npre, true);
+    pdl_wait();
+    pdl_trigger();
+    if (op.done()) {
+        // the prefetched copies land before the CTA leaves
+        if (tid == 0)
+            for (int k = 0; k < npre; ++k) {
+                mbar_arrive(&full[k]);
+                mbar_wait(&full[k], 0);
+            }
+        return;
+    }
     double acc[2] = {0.0, 0.0};
     bool ok = true;
     if (warp == 0) {
         if (lane == 0) {
-            int s = 0, e = 0;
-            if ((int)blockIdx.x < ntiles) {
-                s = __ldg(rp + blockIdx.x * rt);
-                e = __ldg(rp + min((int)blockIdx.x * rt + rt, n));
-            }
             for (int j = 0;; ++j) {
                 const int t = blockIdx.x + j * gridDim.x;
                 if (t >= ntiles) break;
                 const int st = j % STAGES;
-                // bounds of the following tile, loaded while this one is issued
-                const int tn = t + gridDim.x;
-                int ns = 0, ne = 0;
-                if (tn < ntiles) {
-                    ns = __ldg(rp + tn * rt);
-                    ne = __ldg(rp + min(tn * rt + rt, n));
+                if (j < npre) {
+                    mbar_arrive(&full[st]);  // copies already issued
+                    continue;
                 }
-                if (j >= STAGES && !mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1))) {
+                if (!mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1))) {
                     ok = false;
                     break;
                 }
-                unsigned char *stage = smem + st * L.stb;
-                const int r0 = t * rt, r1 = min(r0 + rt, n);
-                const int rp_cnt = (r1 - r0 + 1 + 3) & ~3;  // r0 is a multiple of 4
-                const int cs = s & ~3, ce = (e + 3) & ~3;
-                constexpr int PER = 16 / sizeof(TM);
-                const int vs = s & ~(PER - 1), ve = (e + PER - 1) & ~(PER - 1);
-                int *hdr = reinterpret_cast<int *>(stage + L.rpb + L.cib + L.vab);
-                hdr[0] = cs;
-                hdr[1] = vs;
-                const uint32_t b_rp = rp_cnt * 4, b_ci = (ce - cs) * 4, b_v = (ve - vs) * (uint32_t)sizeof(TM);
-                if (j >= STAGES) fence_proxy_async();
-                mbar_expect_tx(&full[st], b_rp + b_ci + b_v);
-                bulk_g2s(stage, rp + r0, b_rp, &full[st]);
-                if (b_ci) bulk_g2s(stage + L.rpb, ci + cs, b_ci, &full[st]);
-                if (b_v) bulk_g2s(stage + L.rpb + L.cib, v + vs, b_v, &full[st]);
-                s = ns;
-                e = ne;
+                fence_proxy_async();
+                issue(t, j, st, false);
             }
         }
     } else {
@@ -264,7 +293,6 @@ __global__ void __launch_bounds__(NT, 2) k_stream_win(int n, int rt, int cap, in
     constexpr int STAGES = WIN_STAGES;
     constexpr int CONSUMER_WARPS = NT / 32 - 1;
     __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES];
-    if (op.done()) return;
     const WLayout<TM, GX> L(rt, cap, xw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -275,69 +303,114 @@ __global__ void __launch_bounds__(NT, 2) k_stream_win(int n, int rt, int cap, in
         fence_mbar_init();
     }
     __syncthreads();
+    __shared__ int2 m_se[META_T];
+    __shared__ int4 m_w[META_T][WIN_NW / 2];
+    const int my_tiles = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    {
+        constexpr int PARTS = 1 + WIN_NW / 2;
+        for (int q = tid; q < min(my_tiles, META_T) * PARTS; q += NT) {
+            const int j = q / PARTS, part = q % PARTS;
+            const int t = blockIdx.x + j * gridDim.x;
+            if (part == 0) m_se[j] = make_int2(__ldg(rp + t * rt), __ldg(rp + min(t * rt + rt, n)));
+            else m_w[j][part - 1] = __ldg(reinterpret_cast<const int4 *>(wtab) + (size_t)t * (WIN_NW / 2) + part - 1);
+        }
+    }
+    __syncthreads();
+    // The operator part of tile t (the CTA's j-th: row pointers, local
+    // indices, values), its bytes expected without arriving: constant data,
+    // so the first tiles' are copied before the dependency wait.
+    auto issue_op = [&](int t, int j, int st) {
+        unsigned char *stage = smem + st * L.stb;
+        const int r0 = t * rt, r1 = min(r0 + rt, n);
+        const int2 se = j < META_T ? m_se[j] : make_int2(__ldg(rp + r0), __ldg(rp + r1));
+        const int s = se.x, e = se.y;
+        const int rp_cnt = (r1 - r0 + 1 + 3) & ~3;  // r0 is a multiple of 4
+        const int cs = s & ~7, ce = (e + 7) & ~7;
+        constexpr int PER = 16 / sizeof(TM);
+        const int vs = s & ~(PER - 1), ve = (e + PER - 1) & ~(PER - 1);
+        int *hdr = reinterpret_cast<int *>(stage + L.rpb + L.cib + L.vab + L.xwb);
+        hdr[0] = cs;
+        hdr[1] = vs;
+        const uint32_t b_rp = rp_cnt * 4, b_ci = (ce - cs) * 2, b_v = (ve - vs) * (uint32_t)sizeof(TM);
+        mbar_expect_tx_only(&full[st], b_rp + b_ci + b_v);
+        bulk_g2s(stage, rp + r0, b_rp, &full[st]);
+        if (b_ci) bulk_g2s(stage + L.rpb, c16 + cs, b_ci, &full[st]);
+        if (b_v) bulk_g2s(stage + L.rpb + L.cib, v + vs, b_v, &full[st]);
+    };
+    // The windows of the gathered vector for tile t (written by the
+    // predecessor: after the dependency wait), expected with the producer's
+    // arrival.
+    auto issue_win = [&](int t, int j, int st) {
+        unsigned char *stage = smem + st * L.stb;
+        const int r0 = t * rt, r1 = min(r0 + rt, n);
+        const int4 *wrow = reinterpret_cast<const int4 *>(wtab) + (size_t)t * (WIN_NW / 2);
+        int4 wq[WIN_NW / 2];
+#pragma unroll
+        for (int q = 0; q < WIN_NW / 2; ++q) wq[q] = j < META_T ? m_w[j][q] : __ldg(wrow + q);
+        // offset of column r0 in the windows when one window holds columns r0 .. r1-1
+        int dl0 = -1;
+        {
+            int woff = 0;
+#pragma unroll
+            for (int q = 0; q < WIN_NW / 2; ++q) {
+                if (dl0 < 0 && wq[q].y > 0 && r0 >= wq[q].x && r1 <= wq[q].x + wq[q].y) dl0 = woff + r0 - wq[q].x;
+                woff += wq[q].y;
+                if (dl0 < 0 && wq[q].w > 0 && r0 >= wq[q].z && r1 <= wq[q].z + wq[q].w) dl0 = woff + r0 - wq[q].z;
+                woff += wq[q].w;
+            }
+        }
+        reinterpret_cast<int *>(stage + L.rpb + L.cib + L.vab + L.xwb)[2] = dl0;
+        uint32_t b_x = 0;
+#pragma unroll
+        for (int q = 0; q < WIN_NW / 2; ++q) b_x += (uint32_t)(wq[q].y + wq[q].w) * (uint32_t)sizeof(GX);
+        mbar_expect_tx(&full[st], b_x);
+        const GX *gx = op.gsrc();
+        unsigned char *xs = stage + L.rpb + L.cib + L.vab;
+        uint32_t off = 0;
+#pragma unroll
+        for (int q = 0; q < WIN_NW / 2; ++q) {
+            if (wq[q].y > 0) {
+                bulk_g2s(xs + off, gx + wq[q].x, (uint32_t)wq[q].y * (uint32_t)sizeof(GX), &full[st]);
+                off += (uint32_t)wq[q].y * (uint32_t)sizeof(GX);
+            }
+            if (wq[q].w > 0) {
+                bulk_g2s(xs + off, gx + wq[q].z, (uint32_t)wq[q].w * (uint32_t)sizeof(GX), &full[st]);
+                off += (uint32_t)wq[q].w * (uint32_t)sizeof(GX);
+            }
+        }
+    };
+    int npre = 0;
+    if (tid == 0)
+        for (; npre < STAGES && (int)blockIdx.x + npre * (int)gridDim.x < ntiles; ++npre)
+            issue_op(blockIdx.x + npre * gridDim.x, npre, npre);
+    pdl_wait();
+    pdl_trigger();
+    if (op.done()) {
+        // the prefetched copies land before the CTA leaves
+        if (tid == 0)
+            for (int k = 0; k < npre; ++k) {
+                mbar_arrive(&full[k]);
+                mbar_wait(&full[k], 0);
+            }
+        return;
+    }
     double acc[2] = {0.0, 0.0};
     bool ok = true;
     if (warp == 0) {
         if (lane == 0) {
-            const GX *gx = op.gsrc();
             for (int j = 0;; ++j) {
                 const int t = blockIdx.x + j * gridDim.x;
                 if (t >= ntiles) break;
                 const int st = j % STAGES;
-                const int r0 = t * rt, r1 = min(r0 + rt, n);
-                const int s = __ldg(rp + r0), e = __ldg(rp + r1);
-                // window table row: WIN_NW (start, length) pairs
-                const int4 *wrow = reinterpret_cast<const int4 *>(wtab) + (size_t)t * (WIN_NW / 2);
-                int4 wq[WIN_NW / 2];
-#pragma unroll
-                for (int q = 0; q < WIN_NW / 2; ++q) wq[q] = __ldg(wrow + q);
-                if (j >= STAGES && !mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1))) {
-                    ok = false;
-                    break;
-                }
-                unsigned char *stage = smem + st * L.stb;
-                const int rp_cnt = (r1 - r0 + 1 + 3) & ~3;  // r0 is a multiple of 4
-                const int cs = s & ~7, ce = (e + 7) & ~7;
-                constexpr int PER = 16 / sizeof(TM);
-                const int vs = s & ~(PER - 1), ve = (e + PER - 1) & ~(PER - 1);
-                int *hdr = reinterpret_cast<int *>(stage + L.rpb + L.cib + L.vab + L.xwb);
-                hdr[0] = cs;
-                hdr[1] = vs;
-                // offset of column r0 in the windows when one window holds columns r0 .. r1-1
-                int dl0 = -1;
-                {
-                    int woff = 0;
-#pragma unroll
-                    for (int q = 0; q < WIN_NW / 2; ++q) {
-                        if (dl0 < 0 && wq[q].y > 0 && r0 >= wq[q].x && r1 <= wq[q].x + wq[q].y) dl0 = woff + r0 - wq[q].x;
-                        woff += wq[q].y;
-                        if (dl0 < 0 && wq[q].w > 0 && r0 >= wq[q].z && r1 <= wq[q].z + wq[q].w) dl0 = woff + r0 - wq[q].z;
-                        woff += wq[q].w;
+                if (j >= npre) {
+                    if (!mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1))) {
+                        ok = false;
+                        break;
                     }
+                    fence_proxy_async();
+                    issue_op(t, j, st);
                 }
-                hdr[2] = dl0;
-                const uint32_t b_rp = rp_cnt * 4, b_ci = (ce - cs) * 2, b_v = (ve - vs) * (uint32_t)sizeof(TM);
-                uint32_t b_x = 0;
-#pragma unroll
-                for (int q = 0; q < WIN_NW / 2; ++q) b_x += (uint32_t)(wq[q].y + wq[q].w) * (uint32_t)sizeof(GX);
-                if (j >= STAGES) fence_proxy_async();
-                mbar_expect_tx(&full[st], b_rp + b_ci + b_v + b_x);
-                bulk_g2s(stage, rp + r0, b_rp, &full[st]);
-                if (b_ci) bulk_g2s(stage + L.rpb, c16 + cs, b_ci, &full[st]);
-                if (b_v) bulk_g2s(stage + L.rpb + L.cib, v + vs, b_v, &full[st]);
-                unsigned char *xs = stage + L.rpb + L.cib + L.vab;
-                uint32_t off = 0;
-#pragma unroll
-                for (int q = 0; q < WIN_NW / 2; ++q) {
-                    if (wq[q].y > 0) {
-                        bulk_g2s(xs + off, gx + wq[q].x, (uint32_t)wq[q].y * (uint32_t)sizeof(GX), &full[st]);
-                        off += (uint32_t)wq[q].y * (uint32_t)sizeof(GX);
-                    }
-                    if (wq[q].w > 0) {
-                        bulk_g2s(xs + off, gx + wq[q].z, (uint32_t)wq[q].w * (uint32_t)sizeof(GX), &full[st]);
-                        off += (uint32_t)wq[q].w * (uint32_t)sizeof(GX);
-                    }
-                }
+                issue_win(t, j, st);
             }
         }
     } else {

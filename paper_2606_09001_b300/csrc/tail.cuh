@@ -185,6 +185,8 @@ __global__ void __launch_bounds__(THREADS) k_tail(const __grid_constant__ TArgs<
     __shared__ __align__(8) uint64_t bar;
     __shared__ double red[2][THREADS / 32];
     cg::cluster_group cluster = cg::this_cluster();
+    pdl_wait();
+    pdl_trigger();
     if (sc->done) return;  // uniform: read before any barrier by every thread
     const int c = (int)cluster.block_rank();
     const int nl = a.nlev;
