@@ -37,6 +37,8 @@ struct BDev {
     double *part = nullptr;       // [chunk][K][2]
     // outer vectors [n][K], FP64
     double *B = nullptr, *X = nullptr, *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr, *Rold = nullptr;
+    // FP32 copy of R for the mixed V-cycle's finest level (null in the FP64 form)
+    float *R32 = nullptr;
     // per pair (system * K + rhs)
     double *bn2 = nullptr, *tol2 = nullptr, *rz = nullptr, *alpha = nullptr, *beta = nullptr, *rr = nullptr,
            *tr = nullptr;
@@ -254,6 +256,7 @@ __global__ void __launch_bounds__(BT) kb_spmv0(BDev W, const int *rp, const int 
         if (TRUE_RES) {
             const double ri = W.B[e] - spmm_row<double, double>(rp, ci, av, W.X, i, r);
             W.R[e] = ri;
+            if (W.R32) W.R32[e] = (float)ri;
             acc[0] += ri * ri;
         } else {
             const double q = spmm_row<double, double>(rp, ci, av, W.P, i, r);
@@ -290,6 +293,7 @@ __global__ void __launch_bounds__(BT) kb_update(BDev W, int max_iter, int flexib
             if (flexible) W.Rold[e] = ri;
             const double rn = ri - alpha * W.Q[e];
             W.R[e] = rn;
+            if (W.R32) W.R32[e] = (float)rn;
             acc[0] += rn * rn;
         }
     }
@@ -316,6 +320,7 @@ __global__ void __launch_bounds__(BT) kb_init(BDev W, double rtol) {
         const double bi = W.B[e];
         W.X[e] = 0.0;
         W.R[e] = bi;
+        if (W.R32) W.R32[e] = (float)bi;
         W.P[e] = 0.0;
         W.Rold[e] = 0.0;
         W.Z[e] = 0.0;
@@ -392,6 +397,7 @@ static int workspace_build(Hierarchy *h, BatchWorkspace &W) {
     const size_t nk = (size_t)n * K;
     double **vecs[] = {&d.B, &d.X, &d.R, &d.Z, &d.P, &d.Q, &d.Rold};
     for (double **v : vecs) AMG_TRY(a.alloc(v, nk));
+    if (h->cfg.precision == AMG_PRECISION_MIXED) AMG_TRY(a.alloc(&d.R32, nk));
     double **pv[] = {&d.bn2, &d.tol2, &d.rz, &d.alpha, &d.beta, &d.rr, &d.tr};
     for (double **v : pv) AMG_TRY(a.alloc(v, (size_t)d.npairs));
     int **pi[] = {&d.act, &d.first, &d.iters, &d.status};
@@ -471,9 +477,11 @@ static int batch_vcycle(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cudaStr
         const Level &lv = h->L[l];
         const int n = lv.A.nrows, nc = lv.R.nrows;
         {
-            ProfScope ps(&prof, s, "b_presmooth", l,
-                         lv.A.nnz * (4.0 + vb) + (double)n * K * (l == 0 ? 8.0 + vb : 2.0 * vb));
-            if (l == 0)
+            // the input is vb bytes wide on every level (the finest: FP64 R, or its FP32 copy in the mixed form)
+            ProfScope ps(&prof, s, "b_presmooth", l, lv.A.nnz * (4.0 + vb) + (double)n * K * 2.0 * vb);
+            if (l == 0 && mixed)  // the FP32 copy of R: no conversion per gathered entry
+                kb_presmooth<float, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Ah(lv), d.R32, T(0), na);
+            else if (l == 0)
                 kb_presmooth<double, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Ah(lv), d.R, T(0), na);
             else
                 kb_presmooth<TM, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Ah(lv), Bv(l), T(l), na);
@@ -491,7 +499,10 @@ static int batch_vcycle(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cudaStr
         const int n = lv.A.nrows, nc = lv.P.ncols;
         {
             ProfScope ps(&prof, s, "b_prolong", l, lv.P.nnz * (4.0 + vb) + (double)n * vb + (double)(2 * n + nc) * K * vb);
-            if (l == 0)
+            if (l == 0 && mixed)
+                kb_prolong<float, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), d.R32, Xv(1),
+                                                                  T(0), na);
+            else if (l == 0)
                 kb_prolong<double, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), d.R, Xv(1),
                                                                    T(0), na);
             else

@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(BLOCK) k_dense_apply(int m, int ld, const TMAT
 
 // PCG start: x = 0, r = b, p = 0, ||b||^2.
 __global__ void __launch_bounds__(BLOCK) k_pcg_init(int n, const double *__restrict__ b, double *x, double *r,
-                                                    double *p, double *rold, DevScalars *sc, double rtol,
+                                                    double *p, double *rold, float *r32, DevScalars *sc, double rtol,
                                                     double *part, int cap, unsigned *counter) {
     pdl_wait();
     pdl_trigger();
@@ -335,6 +335,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(int n, const double *__restr
         const double bi = b[i];
         x[i] = 0.0;
         r[i] = bi;
+        if (r32) r32[i] = (float)bi;
         p[i] = 0.0;
         if (rold) rold[i] = 0.0;
         acc[0] += bi * bi;
@@ -400,8 +401,9 @@ __device__ void finish_spmv(DevScalars *sc, const double (&tot)[2]) {
 template <int VEC, int SF>
 __global__ void __launch_bounds__(BLOCK) k_spmv_fin(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                     const double *__restrict__ v, const double *__restrict__ x,
-                                                    double *__restrict__ y, const double *__restrict__ dvec,
-                                                    DevScalars *sc, double *part, int cap, unsigned *counter) {
+                                                    double *__restrict__ y, float *__restrict__ y32,
+                                                    const double *__restrict__ dvec, DevScalars *sc, double *part,
+                                                    int cap, unsigned *counter) {
     pdl_wait();
     pdl_trigger();
     if (SF != SF_TRUE_RES && sc->done) return;
@@ -417,6 +419,7 @@ __global__ void __launch_bounds__(BLOCK) k_spmv_fin(int n, const int *__restrict
         if (SF == SF_TRUE_RES) {
             const double ri = dvec[i] - s;
             y[i] = ri;
+            if (y32) y32[i] = (float)ri;
             acc[0] += ri * ri;
         } else {
             y[i] = s;
@@ -432,8 +435,8 @@ __global__ void __launch_bounds__(BLOCK) k_spmv_fin(int n, const int *__restrict
 
 // x += alpha p; (r_old = r;) r -= alpha q; ||r||^2; convergence / iteration cap.
 __global__ void __launch_bounds__(BLOCK) k_pcg_update(int n, double *x, double *r, const double *__restrict__ p,
-                                                      const double *__restrict__ q, double *rold, DevScalars *sc,
-                                                      double *part, int cap, unsigned *counter) {
+                                                      const double *__restrict__ q, double *rold, float *r32,
+                                                      DevScalars *sc, double *part, int cap, unsigned *counter) {
     pdl_wait();
     pdl_trigger();
     if (sc->done) return;
@@ -445,6 +448,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(int n, double *x, double *
         if (rold) rold[i] = ri;
         const double rn = ri - alpha * q[i];
         r[i] = rn;
+        if (r32) r32[i] = (float)rn;
         acc[0] += rn * rn;
     }
     double tot[1];
@@ -714,6 +718,7 @@ int workspace_init(Workspace &W, int n) {
     DevArena &a = W.arena;
     double **vecs[] = {&W.b, &W.x, &W.r, &W.z, &W.p, &W.q, &W.rold, &W.rh, &W.v, &W.ph, &W.s, &W.sh, &W.t, &W.aux};
     for (double **pp : vecs) AMG_TRY(a.alloc(pp, (size_t)n));
+    AMG_TRY(a.alloc(&W.r32, (size_t)n));
     AMG_TRY(a.alloc(&W.scal, 1));
     W.part_cap = num_sms() * 8;
     AMG_TRY(a.alloc(&W.part, (size_t)3 * W.part_cap));
@@ -882,6 +887,7 @@ struct OpFin {
     double *part;
     int cap;
     unsigned *counter;
+    float *y32;  // true residual: FP32 copy of y (may be null)
     struct Pre {
         double d;
     };
@@ -899,6 +905,7 @@ struct OpFin {
         if (SF == SF_TRUE_RES) {
             const double ri = p.d - s;
             y[i] = ri;
+            if (y32) y32[i] = (float)ri;
             acc[0] += ri * ri;
         } else {
             y[i] = s;
@@ -1327,11 +1334,16 @@ int autotune_plans(Hierarchy *h, DevScalars *sc, cudaStream_t s) {
     for (int l = 0; l < h->nsolve - 1; ++l) {
         Level &lv = h->L[l];
         if (mixed) {
-            // level 0's pre-smoothing gathers the FP64 Krylov vector, its
-            // post-smoothing the FP32 iterate: two plans tuned apart
+            // level 0's pre-smoothing gathers the Krylov vector (FP64, or its
+            // FP32 copy in PCG), its post-smoothing the FP32 iterate: two plans
+            // tuned apart
             if (l == 0) {
                 lv.sa_post = lv.sa;
-                AMG_TRY((tune_plan<float, double>(lv.A, lv.A.v32, lv.sa, h->arena, sc, s)));
+                // PCG gathers the FP32 copy of r; BiCGStab's preconditioned vectors are FP64
+                if (h->cfg.solver == AMG_SOLVER_BICGSTAB)
+                    AMG_TRY((tune_plan<float, double>(lv.A, lv.A.v32, lv.sa, h->arena, sc, s)));
+                else
+                    AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa, h->arena, sc, s)));
                 AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa_post, h->arena, sc, s)));
             } else {
                 AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa, h->arena, sc, s)));
@@ -1630,7 +1642,8 @@ static double tail_bytes(const Hierarchy *h, int vb) {
 
 // One V-cycle: z0 = M^-1 b0.  TM = float for the mixed form.
 template <typename TM>
-static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z0, int fin, cudaStream_t s) {
+static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z0, int fin, cudaStream_t s,
+                         const float *b032) {
     const int L = h->nsolve;
     const int cap = W.part_cap;
     const int *done = &W.scal->done;
@@ -1663,18 +1676,25 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         Level &lv = h->L[l];
         Level &nx = h->L[l + 1];
         const int n = lv.A.nrows;
-        const double bb = l == 0 ? 8.0 : vb;
+        const double bb = l == 0 ? (b032 ? 4.0 : 8.0) : vb;  // the finest input: FP32 copy or FP64
         int *err = &W.scal->copy_timeout;
         if (lv.sa.rt) {
             TRACE("presmooth", l, csr_bytes(lv.A, vb) + n * (bb + vb));
             const TM *ah = (const TM *)(mixed ? (const void *)lv.ahat32 : (const void *)lv.ahat);
-            if (l == 0)
+            if (l == 0 && b032 && mixed)
+                AMG_TRY(stream_launch<TM>(lv.sa, n, lv.A.rp, lv.A.ci, ah,
+                                          OpPre<float, TM>{done, reinterpret_cast<const float *>(b032), Tv(lv)}, err, s));
+            else if (l == 0)
                 AMG_TRY(stream_launch<TM>(lv.sa, n, lv.A.rp, lv.A.ci, ah, OpPre<double, TM>{done, b0, Tv(lv)}, err, s));
             else
                 AMG_TRY(stream_launch<TM>(lv.sa, n, lv.A.rp, lv.A.ci, ah, OpPre<TM, TM>{done, Bv(lv), Tv(lv)}, err, s));
         } else {
             TRACE("presmooth", l, csr_bytes(lv.A, vb) + n * (bb + 2.0 * vb));
-            if (l == 0) {
+            if (l == 0 && b032 && mixed) {
+                VEC_DISPATCH(lv.vec_a, AMG_TRY(launch_k(k_presmooth<V, TM, TM>, grid_rows(n, V, cap), BLOCK, 0, s, n,
+                                           lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), reinterpret_cast<const TM *>(b032),
+                                           Tv(lv), done)));
+            } else if (l == 0) {
                 VEC_DISPATCH(lv.vec_a, AMG_TRY(launch_k(k_presmooth<V, double, TM>, grid_rows(n, V, cap), BLOCK, 0, s, 
                                            n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), b0, Tv(lv), done)));
             } else {
@@ -1715,10 +1735,15 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         const int n = lv.A.nrows;
         const int nc = nx.A.nrows;
         const double bb = l == 0 ? 8.0 : vb;
+        const double bbp = l == 0 && b032 ? 4.0 : bb;  // prolongation reads the FP32 copy when given
         int *err = &W.scal->copy_timeout;
         if (lv.sp.rt) {
-            TRACE("prolong", l, csr_bytes(lv.P, vb) + (double)vb * nc + n * (bb + 2.0 * vb));
-            if (l == 0)
+            TRACE("prolong", l, csr_bytes(lv.P, vb) + (double)vb * nc + n * (bbp + 2.0 * vb));
+            if (l == 0 && b032 && mixed)
+                AMG_TRY(stream_launch<TM>(lv.sp, n, lv.P.rp, lv.P.ci, Av(lv.P),
+                                          OpProlong<float, TM>{done, Wv(lv), reinterpret_cast<const float *>(b032), Xv(nx),
+                                                               Tv(lv)}, err, s));
+            else if (l == 0)
                 AMG_TRY(stream_launch<TM>(lv.sp, n, lv.P.rp, lv.P.ci, Av(lv.P),
                                           OpProlong<double, TM>{done, Wv(lv), b0, Xv(nx), Tv(lv)}, err, s));
             else
@@ -1772,9 +1797,12 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
     return AMG_OK;
 }
 
-static int vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z0, int fin, cudaStream_t s) {
-    if (h->cfg.precision == AMG_PRECISION_MIXED) return launch_vcycle<float>(h, W, b0, z0, fin, s);
-    return launch_vcycle<double>(h, W, b0, z0, fin, s);
+// b032: an FP32 copy of b0 (mixed form, may be null), read by the finest
+// level's pre-smoothing and prolongation in place of converting b0.
+static int vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z0, int fin, cudaStream_t s,
+                  const float *b032 = nullptr) {
+    if (h->cfg.precision == AMG_PRECISION_MIXED) return launch_vcycle<float>(h, W, b0, z0, fin, s, b032);
+    return launch_vcycle<double>(h, W, b0, z0, fin, s, nullptr);
 }
 
 static int stream_grid(int n, int cap) { return std::max(1, std::min((n + BLOCK - 1) / BLOCK, cap)); }
@@ -1782,17 +1810,17 @@ static int stream_grid(int n, int cap) { return std::max(1, std::min((n + BLOCK 
 // q = A x with a finisher (the outer, FP64 operator).
 template <int SF>
 static int spmv_fin(Hierarchy *h, Workspace &W, const char *name, const double *x, double *y, const double *dvec,
-                    cudaStream_t s) {
+                    cudaStream_t s, float *y32 = nullptr) {
     const int n = h->n, cap = W.part_cap;
     const Level &l0 = h->L[0];
     TRACE(name, 0, csr_bytes(l0.A, 8) + 16.0 * n + (SF == SF_PCG_ALPHA ? 0.0 : 8.0 * n));
     if (l0.sa64.rt) {
         AMG_TRY(stream_launch<double>(l0.sa64, n, l0.A.rp, l0.A.ci, l0.A.v,
-                                      OpFin<SF>{W.scal, x, y, dvec, W.part, cap, W.counter}, &W.scal->copy_timeout, s));
+                                      OpFin<SF>{W.scal, x, y, dvec, W.part, cap, W.counter, y32}, &W.scal->copy_timeout, s));
         return AMG_OK;
     }
     VEC_DISPATCH(l0.vec_a, AMG_TRY(launch_k(k_spmv_fin<V, SF>, grid_rows(n, V, cap), BLOCK, 0, s, 
-                               n, l0.A.rp, l0.A.ci, l0.A.v, x, y, dvec, W.scal, W.part, cap, W.counter)));
+                               n, l0.A.rp, l0.A.ci, l0.A.v, x, y, y32, dvec, W.scal, W.part, cap, W.counter)));
     AMG_LAUNCH_CHECK();
     return AMG_OK;
 }
@@ -1801,7 +1829,7 @@ static int spmv_fin(Hierarchy *h, Workspace &W, const char *name, const double *
 static int pcg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
     const int n = h->n, cap = W.part_cap;
     const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
-    AMG_TRY(vcycle(h, W, W.r, W.z, FIN_PCG_BETA, s));
+    AMG_TRY(vcycle(h, W, W.r, W.z, FIN_PCG_BETA, s, mixed ? W.r32 : nullptr));
     {
         TRACE("pcg_p", 0, 24.0 * n);
         AMG_TRY(launch_k(k_pcg_p, stream_grid(n, cap), BLOCK, 0, s, n, W.z, W.p, W.scal));
@@ -1809,7 +1837,8 @@ static int pcg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
     AMG_TRY(spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s));
     {
         TRACE("pcg_update", 0, (mixed ? 56.0 : 48.0) * n);
-        AMG_TRY(launch_k(k_pcg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, W.r, W.p, W.q, mixed ? W.rold : nullptr, W.scal,
+        AMG_TRY(launch_k(k_pcg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, W.r, W.p, W.q, mixed ? W.rold : nullptr,
+                         mixed ? W.r32 : nullptr, W.scal,
                                                            W.part, cap, W.counter));
     }
     AMG_LAUNCH_CHECK();
@@ -1829,7 +1858,8 @@ static int cg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
     AMG_TRY(spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s));
     {
         TRACE("pcg_update", 0, 48.0 * n);
-        AMG_TRY(launch_k(k_pcg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, W.r, W.p, W.q, nullptr, W.scal, W.part, cap, W.counter));
+        AMG_TRY(launch_k(k_pcg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, W.r, W.p, W.q, nullptr, nullptr, W.scal,
+                         W.part, cap, W.counter));
     }
     AMG_LAUNCH_CHECK();
     return AMG_OK;
@@ -1914,7 +1944,8 @@ static int read_scalars(Workspace &W, cudaStream_t s) {
 
 // r = b - A x and ||r||^2 into scal->tr; the host reads the scalars.
 static int true_residual(Hierarchy *h, Workspace &W, cudaStream_t s) {
-    AMG_TRY(spmv_fin<SF_TRUE_RES>(h, W, "true_residual", W.x, W.r, W.b, s));
+    AMG_TRY(spmv_fin<SF_TRUE_RES>(h, W, "true_residual", W.x, W.r, W.b, s,
+                                  h->cfg.precision == AMG_PRECISION_MIXED ? W.r32 : nullptr));
     return read_scalars(W, s);
 }
 
@@ -1947,7 +1978,8 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
             AMG_TRY(launch_k(k_bicg_init, stream_grid(n, cap), BLOCK, 0, s, n, W.b, W.x, W.r, W.rh, W.p, W.v, W.scal, c.rtol, W.part,
                                                               cap, W.counter));
         else
-            AMG_TRY(launch_k(k_pcg_init, stream_grid(n, cap), BLOCK, 0, s, n, W.b, W.x, W.r, W.p, W.rold, W.scal, c.rtol, W.part,
+            AMG_TRY(launch_k(k_pcg_init, stream_grid(n, cap), BLOCK, 0, s, n, W.b, W.x, W.r, W.p, W.rold,
+                             c.precision == AMG_PRECISION_MIXED ? W.r32 : nullptr, W.scal, c.rtol, W.part,
                                                              cap, W.counter));
     }
     AMG_LAUNCH_CHECK();

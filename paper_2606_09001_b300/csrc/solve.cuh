@@ -50,6 +50,7 @@ struct Workspace {
     double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *rold = nullptr;
     double *rh = nullptr, *v = nullptr, *ph = nullptr, *s = nullptr, *sh = nullptr, *t = nullptr;
     double *aux = nullptr;                                 // adjoint: forward solution x
+    float *r32 = nullptr;                                  // mixed PCG: FP32 copy of r (the V-cycle's input)
     DevScalars *scal = nullptr;                            // device
     DevScalars *scal_h = nullptr;                          // pinned host mirror
     double *part = nullptr;                                // per-block partial sums (3 x part_cap)
