@@ -524,20 +524,23 @@ __global__ void __launch_bounds__(BLOCK) k_bicg_restart(int n, const double *__r
 
 // p = r + beta (p - omega v), beta = (rho / rho_old)(alpha / omega); counts the iteration.
 __global__ void __launch_bounds__(BLOCK) k_bicg_p(int n, const double *__restrict__ r, double *p,
-                                                  const double *__restrict__ v, DevScalars *sc) {
+                                                  const double *__restrict__ v, float *p32, DevScalars *sc) {
     pdl_wait();
     pdl_trigger();
     if (sc->done) return;
     const double beta = (sc->rho / sc->rho_old) * (sc->alpha / sc->omega);
     const double omega = sc->omega;
-    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK)
-        p[i] = r[i] + beta * (p[i] - omega * v[i]);
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+        const double pi = r[i] + beta * (p[i] - omega * v[i]);
+        p[i] = pi;
+        if (p32) p32[i] = (float)pi;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) sc->iters += 1;
 }
 
 // s = r - alpha v; x += alpha p^; ||s||^2 (early exit when small).
 __global__ void __launch_bounds__(BLOCK) k_bicg_s(int n, const double *__restrict__ r, const double *__restrict__ v,
-                                                  double *s, double *x, const double *__restrict__ ph,
+                                                  double *s, float *s32, double *x, const double *__restrict__ ph,
                                                   DevScalars *sc, double *part, int cap, unsigned *counter) {
     pdl_wait();
     pdl_trigger();
@@ -547,6 +550,7 @@ __global__ void __launch_bounds__(BLOCK) k_bicg_s(int n, const double *__restric
     for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
         const double si = r[i] - alpha * v[i];
         s[i] = si;
+        if (s32) s32[i] = (float)si;
         x[i] += alpha * ph[i];
         acc[0] += si * si;
     }
@@ -1334,16 +1338,12 @@ int autotune_plans(Hierarchy *h, DevScalars *sc, cudaStream_t s) {
     for (int l = 0; l < h->nsolve - 1; ++l) {
         Level &lv = h->L[l];
         if (mixed) {
-            // level 0's pre-smoothing gathers the Krylov vector (FP64, or its
-            // FP32 copy in PCG), its post-smoothing the FP32 iterate: two plans
-            // tuned apart
+            // level 0's pre-smoothing gathers the FP32 copy of the Krylov
+            // vector, its post-smoothing the FP32 iterate: two plans tuned apart
             if (l == 0) {
                 lv.sa_post = lv.sa;
-                // PCG gathers the FP32 copy of r; BiCGStab's preconditioned vectors are FP64
-                if (h->cfg.solver == AMG_SOLVER_BICGSTAB)
-                    AMG_TRY((tune_plan<float, double>(lv.A, lv.A.v32, lv.sa, h->arena, sc, s)));
-                else
-                    AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa, h->arena, sc, s)));
+                // the Krylov solvers hand the V-cycle FP32 copies of its input
+                AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa, h->arena, sc, s)));
                 AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa_post, h->arena, sc, s)));
             } else {
                 AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa, h->arena, sc, s)));
@@ -1867,23 +1867,26 @@ static int cg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
 
 static int bicg_iteration(Hierarchy *h, Workspace &W, bool precond, cudaStream_t s) {
     const int n = h->n, cap = W.part_cap;
+    // the mixed V-cycle reads FP32 copies of p and s (one buffer, used in turn)
+    float *v32 = precond && h->cfg.precision == AMG_PRECISION_MIXED ? W.r32 : nullptr;
     {
-        TRACE("bicg_p", 0, 32.0 * n);
-        AMG_TRY(launch_k(k_bicg_p, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.p, W.v, W.scal));
+        TRACE("bicg_p", 0, (v32 ? 36.0 : 32.0) * n);
+        AMG_TRY(launch_k(k_bicg_p, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.p, W.v, v32, W.scal));
     }
     const double *ph = W.p;
     if (precond) {
-        AMG_TRY(vcycle(h, W, W.p, W.ph, FIN_NONE, s));
+        AMG_TRY(vcycle(h, W, W.p, W.ph, FIN_NONE, s, v32));
         ph = W.ph;
     }
     AMG_TRY(spmv_fin<SF_BICG_ALPHA>(h, W, "spmv_rv", ph, W.v, W.rh, s));
     {
         TRACE("bicg_s", 0, 48.0 * n);
-        AMG_TRY(launch_k(k_bicg_s, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.v, W.s, W.x, ph, W.scal, W.part, cap, W.counter));
+        AMG_TRY(launch_k(k_bicg_s, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.v, W.s, v32, W.x, ph, W.scal, W.part, cap,
+                         W.counter));
     }
     const double *sh = W.s;
     if (precond) {
-        AMG_TRY(vcycle(h, W, W.s, W.sh, FIN_NONE, s));
+        AMG_TRY(vcycle(h, W, W.s, W.sh, FIN_NONE, s, v32));
         sh = W.sh;
     }
     AMG_TRY(spmv_fin<SF_BICG_OMEGA>(h, W, "spmv_ts", sh, W.t, W.s, s));
