@@ -83,6 +83,8 @@ def lib():
             L.or_setup.argtypes = [C.POINTER(_Config), C.c_int, C.c_longlong, _i32p, _i32p, _f64p,
                                    C.POINTER(C.c_int)]
             L.or_setup.restype = C.c_void_p
+            L.or_resetup.argtypes = [C.c_void_p, _f64p, C.POINTER(C.c_int)]
+            L.or_resetup.restype = C.c_void_p
             L.or_hier_free.argtypes = [C.c_void_p]
             L.or_hier_nlevels.argtypes = [C.c_void_p]
             L.or_hier_symmetric.argtypes = [C.c_void_p]
@@ -213,6 +215,22 @@ class Hierarchy:
             raise OracleError(self.status)
         self._h = C.c_void_p(h)
         self.n = A.n
+
+    def resetup(self, values) -> "Hierarchy":
+        """A new hierarchy for the same pattern with new values, keeping this
+        one's aggregates (hence every sparsity pattern) and recomputing every
+        value: the numeric re-setup of the cached-setup path (Sec. 2.1)."""
+        st = C.c_int()
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        h = lib().or_resetup(self._h, v, C.byref(st))
+        if not h:
+            raise OracleError(st.value)
+        out = Hierarchy.__new__(Hierarchy)
+        out._cfg = self._cfg
+        out._h = C.c_void_p(h)
+        out.status = st.value
+        out.n = self.n
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

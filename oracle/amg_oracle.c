@@ -747,6 +747,50 @@ or_hier *or_setup(const or_config *cfg_in, int n, long long nnz, const int *rp, 
     return h;
 }
 
+/* Numeric re-setup (Sec. 2.1, C++/CUDA backend: on a cache hit the setup is
+ * repeated against new coefficients while the structure of the first setup
+ * is kept).  Reading: the aggregates of every level and hence every sparsity
+ * pattern (P, R, the coarse operators) are those of `old`; the smoother
+ * weights, omega_P, P, R, the Galerkin products and the coarsest factor are
+ * recomputed from the new values v (same pattern as old's finest operator),
+ * by the same formulas as or_setup.  The symmetry flag is kept. */
+or_hier *or_resetup(const or_hier *old, const double *v, int *status) {
+    const ocsr *A0 = &old->A[0];
+    or_hier *h = (or_hier *)calloc(1, sizeof(or_hier));
+    if (!h) { *status = OR_ERR_OOM; return NULL; }
+    h->cfg = old->cfg;
+    int st;
+    if (csr_copy(&h->A[0], A0->nrows, A0->nnz, A0->rp, A0->ci, v)) { *status = OR_ERR_OOM; or_hier_free(h); return NULL; }
+    if ((st = or_validate(A0->nrows, A0->nnz, A0->rp, A0->ci, v))) { *status = st; or_hier_free(h); return NULL; }
+    h->symmetric = old->symmetric;
+    const int L = old->nlevels;
+    for (int l = 0; l < L; ++l) {
+        ocsr *A = &h->A[l];
+        h->dinv[l] = smoother_weights(A, &h->cfg);
+        if (l == L - 1) break;
+        const int n = A->nrows, nc = old->A[l + 1].nrows;
+        h->agg[l] = (int *)malloc((size_t)n * sizeof(int));
+        if (!h->agg[l]) { *status = OR_ERR_OOM; or_hier_free(h); return NULL; }
+        memcpy(h->agg[l], old->agg[l], (size_t)n * sizeof(int));
+        if ((st = prolongator(A, h->agg[l], nc, &h->P[l], &h->rho[l]))) { *status = st; or_hier_free(h); return NULL; }
+        if ((st = csr_transpose(&h->P[l], &h->R[l]))) { *status = st; or_hier_free(h); return NULL; }
+        if ((st = galerkin(A, &h->P[l], &h->R[l], &h->A[l + 1]))) { *status = st; or_hier_free(h); return NULL; }
+    }
+    h->nlevels = L;
+    ocsr *Ac = &h->A[L - 1];
+    const int m = Ac->nrows;
+    h->nc = m;
+    h->dense = (double *)calloc((size_t)m * m, sizeof(double));
+    h->piv = (int *)malloc((size_t)m * sizeof(int));
+    if (!h->dense || !h->piv) { *status = OR_ERR_OOM; or_hier_free(h); return NULL; }
+    for (int i = 0; i < m; ++i)
+        for (int k = Ac->rp[i]; k < Ac->rp[i + 1]; ++k) h->dense[i * m + Ac->ci[k]] = Ac->v[k];
+    st = h->symmetric ? dense_cholesky(h->dense, m) : dense_lu(h->dense, h->piv, m);
+    if (st) { *status = st; or_hier_free(h); return NULL; }
+    *status = OR_OK;
+    return h;
+}
+
 void or_hier_free(or_hier *h) {
     if (!h) return;
     for (int l = 0; l < OR_MAX_LEVELS; ++l) {

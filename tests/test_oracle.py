@@ -510,3 +510,74 @@ def test_symmetric_detection():
     v = A.values.copy()
     v[1] = np.nextafter(v[1], 0)  # break bitwise symmetry of one pair
     assert not O.Hierarchy(M.CSR(A.row_ptr, A.col_idx, v)).symmetric
+
+
+# --------------------------------------------------------------------------
+# Numeric re-setup with the hierarchy's structure kept (Sec. 2.1 caching)
+# --------------------------------------------------------------------------
+
+def _same_hierarchy(h1, h2):
+    assert h1.nlevels == h2.nlevels
+    for l in range(h1.nlevels):
+        a, b = h1.level(l), h2.level(l)
+        for m1, m2 in [(a.A, b.A)] + ([(a.P, b.P), (a.R, b.R)] if l < h1.nlevels - 1 else []):
+            assert np.array_equal(m1.row_ptr, m2.row_ptr) and np.array_equal(m1.col_idx, m2.col_idx)
+            assert np.array_equal(m1.values.view(np.int64), m2.values.view(np.int64))
+        if l < h1.nlevels - 1:
+            assert np.array_equal(a.agg, b.agg)
+
+
+@pytest.mark.parametrize("maker", [lambda: M.poisson2d(20), lambda: M.diffusion3d_grf(N=10).A,
+                                   lambda: M.convection_diffusion_upwind(8)])
+def test_resetup_same_values_is_setup(maker):
+    A = maker()
+    h = O.Hierarchy(A, {"coarse_max": 16})
+    _same_hierarchy(h, h.resetup(A.values))
+
+
+@pytest.mark.parametrize("maker", [lambda: M.poisson2d(20), lambda: M.diffusion3d_grf(N=10).A])
+def test_resetup_doubled_values(maker):
+    """Doubling every value is exact: D^-1 A and the strength test are unchanged,
+    so P and the aggregates stay, every coarse operator doubles exactly, and the
+    result equals a fresh setup of 2A."""
+    A = maker()
+    h = O.Hierarchy(A, {"coarse_max": 16})
+    A2 = M.CSR(A.row_ptr, A.col_idx, 2.0 * A.values)
+    hr = h.resetup(A2.values)
+    _same_hierarchy(hr, O.Hierarchy(A2, {"coarse_max": 16}))
+    for l in range(h.nlevels):
+        assert np.array_equal(hr.level(l).A.values, 2.0 * h.level(l).A.values)
+        if l < h.nlevels - 1:
+            assert np.array_equal(hr.level(l).P.values, h.level(l).P.values)
+
+
+def test_resetup_new_coefficients_keeps_structure_and_is_galerkin():
+    """New log-conductivities: the aggregates and patterns are the old ones, the
+    values follow the prolongator and Galerkin definitions (dense check), and
+    the cycle still preconditions PCG to the tolerance."""
+    rng = np.random.default_rng(7)
+    A = M.diffusion_fv(np.exp(rng.normal(size=(18, 18))))
+    Anew = M.diffusion_fv(np.exp(rng.normal(size=(18, 18))))
+    assert np.array_equal(A.col_idx, Anew.col_idx)
+    h = O.Hierarchy(A, {"coarse_max": 8})
+    hr = h.resetup(Anew.values)
+    assert hr.nlevels == h.nlevels >= 3
+    for l in range(h.nlevels - 1):
+        lv, nx_ = hr.level(l), hr.level(l + 1)
+        assert np.array_equal(lv.agg, h.level(l).agg)
+        assert np.array_equal(lv.P.col_idx, h.level(l).P.col_idx)
+        n, nc = lv.A.n, nx_.A.n
+        Ad = lvl_sp(lv.A, n).toarray()
+        T = np.zeros((n, nc))
+        T[np.arange(n), lv.agg] = 1.0
+        d = np.diag(Ad)
+        rho = np.max(np.abs(Ad).sum(1) / np.abs(d))
+        Pd = (np.eye(n) - (4.0 / 3.0) / rho * (Ad / d[:, None])) @ T
+        P = lvl_sp(lv.P, nc).toarray()
+        assert np.allclose(P, Pd, rtol=0, atol=1e-14)
+        Ac_dense = P.T @ Ad @ P
+        assert np.abs(lvl_sp(nx_.A, nc).toarray() - Ac_dense).max() <= 1e-13 * np.abs(Ac_dense).max()
+    b = rng.uniform(-1, 1, A.n)
+    x, info = hr.solve(b)
+    assert info.status == 0
+    assert np.linalg.norm(to_sp(Anew) @ x - b) <= 1e-8 * np.linalg.norm(b) * 1.0001
