@@ -122,6 +122,21 @@ int amg_config_default(amg_config *cfg);
 int amg_setup(const amg_config *cfg, int n, long long nnz, const int *row_ptr, const int *col_idx,
               const double *values, void *cuda_stream, amg_handle *out);
 
+/* Numeric re-setup for new values on the same sparsity pattern (Sec. 2.1:
+ * on a cache hit the setup is repeated against the new coefficients while
+ * the structure of the first setup is reused).  values: nnz entries in the
+ * order of the col_idx given to amg_setup (host or device).  Every level
+ * keeps its aggregates, so P, R and every coarse operator keep their
+ * patterns; the smoother weights, the prolongator's omega, P, R = P^T, the
+ * Galerkin products, the coarsest factor and all FP32 copies are recomputed
+ * from the new values, much faster than a new setup.  A cached hierarchy of
+ * A^T (nonsymmetric adjoint) is re-set up too.  Synchronises the stream.
+ * Errors: AMG_ERR_ZERO_DIAG, AMG_NOT_SPD (coarsest level), AMG_ERR_ARG (NULL
+ * argument, or new values that change the detected symmetry),
+ * AMG_ERR_UNSUPPORTED (batched handles), AMG_ERR_CUDA; after an error the
+ * handle's values are partly updated and the handle must be freed. */
+int amg_resetup(amg_handle h, const double *values, void *cuda_stream);
+
 /* Solves A x = b from x0 = 0 with the handle's solver; b and x have n entries.
  * info may be NULL.  Returns AMG_OK or a soft/hard status (see above). */
 int amg_solve(amg_handle h, const double *b, double *x, void *cuda_stream, amg_info *info);

@@ -23,7 +23,7 @@ SMOOTHERS = {"JACOBI": 0, "L1_JACOBI": 1}
 PRECISIONS = {"FP64": 0, "MIXED": 1}
 
 # Every symbol the header declares.
-EXPORTS = ("amg_config_default", "amg_setup", "amg_solve", "amg_adjoint", "amg_vcycle", "amg_get_info",
+EXPORTS = ("amg_config_default", "amg_setup", "amg_resetup", "amg_solve", "amg_adjoint", "amg_vcycle", "amg_get_info",
            "amg_get_level", "amg_get_aggregates", "amg_profile", "amg_profile_summary", "amg_profile_record",
            "amg_setup_batched", "amg_solve_batched", "amg_batch_level", "amg_cg_solve_noalloc", "amg_free", "amg_status_string", "amg_last_error")
 
@@ -59,6 +59,7 @@ def load() -> C.CDLL:
         vp, i, ll, d = C.c_void_p, C.c_int, C.c_longlong, C.c_double
         L.amg_config_default.argtypes = [C.POINTER(AmgConfig)]
         L.amg_setup.argtypes = [C.POINTER(AmgConfig), i, ll, vp, vp, vp, vp, C.POINTER(vp)]
+        L.amg_resetup.argtypes = [vp, vp, vp]
         L.amg_solve.argtypes = [vp, vp, vp, vp, C.POINTER(AmgInfo)]
         L.amg_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, C.POINTER(AmgInfo)]
         L.amg_vcycle.argtypes = [vp, vp, vp, vp]

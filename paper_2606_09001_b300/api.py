@@ -128,6 +128,7 @@ class Solver:
             raise AMGError(rc, "amg_setup")
         self._h = h
         self._L = L
+        self.generation = 0  # counts re-setups (values the handle currently holds)
 
     # -- lifetime --
     def close(self):
@@ -146,6 +147,20 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+    def resetup(self, values, stream: int | None = None):
+        """Numeric re-setup for new values on the same pattern: the hierarchy's
+        structure (aggregates, every sparsity pattern) is kept and every value
+        recomputed (Sec. 2.1's cache hit)."""
+        _check_dtype(values, "f64")
+        if int(values.shape[0]) != self.nnz:
+            raise ValueError(f"expected {self.nnz} values, got {int(values.shape[0])}")
+        s = _stream_of(values) if stream is None else stream
+        rc = self._L.amg_resetup(self._h, _ptr(values), s)
+        if rc != _lib.AMG_OK:
+            self.close()  # a failed re-setup leaves the values partly updated
+            raise AMGError(rc, "amg_resetup")
+        self.generation += 1
 
     # -- solves --
     def solve(self, b, x=None, stream: int | None = None, info: bool = True, check: bool = False):
@@ -332,16 +347,18 @@ def _digest(*arrays) -> str:
 class SetupCache:
     """LRU cache of Solver handles keyed by a hash of the full sparsity
     pattern, the dimensions, the precision and the configuration (the key
-    the paper's backend uses).  A hit whose values differ rebuilds the
-    hierarchy for the new values.  The pattern hash is memoised per tensor
-    (identity and version counter); values are compared exactly against a
-    stored copy on their own device."""
+    the paper's backend uses).  A hit whose values differ re-sets the cached
+    hierarchy up for the new values, keeping its structure (Sec. 2.1); with
+    resetup=False it builds a new hierarchy instead.  The pattern hash is
+    memoised per tensor (identity and version counter); values are compared
+    exactly against a stored copy on their own device."""
 
-    def __init__(self, capacity: int = 8):
+    def __init__(self, capacity: int = 8, resetup: bool = True):
         self.capacity = capacity
+        self.resetup = resetup
         self._d: OrderedDict = OrderedDict()
         self._pattern_memo: dict = {}
-        self.hits = self.misses = 0
+        self.hits = self.misses = self.resetups = 0
 
     def _pattern_digest(self, row_ptr, col_idx) -> str:
         if isinstance(row_ptr, torch.Tensor) and isinstance(col_idx, torch.Tensor):
@@ -375,11 +392,17 @@ class SetupCache:
             self._d.move_to_end(k)
             self.hits += 1
             return ent[0]
+        kept = values.detach().clone() if isinstance(values, torch.Tensor) else np.array(values, copy=True)
+        if ent is not None and self.resetup:
+            ent[0].resetup(values)
+            self._d[k] = (ent[0], kept)
+            self._d.move_to_end(k)
+            self.resetups += 1
+            return ent[0]
         self.misses += 1
         if ent is not None:
             ent[0].close()
         s = Solver(row_ptr, col_idx, values, cfg)
-        kept = values.detach().clone() if isinstance(values, torch.Tensor) else np.array(values, copy=True)
         self._d[k] = (s, kept)
         self._d.move_to_end(k)
         while len(self._d) > self.capacity:

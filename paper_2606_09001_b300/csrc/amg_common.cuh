@@ -187,6 +187,7 @@ struct Hierarchy {
     int nc = 0;
     double *cinv = nullptr;
     float *cinv32 = nullptr;
+    double *cinv_last = nullptr;  // the coarsest level's dense inverse (also when collapsed)
     // copies of the dense operator with rows padded to nc_ld entries (a
     // multiple of 4, zero-filled) for 16-byte vector loads
     int nc_ld = 0;
@@ -242,6 +243,9 @@ int exclusive_scan_int(const int *in, int *out, int n, int *total_host, cudaStre
 int transpose_csr(const DevCSR &a, DevCSR &t, DevArena &arena, cudaStream_t s);
 int build_hierarchy(Hierarchy *h, const int *rp, const int *ci, const double *v, cudaStream_t s);
 int tail_prepare(Hierarchy *h, cudaStream_t s);
+// Numeric re-setup: new values on the same pattern, the structure (aggregates,
+// every sparsity pattern, plans) kept and every value recomputed in place.
+int resetup_hierarchy(Hierarchy *h, const double *values, cudaStream_t s);
 int build_hierarchy_batched(Hierarchy *h, const int *rp, const int *ci, const double *v, const int *sys_off_host,
                             int nsys, cudaStream_t s);
 void free_hierarchy(Hierarchy *h);

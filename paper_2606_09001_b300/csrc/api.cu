@@ -349,6 +349,34 @@ int amg_profile_record(amg_handle h, int i, char *name, int name_len, int *level
     return AMG_OK;
 }
 
+int amg_resetup(amg_handle h, const double *values, void *cuda_stream) {
+    if (!h || !values) return AMG_ERR_ARG;
+    if (h->H.nsys > 0) {
+        set_last_error("amg_resetup: not provided for batched handles");
+        return AMG_ERR_UNSUPPORTED;
+    }
+    AMG_TRY(enter(h, cuda_stream));
+    const auto t0 = clk::now();
+    int rc = resetup_hierarchy(&h->H, values, h->s);
+    if (rc == AMG_OK && h->HT) {
+        // the cached hierarchy of A^T follows: its values are the transpose of the new ones
+        DevArena tmp;
+        DevCSR At;
+        rc = transpose_csr(h->H.L[0].A, At, tmp, h->s);
+        if (rc == AMG_OK) rc = resetup_hierarchy(h->HT, At.v, h->s);
+        const cudaError_t e = cudaStreamSynchronize(h->s);
+        tmp.free_all();
+        if (rc == AMG_OK && e != cudaSuccess) {
+            set_last_error("amg_resetup: %s", cudaGetErrorString(e));
+            rc = AMG_ERR_CUDA;
+        }
+    }
+    if (rc != AMG_OK) return rc;
+    AMG_TRY(leave(h, cuda_stream, true));
+    h->H.setup_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    return AMG_OK;
+}
+
 int amg_setup_batched(const amg_config *cfg, int nsys, const int *sys_off, int n, long long nnz,
                       const int *row_ptr, const int *col_idx, const double *values, void *cuda_stream,
                       amg_handle *out) {

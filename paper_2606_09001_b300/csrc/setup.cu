@@ -1125,6 +1125,7 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
         AMG_TRY(sc.alloc(&piv, (size_t)m));
         AMG_TRY(sc.alloc(&st, 1));
         AMG_TRY(ar.alloc(&h->cinv, (size_t)m * m));
+        h->cinv_last = h->cinv;
         k_csr_to_dense<<<1, 256, 0, s>>>(m, Lc.A.rp, Lc.A.ci, Lc.A.v, dense);
         k_dense_factor_inverse<<<1, 256, 0, s>>>(m, h->symmetric, dense, piv, h->cinv, st);
         AMG_LAUNCH_CHECK();
@@ -1394,8 +1395,8 @@ static int pad_dense(Hierarchy *h, cudaStream_t s) {
     const int ld = (m + 3) / 4 * 4;
     const long long tot = (long long)m * ld;
     h->nc_ld = ld;
-    AMG_TRY(h->arena.alloc(&h->cpad64, (size_t)tot));
-    if (h->cfg.precision == AMG_PRECISION_MIXED) AMG_TRY(h->arena.alloc(&h->cpad32, (size_t)tot));
+    if (!h->cpad64) AMG_TRY(h->arena.alloc(&h->cpad64, (size_t)tot));
+    if (h->cfg.precision == AMG_PRECISION_MIXED && !h->cpad32) AMG_TRY(h->arena.alloc(&h->cpad32, (size_t)tot));
     k_pad_dense<<<grid_ll(tot), 256, 0, s>>>(m, ld, h->cinv, h->cpad64, h->cpad32);
     AMG_LAUNCH_CHECK();
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1411,15 +1412,19 @@ constexpr int COLLAPSE_MAX = 2048;
 
 static int collapse_coarse(Hierarchy *h, cudaStream_t s) {
     const int L = h->nlevels;
-    h->nsolve = L;
+    // a re-setup keeps the collapsed level and writes into the existing buffers
+    const bool again = h->nsolve > 0 && h->nsolve < L;
     int tc = 1;
-    while (tc < L && h->L[tc].A.nrows > COLLAPSE_MAX) ++tc;
+    if (again) tc = h->nsolve - 1;
+    else
+        while (tc < L && h->L[tc].A.nrows > COLLAPSE_MAX) ++tc;
+    h->nsolve = L;
     if (tc >= L - 1) return pad_dense(h, s);
     DevArena &ar = h->arena;
     Scratch sc;
     const int nmax = h->L[tc].A.nrows;
     const size_t sq = (size_t)nmax * nmax;
-    double *E, *Y, *Z, *T, *U, *Mnext = h->cinv, *Mcur = nullptr;
+    double *E, *Y, *Z, *T, *U, *Mnext = h->cinv_last, *Mcur = nullptr;
     AMG_TRY(sc.alloc(&E, sq));
     AMG_TRY(sc.alloc(&Y, sq));
     AMG_TRY(sc.alloc(&Z, sq));
@@ -1429,8 +1434,12 @@ static int collapse_coarse(Hierarchy *h, cudaStream_t s) {
         const Level &lv = h->L[l];
         const int n = lv.A.nrows, m = lv.R.nrows;
         const long long nn = (long long)n * n, mn = (long long)m * n;
-        if (l == tc) AMG_TRY(ar.alloc(&Mcur, (size_t)nn));
-        else AMG_TRY(sc.alloc(&Mcur, (size_t)nn));
+        if (l == tc) {
+            if (again) Mcur = h->cinv;
+            else AMG_TRY(ar.alloc(&Mcur, (size_t)nn));
+        } else {
+            AMG_TRY(sc.alloc(&Mcur, (size_t)nn));
+        }
         AMG_CUDA_TRY(cudaMemsetAsync(E, 0, sizeof(double) * nn, s));
         k_dense_i_minus_aw<<<grid_for(n), 256, 0, s>>>(n, lv.A.rp, lv.A.ci, lv.A.v, lv.w, E);
         k_spmm_dense<<<grid_ll(mn), 256, 0, s>>>(m, n, lv.R.rp, lv.R.ci, lv.R.v, E, Y);   // Y = R (I - A W)
@@ -1446,11 +1455,148 @@ static int collapse_coarse(Hierarchy *h, cudaStream_t s) {
     h->nc = nmax;
     h->cinv = Mcur;
     if (h->cfg.precision == AMG_PRECISION_MIXED) {
-        AMG_TRY(ar.alloc(&h->cinv32, sq));
+        if (!h->cinv32) AMG_TRY(ar.alloc(&h->cinv32, sq));
         k_to_f32_ll<<<grid_ll((long long)sq), 256, 0, s>>>(Mcur, h->cinv32, (long long)sq);
         AMG_LAUNCH_CHECK();
     }
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return pad_dense(h, s);
+}
+
+// Numeric re-setup (Sec. 2.1: on a cache hit the setup is repeated against
+// the new coefficients while the structure of the first setup is reused).
+// Every level keeps its aggregates, so P, R and every coarse operator keep
+// their patterns; the smoother weights, omega_P, P, R (= P^T), the Galerkin
+// products, the coarsest inverse, the collapsed operator and all FP32 copies
+// are recomputed from the new values by the same kernels as the setup, and
+// written into the existing arrays -- every pointer the streaming plans,
+// windows, tail tables and captured graphs hold stays valid.
+int resetup_hierarchy(Hierarchy *h, const double *v_in, cudaStream_t s) {
+    const amg_config &cfg = h->cfg;
+    const int L = h->nlevels;
+    Level &L0 = h->L[0];
+    AMG_CUDA_TRY(cudaMemcpyAsync(L0.A.v, v_in, sizeof(double) * (size_t)L0.A.nnz, cudaMemcpyDefault, s));
+    if (cfg.symmetric < 0) {
+        // the detected symmetry fixes the coarsest factor and the adjoint's hierarchy
+        DevArena tmp;
+        DevCSR At;
+        int rc = transpose_csr(L0.A, At, tmp, s);
+        int *differ = nullptr;
+        if (rc == AMG_OK) rc = tmp.alloc(&differ, 1);
+        if (rc < 0) {
+            tmp.free_all();
+            return rc;
+        }
+        cudaMemsetAsync(differ, 0, sizeof(int), s);
+        k_compare_csr<<<grid_for(L0.A.nnz + L0.A.nrows + 1), 256, 0, s>>>(L0.A.nrows, L0.A.nnz, L0.A.rp, L0.A.ci, L0.A.v,
+                                                                          At.rp, At.ci, At.v, differ);
+        int d = 1;
+        cudaMemcpyAsync(&d, differ, sizeof(int), cudaMemcpyDeviceToHost, s);
+        const cudaError_t e = cudaStreamSynchronize(s);
+        tmp.free_all();
+        AMG_CUDA_TRY(e);
+        if ((d ? 0 : 1) != h->symmetric) {
+            set_last_error("the new values change the matrix's symmetry: set up a new handle");
+            return AMG_ERR_ARG;
+        }
+    }
+    for (int l = 0; l < L; ++l) {
+        Level &Lv = h->L[l];
+        DevCSR &A = Lv.A;
+        const int nl = A.nrows;
+        Scratch sc;
+        double *diag;
+        int *bad;
+        AMG_TRY(sc.alloc(&diag, (size_t)nl));
+        AMG_TRY(sc.alloc(&bad, 1));
+        AMG_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        k_find_diag<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, diag, bad);
+        AMG_LAUNCH_CHECK();
+        int hbad = 0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hbad) {
+            set_last_error("level %d has a zero diagonal", l);
+            return AMG_ERR_ZERO_DIAG;
+        }
+        k_smoother_weights<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.v, diag, cfg.omega,
+                                                        cfg.smoother == AMG_SMOOTHER_L1_JACOBI, Lv.w);
+        AMG_LAUNCH_CHECK();
+        if (l == L - 1) break;
+        const int nc = Lv.R.nrows;
+        unsigned long long *rho_bits;
+        AMG_TRY(sc.alloc(&rho_bits, 1));
+        AMG_CUDA_TRY(cudaMemsetAsync(rho_bits, 0, sizeof(unsigned long long), s));
+        k_gershgorin<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.v, diag, rho_bits);
+        AMG_LAUNCH_CHECK();
+        unsigned long long hb = 0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&hb, rho_bits, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        double rho;
+        memcpy(&rho, &hb, sizeof(rho));
+        Lv.rho = rho;
+        const double c43 = 4.0 / 3.0;
+        ProlongEpi epi{Lv.agg, diag, c43 / rho};
+        int *trp;
+        AMG_TRY(sc.alloc(&trp, (size_t)nl + 1));
+        k_iota<<<grid_for(nl + 1), 256, 0, s>>>(trp, nl + 1);
+        AMG_LAUNCH_CHECK();
+        DevCSR Pn, Rn, AP, Acn;
+        AMG_TRY((spgemm<EPI_PROLONG>(nl, nc, A.rp, A.ci, A.v, trp, Lv.agg, nullptr, epi, Pn, sc.arena, s)));
+        AMG_TRY(transpose_csr(Pn, Rn, sc.arena, s));
+        AMG_TRY((spgemm<EPI_NONE>(nl, nc, A.rp, A.ci, A.v, Pn.rp, Pn.ci, Pn.v, ProlongEpi{}, AP, sc.arena, s)));
+        AMG_TRY((spgemm<EPI_NONE>(nc, nc, Rn.rp, Rn.ci, Rn.v, AP.rp, AP.ci, AP.v, ProlongEpi{}, Acn, sc.arena, s)));
+        DevCSR &An = h->L[l + 1].A;
+        if (Pn.nnz != Lv.P.nnz || Rn.nnz != Lv.R.nnz || Acn.nnz != An.nnz) {
+            set_last_error("re-setup produced a different pattern on level %d", l);
+            return AMG_ERR_CUDA;
+        }
+        AMG_CUDA_TRY(cudaMemcpyAsync(Lv.P.v, Pn.v, sizeof(double) * (size_t)Pn.nnz, cudaMemcpyDeviceToDevice, s));
+        AMG_CUDA_TRY(cudaMemcpyAsync(Lv.R.v, Rn.v, sizeof(double) * (size_t)Rn.nnz, cudaMemcpyDeviceToDevice, s));
+        AMG_CUDA_TRY(cudaMemcpyAsync(An.v, Acn.v, sizeof(double) * (size_t)Acn.nnz, cudaMemcpyDeviceToDevice, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    // coarsest inverse
+    {
+        Level &Lc = h->L[L - 1];
+        Scratch sc;
+        double *dense;
+        int *piv, *st;
+        const int m = Lc.A.nrows;
+        AMG_TRY(sc.alloc(&dense, (size_t)m * m));
+        AMG_TRY(sc.alloc(&piv, (size_t)m));
+        AMG_TRY(sc.alloc(&st, 1));
+        k_csr_to_dense<<<1, 256, 0, s>>>(m, Lc.A.rp, Lc.A.ci, Lc.A.v, dense);
+        k_dense_factor_inverse<<<1, 256, 0, s>>>(m, h->symmetric, dense, piv, h->cinv_last, st);
+        AMG_LAUNCH_CHECK();
+        int hst = -1;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hst != AMG_OK) {
+            set_last_error("coarsest level (%d rows) is not %s", m, h->symmetric ? "SPD" : "invertible");
+            return AMG_NOT_SPD;
+        }
+    }
+    // A W and the FP32 copies
+    const bool mixed = cfg.precision == AMG_PRECISION_MIXED;
+    for (int k = 0; k < L; ++k) {
+        Level &Lv = h->L[k];
+        const int nl = Lv.A.nrows;
+        const bool last = k == L - 1;
+        if (Lv.ahat) k_scale_cols<<<grid_for(nl), 256, 0, s>>>(nl, Lv.A.rp, Lv.A.ci, Lv.A.v, Lv.w, Lv.ahat, Lv.ahat32);
+        if (mixed) {
+            k_to_f32<<<grid_for(Lv.A.nnz), 256, 0, s>>>(Lv.A.v, Lv.A.v32, Lv.A.nnz);
+            k_to_f32<<<grid_for(nl), 256, 0, s>>>(Lv.w, Lv.w32, nl);
+            if (!last) {
+                k_to_f32<<<grid_for(Lv.P.nnz), 256, 0, s>>>(Lv.P.v, Lv.P.v32, Lv.P.nnz);
+                k_to_f32<<<grid_for(Lv.R.nnz), 256, 0, s>>>(Lv.R.v, Lv.R.v32, Lv.R.nnz);
+            }
+        }
+        AMG_LAUNCH_CHECK();
+    }
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    // the collapsed coarse end (in place) and the padded dense copies
+    if (h->nsolve < h->nlevels) return collapse_coarse(h, s);
     return pad_dense(h, s);
 }
 

@@ -98,8 +98,13 @@ def test_setup_cache_reuses_hierarchy_across_backward():
     loss_and_grads(theta, b, xt, A, {"rtol": 1e-10}, cache)
     assert cache.misses == 1 and cache.hits >= 1
     loss_and_grads(theta + 0.1, b, xt, A, {"rtol": 1e-10}, cache)
-    assert cache.misses == 2  # new values: a fresh setup
+    assert cache.misses == 1 and cache.resetups == 1  # new values: numeric re-setup of the cached hierarchy
     cache.clear()
+    fresh = api.SetupCache(resetup=False)
+    loss_and_grads(theta, b, xt, A, {"rtol": 1e-10}, fresh)
+    loss_and_grads(theta + 0.1, b, xt, A, {"rtol": 1e-10}, fresh)
+    assert fresh.misses == 2 and fresh.resetups == 0  # without re-setup: a fresh setup
+    fresh.clear()
 
 
 def test_autograd_nonsymmetric_fd():
