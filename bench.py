@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--forms", default="mixed,fp64", help="comma list of precision forms to time (first = headline)")
     p.add_argument("--no-trace", action="store_true", help="skip the per-kernel traced pass (profiler captures)")
+    p.add_argument("--layout", default="AUTO", choices=["AUTO", "CSR", "WINDOWED", "SLICED_ELL"],
+                   help="tile layout of the streaming kernels (default: autotuned per operator)")
     return p.parse_args()
 
 
@@ -288,6 +290,21 @@ def trace_pass(s, b, x, g, lam, dA, steps, dev, step=None):
     return roofline, kernels, vc_bytes, vc_ms
 
 
+def plan_summary(s) -> dict:
+    """The streaming plans setup chose for the levels that stream:
+    {"L<l>": {op: "<layout>/<rows per tile>x<threads per row>"}}."""
+    out = {}
+    for l in range(s.info().nlevels):
+        ops = {}
+        for op in ("pre", "post", "P", "R") + (("krylov",) if l == 0 else ()):
+            p = s.plan(l, op)
+            if p["layout"]:
+                ops[op] = f'{p["layout"]}/{p["rows_per_tile"]}x{p["threads_per_row"]}'
+        if ops:
+            out[f"L{l}"] = ops
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2606_09001_b300 import api
@@ -324,7 +341,8 @@ def run_ours(args):
     form_list = [f.strip() for f in args.forms.split(",") if f.strip()]
     primary = form_list[0]
     for form in form_list:
-        s = api.Solver(rp, ci, vals, {"solver": solver, "precision": form.upper() if form == "mixed" else "FP64"})
+        s = api.Solver(rp, ci, vals, {"solver": solver, "precision": form.upper() if form == "mixed" else "FP64",
+                                      "layout": args.layout})
         solvers[form] = s
         setup_ms = s.info().setup_ms  # the cold setup (re-setups below overwrite the handle's figure)
 
@@ -385,6 +403,7 @@ def run_ours(args):
         _, _, ainfo = s.adjoint(x, g, lam, dA)
         forms[form] = {"ms_per_step": ms, "solve_iters": sinfo.iters, "adjoint_iters": ainfo.iters,
                        "setup_ms": setup_ms, "resetup_ms": resetup_ms, "resetup_solve_ms": resetup_solve_ms,
+                       "plans": plan_summary(s),
                        "rel_res_true": sinfo.rel_res_true, "adjoint_rel_res_true": ainfo.rel_res_true,
                        "gpu_launches": launches,
                        "launches_per_step": launches / args.steps}
@@ -448,7 +467,7 @@ def run_ours(args):
             "config": {"workload": args.workload, "description": desc, "n": n, "nnz": nnz, "rtol": 1e-8,
                        "solver": solver, "precision": {"mixed": "mixed (FP32 V-cycle, FP64 Krylov)", "fp64": "FP64"}[primary],
                        "levels": info.nlevels, "rows": info.rows, "operator_complexity": info.operator_complexity,
-                       "setup_ms": mixed.get("setup_ms"),
+                       "setup_ms": mixed.get("setup_ms"), "layout": args.layout,
                        "l2": "inputs larger than L2: level-0 operator alone is "
                              f"{nnz * 12 / 1e6:.0f} MB FP64 / {nnz * 8 / 1e6:.0f} MB FP32",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

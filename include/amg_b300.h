@@ -80,6 +80,14 @@ extern "C" {
 #define AMG_PRECISION_MIXED 1 /* FP32 hierarchy values and V-cycle arithmetic inside FP64 Krylov;
                                  FP64 true residual, dot products and coarsest solve */
 
+/* Tile layouts of the streaming kernels that run the large operators (the
+ * level operators A_l, P_l, R_l with at least 16384 rows).  By default the
+ * setup times each operator's candidate layouts and keeps the fastest. */
+#define AMG_LAYOUT_AUTO 0       /* timed trial over all layouts (default) */
+#define AMG_LAYOUT_CSR 1        /* CSR row tiles; the vector gathered from global memory */
+#define AMG_LAYOUT_WINDOWED 2   /* CSR row tiles; windows of the vector staged in shared memory */
+#define AMG_LAYOUT_SLICED_ELL 3 /* 32-row slices stored slot-major, one thread per row; windows staged */
+
 typedef struct amg_handle_s *amg_handle; /* opaque, owned by the library until amg_free */
 
 typedef struct {
@@ -94,6 +102,8 @@ typedef struct {
     int max_restarts; /* restarts from x while the true residual is above rtol; default 3 */
     int precision;    /* AMG_PRECISION_*; default FP64 */
     int symmetric;    /* -1 detect (pattern symmetric and values bitwise equal), 0 no, 1 yes; default -1 */
+    int layout;       /* AMG_LAYOUT_*: restricts the timed trial to one tile layout (an operator that
+                         layout does not fit keeps the CSR layout); default AMG_LAYOUT_AUTO */
 } amg_config;
 
 typedef struct {
@@ -170,6 +180,15 @@ int amg_get_level(amg_handle h, int level, int which, long long *dims, int *row_
 /* Copies the aggregate index of every row of level l (l < nlevels - 1). */
 int amg_get_aggregates(amg_handle h, int level, int *agg);
 
+/* The streaming plan chosen at setup for one operator of level l: which = 0
+ * A_l W (pre-smoothing), 1 P_l (prolongation), 2 R_l (restriction), 3 A_l
+ * (post-smoothing), 4 the FP64 A of the Krylov products (level 0 only).
+ * plan[0] = layout (AMG_LAYOUT_CSR, _WINDOWED or _SLICED_ELL; 0 when the
+ * operator has no streaming plan and runs on the row-vector kernels),
+ * plan[1] = rows per tile, plan[2] = threads per row, plan[3] = tiles.
+ * Errors: AMG_ERR_ARG (NULL, level or which out of range). */
+int amg_get_plan(amg_handle h, int level, int which, int plan[4]);
+
 /* Per-kernel tracing of the solve phase.  The paper reports wall-clock times
  * only; this is the library's own instrumentation.  amg_profile(h, 1) clears
  * the records and brackets every later solve-phase kernel launch of the
@@ -234,6 +253,15 @@ int amg_solve_batched(amg_handle h, int nrhs, const double *B, double *X, int *i
  * its first row on this level (row_off[*nsys_level] = the level's rows) and
  * final[j] 1 if its coarsening ends here (solved densely on this level). */
 int amg_batch_level(amg_handle h, int level, int *nsys_level, int *sys, int *row_off, int *final_flags);
+
+/* The FP64 <-> FP32 conversions of the mixed-precision form, which run on
+ * the integer pipes (a hardware cvt between the two formats issues on the
+ * FP64 pipe): out[i] = in[i] rounded to nearest even (amg_narrow_f64) or
+ * exactly (amg_widen_f32), as IEEE 754 specifies, for i < n.  Device
+ * pointers; stream-ordered on cuda_stream.  Errors: AMG_ERR_ARG (NULL
+ * pointer with n > 0, n < 0), AMG_ERR_CUDA. */
+int amg_narrow_f64(const double *in, float *out, long long n, void *cuda_stream);
+int amg_widen_f32(const float *in, double *out, long long n, void *cuda_stream);
 
 /* Largest system amg_cg_solve_noalloc accepts (rows). */
 #define AMG_NOALLOC_MAX_N (1 << 18)

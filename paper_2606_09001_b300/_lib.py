@@ -21,17 +21,18 @@ AMG_BATCH_MAX_RHS = 8
 SOLVERS = {"PCG": 0, "BICGSTAB": 1, "CG": 2, "BICGSTAB_NOPREC": 3}
 SMOOTHERS = {"JACOBI": 0, "L1_JACOBI": 1}
 PRECISIONS = {"FP64": 0, "MIXED": 1}
+LAYOUTS = {"AUTO": 0, "CSR": 1, "WINDOWED": 2, "SLICED_ELL": 3}
 
 # Every symbol the header declares.
 EXPORTS = ("amg_config_default", "amg_setup", "amg_resetup", "amg_solve", "amg_adjoint", "amg_vcycle", "amg_get_info",
-           "amg_get_level", "amg_get_aggregates", "amg_profile", "amg_profile_summary", "amg_profile_record",
-           "amg_setup_batched", "amg_solve_batched", "amg_batch_level", "amg_cg_solve_noalloc", "amg_free", "amg_status_string", "amg_last_error")
+           "amg_get_level", "amg_get_aggregates", "amg_get_plan", "amg_profile", "amg_profile_summary", "amg_profile_record",
+           "amg_setup_batched", "amg_solve_batched", "amg_batch_level", "amg_cg_solve_noalloc", "amg_narrow_f64", "amg_widen_f32", "amg_free", "amg_status_string", "amg_last_error")
 
 
 class AmgConfig(C.Structure):
     _fields_ = [("solver", C.c_int), ("smoother", C.c_int), ("omega", C.c_double), ("theta", C.c_double),
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int),
-                ("max_restarts", C.c_int), ("precision", C.c_int), ("symmetric", C.c_int)]
+                ("max_restarts", C.c_int), ("precision", C.c_int), ("symmetric", C.c_int), ("layout", C.c_int)]
 
 
 class AmgInfo(C.Structure):
@@ -66,6 +67,9 @@ def load() -> C.CDLL:
         L.amg_get_info.argtypes = [vp, C.POINTER(AmgInfo)]
         L.amg_get_level.argtypes = [vp, i, i, C.POINTER(ll), vp, vp, vp]
         L.amg_get_aggregates.argtypes = [vp, i, vp]
+        L.amg_get_plan.argtypes = [vp, i, i, vp]
+        L.amg_narrow_f64.argtypes = [vp, vp, C.c_longlong, vp]
+        L.amg_widen_f32.argtypes = [vp, vp, C.c_longlong, vp]
         L.amg_profile.argtypes = [vp, i]
         L.amg_profile_summary.argtypes = [vp, C.POINTER(ll), C.POINTER(i)]
         L.amg_profile_record.argtypes = [vp, i, C.c_char_p, i, C.POINTER(i), C.POINTER(ll), C.POINTER(C.c_double),

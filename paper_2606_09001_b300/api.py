@@ -58,7 +58,8 @@ class Info:
 
 def make_config(config: dict | None = None) -> AmgConfig:
     """AMG configuration from a dict; unspecified keys keep the defaults.
-    'solver', 'smoother' and 'precision' accept names (e.g. "PCG", "MIXED")."""
+    'solver', 'smoother', 'precision' and 'layout' accept names (e.g. "PCG",
+    "MIXED", "SLICED_ELL")."""
     c = AmgConfig()
     _lib.load().amg_config_default(C.byref(c))
     for k, v in (config or {}).items():
@@ -68,6 +69,8 @@ def make_config(config: dict | None = None) -> AmgConfig:
             v = _lib.SMOOTHERS[v.upper()]
         elif k == "precision" and isinstance(v, str):
             v = _lib.PRECISIONS[v.upper()]
+        elif k == "layout" and isinstance(v, str):
+            v = _lib.LAYOUTS[v.upper()]
         if not hasattr(c, k):
             raise KeyError(f"unknown config key {k!r}")
         setattr(c, k, v)
@@ -263,6 +266,20 @@ class Solver:
         if rc < 0:
             raise AMGError(rc, "amg_get_aggregates")
         return agg
+
+    PLAN_OPS = {"pre": 0, "P": 1, "R": 2, "post": 3, "krylov": 4}
+    LAYOUT_NAMES = {0: None, 1: "CSR", 2: "WINDOWED", 3: "SLICED_ELL"}
+
+    def plan(self, l: int, op: str) -> dict:
+        """The streaming plan setup chose for one operator of level l (op in
+        PLAN_OPS): layout name (None: row-vector kernels), rows per tile,
+        threads per row, tiles."""
+        out = (C.c_int * 4)()
+        rc = self._L.amg_get_plan(self._h, l, self.PLAN_OPS[op], out)
+        if rc < 0:
+            raise AMGError(rc, "amg_get_plan")
+        return {"layout": self.LAYOUT_NAMES[out[0]], "rows_per_tile": out[1], "threads_per_row": out[2],
+                "tiles": out[3]}
 
 
 class BatchedSolver(Solver):

@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "amg_b300.h"
@@ -132,12 +133,28 @@ struct DevScalars {
 struct StreamPlan {
     int rt = 0, vec = 0, cap = 0, ntiles = 0;
     int nt = 512;  // threads per CTA (768: the wide variant, 4-byte values only)
-    // windowed plans (c16 != null): per tile up to 4 windows of the gathered
-    // vector (start, length pairs; ntiles x 8 ints), 16-bit local column
-    // indices, and the window capacity per stage in elements
+    // windowed plans (c16 != null, or ell): per tile up to 16 windows of the
+    // gathered vector (start, length pairs; ntiles x 32 ints), 16-bit local
+    // column indices, and the window capacity per stage in elements
     int xw = 0;
     const int *wtab = nullptr;
     const uint16_t *c16 = nullptr;
+    // sliced-ELL plans (ell = 1; windowed, rt a multiple of 32): the entries
+    // of each 32-row slice g stored slot-major from soff[g] (a multiple of 32;
+    // ceil(n/32) + 1 offsets), padded to the slice's longest row; ec holds the
+    // local indices in that order and eperm the stored entry each of the ne
+    // slots holds (-1: padding).  Value arrays are laid out in slot order per
+    // plan: ev_dst[k] is the copy of CSR values ev_src[k] (vbytes[k] per value).
+    int ell = 0;
+    long long ne = 0;
+    const int *soff = nullptr;
+    const uint16_t *ec = nullptr;
+    const int *eperm = nullptr;
+    static constexpr int EV_MAX = 4;
+    int nev = 0;
+    const void *ev_src[EV_MAX] = {};
+    void *ev_dst[EV_MAX] = {};
+    int ev_bytes[EV_MAX] = {};
 };
 
 struct Level {
@@ -246,9 +263,79 @@ int tail_prepare(Hierarchy *h, cudaStream_t s);
 // Numeric re-setup: new values on the same pattern, the structure (aggregates,
 // every sparsity pattern, plans) kept and every value recomputed in place.
 int resetup_hierarchy(Hierarchy *h, const double *values, cudaStream_t s);
+// Lays the sliced-ELL plans' value arrays out again from the CSR values
+// (after a numeric re-setup).
+int ell_refresh(Hierarchy *h, cudaStream_t s);
 int build_hierarchy_batched(Hierarchy *h, const int *rp, const int *ci, const double *v, const int *sys_off_host,
                             int nsys, cudaStream_t s);
 void free_hierarchy(Hierarchy *h);
 int num_sms();
+
+// ---------------------------------------------------------------------------
+// FP32 <-> FP64 conversions on the integer pipes
+// ---------------------------------------------------------------------------
+//
+// A cvt between FP32 and FP64 issues on the FP64 pipe, at the rate of an FP64
+// FMA (under two per clock per SM on this GPU), and the FP64 Krylov kernels
+// already keep that pipe busy.  These conversions take the IEEE 754 binary32
+// and binary64 encodings apart with integer operations instead: widening is
+// exact, narrowing rounds to nearest, ties to even; infinities, subnormals
+// and signed zeros convert as IEEE 754 specifies, and a NaN stays a (quiet)
+// NaN with its leading payload bits.
+
+// binary32 -> binary64 (exact)
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned long long bits;
+    if (e - 1u < 254u) {  // normal: rebias the exponent (1023 - 127), widen the fraction
+        bits = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+    } else if (e == 255u) {  // infinity, or NaN made quiet
+        bits = sign | 0x7ff0000000000000ull | ((unsigned long long)m << 29) | (m ? (1ull << 51) : 0ull);
+    } else if (m == 0u) {  // signed zero
+        bits = sign;
+    } else {  // subnormal m 2^-149 = 1.f 2^(p - 149), p the leading one's position
+        const int p = 31 - __clz((int)m);
+        bits = sign | ((unsigned long long)(p + 874) << 52) | (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+    }
+    return __longlong_as_double((long long)bits);
+}
+
+// binary64 -> binary32, round to nearest even
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+    const int e = (int)((u >> 52) & 0x7ff);
+    const unsigned long long m = u & 0xfffffffffffffull;
+    const int ef = e - 896;  // the binary32 biased exponent
+    if (ef > 0 && ef < 255) {
+        // normal range: keep 23 fraction bits and round on the 29 dropped
+        // ones; a carry out of the fraction increments the exponent (up to
+        // infinity), as rounding requires
+        const unsigned hi = (unsigned)(m >> 29), rem = (unsigned)m & 0x1fffffffu;
+        const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (hi & 1u))) ? 1u : 0u;
+        return __uint_as_float(sign | (((unsigned)ef << 23) + hi + up));
+    }
+    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x00400000u | (unsigned)(m >> 29) : 0u));
+    if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);  // beyond the binary32 range
+    // binary32 subnormal or zero: the 53-bit significand in units of 2^-149,
+    // i.e. shifted right by 30 - ef (binary64 subnormals are far below)
+    const int sh = 30 - ef;
+    if (e == 0 || sh > 54) return __uint_as_float(sign);
+    const unsigned long long M = m | (1ull << 52);
+    const unsigned long long q = M >> sh, r = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    const unsigned long long up = (r > half || (r == half && (q & 1ull))) ? 1ull : 0ull;
+    return __uint_as_float(sign | (unsigned)(q + up));
+}
+
+// Value conversion between the library's floating types, FP32 <-> FP64 on
+// the integer pipes.
+template <typename To, typename From>
+__device__ __forceinline__ To fcvt(From v) {
+    if constexpr (std::is_same<To, float>::value && std::is_same<From, double>::value) return f64_to_f32_rn(v);
+    else if constexpr (std::is_same<To, double>::value && std::is_same<From, float>::value) return f32_to_f64(v);
+    else return static_cast<To>(v);
+}
 
 }  // namespace amg

@@ -1,4 +1,5 @@
 // api.cu -- the C ABI of libamgb300 (declared in include/amg_b300.h).
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <new>
@@ -32,7 +33,7 @@ int check_config(const amg_config &c) {
     if (c.solver < 0 || c.solver > 3 || (c.smoother != 0 && c.smoother != 1) || !(c.omega > 0.0) ||
         !(c.theta >= 0.0) || c.coarse_max < 1 || c.max_levels < 1 || c.max_levels > AMG_MAX_LEVELS ||
         !(c.rtol > 0.0) || c.max_iter < 1 || c.max_restarts < 0 || (c.precision != 0 && c.precision != 1) ||
-        c.symmetric < -1 || c.symmetric > 1) {
+        c.symmetric < -1 || c.symmetric > 1 || c.layout < AMG_LAYOUT_AUTO || c.layout > AMG_LAYOUT_SLICED_ELL) {
         set_last_error("invalid amg_config");
         return AMG_ERR_ARG;
     }
@@ -155,6 +156,7 @@ int amg_config_default(amg_config *c) {
     c->max_restarts = 3;
     c->precision = AMG_PRECISION_FP64;
     c->symmetric = -1;
+    c->layout = AMG_LAYOUT_AUTO;
     return AMG_OK;
 }
 
@@ -314,6 +316,47 @@ int amg_get_level(amg_handle h, int level, int which, long long *dims, int *row_
 int amg_get_aggregates(amg_handle h, int level, int *agg) {
     if (!h || !agg || level < 0 || level >= h->H.nlevels - 1) return AMG_ERR_ARG;
     AMG_CUDA_TRY(cudaMemcpy(agg, h->H.L[level].agg, sizeof(int) * (size_t)h->H.L[level].A.nrows, cudaMemcpyDefault));
+    return AMG_OK;
+}
+
+namespace {
+__global__ void k_narrow(const double *__restrict__ in, float *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = amg::f64_to_f32_rn(in[i]);
+}
+__global__ void k_widen(const float *__restrict__ in, double *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = amg::f32_to_f64(in[i]);
+}
+int conv_grid(long long n) { return (int)std::max(1LL, std::min((n + 255) / 256, 4096LL)); }
+}  // namespace
+
+int amg_narrow_f64(const double *in, float *out, long long n, void *cuda_stream) {
+    if (n < 0 || (n > 0 && (!in || !out))) return AMG_ERR_ARG;
+    if (n == 0) return AMG_OK;
+    k_narrow<<<conv_grid(n), 256, 0, (cudaStream_t)cuda_stream>>>(in, out, n);
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+int amg_widen_f32(const float *in, double *out, long long n, void *cuda_stream) {
+    if (n < 0 || (n > 0 && (!in || !out))) return AMG_ERR_ARG;
+    if (n == 0) return AMG_OK;
+    k_widen<<<conv_grid(n), 256, 0, (cudaStream_t)cuda_stream>>>(in, out, n);
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+int amg_get_plan(amg_handle h, int level, int which, int plan[4]) {
+    if (!h || !plan || level < 0 || level >= h->H.nlevels || which < 0 || which > 4 || (which == 4 && level != 0))
+        return AMG_ERR_ARG;
+    const Level &lv = h->H.L[level];
+    const StreamPlan *ps[] = {&lv.sa, &lv.sp, &lv.sr, &lv.sa_post, &lv.sa64};
+    const StreamPlan &p = *ps[which];
+    plan[0] = p.rt == 0 ? 0 : p.ell ? AMG_LAYOUT_SLICED_ELL : p.c16 ? AMG_LAYOUT_WINDOWED : AMG_LAYOUT_CSR;
+    plan[1] = p.rt;
+    plan[2] = p.vec;
+    plan[3] = p.ntiles;
     return AMG_OK;
 }
 

@@ -79,11 +79,11 @@ __device__ __forceinline__ TA spmm_row(const int *__restrict__ rp, const int *__
     for (; k + 3 < e; k += 4) {
         const int j0 = ci[k], j1 = ci[k + 1], j2 = ci[k + 2], j3 = ci[k + 3];
         const TA a0 = v[k], a1 = v[k + 1], a2 = v[k + 2], a3 = v[k + 3];
-        const TA x0 = (TA)x[(size_t)j0 * K + r], x1 = (TA)x[(size_t)j1 * K + r];
-        const TA x2 = (TA)x[(size_t)j2 * K + r], x3 = (TA)x[(size_t)j3 * K + r];
+        const TA x0 = fcvt<TA>(x[(size_t)j0 * K + r]), x1 = fcvt<TA>(x[(size_t)j1 * K + r]);
+        const TA x2 = fcvt<TA>(x[(size_t)j2 * K + r]), x3 = fcvt<TA>(x[(size_t)j3 * K + r]);
         s += a0 * x0 + a1 * x1 + a2 * x2 + a3 * x3;
     }
-    for (; k < e; ++k) s += v[k] * (TA)x[(size_t)ci[k] * K + r];
+    for (; k < e; ++k) s += v[k] * fcvt<TA>(x[(size_t)ci[k] * K + r]);
     return s;
 }
 
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(BT) kb_presmooth(int n, const int *rp, const i
                                                    const TB *b, TM *t, const int *nact) {
     if (*nact == 0) return;
     ROWS_K(n)
-    t[(size_t)i * K + r] = (TM)b[(size_t)i * K + r] - spmm_row<TM, TB>(rp, ci, ahat, b, i, r);
+    t[(size_t)i * K + r] = fcvt<TM>(b[(size_t)i * K + r]) - spmm_row<TM, TB>(rp, ci, ahat, b, i, r);
 }
 }
 
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(BT) kb_prolong(int n, const int *rp, const int
                                                  const TB *b, const TM *xc, TM *t, const int *nact) {
     if (*nact == 0) return;
     ROWS_K(n)
-    t[(size_t)i * K + r] = w[i] * (TM)b[(size_t)i * K + r] + spmm_row<TM, TM>(rp, ci, pv, xc, i, r);
+    t[(size_t)i * K + r] = w[i] * fcvt<TM>(b[(size_t)i * K + r]) + spmm_row<TM, TM>(rp, ci, pv, xc, i, r);
 }
 }
 
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(BT) kb_postsmooth(int n, const int *rp, const 
     const TM wi = w[i];
     if (wi != (TM)0) {
         const TM s = spmm_row<TM, TM>(rp, ci, av, t, i, r);
-        x[(size_t)i * K + r] = (TO)(t[(size_t)i * K + r] + wi * ((TM)b[(size_t)i * K + r] - s));
+        x[(size_t)i * K + r] = fcvt<TO>(t[(size_t)i * K + r] + wi * (fcvt<TM>(b[(size_t)i * K + r]) - s));
     }
 }
 }
@@ -146,8 +146,8 @@ __global__ void __launch_bounds__(BT) kb_dense(const int *r0s, const int *ms, co
     for (int e = threadIdx.x; e < m * K; e += BT) {
         const int i = e / K, r = e % K;
         double s = 0.0;
-        for (int j = 0; j < m; ++j) s += inv[(size_t)i * m + j] * (double)b[(size_t)(r0 + j) * K + r];
-        x[(size_t)(r0 + i) * K + r] = (TO)s;
+        for (int j = 0; j < m; ++j) s += inv[(size_t)i * m + j] * fcvt<double>(b[(size_t)(r0 + j) * K + r]);
+        x[(size_t)(r0 + i) * K + r] = fcvt<TO>(s);
     }
 }
 
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(BT) kb_post0(BDev W, const int *rp, const int 
         double o;
         if (wi != (TM)0) {
             const TM s = spmm_row<TM, TM>(rp, ci, av, t, i, r);
-            o = (double)(t[e] + wi * ((TM)W.R[e] - s));
+            o = fcvt<double>(t[e] + wi * (fcvt<TM>(W.R[e]) - s));
             W.Z[e] = o;
         } else {
             o = W.Z[e];
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(BT) kb_spmv0(BDev W, const int *rp, const int 
         if (TRUE_RES) {
             const double ri = W.B[e] - spmm_row<double, double>(rp, ci, av, W.X, i, r);
             W.R[e] = ri;
-            if (W.R32) W.R32[e] = (float)ri;
+            if (W.R32) W.R32[e] = f64_to_f32_rn(ri);
             acc[0] += ri * ri;
         } else {
             const double q = spmm_row<double, double>(rp, ci, av, W.P, i, r);
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(BT) kb_update(BDev W, int max_iter, int flexib
             if (flexible) W.Rold[e] = ri;
             const double rn = ri - alpha * W.Q[e];
             W.R[e] = rn;
-            if (W.R32) W.R32[e] = (float)rn;
+            if (W.R32) W.R32[e] = f64_to_f32_rn(rn);
             acc[0] += rn * rn;
         }
     }
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(BT) kb_init(BDev W, double rtol) {
         const double bi = W.B[e];
         W.X[e] = 0.0;
         W.R[e] = bi;
-        if (W.R32) W.R32[e] = (float)bi;
+        if (W.R32) W.R32[e] = f64_to_f32_rn(bi);
         W.P[e] = 0.0;
         W.Rold[e] = 0.0;
         W.Z[e] = 0.0;

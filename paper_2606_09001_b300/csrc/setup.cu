@@ -1596,8 +1596,9 @@ int resetup_hierarchy(Hierarchy *h, const double *v_in, cudaStream_t s) {
     }
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
     // the collapsed coarse end (in place) and the padded dense copies
-    if (h->nsolve < h->nlevels) return collapse_coarse(h, s);
-    return pad_dense(h, s);
+    AMG_TRY(h->nsolve < h->nlevels ? collapse_coarse(h, s) : pad_dense(h, s));
+    // the sliced-ELL plans' slot-order copies of the new values
+    return ell_refresh(h, s);
 }
 
 int build_hierarchy_batched(Hierarchy *h, const int *rp_in, const int *ci_in, const double *v_in,

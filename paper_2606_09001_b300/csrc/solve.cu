@@ -110,7 +110,7 @@ __device__ __forceinline__ void fail(DevScalars *sc, int status) {
 // ---------------------------------------------------------------------------
 
 template <typename TM, typename T>
-__device__ __forceinline__ TM ld(const T *p, int i) { return (TM)__ldg(p + i); }
+__device__ __forceinline__ TM ld(const T *p, int i) { return fcvt<TM>(__ldg(p + i)); }
 
 // ---------------------------------------------------------------------------
 // V-cycle kernels: VEC threads per row, grid-stride over warps so that every
@@ -230,11 +230,11 @@ __global__ void __launch_bounds__(BLOCK) k_postsmooth(int n, const int *__restri
     if (valid && lane_ == 0) {
         const TM bi = ld<TM>(b, i);
         const TM xi = t[i] + ld<TM>(w, i) * (bi - s);
-        const TO o = (TO)xi;
+        const TO o = fcvt<TO>(xi);
         out[i] = o;
         if (FIN == FIN_PCG_BETA) {
-            acc[0] += (double)ld<double>(b, i) * (double)o;
-            if (rold) acc[1] += rold[i] * (double)o;
+            acc[0] += ld<double>(b, i) * fcvt<double>(o);
+            if (rold) acc[1] += rold[i] * fcvt<double>(o);
         }
     }
     ROW_LOOP_END
@@ -253,17 +253,17 @@ __global__ void __launch_bounds__(BLOCK) k_coarse(int m, const double *__restric
     pdl_trigger();
     if (sc->done) return;
     __shared__ double sb[AMG_DENSE_MAX];
-    for (int i = threadIdx.x; i < m; i += BLOCK) sb[i] = (double)b[i];
+    for (int i = threadIdx.x; i < m; i += BLOCK) sb[i] = fcvt<double>(b[i]);
     __syncthreads();
     double acc[2] = {0.0, 0.0};
     for (int i = threadIdx.x; i < m; i += BLOCK) {
         double s = 0.0;
         for (int j = 0; j < m; ++j) s += cinv[(size_t)i * m + j] * sb[j];
-        const TO o = (TO)s;
+        const TO o = fcvt<TO>(s);
         x[i] = o;
         if (FIN == FIN_PCG_BETA) {
-            acc[0] += sb[i] * (double)o;
-            if (rold) acc[1] += rold[i] * (double)o;
+            acc[0] += sb[i] * fcvt<double>(o);
+            if (rold) acc[1] += rold[i] * fcvt<double>(o);
         }
     }
     if (FIN == FIN_PCG_BETA) {
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(int n, const double *__restr
         const double bi = b[i];
         x[i] = 0.0;
         r[i] = bi;
-        if (r32) r32[i] = (float)bi;
+        if (r32) r32[i] = f64_to_f32_rn(bi);
         p[i] = 0.0;
         if (rold) rold[i] = 0.0;
         acc[0] += bi * bi;
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(BLOCK) k_spmv_fin(int n, const int *__restrict
         if (SF == SF_TRUE_RES) {
             const double ri = dvec[i] - s;
             y[i] = ri;
-            if (y32) y32[i] = (float)ri;
+            if (y32) y32[i] = f64_to_f32_rn(ri);
             acc[0] += ri * ri;
         } else {
             y[i] = s;
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(int n, double *x, double *
         if (rold) rold[i] = ri;
         const double rn = ri - alpha * q[i];
         r[i] = rn;
-        if (r32) r32[i] = (float)rn;
+        if (r32) r32[i] = f64_to_f32_rn(rn);
         acc[0] += rn * rn;
     }
     double tot[1];
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(BLOCK) k_bicg_p(int n, const double *__restric
     for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
         const double pi = r[i] + beta * (p[i] - omega * v[i]);
         p[i] = pi;
-        if (p32) p32[i] = (float)pi;
+        if (p32) p32[i] = f64_to_f32_rn(pi);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) sc->iters += 1;
 }
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(BLOCK) k_bicg_s(int n, const double *__restric
     for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
         const double si = r[i] - alpha * v[i];
         s[i] = si;
-        if (s32) s32[i] = (float)si;
+        if (s32) s32[i] = f64_to_f32_rn(si);
         x[i] += alpha * ph[i];
         acc[0] += si * si;
     }
@@ -756,14 +756,15 @@ struct OpPre {
         TB b;
     };
     __device__ bool done() const { return *dn != 0; }
-    __device__ TM gather(int j) const { return (TM)__ldg(b + j); }
+    __device__ TM gather(int j) const { return fcvt<TM>(__ldg(b + j)); }
     using GX = TB;
     __device__ const GX *gsrc() const { return b; }
     __device__ Pre load(int i) const { return Pre{__ldg(b + i)}; }
     static constexpr bool SELF = true;  // the epilogue needs the gathered vector's own entry
+    static constexpr int NROWV = 0, ROWV_BYTES = 0;  // row operands staged by the sliced-ELL kernel
     __device__ Pre load_rest(int) const { return Pre{}; }
     __device__ void put_self(Pre &p, GX v) const { p.b = v; }
-    __device__ void finish(int i, TM s, const Pre &p, double (&)[2]) const { r[i] = (TM)p.b - s; }
+    __device__ void finish(int i, TM s, const Pre &p, double (&)[2]) const { r[i] = fcvt<TM>(p.b) - s; }
     template <int NT>
     __device__ void reduce(double (&)[2]) const {}
 };
@@ -781,6 +782,7 @@ struct OpSpmv {
     __device__ const GX *gsrc() const { return x; }
     __device__ Pre load(int) const { return Pre{}; }
     static constexpr bool SELF = false;
+    static constexpr int NROWV = 0, ROWV_BYTES = 0;
     __device__ Pre load_rest(int i) const { return load(i); }
     __device__ void put_self(Pre &, GX) const {}
     __device__ void finish(int i, TM s, const Pre &, double (&)[2]) const { y[i] = s; }
@@ -797,11 +799,12 @@ struct OpTune {
     TM *y;
     struct Pre {};
     __device__ bool done() const { return *dn != 0; }
-    __device__ TM gather(int j) const { return (TM)__ldg(x + j); }
+    __device__ TM gather(int j) const { return fcvt<TM>(__ldg(x + j)); }
     using GX = TG;
     __device__ const GX *gsrc() const { return x; }
     __device__ Pre load(int) const { return Pre{}; }
     static constexpr bool SELF = false;
+    static constexpr int NROWV = 0, ROWV_BYTES = 0;
     __device__ Pre load_rest(int i) const { return load(i); }
     __device__ void put_self(Pre &, GX) const {}
     __device__ void finish(int i, TM s, const Pre &, double (&)[2]) const { y[i] = s; }
@@ -828,8 +831,20 @@ struct OpProlong {
     __device__ Pre load(int i) const { return Pre{__ldg(w + i), __ldg(b + i)}; }
     static constexpr bool SELF = false;
     __device__ Pre load_rest(int i) const { return load(i); }
+    // row operands the sliced-ELL kernel stages with each tile: w, b
+    static constexpr int NROWV = 2, ROWV_BYTES = (int)(sizeof(TM) + sizeof(TB));
+    __device__ int rowv(const void **src, int *eb) const {
+        src[0] = w;
+        eb[0] = (int)sizeof(TM);
+        src[1] = b;
+        eb[1] = (int)sizeof(TB);
+        return 2;
+    }
+    __device__ Pre load_rowv(const unsigned char *const *rv, int rl) const {
+        return Pre{reinterpret_cast<const TM *>(rv[0])[rl], reinterpret_cast<const TB *>(rv[1])[rl]};
+    }
     __device__ void put_self(Pre &, GX) const {}
-    __device__ void finish(int i, TM s, const Pre &p, double (&)[2]) const { t[i] = p.w * (TM)p.b + s; }
+    __device__ void finish(int i, TM s, const Pre &p, double (&)[2]) const { t[i] = p.w * fcvt<TM>(p.b) + s; }
     template <int NT>
     __device__ void reduce(double (&)[2]) const {}
 };
@@ -862,13 +877,30 @@ struct OpPost {
     __device__ Pre load_rest(int i) const {
         return Pre{(TM)0, __ldg(w + i), __ldg(b + i), (FIN == FIN_PCG_BETA && rold) ? __ldg(rold + i) : 0.0};
     }
+    // row operands the sliced-ELL kernel stages with each tile: w, b (and r_old)
+    static constexpr int NROWV = FIN == FIN_PCG_BETA ? 3 : 2;
+    static constexpr int ROWV_BYTES = (int)(sizeof(TM) + sizeof(TB)) + (FIN == FIN_PCG_BETA ? 8 : 0);
+    __device__ int rowv(const void **src, int *eb) const {
+        src[0] = w;
+        eb[0] = (int)sizeof(TM);
+        src[1] = b;
+        eb[1] = (int)sizeof(TB);
+        if (FIN != FIN_PCG_BETA || !rold) return 2;
+        src[2] = rold;
+        eb[2] = 8;
+        return 3;
+    }
+    __device__ Pre load_rowv(const unsigned char *const *rv, int rl) const {
+        return Pre{(TM)0, reinterpret_cast<const TM *>(rv[0])[rl], reinterpret_cast<const TB *>(rv[1])[rl],
+                   (FIN == FIN_PCG_BETA && rold) ? reinterpret_cast<const double *>(rv[2])[rl] : 0.0};
+    }
     __device__ void put_self(Pre &p, GX v) const { p.t = v; }
     __device__ void finish(int i, TM s, const Pre &p, double (&acc)[2]) const {
-        const TO o = (TO)(p.t + p.w * ((TM)p.b - s));
+        const TO o = fcvt<TO>(p.t + p.w * (fcvt<TM>(p.b) - s));
         out[i] = o;
         if (FIN == FIN_PCG_BETA) {
-            acc[0] += (double)p.b * (double)o;
-            acc[1] += p.ro * (double)o;
+            acc[0] += fcvt<double>(p.b) * fcvt<double>(o);
+            acc[1] += p.ro * fcvt<double>(o);
         }
     }
     template <int NT>
@@ -901,6 +933,7 @@ struct OpFin {
     __device__ const GX *gsrc() const { return x; }
     __device__ Pre load(int i) const { return Pre{SF == SF_PCG_ALPHA ? __ldg(x + i) : __ldg(dvec + i)}; }
     static constexpr bool SELF = SF == SF_PCG_ALPHA;
+    static constexpr int NROWV = 0, ROWV_BYTES = 0;
     __device__ Pre load_rest(int i) const { return SELF ? Pre{} : load(i); }
     __device__ void put_self(Pre &p, GX v) const {
         if (SELF) p.d = v;
@@ -909,7 +942,7 @@ struct OpFin {
         if (SF == SF_TRUE_RES) {
             const double ri = p.d - s;
             y[i] = ri;
-            if (y32) y32[i] = (float)ri;
+            if (y32) y32[i] = f64_to_f32_rn(ri);
             acc[0] += ri * ri;
         } else {
             y[i] = s;
@@ -973,10 +1006,47 @@ static int stream_launch_vec(const StreamPlan &pl, int n, const int *rp, const i
     return stream_launch_nt<TM, VEC, Op, 512>(pl, n, rp, ci, v, op, err, s);
 }
 
+// The slot-order copy of CSR values v bound to sliced-ELL plan pl, or null.
+static const void *ell_values(const StreamPlan &pl, const void *v) {
+    for (int k = 0; k < pl.nev; ++k)
+        if (pl.ev_src[k] == v) return pl.ev_dst[k];
+    return nullptr;
+}
+
+template <typename TM, class Op>
+static int stream_launch_ell(const StreamPlan &pl, int n, const TM *v, const Op &op, int *err, cudaStream_t s) {
+    const TM *ev = static_cast<const TM *>(ell_values(pl, v));
+    if (!ev) {
+        set_last_error("streaming pass: the operator's values are not laid out for its sliced-ELL plan");
+        return AMG_ERR_ARG;
+    }
+    using GX = typename Op::GX;
+    // the epilogue's row operands are staged while two CTAs per SM still fit
+    int rows = Op::NROWV > 0 ? 1 : 0;
+    int smem = stream::smem_bytes_ell<TM, GX>(pl.cap, pl.xw, pl.rt, rows ? Op::ROWV_BYTES : 0);
+    if (rows && 2 * (smem + 11 * 1024) > 228 * 1024) {
+        rows = 0;
+        smem = stream::smem_bytes_ell<TM, GX>(pl.cap, pl.xw, pl.rt, 0);
+    }
+    static int attr_set = 0;
+    if (smem > attr_set) {
+        AMG_CUDA_TRY(cudaFuncSetAttribute(stream::k_stream_ell<TM, Op, 512>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_set = smem;
+    }
+    const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 11 * 1024)));
+    const int grid = std::max(1, std::min(pl.ntiles, per_sm * num_sms()));
+    AMG_TRY(launch_k(stream::k_stream_ell<TM, Op, 512>, grid, 512, smem, s, n, pl.rt, pl.cap, pl.xw, pl.ntiles, pl.soff,
+                     pl.ec, ev, pl.wtab, op, rows, err));
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
 // One streaming pass of a CSR operator whose plan is usable (pl.rt > 0).
 template <typename TM, class Op>
 static int stream_launch(const StreamPlan &pl, int n, const int *rp, const int *ci, const TM *v, const Op &op,
                          int *err, cudaStream_t s) {
+    if (pl.ell) return stream_launch_ell<TM, Op>(pl, n, v, op, err, s);
     switch (pl.vec) {
         case 1: return stream_launch_vec<TM, 1, Op>(pl, n, rp, ci, v, op, err, s);
         case 2: return stream_launch_vec<TM, 2, Op>(pl, n, rp, ci, v, op, err, s);
@@ -1247,11 +1317,136 @@ static bool build_windows(const DevCSR &m, StreamPlan &p, int worst_tile, int gx
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// Sliced-ELL plans (stream::k_stream_ell)
+// ---------------------------------------------------------------------------
+
+// The width (longest row) of each 32-row slice.
+__global__ void k_ell_width(int n, int nsl, const int *__restrict__ rp, int *wd) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nsl) return;
+    const int r0 = g * 32, r1 = min(r0 + 32, n);
+    int w = 0;
+    for (int r = r0; r < r1; ++r) w = max(w, rp[r + 1] - rp[r]);
+    wd[g] = w;
+}
+
+// One thread per slice row: its local indices in slot order and the stored
+// entry each slot holds; padding slots (-1) repeat the row's first index (0
+// for an empty row, whose tile still has a window if the slice has a slot).
+__global__ void k_ell_fill(int n, int nsl, const int *__restrict__ rp, const uint16_t *__restrict__ c16,
+                           const int *__restrict__ soff, int *eperm, uint16_t *ec) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (long long)nsl * 32) return;
+    const int g = (int)(r >> 5), lane = (int)(r & 31);
+    const int s0 = soff[g], wd = (soff[g + 1] - s0) >> 5;
+    const int b = r < n ? rp[r] : 0, len = r < n ? rp[r + 1] - b : 0;
+    const uint16_t pad = len > 0 ? c16[b] : (uint16_t)0;
+    for (int u = 0; u < wd; ++u) {
+        const int pos = s0 + u * 32 + lane;
+        eperm[pos] = u < len ? b + u : -1;
+        ec[pos] = u < len ? c16[b + u] : pad;
+    }
+}
+
+// dst = the values of src in slot order (zero in padding slots).
+template <typename T>
+__global__ void k_ell_vals(long long ne, const int *__restrict__ eperm, const T *__restrict__ src, T *dst) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ne; k += (long long)gridDim.x * blockDim.x) {
+        const int e = eperm[k];
+        dst[k] = e >= 0 ? src[e] : T(0);
+    }
+}
+
+static int ell_lay_out(const StreamPlan &pl, const void *src, void *dst, int vbytes, cudaStream_t s) {
+    if (pl.ne == 0) return AMG_OK;
+    const int grid = (int)std::min<long long>((pl.ne + 255) / 256, 16LL * num_sms());
+    if (vbytes == 4)
+        k_ell_vals<float><<<grid, 256, 0, s>>>(pl.ne, pl.eperm, static_cast<const float *>(src), static_cast<float *>(dst));
+    else
+        k_ell_vals<double><<<grid, 256, 0, s>>>(pl.ne, pl.eperm, static_cast<const double *>(src),
+                                                static_cast<double *>(dst));
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+// Turns windowed plan p (local indices c16 built for its tiles; rt a multiple
+// of 32) into a sliced-ELL plan with its tables in `scr`.  Returns false when
+// the padded tiles do not fit two CTAs per SM or the entry count overflows.
+template <typename TM>
+static bool build_ell(const DevCSR &m, StreamPlan &p, int gx_bytes, Scratch &scr, cudaStream_t s) {
+    const int n = m.nrows, nsl = (n + 31) / 32, spt = p.rt / 32;
+    int *wd = nullptr, *soff = nullptr;
+    if (p.rt % 32 != 0 || !p.c16 || scr.alloc(&wd, (size_t)nsl) < 0 || scr.alloc(&soff, (size_t)nsl + 1) < 0) {
+        cudaGetLastError();
+        return false;
+    }
+    k_ell_width<<<(nsl + 255) / 256, 256, 0, s>>>(n, nsl, m.rp, wd);
+    std::vector<int> w((size_t)nsl), so((size_t)nsl + 1);
+    if (cudaMemcpyAsync(w.data(), wd, sizeof(int) * (size_t)nsl, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    long long tot = 0;
+    for (int g = 0; g < nsl; ++g) {
+        so[g] = (int)tot;
+        tot += 32LL * w[g];
+        if (tot > INT_MAX - 64) return false;
+    }
+    so[nsl] = (int)tot;
+    int worst = 0;
+    for (int g0 = 0; g0 < nsl; g0 += spt) worst = std::max(worst, so[std::min(g0 + spt, nsl)] - so[g0]);
+    const int cap = std::max(64, (worst + 63) / 64 * 64);
+    // two CTAs per SM: 228 KB less 1 KB reserved per CTA and the descriptors'
+    // static shared memory (about 9 KB)
+    const int per_cta = (228 * 1024) / 2 - 1024 - 10 * 1024;
+    const int stage = stream::align16(cap * (int)sizeof(TM)) + stream::align16(cap * 2) +
+                      stream::align16(p.xw * gx_bytes) + 16;
+    if (stream::WIN_STAGES * stage > per_cta) return false;
+    int *eperm = nullptr;
+    uint16_t *ec = nullptr;
+    if (scr.alloc(&eperm, (size_t)std::max(1LL, tot)) < 0 || scr.alloc(&ec, (size_t)std::max(1LL, tot)) < 0) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaMemcpyAsync(soff, so.data(), sizeof(int) * so.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const long long rows = (long long)nsl * 32;
+    k_ell_fill<<<(int)((rows + 255) / 256), 256, 0, s>>>(n, nsl, m.rp, p.c16, soff, eperm, ec);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    p.ell = 1;
+    p.ne = tot;
+    p.soff = soff;
+    p.ec = ec;
+    p.eperm = eperm;
+    p.cap = cap;
+    p.c16 = nullptr;
+    p.vec = 1;
+    p.nt = 512;
+    return true;
+}
+
+// What a plan is timed with: the pass it serves, epilogue included, on
+// scratch vectors (y = M x for passes without an epilogue of their own).
+enum TuneKind { TUNE_SPMV, TUNE_PRE, TUNE_POST0, TUNE_POST, TUNE_PROLONG, TUNE_ALPHA };
+
+template <typename T>
+__global__ void k_fill(size_t n, T v, T *out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) out[i] = v;
+}
+
 // Times y = M x with each candidate (the best of three trials of ten launches,
 // after one warm-up) and keeps the fastest plan.  x and y are scratch vectors
 // of the operator's sizes.
 template <typename TM, typename TG>
-static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &ar, DevScalars *sc, cudaStream_t s) {
+static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &ar, int layout, TuneKind kind,
+                     cudaStream_t s) {
     const int gx_bytes = sizeof(TG);
     std::vector<StreamPlan> cands = plan_candidates(m, pl, sizeof(TM) == 4, s);
     Scratch scr;
@@ -1267,55 +1462,179 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &
             for (int r0 = 0; r0 < m.nrows; r0 += w.rt) worst = std::max(worst, rp[std::min(r0 + w.rt, m.nrows)] - rp[r0]);
             if (build_windows<TM>(m, w, worst, gx_bytes, scr, s)) cands.push_back(w);
         }
+        // sliced-ELL variants: tiles of one or two passes of the 15 consumer
+        // warps (a slice each), and of 7 slices for small operators
+        for (int rt : {480, 960, 224}) {
+            if ((long long)m.nrows < 2LL * rt) continue;
+            StreamPlan w;
+            w.rt = rt;
+            w.vec = 1;
+            w.nt = 512;
+            w.ntiles = (m.nrows + rt - 1) / rt;
+            int worst = 0;
+            for (int r0 = 0; r0 < m.nrows; r0 += rt) worst = std::max(worst, rp[std::min(r0 + rt, m.nrows)] - rp[r0]);
+            if (worst + 8 > 65536 || !build_windows<TM>(m, w, worst, gx_bytes, scr, s) ||
+                !build_ell<TM>(m, w, gx_bytes, scr, s))
+                continue;
+            TM *ev = nullptr;
+            if (scr.alloc(&ev, (size_t)std::max(1LL, w.ne)) < 0) {
+                cudaGetLastError();
+                continue;
+            }
+            if (ell_lay_out(w, vals, ev, (int)sizeof(TM), s) < 0) continue;
+            w.nev = 1;
+            w.ev_src[0] = vals;
+            w.ev_dst[0] = ev;
+            w.ev_bytes[0] = (int)sizeof(TM);
+            cands.push_back(w);
+        }
     }
-    if (cands.size() <= 1) return AMG_OK;
+    if (layout != AMG_LAYOUT_AUTO) {
+        // only the requested layout (the heuristic CSR plan when none fits)
+        auto kind = [](const StreamPlan &p) {
+            return p.ell ? AMG_LAYOUT_SLICED_ELL : p.c16 ? AMG_LAYOUT_WINDOWED : AMG_LAYOUT_CSR;
+        };
+        std::vector<StreamPlan> keep;
+        for (const StreamPlan &c : cands)
+            if (kind(c) == layout) keep.push_back(c);
+        if (keep.empty() && !cands.empty()) keep.push_back(cands[0]);
+        cands.swap(keep);
+    }
+    if (cands.empty()) return AMG_OK;
+    if (cands.size() == 1 && !cands[0].ell && !cands[0].c16) {
+        pl = cands[0];
+        return AMG_OK;
+    }
+    // scratch operands: the gathered vector, weights, right-hand sides and
+    // r_old set to constants (ones and halves keep every dot product finite,
+    // and p.Ap = sum_ij a_ij > 0 for the M-matrices of diffusion problems),
+    // outputs, and the reductions' partial sums and scalars of their own
+    const size_t nr = (size_t)m.nrows, ncl = (size_t)m.ncols;
+    const int cap = num_sms() * 8;
     TG *x = nullptr;
-    TM *y = nullptr;
+    TM *w = nullptr, *bm = nullptr;
+    double *y = nullptr, *bd = nullptr, *ro = nullptr, *part = nullptr;
+    unsigned *cnt = nullptr;
+    DevScalars *tsc = nullptr;
     int *err = nullptr;
-    AMG_TRY(scr.alloc(&x, (size_t)m.ncols));
-    AMG_TRY(scr.alloc(&y, (size_t)m.nrows));
+    AMG_TRY(scr.alloc(&x, ncl));
+    AMG_TRY(scr.alloc(&y, std::max(nr, ncl)));
+    AMG_TRY(scr.alloc(&w, nr));
+    AMG_TRY(scr.alloc(&bm, nr));
+    AMG_TRY(scr.alloc(&bd, nr));
+    AMG_TRY(scr.alloc(&ro, nr));
+    AMG_TRY(scr.alloc(&part, (size_t)3 * cap));
+    AMG_TRY(scr.alloc(&cnt, 4));
+    AMG_TRY(scr.alloc(&tsc, 1));
     AMG_TRY(scr.alloc(&err, 1));
-    AMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(TG) * (size_t)m.ncols, s));
+    k_fill<TG><<<256, 256, 0, s>>>(ncl, (TG)1, x);
+    k_fill<TM><<<256, 256, 0, s>>>(nr, (TM)0.5, w);
+    k_fill<TM><<<256, 256, 0, s>>>(nr, (TM)1, bm);
+    k_fill<double><<<256, 256, 0, s>>>(nr, 1.0, bd);
+    k_fill<double><<<256, 256, 0, s>>>(nr, 0.5, ro);
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned), s));
     AMG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-    int *dn = &sc->done;  // 0 between solves
+    constexpr bool same = std::is_same<TM, TG>::value;
+    const TM *xm = reinterpret_cast<const TM *>(x);  // the gathered vector as TM (kinds with TG = TM)
+    TM *ym = reinterpret_cast<TM *>(y);
+    auto launch = [&](const StreamPlan &c) -> int {
+        if constexpr (same) {
+            if (kind == TUNE_POST0)
+                return stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals,
+                                         OpPost<double, TM, double, FIN_PCG_BETA>{tsc, w, bd, xm, y, ro, part, cap, cnt},
+                                         err, s);
+            if (kind == TUNE_POST)
+                return stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals,
+                                         OpPost<TM, TM, TM, FIN_NONE>{tsc, w, bm, xm, ym, nullptr, part, cap, cnt}, err, s);
+            if (kind == TUNE_PROLONG)
+                return stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals, OpProlong<TM, TM>{&tsc->done, w, bm, xm, ym},
+                                         err, s);
+            if constexpr (std::is_same<TM, double>::value)
+                if (kind == TUNE_ALPHA)
+                    return stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals,
+                                             OpFin<SF_PCG_ALPHA>{tsc, x, y, nullptr, part, cap, cnt, nullptr}, err, s);
+        }
+        if (kind == TUNE_PRE)
+            return stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals, OpPre<TG, TM>{&tsc->done, x, ym}, err, s);
+        return stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals, OpTune<TM, TG>{&tsc->done, x, ym}, err, s);
+    };
     cudaEvent_t e0, e1;
     AMG_CUDA_TRY(cudaEventCreate(&e0));
     AMG_CUDA_TRY(cudaEventCreate(&e1));
-    // cands[0] is the heuristic plan; another candidate must beat it by 3 %
+    // cands[0] is the heuristic plan; another candidate must beat it by 3 %.
+    // A pass whose finisher stops the scalars (a p.Ap <= 0 on these
+    // operands) is timed as y = M x instead.
     float base_ms = 0.f, best = 1e30f;
     StreamPlan chosen = pl;
     int rc = AMG_OK;
-    for (size_t ci_ = 0; ci_ < cands.size(); ++ci_) {
-        const StreamPlan &c = cands[ci_];
-        OpTune<TM, TG> op{dn, x, y};
-        if ((rc = stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals, op, err, s)) < 0) break;
-        // best of three trials of ten launches
-        float ms = 1e30f;
-        for (int trial = 0; trial < 3 && rc >= 0; ++trial) {
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < 10; ++r)
-                if ((rc = stream_launch<TM>(c, m.nrows, m.rp, m.ci, vals, op, err, s)) < 0) break;
-            cudaEventRecord(e1, s);
-            if (rc < 0 || cudaEventSynchronize(e1) != cudaSuccess) {
-                rc = rc < 0 ? rc : AMG_ERR_CUDA;
+    for (int pass = 0; pass < 2 && rc >= 0; ++pass) {
+        bool stopped_any = false;
+        base_ms = 0.f;
+        best = 1e30f;
+        chosen = pl;
+        for (size_t ci_ = 0; ci_ < cands.size() && !stopped_any; ++ci_) {
+            const StreamPlan &c = cands[ci_];
+            if ((rc = cudaMemsetAsync(tsc, 0, sizeof(DevScalars), s) == cudaSuccess ? AMG_OK : AMG_ERR_CUDA) < 0) break;
+            if ((rc = launch(c)) < 0) break;
+            // best of three trials of ten launches
+            float ms = 1e30f;
+            for (int trial = 0; trial < 3 && rc >= 0; ++trial) {
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 10; ++r)
+                    if ((rc = launch(c)) < 0) break;
+                cudaEventRecord(e1, s);
+                if (rc < 0 || cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = rc < 0 ? rc : AMG_ERR_CUDA;
+                    break;
+                }
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                ms = std::min(ms, t);
+            }
+            if (rc < 0) break;
+            int stopped = 0;
+            if (cudaMemcpy(&stopped, &tsc->done, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                rc = AMG_ERR_CUDA;
                 break;
             }
-            float t = 0.f;
-            cudaEventElapsedTime(&t, e0, e1);
-            ms = std::min(ms, t);
+            stopped_any = stopped != 0;
+            if (ci_ == 0) base_ms = ms;
+            if (ms < best && (ci_ == 0 || ms < 0.97f * base_ms)) {
+                best = ms;
+                chosen = c;
+            }
         }
-        if (rc < 0) break;
-        if (ci_ == 0) base_ms = ms;
-        if (ms < best && (ci_ == 0 || ms < 0.97f * base_ms)) {
-            best = ms;
-            chosen = c;
-        }
+        if (rc < 0 || !stopped_any || kind == TUNE_SPMV) break;
+        kind = TUNE_SPMV;  // time every candidate again as y = M x
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
     if (rc < 0) return rc;
-    if (chosen.c16) {
+    if (chosen.ell) {
+        // keep the chosen tables (the candidates live in scratch memory); the
+        // value arrays are laid out for the plan by ell_bind
+        const int nsl = (m.nrows + 31) / 32;
+        int *wtab = nullptr, *soff = nullptr, *eperm = nullptr;
+        uint16_t *ec = nullptr;
+        const size_t ne = (size_t)std::max(1LL, chosen.ne);
+        AMG_TRY(ar.alloc(&wtab, (size_t)chosen.ntiles * 2 * stream::WIN_NW));
+        AMG_TRY(ar.alloc(&soff, (size_t)nsl + 1));
+        AMG_TRY(ar.alloc(&eperm, ne));
+        AMG_TRY(ar.alloc(&ec, ne));
+        AMG_CUDA_TRY(cudaMemcpyAsync(wtab, chosen.wtab, sizeof(int) * (size_t)chosen.ntiles * 2 * stream::WIN_NW,
+                                     cudaMemcpyDeviceToDevice, s));
+        AMG_CUDA_TRY(cudaMemcpyAsync(soff, chosen.soff, sizeof(int) * ((size_t)nsl + 1), cudaMemcpyDeviceToDevice, s));
+        AMG_CUDA_TRY(cudaMemcpyAsync(eperm, chosen.eperm, sizeof(int) * ne, cudaMemcpyDeviceToDevice, s));
+        AMG_CUDA_TRY(cudaMemcpyAsync(ec, chosen.ec, sizeof(uint16_t) * ne, cudaMemcpyDeviceToDevice, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        chosen.wtab = wtab;
+        chosen.soff = soff;
+        chosen.eperm = eperm;
+        chosen.ec = ec;
+        chosen.nev = 0;
+    } else if (chosen.c16) {
         // keep the chosen windows (the candidates live in scratch memory)
         int *wtab = nullptr;
         uint16_t *c16 = nullptr;
@@ -1332,35 +1651,105 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &
     return AMG_OK;
 }
 
-// Refines every streaming plan of the hierarchy by timed trial (the autotuner).
-int autotune_plans(Hierarchy *h, DevScalars *sc, cudaStream_t s) {
+template <class F>
+static void for_each_plan(Hierarchy *h, F f) {
+    for (int l = 0; l < h->nlevels; ++l) {
+        Level &lv = h->L[l];
+        for (StreamPlan *p : {&lv.sa, &lv.sa_post, &lv.sp, &lv.sr, &lv.sa64}) f(*p);
+    }
+}
+
+// Lays out, in the hierarchy's arena, CSR values src for sliced-ELL plan pl
+// (nothing for other plans); plans of one layout (the same slice offsets)
+// share a copy.
+static int ell_bind_one(Hierarchy *h, StreamPlan &pl, const void *src, int vbytes, cudaStream_t s) {
+    if (!pl.ell || !src || ell_values(pl, src)) return AMG_OK;
+    if (pl.nev == StreamPlan::EV_MAX) {
+        set_last_error("sliced-ELL plan: more than %d value arrays", StreamPlan::EV_MAX);
+        return AMG_ERR_ARG;
+    }
+    void *dst = nullptr;
+    for_each_plan(h, [&](StreamPlan &q) {
+        if (!dst && q.ell && q.soff == pl.soff) dst = const_cast<void *>(ell_values(q, src));
+    });
+    if (!dst) {
+        const size_t ne = (size_t)std::max(1LL, pl.ne);
+        if (vbytes == 4) {
+            float *d = nullptr;
+            AMG_TRY(h->arena.alloc(&d, ne));
+            dst = d;
+        } else {
+            double *d = nullptr;
+            AMG_TRY(h->arena.alloc(&d, ne));
+            dst = d;
+        }
+        AMG_TRY(ell_lay_out(pl, src, dst, vbytes, s));
+    }
+    pl.ev_src[pl.nev] = src;
+    pl.ev_dst[pl.nev] = dst;
+    pl.ev_bytes[pl.nev] = vbytes;
+    ++pl.nev;
+    return AMG_OK;
+}
+
+// Binds every sliced-ELL plan to the value arrays the solve launches it with.
+static int ell_bind(Hierarchy *h, cudaStream_t s) {
     const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
-    for (int l = 0; l < h->nsolve - 1; ++l) {
+    for (int l = 0; l < h->nlevels; ++l) {
         Level &lv = h->L[l];
         if (mixed) {
-            // level 0's pre-smoothing gathers the FP32 copy of the Krylov
-            // vector, its post-smoothing the FP32 iterate: two plans tuned apart
-            if (l == 0) {
-                lv.sa_post = lv.sa;
-                // the Krylov solvers hand the V-cycle FP32 copies of its input
-                AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa, h->arena, sc, s)));
-                AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa_post, h->arena, sc, s)));
-            } else {
-                AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa, h->arena, sc, s)));
-                lv.sa_post = lv.sa;
-            }
-            AMG_TRY((tune_plan<float, float>(lv.P, lv.P.v32, lv.sp, h->arena, sc, s)));
-            AMG_TRY((tune_plan<float, float>(lv.R, lv.R.v32, lv.sr, h->arena, sc, s)));
+            AMG_TRY(ell_bind_one(h, lv.sa, lv.ahat32, 4, s));
+            AMG_TRY(ell_bind_one(h, lv.sa_post, lv.A.v32, 4, s));
+            AMG_TRY(ell_bind_one(h, lv.sp, lv.P.v32, 4, s));
+            AMG_TRY(ell_bind_one(h, lv.sr, lv.R.v32, 4, s));
         } else {
-            AMG_TRY((tune_plan<double, double>(lv.A, lv.A.v, lv.sa, h->arena, sc, s)));
-            lv.sa_post = lv.sa;
-            AMG_TRY((tune_plan<double, double>(lv.P, lv.P.v, lv.sp, h->arena, sc, s)));
-            AMG_TRY((tune_plan<double, double>(lv.R, lv.R.v, lv.sr, h->arena, sc, s)));
+            AMG_TRY(ell_bind_one(h, lv.sa, lv.ahat, 8, s));
+            AMG_TRY(ell_bind_one(h, lv.sa_post, lv.A.v, 8, s));
+            AMG_TRY(ell_bind_one(h, lv.sp, lv.P.v, 8, s));
+            AMG_TRY(ell_bind_one(h, lv.sr, lv.R.v, 8, s));
         }
     }
-    if (mixed) AMG_TRY((tune_plan<double, double>(h->L[0].A, h->L[0].A.v, h->L[0].sa64, h->arena, sc, s)));
-    else h->L[0].sa64 = h->L[0].sa;
+    AMG_TRY(ell_bind_one(h, h->L[0].sa64, h->L[0].A.v, 8, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
     return AMG_OK;
+}
+
+int ell_refresh(Hierarchy *h, cudaStream_t s) {
+    int rc = AMG_OK;
+    for_each_plan(h, [&](StreamPlan &q) {
+        if (!q.ell) return;
+        for (int k = 0; k < q.nev && rc == AMG_OK; ++k) rc = ell_lay_out(q, q.ev_src[k], q.ev_dst[k], q.ev_bytes[k], s);
+    });
+    AMG_TRY(rc);
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+// Refines every streaming plan of the hierarchy by timed trial (the autotuner).
+int autotune_plans(Hierarchy *h, DevScalars *, cudaStream_t s) {
+    const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
+    const int lay = h->cfg.layout;
+    for (int l = 0; l < h->nsolve - 1; ++l) {
+        Level &lv = h->L[l];
+        // pre- and post-smoothing gather different vectors and run different
+        // epilogues: their plans of A are tuned apart
+        lv.sa_post = lv.sa;
+        const TuneKind post = l == 0 ? TUNE_POST0 : TUNE_POST;
+        if (mixed) {
+            // the Krylov solvers hand the finest level FP32 copies of its input
+            AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa, h->arena, lay, TUNE_PRE, s)));
+            AMG_TRY((tune_plan<float, float>(lv.A, lv.A.v32, lv.sa_post, h->arena, lay, post, s)));
+            AMG_TRY((tune_plan<float, float>(lv.P, lv.P.v32, lv.sp, h->arena, lay, TUNE_PROLONG, s)));
+            AMG_TRY((tune_plan<float, float>(lv.R, lv.R.v32, lv.sr, h->arena, lay, TUNE_SPMV, s)));
+        } else {
+            AMG_TRY((tune_plan<double, double>(lv.A, lv.A.v, lv.sa, h->arena, lay, TUNE_PRE, s)));
+            AMG_TRY((tune_plan<double, double>(lv.A, lv.A.v, lv.sa_post, h->arena, lay, post, s)));
+            AMG_TRY((tune_plan<double, double>(lv.P, lv.P.v, lv.sp, h->arena, lay, TUNE_PROLONG, s)));
+            AMG_TRY((tune_plan<double, double>(lv.R, lv.R.v, lv.sr, h->arena, lay, TUNE_SPMV, s)));
+        }
+    }
+    AMG_TRY((tune_plan<double, double>(h->L[0].A, h->L[0].A.v, h->L[0].sa64, h->arena, lay, TUNE_ALPHA, s)));
+    return ell_bind(h, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -283,6 +283,50 @@ constexpr int WIN_STAGES = 2;
 template <typename TM, typename GX, int NT = THREADS>
 inline int smem_bytes_win(int rt, int cap, int xw) { return WIN_STAGES * WLayout<TM, GX>(rt, cap, xw).stb; }
 
+// Producer side of the windowed kernels: bulk-copies the windows of the
+// gathered vector gx for tile t (the CTA's j-th; its descriptors from the
+// shared table m_w for the first META_T tiles, else from wtab) into xs, and
+// stores at *dl0_out the offset of column r0 in the windows when one window
+// holds the tile's own rows r0 .. r1-1 (else -1).  The copies' bytes are
+// expected with the caller's arrival on `full`.
+template <typename GX>
+__device__ __forceinline__ void issue_windows(const int *__restrict__ wtab, const int4 (*m_w)[WIN_NW / 2], int t, int j,
+                                              int r0, int r1, const GX *gx, unsigned char *xs, int *dl0_out,
+                                              uint64_t *full) {
+    const int4 *wrow = reinterpret_cast<const int4 *>(wtab) + (size_t)t * (WIN_NW / 2);
+    int4 wq[WIN_NW / 2];
+#pragma unroll
+    for (int q = 0; q < WIN_NW / 2; ++q) wq[q] = j < META_T ? m_w[j][q] : __ldg(wrow + q);
+    int dl0 = -1;
+    {
+        int woff = 0;
+#pragma unroll
+        for (int q = 0; q < WIN_NW / 2; ++q) {
+            if (dl0 < 0 && wq[q].y > 0 && r0 >= wq[q].x && r1 <= wq[q].x + wq[q].y) dl0 = woff + r0 - wq[q].x;
+            woff += wq[q].y;
+            if (dl0 < 0 && wq[q].w > 0 && r0 >= wq[q].z && r1 <= wq[q].z + wq[q].w) dl0 = woff + r0 - wq[q].z;
+            woff += wq[q].w;
+        }
+    }
+    *dl0_out = dl0;
+    uint32_t b_x = 0;
+#pragma unroll
+    for (int q = 0; q < WIN_NW / 2; ++q) b_x += (uint32_t)(wq[q].y + wq[q].w) * (uint32_t)sizeof(GX);
+    mbar_expect_tx(full, b_x);
+    uint32_t off = 0;
+#pragma unroll
+    for (int q = 0; q < WIN_NW / 2; ++q) {
+        if (wq[q].y > 0) {
+            bulk_g2s(xs + off, gx + wq[q].x, (uint32_t)wq[q].y * (uint32_t)sizeof(GX), full);
+            off += (uint32_t)wq[q].y * (uint32_t)sizeof(GX);
+        }
+        if (wq[q].w > 0) {
+            bulk_g2s(xs + off, gx + wq[q].z, (uint32_t)wq[q].w * (uint32_t)sizeof(GX), full);
+            off += (uint32_t)wq[q].w * (uint32_t)sizeof(GX);
+        }
+    }
+}
+
 template <typename TM, int VEC, class Op, int NT = THREADS>
 __global__ void __launch_bounds__(NT, 2) k_stream_win(int n, int rt, int cap, int xw, int ntiles,
                                                       const int *__restrict__ rp, const uint16_t *__restrict__ c16,
@@ -343,41 +387,8 @@ __global__ void __launch_bounds__(NT, 2) k_stream_win(int n, int rt, int cap, in
     auto issue_win = [&](int t, int j, int st) {
         unsigned char *stage = smem + st * L.stb;
         const int r0 = t * rt, r1 = min(r0 + rt, n);
-        const int4 *wrow = reinterpret_cast<const int4 *>(wtab) + (size_t)t * (WIN_NW / 2);
-        int4 wq[WIN_NW / 2];
-#pragma unroll
-        for (int q = 0; q < WIN_NW / 2; ++q) wq[q] = j < META_T ? m_w[j][q] : __ldg(wrow + q);
-        // offset of column r0 in the windows when one window holds columns r0 .. r1-1
-        int dl0 = -1;
-        {
-            int woff = 0;
-#pragma unroll
-            for (int q = 0; q < WIN_NW / 2; ++q) {
-                if (dl0 < 0 && wq[q].y > 0 && r0 >= wq[q].x && r1 <= wq[q].x + wq[q].y) dl0 = woff + r0 - wq[q].x;
-                woff += wq[q].y;
-                if (dl0 < 0 && wq[q].w > 0 && r0 >= wq[q].z && r1 <= wq[q].z + wq[q].w) dl0 = woff + r0 - wq[q].z;
-                woff += wq[q].w;
-            }
-        }
-        reinterpret_cast<int *>(stage + L.rpb + L.cib + L.vab + L.xwb)[2] = dl0;
-        uint32_t b_x = 0;
-#pragma unroll
-        for (int q = 0; q < WIN_NW / 2; ++q) b_x += (uint32_t)(wq[q].y + wq[q].w) * (uint32_t)sizeof(GX);
-        mbar_expect_tx(&full[st], b_x);
-        const GX *gx = op.gsrc();
-        unsigned char *xs = stage + L.rpb + L.cib + L.vab;
-        uint32_t off = 0;
-#pragma unroll
-        for (int q = 0; q < WIN_NW / 2; ++q) {
-            if (wq[q].y > 0) {
-                bulk_g2s(xs + off, gx + wq[q].x, (uint32_t)wq[q].y * (uint32_t)sizeof(GX), &full[st]);
-                off += (uint32_t)wq[q].y * (uint32_t)sizeof(GX);
-            }
-            if (wq[q].w > 0) {
-                bulk_g2s(xs + off, gx + wq[q].z, (uint32_t)wq[q].w * (uint32_t)sizeof(GX), &full[st]);
-                off += (uint32_t)wq[q].w * (uint32_t)sizeof(GX);
-            }
-        }
+        issue_windows<GX>(wtab, m_w, t, j, r0, r1, op.gsrc(), stage + L.rpb + L.cib + L.vab,
+                          reinterpret_cast<int *>(stage + L.rpb + L.cib + L.vab + L.xwb) + 2, &full[st]);
     };
     int npre = 0;
     if (tid == 0)
@@ -449,12 +460,257 @@ __global__ void __launch_bounds__(NT, 2) k_stream_win(int n, int rt, int cap, in
 #pragma unroll
                         for (int u = 0; u < UNR; ++u) {
                             const int k = kb + u * VEC;
-                            if (k < k1) sum += vals[k - vsb] * (TM)xs[cis[k - cs]];
+                            if (k < k1) sum += vals[k - vsb] * fcvt<TM>(xs[cis[k - cs]]);
                         }
                     }
                 }
                 if (VEC > 1) sum = group_sum<VEC>(sum);
                 if (vl == 0 && rl < rows) op.finish(r0 + rl, sum, pre, acc);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+        }
+    }
+    if (!ok) {
+        atomicExch(err, 1);
+        for (int k = 0; k < STAGES; ++k) mbar_try_wait(&full[k], 0);
+    }
+    op.template reduce<NT>(acc);
+}
+
+// ---------------------------------------------------------------------------
+// Sliced-ELL variant: one thread per row, slot-major tiles
+// ---------------------------------------------------------------------------
+//
+// The windowed layout with each 32-row slice's entries stored slot-major:
+// entry u of row 32g + l sits at soff[g] + 32u + l, the slice padded to its
+// longest row with zero values (whose local index is some valid window
+// offset, so the padding adds +-0 to the row's sum).  A warp takes a slice,
+// one lane per row: per slot its 32 lanes read 32 consecutive values and
+// indices, and on stencil operators 32 consecutive entries of the staged
+// vector, which is the fewest shared-memory wavefronts a stored entry can
+// cost; the CSR kernels' lanes instead read entries strided by the row
+// length.  Each row is summed in CSR order, and the epilogue runs on all 32
+// lanes with coalesced loads and stores.  Tiles are rt rows, a multiple of
+// 32; soff[g] is a multiple of 32 entries, so every bulk copy starts on a
+// 16-byte boundary and moves a multiple of 16 bytes.
+//
+// The epilogue's own row operands (Op::rowv: up to three vectors indexed by
+// row, e.g. the smoother weights and right-hand side) are staged too when
+// `rows` is set: each tile's range of each vector, in whole 16-byte chunks,
+// bulk-copied with the tile, so the epilogue reads shared memory instead of
+// waiting on global loads.  The rows of a ragged chunk (the last tile's last
+// n % 4 rows) and vectors not 16-byte aligned fall back to global loads.
+
+constexpr int ROWV_MAX = 3;
+
+template <typename TM, typename GX>
+struct ELayout {
+    int vab, cib, xwb, rvb, stb;
+    // rvbytes: staged row-operand bytes per row (0: none)
+    __host__ __device__ ELayout(int cap, int xw, int rt, int rvbytes)
+        : vab(align16(cap * (int)sizeof(TM))), cib(align16(cap * 2)), xwb(align16(xw * (int)sizeof(GX))),
+          rvb(rvbytes ? align16(rt * rvbytes + 16 * ROWV_MAX) : 0), stb(vab + cib + xwb + rvb + 16) {}
+};
+
+template <typename TM, typename GX>
+inline int smem_bytes_ell(int cap, int xw, int rt, int rvbytes) {
+    return WIN_STAGES * ELayout<TM, GX>(cap, xw, rt, rvbytes).stb;
+}
+
+template <typename TM, class Op, int NT = THREADS>
+__global__ void __launch_bounds__(NT, 2) k_stream_ell(int n, int rt, int cap, int xw, int ntiles,
+                                                      const int *__restrict__ soff, const uint16_t *__restrict__ ec,
+                                                      const TM *__restrict__ ev, const int *__restrict__ wtab, Op op,
+                                                      int rows, int *err) {
+    using GX = typename Op::GX;
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int STAGES = WIN_STAGES;
+    constexpr int CONSUMER_WARPS = NT / 32 - 1;
+    __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES];
+    const ELayout<TM, GX> L(cap, xw, rt, rows ? Op::ROWV_BYTES : 0);
+    // the staged row operands: sources, element sizes, offsets in a stage
+    const void *rsrc[ROWV_MAX] = {};
+    int reb[ROWV_MAX] = {0, 0, 0}, roff[ROWV_MAX] = {0, 0, 0}, nrv = 0;
+    if constexpr (Op::NROWV > 0) {
+        if (rows) {
+            nrv = op.rowv(rsrc, reb);
+            int o = 0;
+#pragma unroll
+            for (int k = 0; k < ROWV_MAX; ++k) {
+                if (k >= nrv) reb[k] = 0;
+                else if (reinterpret_cast<uintptr_t>(rsrc[k]) & 15) nrv = 0;  // not bulk-copyable: global loads
+                roff[k] = o;
+                o += align16(rt * reb[k]);
+            }
+        }
+    }
+    const bool staged = nrv > 0;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int spt = rt >> 5;          // slices per tile
+    const int nsl_all = (n + 31) >> 5;  // slices of the operator
+    if (tid == 0) {
+        for (int k = 0; k < STAGES; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], CONSUMER_WARPS);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    __shared__ int2 m_se[META_T];
+    __shared__ int4 m_w[META_T][WIN_NW / 2];
+    const int my_tiles = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    {
+        constexpr int PARTS = 1 + WIN_NW / 2;
+        for (int q = tid; q < min(my_tiles, META_T) * PARTS; q += NT) {
+            const int j = q / PARTS, part = q % PARTS;
+            const int t = blockIdx.x + j * gridDim.x;
+            if (part == 0) m_se[j] = make_int2(__ldg(soff + t * spt), __ldg(soff + min(t * spt + spt, nsl_all)));
+            else m_w[j][part - 1] = __ldg(reinterpret_cast<const int4 *>(wtab) + (size_t)t * (WIN_NW / 2) + part - 1);
+        }
+    }
+    __syncthreads();
+    // The operator part of tile t (values, local indices), its bytes expected
+    // without arriving: constant data, copied for the first tiles before the
+    // dependency wait.
+    auto issue_op = [&](int t, int j, int st) {
+        unsigned char *stage = smem + st * L.stb;
+        const int g0 = t * spt;
+        const int2 se = j < META_T ? m_se[j] : make_int2(__ldg(soff + g0), __ldg(soff + min(g0 + spt, nsl_all)));
+        reinterpret_cast<int *>(stage + L.vab + L.cib + L.xwb + L.rvb)[0] = se.x;
+        const uint32_t ne = (uint32_t)(se.y - se.x);
+        const uint32_t b_v = ne * (uint32_t)sizeof(TM), b_c = ne * 2u;
+        mbar_expect_tx_only(&full[st], b_v + b_c);
+        if (ne) {
+            bulk_g2s(stage, ev + se.x, b_v, &full[st]);
+            bulk_g2s(stage + L.vab, ec + se.x, b_c, &full[st]);
+        }
+    };
+    // the row operands and windows of tile t (written by predecessors: after
+    // the dependency wait), the windows' copies arriving for the producer
+    auto issue_win = [&](int t, int j, int st) {
+        unsigned char *stage = smem + st * L.stb;
+        const int r0 = t * rt, r1 = min(r0 + rt, n);
+        if (staged) {
+            const int rs = (r1 - r0) & ~3;  // whole 16-byte chunks of every operand
+            uint32_t bytes = 0;
+#pragma unroll
+            for (int k = 0; k < ROWV_MAX; ++k) bytes += (uint32_t)(rs * reb[k]);
+            if (bytes) {
+                mbar_expect_tx_only(&full[st], bytes);
+                unsigned char *rvb = stage + L.vab + L.cib + L.xwb;
+#pragma unroll
+                for (int k = 0; k < ROWV_MAX; ++k)
+                    if (reb[k])
+                        bulk_g2s(rvb + roff[k], static_cast<const unsigned char *>(rsrc[k]) + (size_t)r0 * reb[k],
+                                 (uint32_t)(rs * reb[k]), &full[st]);
+            }
+        }
+        issue_windows<GX>(wtab, m_w, t, j, r0, r1, op.gsrc(), stage + L.vab + L.cib,
+                          reinterpret_cast<int *>(stage + L.vab + L.cib + L.xwb + L.rvb) + 1, &full[st]);
+    };
+    int npre = 0;
+    if (tid == 0)
+        for (; npre < STAGES && (int)blockIdx.x + npre * (int)gridDim.x < ntiles; ++npre)
+            issue_op(blockIdx.x + npre * gridDim.x, npre, npre);
+    pdl_wait();
+    pdl_trigger();
+    if (op.done()) {
+        // the prefetched copies land before the CTA leaves
+        if (tid == 0)
+            for (int k = 0; k < npre; ++k) {
+                mbar_arrive(&full[k]);
+                mbar_wait(&full[k], 0);
+            }
+        return;
+    }
+    double acc[2] = {0.0, 0.0};
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int j = 0;; ++j) {
+                const int t = blockIdx.x + j * gridDim.x;
+                if (t >= ntiles) break;
+                const int st = j % STAGES;
+                if (j >= npre) {
+                    if (!mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    fence_proxy_async();
+                    issue_op(t, j, st);
+                }
+                issue_win(t, j, st);
+            }
+        }
+    } else {
+        const int cw = warp - 1;
+        for (int j = 0;; ++j) {
+            const int t = blockIdx.x + j * gridDim.x;
+            if (t >= ntiles) break;
+            const int st = j % STAGES;
+            const int r0 = t * rt, g0 = t * spt;
+            const int nsl = min(spt, nsl_all - g0);
+            // the warp's first slice: its entry range and the rows' epilogue
+            // operands, loaded before the stage wait so the latencies overlap
+            int sl = cw;
+            int sb0 = 0, sb1 = 0;
+            typename Op::Pre pre{};
+            if (sl < nsl) {
+                sb0 = __ldg(soff + g0 + sl);
+                sb1 = __ldg(soff + g0 + sl + 1);
+                const int row = r0 + sl * 32 + lane;
+                if (!staged && row < n) pre = op.load_rest(row);
+            }
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / STAGES) & 1)))) {  // warp-uniform
+                ok = false;
+                break;
+            }
+            const unsigned char *stage = smem + st * L.stb;
+            const TM *vals = reinterpret_cast<const TM *>(stage);
+            const uint16_t *cis = reinterpret_cast<const uint16_t *>(stage + L.vab);
+            const GX *xs = reinterpret_cast<const GX *>(stage + L.vab + L.cib);
+            const int *hdr = reinterpret_cast<const int *>(stage + L.vab + L.cib + L.xwb + L.rvb);
+            const int e0 = hdr[0], dl0 = hdr[1];
+            const int rs = (min(r0 + rt, n) - r0) & ~3;  // rows whose operands are staged
+            while (sl < nsl) {
+                const int rl = sl * 32 + lane, row = r0 + rl;
+                if constexpr (Op::NROWV > 0) {
+                    if (staged) {
+                        const unsigned char *rvb = stage + L.vab + L.cib + L.xwb;
+                        const unsigned char *rv[ROWV_MAX] = {rvb + roff[0], rvb + roff[1], rvb + roff[2]};
+                        if (rl < rs) pre = op.load_rowv(rv, rl);
+                        else if (row < n) pre = op.load_rest(row);
+                    }
+                }
+                const int wd = (sb1 - sb0) >> 5;  // warp-uniform
+                const TM *vp = vals + (sb0 - e0) + lane;
+                const uint16_t *cp = cis + (sb0 - e0) + lane;
+                TM sum = 0;
+                int u = 0;
+                for (; u + 4 <= wd; u += 4) {
+                    TM a[4];
+                    int c[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        a[q] = vp[(u + q) * 32];
+                        c[q] = cp[(u + q) * 32];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) sum += a[q] * fcvt<TM>(xs[c[q]]);
+                }
+                for (; u < wd; ++u) sum += vp[u * 32] * fcvt<TM>(xs[cp[u * 32]]);
+                if (row < n) {
+                    if (Op::SELF) op.put_self(pre, dl0 >= 0 ? xs[dl0 + rl] : __ldg(op.gsrc() + row));
+                    op.finish(row, sum, pre, acc);
+                }
+                sl += CONSUMER_WARPS;
+                if (sl < nsl) {
+                    sb0 = __ldg(soff + g0 + sl);
+                    sb1 = __ldg(soff + g0 + sl + 1);
+                    const int row2 = r0 + sl * 32 + lane;
+                    if (!staged) pre = row2 < n ? op.load_rest(row2) : typename Op::Pre{};
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);

@@ -237,14 +237,14 @@ __global__ void __launch_bounds__(THREADS) k_tail(const __grid_constant__ TArgs<
         TM *bs = lv.bs_off >= 0 ? reinterpret_cast<TM *>(smem + lv.bs_off) : nullptr;
         // t = b - A (W b)
         stage(xs, lv.n, [&](int j) {
-            const TM bj = fin0 ? (TM)__ldg(b0 + j) : ldcg(lv.b + j);
+            const TM bj = fin0 ? fcvt<TM>(__ldg(b0 + j)) : ldcg(lv.b + j);
             if (bs) bs[j] = bj;
             return (ws ? ws[j] : __ldg(lv.w + j)) * bj;
         });
         ready();
         if (ok)
             op_rows<TM, TM, TM>(lv.A, c, smem, xs, [&](int i, TM s) {
-                lv.t[i] = (bs ? bs[i] : fin0 ? (TM)__ldg(b0 + i) : ldcg(lv.b + i)) - s;
+                lv.t[i] = (bs ? bs[i] : fin0 ? fcvt<TM>(__ldg(b0 + i)) : ldcg(lv.b + i)) - s;
             });
         cluster.sync();
         // b_next = R t
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(THREADS) k_tail(const __grid_constant__ TArgs<
         const TLevel<TM> &lc = a.L[nl - 1];
         stage(xs, a.nc, [&](int j) { return ldcg(lc.b + j); });
         ready();
-        if (ok) op_rows<double, TM, double>(a.C, c, smem, xs, [&](int i, double s) { lc.x[i] = (TM)s; });
+        if (ok) op_rows<double, TM, double>(a.C, c, smem, xs, [&](int i, double s) { lc.x[i] = fcvt<TM>(s); });
         cluster.sync();
     }
     // up: prolongation, post-smoothing
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(THREADS) k_tail(const __grid_constant__ TArgs<
         const TM *ws = lv.ws_off >= 0 ? reinterpret_cast<const TM *>(smem + lv.ws_off) : nullptr;
         const TM *bs = lv.bs_off >= 0 ? reinterpret_cast<const TM *>(smem + lv.bs_off) : nullptr;
         auto wof = [&](int i) { return ws ? ws[i] : __ldg(lv.w + i); };
-        auto bof = [&](int i) { return bs ? bs[i] : fin0 ? (TM)__ldg(b0 + i) : ldcg(lv.b + i); };
+        auto bof = [&](int i) { return bs ? bs[i] : fin0 ? fcvt<TM>(__ldg(b0 + i)) : ldcg(lv.b + i); };
         // t = W b + P x_next
         stage(xs, nx.n, [&](int j) { return ldcg(nx.x + j); });
         if (ok) op_rows<TM, TM, TM>(lv.P, c, smem, xs, [&](int i, TM s) { lv.t[i] = wof(i) * bof(i) + s; });
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(THREADS) k_tail(const __grid_constant__ TArgs<
             op_rows<TM, TM, TM>(lv.A, c, smem, xs, [&](int i, TM s) {
                 const TM xi = xs[i] + wof(i) * (bof(i) - s);
                 if (fin0) {
-                    const double o = (double)xi;
+                    const double o = fcvt<double>(xi);
                     z0[i] = o;
                     if (fin) {
                         acc[0] += __ldg(b0 + i) * o;

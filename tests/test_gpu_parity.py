@@ -33,6 +33,7 @@ def ocfg(cfg):
     """The oracle's configuration for a library configuration dict."""
     c = dict(cfg or {})
     c.pop("precision", None)
+    c.pop("layout", None)
     if isinstance(c.get("solver"), str):
         c["solver"] = _lib.SOLVERS[c["solver"]]
     if isinstance(c.get("smoother"), str):

@@ -28,6 +28,7 @@ def gpu_solver(A, cfg=None):
 def ocfg(cfg):
     c = dict(cfg or {})
     c.pop("precision", None)
+    c.pop("layout", None)
     if isinstance(c.get("solver"), str):
         c["solver"] = _lib.SOLVERS[c["solver"]]
     return c
