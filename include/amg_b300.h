@@ -68,8 +68,8 @@ extern "C" {
 /* Solvers. */
 #define AMG_SOLVER_PCG 0            /* AMG-preconditioned CG (SPD A) */
 #define AMG_SOLVER_BICGSTAB 1       /* AMG right-preconditioned BiCGStab */
-#define AMG_SOLVER_CG 2             /* CG without preconditioner */
-#define AMG_SOLVER_BICGSTAB_NOPREC 3 /* BiCGStab without preconditioner */
+#define AMG_SOLVER_CG 2             /* CG without preconditioner (setup builds no coarse levels) */
+#define AMG_SOLVER_BICGSTAB_NOPREC 3 /* BiCGStab without preconditioner (no coarse levels either) */
 
 /* Smoothers. */
 #define AMG_SMOOTHER_JACOBI 0    /* x <- x + omega D^-1 (b - A x) */
@@ -163,7 +163,9 @@ int amg_adjoint(amg_handle h, const double *x, const double *g, double *lambda, 
 
 /* Applies the AMG preconditioner once: z = M^-1 r (one V(1,1) cycle from
  * z = 0), the operator the Krylov solvers use (Sec. 2.2, preconditioner
- * export).  r and z have n entries. */
+ * export).  r and z have n entries.  A handle set up for an unpreconditioned
+ * solver (AMG_SOLVER_CG, AMG_SOLVER_BICGSTAB_NOPREC) holds the finest level
+ * only and returns AMG_ERR_UNSUPPORTED. */
 int amg_vcycle(amg_handle h, const double *r, double *z, void *cuda_stream);
 
 /* Hierarchy statistics (nlevels, rows, nnz, operator_complexity, setup_ms).

@@ -205,6 +205,11 @@ struct Hierarchy {
     double *cinv = nullptr;
     float *cinv32 = nullptr;
     double *cinv_last = nullptr;  // the coarsest level's dense inverse (also when collapsed)
+    // Symmetry re-detection at re-setup (the pattern is fixed): tmap[k] is the
+    // position of entry k's mirror a_ji when the pattern is symmetric
+    // (tmap_state 1), built at the first re-setup; -1: pattern nonsymmetric.
+    int *tmap = nullptr;
+    int tmap_state = 0;
     // copies of the dense operator with rows padded to nc_ld entries (a
     // multiple of 4, zero-filled) for 16-byte vector loads
     int nc_ld = 0;

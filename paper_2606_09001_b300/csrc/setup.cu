@@ -975,6 +975,9 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
     }
 
     // ---- levels ----
+    // Unpreconditioned Krylov solvers keep the finest level only: no coarse
+    // levels, coarse solve or cycle are built (nor re-set up).
+    const bool precond = cfg.solver == AMG_SOLVER_PCG || cfg.solver == AMG_SOLVER_BICGSTAB;
     int l = 0;
     for (;;) {
         Level &Lv = h->L[l];
@@ -999,7 +1002,7 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
         k_smoother_weights<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.v, diag, cfg.omega,
                                                         cfg.smoother == AMG_SMOOTHER_L1_JACOBI, Lv.w);
         AMG_LAUNCH_CHECK();
-        if (nl <= cfg.coarse_max || l + 1 >= cfg.max_levels || l + 1 >= AMG_MAX_LEVELS) break;
+        if (!precond || nl <= cfg.coarse_max || l + 1 >= cfg.max_levels || l + 1 >= AMG_MAX_LEVELS) break;
 
         // strength
         const double theta_l = ldexp(cfg.theta, -l);
@@ -1111,12 +1114,12 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
 
     // ---- coarsest level: dense factor + inverse ----
     Level &Lc = h->L[l];
-    h->nc = Lc.A.nrows;
+    h->nc = precond ? Lc.A.nrows : 0;
     if (h->nc > AMG_DENSE_MAX) {
         set_last_error("coarsening stopped at level %d with %d rows (> %d)", l, h->nc, AMG_DENSE_MAX);
         return AMG_ERR_STALL;
     }
-    {
+    if (precond) {
         Scratch sc;
         double *dense;
         int *piv, *st;
@@ -1186,6 +1189,10 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
         }
     }
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!precond) {
+        h->nsolve = 1;
+        return AMG_OK;
+    }
     AMG_TRY(collapse_coarse(h, s));
     return tail_prepare(h, s);
 }
@@ -1471,6 +1478,83 @@ static int collapse_coarse(Hierarchy *h, cudaStream_t s) {
 // are recomputed from the new values by the same kernels as the setup, and
 // written into the existing arrays -- every pointer the streaming plans,
 // windows, tail tables and captured graphs hold stays valid.
+// The index of every stored entry, as a value (exact in FP64 below 2^53).
+__global__ void k_entry_index(long long nnz, double *v) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x)
+        v[k] = (double)k;
+}
+
+// Pattern of the transpose equal to the pattern: record the mirror map.
+__global__ void k_mirror_map(int n, long long nnz, const int *rp1, const int *ci1, const int *rp2, const int *ci2,
+                             const double *idx2, int *tmap, int *differ) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz + n + 1;
+         k += (long long)gridDim.x * blockDim.x) {
+        if (k < nnz) {
+            if (ci1[k] != ci2[k]) atomicExch(differ, 1);
+            tmap[k] = (int)idx2[k];
+        } else if (rp1[k - nnz] != rp2[k - nnz]) {
+            atomicExch(differ, 1);
+        }
+    }
+}
+
+// Values symmetric (bitwise) through the mirror map.
+__global__ void k_compare_mirror(long long nnz, const double *v, const int *tmap, int *differ) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x)
+        if (__double_as_longlong(v[k]) != __double_as_longlong(__ldg(v + tmap[k]))) atomicExch(differ, 1);
+}
+
+// Whether the finest level's current values are symmetric (bitwise), by the
+// mirror map of its fixed pattern (built on first use).
+static int values_symmetric(Hierarchy *h, cudaStream_t s, bool *sym) {
+    Level &L0 = h->L[0];
+    const int n = L0.A.nrows;
+    const long long nnz = L0.A.nnz;
+    if (h->tmap_state == 0) {
+        DevArena tmp;
+        DevCSR I = L0.A, It;
+        int *differ = nullptr;
+        int rc = tmp.alloc(&I.v, (size_t)std::max(1LL, nnz));
+        if (rc == AMG_OK) rc = tmp.alloc(&differ, 1);
+        if (rc == AMG_OK) {
+            k_entry_index<<<grid_for(nnz), 256, 0, s>>>(nnz, I.v);
+            rc = transpose_csr(I, It, tmp, s);
+        }
+        if (rc == AMG_OK) rc = h->arena.alloc(&h->tmap, (size_t)std::max(1LL, nnz));
+        if (rc < 0) {
+            tmp.free_all();
+            return rc;
+        }
+        cudaMemsetAsync(differ, 0, sizeof(int), s);
+        k_mirror_map<<<grid_for(nnz + n + 1), 256, 0, s>>>(n, nnz, L0.A.rp, L0.A.ci, It.rp, It.ci, It.v, h->tmap, differ);
+        int d = 1;
+        cudaMemcpyAsync(&d, differ, sizeof(int), cudaMemcpyDeviceToHost, s);
+        const cudaError_t e = cudaStreamSynchronize(s);
+        tmp.free_all();
+        AMG_CUDA_TRY(e);
+        h->tmap_state = d ? -1 : 1;
+        if (d) {
+            h->arena.release(h->tmap);
+            h->tmap = nullptr;
+        }
+    }
+    if (h->tmap_state < 0) {
+        *sym = false;
+        return AMG_OK;
+    }
+    Scratch sc;
+    int *differ = nullptr;
+    AMG_TRY(sc.alloc(&differ, 1));
+    AMG_CUDA_TRY(cudaMemsetAsync(differ, 0, sizeof(int), s));
+    k_compare_mirror<<<grid_for(nnz), 256, 0, s>>>(nnz, L0.A.v, h->tmap, differ);
+    AMG_LAUNCH_CHECK();
+    int d = 1;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&d, differ, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    *sym = d == 0;
+    return AMG_OK;
+}
+
 int resetup_hierarchy(Hierarchy *h, const double *v_in, cudaStream_t s) {
     const amg_config &cfg = h->cfg;
     const int L = h->nlevels;
@@ -1478,24 +1562,9 @@ int resetup_hierarchy(Hierarchy *h, const double *v_in, cudaStream_t s) {
     AMG_CUDA_TRY(cudaMemcpyAsync(L0.A.v, v_in, sizeof(double) * (size_t)L0.A.nnz, cudaMemcpyDefault, s));
     if (cfg.symmetric < 0) {
         // the detected symmetry fixes the coarsest factor and the adjoint's hierarchy
-        DevArena tmp;
-        DevCSR At;
-        int rc = transpose_csr(L0.A, At, tmp, s);
-        int *differ = nullptr;
-        if (rc == AMG_OK) rc = tmp.alloc(&differ, 1);
-        if (rc < 0) {
-            tmp.free_all();
-            return rc;
-        }
-        cudaMemsetAsync(differ, 0, sizeof(int), s);
-        k_compare_csr<<<grid_for(L0.A.nnz + L0.A.nrows + 1), 256, 0, s>>>(L0.A.nrows, L0.A.nnz, L0.A.rp, L0.A.ci, L0.A.v,
-                                                                          At.rp, At.ci, At.v, differ);
-        int d = 1;
-        cudaMemcpyAsync(&d, differ, sizeof(int), cudaMemcpyDeviceToHost, s);
-        const cudaError_t e = cudaStreamSynchronize(s);
-        tmp.free_all();
-        AMG_CUDA_TRY(e);
-        if ((d ? 0 : 1) != h->symmetric) {
+        bool sym = false;
+        AMG_TRY(values_symmetric(h, s, &sym));
+        if ((sym ? 1 : 0) != h->symmetric) {
             set_last_error("the new values change the matrix's symmetry: set up a new handle");
             return AMG_ERR_ARG;
         }
@@ -1556,8 +1625,8 @@ int resetup_hierarchy(Hierarchy *h, const double *v_in, cudaStream_t s) {
         AMG_CUDA_TRY(cudaMemcpyAsync(An.v, Acn.v, sizeof(double) * (size_t)Acn.nnz, cudaMemcpyDeviceToDevice, s));
         AMG_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    // coarsest inverse
-    {
+    // coarsest inverse (none for unpreconditioned handles)
+    if (h->nc > 0) {
         Level &Lc = h->L[L - 1];
         Scratch sc;
         double *dense;
@@ -1596,7 +1665,7 @@ int resetup_hierarchy(Hierarchy *h, const double *v_in, cudaStream_t s) {
     }
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
     // the collapsed coarse end (in place) and the padded dense copies
-    AMG_TRY(h->nsolve < h->nlevels ? collapse_coarse(h, s) : pad_dense(h, s));
+    if (h->nc > 0) AMG_TRY(h->nsolve < h->nlevels ? collapse_coarse(h, s) : pad_dense(h, s));
     // the sliced-ELL plans' slot-order copies of the new values
     return ell_refresh(h, s);
 }

@@ -2454,6 +2454,10 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
 }
 
 int vcycle_apply(Hierarchy *h, Workspace &W, const double *r, double *z, cudaStream_t s) {
+    if (h->nc == 0) {
+        set_last_error("amg_vcycle: the handle was set up for an unpreconditioned solver (no hierarchy)");
+        return AMG_ERR_UNSUPPORTED;
+    }
     AMG_TRY(set_control(W, s, 0, AMG_OK, 0, h->cfg.max_iter, 1));
     return vcycle(h, W, r, z, FIN_NONE, s);
 }

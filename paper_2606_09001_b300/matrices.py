@@ -309,3 +309,13 @@ def convdiff3d_upwind(seed: int = SEED_BASE + 4, N: int = 160, peclet=(10.0, 5.0
     A = convection_diffusion_upwind(N, peclet)
     b = rng.uniform(-1.0, 1.0, size=A.n)
     return Workload(f"convdiff3d_upwind_{N}^3", A, b, {"N": N, "peclet": peclet})
+
+
+def tridiagonal_1e7(n: int = 10**7, diagonal_value: float = 4.0) -> Workload:
+    """The well-conditioned Toeplitz system the paper times its unpreconditioned
+    CG and BiCGStab on (Sec. 4, Fig. 2): tridiag(-1, d, -1) with n = 10^7 and
+    b = ones; d = 4 is the example's true diagonal (Sec. 3.2), recovered from
+    d = 10 by the optimisation loop."""
+    A = tridiagonal_matrix(n, diagonal_value)
+    return Workload(f"tridiagonal_{n}", A, rhs_ones(n), {"diag": diagonal_value, "init_diag": 10.0})
+

@@ -5,6 +5,7 @@ and the solves, adjoints, cache and autograd paths built on it."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
+import scipy.sparse.linalg  # noqa: F401  (sp.linalg)
 import torch
 
 import oracle as O
@@ -167,3 +168,28 @@ def test_autograd_interleaved_forwards_use_their_own_values():
     (xb ** 2).sum().backward()
     assert torch.linalg.norm(g_interleaved - v0b.grad) <= 1e-6 * torch.linalg.norm(v0b.grad)
     del x1
+
+
+@pytest.mark.parametrize("solver", ["CG", "BICGSTAB_NOPREC"])
+def test_unpreconditioned_handle_keeps_the_finest_level_only(solver):
+    """An unpreconditioned solver's handle builds no coarse levels: one level,
+    no V-cycle to export, and a re-setup that only takes the new values."""
+    A0 = M.tridiagonal_matrix(5000, 4.0)
+    A1 = M.tridiagonal_matrix(5000, 3.0)
+    s = gpu_solver(A0, {"solver": solver})
+    assert s.info().nlevels == 1
+    L = _lib.load()
+    r = dev(np.ones(A0.n))
+    z = torch.empty_like(r)
+    assert L.amg_vcycle(s._h, r.data_ptr(), z.data_ptr(), None) == _lib.AMG_ERR_UNSUPPORTED
+    b = np.random.default_rng(5).uniform(-1, 1, A1.n)
+    s.resetup(dev(A1.values))
+    x, info = s.solve(dev(b))
+    _, io = O.Hierarchy(A1, {"solver": _lib.SOLVERS[solver]}).solve(b)
+    A1s = sp.csr_matrix((A1.values, A1.col_idx, A1.row_ptr), shape=(A1.n, A1.n))
+    xt = sp.linalg.spsolve(A1s.tocsc(), b)
+    assert info.status == 0 and info.rel_res_true <= 1e-8
+    assert abs(info.iters - io.iters) <= 2, (info.iters, io.iters)
+    assert np.linalg.norm(x.cpu().numpy() - xt) <= 1e-7 * np.linalg.norm(xt)
+    lam, dA, ainfo = s.adjoint(x, dev(np.ones(A1.n)))
+    assert ainfo.status == 0 and ainfo.rel_res_true <= 1e-8
