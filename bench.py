@@ -249,24 +249,35 @@ def run_reference(args):
 # Our arm
 # ---------------------------------------------------------------------------
 
-def load_traffic(kernel: str):
-    """DRAM traffic per launch of `kernel` from the committed ncu summary, if
-    it was taken on the current kernel source."""
+KERNEL_SOURCES = ("solve.cu", "stream.cuh", "amg_common.cuh")
+
+
+def kernel_src_digest() -> str:
+    """Digest of the streaming kernels' sources: a traffic figure taken on
+    other sources is not used."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2606_09001_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(workload: str, kernel: str):
+    """DRAM traffic per launch of `kernel` on `workload` from the committed ncu
+    summary, if it was taken on the current kernel sources."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(path))
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_2606_09001_b300", "csrc", "solve.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    ent = d.get(kernel)
-    if not ent or ent.get("solve_cu_sha256_16") != digest:
+    ent = d.get(workload, {}).get(kernel)
+    if not ent or ent.get("kernel_src_sha256_16") != kernel_src_digest():
         return None
     return ent.get("bytes_per_launch_full")
 
 
-def trace_pass(s, b, x, g, lam, dA, steps, dev, step=None):
+def trace_pass(s, b, x, g, lam, dA, steps, dev, step=None, workload: str = ""):
     """Per-kernel CUDA-event trace of solve + adjoint steps (separate from the
     timed region); returns (roofline, kernel table, V-cycle bytes, V-cycle ms)."""
     import torch
@@ -297,7 +308,7 @@ def trace_pass(s, b, x, g, lam, dA, steps, dev, step=None):
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                 "bytes_per_launch": top["bytes"] / top["launches"], "ms_per_launch": top["ms"] / top["launches"],
-                "share_of_traced_time": top["ms"] / tot_ms, "traffic": load_traffic(top_name)}
+                "share_of_traced_time": top["ms"] / tot_ms, "traffic": load_traffic(workload, top_name)}
     by_level = {}
     for r in recs:
         key = r["level"] if r["name"] in vc_names else "outer"
@@ -438,7 +449,8 @@ def run_ours(args):
     # per-kernel trace of the headline form (a separate pass of the same steps)
     roofline, kernels, vc_bytes, vc_ms = None, None, 0.0, 0.0
     if not args.no_trace:
-        roofline, kernels, vc_bytes, vc_ms = trace_pass(solvers[primary], b, x, g, lam, dA, args.steps, dev)
+        roofline, kernels, vc_bytes, vc_ms = trace_pass(solvers[primary], b, x, g, lam, dA, args.steps, dev,
+                                                        workload=args.workload)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -635,7 +647,7 @@ def run_batched(args, world, rank, dev, barrier):
     if not args.no_trace:
         sp = solvers[primary]
         roofline, kernels, vc_bytes, vc_ms = trace_pass(sp, None, None, None, None, None, args.steps, dev,
-                                                        step=lambda: sp.solve(B, X, info=False))
+                                                        step=lambda: sp.solve(B, X, info=False), workload=args.workload)
     e2e = None
     if not args.no_e2e:
         s = solvers[primary]

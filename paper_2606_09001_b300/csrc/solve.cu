@@ -325,9 +325,10 @@ __global__ void __launch_bounds__(BLOCK) k_dense_apply(int m, int ld, const TMAT
 // ---------------------------------------------------------------------------
 
 // PCG start: x = 0, r = b, p = 0, ||b||^2.
+// cg: unpreconditioned CG, whose r.z is r.r (b.b here) with no beta pass.
 __global__ void __launch_bounds__(BLOCK) k_pcg_init(int n, const double *__restrict__ b, double *x, double *r,
                                                     double *p, double *rold, float *r32, DevScalars *sc, double rtol,
-                                                    double *part, int cap, unsigned *counter) {
+                                                    double *part, int cap, unsigned *counter, int cg) {
     pdl_wait();
     pdl_trigger();
     double acc[1] = {0.0};
@@ -348,6 +349,10 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(int n, const double *__restr
         sc->iters = 0;
         sc->beta = 0.0;
         sc->first = 1;
+        if (cg) {
+            sc->rz = tot[0];
+            sc->first = 0;
+        }
         sc->status = AMG_OK;
         sc->done = 0;
         if (!finite(tot[0])) fail(sc, AMG_NAN);
@@ -436,7 +441,8 @@ __global__ void __launch_bounds__(BLOCK) k_spmv_fin(int n, const int *__restrict
 // x += alpha p; (r_old = r;) r -= alpha q; ||r||^2; convergence / iteration cap.
 __global__ void __launch_bounds__(BLOCK) k_pcg_update(int n, double *x, double *r, const double *__restrict__ p,
                                                       const double *__restrict__ q, double *rold, float *r32,
-                                                      DevScalars *sc, double *part, int cap, unsigned *counter) {
+                                                      DevScalars *sc, double *part, int cap, unsigned *counter,
+                                                      int cg) {
     pdl_wait();
     pdl_trigger();
     if (sc->done) return;
@@ -455,6 +461,11 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(int n, double *x, double *
     if (reduce_last<1>(acc, part, cap, counter, tot) && threadIdx.x == 0) {
         sc->iters += 1;
         sc->rr = tot[0];
+        if (cg) {
+            // unpreconditioned CG: z = r, so the next beta is ||r_new||^2 / ||r||^2
+            sc->beta = tot[0] / sc->rz;
+            sc->rz = tot[0];
+        }
         if (!finite(tot[0])) fail(sc, AMG_NAN);
         else if (tot[0] <= sc->tol2) sc->done = 1;
         else if (sc->iters >= sc->max_iter) fail(sc, AMG_MAXIT);
@@ -613,18 +624,6 @@ __global__ void __launch_bounds__(BLOCK) k_grad_values(int n, const int *__restr
     ROW_LOOP_END
 }
 
-// Unpreconditioned CG: z is r itself; beta comes from r.r.
-__global__ void __launch_bounds__(BLOCK) k_cg_beta(int n, const double *__restrict__ r, DevScalars *sc, double *part,
-                                                   int cap, unsigned *counter) {
-    pdl_wait();
-    pdl_trigger();
-    if (sc->done) return;
-    double acc[2] = {0.0, 0.0};
-    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) acc[0] += r[i] * r[i];
-    double tot[2];
-    if (reduce_last<2>(acc, part, cap, counter, tot) && threadIdx.x == 0) finish_pcg_beta(sc, tot);
-}
-
 // Host-chosen control fields of the device scalars.
 __global__ void k_set_control(DevScalars *sc, int done, int status, int flexible, int max_iter, int reset_iters) {
     pdl_wait();
@@ -640,9 +639,17 @@ __global__ void k_set_control(DevScalars *sc, int done, int status, int flexible
 }
 
 // The next preconditioner application starts a new recursion (beta = 0, p = z).
-__global__ void k_pcg_restart(DevScalars *sc) {
+__global__ void k_pcg_restart(DevScalars *sc, int cg) {
     pdl_wait();
-    pdl_trigger(); sc->first = 1; }
+    pdl_trigger();
+    if (cg) {  // unpreconditioned CG: p = r, r.z = ||r||^2 of the true residual
+        sc->beta = 0.0;
+        sc->rz = sc->tr;
+        sc->first = 0;
+    } else {
+        sc->first = 1;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Tracing
@@ -1562,17 +1569,16 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &
     cudaEvent_t e0, e1;
     AMG_CUDA_TRY(cudaEventCreate(&e0));
     AMG_CUDA_TRY(cudaEventCreate(&e1));
-    // cands[0] is the heuristic plan; another candidate must beat it by 3 %.
-    // A pass whose finisher stops the scalars (a p.Ap <= 0 on these
-    // operands) is timed as y = M x instead.
-    float base_ms = 0.f, best = 1e30f;
+    // Among the candidates within 3 % of the fastest (the trials' noise), the
+    // first by layout -- sliced-ELL, windowed, CSR -- then by candidate order
+    // is kept, so near-ties resolve the same way in every run.  A pass whose
+    // finisher stops the scalars (a p.Ap <= 0 on these operands) is timed as
+    // y = M x instead.
+    std::vector<float> times(cands.size(), 1e30f);
     StreamPlan chosen = pl;
     int rc = AMG_OK;
     for (int pass = 0; pass < 2 && rc >= 0; ++pass) {
         bool stopped_any = false;
-        base_ms = 0.f;
-        best = 1e30f;
-        chosen = pl;
         for (size_t ci_ = 0; ci_ < cands.size() && !stopped_any; ++ci_) {
             const StreamPlan &c = cands[ci_];
             if ((rc = cudaMemsetAsync(tsc, 0, sizeof(DevScalars), s) == cudaSuccess ? AMG_OK : AMG_ERR_CUDA) < 0) break;
@@ -1599,14 +1605,18 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &
                 break;
             }
             stopped_any = stopped != 0;
-            if (ci_ == 0) base_ms = ms;
-            if (ms < best && (ci_ == 0 || ms < 0.97f * base_ms)) {
-                best = ms;
-                chosen = c;
-            }
+            times[ci_] = ms;
         }
         if (rc < 0 || !stopped_any || kind == TUNE_SPMV) break;
         kind = TUNE_SPMV;  // time every candidate again as y = M x
+    }
+    if (rc >= 0) {
+        const float fastest = *std::min_element(times.begin(), times.end());
+        auto rank = [](const StreamPlan &p) { return p.ell ? 0 : p.c16 ? 1 : 2; };
+        int pick = -1;
+        for (size_t q = 0; q < cands.size(); ++q)
+            if (times[q] <= 1.03f * fastest && (pick < 0 || rank(cands[q]) < rank(cands[pick]))) pick = (int)q;
+        if (pick >= 0) chosen = cands[pick];
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2228,7 +2238,7 @@ static int pcg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
         TRACE("pcg_update", 0, (mixed ? 56.0 : 48.0) * n);
         AMG_TRY(launch_k(k_pcg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, W.r, W.p, W.q, mixed ? W.rold : nullptr,
                          mixed ? W.r32 : nullptr, W.scal,
-                                                           W.part, cap, W.counter));
+                                                           W.part, cap, W.counter, 0));
     }
     AMG_LAUNCH_CHECK();
     return AMG_OK;
@@ -2237,10 +2247,6 @@ static int pcg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
 static int cg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
     const int n = h->n, cap = W.part_cap;
     {
-        TRACE("cg_beta", 0, 8.0 * n);
-        AMG_TRY(launch_k(k_cg_beta, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.scal, W.part, cap, W.counter));
-    }
-    {
         TRACE("pcg_p", 0, 24.0 * n);
         AMG_TRY(launch_k(k_pcg_p, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.p, W.scal));
     }
@@ -2248,7 +2254,7 @@ static int cg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
     {
         TRACE("pcg_update", 0, 48.0 * n);
         AMG_TRY(launch_k(k_pcg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, W.r, W.p, W.q, nullptr, nullptr, W.scal,
-                         W.part, cap, W.counter));
+                         W.part, cap, W.counter, 1));
     }
     AMG_LAUNCH_CHECK();
     return AMG_OK;
@@ -2371,8 +2377,8 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
                                                               cap, W.counter));
         else
             AMG_TRY(launch_k(k_pcg_init, stream_grid(n, cap), BLOCK, 0, s, n, W.b, W.x, W.r, W.p, W.rold,
-                             c.precision == AMG_PRECISION_MIXED ? W.r32 : nullptr, W.scal, c.rtol, W.part,
-                                                             cap, W.counter));
+                             c.precision == AMG_PRECISION_MIXED ? W.r32 : nullptr, W.scal, c.rtol, W.part, cap,
+                             W.counter, precond ? 0 : 1));
     }
     AMG_LAUNCH_CHECK();
     AMG_TRY(read_scalars(W, s));
@@ -2432,7 +2438,7 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
         } else {
             AMG_TRY(set_control(W, s, 0, AMG_OK, flexible, c.max_iter, 0));
             TRACE("control", 0, 0.0);
-            AMG_TRY(launch_k(k_pcg_restart, 1, 1, 0, s, W.scal));
+            AMG_TRY(launch_k(k_pcg_restart, 1, 1, 0, s, W.scal, precond ? 0 : 1));
             AMG_LAUNCH_CHECK();
         }
     }
