@@ -49,7 +49,7 @@ class _Config(C.Structure):
     _fields_ = [("solver", C.c_int), ("smoother", C.c_int), ("omega", C.c_double),
                 ("theta", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
                 ("rtol", C.c_double), ("max_iter", C.c_int), ("max_restarts", C.c_int),
-                ("symmetric", C.c_int)]
+                ("symmetric", C.c_int), ("adjoint_reuse", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -85,6 +85,8 @@ def lib():
             L.or_setup.restype = C.c_void_p
             L.or_resetup.argtypes = [C.c_void_p, _f64p, C.POINTER(C.c_int)]
             L.or_resetup.restype = C.c_void_p
+            L.or_transposed.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+            L.or_transposed.restype = C.c_void_p
             L.or_hier_free.argtypes = [C.c_void_p]
             L.or_hier_nlevels.argtypes = [C.c_void_p]
             L.or_hier_symmetric.argtypes = [C.c_void_p]
@@ -223,6 +225,21 @@ class Hierarchy:
         st = C.c_int()
         v = np.ascontiguousarray(values, dtype=np.float64)
         h = lib().or_resetup(self._h, v, C.byref(st))
+        if not h:
+            raise OracleError(st.value)
+        out = Hierarchy.__new__(Hierarchy)
+        out._cfg = self._cfg
+        out._h = C.c_void_p(h)
+        out.status = st.value
+        out.n = self.n
+        return out
+
+    def transposed(self) -> "Hierarchy":
+        """The hierarchy of A^T that keeps this one's aggregates, P and R and
+        transposes every level operator (the adjoint's hierarchy with
+        adjoint_reuse)."""
+        st = C.c_int()
+        h = lib().or_transposed(self._h, C.byref(st))
         if not h:
             raise OracleError(st.value)
         out = Hierarchy.__new__(Hierarchy)

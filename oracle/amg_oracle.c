@@ -59,6 +59,7 @@ typedef struct {
     int max_iter;     /* default 500 */
     int max_restarts; /* true-residual restarts, default 3 */
     int symmetric;    /* -1 detect, 0 no, 1 yes */
+    int adjoint_reuse; /* nonsymmetric adjoint: 0 sets up a hierarchy of A^T, 1 transposes A's (or_transposed) */
 } or_config;
 
 typedef struct {
@@ -660,6 +661,7 @@ void or_config_default(or_config *c) {
     c->max_iter = 500;
     c->max_restarts = 3;
     c->symmetric = -1;
+    c->adjoint_reuse = 0;
 }
 
 /* Symmetric = pattern symmetric and values bitwise equal. */
@@ -787,6 +789,56 @@ or_hier *or_resetup(const or_hier *old, const double *v, int *status) {
         for (int k = Ac->rp[i]; k < Ac->rp[i + 1]; ++k) h->dense[i * m + Ac->ci[k]] = Ac->v[k];
     st = h->symmetric ? dense_cholesky(h->dense, m) : dense_lu(h->dense, h->piv, m);
     if (st) { *status = st; or_hier_free(h); return NULL; }
+    *status = OR_OK;
+    return h;
+}
+
+/* The hierarchy of A^T that reuses A's: the same aggregates, P and R = P^T,
+ * with every level operator the transpose of A's.  Since R = P^T, the
+ * transpose of A's Galerkin product is the Galerkin product of the
+ * transposed operator, R A_l^T P = (R A_l P)^T = A_{l+1}^T, so this is a
+ * smoothed-aggregation-style hierarchy of A^T without a second setup (reusing
+ * P, which was smoothed with A rather than A^T, is the reading).  Smoother
+ * weights come from the transposed operators (the same diagonal; column sums
+ * for L1-Jacobi); the coarsest level is factored by LU. */
+or_hier *or_transposed(const or_hier *f, int *status) {
+    or_hier *h = (or_hier *)calloc(1, sizeof(or_hier));
+    if (!h) { *status = OR_ERR_OOM; return NULL; }
+    h->cfg = f->cfg;
+    h->symmetric = 0;
+    const int L = f->nlevels;
+    int st;
+    for (int l = 0; l < L; ++l) {
+        if ((st = csr_transpose(&f->A[l], &h->A[l]))) { *status = st; or_hier_free(h); return NULL; }
+        h->dinv[l] = smoother_weights(&h->A[l], &h->cfg);
+        if (!h->dinv[l]) { *status = OR_ERR_OOM; or_hier_free(h); return NULL; }
+        if (l == L - 1) break;
+        const int n = f->A[l].nrows;
+        const ocsr *P = &f->P[l], *R = &f->R[l];
+        h->agg[l] = (int *)malloc((size_t)n * sizeof(int));
+        if (!h->agg[l] || csr_alloc(&h->P[l], P->nrows, P->ncols, P->nnz) ||
+            csr_alloc(&h->R[l], R->nrows, R->ncols, R->nnz)) {
+            *status = OR_ERR_OOM; or_hier_free(h); return NULL;
+        }
+        memcpy(h->agg[l], f->agg[l], (size_t)n * sizeof(int));
+        memcpy(h->P[l].rp, P->rp, ((size_t)P->nrows + 1) * sizeof(int));
+        memcpy(h->P[l].ci, P->ci, (size_t)P->nnz * sizeof(int));
+        memcpy(h->P[l].v, P->v, (size_t)P->nnz * sizeof(double));
+        memcpy(h->R[l].rp, R->rp, ((size_t)R->nrows + 1) * sizeof(int));
+        memcpy(h->R[l].ci, R->ci, (size_t)R->nnz * sizeof(int));
+        memcpy(h->R[l].v, R->v, (size_t)R->nnz * sizeof(double));
+        h->rho[l] = f->rho[l];
+    }
+    h->nlevels = L;
+    const ocsr *Ac = &h->A[L - 1];
+    const int m = Ac->nrows;
+    h->nc = m;
+    h->dense = (double *)calloc((size_t)m * m, sizeof(double));
+    h->piv = (int *)malloc((size_t)m * sizeof(int));
+    if (!h->dense || !h->piv) { *status = OR_ERR_OOM; or_hier_free(h); return NULL; }
+    for (int i = 0; i < m; ++i)
+        for (int k = Ac->rp[i]; k < Ac->rp[i + 1]; ++k) h->dense[i * m + Ac->ci[k]] = Ac->v[k];
+    if ((st = dense_lu(h->dense, h->piv, m))) { *status = st; or_hier_free(h); return NULL; }
     *status = OR_OK;
     return h;
 }
@@ -1035,12 +1087,17 @@ int or_solve(const or_hier *h, const double *b, double *x, or_info *info) {
 
 /* lambda solves A^T lambda = g with the same solver and configuration; for a
  * symmetric A the forward hierarchy is reused, otherwise a hierarchy is set
- * up on A^T (once, kept with the handle).  dL/dA on the stored pattern:
+ * up on A^T (once, kept with the handle), or with adjoint_reuse the
+ * transposed hierarchy of or_transposed.  dL/dA on the stored pattern:
  * dA_k = -lambda_{row(k)} x_{col(k)};  dL/db = lambda. */
 int or_adjoint(or_hier *h, const double *x, const double *g, double *lambda, double *dA, or_info *info) {
     const or_hier *hs = h;
     if (!h->symmetric) {
-        if (!h->adj) {
+        if (!h->adj && h->cfg.adjoint_reuse) {
+            int st;
+            h->adj = or_transposed(h, &st);
+            if (!h->adj) return st;
+        } else if (!h->adj) {
             ocsr At;
             if (csr_transpose(&h->A[0], &At)) return OR_ERR_OOM;
             or_config c = h->cfg;

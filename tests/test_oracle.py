@@ -581,3 +581,71 @@ def test_resetup_new_coefficients_keeps_structure_and_is_galerkin():
     x, info = hr.solve(b)
     assert info.status == 0
     assert np.linalg.norm(to_sp(Anew) @ x - b) <= 1e-8 * np.linalg.norm(b) * 1.0001
+
+
+# ---------------------------------------------------------------------------
+# Transposed-hierarchy reuse for the nonsymmetric adjoint
+# ---------------------------------------------------------------------------
+
+def test_transposed_hierarchy_is_exact_transpose_and_galerkin_for_At():
+    """or_transposed keeps A's aggregates, P and R and transposes every level
+    operator exactly; since R = P^T each transposed level is the Galerkin
+    product of the level above it with A's P (dense check)."""
+    A = M.convection_diffusion_upwind(10)
+    h = O.Hierarchy(A, {"solver": 1, "coarse_max": 16})
+    t = h.transposed()
+    assert t.nlevels == h.nlevels >= 3 and not t.symmetric
+    for l in range(h.nlevels):
+        a, b = h.level(l), t.level(l)
+        n = a.A.n
+        Ad = lvl_sp(a.A, n).toarray()
+        assert np.array_equal(lvl_sp(b.A, n).toarray(), Ad.T)  # bit for bit
+        if l < h.nlevels - 1:
+            assert np.array_equal(b.agg, a.agg)
+            for X, Y in ((a.P, b.P), (a.R, b.R)):
+                assert np.array_equal(X.row_ptr, Y.row_ptr) and np.array_equal(X.col_idx, Y.col_idx)
+                assert np.array_equal(X.values, Y.values)
+            nc = h.level(l + 1).A.n
+            P = lvl_sp(a.P, nc).toarray()
+            Gal = P.T @ Ad.T @ P
+            At_next = lvl_sp(t.level(l + 1).A, nc).toarray()
+            assert np.abs(At_next - Gal).max() <= 1e-13 * np.abs(Gal).max()
+
+
+def test_transposed_hierarchy_of_symmetric_matrix_gives_the_same_cycle():
+    """For a symmetric A the finest transposed level is A itself and the coarse
+    ones equal A's up to the rounding of their Galerkin sums (which are
+    symmetric in exact arithmetic only), so the cycle is A's up to rounding
+    and the coarsest factor (LU in place of Cholesky)."""
+    A = M.poisson2d(30)
+    h = O.Hierarchy(A)
+    t = h.transposed()
+    assert np.array_equal(t.level(0).A.values, h.level(0).A.values)
+    for l in range(1, h.nlevels):
+        a, b = h.level(l).A.values, t.level(l).A.values
+        assert np.array_equal(t.level(l).A.col_idx, h.level(l).A.col_idx)
+        assert np.abs(b - a).max() <= 1e-14 * np.abs(a).max()
+    r = np.random.default_rng(2).uniform(-1, 1, A.n)
+    z, zt = h.vcycle(r), t.vcycle(r)
+    assert np.linalg.norm(zt - z) <= 1e-12 * np.linalg.norm(z)
+
+
+def test_adjoint_reuse_solves_the_transposed_system():
+    """With adjoint_reuse the adjoint solve runs BiCGStab on A^T with the
+    transposed hierarchy: lambda satisfies A^T lambda = g to the tolerance and
+    agrees with the adjoint of a hierarchy set up on A^T."""
+    A = M.convection_diffusion_upwind(12)
+    rng = np.random.default_rng(4)
+    b, g = rng.uniform(-1, 1, A.n), rng.uniform(-1, 1, A.n)
+    At = to_sp(A).T.tocsr()
+    lams = []
+    for reuse in (0, 1):
+        h = O.Hierarchy(A, {"solver": 1, "adjoint_reuse": reuse, "rtol": 1e-12})
+        x, _ = h.solve(b)
+        lam, dA, info = h.adjoint(x, g, A.nnz)
+        assert info.status == 0
+        assert np.linalg.norm(At @ lam - g) <= 1e-12 * np.linalg.norm(g) * 1.0001
+        rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+        assert np.array_equal(dA, -(lam[rows] * x[A.col_idx]))
+        lams.append(lam)
+    assert np.linalg.norm(lams[1] - lams[0]) <= 1e-9 * np.linalg.norm(lams[0])
