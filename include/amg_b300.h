@@ -104,6 +104,9 @@ typedef struct {
     int symmetric;    /* -1 detect (pattern symmetric and values bitwise equal), 0 no, 1 yes; default -1 */
     int layout;       /* AMG_LAYOUT_*: restricts the timed trial to one tile layout (an operator that
                          layout does not fit keeps the CSR layout); default AMG_LAYOUT_AUTO */
+    int adjoint_reuse; /* adjoint of a nonsymmetric A: 0 sets up a hierarchy of A^T of its own (as
+                          Sec. 2.1 describes; default); 1 reuses A's aggregates, P and R = P^T with
+                          every level operator transposed (R A_l^T P = A_{l+1}^T), no second setup */
 } amg_config;
 
 typedef struct {

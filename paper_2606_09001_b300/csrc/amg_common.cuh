@@ -210,6 +210,9 @@ struct Hierarchy {
     // (tmap_state 1), built at the first re-setup; -1: pattern nonsymmetric.
     int *tmap = nullptr;
     int tmap_state = 0;
+    // set for the adjoint's hierarchy that reuses a forward hierarchy's
+    // aggregates and prolongators (it shares their arrays)
+    const Hierarchy *transposed_of = nullptr;
     // copies of the dense operator with rows padded to nc_ld entries (a
     // multiple of 4, zero-filled) for 16-byte vector loads
     int nc_ld = 0;
@@ -268,6 +271,10 @@ int tail_prepare(Hierarchy *h, cudaStream_t s);
 // Numeric re-setup: new values on the same pattern, the structure (aggregates,
 // every sparsity pattern, plans) kept and every value recomputed in place.
 int resetup_hierarchy(Hierarchy *h, const double *values, cudaStream_t s);
+// The adjoint's hierarchy of A^T reusing h's aggregates and prolongators, and
+// its refresh after a re-setup of h.
+int build_transposed_hierarchy(Hierarchy *ht, const Hierarchy *h, cudaStream_t s);
+int refresh_transposed_hierarchy(Hierarchy *ht, const Hierarchy *h, cudaStream_t s);
 // Lays the sliced-ELL plans' value arrays out again from the CSR values
 // (after a numeric re-setup).
 int ell_refresh(Hierarchy *h, cudaStream_t s);

@@ -33,7 +33,8 @@ int check_config(const amg_config &c) {
     if (c.solver < 0 || c.solver > 3 || (c.smoother != 0 && c.smoother != 1) || !(c.omega > 0.0) ||
         !(c.theta >= 0.0) || c.coarse_max < 1 || c.max_levels < 1 || c.max_levels > AMG_MAX_LEVELS ||
         !(c.rtol > 0.0) || c.max_iter < 1 || c.max_restarts < 0 || (c.precision != 0 && c.precision != 1) ||
-        c.symmetric < -1 || c.symmetric > 1 || c.layout < AMG_LAYOUT_AUTO || c.layout > AMG_LAYOUT_SLICED_ELL) {
+        c.symmetric < -1 || c.symmetric > 1 || c.layout < AMG_LAYOUT_AUTO || c.layout > AMG_LAYOUT_SLICED_ELL ||
+        (c.adjoint_reuse != 0 && c.adjoint_reuse != 1)) {
         set_last_error("invalid amg_config");
         return AMG_ERR_ARG;
     }
@@ -157,6 +158,7 @@ int amg_config_default(amg_config *c) {
     c->precision = AMG_PRECISION_FP64;
     c->symmetric = -1;
     c->layout = AMG_LAYOUT_AUTO;
+    c->adjoint_reuse = 0;
     return AMG_OK;
 }
 
@@ -226,13 +228,20 @@ int amg_adjoint(amg_handle h, const double *x, const double *g, double *lambda, 
     Hierarchy *H = &h->H;
     if (!h->H.symmetric) {
         if (!h->HT) {
-            // A^T: transpose on the device, then a full setup of its own
+            // A^T: transpose on the device, then a full setup of its own, or
+            // (adjoint_reuse, preconditioned solvers) the transpose of A's hierarchy
             Hierarchy *HT = new (std::nothrow) Hierarchy();
             if (!HT) return AMG_ERR_OOM;
             DevArena tmp;
             DevCSR At;
-            int rc = transpose_csr(h->H.L[0].A, At, tmp, h->s);
-            if (rc == AMG_OK) {
+            const bool reuse = h->H.cfg.adjoint_reuse && h->H.nc > 0;
+            int rc = reuse ? AMG_OK : transpose_csr(h->H.L[0].A, At, tmp, h->s);
+            if (rc == AMG_OK && reuse) {
+                const auto t0 = clk::now();
+                rc = build_transposed_hierarchy(HT, &h->H, h->s);
+                if (rc == AMG_OK) rc = autotune_plans(HT, h->W.scal, h->s);
+                HT->setup_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+            } else if (rc == AMG_OK) {
                 HT->cfg = h->H.cfg;
                 HT->cfg.symmetric = 0;
                 HT->n = n;
@@ -401,7 +410,10 @@ int amg_resetup(amg_handle h, const double *values, void *cuda_stream) {
     AMG_TRY(enter(h, cuda_stream));
     const auto t0 = clk::now();
     int rc = resetup_hierarchy(&h->H, values, h->s);
-    if (rc == AMG_OK && h->HT) {
+    if (rc == AMG_OK && h->HT && h->HT->transposed_of) {
+        // the transposed hierarchy follows A's: its operators are transposed again
+        rc = refresh_transposed_hierarchy(h->HT, &h->H, h->s);
+    } else if (rc == AMG_OK && h->HT) {
         // the cached hierarchy of A^T follows: its values are the transpose of the new ones
         DevArena tmp;
         DevCSR At;

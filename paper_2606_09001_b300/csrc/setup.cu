@@ -908,6 +908,100 @@ static int choose_vec(long long nnz, int nrows) {
 
 static int collapse_coarse(Hierarchy *h, cudaStream_t s);
 
+// The part of a setup after the levels' operators exist (levels 0 ..
+// h->nlevels - 1 with A, and P, R, agg, w on all but the last): the coarsest
+// dense factor and inverse, FP32 copies, work vectors, streaming plans, the
+// collapsed coarse end and the fused tail.
+static int finish_build(Hierarchy *h, bool precond, cudaStream_t s) {
+    const amg_config &cfg = h->cfg;
+    DevArena &ar = h->arena;
+
+    // ---- coarsest level: dense factor + inverse ----
+    const int l = h->nlevels - 1;
+    Level &Lc = h->L[l];
+    h->nc = precond ? Lc.A.nrows : 0;
+    if (h->nc > AMG_DENSE_MAX) {
+        set_last_error("coarsening stopped at level %d with %d rows (> %d)", l, h->nc, AMG_DENSE_MAX);
+        return AMG_ERR_STALL;
+    }
+    if (precond) {
+        Scratch sc;
+        double *dense;
+        int *piv, *st;
+        const int m = h->nc;
+        AMG_TRY(sc.alloc(&dense, (size_t)m * m));
+        AMG_TRY(sc.alloc(&piv, (size_t)m));
+        AMG_TRY(sc.alloc(&st, 1));
+        AMG_TRY(ar.alloc(&h->cinv, (size_t)m * m));
+        h->cinv_last = h->cinv;
+        k_csr_to_dense<<<1, 256, 0, s>>>(m, Lc.A.rp, Lc.A.ci, Lc.A.v, dense);
+        k_dense_factor_inverse<<<1, 256, 0, s>>>(m, h->symmetric, dense, piv, h->cinv, st);
+        AMG_LAUNCH_CHECK();
+        int hst = -1;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hst != AMG_OK) {
+            set_last_error("coarsest level (%d rows) is not %s", m, h->symmetric ? "SPD" : "invertible");
+            return AMG_NOT_SPD;
+        }
+    }
+
+    // ---- FP32 copies, work vectors, launch shapes ----
+    const bool mixed = cfg.precision == AMG_PRECISION_MIXED;
+    for (int k = 0; k < h->nlevels; ++k) {
+        Level &Lv = h->L[k];
+        const int nl = Lv.A.nrows;
+        const bool last = k == h->nlevels - 1;
+        Lv.vec_a = choose_vec(Lv.A.nnz, nl);
+        if (!last) {
+            Lv.vec_p = choose_vec(Lv.P.nnz, nl);
+            Lv.vec_r = choose_vec(Lv.R.nnz, Lv.R.nrows);
+        }
+        AMG_TRY(ar.alloc(&Lv.t, (size_t)nl));
+        if (k > 0) {
+            AMG_TRY(ar.alloc(&Lv.b, (size_t)nl));
+            AMG_TRY(ar.alloc(&Lv.x, (size_t)nl));
+        }
+        const int cap = 4096;  // stage capacity (stream::CAP)
+        if (k == 0) AMG_TRY(plan_stream(Lv.A, cap, Lv.sa64, s));
+        if (!last) {
+            AMG_TRY(plan_stream(Lv.A, cap, Lv.sa, s));
+            Lv.sa_post = Lv.sa;
+            AMG_TRY(plan_stream(Lv.P, cap, Lv.sp, s));
+            AMG_TRY(plan_stream(Lv.R, cap, Lv.sr, s));
+            AMG_TRY(ar.alloc(&Lv.ahat, (size_t)std::max(1LL, Lv.A.nnz)));
+            if (mixed) AMG_TRY(ar.alloc(&Lv.ahat32, (size_t)std::max(1LL, Lv.A.nnz)));
+            k_scale_cols<<<grid_for(nl), 256, 0, s>>>(nl, Lv.A.rp, Lv.A.ci, Lv.A.v, Lv.w, Lv.ahat, Lv.ahat32);
+            AMG_LAUNCH_CHECK();
+        }
+        if (mixed) {
+            AMG_TRY(ar.alloc(&Lv.A.v32, (size_t)std::max(1LL, Lv.A.nnz)));
+            k_to_f32<<<grid_for(Lv.A.nnz), 256, 0, s>>>(Lv.A.v, Lv.A.v32, Lv.A.nnz);
+            AMG_TRY(ar.alloc(&Lv.w32, (size_t)nl));
+            k_to_f32<<<grid_for(nl), 256, 0, s>>>(Lv.w, Lv.w32, nl);
+            if (!last) {
+                AMG_TRY(ar.alloc(&Lv.P.v32, (size_t)std::max(1LL, Lv.P.nnz)));
+                k_to_f32<<<grid_for(Lv.P.nnz), 256, 0, s>>>(Lv.P.v, Lv.P.v32, Lv.P.nnz);
+                AMG_TRY(ar.alloc(&Lv.R.v32, (size_t)std::max(1LL, Lv.R.nnz)));
+                k_to_f32<<<grid_for(Lv.R.nnz), 256, 0, s>>>(Lv.R.v, Lv.R.v32, Lv.R.nnz);
+            }
+            AMG_LAUNCH_CHECK();
+            AMG_TRY(ar.alloc(&Lv.t32, (size_t)nl));
+            if (k > 0) {
+                AMG_TRY(ar.alloc(&Lv.b32, (size_t)nl));
+                AMG_TRY(ar.alloc(&Lv.x32, (size_t)nl));
+            }
+        }
+    }
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!precond) {
+        h->nsolve = 1;
+        return AMG_OK;
+    }
+    AMG_TRY(collapse_coarse(h, s));
+    return tail_prepare(h, s);
+}
+
 int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const double *v_in, cudaStream_t s) {
     const amg_config &cfg = h->cfg;
     const int n = h->n;
@@ -1111,90 +1205,7 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
         ++l;
     }
     h->nlevels = l + 1;
-
-    // ---- coarsest level: dense factor + inverse ----
-    Level &Lc = h->L[l];
-    h->nc = precond ? Lc.A.nrows : 0;
-    if (h->nc > AMG_DENSE_MAX) {
-        set_last_error("coarsening stopped at level %d with %d rows (> %d)", l, h->nc, AMG_DENSE_MAX);
-        return AMG_ERR_STALL;
-    }
-    if (precond) {
-        Scratch sc;
-        double *dense;
-        int *piv, *st;
-        const int m = h->nc;
-        AMG_TRY(sc.alloc(&dense, (size_t)m * m));
-        AMG_TRY(sc.alloc(&piv, (size_t)m));
-        AMG_TRY(sc.alloc(&st, 1));
-        AMG_TRY(ar.alloc(&h->cinv, (size_t)m * m));
-        h->cinv_last = h->cinv;
-        k_csr_to_dense<<<1, 256, 0, s>>>(m, Lc.A.rp, Lc.A.ci, Lc.A.v, dense);
-        k_dense_factor_inverse<<<1, 256, 0, s>>>(m, h->symmetric, dense, piv, h->cinv, st);
-        AMG_LAUNCH_CHECK();
-        int hst = -1;
-        AMG_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(int), cudaMemcpyDeviceToHost, s));
-        AMG_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hst != AMG_OK) {
-            set_last_error("coarsest level (%d rows) is not %s", m, h->symmetric ? "SPD" : "invertible");
-            return AMG_NOT_SPD;
-        }
-    }
-
-    // ---- FP32 copies, work vectors, launch shapes ----
-    const bool mixed = cfg.precision == AMG_PRECISION_MIXED;
-    for (int k = 0; k < h->nlevels; ++k) {
-        Level &Lv = h->L[k];
-        const int nl = Lv.A.nrows;
-        const bool last = k == h->nlevels - 1;
-        Lv.vec_a = choose_vec(Lv.A.nnz, nl);
-        if (!last) {
-            Lv.vec_p = choose_vec(Lv.P.nnz, nl);
-            Lv.vec_r = choose_vec(Lv.R.nnz, Lv.R.nrows);
-        }
-        AMG_TRY(ar.alloc(&Lv.t, (size_t)nl));
-        if (k > 0) {
-            AMG_TRY(ar.alloc(&Lv.b, (size_t)nl));
-            AMG_TRY(ar.alloc(&Lv.x, (size_t)nl));
-        }
-        const int cap = 4096;  // stage capacity (stream::CAP)
-        if (k == 0) AMG_TRY(plan_stream(Lv.A, cap, Lv.sa64, s));
-        if (!last) {
-            AMG_TRY(plan_stream(Lv.A, cap, Lv.sa, s));
-            Lv.sa_post = Lv.sa;
-            AMG_TRY(plan_stream(Lv.P, cap, Lv.sp, s));
-            AMG_TRY(plan_stream(Lv.R, cap, Lv.sr, s));
-            AMG_TRY(ar.alloc(&Lv.ahat, (size_t)std::max(1LL, Lv.A.nnz)));
-            if (mixed) AMG_TRY(ar.alloc(&Lv.ahat32, (size_t)std::max(1LL, Lv.A.nnz)));
-            k_scale_cols<<<grid_for(nl), 256, 0, s>>>(nl, Lv.A.rp, Lv.A.ci, Lv.A.v, Lv.w, Lv.ahat, Lv.ahat32);
-            AMG_LAUNCH_CHECK();
-        }
-        if (mixed) {
-            AMG_TRY(ar.alloc(&Lv.A.v32, (size_t)std::max(1LL, Lv.A.nnz)));
-            k_to_f32<<<grid_for(Lv.A.nnz), 256, 0, s>>>(Lv.A.v, Lv.A.v32, Lv.A.nnz);
-            AMG_TRY(ar.alloc(&Lv.w32, (size_t)nl));
-            k_to_f32<<<grid_for(nl), 256, 0, s>>>(Lv.w, Lv.w32, nl);
-            if (!last) {
-                AMG_TRY(ar.alloc(&Lv.P.v32, (size_t)std::max(1LL, Lv.P.nnz)));
-                k_to_f32<<<grid_for(Lv.P.nnz), 256, 0, s>>>(Lv.P.v, Lv.P.v32, Lv.P.nnz);
-                AMG_TRY(ar.alloc(&Lv.R.v32, (size_t)std::max(1LL, Lv.R.nnz)));
-                k_to_f32<<<grid_for(Lv.R.nnz), 256, 0, s>>>(Lv.R.v, Lv.R.v32, Lv.R.nnz);
-            }
-            AMG_LAUNCH_CHECK();
-            AMG_TRY(ar.alloc(&Lv.t32, (size_t)nl));
-            if (k > 0) {
-                AMG_TRY(ar.alloc(&Lv.b32, (size_t)nl));
-                AMG_TRY(ar.alloc(&Lv.x32, (size_t)nl));
-            }
-        }
-    }
-    AMG_CUDA_TRY(cudaStreamSynchronize(s));
-    if (!precond) {
-        h->nsolve = 1;
-        return AMG_OK;
-    }
-    AMG_TRY(collapse_coarse(h, s));
-    return tail_prepare(h, s);
+    return finish_build(h, precond, s);
 }
 
 
@@ -1555,6 +1566,58 @@ static int values_symmetric(Hierarchy *h, cudaStream_t s, bool *sym) {
     return AMG_OK;
 }
 
+// The part of a re-setup after every level operator, P, R and weight holds
+// its new values: the coarsest inverse, A W and the FP32 copies, the
+// collapsed coarse end (or the padded dense copies) and the sliced-ELL plans'
+// value copies.
+static int refresh_derived(Hierarchy *h, cudaStream_t s) {
+    const amg_config &cfg = h->cfg;
+    const int L = h->nlevels;
+    // coarsest inverse (none for unpreconditioned handles)
+    if (h->nc > 0) {
+        Level &Lc = h->L[L - 1];
+        Scratch sc;
+        double *dense;
+        int *piv, *st;
+        const int m = Lc.A.nrows;
+        AMG_TRY(sc.alloc(&dense, (size_t)m * m));
+        AMG_TRY(sc.alloc(&piv, (size_t)m));
+        AMG_TRY(sc.alloc(&st, 1));
+        k_csr_to_dense<<<1, 256, 0, s>>>(m, Lc.A.rp, Lc.A.ci, Lc.A.v, dense);
+        k_dense_factor_inverse<<<1, 256, 0, s>>>(m, h->symmetric, dense, piv, h->cinv_last, st);
+        AMG_LAUNCH_CHECK();
+        int hst = -1;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hst != AMG_OK) {
+            set_last_error("coarsest level (%d rows) is not %s", m, h->symmetric ? "SPD" : "invertible");
+            return AMG_NOT_SPD;
+        }
+    }
+    // A W and the FP32 copies
+    const bool mixed = cfg.precision == AMG_PRECISION_MIXED;
+    for (int k = 0; k < L; ++k) {
+        Level &Lv = h->L[k];
+        const int nl = Lv.A.nrows;
+        const bool last = k == L - 1;
+        if (Lv.ahat) k_scale_cols<<<grid_for(nl), 256, 0, s>>>(nl, Lv.A.rp, Lv.A.ci, Lv.A.v, Lv.w, Lv.ahat, Lv.ahat32);
+        if (mixed) {
+            k_to_f32<<<grid_for(Lv.A.nnz), 256, 0, s>>>(Lv.A.v, Lv.A.v32, Lv.A.nnz);
+            k_to_f32<<<grid_for(nl), 256, 0, s>>>(Lv.w, Lv.w32, nl);
+            if (!last) {
+                k_to_f32<<<grid_for(Lv.P.nnz), 256, 0, s>>>(Lv.P.v, Lv.P.v32, Lv.P.nnz);
+                k_to_f32<<<grid_for(Lv.R.nnz), 256, 0, s>>>(Lv.R.v, Lv.R.v32, Lv.R.nnz);
+            }
+        }
+        AMG_LAUNCH_CHECK();
+    }
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    // the collapsed coarse end (in place) and the padded dense copies
+    if (h->nc > 0) AMG_TRY(h->nsolve < h->nlevels ? collapse_coarse(h, s) : pad_dense(h, s));
+    // the sliced-ELL plans' slot-order copies of the new values
+    return ell_refresh(h, s);
+}
+
 int resetup_hierarchy(Hierarchy *h, const double *v_in, cudaStream_t s) {
     const amg_config &cfg = h->cfg;
     const int L = h->nlevels;
@@ -1625,49 +1688,7 @@ int resetup_hierarchy(Hierarchy *h, const double *v_in, cudaStream_t s) {
         AMG_CUDA_TRY(cudaMemcpyAsync(An.v, Acn.v, sizeof(double) * (size_t)Acn.nnz, cudaMemcpyDeviceToDevice, s));
         AMG_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    // coarsest inverse (none for unpreconditioned handles)
-    if (h->nc > 0) {
-        Level &Lc = h->L[L - 1];
-        Scratch sc;
-        double *dense;
-        int *piv, *st;
-        const int m = Lc.A.nrows;
-        AMG_TRY(sc.alloc(&dense, (size_t)m * m));
-        AMG_TRY(sc.alloc(&piv, (size_t)m));
-        AMG_TRY(sc.alloc(&st, 1));
-        k_csr_to_dense<<<1, 256, 0, s>>>(m, Lc.A.rp, Lc.A.ci, Lc.A.v, dense);
-        k_dense_factor_inverse<<<1, 256, 0, s>>>(m, h->symmetric, dense, piv, h->cinv_last, st);
-        AMG_LAUNCH_CHECK();
-        int hst = -1;
-        AMG_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(int), cudaMemcpyDeviceToHost, s));
-        AMG_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hst != AMG_OK) {
-            set_last_error("coarsest level (%d rows) is not %s", m, h->symmetric ? "SPD" : "invertible");
-            return AMG_NOT_SPD;
-        }
-    }
-    // A W and the FP32 copies
-    const bool mixed = cfg.precision == AMG_PRECISION_MIXED;
-    for (int k = 0; k < L; ++k) {
-        Level &Lv = h->L[k];
-        const int nl = Lv.A.nrows;
-        const bool last = k == L - 1;
-        if (Lv.ahat) k_scale_cols<<<grid_for(nl), 256, 0, s>>>(nl, Lv.A.rp, Lv.A.ci, Lv.A.v, Lv.w, Lv.ahat, Lv.ahat32);
-        if (mixed) {
-            k_to_f32<<<grid_for(Lv.A.nnz), 256, 0, s>>>(Lv.A.v, Lv.A.v32, Lv.A.nnz);
-            k_to_f32<<<grid_for(nl), 256, 0, s>>>(Lv.w, Lv.w32, nl);
-            if (!last) {
-                k_to_f32<<<grid_for(Lv.P.nnz), 256, 0, s>>>(Lv.P.v, Lv.P.v32, Lv.P.nnz);
-                k_to_f32<<<grid_for(Lv.R.nnz), 256, 0, s>>>(Lv.R.v, Lv.R.v32, Lv.R.nnz);
-            }
-        }
-        AMG_LAUNCH_CHECK();
-    }
-    AMG_CUDA_TRY(cudaStreamSynchronize(s));
-    // the collapsed coarse end (in place) and the padded dense copies
-    if (h->nc > 0) AMG_TRY(h->nsolve < h->nlevels ? collapse_coarse(h, s) : pad_dense(h, s));
-    // the sliced-ELL plans' slot-order copies of the new values
-    return ell_refresh(h, s);
+    return refresh_derived(h, s);
 }
 
 int build_hierarchy_batched(Hierarchy *h, const int *rp_in, const int *ci_in, const double *v_in,
@@ -1988,6 +2009,74 @@ int build_hierarchy_batched(Hierarchy *h, const int *rp_in, const int *ci_in, co
     }
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
     return AMG_OK;
+}
+
+// The adjoint's hierarchy of A^T reusing A's (ht set up from h, which must
+// be preconditioned and nonsymmetric): the same aggregates, P and R = P^T
+// (their index and FP64 value arrays shared with h, which outlives ht),
+// every level operator the exact transpose of h's -- since R = P^T, the
+// Galerkin product of the transposed level above -- and smoother weights
+// from the transposed operators; the rest is built as for any hierarchy.
+static int transpose_levels(Hierarchy *ht, const Hierarchy *h, bool alloc, cudaStream_t s) {
+    const amg_config &cfg = ht->cfg;
+    for (int l = 0; l < h->nlevels; ++l) {
+        Level &Lt = ht->L[l];
+        const Level &Lf = h->L[l];
+        const int nl = Lf.A.nrows;
+        if (alloc) {
+            AMG_TRY(transpose_csr(Lf.A, Lt.A, ht->arena, s));
+        } else {
+            DevArena tmp;
+            DevCSR At;
+            int rc = transpose_csr(Lf.A, At, tmp, s);
+            if (rc == AMG_OK && cudaMemcpyAsync(Lt.A.v, At.v, sizeof(double) * (size_t)At.nnz, cudaMemcpyDeviceToDevice,
+                                                s) != cudaSuccess)
+                rc = AMG_ERR_CUDA;
+            const cudaError_t e = cudaStreamSynchronize(s);
+            tmp.free_all();
+            AMG_TRY(rc);
+            AMG_CUDA_TRY(e);
+        }
+        Scratch sc;
+        double *diag;
+        int *bad;
+        AMG_TRY(sc.alloc(&diag, (size_t)nl));
+        AMG_TRY(sc.alloc(&bad, 1));
+        AMG_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        k_find_diag<<<grid_for(nl), 256, 0, s>>>(nl, Lt.A.rp, Lt.A.ci, Lt.A.v, diag, bad);
+        if (alloc) AMG_TRY(ht->arena.alloc(&Lt.w, (size_t)nl));
+        k_smoother_weights<<<grid_for(nl), 256, 0, s>>>(nl, Lt.A.rp, Lt.A.v, diag, cfg.omega,
+                                                        cfg.smoother == AMG_SMOOTHER_L1_JACOBI, Lt.w);
+        AMG_LAUNCH_CHECK();
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (alloc && l < h->nlevels - 1) {
+            // shared with h: patterns and FP64 values (FP32 copies are ht's own)
+            Lt.P = Lf.P;
+            Lt.R = Lf.R;
+            Lt.P.v32 = nullptr;
+            Lt.R.v32 = nullptr;
+            Lt.agg = Lf.agg;
+            Lt.rho = Lf.rho;
+        }
+    }
+    return AMG_OK;
+}
+
+int build_transposed_hierarchy(Hierarchy *ht, const Hierarchy *h, cudaStream_t s) {
+    ht->cfg = h->cfg;
+    ht->cfg.symmetric = 0;
+    ht->symmetric = 0;
+    ht->n = h->n;
+    ht->nnz = h->nnz;
+    ht->transposed_of = h;
+    AMG_TRY(transpose_levels(ht, h, true, s));
+    ht->nlevels = h->nlevels;
+    return finish_build(ht, true, s);
+}
+
+int refresh_transposed_hierarchy(Hierarchy *ht, const Hierarchy *h, cudaStream_t s) {
+    AMG_TRY(transpose_levels(ht, h, false, s));
+    return refresh_derived(ht, s);
 }
 
 void free_hierarchy(Hierarchy *h) {
