@@ -432,8 +432,10 @@ def run_ours(args):
         s.resetup(vals)  # the first re-setup allocates its scratch
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push(f"resetup_{form}")
         for _ in range(3):
             s.resetup(vals)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(dev)
         resetup_ms = (time.perf_counter() - t0) * 1e3 / 3
         t0 = time.perf_counter()

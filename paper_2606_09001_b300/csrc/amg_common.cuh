@@ -174,6 +174,10 @@ struct Level {
     double *b = nullptr, *t = nullptr, *x = nullptr;
     float *b32 = nullptr, *t32 = nullptr, *x32 = nullptr;
     int vec_a = 8, vec_p = 8, vec_r = 8;  // threads per row chosen per operator
+    // kept for numeric re-setup (built at the first one): the pattern (and a
+    // value buffer) of A P, and R's entries as positions in P (R = P^T)
+    DevCSR AP;
+    int *rperm = nullptr;
 };
 
 // One level of a block-diagonal batch: which systems are present, where their

@@ -702,6 +702,146 @@ static int spgemm(int nrows, int ncols, const int *xrp, const int *xci, const do
     return AMG_OK;
 }
 
+// Numeric products on a known pattern (re-setup): C = X Y where C's sorted
+// row pattern (crp, cci) is that of an earlier product of the same patterns.
+// Every product x_ik y_kJ is added at J's position in its row (binary search
+// of the row's columns), in increasing k as in k_spgemm -- whose results
+// these kernels equal bit for bit -- and the epilogue runs on the finished
+// sums.  A product outside the pattern (never, for the setup's patterns) is
+// reported through *bad and dropped.  Two shapes:
+//   k_spgemm_known_thread: a thread per output row, for products whose rows
+//     pair few entries (the finest levels): 32 rows' loads in flight per warp;
+//   k_spgemm_known_warp: a warp per output row, entries of X in order and the
+//     lanes over the (distinct) columns of each Y row, the row's columns and
+//     sums in shared memory when it has at most KCAP entries.
+constexpr int KCAP = 512;
+constexpr int KWARPS = 8;
+
+__device__ __forceinline__ int lower_bound_col(const int *c, int n, int J) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (c[mid] < J) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int EPI>
+__device__ __forceinline__ double prolong_epilogue(double val, int col, int i, const ProlongEpi &epi) {
+    if (EPI == EPI_PROLONG) {
+        const double t = __ddiv_rn(val, epi.diag[i]);
+        const double delta = (col == epi.agg[i]) ? 1.0 : 0.0;
+        const double om = epi.omega_row ? epi.omega_row[i] : epi.omega_p;
+        val = __dsub_rn(delta, __dmul_rn(om, t));
+    }
+    return val;
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(256) k_spgemm_known_thread(int nrows, const int *__restrict__ xrp,
+                                                            const int *__restrict__ xci, const double *__restrict__ xv,
+                                                            const int *__restrict__ yrp, const int *__restrict__ yci,
+                                                            const double *__restrict__ yv,
+                                                            const int *__restrict__ crp, const int *__restrict__ cci,
+                                                            double *cv, ProlongEpi epi, int *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x) {
+        const int c0 = crp[i], cn = crp[i + 1] - c0;
+        const int *cols = cci + c0;
+        double *vals = cv + c0;
+        for (int a = 0; a < cn; ++a) vals[a] = 0.0;
+        const int pe = xrp[i + 1];
+        for (int p = xrp[i]; p < pe; ++p) {
+            const int k = xci[p];
+            const double xk = xv ? xv[p] : 1.0;
+            const int qe = yrp[k + 1];
+            for (int q = yrp[k]; q < qe; ++q) {
+                const int J = yci[q];
+                const int pos = lower_bound_col(cols, cn, J);
+                if (pos >= cn || cols[pos] != J) {
+                    atomicExch(bad, 1);
+                    continue;
+                }
+                vals[pos] = __dadd_rn(vals[pos], __dmul_rn(xk, yv ? yv[q] : 1.0));
+            }
+        }
+        if (EPI == EPI_PROLONG)
+            for (int a = 0; a < cn; ++a) vals[a] = prolong_epilogue<EPI>(vals[a], cols[a], i, epi);
+    }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(KWARPS * 32) k_spgemm_known_warp(int nrows, const int *__restrict__ xrp,
+                                                                  const int *__restrict__ xci,
+                                                                  const double *__restrict__ xv,
+                                                                  const int *__restrict__ yrp,
+                                                                  const int *__restrict__ yci,
+                                                                  const double *__restrict__ yv,
+                                                                  const int *__restrict__ crp,
+                                                                  const int *__restrict__ cci, double *cv,
+                                                                  ProlongEpi epi, int *bad) {
+    __shared__ int s_cols[KWARPS][KCAP];
+    __shared__ double s_vals[KWARPS][KCAP];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int i = blockIdx.x * KWARPS + wib; i < nrows; i += gridDim.x * KWARPS) {
+        const int c0 = crp[i], cn = crp[i + 1] - c0;
+        const bool staged = cn <= KCAP;
+        const int *cols = staged ? s_cols[wib] : cci + c0;
+        double *vals = staged ? s_vals[wib] : cv + c0;
+        for (int a = lane; a < cn; a += 32) {
+            if (staged) s_cols[wib][a] = cci[c0 + a];
+            vals[a] = 0.0;
+        }
+        __syncwarp();
+        const int pe = xrp[i + 1];
+        for (int p = xrp[i]; p < pe; ++p) {
+            const int k = xci[p];
+            const double xk = xv ? xv[p] : 1.0;
+            const int qe = yrp[k + 1];
+            for (int q = yrp[k] + lane; q < qe; q += 32) {
+                const int J = yci[q];
+                const int pos = lower_bound_col(cols, cn, J);
+                if (pos >= cn || cols[pos] != J) {
+                    atomicExch(bad, 1);
+                    continue;
+                }
+                vals[pos] = __dadd_rn(vals[pos], __dmul_rn(xk, yv ? yv[q] : 1.0));
+            }
+            __syncwarp();
+        }
+        for (int a = lane; a < cn; a += 32) cv[c0 + a] = prolong_epilogue<EPI>(vals[a], cols[a], i, epi);
+        __syncwarp();
+    }
+}
+
+// C.v = X Y on C's known pattern (C.rp, C.ci, C.nnz as set up before);
+// *bad is set if a product falls outside it.  ypairs: the mean number of
+// entries of Y's rows, which with X's picks the kernel shape.
+template <int EPI>
+static int spgemm_known(int nrows, const int *xrp, const int *xci, const double *xv, long long xnnz, const int *yrp,
+                        const int *yci, const double *yv, double ymean, ProlongEpi epi, const DevCSR &C, int *bad,
+                        cudaStream_t s) {
+    if (nrows == 0) return AMG_OK;
+    const double pairs = (double)xnnz / nrows * ymean;
+    if (pairs <= 96.0) {
+        const int blocks = (int)std::min<long long>((nrows + 255) / 256, (long long)num_sms() * 16);
+        k_spgemm_known_thread<EPI><<<std::max(blocks, 1), 256, 0, s>>>(nrows, xrp, xci, xv, yrp, yci, yv, C.rp, C.ci,
+                                                                         C.v, epi, bad);
+    } else {
+        const int blocks = (int)std::min<long long>((nrows + KWARPS - 1) / KWARPS, (long long)num_sms() * 8);
+        k_spgemm_known_warp<EPI><<<std::max(blocks, 1), KWARPS * 32, 0, s>>>(nrows, xrp, xci, xv, yrp, yci, yv, C.rp,
+                                                                               C.ci, C.v, epi, bad);
+    }
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+// dst[k] = src[perm[k]]
+__global__ void k_gather_values(long long n, const int *__restrict__ perm, const double *__restrict__ src, double *dst) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        dst[k] = src[perm[k]];
+}
+
 // ===========================================================================
 // Dense coarsest level: factor (Cholesky if symmetric, else LU with partial
 // pivoting) and explicit inverse, one thread block, FP64.
@@ -1495,6 +1635,12 @@ __global__ void k_entry_index(long long nnz, double *v) {
         v[k] = (double)k;
 }
 
+// Entry positions carried through a transpose as values, back to ints.
+__global__ void k_to_int(long long n, const double *v, int *out) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        out[k] = (int)v[k];
+}
+
 // Pattern of the transpose equal to the pattern: record the mirror map.
 __global__ void k_mirror_map(int n, long long nnz, const int *rp1, const int *ci1, const int *rp2, const int *ci2,
                              const double *idx2, int *tmap, int *differ) {
@@ -1673,20 +1819,38 @@ int resetup_hierarchy(Hierarchy *h, const double *v_in, cudaStream_t s) {
         AMG_TRY(sc.alloc(&trp, (size_t)nl + 1));
         k_iota<<<grid_for(nl + 1), 256, 0, s>>>(trp, nl + 1);
         AMG_LAUNCH_CHECK();
-        DevCSR Pn, Rn, AP, Acn;
-        AMG_TRY((spgemm<EPI_PROLONG>(nl, nc, A.rp, A.ci, A.v, trp, Lv.agg, nullptr, epi, Pn, sc.arena, s)));
-        AMG_TRY(transpose_csr(Pn, Rn, sc.arena, s));
-        AMG_TRY((spgemm<EPI_NONE>(nl, nc, A.rp, A.ci, A.v, Pn.rp, Pn.ci, Pn.v, ProlongEpi{}, AP, sc.arena, s)));
-        AMG_TRY((spgemm<EPI_NONE>(nc, nc, Rn.rp, Rn.ci, Rn.v, AP.rp, AP.ci, AP.v, ProlongEpi{}, Acn, sc.arena, s)));
-        DevCSR &An = h->L[l + 1].A;
-        if (Pn.nnz != Lv.P.nnz || Rn.nnz != Lv.R.nnz || Acn.nnz != An.nnz) {
-            set_last_error("re-setup produced a different pattern on level %d", l);
+        // the patterns are those of the setup: every product is numeric only,
+        // written in place (A P's pattern and R's permutation kept from the
+        // first re-setup)
+        AMG_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        AMG_TRY((spgemm_known<EPI_PROLONG>(nl, A.rp, A.ci, A.v, A.nnz, trp, Lv.agg, nullptr, 1.0, epi, Lv.P, bad, s)));
+        if (!Lv.rperm) {
+            DevCSR I = Lv.P, It;
+            AMG_TRY(sc.alloc(&I.v, (size_t)std::max(1LL, Lv.P.nnz)));
+            k_entry_index<<<grid_for(Lv.P.nnz), 256, 0, s>>>(Lv.P.nnz, I.v);
+            AMG_TRY(transpose_csr(I, It, sc.arena, s));
+            AMG_TRY(h->arena.alloc(&Lv.rperm, (size_t)std::max(1LL, Lv.R.nnz)));
+            k_to_int<<<grid_for(Lv.R.nnz), 256, 0, s>>>(Lv.R.nnz, It.v, Lv.rperm);
+            AMG_LAUNCH_CHECK();
+        }
+        k_gather_values<<<grid_for(Lv.R.nnz), 256, 0, s>>>(Lv.R.nnz, Lv.rperm, Lv.P.v, Lv.R.v);
+        AMG_LAUNCH_CHECK();
+        if (!Lv.AP.rp) {
+            AMG_TRY((spgemm<EPI_NONE>(nl, nc, A.rp, A.ci, A.v, Lv.P.rp, Lv.P.ci, Lv.P.v, ProlongEpi{}, Lv.AP, h->arena, s)));
+        } else {
+            AMG_TRY((spgemm_known<EPI_NONE>(nl, A.rp, A.ci, A.v, A.nnz, Lv.P.rp, Lv.P.ci, Lv.P.v,
+                                             (double)Lv.P.nnz / std::max(1, Lv.P.nrows), ProlongEpi{}, Lv.AP, bad, s)));
+        }
+        AMG_TRY((spgemm_known<EPI_NONE>(nc, Lv.R.rp, Lv.R.ci, Lv.R.v, Lv.R.nnz, Lv.AP.rp, Lv.AP.ci, Lv.AP.v,
+                                         (double)Lv.AP.nnz / std::max(1, Lv.AP.nrows), ProlongEpi{}, h->L[l + 1].A,
+                                         bad, s)));
+        hbad = 0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hbad) {
+            set_last_error("re-setup: a product left the setup's pattern on level %d", l);
             return AMG_ERR_CUDA;
         }
-        AMG_CUDA_TRY(cudaMemcpyAsync(Lv.P.v, Pn.v, sizeof(double) * (size_t)Pn.nnz, cudaMemcpyDeviceToDevice, s));
-        AMG_CUDA_TRY(cudaMemcpyAsync(Lv.R.v, Rn.v, sizeof(double) * (size_t)Rn.nnz, cudaMemcpyDeviceToDevice, s));
-        AMG_CUDA_TRY(cudaMemcpyAsync(An.v, Acn.v, sizeof(double) * (size_t)Acn.nnz, cudaMemcpyDeviceToDevice, s));
-        AMG_CUDA_TRY(cudaStreamSynchronize(s));
     }
     return refresh_derived(h, s);
 }
