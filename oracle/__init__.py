@@ -49,7 +49,8 @@ class _Config(C.Structure):
     _fields_ = [("solver", C.c_int), ("smoother", C.c_int), ("omega", C.c_double),
                 ("theta", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
                 ("rtol", C.c_double), ("max_iter", C.c_int), ("max_restarts", C.c_int),
-                ("symmetric", C.c_int), ("adjoint_reuse", C.c_int)]
+                ("symmetric", C.c_int), ("adjoint_reuse", C.c_int),
+                ("amg_type", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -86,6 +87,8 @@ def lib():
             L.or_resetup.argtypes = [C.c_void_p, _f64p, C.POINTER(C.c_int)]
             L.or_resetup.restype = C.c_void_p
             L.or_transposed.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+            L.or_classical_split.argtypes = [C.c_int, C.c_longlong, _i32p, _i32p, _f64p, _i32p,
+                                             C.POINTER(C.c_int)]
             L.or_transposed.restype = C.c_void_p
             L.or_hier_free.argtypes = [C.c_void_p]
             L.or_hier_nlevels.argtypes = [C.c_void_p]
@@ -318,6 +321,18 @@ class OracleError(RuntimeError):
     def __init__(self, status):
         super().__init__(f"oracle setup failed with status {status}")
         self.status = status
+
+
+def classical_split(A):
+    """The classical C/F splitting of A (strength, PMIS): (cf with 1 for C and
+    0 for F, rounds)."""
+    rp, ci, v = _csr_args(A)
+    cf = np.empty(A.n, np.int32)
+    r = C.c_int()
+    st = lib().or_classical_split(A.n, A.nnz, rp, ci, v, cf, C.byref(r))
+    if st:
+        raise OracleError(st)
+    return cf, r.value
 
 
 def solve(A, b, config: dict | None = None):

@@ -60,6 +60,7 @@ typedef struct {
     int max_restarts; /* true-residual restarts, default 3 */
     int symmetric;    /* -1 detect, 0 no, 1 yes */
     int adjoint_reuse; /* nonsymmetric adjoint: 0 sets up a hierarchy of A^T, 1 transposes A's (or_transposed) */
+    int amg_type;     /* 0 smoothed aggregation, 1 classical Ruge-Stueben (strength, PMIS, direct interpolation) */
 } or_config;
 
 typedef struct {
@@ -563,6 +564,155 @@ static int spgemm(const ocsr *X, const ocsr *Y, ocsr *C) {
 
 /* A_c = P^T (A P): AP first, then R = P^T times AP, so (A_c)_IJ accumulates
  * P_iI (AP)_iJ in increasing fine index i. */
+/* ------------------------------------------------------------------------ */
+/* Classical (Ruge-Stueben) coarsening: the paper's other AMG family (its     */
+/* Sec. 3.5 runs classical and aggregation AMG through the wrapped library;   */
+/* the method itself is not given, so the textbook steps below are the       */
+/* reading: Ruge & Stueben 1987, Stueben 2001, De Sterck, Yang & Heys 2006).   */
+/* ------------------------------------------------------------------------ */
+
+#define OR_THETA_CLASSICAL 0.25
+
+/* Strong dependencies of row i (the directed relation S_i): j != i with
+ * -a_ij >= theta_c max_{k != i}(-a_ik) and that maximum positive; theta_c =
+ * 1/4 scales exactly.  Pattern-only CSR, columns ascending. */
+static int strength_classical(const ocsr *a, ocsr *S) {
+    const int n = a->nrows;
+    long long cnt = 0;
+    double *thr = (double *)malloc((size_t)n * sizeof(double));
+    if (!thr) return OR_ERR_OOM;
+    for (int pass = 0; pass < 2; ++pass) {
+        long long pos = 0;
+        for (int i = 0; i < n; ++i) {
+            if (pass == 0) {
+                double m = 0.0;
+                for (int k = a->rp[i]; k < a->rp[i + 1]; ++k)
+                    if (a->ci[k] != i && -a->v[k] > m) m = -a->v[k];
+                thr[i] = m > 0.0 ? OR_THETA_CLASSICAL * m : -1.0; /* -1: no strong dependency */
+            } else {
+                S->rp[i] = (int)pos;
+            }
+            for (int k = a->rp[i]; k < a->rp[i + 1]; ++k) {
+                const int j = a->ci[k];
+                if (j == i || thr[i] < 0.0 || !(-a->v[k] >= thr[i])) continue;
+                if (pass == 0) cnt++;
+                else { S->ci[pos] = j; S->v[pos] = 1.0; pos++; }
+            }
+        }
+        if (pass == 0) {
+            if (csr_alloc(S, n, n, cnt)) { free(thr); return OR_ERR_OOM; }
+        } else {
+            S->rp[n] = (int)pos;
+        }
+    }
+    free(thr);
+    return OR_OK;
+}
+
+/* PMIS C/F splitting.  Weight w_i = |S^T_i| + fmix32(i) 2^-32 (the number of
+ * points i strongly influences plus a hash fraction: no two weights tie).
+ * Points that influence none (w_i < 1) start as F.  Each round, computed
+ * from the state at its start: (a) every undecided point whose weight
+ * exceeds that of every undecided neighbour in S_i or S^T_i becomes C;
+ * (b) every still undecided point with a strong dependency on a new C point
+ * becomes F.  cf[i]: 1 C, 0 F. */
+static int pmis(const ocsr *S, const ocsr *St, int *cf, int *nrounds) {
+    const int n = S->nrows;
+    double *w = (double *)malloc((size_t)n * sizeof(double));
+    int *st = (int *)malloc((size_t)n * sizeof(int));  /* -1 undecided, 0 F, 1 C */
+    int *newc = (int *)malloc((size_t)n * sizeof(int));
+    if (!w || !st || !newc) { free(w); free(st); free(newc); return OR_ERR_OOM; }
+    for (int i = 0; i < n; ++i) {
+        w[i] = (double)(St->rp[i + 1] - St->rp[i]) + ldexp((double)or_fmix32((uint32_t)i), -32);
+        st[i] = w[i] < 1.0 ? 0 : -1;
+    }
+    int rounds = 0;
+    for (;;) {
+        int und = 0;
+        for (int i = 0; i < n; ++i) und += st[i] < 0;
+        if (!und) break;
+        ++rounds;
+        for (int i = 0; i < n; ++i) {
+            newc[i] = 0;
+            if (st[i] >= 0) continue;
+            int best = 1;
+            for (int k = S->rp[i]; k < S->rp[i + 1] && best; ++k) { int j = S->ci[k]; if (st[j] < 0 && w[j] >= w[i]) best = 0; }
+            for (int k = St->rp[i]; k < St->rp[i + 1] && best; ++k) { int j = St->ci[k]; if (st[j] < 0 && w[j] >= w[i]) best = 0; }
+            newc[i] = best;
+        }
+        for (int i = 0; i < n; ++i) if (newc[i]) st[i] = 1;
+        for (int i = 0; i < n; ++i) {
+            if (st[i] >= 0) continue;
+            for (int k = S->rp[i]; k < S->rp[i + 1]; ++k) if (newc[S->ci[k]]) { st[i] = 0; break; }
+        }
+    }
+    for (int i = 0; i < n; ++i) cf[i] = st[i];
+    if (nrounds) *nrounds = rounds;
+    free(w); free(st); free(newc);
+    return OR_OK;
+}
+
+/* Direct interpolation (Stueben 2001): a C point keeps its value (P row e_c);
+ * an F point i with strong C dependencies C_i interpolates from them with
+ * w_ij = -(alpha a_ij) / d, alpha = (sum of the negative off-diagonal a_ik)
+ * / (sum of a_ik over C_i), d = a_ii + (sum of the positive off-diagonal
+ * a_ik); every strong dependency is negative, so the positive entries are
+ * the ones lumped into d.  Sums run in CSR order.  An F point without strong
+ * C dependencies gets an empty row.  cidx[i]: coarse index of C point i,
+ * -1 for F. */
+static int direct_interp(const ocsr *a, const ocsr *S, const int *cidx, int nc, ocsr *P) {
+    const int n = a->nrows;
+    long long cnt = 0;
+    for (int i = 0; i < n; ++i) {
+        if (cidx[i] >= 0) { cnt++; continue; }
+        for (int k = S->rp[i]; k < S->rp[i + 1]; ++k) cnt += cidx[S->ci[k]] >= 0;
+    }
+    if (csr_alloc(P, n, nc, cnt)) return OR_ERR_OOM;
+    long long pos = 0;
+    for (int i = 0; i < n; ++i) {
+        P->rp[i] = (int)pos;
+        if (cidx[i] >= 0) { P->ci[pos] = cidx[i]; P->v[pos] = 1.0; pos++; continue; }
+        double neg = 0.0, posv = 0.0, negc = 0.0, aii = 0.0;
+        int s = S->rp[i];
+        for (int k = a->rp[i]; k < a->rp[i + 1]; ++k) {
+            const int j = a->ci[k];
+            const double v = a->v[k];
+            if (j == i) { aii = v; continue; }
+            if (v < 0.0) neg = neg + v;
+            else posv = posv + v;
+            while (s < S->rp[i + 1] && S->ci[s] < j) ++s;
+            if (s < S->rp[i + 1] && S->ci[s] == j && cidx[j] >= 0) negc = negc + v;
+        }
+        if (negc == 0.0) continue; /* no strong C dependency: empty row */
+        const double alpha = neg / negc, d = aii + posv;
+        s = S->rp[i];
+        for (int k = a->rp[i]; k < a->rp[i + 1]; ++k) {
+            const int j = a->ci[k];
+            if (j == i) continue;
+            while (s < S->rp[i + 1] && S->ci[s] < j) ++s;
+            if (s < S->rp[i + 1] && S->ci[s] == j && cidx[j] >= 0) {
+                P->ci[pos] = cidx[j];
+                P->v[pos] = -(alpha * a->v[k]) / d;
+                pos++;
+            }
+        }
+    }
+    P->rp[n] = (int)pos;
+    P->nnz = pos;
+    return OR_OK;
+}
+
+/* Exported for tests: the classical strength pattern and the PMIS splitting. */
+int or_classical_split(int n, long long nnz, const int *rp, const int *ci, const double *v, int *cf, int *nrounds) {
+    ocsr a = {n, n, nnz, (int *)rp, (int *)ci, (double *)v}, S, St;
+    int st = strength_classical(&a, &S);
+    if (st) return st;
+    if ((st = csr_transpose(&S, &St))) { csr_free(&S); return st; }
+    st = pmis(&S, &St, cf, nrounds);
+    csr_free(&S); csr_free(&St);
+    return st;
+}
+
 static int galerkin(const ocsr *A, const ocsr *P, const ocsr *R, ocsr *Ac) {
     ocsr AP;
     int st = spgemm(A, P, &AP);
@@ -662,6 +812,7 @@ void or_config_default(or_config *c) {
     c->max_restarts = 3;
     c->symmetric = -1;
     c->adjoint_reuse = 0;
+    c->amg_type = 0;
 }
 
 /* Symmetric = pattern symmetric and values bitwise equal. */
@@ -715,6 +866,26 @@ or_hier *or_setup(const or_config *cfg_in, int n, long long nnz, const int *rp, 
         if (A->nrows <= cfg.coarse_max || l + 1 >= cfg.max_levels || l + 1 >= OR_MAX_LEVELS) break;
         /* strength threshold halves at every coarser level: theta_l = theta 2^-l
          * (Vanek, Mandel & Brezina 1996); scaling by a power of two is exact */
+        if (cfg.amg_type == 1) {
+            /* classical: strength, PMIS C/F, direct interpolation; agg[l]
+             * holds each row's coarse index (-1 for F points) */
+            ocsr S, St;
+            if ((st = strength_classical(A, &S))) { *status = st; or_hier_free(h); return NULL; }
+            if ((st = csr_transpose(&S, &St))) { csr_free(&S); *status = st; or_hier_free(h); return NULL; }
+            h->agg[l] = (int *)malloc((size_t)A->nrows * sizeof(int));
+            st = h->agg[l] ? pmis(&S, &St, h->agg[l], NULL) : OR_ERR_OOM;
+            int nc = 0;
+            if (!st)
+                for (int i = 0; i < A->nrows; ++i) h->agg[l][i] = h->agg[l][i] ? nc++ : -1;
+            if (!st && nc > 0 && nc < A->nrows) st = direct_interp(A, &S, h->agg[l], nc, &h->P[l]);
+            csr_free(&S); csr_free(&St);
+            if (st) { *status = st; or_hier_free(h); return NULL; }
+            if (nc == 0 || nc >= A->nrows) { free(h->agg[l]); h->agg[l] = NULL; break; } /* stalled */
+            if ((st = csr_transpose(&h->P[l], &h->R[l]))) { *status = st; or_hier_free(h); return NULL; }
+            if ((st = galerkin(A, &h->P[l], &h->R[l], &h->A[l + 1]))) { *status = st; or_hier_free(h); return NULL; }
+            l++;
+            continue;
+        }
         double theta_l = ldexp(cfg.theta, -l);
         ocsr S;
         if ((st = strength(A, theta_l, &S))) { *status = st; or_hier_free(h); return NULL; }
@@ -758,6 +929,7 @@ or_hier *or_setup(const or_config *cfg_in, int n, long long nnz, const int *rp, 
  * by the same formulas as or_setup.  The symmetry flag is kept. */
 or_hier *or_resetup(const or_hier *old, const double *v, int *status) {
     const ocsr *A0 = &old->A[0];
+    if (old->cfg.amg_type == 1) { *status = OR_ERR_ARG; return NULL; } /* aggregation hierarchies only */
     or_hier *h = (or_hier *)calloc(1, sizeof(or_hier));
     if (!h) { *status = OR_ERR_OOM; return NULL; }
     h->cfg = old->cfg;

@@ -649,3 +649,92 @@ def test_adjoint_reuse_solves_the_transposed_system():
         assert np.array_equal(dA, -(lam[rows] * x[A.col_idx]))
         lams.append(lam)
     assert np.linalg.norm(lams[1] - lams[0]) <= 1e-9 * np.linalg.norm(lams[0])
+
+
+# ---------------------------------------------------------------------------
+# Classical Ruge-Stueben coarsening (amg_type = 1)
+# ---------------------------------------------------------------------------
+
+def classical_strength_dense(A):
+    """The strong dependencies S_i of the definition (dense, for small A)."""
+    Ad = to_sp(A).toarray()
+    S = np.zeros_like(Ad, dtype=bool)
+    for i in range(A.n):
+        off = -np.delete(Ad[i], i)
+        m = off.max() if off.size else 0.0
+        if m > 0:
+            S[i] = -Ad[i] >= 0.25 * m
+            S[i, i] = False
+    return S & (Ad != 0)
+
+
+@pytest.mark.parametrize("maker", [lambda: M.poisson2d(23), lambda: M.convection_diffusion_upwind(7),
+                                   lambda: M.diffusion_fv(np.exp(np.random.default_rng(5).normal(size=(16, 16))))])
+def test_classical_split_is_a_pmis_splitting(maker):
+    """No two C points depend strongly on each other (whichever turned C
+    first would have turned the other F), which for a symmetric S makes the C
+    points independent; every F point that influences some point depends
+    strongly on a C point (PMIS turns a point F only next to a new C point);
+    the splitting is complete."""
+    A = maker()
+    cf, rounds = O.classical_split(A)
+    S = classical_strength_dense(A)
+    C = cf == 1
+    assert set(np.unique(cf)) <= {0, 1} and rounds >= 1 and C.any() and (~C).any()
+    assert not (S & S.T)[np.ix_(C, C)].any()
+    if (S == S.T).all():
+        assert not S[np.ix_(C, C)].any()
+    influences = S.sum(0) > 0  # i strongly influences some point
+    for i in np.where(~C & influences)[0]:
+        assert S[i, C].any(), i
+
+
+def test_classical_split_1d_laplacian_alternates():
+    """On tridiag(-1, 2, -1) every neighbour is strong; the C points form an
+    independent set and every F point sits next to a C point, so no two
+    neighbours are both C and no two consecutive points are both F except
+    where both have a C neighbour on their other side."""
+    A = M.tridiagonal_matrix(200, 2.0)
+    cf, _ = O.classical_split(A)
+    c = np.where(cf == 1)[0]
+    assert (np.diff(c) >= 2).all() and (np.diff(c) <= 3).all()
+    assert c[0] <= 1 and c[-1] >= 198
+
+
+def test_classical_interpolation_reproduces_constants_and_is_galerkin():
+    """Direct interpolation: an F row of a zero-row-sum stencil sums to 1 (the
+    lumped diagonal equals minus the negative off-diagonal sum), a C row is a
+    unit row; the coarse operators are P^T A P (dense check)."""
+    A = M.poisson2d(24)
+    h = O.Hierarchy(A, {"amg_type": 1, "coarse_max": 16})
+    assert h.nlevels >= 3
+    lv = h.level(0)
+    n, nc = lv.A.n, h.level(1).A.n
+    P = lvl_sp(lv.P, nc).toarray()
+    Ad = lvl_sp(lv.A, n).toarray()
+    cidx = lv.agg
+    assert np.array_equal(np.sort(cidx[cidx >= 0]), np.arange(nc))
+    for i in range(n):
+        if cidx[i] >= 0:
+            assert P[i, cidx[i]] == 1.0 and np.count_nonzero(P[i]) == 1
+        elif np.isclose(Ad[i].sum(), 0.0) and P[i].any():
+            assert abs(P[i].sum() - 1.0) <= 1e-14
+    for l in range(h.nlevels - 1):
+        a, nx_ = h.level(l), h.level(l + 1)
+        Pd = lvl_sp(a.P, nx_.A.n).toarray()
+        Gal = Pd.T @ lvl_sp(a.A, a.A.n).toarray() @ Pd
+        assert np.abs(lvl_sp(nx_.A, nx_.A.n).toarray() - Gal).max() <= 1e-13 * np.abs(Gal).max()
+
+
+@pytest.mark.parametrize("maker,solver", [(lambda: M.poisson2d(40), 0),
+                                          (lambda: M.diffusion_fv(np.exp(np.random.default_rng(2).normal(size=(32, 32)))), 0),
+                                          (lambda: M.convection_diffusion_upwind(10), 1)])
+def test_classical_amg_preconditions_krylov(maker, solver):
+    A = maker()
+    b = np.random.default_rng(6).uniform(-1, 1, A.n)
+    h = O.Hierarchy(A, {"amg_type": 1, "solver": solver})
+    x, info = h.solve(b)
+    assert info.status == 0 and info.iters <= 40
+    assert np.linalg.norm(to_sp(A) @ x - b) <= 1e-8 * np.linalg.norm(b) * 1.0001
+    _, plain = O.Hierarchy(A, {"solver": 2 if solver == 0 else 3, "max_iter": 5000}).solve(b)
+    assert info.iters < plain.iters / 2
