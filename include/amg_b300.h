@@ -80,6 +80,11 @@ extern "C" {
 #define AMG_PRECISION_MIXED 1 /* FP32 hierarchy values and V-cycle arithmetic inside FP64 Krylov;
                                  FP64 true residual, dot products and coarsest solve */
 
+/* AMG families (amg_config.amg_type). */
+#define AMG_TYPE_AGGREGATION 0 /* smoothed aggregation (default) */
+#define AMG_TYPE_CLASSICAL 1   /* classical Ruge-Stueben: strength -a_ij >= 1/4 max_k(-a_ik), PMIS
+                                  C/F splitting, direct interpolation */
+
 /* Tile layouts of the streaming kernels that run the large operators (the
  * level operators A_l, P_l, R_l with at least 16384 rows).  By default the
  * setup times each operator's candidate layouts and keeps the fastest. */
@@ -107,6 +112,8 @@ typedef struct {
     int adjoint_reuse; /* adjoint of a nonsymmetric A: 0 sets up a hierarchy of A^T of its own (as
                           Sec. 2.1 describes; default); 1 reuses A's aggregates, P and R = P^T with
                           every level operator transposed (R A_l^T P = A_{l+1}^T), no second setup */
+    int amg_type;     /* AMG_TYPE_*; default AMG_TYPE_AGGREGATION.  theta applies to aggregation;
+                         amg_resetup and batches take aggregation hierarchies only */
 } amg_config;
 
 typedef struct {

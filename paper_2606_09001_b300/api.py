@@ -71,6 +71,8 @@ def make_config(config: dict | None = None) -> AmgConfig:
             v = _lib.PRECISIONS[v.upper()]
         elif k == "layout" and isinstance(v, str):
             v = _lib.LAYOUTS[v.upper()]
+        elif k == "amg_type" and isinstance(v, str):
+            v = _lib.AMG_TYPES[v.upper()]
         if not hasattr(c, k):
             raise KeyError(f"unknown config key {k!r}")
         setattr(c, k, v)

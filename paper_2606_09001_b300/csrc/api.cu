@@ -34,7 +34,8 @@ int check_config(const amg_config &c) {
         !(c.theta >= 0.0) || c.coarse_max < 1 || c.max_levels < 1 || c.max_levels > AMG_MAX_LEVELS ||
         !(c.rtol > 0.0) || c.max_iter < 1 || c.max_restarts < 0 || (c.precision != 0 && c.precision != 1) ||
         c.symmetric < -1 || c.symmetric > 1 || c.layout < AMG_LAYOUT_AUTO || c.layout > AMG_LAYOUT_SLICED_ELL ||
-        (c.adjoint_reuse != 0 && c.adjoint_reuse != 1)) {
+        (c.adjoint_reuse != 0 && c.adjoint_reuse != 1) ||
+        (c.amg_type != AMG_TYPE_AGGREGATION && c.amg_type != AMG_TYPE_CLASSICAL)) {
         set_last_error("invalid amg_config");
         return AMG_ERR_ARG;
     }
@@ -159,6 +160,7 @@ int amg_config_default(amg_config *c) {
     c->symmetric = -1;
     c->layout = AMG_LAYOUT_AUTO;
     c->adjoint_reuse = 0;
+    c->amg_type = AMG_TYPE_AGGREGATION;
     return AMG_OK;
 }
 
@@ -446,8 +448,8 @@ int amg_setup_batched(const amg_config *cfg, int nsys, const int *sys_off, int n
     if (cfg) c = *cfg;
     else amg_config_default(&c);
     AMG_TRY(check_config(c));
-    if (c.solver != AMG_SOLVER_PCG) {
-        set_last_error("amg_setup_batched: only AMG_SOLVER_PCG is supported for batches");
+    if (c.solver != AMG_SOLVER_PCG || c.amg_type != AMG_TYPE_AGGREGATION) {
+        set_last_error("amg_setup_batched: only AMG_SOLVER_PCG with aggregation AMG is supported for batches");
         return AMG_ERR_UNSUPPORTED;
     }
     std::vector<int> off((size_t)nsys + 1);

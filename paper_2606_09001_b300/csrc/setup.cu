@@ -400,6 +400,145 @@ __global__ void k_mis_update(int n, const int *srp, const int *sci, const unsign
 // ===========================================================================
 
 // active (may be null): rows of systems still coarsening in a batch.
+// ===========================================================================
+// Classical (Ruge-Stueben) coarsening: strength, PMIS splitting, direct
+// interpolation (amg_type = AMG_TYPE_CLASSICAL; the same readings as the
+// oracle, step for step)
+// ===========================================================================
+
+constexpr double THETA_CLASSICAL = 0.25;
+
+// Strong dependencies of row i: j != i with -a_ij >= 1/4 max_{k != i}(-a_ik)
+// and that maximum positive.  FILL = false counts per row, true fills.
+template <bool FILL>
+__global__ void k_strength_classical(int n, const int *rp, const int *ci, const double *v, int *cnt, const int *srp,
+                                     int *sci) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double m = 0.0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k)
+            if (ci[k] != i && -v[k] > m) m = -v[k];
+        const double thr = m > 0.0 ? __dmul_rn(THETA_CLASSICAL, m) : -1.0;
+        int c = 0, pos = FILL ? srp[i] : 0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const int j = ci[k];
+            if (j == i || thr < 0.0 || !(-v[k] >= thr)) continue;
+            if (FILL) sci[pos++] = j;
+            else ++c;
+        }
+        if (!FILL) cnt[i] = c;
+    }
+}
+
+// PMIS weights w_i = |S^T_i| + fmix32(i) 2^-32; points influencing none start F.
+__global__ void k_pmis_init(int n, const int *strp, double *w, int *st) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        w[i] = (double)(strp[i + 1] - strp[i]) + ldexp((double)fmix32((uint32_t)i), -32);
+        st[i] = w[i] < 1.0 ? 0 : -1;
+    }
+}
+
+// A round's selection, from the state at its start: an undecided point whose
+// weight exceeds every undecided neighbour's in S_i and S^T_i becomes C.
+__global__ void k_pmis_select(int n, const int *srp, const int *sci, const int *strp, const int *stci, const double *w,
+                              const int *st, int *newc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int best = st[i] < 0;
+        for (int k = srp[i]; k < srp[i + 1] && best; ++k) {
+            const int j = sci[k];
+            if (st[j] < 0 && w[j] >= w[i]) best = 0;
+        }
+        for (int k = strp[i]; k < strp[i + 1] && best; ++k) {
+            const int j = stci[k];
+            if (st[j] < 0 && w[j] >= w[i]) best = 0;
+        }
+        newc[i] = best;
+    }
+}
+
+// The round's update: new C points, then undecided points with a strong
+// dependency on a new C point become F; *und counts the undecided left.
+__global__ void k_pmis_update(int n, const int *srp, const int *sci, const int *newc, int *st, int *und) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (newc[i]) {
+            st[i] = 1;
+            continue;
+        }
+        if (st[i] >= 0) continue;
+        bool f = false;
+        for (int k = srp[i]; k < srp[i + 1] && !f; ++k) f = newc[sci[k]] != 0;
+        if (f) st[i] = 0;
+        else atomicAdd(und, 1);
+    }
+}
+
+__global__ void k_c_flags(int n, const int *st, int *flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) flag[i] = st[i] == 1;
+}
+
+__global__ void k_c_index(int n, const int *st, const int *scan, int *cidx) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        cidx[i] = st[i] == 1 ? scan[i] : -1;
+}
+
+// Direct interpolation.  FILL = false counts each row's entries (a C row 1,
+// an F row its strong C dependencies); FILL = true writes them: a C row the
+// unit entry, an F row w_ij = -(alpha a_ij) / d with alpha = (sum of the
+// negative off-diagonal a_ik) / (sum over its strong C dependencies) and
+// d = a_ii + (sum of the positive off-diagonal a_ik), sums in CSR order.
+template <bool FILL>
+__global__ void k_interp_direct(int n, const int *rp, const int *ci, const double *v, const int *srp, const int *sci,
+                                const int *cidx, int *cnt, const int *prp, int *pci, double *pv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (cidx[i] >= 0) {
+            if (FILL) {
+                pci[prp[i]] = cidx[i];
+                pv[prp[i]] = 1.0;
+            } else {
+                cnt[i] = 1;
+            }
+            continue;
+        }
+        double neg = 0.0, posv = 0.0, negc = 0.0, aii = 0.0;
+        int nc_i = 0;
+        int sp = srp[i];
+        const int se = srp[i + 1];
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const int j = ci[k];
+            const double a = v[k];
+            if (j == i) {
+                aii = a;
+                continue;
+            }
+            if (a < 0.0) neg = __dadd_rn(neg, a);
+            else posv = __dadd_rn(posv, a);
+            while (sp < se && sci[sp] < j) ++sp;
+            if (sp < se && sci[sp] == j && cidx[j] >= 0) {
+                negc = __dadd_rn(negc, a);
+                ++nc_i;
+            }
+        }
+        if (negc == 0.0) nc_i = 0;  // no strong C dependency: an empty row
+        if (!FILL) {
+            cnt[i] = nc_i;
+            continue;
+        }
+        if (nc_i == 0) continue;
+        const double alpha = __ddiv_rn(neg, negc), d = __dadd_rn(aii, posv);
+        int pos = prp[i];
+        sp = srp[i];
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const int j = ci[k];
+            if (j == i) continue;
+            while (sp < se && sci[sp] < j) ++sp;
+            if (sp < se && sci[sp] == j && cidx[j] >= 0) {
+                pci[pos] = cidx[j];
+                pv[pos] = __ddiv_rn(-__dmul_rn(alpha, v[k]), d);
+                ++pos;
+            }
+        }
+    }
+}
+
 __global__ void k_root_flags(int n, const unsigned long long *t, int *flag, const unsigned char *active = nullptr) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         flag[i] = (t[i] >> 32) == 2ull && (!active || active[i]);
@@ -1238,6 +1377,84 @@ int build_hierarchy(Hierarchy *h, const int *rp_in, const int *ci_in, const doub
         AMG_LAUNCH_CHECK();
         if (!precond || nl <= cfg.coarse_max || l + 1 >= cfg.max_levels || l + 1 >= AMG_MAX_LEVELS) break;
 
+        if (cfg.amg_type == AMG_TYPE_CLASSICAL) {
+            // classical: strength, PMIS splitting, direct interpolation; agg
+            // holds each row's coarse index (-1 for an F point)
+            int *cnt, *srp, *sci;
+            AMG_TRY(sc.alloc(&cnt, (size_t)nl + 1));
+            AMG_TRY(sc.alloc(&srp, (size_t)nl + 1));
+            k_strength_classical<false><<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, cnt, nullptr, nullptr);
+            AMG_LAUNCH_CHECK();
+            int snnz = 0;
+            AMG_TRY(exclusive_scan_int(cnt, srp, nl, &snnz, s));
+            AMG_TRY(sc.alloc(&sci, (size_t)std::max(1, snnz)));
+            k_strength_classical<true><<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, nullptr, srp, sci);
+            AMG_LAUNCH_CHECK();
+            DevCSR S, St;
+            S.nrows = S.ncols = nl;
+            S.nnz = snnz;
+            S.rp = srp;
+            S.ci = sci;
+            AMG_TRY(transpose_csr(S, St, sc.arena, s));
+            double *w;
+            int *st, *newc, *und;
+            AMG_TRY(sc.alloc(&w, (size_t)nl));
+            AMG_TRY(sc.alloc(&st, (size_t)nl));
+            AMG_TRY(sc.alloc(&newc, (size_t)nl));
+            AMG_TRY(sc.alloc(&und, 1));
+            k_pmis_init<<<grid_for(nl), 256, 0, s>>>(nl, St.rp, w, st);
+            AMG_LAUNCH_CHECK();
+            int rounds = 0, hund = 1;
+            while (hund > 0) {
+                if (++rounds > 100000) {
+                    set_last_error("PMIS rounds did not terminate at level %d", l);
+                    return AMG_ERR_STALL;
+                }
+                AMG_CUDA_TRY(cudaMemsetAsync(und, 0, sizeof(int), s));
+                k_pmis_select<<<grid_for(nl), 256, 0, s>>>(nl, srp, sci, St.rp, St.ci, w, st, newc);
+                k_pmis_update<<<grid_for(nl), 256, 0, s>>>(nl, srp, sci, newc, st, und);
+                AMG_LAUNCH_CHECK();
+                AMG_CUDA_TRY(cudaMemcpyAsync(&hund, und, sizeof(int), cudaMemcpyDeviceToHost, s));
+                AMG_CUDA_TRY(cudaStreamSynchronize(s));
+            }
+            int *flag, *cscan;
+            AMG_TRY(sc.alloc(&flag, (size_t)nl + 1));
+            AMG_TRY(sc.alloc(&cscan, (size_t)nl + 1));
+            k_c_flags<<<grid_for(nl), 256, 0, s>>>(nl, st, flag);
+            AMG_LAUNCH_CHECK();
+            int ncc = 0;
+            AMG_TRY(exclusive_scan_int(flag, cscan, nl, &ncc, s));
+            if (ncc == 0 || ncc >= nl) break;  // coarsening stalled: this level is the last
+            AMG_TRY(ar.alloc(&Lv.agg, (size_t)nl));
+            k_c_index<<<grid_for(nl), 256, 0, s>>>(nl, st, cscan, Lv.agg);
+            int *pcnt;
+            AMG_TRY(sc.alloc(&pcnt, (size_t)nl + 1));
+            k_interp_direct<false><<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, srp, sci, Lv.agg, pcnt, nullptr,
+                                                                 nullptr, nullptr);
+            AMG_LAUNCH_CHECK();
+            DevCSR &P = Lv.P;
+            P.nrows = nl;
+            P.ncols = ncc;
+            AMG_TRY(ar.alloc(&P.rp, (size_t)nl + 1));
+            int pnnz = 0;
+            AMG_TRY(exclusive_scan_int(pcnt, P.rp, nl, &pnnz, s));
+            P.nnz = pnnz;
+            AMG_TRY(ar.alloc(&P.ci, (size_t)std::max(1, pnnz)));
+            AMG_TRY(ar.alloc(&P.v, (size_t)std::max(1, pnnz)));
+            k_interp_direct<true><<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, srp, sci, Lv.agg, nullptr, P.rp,
+                                                                P.ci, P.v);
+            AMG_LAUNCH_CHECK();
+            Lv.rho = 0.0;
+            AMG_TRY(transpose_csr(P, Lv.R, ar, s));
+            DevCSR AP;
+            AMG_TRY((spgemm<EPI_NONE>(nl, ncc, A.rp, A.ci, A.v, P.rp, P.ci, P.v, ProlongEpi{}, AP, sc.arena, s)));
+            Level &Ln = h->L[l + 1];
+            AMG_TRY((spgemm<EPI_NONE>(ncc, ncc, Lv.R.rp, Lv.R.ci, Lv.R.v, AP.rp, AP.ci, AP.v, ProlongEpi{}, Ln.A, ar, s)));
+            AMG_CUDA_TRY(cudaStreamSynchronize(s));
+            ++l;
+            continue;
+        }
+
         // strength
         const double theta_l = ldexp(cfg.theta, -l);
         const double t2 = theta_l * theta_l;
@@ -1766,6 +1983,10 @@ static int refresh_derived(Hierarchy *h, cudaStream_t s) {
 
 int resetup_hierarchy(Hierarchy *h, const double *v_in, cudaStream_t s) {
     const amg_config &cfg = h->cfg;
+    if (cfg.amg_type == AMG_TYPE_CLASSICAL && h->nc > 0) {
+        set_last_error("amg_resetup: provided for aggregation hierarchies (and unpreconditioned handles) only");
+        return AMG_ERR_UNSUPPORTED;
+    }
     const int L = h->nlevels;
     Level &L0 = h->L[0];
     AMG_CUDA_TRY(cudaMemcpyAsync(L0.A.v, v_in, sizeof(double) * (size_t)L0.A.nnz, cudaMemcpyDefault, s));

@@ -989,6 +989,11 @@ static int stream_launch_nt(const StreamPlan &pl, int n, const int *rp, const in
         return AMG_OK;
         }
     }
+    if (pl.rt % 16 != 0) {
+        // the row-pointer bulk copies need tiles starting on 16-byte boundaries
+        set_last_error("streaming pass: tile height %d is not a multiple of 16", pl.rt);
+        return AMG_ERR_ARG;
+    }
     const int smem = stream::smem_bytes<TM, NT>(pl.rt, pl.cap);
     static int attr_set = 0;  // largest dynamic shared memory enabled for this instantiation
     if (smem > attr_set) {
@@ -1118,7 +1123,10 @@ static std::vector<StreamPlan> plan_candidates(const DevCSR &m, const StreamPlan
             if (vec > 32) continue;
             const int pass = 23 * 32 / vec;
             for (int rt : {pass, 2 * pass}) {
-                if (rt > stream::RT_MAX || worst(rt) > 6144 - 8) continue;
+                // tiles start at multiples of 16 rows, so every bulk copy of
+                // row pointers starts on a 16-byte boundary (23 * 32 / vec is
+                // not a multiple of 16 for vec >= 4)
+                if (rt % 16 != 0 || rt > stream::RT_MAX || worst(rt) > 6144 - 8) continue;
                 StreamPlan p = base;
                 p.nt = 768;
                 p.cap = 6144;
@@ -1945,14 +1953,28 @@ static int build_tail_table(Hierarchy *h, int t, int cta, std::vector<unsigned c
     return AMG_OK;
 }
 
+// Raises k_tail<TM>'s dynamic shared-memory limit to at least smem.  The
+// limit belongs to the kernel, shared by every hierarchy in the process, so
+// it only grows: lowering it for one hierarchy (e.g. an adjoint's) would make
+// another's larger tail fail to launch.
+template <typename TM>
+static bool tail_smem_limit(int smem) {
+    static int limit = 0;
+    if (smem <= limit) return true;
+    if (cudaFuncSetAttribute((const void *)tail::k_tail<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    limit = smem;
+    return true;
+}
+
 template <typename TM>
 static int tail_cluster_size(int smem) {
     const void *fn = (const void *)tail::k_tail<TM>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
+    if (!tail_smem_limit<TM>(smem)) return 0;
     for (int cs : {16, 8}) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cs);
@@ -2024,6 +2046,10 @@ static int launch_tail(Hierarchy *h, Workspace &W, const double *b0, double *z0,
     cfg.attrs = at;
     cfg.numAttrs = 1;
     const tail::TArgs<TM> &args = *(const tail::TArgs<TM> *)(mixed ? h->tail_args32.data() : h->tail_args64.data());
+    if (!tail_smem_limit<TM>((int)cfg.dynamicSmemBytes)) {
+        set_last_error("fused tail: %d bytes of shared memory refused", (int)cfg.dynamicSmemBytes);
+        return AMG_ERR_CUDA;
+    }
     AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, tail::k_tail<TM>, args, b0, z0, rold, fin, W.scal));
     return AMG_OK;
 }
