@@ -927,9 +927,46 @@ or_hier *or_setup(const or_config *cfg_in, int n, long long nnz, const int *rp, 
  * weights, omega_P, P, R, the Galerkin products and the coarsest factor are
  * recomputed from the new values v (same pattern as old's finest operator),
  * by the same formulas as or_setup.  The symmetry flag is kept. */
+/* Re-setup of a classical level's interpolation: the C/F map and P's pattern
+ * (each F row's interpolation set C_i) are kept and the weights recomputed
+ * from the new values by the direct-interpolation formula, with the sum over
+ * C_i taken over P's columns whatever the new entries' signs; a row whose
+ * sum over C_i is zero gets zero weights. */
+static int direct_interp_values(const ocsr *a, const int *cidx, ocsr *P) {
+    const int n = a->nrows;
+    for (int i = 0; i < n; ++i) {
+        const int p0 = P->rp[i], p1 = P->rp[i + 1];
+        if (cidx[i] >= 0 || p0 == p1) continue; /* C rows stay unit rows */
+        double neg = 0.0, posv = 0.0, negc = 0.0, aii = 0.0;
+        int q = p0;
+        for (int k = a->rp[i]; k < a->rp[i + 1]; ++k) {
+            const int j = a->ci[k];
+            const double v = a->v[k];
+            if (j == i) { aii = v; continue; }
+            if (v < 0.0) neg = neg + v;
+            else posv = posv + v;
+            if (cidx[j] >= 0) {
+                while (q < p1 && P->ci[q] < cidx[j]) ++q;
+                if (q < p1 && P->ci[q] == cidx[j]) negc = negc + v;
+            }
+        }
+        q = p0;
+        for (int k = a->rp[i]; k < a->rp[i + 1]; ++k) {
+            const int j = a->ci[k];
+            if (j == i || cidx[j] < 0) continue;
+            while (q < p1 && P->ci[q] < cidx[j]) ++q;
+            if (q < p1 && P->ci[q] == cidx[j]) {
+                if (negc == 0.0) { P->v[q] = 0.0; continue; }
+                const double alpha = neg / negc, d = aii + posv;
+                P->v[q] = -(alpha * a->v[k]) / d;
+            }
+        }
+    }
+    return OR_OK;
+}
+
 or_hier *or_resetup(const or_hier *old, const double *v, int *status) {
     const ocsr *A0 = &old->A[0];
-    if (old->cfg.amg_type == 1) { *status = OR_ERR_ARG; return NULL; } /* aggregation hierarchies only */
     or_hier *h = (or_hier *)calloc(1, sizeof(or_hier));
     if (!h) { *status = OR_ERR_OOM; return NULL; }
     h->cfg = old->cfg;
@@ -946,7 +983,16 @@ or_hier *or_resetup(const or_hier *old, const double *v, int *status) {
         h->agg[l] = (int *)malloc((size_t)n * sizeof(int));
         if (!h->agg[l]) { *status = OR_ERR_OOM; or_hier_free(h); return NULL; }
         memcpy(h->agg[l], old->agg[l], (size_t)n * sizeof(int));
-        if ((st = prolongator(A, h->agg[l], nc, &h->P[l], &h->rho[l]))) { *status = st; or_hier_free(h); return NULL; }
+        if (h->cfg.amg_type == 1) {
+            const ocsr *Po = &old->P[l];
+            if (csr_alloc(&h->P[l], Po->nrows, Po->ncols, Po->nnz)) { *status = OR_ERR_OOM; or_hier_free(h); return NULL; }
+            memcpy(h->P[l].rp, Po->rp, ((size_t)Po->nrows + 1) * sizeof(int));
+            memcpy(h->P[l].ci, Po->ci, (size_t)Po->nnz * sizeof(int));
+            memcpy(h->P[l].v, Po->v, (size_t)Po->nnz * sizeof(double)); /* C rows: unit entries */
+            direct_interp_values(A, h->agg[l], &h->P[l]);
+        } else if ((st = prolongator(A, h->agg[l], nc, &h->P[l], &h->rho[l]))) {
+            *status = st; or_hier_free(h); return NULL;
+        }
         if ((st = csr_transpose(&h->P[l], &h->R[l]))) { *status = st; or_hier_free(h); return NULL; }
         if ((st = galerkin(A, &h->P[l], &h->R[l], &h->A[l + 1]))) { *status = st; or_hier_free(h); return NULL; }
     }

@@ -738,3 +738,44 @@ def test_classical_amg_preconditions_krylov(maker, solver):
     assert np.linalg.norm(to_sp(A) @ x - b) <= 1e-8 * np.linalg.norm(b) * 1.0001
     _, plain = O.Hierarchy(A, {"solver": 2 if solver == 0 else 3, "max_iter": 5000}).solve(b)
     assert info.iters < plain.iters / 2
+
+
+def test_classical_resetup_keeps_splitting_and_is_galerkin():
+    """Classical re-setup: the C/F map and P's pattern stay, the weights follow
+    the direct-interpolation formula on the new values (same values: the same
+    hierarchy), the coarse operators are P^T A P."""
+    rng = np.random.default_rng(8)
+    A = M.diffusion_fv(np.exp(rng.normal(size=(20, 20))))
+    Anew = M.diffusion_fv(np.exp(rng.normal(size=(20, 20))))
+    h = O.Hierarchy(A, {"amg_type": 1, "coarse_max": 8})
+    same = h.resetup(A.values)
+    for l in range(h.nlevels):
+        assert np.array_equal(same.level(l).A.values, h.level(l).A.values)
+    hr = h.resetup(Anew.values)
+    assert hr.nlevels == h.nlevels >= 3
+    for l in range(h.nlevels - 1):
+        lv, nx_ = hr.level(l), hr.level(l + 1)
+        assert np.array_equal(lv.agg, h.level(l).agg)
+        assert np.array_equal(lv.P.col_idx, h.level(l).P.col_idx)
+        n, nc = lv.A.n, nx_.A.n
+        Ad = lvl_sp(lv.A, n).toarray()
+        P = lvl_sp(lv.P, nc).toarray()
+        cidx = lv.agg
+        for i in range(n):
+            if cidx[i] >= 0:
+                assert P[i, cidx[i]] == 1.0
+                continue
+            Ci = np.where(P[i] != 0)[0]
+            if Ci.size == 0:
+                continue
+            fine = np.array([np.where(cidx == c)[0][0] for c in Ci])
+            off = np.delete(Ad[i], i)
+            alpha = off[off < 0].sum() / Ad[i, fine].sum()
+            d = Ad[i, i] + off[off > 0].sum()
+            assert np.allclose(P[i, Ci], -alpha * Ad[i, fine] / d, rtol=1e-13, atol=0)
+        Gal = P.T @ Ad @ P
+        assert np.abs(lvl_sp(nx_.A, nc).toarray() - Gal).max() <= 1e-13 * np.abs(Gal).max()
+    b = rng.uniform(-1, 1, A.n)
+    x, info = hr.solve(b)
+    assert info.status == 0
+    assert np.linalg.norm(to_sp(Anew) @ x - b) <= 1e-8 * np.linalg.norm(b) * 1.0001
