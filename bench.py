@@ -432,17 +432,6 @@ def run_ours(args):
             ms = tt.item()
         # warm re-setup (new values on the cached pattern; the same values here,
         # which costs the same) and re-setup + solve, the paper's repeated step
-        resetup_ms = resetup_solve_ms = None
-        if args.amg_type == "CLASSICAL":  # re-setup is provided for aggregation hierarchies
-            _, sinfo = s.solve(b, x)
-            _, _, ainfo = s.adjoint(x, g, lam, dA)
-            forms[form] = {"ms_per_step": ms, "solve_iters": sinfo.iters, "adjoint_iters": ainfo.iters,
-                           "setup_ms": setup_ms, "first_adjoint_ms": first_adjoint_ms, "plans": plan_summary(s),
-                           "rel_res_true": sinfo.rel_res_true, "adjoint_rel_res_true": ainfo.rel_res_true,
-                           "gpu_launches": launches, "launches_per_step": launches / args.steps}
-            if clocks:
-                forms[form]["clocks"] = clocks
-            continue
         s.resetup(vals)  # the first re-setup allocates its scratch
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()

@@ -113,7 +113,7 @@ typedef struct {
                           Sec. 2.1 describes; default); 1 reuses A's aggregates, P and R = P^T with
                           every level operator transposed (R A_l^T P = A_{l+1}^T), no second setup */
     int amg_type;     /* AMG_TYPE_*; default AMG_TYPE_AGGREGATION.  theta applies to aggregation;
-                         amg_resetup and batches take aggregation hierarchies only */
+                         batches take aggregation hierarchies only */
 } amg_config;
 
 typedef struct {
@@ -149,7 +149,9 @@ int amg_setup(const amg_config *cfg, int n, long long nnz, const int *row_ptr, c
  * keeps its aggregates, so P, R and every coarse operator keep their
  * patterns; the smoother weights, the prolongator's omega, P, R = P^T, the
  * Galerkin products, the coarsest factor and all FP32 copies are recomputed
- * from the new values, much faster than a new setup.  A cached hierarchy of
+ * from the new values, much faster than a new setup.  A classical hierarchy
+ * keeps its C/F splittings and interpolation patterns and recomputes the
+ * direct-interpolation weights.  A cached hierarchy of
  * A^T (nonsymmetric adjoint) is re-set up too.  Synchronises the stream.
  * Errors: AMG_ERR_ZERO_DIAG, AMG_NOT_SPD (coarsest level), AMG_ERR_ARG (NULL
  * argument, or new values that change the detected symmetry),

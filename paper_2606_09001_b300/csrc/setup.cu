@@ -539,6 +539,51 @@ __global__ void k_interp_direct(int n, const int *rp, const int *ci, const doubl
     }
 }
 
+// Re-setup of a classical level's interpolation: P's pattern (each F row's
+// interpolation set, as coarse columns) and the C/F map are kept; the
+// direct-interpolation weights are recomputed from the new values, the sum
+// over the set taken whatever the new entries' signs, zero weights where it
+// is zero.  C rows keep their unit entries.
+__global__ void k_interp_direct_values(int n, const int *rp, const int *ci, const double *v, const int *cidx,
+                                       const int *prp, const int *pci, double *pv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p0 = prp[i], p1 = prp[i + 1];
+        if (cidx[i] >= 0 || p0 == p1) continue;
+        double neg = 0.0, posv = 0.0, negc = 0.0, aii = 0.0;
+        int q = p0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const int j = ci[k];
+            const double a = v[k];
+            if (j == i) {
+                aii = a;
+                continue;
+            }
+            if (a < 0.0) neg = __dadd_rn(neg, a);
+            else posv = __dadd_rn(posv, a);
+            const int c = cidx[j];
+            if (c >= 0) {
+                while (q < p1 && pci[q] < c) ++q;
+                if (q < p1 && pci[q] == c) negc = __dadd_rn(negc, a);
+            }
+        }
+        q = p0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const int j = ci[k];
+            const int c = cidx[j];
+            if (j == i || c < 0) continue;
+            while (q < p1 && pci[q] < c) ++q;
+            if (q < p1 && pci[q] == c) {
+                if (negc == 0.0) {
+                    pv[q] = 0.0;
+                    continue;
+                }
+                const double alpha = __ddiv_rn(neg, negc), d = __dadd_rn(aii, posv);
+                pv[q] = __ddiv_rn(-__dmul_rn(alpha, v[k]), d);
+            }
+        }
+    }
+}
+
 __global__ void k_root_flags(int n, const unsigned long long *t, int *flag, const unsigned char *active = nullptr) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         flag[i] = (t[i] >> 32) == 2ull && (!active || active[i]);
@@ -1983,10 +2028,6 @@ static int refresh_derived(Hierarchy *h, cudaStream_t s) {
 
 int resetup_hierarchy(Hierarchy *h, const double *v_in, cudaStream_t s) {
     const amg_config &cfg = h->cfg;
-    if (cfg.amg_type == AMG_TYPE_CLASSICAL && h->nc > 0) {
-        set_last_error("amg_resetup: provided for aggregation hierarchies (and unpreconditioned handles) only");
-        return AMG_ERR_UNSUPPORTED;
-    }
     const int L = h->nlevels;
     Level &L0 = h->L[0];
     AMG_CUDA_TRY(cudaMemcpyAsync(L0.A.v, v_in, sizeof(double) * (size_t)L0.A.nnz, cudaMemcpyDefault, s));
@@ -2044,7 +2085,12 @@ int resetup_hierarchy(Hierarchy *h, const double *v_in, cudaStream_t s) {
         // written in place (A P's pattern and R's permutation kept from the
         // first re-setup)
         AMG_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
-        AMG_TRY((spgemm_known<EPI_PROLONG>(nl, A.rp, A.ci, A.v, A.nnz, trp, Lv.agg, nullptr, 1.0, epi, Lv.P, bad, s)));
+        if (cfg.amg_type == AMG_TYPE_CLASSICAL) {
+            k_interp_direct_values<<<grid_for(nl), 256, 0, s>>>(nl, A.rp, A.ci, A.v, Lv.agg, Lv.P.rp, Lv.P.ci, Lv.P.v);
+            AMG_LAUNCH_CHECK();
+        } else {
+            AMG_TRY((spgemm_known<EPI_PROLONG>(nl, A.rp, A.ci, A.v, A.nnz, trp, Lv.agg, nullptr, 1.0, epi, Lv.P, bad, s)));
+        }
         if (!Lv.rperm) {
             DevCSR I = Lv.P, It;
             AMG_TRY(sc.alloc(&I.v, (size_t)std::max(1LL, Lv.P.nnz)));

@@ -102,12 +102,43 @@ def test_classical_adjoint_parity(name):
     assert np.array_equal(dA.cpu().numpy(), -lam[A.row_of()] * x.cpu().numpy()[A.col_idx])
 
 
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+@pytest.mark.parametrize("pair", ["grf3d_24", "grf3d_33", "convdiff_14"])
+def test_classical_resetup_bit_exact(pair, precision):
+    """Classical re-setup: the C/F map and P's pattern kept, weights and every
+    coarse operator recomputed, bit for bit against the oracle's re-setup."""
+    if pair.startswith("grf3d"):
+        N = int(pair.split("_")[1])
+        A0, A1 = M.diffusion3d_grf(N=N).A, M.diffusion3d_grf(seed=9, N=N).A
+        cfg = dict(CL, precision=precision)
+    else:
+        A0 = CASES[pair]()
+        rng = np.random.default_rng(13)
+        A1 = M.CSR(A0.row_ptr, A0.col_idx, A0.values * rng.uniform(0.8, 1.25, A0.nnz))
+        cfg = dict(CL, precision=precision, solver="BICGSTAB")
+    s = solver(A0, cfg)
+    s.resetup(dev(A1.values))
+    h = O.Hierarchy(A0, ocfg(cfg)).resetup(A1.values)
+    assert s.info().nlevels == h.nlevels
+    for l in range(h.nlevels):
+        lv = h.level(l)
+        rp, ci, v, _ = s.level(l, "A")
+        assert np.array_equal(ci, lv.A.col_idx) and np.array_equal(v.view(np.int64), lv.A.values.view(np.int64)), l
+        if l < h.nlevels - 1:
+            assert np.array_equal(s.aggregates(l), lv.agg)
+            for which, ref in (("P", lv.P), ("R", lv.R)):
+                rp, ci, v, _ = s.level(l, which)
+                assert np.array_equal(ci, ref.col_idx)
+                assert np.array_equal(v.view(np.int64), ref.values.view(np.int64)), (which, l)
+    b = np.random.default_rng(4).uniform(-1, 1, A1.n)
+    x, info = s.solve(dev(b))
+    _, io = h.solve(b)
+    assert info.status == 0 and info.rel_res_true <= 1e-8
+    assert abs(info.iters - io.iters) <= 2, (info.iters, io.iters)
+
+
 def test_classical_limits():
     A = M.poisson2d(40)
-    s = solver(A, CL)
-    with pytest.raises(api.AMGError) as e:
-        s.resetup(dev(A.values))
-    assert e.value.code == _lib.AMG_ERR_UNSUPPORTED
     blocks = [M.poisson2d(10), M.poisson2d(12)]
     Ab, off = M.block_diag(blocks)
     with pytest.raises(api.AMGError) as e:
