@@ -518,6 +518,23 @@ inline int smem_bytes_ell(int cap, int xw, int rt, int rvbytes) {
     return WIN_STAGES * ELayout<TM, GX>(cap, xw, rt, rvbytes).stb;
 }
 
+// One lane's row of a slice with exactly W slots: every value, index and
+// staged-vector load issues before the first FMA; the sum keeps slot order.
+template <int W, typename TM, typename GX>
+__device__ __forceinline__ TM slot_sum(const TM *vp, const uint16_t *cp, const GX *xs) {
+    TM a[W];
+    int c[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        a[q] = vp[q * 32];
+        c[q] = cp[q * 32];
+    }
+    TM sum = 0;
+#pragma unroll
+    for (int q = 0; q < W; ++q) sum += a[q] * fcvt<TM>(xs[c[q]]);
+    return sum;
+}
+
 template <typename TM, class Op, int NT = THREADS>
 __global__ void __launch_bounds__(NT, 2) k_stream_ell(int n, int rt, int cap, int xw, int ntiles,
                                                       const int *__restrict__ soff, const uint16_t *__restrict__ ec,
@@ -686,20 +703,34 @@ __global__ void __launch_bounds__(NT, 2) k_stream_ell(int n, int rt, int cap, in
                 const int wd = (sb1 - sb0) >> 5;  // warp-uniform
                 const TM *vp = vals + (sb0 - e0) + lane;
                 const uint16_t *cp = cis + (sb0 - e0) + lane;
+                // stencil widths run fully unrolled (wd is warp-uniform)
                 TM sum = 0;
-                int u = 0;
-                for (; u + 4 <= wd; u += 4) {
-                    TM a[4];
-                    int c[4];
+                switch (wd) {
+                    case 0: break;
+                    case 1: sum = slot_sum<1>(vp, cp, xs); break;
+                    case 2: sum = slot_sum<2>(vp, cp, xs); break;
+                    case 3: sum = slot_sum<3>(vp, cp, xs); break;
+                    case 4: sum = slot_sum<4>(vp, cp, xs); break;
+                    case 5: sum = slot_sum<5>(vp, cp, xs); break;
+                    case 6: sum = slot_sum<6>(vp, cp, xs); break;
+                    case 7: sum = slot_sum<7>(vp, cp, xs); break;
+                    case 8: sum = slot_sum<8>(vp, cp, xs); break;
+                    default: {
+                        int u = 0;
+                        for (; u + 4 <= wd; u += 4) {
+                            TM a[4];
+                            int c[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        a[q] = vp[(u + q) * 32];
-                        c[q] = cp[(u + q) * 32];
+                            for (int q = 0; q < 4; ++q) {
+                                a[q] = vp[(u + q) * 32];
+                                c[q] = cp[(u + q) * 32];
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) sum += a[q] * fcvt<TM>(xs[c[q]]);
+                        }
+                        for (; u < wd; ++u) sum += vp[u * 32] * fcvt<TM>(xs[cp[u * 32]]);
                     }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) sum += a[q] * fcvt<TM>(xs[c[q]]);
                 }
-                for (; u < wd; ++u) sum += vp[u * 32] * fcvt<TM>(xs[cp[u * 32]]);
                 if (row < n) {
                     if (Op::SELF) op.put_self(pre, dl0 >= 0 ? xs[dl0 + rl] : __ldg(op.gsrc() + row));
                     op.finish(row, sum, pre, acc);
