@@ -79,6 +79,9 @@ def parse():
                    help="AMG family: smoothed aggregation (default) or classical Ruge-Stueben")
     p.add_argument("--adjoint-reuse", action="store_true",
                    help="nonsymmetric adjoint on A's hierarchy transposed instead of a setup of A^T")
+    p.add_argument("--fuse-coarse", type=int, default=1, choices=[0, 1, 2],
+                   help="coarse levels below the streaming threshold: 1 single-cluster tail where they fit "
+                        "(default), 2 one cooperative whole-GPU launch, 0 one launch per pass")
     return p.parse_args()
 
 
@@ -381,7 +384,7 @@ def run_ours(args):
     for form in form_list:
         s = api.Solver(rp, ci, vals, {"solver": solver, "precision": form.upper() if form == "mixed" else "FP64",
                                       "layout": args.layout, "adjoint_reuse": int(args.adjoint_reuse),
-                                      "amg_type": args.amg_type})
+                                      "amg_type": args.amg_type, "fuse_coarse": args.fuse_coarse})
         solvers[form] = s
         setup_ms = s.info().setup_ms  # the cold setup (re-setups below overwrite the handle's figure)
         # the first adjoint (a nonsymmetric A's builds the hierarchy of A^T), timed apart
@@ -521,6 +524,7 @@ def run_ours(args):
                        "solver": solver, "precision": {"mixed": "mixed (FP32 V-cycle, FP64 Krylov)", "fp64": "FP64"}[primary],
                        "levels": info.nlevels, "rows": info.rows, "operator_complexity": info.operator_complexity,
                        "setup_ms": mixed.get("setup_ms"), "layout": args.layout, "amg_type": args.amg_type,
+                       "fuse_coarse": args.fuse_coarse,
                        "adjoint_hierarchy": "A's, transposed" if args.adjoint_reuse else "own setup of A^T",
                        "l2": "inputs larger than L2: level-0 operator alone is "
                              f"{nnz * 12 / 1e6:.0f} MB FP64 / {nnz * 8 / 1e6:.0f} MB FP32",

@@ -114,6 +114,11 @@ typedef struct {
                           every level operator transposed (R A_l^T P = A_{l+1}^T), no second setup */
     int amg_type;     /* AMG_TYPE_*; default AMG_TYPE_AGGREGATION.  theta applies to aggregation;
                          batches take aggregation hierarchies only */
+    int fuse_coarse;  /* launches of the coarse levels below 16384 rows that no streaming plan covers:
+                         1 (default) the single-cluster tail where those levels fit it (at most 400000
+                         entries per level), else one launch per pass; 2 one cooperative whole-GPU
+                         launch for the run of them with the dense end of the cycle, a grid barrier
+                         between passes (same bits as one launch per pass); 0 one launch per pass */
 } amg_config;
 
 typedef struct {

@@ -35,7 +35,8 @@ int check_config(const amg_config &c) {
         !(c.rtol > 0.0) || c.max_iter < 1 || c.max_restarts < 0 || (c.precision != 0 && c.precision != 1) ||
         c.symmetric < -1 || c.symmetric > 1 || c.layout < AMG_LAYOUT_AUTO || c.layout > AMG_LAYOUT_SLICED_ELL ||
         (c.adjoint_reuse != 0 && c.adjoint_reuse != 1) ||
-        (c.amg_type != AMG_TYPE_AGGREGATION && c.amg_type != AMG_TYPE_CLASSICAL)) {
+        (c.amg_type != AMG_TYPE_AGGREGATION && c.amg_type != AMG_TYPE_CLASSICAL) ||
+        c.fuse_coarse < 0 || c.fuse_coarse > 2) {
         set_last_error("invalid amg_config");
         return AMG_ERR_ARG;
     }
@@ -161,6 +162,7 @@ int amg_config_default(amg_config *c) {
     c->layout = AMG_LAYOUT_AUTO;
     c->adjoint_reuse = 0;
     c->amg_type = AMG_TYPE_AGGREGATION;
+    c->fuse_coarse = 1;
     return AMG_OK;
 }
 

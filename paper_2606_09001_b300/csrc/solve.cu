@@ -13,6 +13,7 @@
 #include "solve.cuh"
 #include "stream.cuh"
 #include "tail.cuh"
+#include "mid.cuh"
 
 namespace amg {
 
@@ -624,8 +625,11 @@ __global__ void __launch_bounds__(BLOCK) k_grad_values(int n, const int *__restr
     ROW_LOOP_END
 }
 
-// Host-chosen control fields of the device scalars.
-__global__ void k_set_control(DevScalars *sc, int done, int status, int flexible, int max_iter, int reset_iters) {
+// Host-chosen control fields of the device scalars.  A reset also clears the
+// arrival count of the fused coarse levels' grid barrier (left nonzero only
+// by a barrier wait that gave up).
+__global__ void k_set_control(DevScalars *sc, int done, int status, int flexible, int max_iter, int reset_iters,
+                              unsigned *gbar) {
     pdl_wait();
     pdl_trigger();
     sc->done = done;
@@ -635,6 +639,7 @@ __global__ void k_set_control(DevScalars *sc, int done, int status, int flexible
     if (reset_iters) {
         sc->iters = 0;
         sc->copy_timeout = 0;
+        gbar[0] = 0;
     }
 }
 
@@ -735,6 +740,8 @@ int workspace_init(Workspace &W, int n) {
     AMG_TRY(a.alloc(&W.part, (size_t)3 * W.part_cap));
     AMG_TRY(a.alloc(&W.counter, 4));
     AMG_CUDA_TRY(cudaMemset(W.counter, 0, 4 * sizeof(unsigned)));
+    AMG_TRY(a.alloc(&W.gbar, 2));
+    AMG_CUDA_TRY(cudaMemset(W.gbar, 0, 2 * sizeof(unsigned)));
     AMG_CUDA_TRY(cudaMemset(W.scal, 0, sizeof(DevScalars)));
     AMG_CUDA_TRY(cudaMallocHost(&W.scal_h, sizeof(DevScalars)));
     memset(W.scal_h, 0, sizeof(DevScalars));
@@ -2003,7 +2010,7 @@ static int tail_cluster_size(int smem) {
 int tail_prepare(Hierarchy *h, cudaStream_t) {
     h->tail_start = -1;
     const int L = h->nsolve;
-    if (L < 2) return AMG_OK;
+    if (L < 2 || h->cfg.fuse_coarse != 1) return AMG_OK;
     int t = L - 1;
     while (t > 0 && h->L[t - 1].sa.rt == 0 && h->L[t - 1].A.nrows < 16384 && h->L[t - 1].A.nnz <= 400000) --t;
     if (t > L - 2 || L - t > tail::MAX_LEVELS) return AMG_OK;
@@ -2065,6 +2072,114 @@ static double tail_bytes(const Hierarchy *h, int vb) {
     return by + 8.0 * h->nc * h->nc + 2.0 * vb * h->nc;
 }
 
+// First level m of the cooperative coarse launch (mid.cuh; fuse_coarse = 2),
+// or -1: levels m..L-2 all have fewer than 16384 rows and no streaming plan,
+// m >= 1 (the finest level reads the FP64 input and finishes the Krylov
+// scalars) and the cycle ends in the dense operator.
+static int mid_level(const Hierarchy *h) {
+    const int L = h->nsolve;
+    if (h->cfg.fuse_coarse != 2 || h->tail_start >= 0 || L < 3 || h->nc_ld > mid::DENSE_LD) return -1;
+    auto small = [](const Level &lv) {
+        return !lv.sa.rt && !lv.sa_post.rt && !lv.sp.rt && !lv.sr.rt && lv.A.nrows < 16384;
+    };
+    int m = L - 1;
+    while (m - 1 >= 1 && L - m < mid::MAX_LEVELS + 1 && small(h->L[m - 1])) --m;
+    return m < L - 1 ? m : -1;
+}
+
+// CTAs of the cooperative launch: up to two per SM, as the occupancy allows.
+template <typename TM, typename TMAT>
+static int mid_grid() {
+    static int g = 0;
+    if (!g) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mid::k_mid<TM, TMAT>, mid::THREADS, 0) != cudaSuccess)
+            return 0;
+        g = std::min(per_sm, 2) * num_sms();
+    }
+    return g;
+}
+
+// Levels m..L-1 of one V-cycle (and the restriction into level m when it is
+// not streamed) as one cooperative launch.
+template <typename TM>
+static int launch_mid(Hierarchy *h, Workspace &W, int m, cudaStream_t s) {
+    const bool mixed = sizeof(TM) == 4;
+    auto Av = [&](const DevCSR &a) -> const TM * { return (const TM *)(mixed ? (const void *)a.v32 : (const void *)a.v); };
+    auto Wv = [&](const Level &lv) -> const TM * { return (const TM *)(mixed ? (const void *)lv.w32 : (const void *)lv.w); };
+    auto Tv = [&](const Level &lv) -> TM * { return (TM *)(mixed ? (void *)lv.t32 : (void *)lv.t); };
+    auto Bv = [&](const Level &lv) -> TM * { return (TM *)(mixed ? (void *)lv.b32 : (void *)lv.b); };
+    auto Xv = [&](const Level &lv) -> TM * { return (TM *)(mixed ? (void *)lv.x32 : (void *)lv.x); };
+    const int L = h->nsolve;
+    mid::MArgs<TM> a = {};
+    a.nlev = L - 1 - m;
+    const Level &lp = h->L[m - 1];
+    if (!lp.sr.rt) {
+        a.r0n = lp.R.nrows;
+        a.r0vec = lp.vec_r;
+        a.r0rp = lp.R.rp;
+        a.r0ci = lp.R.ci;
+        a.r0v = Av(lp.R);
+        a.r0x = Tv(lp);
+    }
+    for (int k = 0; k < a.nlev; ++k) {
+        const Level &lv = h->L[m + k];
+        mid::MLevel<TM> &o = a.L[k];
+        o.n = lv.A.nrows;
+        o.nc = lv.R.nrows;
+        o.vec_a = lv.vec_a;
+        o.vec_p = lv.vec_p;
+        o.vec_r = lv.vec_r;
+        o.arp = lv.A.rp, o.aci = lv.A.ci, o.av = Av(lv.A);
+        o.prp = lv.P.rp, o.pci = lv.P.ci, o.pv = Av(lv.P);
+        o.rrp = lv.R.rp, o.rci = lv.R.ci, o.rv = Av(lv.R);
+        o.w = Wv(lv);
+        o.b = Bv(lv), o.t = Tv(lv), o.x = Xv(lv);
+    }
+    const Level &lc = h->L[L - 1];
+    const bool m32 = mixed && h->cpad32;
+    a.dm = h->nc;
+    a.dld = h->nc_ld;
+    a.M = m32 ? (const void *)h->cpad32 : (const void *)h->cpad64;
+    a.db = Bv(lc);
+    a.dx = Xv(lc);
+    const int grid = m32 ? mid_grid<TM, float>() : mid_grid<TM, double>();
+    if (grid <= 0) {
+        set_last_error("fused coarse levels: no resident CTA");
+        return AMG_ERR_CUDA;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(mid::THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const int *done = &W.scal->done;
+    int *err = &W.scal->copy_timeout;
+    if (m32)
+        AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, mid::k_mid<TM, float>, a, W.gbar, done, err));
+    else
+        AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, mid::k_mid<TM, double>, a, W.gbar, done, err));
+    return AMG_OK;
+}
+
+// Algorithmic bytes of the fused coarse levels (one V-cycle).
+static double mid_bytes(const Hierarchy *h, int m, int vb) {
+    const bool m32 = vb == 4 && h->cpad32;
+    const Level &lp = h->L[m - 1];
+    double by = lp.sr.rt ? 0.0 : csr_bytes(lp.R, vb) + (double)vb * (lp.A.nrows + lp.R.nrows);
+    for (int l = m; l < h->nsolve - 1; ++l) {  // the sum of the per-pass figures
+        const Level &lv = h->L[l];
+        by += 2.0 * csr_bytes(lv.A, vb) + csr_bytes(lv.P, vb) + csr_bytes(lv.R, vb) + 11.0 * vb * lv.A.nrows +
+              2.0 * vb * lv.R.nrows;
+    }
+    const double nc = h->nc;
+    return by + nc * nc * (m32 ? 4.0 : 8.0) + 2.0 * vb * nc;
+}
+
 // One V-cycle: z0 = M^-1 b0.  TM = float for the mixed form.
 template <typename TM>
 static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z0, int fin, cudaStream_t s,
@@ -2091,7 +2206,9 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         AMG_LAUNCH_CHECK();
         return AMG_OK;
     }
-    const int tl = h->tail_start >= 0 ? h->tail_start : L - 1;  // first level handled by the fused tail
+    const int mm = mid_level(h);  // first level of the cooperative coarse launch, or -1
+    // first level handled by the fused tail or the cooperative launch
+    const int tl = h->tail_start >= 0 ? h->tail_start : (mm > 0 ? mm : L - 1);
     if (h->tail_start == 0) {
         TRACE("tail", 0, tail_bytes(h, vb));
         return launch_tail<TM>(h, W, b0, z0, rold, fin == FIN_PCG_BETA, s);
@@ -2128,7 +2245,7 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
             }
         }
         const int nc = lv.R.nrows;
-        {
+        if (l != mm - 1 || lv.sr.rt) {  // the cooperative launch restricts into its first level itself
             TRACE("restrict", l, csr_bytes(lv.R, vb) + (double)vb * (n + nc));
             if (lv.sr.rt)
                 AMG_TRY(stream_launch<TM>(lv.sr, nc, lv.R.rp, lv.R.ci, Av(lv.R), OpSpmv<TM>{done, Tv(lv), Bv(nx)}, err, s));
@@ -2141,6 +2258,10 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
     if (h->tail_start > 0) {
         TRACE("tail", tl, tail_bytes(h, vb));
         AMG_TRY(launch_tail<TM>(h, W, nullptr, nullptr, nullptr, 0, s));
+    } else if (mm > 0) {
+        TRACE("mid", mm, mid_bytes(h, mm, vb));
+        AMG_TRY(launch_mid<TM>(h, W, mm, s));
+        AMG_LAUNCH_CHECK();
     } else {
         Level &lc = h->L[L - 1];
         const double m = h->nc;
@@ -2375,7 +2496,7 @@ static int true_residual(Hierarchy *h, Workspace &W, cudaStream_t s) {
 
 static int set_control(Workspace &W, cudaStream_t s, int done, int status, int flexible, int max_iter, int reset) {
     TRACE("control", 0, 0.0);
-    AMG_TRY(launch_k(k_set_control, 1, 1, 0, s, W.scal, done, status, flexible, max_iter, reset));
+    AMG_TRY(launch_k(k_set_control, 1, 1, 0, s, W.scal, done, status, flexible, max_iter, reset, W.gbar));
     AMG_LAUNCH_CHECK();
     return AMG_OK;
 }
@@ -2479,7 +2600,8 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
     if (status == AMG_OK && !(res->rel_res_true <= c.rtol)) res->status = AMG_MAXIT;
     W.prof.collect();
     if (W.scal_h->copy_timeout) {
-        set_last_error("a bulk-copy wait in a streaming kernel timed out");
+        set_last_error(W.scal_h->copy_timeout & 2 ? "a grid-barrier wait of the fused coarse levels timed out"
+                                                  : "a bulk-copy wait in a streaming kernel timed out");
         return AMG_ERR_CUDA;
     }
     return AMG_OK;

@@ -55,6 +55,7 @@ struct Workspace {
     DevScalars *scal_h = nullptr;                          // pinned host mirror
     double *part = nullptr;                                // per-block partial sums (3 x part_cap)
     unsigned *counter = nullptr;                           // last-block ticket
+    unsigned *gbar = nullptr;                              // grid barrier of the fused coarse levels
     int part_cap = 0;
     DevArena arena;
     Profiler prof;

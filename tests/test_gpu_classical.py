@@ -30,7 +30,7 @@ def ocfg(cfg):
     for k, v in cfg.items():
         if k == "solver":
             c[k] = _lib.SOLVERS[v]
-        elif k not in ("precision", "layout", "amg_type"):
+        elif k not in ("precision", "layout", "amg_type", "fuse_coarse"):
             c[k] = v
     return c
 

@@ -30,6 +30,7 @@ def ocfg(cfg):
     c = dict(cfg or {})
     c.pop("precision", None)
     c.pop("layout", None)
+    c.pop("fuse_coarse", None)
     if isinstance(c.get("solver"), str):
         c["solver"] = _lib.SOLVERS[c["solver"]]
     return c
