@@ -19,6 +19,9 @@ struct amg_handle_s {
     amg_batch_ws *BW = nullptr;  // batched handles only
     cudaStream_t s = nullptr; // private stream; ordered after/before the caller's stream by events
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // side stream of the adjoint's host copy of x (created on first use)
+    cudaStream_t s_aux = nullptr;
+    cudaEvent_t ev_aux0 = nullptr, ev_aux1 = nullptr;
     double *dA_stage = nullptr;  // device staging of dL/dA for host outputs
     DevArena extra;
     SolveResult last;
@@ -101,6 +104,9 @@ void destroy(amg_handle h) {
     h->extra.free_all();
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->ev_aux0) cudaEventDestroy(h->ev_aux0);
+    if (h->ev_aux1) cudaEventDestroy(h->ev_aux1);
+    if (h->s_aux) cudaStreamDestroy(h->s_aux);
     if (h->s) cudaStreamDestroy(h->s);
     delete h;
 }
@@ -266,10 +272,42 @@ int amg_adjoint(amg_handle h, const double *x, const double *g, double *lambda, 
         }
         H = h->HT;
     }
-    AMG_CUDA_TRY(cudaMemcpyAsync(h->W.aux, x, sizeof(double) * n, cudaMemcpyDefault, h->s));
+    // x is read only by the gradient, after the solve.  On the device the
+    // gradient reads it in place; from the host it is copied on a side stream
+    // while the solve runs (after the work already queued on the private
+    // stream, which may still read W.aux).
+    const double *xg = x;
+    bool side = false;
+    auto overlaps = [](const void *a, size_t na, const void *b, size_t nb) {
+        const char *pa = static_cast<const char *>(a), *pb = static_cast<const char *>(b);
+        return b && pa < pb + nb && pb < pa + na;
+    };
+    const size_t xb = sizeof(double) * n;
+    if (dA && is_device_ptr(x) &&
+        (overlaps(x, xb, lambda, xb) || overlaps(x, xb, dA, sizeof(double) * (size_t)nnz))) {
+        // x shares memory with an output written before the gradient reads it
+        AMG_CUDA_TRY(cudaMemcpyAsync(h->W.aux, x, xb, cudaMemcpyDefault, h->s));
+        xg = h->W.aux;
+    } else if (dA && !is_device_ptr(x)) {
+        if (!h->s_aux && (cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking) != cudaSuccess ||
+                          cudaEventCreateWithFlags(&h->ev_aux0, cudaEventDisableTiming) != cudaSuccess ||
+                          cudaEventCreateWithFlags(&h->ev_aux1, cudaEventDisableTiming) != cudaSuccess)) {
+            set_last_error("amg_adjoint: side stream not created");
+            return AMG_ERR_CUDA;
+        }
+        AMG_CUDA_TRY(cudaEventRecord(h->ev_aux0, h->s));
+        AMG_CUDA_TRY(cudaStreamWaitEvent(h->s_aux, h->ev_aux0, 0));
+        AMG_CUDA_TRY(cudaMemcpyAsync(h->W.aux, x, sizeof(double) * n, cudaMemcpyDefault, h->s_aux));
+        AMG_CUDA_TRY(cudaEventRecord(h->ev_aux1, h->s_aux));
+        xg = h->W.aux;
+        side = true;
+    }
     AMG_CUDA_TRY(cudaMemcpyAsync(h->W.b, g, sizeof(double) * n, cudaMemcpyDefault, h->s));
     int rc = run_solve(h, H, h->s);
-    if (rc < 0) return rc;
+    if (rc < 0) {
+        if (side) cudaStreamSynchronize(h->s_aux);  // the copy reads the caller's buffer
+        return rc;
+    }
     // W.x = lambda
     bool host_out = false;
     if (lambda) {
@@ -277,11 +315,12 @@ int amg_adjoint(amg_handle h, const double *x, const double *g, double *lambda, 
         host_out |= !is_device_ptr(lambda);
     }
     if (dA) {
+        if (side) AMG_CUDA_TRY(cudaStreamWaitEvent(h->s, h->ev_aux1, 0));
         if (is_device_ptr(dA)) {
-            AMG_TRY(grad_values(&h->H, h->W, h->W.x, h->W.aux, dA, h->s));
+            AMG_TRY(grad_values(&h->H, h->W, h->W.x, xg, dA, h->s));
         } else {
             if (!h->dA_stage) AMG_TRY(h->extra.alloc(&h->dA_stage, (size_t)nnz));
-            AMG_TRY(grad_values(&h->H, h->W, h->W.x, h->W.aux, h->dA_stage, h->s));
+            AMG_TRY(grad_values(&h->H, h->W, h->W.x, xg, h->dA_stage, h->s));
             AMG_CUDA_TRY(cudaMemcpyAsync(dA, h->dA_stage, sizeof(double) * nnz, cudaMemcpyDefault, h->s));
             host_out = true;
         }

@@ -201,6 +201,33 @@ def test_host_pointers_match_device():
     assert np.array_equal(lam, lam2.cpu().numpy()) and np.array_equal(dA, dA2.cpu().numpy())
 
 
+def test_adjoint_x_may_share_an_output_buffer():
+    """x read in place by the gradient must not be the lambda buffer the
+    adjoint fills first: such a call keeps a private copy of x."""
+    A = M.diffusion3d_grf(N=16).A
+    s = gpu_solver(A)
+    rng = np.random.default_rng(12)
+    x, _ = s.solve(dev(rng.uniform(-1, 1, A.n)))
+    g = dev(rng.uniform(-1, 1, A.n))
+    lam_ref, dA_ref, _ = s.adjoint(x, g)
+    xa = x.clone()
+    lam, dA, _ = s.adjoint(xa, g, lam=xa)
+    assert lam.data_ptr() == xa.data_ptr()
+    assert torch.equal(lam, lam_ref) and torch.equal(dA, dA_ref)
+
+
+def test_host_pointers_nonsymmetric_adjoint():
+    A = M.convdiff3d_upwind(N=14).A
+    rng = np.random.default_rng(8)
+    b, g = rng.uniform(-1, 1, A.n), rng.uniform(-1, 1, A.n)
+    s_host = api.Solver(A.row_ptr, A.col_idx, A.values, {"solver": "BICGSTAB"})
+    x_host, _ = s_host.solve(b)
+    lam, dA, info = s_host.adjoint(x_host, g)
+    assert info.status == 0
+    lam2, dA2, _ = gpu_solver(A, {"solver": "BICGSTAB"}).adjoint(dev(x_host), dev(g))
+    assert np.array_equal(lam, lam2.cpu().numpy()) and np.array_equal(dA, dA2.cpu().numpy())
+
+
 def test_repeated_solves_are_deterministic():
     A = M.diffusion3d_grf(N=20).A
     s = gpu_solver(A)
