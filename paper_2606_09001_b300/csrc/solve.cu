@@ -194,14 +194,15 @@ __global__ void __launch_bounds__(BLOCK) k_prolong(int n, const int *__restrict_
 enum Fin { FIN_NONE = 0, FIN_PCG_BETA = 1 };
 
 // Finisher of the PCG preconditioner application: rz_new = r.z (and, for the
-// flexible form, z.r_old); beta = rz_new / rz (or (rz_new - z.r_old) / rz);
-// the first iteration after a (re)start uses beta = 0.
+// flexible form, z.q with q = A p of the previous iteration); beta = rz_new / rz,
+// or for the flexible form z.(r - r_old) / rz = -alpha z.q / rz (r - r_old =
+// -alpha q); the first iteration after a (re)start uses beta = 0.
 __device__ void finish_pcg_beta(DevScalars *sc, const double *tot) {
     const double rz_new = tot[0];
     if (!finite(rz_new)) { fail(sc, AMG_NAN); return; }
     double beta = 0.0;
     if (!sc->first) {
-        const double num = sc->flexible ? rz_new - tot[1] : rz_new;
+        const double num = sc->flexible ? -sc->alpha * tot[1] : rz_new;
         beta = num / sc->rz;
     }
     sc->first = 0;
@@ -210,12 +211,13 @@ __device__ void finish_pcg_beta(DevScalars *sc, const double *tot) {
 }
 
 // x = t + W (b - A t): post-smoothing.  FIN_PCG_BETA also reduces r.z (r = b,
-// the V-cycle input) and z.r_old, and finishes beta.
+// the V-cycle input) and, for the flexible form, z.qprev (qprev = A p of the
+// previous iteration), and finishes beta.
 template <int VEC, typename TB, typename TM, typename TO, int FIN>
 __global__ void __launch_bounds__(BLOCK) k_postsmooth(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                       const TM *__restrict__ v, const TM *__restrict__ w,
                                                       const TB *__restrict__ b, const TM *__restrict__ t,
-                                                      TO *__restrict__ out, const double *__restrict__ rold,
+                                                      TO *__restrict__ out, const double *__restrict__ qprev,
                                                       DevScalars *sc, double *part, int cap, unsigned *counter) {
     pdl_wait();
     pdl_trigger();
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(BLOCK) k_postsmooth(int n, const int *__restri
         out[i] = o;
         if (FIN == FIN_PCG_BETA) {
             acc[0] += ld<double>(b, i) * fcvt<double>(o);
-            if (rold) acc[1] += rold[i] * fcvt<double>(o);
+            if (qprev) acc[1] += qprev[i] * fcvt<double>(o);
         }
     }
     ROW_LOOP_END
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(BLOCK) k_postsmooth(int n, const int *__restri
 // Coarsest level: x = A_c^-1 b in FP64 with the stored dense inverse (one block).
 template <typename TI, typename TO, int FIN>
 __global__ void __launch_bounds__(BLOCK) k_coarse(int m, const double *__restrict__ cinv, const TI *__restrict__ b,
-                                                  TO *__restrict__ x, const double *__restrict__ rold,
+                                                  TO *__restrict__ x, const double *__restrict__ qprev,
                                                   DevScalars *sc, double *part, int cap, unsigned *counter) {
     pdl_wait();
     pdl_trigger();
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(BLOCK) k_coarse(int m, const double *__restric
         x[i] = o;
         if (FIN == FIN_PCG_BETA) {
             acc[0] += sb[i] * fcvt<double>(o);
-            if (rold) acc[1] += rold[i] * fcvt<double>(o);
+            if (qprev) acc[1] += qprev[i] * fcvt<double>(o);
         }
     }
     if (FIN == FIN_PCG_BETA) {
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(BLOCK) k_dense_apply(int m, int ld, const TMAT
 // PCG start: x = 0, r = b, p = 0, ||b||^2.
 // cg: unpreconditioned CG, whose r.z is r.r (b.b here) with no beta pass.
 __global__ void __launch_bounds__(BLOCK) k_pcg_init(int n, const double *__restrict__ b, double *x, double *r,
-                                                    double *p, double *rold, float *r32, DevScalars *sc, double rtol,
+                                                    double *p, float *r32, DevScalars *sc, double rtol,
                                                     double *part, int cap, unsigned *counter, int cg) {
     pdl_wait();
     pdl_trigger();
@@ -339,7 +341,6 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(int n, const double *__restr
         r[i] = bi;
         if (r32) r32[i] = f64_to_f32_rn(bi);
         p[i] = 0.0;
-        if (rold) rold[i] = 0.0;
         acc[0] += bi * bi;
     }
     double tot[1];
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(BLOCK) k_spmv_fin(int n, const int *__restrict
 
 // x += alpha p; (r_old = r;) r -= alpha q; ||r||^2; convergence / iteration cap.
 __global__ void __launch_bounds__(BLOCK) k_pcg_update(int n, double *x, double *r, const double *__restrict__ p,
-                                                      const double *__restrict__ q, double *rold, float *r32,
+                                                      const double *__restrict__ q, float *r32,
                                                       DevScalars *sc, double *part, int cap, unsigned *counter,
                                                       int cg) {
     pdl_wait();
@@ -451,9 +452,7 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(int n, double *x, double *
     double acc[1] = {0.0};
     for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
         x[i] += alpha * p[i];
-        const double ri = r[i];
-        if (rold) rold[i] = ri;
-        const double rn = ri - alpha * q[i];
+        const double rn = r[i] - alpha * q[i];
         r[i] = rn;
         if (r32) r32[i] = f64_to_f32_rn(rn);
         acc[0] += rn * rn;
@@ -732,7 +731,7 @@ ProfScope::~ProfScope() {
 int workspace_init(Workspace &W, int n) {
     W.n = n;
     DevArena &a = W.arena;
-    double **vecs[] = {&W.b, &W.x, &W.r, &W.z, &W.p, &W.q, &W.rold, &W.rh, &W.v, &W.ph, &W.s, &W.sh, &W.t, &W.aux};
+    double **vecs[] = {&W.b, &W.x, &W.r, &W.z, &W.p, &W.q, &W.rh, &W.v, &W.ph, &W.s, &W.sh, &W.t, &W.aux};
     for (double **pp : vecs) AMG_TRY(a.alloc(pp, (size_t)n));
     AMG_TRY(a.alloc(&W.r32, (size_t)n));
     AMG_TRY(a.alloc(&W.scal, 1));
@@ -871,7 +870,7 @@ struct OpPost {
     const TB *b;
     const TM *t;
     TO *out;
-    const double *rold;
+    const double *qprev;  // flexible PCG: A p of the previous iteration (else null)
     double *part;
     int cap;
     unsigned *counter;
@@ -885,13 +884,13 @@ struct OpPost {
     using GX = TM;
     __device__ const GX *gsrc() const { return t; }
     __device__ Pre load(int i) const {
-        return Pre{__ldg(t + i), __ldg(w + i), __ldg(b + i), (FIN == FIN_PCG_BETA && rold) ? __ldg(rold + i) : 0.0};
+        return Pre{__ldg(t + i), __ldg(w + i), __ldg(b + i), (FIN == FIN_PCG_BETA && qprev) ? __ldg(qprev + i) : 0.0};
     }
     static constexpr bool SELF = true;
     __device__ Pre load_rest(int i) const {
-        return Pre{(TM)0, __ldg(w + i), __ldg(b + i), (FIN == FIN_PCG_BETA && rold) ? __ldg(rold + i) : 0.0};
+        return Pre{(TM)0, __ldg(w + i), __ldg(b + i), (FIN == FIN_PCG_BETA && qprev) ? __ldg(qprev + i) : 0.0};
     }
-    // row operands the sliced-ELL kernel stages with each tile: w, b (and r_old)
+    // row operands the sliced-ELL kernel stages with each tile: w, b (and qprev)
     static constexpr int NROWV = FIN == FIN_PCG_BETA ? 3 : 2;
     static constexpr int ROWV_BYTES = (int)(sizeof(TM) + sizeof(TB)) + (FIN == FIN_PCG_BETA ? 8 : 0);
     __device__ int rowv(const void **src, int *eb) const {
@@ -899,14 +898,14 @@ struct OpPost {
         eb[0] = (int)sizeof(TM);
         src[1] = b;
         eb[1] = (int)sizeof(TB);
-        if (FIN != FIN_PCG_BETA || !rold) return 2;
-        src[2] = rold;
+        if (FIN != FIN_PCG_BETA || !qprev) return 2;
+        src[2] = qprev;
         eb[2] = 8;
         return 3;
     }
     __device__ Pre load_rowv(const unsigned char *const *rv, int rl) const {
         return Pre{(TM)0, reinterpret_cast<const TM *>(rv[0])[rl], reinterpret_cast<const TB *>(rv[1])[rl],
-                   (FIN == FIN_PCG_BETA && rold) ? reinterpret_cast<const double *>(rv[2])[rl] : 0.0};
+                   (FIN == FIN_PCG_BETA && qprev) ? reinterpret_cast<const double *>(rv[2])[rl] : 0.0};
     }
     __device__ void put_self(Pre &p, GX v) const { p.t = v; }
     __device__ void finish(int i, TM s, const Pre &p, double (&acc)[2]) const {
@@ -2037,7 +2036,7 @@ int tail_prepare(Hierarchy *h, cudaStream_t) {
 }
 
 template <typename TM>
-static int launch_tail(Hierarchy *h, Workspace &W, const double *b0, double *z0, const double *rold, int fin,
+static int launch_tail(Hierarchy *h, Workspace &W, const double *b0, double *z0, const double *qprev, int fin,
                        cudaStream_t s) {
     const bool mixed = sizeof(TM) == 4;
     cudaLaunchConfig_t cfg = {};
@@ -2057,7 +2056,7 @@ static int launch_tail(Hierarchy *h, Workspace &W, const double *b0, double *z0,
         set_last_error("fused tail: %d bytes of shared memory refused", (int)cfg.dynamicSmemBytes);
         return AMG_ERR_CUDA;
     }
-    AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, tail::k_tail<TM>, args, b0, z0, rold, fin, W.scal));
+    AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, tail::k_tail<TM>, args, b0, z0, qprev, fin, W.scal));
     return AMG_OK;
 }
 
@@ -2194,15 +2193,16 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
     auto Tv = [&](const Level &lv) -> TM * { return (TM *)(mixed ? (void *)lv.t32 : (void *)lv.t); };
     auto Bv = [&](const Level &lv) -> TM * { return (TM *)(mixed ? (void *)lv.b32 : (void *)lv.b); };
     auto Xv = [&](const Level &lv) -> TM * { return (TM *)(mixed ? (void *)lv.x32 : (void *)lv.x); };
-    const double *rold = (fin == FIN_PCG_BETA && h->cfg.precision == AMG_PRECISION_MIXED) ? W.rold : nullptr;
+    // the flexible beta's z.q with the previous iteration's q = A p
+    const double *qprev = (fin == FIN_PCG_BETA && h->cfg.precision == AMG_PRECISION_MIXED) ? W.q : nullptr;
 
     if (L == 1) {
         const double m = h->nc;
         TRACE("coarse", 0, m * m * 8.0 + 16.0 * m + (fin == FIN_PCG_BETA ? 8.0 * m : 0.0));
         if (fin == FIN_PCG_BETA)
-            AMG_TRY(launch_k(k_coarse<double, double, FIN_PCG_BETA>, 1, BLOCK, 0, s, h->nc, h->cinv, b0, z0, rold, W.scal, W.part, cap, W.counter));
+            AMG_TRY(launch_k(k_coarse<double, double, FIN_PCG_BETA>, 1, BLOCK, 0, s, h->nc, h->cinv, b0, z0, qprev, W.scal, W.part, cap, W.counter));
         else
-            AMG_TRY(launch_k(k_coarse<double, double, FIN_NONE>, 1, BLOCK, 0, s, h->nc, h->cinv, b0, z0, rold, W.scal, W.part, cap, W.counter));
+            AMG_TRY(launch_k(k_coarse<double, double, FIN_NONE>, 1, BLOCK, 0, s, h->nc, h->cinv, b0, z0, qprev, W.scal, W.part, cap, W.counter));
         AMG_LAUNCH_CHECK();
         return AMG_OK;
     }
@@ -2211,7 +2211,7 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
     const int tl = h->tail_start >= 0 ? h->tail_start : (mm > 0 ? mm : L - 1);
     if (h->tail_start == 0) {
         TRACE("tail", 0, tail_bytes(h, vb));
-        return launch_tail<TM>(h, W, b0, z0, rold, fin == FIN_PCG_BETA, s);
+        return launch_tail<TM>(h, W, b0, z0, qprev, fin == FIN_PCG_BETA, s);
     }
     // down
     for (int l = 0; l < tl; ++l) {
@@ -2307,12 +2307,12 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         }
         {
             const double ob = l == 0 ? 8.0 : vb;
-            TRACE("postsmooth", l, csr_bytes(lv.A, vb) + n * (2.0 * vb + bb + ob) + (rold && l == 0 ? 8.0 * n : 0.0));
+            TRACE("postsmooth", l, csr_bytes(lv.A, vb) + n * (2.0 * vb + bb + ob) + (qprev && l == 0 ? 8.0 * n : 0.0));
             if (lv.sa_post.rt) {
                 const int *rp_ = lv.A.rp, *ci_ = lv.A.ci;
                 if (l == 0 && fin == FIN_PCG_BETA)
                     AMG_TRY(stream_launch<TM>(lv.sa_post, n, rp_, ci_, Av(lv.A),
-                                              OpPost<double, TM, double, FIN_PCG_BETA>{W.scal, Wv(lv), b0, Tv(lv), z0, rold,
+                                              OpPost<double, TM, double, FIN_PCG_BETA>{W.scal, Wv(lv), b0, Tv(lv), z0, qprev,
                                                                                          W.part, cap, W.counter},
                                               err, s));
                 else if (l == 0)
@@ -2328,7 +2328,7 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
             } else if (l == 0) {
                 if (fin == FIN_PCG_BETA) {
                     VEC_DISPATCH(lv.vec_a, AMG_TRY(launch_k(k_postsmooth<V, double, TM, double, FIN_PCG_BETA>, grid_rows(n, V, cap), BLOCK, 0, s, 
-                                               n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), b0, Tv(lv), z0, rold, W.scal, W.part, cap, W.counter)));
+                                               n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), b0, Tv(lv), z0, qprev, W.scal, W.part, cap, W.counter)));
                 } else {
                     VEC_DISPATCH(lv.vec_a, AMG_TRY(launch_k(k_postsmooth<V, double, TM, double, FIN_NONE>, grid_rows(n, V, cap), BLOCK, 0, s, 
                                                n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), b0, Tv(lv), z0, nullptr, W.scal, W.part, cap, W.counter)));
@@ -2382,8 +2382,8 @@ static int pcg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
     }
     AMG_TRY(spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s));
     {
-        TRACE("pcg_update", 0, (mixed ? 56.0 : 48.0) * n);
-        AMG_TRY(launch_k(k_pcg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, W.r, W.p, W.q, mixed ? W.rold : nullptr,
+        TRACE("pcg_update", 0, (mixed ? 52.0 : 48.0) * n);
+        AMG_TRY(launch_k(k_pcg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, W.r, W.p, W.q,
                          mixed ? W.r32 : nullptr, W.scal,
                                                            W.part, cap, W.counter, 0));
     }
@@ -2400,7 +2400,7 @@ static int cg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
     AMG_TRY(spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s));
     {
         TRACE("pcg_update", 0, 48.0 * n);
-        AMG_TRY(launch_k(k_pcg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, W.r, W.p, W.q, nullptr, nullptr, W.scal,
+        AMG_TRY(launch_k(k_pcg_update, stream_grid(n, cap), BLOCK, 0, s, n, W.x, W.r, W.p, W.q, nullptr, W.scal,
                          W.part, cap, W.counter, 1));
     }
     AMG_LAUNCH_CHECK();
@@ -2518,12 +2518,12 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
 
     AMG_TRY(set_control(W, s, 0, AMG_OK, flexible, c.max_iter, 1));
     {
-        TRACE(bicg ? "bicg_init" : "pcg_init", 0, (bicg ? 48.0 : 40.0) * n);
+        TRACE(bicg ? "bicg_init" : "pcg_init", 0, (bicg ? 48.0 : 32.0) * n);
         if (bicg)
             AMG_TRY(launch_k(k_bicg_init, stream_grid(n, cap), BLOCK, 0, s, n, W.b, W.x, W.r, W.rh, W.p, W.v, W.scal, c.rtol, W.part,
                                                               cap, W.counter));
         else
-            AMG_TRY(launch_k(k_pcg_init, stream_grid(n, cap), BLOCK, 0, s, n, W.b, W.x, W.r, W.p, W.rold,
+            AMG_TRY(launch_k(k_pcg_init, stream_grid(n, cap), BLOCK, 0, s, n, W.b, W.x, W.r, W.p,
                              c.precision == AMG_PRECISION_MIXED ? W.r32 : nullptr, W.scal, c.rtol, W.part, cap,
                              W.counter, precond ? 0 : 1));
     }

@@ -47,7 +47,7 @@ struct ProfScope {
 struct Workspace {
     int n = 0;
     double *b = nullptr, *x = nullptr;                     // right-hand side / solution (handle-owned)
-    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *rold = nullptr;
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     double *rh = nullptr, *v = nullptr, *ph = nullptr, *s = nullptr, *sh = nullptr, *t = nullptr;
     double *aux = nullptr;                                 // adjoint: forward solution x
     float *r32 = nullptr;                                  // mixed PCG: FP32 copy of r (the V-cycle's input)

@@ -175,11 +175,11 @@ __device__ __forceinline__ void stage(TM *xs, int len, G g) {
 }
 
 // b0/z0: finest right-hand side and result when the tail starts at level 0
-// (FP64); rold: flexible PCG's previous residual (mixed); fin: compute the PCG
-// beta from r.z (level-0 tails only).
+// (FP64); qprev: flexible PCG's previous iteration's q = A p (mixed); fin:
+// compute the PCG beta from r.z (level-0 tails only).
 template <typename TM>
 __global__ void __launch_bounds__(THREADS) k_tail(const __grid_constant__ TArgs<TM> a, const double *__restrict__ b0,
-                                                  double *__restrict__ z0, const double *__restrict__ rold, int fin,
+                                                  double *__restrict__ z0, const double *__restrict__ qprev, int fin,
                                                   DevScalars *sc) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(THREADS) k_tail(const __grid_constant__ TArgs<
                     z0[i] = o;
                     if (fin) {
                         acc[0] += __ldg(b0 + i) * o;
-                        if (rold) acc[1] += __ldg(rold + i) * o;
+                        if (qprev) acc[1] += __ldg(qprev + i) * o;
                     }
                 } else {
                     lv.x[i] = xi;
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(THREADS) k_tail(const __grid_constant__ TArgs<
         if (k > 0) cluster.sync();
     }
     if (l0 && fin) {
-        // cluster-wide reduction of r.z (and z.r_old) into CTA 0, then beta
+        // cluster-wide reduction of r.z (and z.qprev) into CTA 0, then beta
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         for (int q = 0; q < 2; ++q) {
             double v = warp_sum(acc[q]);
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(THREADS) k_tail(const __grid_constant__ TArgs<
                 sc->done = 1;
             } else {
                 double beta = 0.0;
-                if (!sc->first) beta = (sc->flexible ? tot[0] - tot[1] : tot[0]) / sc->rz;
+                if (!sc->first) beta = (sc->flexible ? -sc->alpha * tot[1] : tot[0]) / sc->rz;  // z.(r - r_old) = -alpha z.q
                 sc->first = 0;
                 sc->beta = beta;
                 sc->rz = tot[0];
