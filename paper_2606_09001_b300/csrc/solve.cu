@@ -368,10 +368,23 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_p(int n, const double *__restrict
     pdl_trigger();
     if (sc->done) return;
     const double beta = sc->beta;
+    // pairs of entries as 16-byte accesses (the workspace vectors are
+    // allocation-aligned), then the odd last entry
+    const int n2 = n >> 1, g0 = blockIdx.x * BLOCK + threadIdx.x, gs = gridDim.x * BLOCK;
+    const double2 *z2 = reinterpret_cast<const double2 *>(z);
+    double2 *p2 = reinterpret_cast<double2 *>(p);
     if (beta == 0.0) {  // first step after a (re)start: p = z exactly
-        for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) p[i] = z[i];
+        for (int i = g0; i < n2; i += gs) p2[i] = z2[i];
+        if ((n & 1) && g0 == 0) p[n - 1] = z[n - 1];
     } else {
-        for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) p[i] = z[i] + beta * p[i];
+        for (int i = g0; i < n2; i += gs) {
+            const double2 zv = z2[i];
+            double2 pv = p2[i];
+            pv.x = zv.x + beta * pv.x;
+            pv.y = zv.y + beta * pv.y;
+            p2[i] = pv;
+        }
+        if ((n & 1) && g0 == 0) p[n - 1] = z[n - 1] + beta * p[n - 1];
     }
 }
 
@@ -450,7 +463,27 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_update(int n, double *x, double *
     if (sc->done) return;
     const double alpha = sc->alpha;
     double acc[1] = {0.0};
-    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+    // pairs of entries as 16-byte accesses (the workspace vectors are
+    // allocation-aligned), then the odd last entry
+    const int n2 = n >> 1, g0 = blockIdx.x * BLOCK + threadIdx.x, gs = gridDim.x * BLOCK;
+    double2 *x2 = reinterpret_cast<double2 *>(x), *r2 = reinterpret_cast<double2 *>(r);
+    const double2 *p2 = reinterpret_cast<const double2 *>(p), *q2 = reinterpret_cast<const double2 *>(q);
+    for (int i = g0; i < n2; i += gs) {
+        double2 xv = x2[i];
+        const double2 pv = p2[i], qv = q2[i];
+        double2 rv = r2[i];
+        xv.x += alpha * pv.x;
+        xv.y += alpha * pv.y;
+        rv.x = rv.x - alpha * qv.x;
+        rv.y = rv.y - alpha * qv.y;
+        x2[i] = xv;
+        r2[i] = rv;
+        if (r32) reinterpret_cast<float2 *>(r32)[i] = make_float2(f64_to_f32_rn(rv.x), f64_to_f32_rn(rv.y));
+        acc[0] += rv.x * rv.x;
+        acc[0] += rv.y * rv.y;
+    }
+    if ((n & 1) && g0 == 0) {
+        const int i = n - 1;
         x[i] += alpha * p[i];
         const double rn = r[i] - alpha * q[i];
         r[i] = rn;
