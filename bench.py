@@ -96,9 +96,13 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons every 20 ms.  Each sample carries
+    nvidia-smi's own timestamp (the pipe may deliver lines late), and the
+    summary keeps the samples inside the window mark() records: the timed
+    region.  With none inside (a region shorter than the sampling period), it
+    keeps every sample and says so."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
@@ -106,9 +110,10 @@ class ClockSampler:
         self.samples = []
         self.proc = None
         self.gpu_id = gpu_id
+        self.window = None
 
     def start(self):
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "20"]
         if self.gpu_id:
             cmd += ["-i", self.gpu_id]
         try:
@@ -120,14 +125,28 @@ class ClockSampler:
         self.thread.start()
 
     def _read(self):
+        import datetime
         for line in self.proc.stdout:
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 7:
-                self.samples.append(parts)
+            if len(parts) >= 8:
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                except ValueError:
+                    ts = None
+                self.samples.append([ts] + parts[1:])
+
+    @staticmethod
+    def now():
+        import datetime
+        return datetime.datetime.now()
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.1)  # the samples of the region's last moments reach the pipe
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -136,12 +155,17 @@ class ClockSampler:
         self.thread.join(timeout=2)
         if not self.samples:
             return None
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        chosen, where = self.samples, "around the timed region (none inside it)"
+        if self.window:
+            inside = [x for x in self.samples if x[0] is not None and self.window[0] <= x[0] <= self.window[1]]
+            if inside:
+                chosen, where = inside, "inside the timed region"
+        sm = [float(x[1]) for x in chosen if x[1].replace(".", "").isdigit()]
+        mx = [float(x[2]) for x in chosen if x[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower() == "active"})
+        reasons = sorted({names[k] for x in chosen for k in range(4) if x[4 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(chosen), "sampled": where, "interval_ms": 20}
 
 
 def dist_init():
@@ -418,6 +442,7 @@ def run_ours(args):
         barrier()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = ClockSampler.now()
         e0.record(stream)
         torch.cuda.nvtx.range_push(f"timed_{form}")  # profilers select the timed region by this range
         for _ in range(args.steps):
@@ -425,8 +450,11 @@ def run_ours(args):
         torch.cuda.nvtx.range_pop()
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        w1 = ClockSampler.now()
         barrier()
         ms = e0.elapsed_time(e1) / args.steps
+        if sampler:
+            sampler.mark(w0, w1)
         clocks = sampler.stop() if sampler else None
         launches, _ = s.profile_records()
         if world > 1:
@@ -641,6 +669,7 @@ def run_batched(args, world, rank, dev, barrier):
         barrier()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = ClockSampler.now()
         e0.record(stream)
         torch.cuda.nvtx.range_push(f"timed_{form}")  # profilers select the timed region by this range
         for _ in range(args.steps):
@@ -648,8 +677,11 @@ def run_batched(args, world, rank, dev, barrier):
         torch.cuda.nvtx.range_pop()
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        w1 = ClockSampler.now()
         barrier()
         ms = e0.elapsed_time(e1) / args.steps
+        if sampler:
+            sampler.mark(w0, w1)
         clocks = sampler.stop() if sampler else None
         launches, _ = s.profile_records()
         if world > 1:
