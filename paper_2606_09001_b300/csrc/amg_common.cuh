@@ -230,10 +230,12 @@ struct Hierarchy {
     int tail_cluster = 0;
     std::vector<unsigned char> tail_args64, tail_args32;  // host copies of the kernel's parameter tables
     int tail_smem64 = 0, tail_smem32 = 0;  // dynamic shared memory of each table's launch
-    // One Krylov iteration captured as a CUDA graph (replayed per iteration);
-    // iter_kind: which iteration it holds, iter_kernels: launches it contains.
+    // iter_count Krylov iterations captured as one CUDA graph (replayed between
+    // the host's convergence polls); iter_kind: which iteration it holds,
+    // iter_kernels: launches it contains.
     cudaGraphExec_t iter_exec = nullptr;
     int iter_kind = -1;
+    int iter_count = 0;
     int iter_kernels = 0;
     DevArena arena;
     double setup_ms = 0.0;

@@ -2487,14 +2487,21 @@ static int iterate(Hierarchy *h, Workspace &W, int kind, cudaStream_t s) {
 // replayed, which removes most of the per-launch cost of the ~25 kernels; the
 // launch count still advances by the kernels the graph holds.  With
 // per-kernel tracing on, the kernels are launched directly.
-static int run_iteration(Hierarchy *h, Workspace &W, int kind, cudaStream_t s) {
-    if (W.prof.on) return iterate(h, W, kind, s);
-    if (!h->iter_exec || h->iter_kind != kind) {
+// `count` Krylov iterations: one CUDA graph (captured once per solver kind)
+// whose iterations are chained by programmatic edges like the kernels within
+// one, or, while tracing, plain launches.
+static int run_iterations(Hierarchy *h, Workspace &W, int kind, int count, cudaStream_t s) {
+    if (W.prof.on) {
+        for (int k = 0; k < count; ++k) AMG_TRY(iterate(h, W, kind, s));
+        return AMG_OK;
+    }
+    if (!h->iter_exec || h->iter_kind != kind || h->iter_count != count) {
         if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
         h->iter_exec = nullptr;
         const long long before = W.prof.launches;
         AMG_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        const int rc = iterate(h, W, kind, s);
+        int rc = AMG_OK;
+        for (int k = 0; k < count && rc >= 0; ++k) rc = iterate(h, W, kind, s);
         cudaGraph_t g = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(s, &g);
         if (rc < 0) {
@@ -2506,6 +2513,7 @@ static int run_iteration(Hierarchy *h, Workspace &W, int kind, cudaStream_t s) {
         cudaGraphDestroy(g);
         AMG_CUDA_TRY(ie);
         h->iter_kind = kind;
+        h->iter_count = count;
         h->iter_kernels = (int)(W.prof.launches - before);
         W.prof.launches = before;
     }
@@ -2580,9 +2588,7 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
         // iterate until the device marks the solve done; the device sets done
         // at max_iter at the latest, launch_cap only guards the host loop
         for (;;) {
-            for (int k = 0; k < chunk; ++k) {
-                AMG_TRY(run_iteration(h, W, bicg ? (precond ? 3 : 2) : (precond ? 1 : 0), s));
-            }
+            AMG_TRY(run_iterations(h, W, bicg ? (precond ? 3 : 2) : (precond ? 1 : 0), chunk, s));
             launched += chunk;
             AMG_TRY(read_scalars(W, s));
             if (W.scal_h->done) break;
