@@ -175,24 +175,26 @@ __device__ void p_post(const MLevel<TM> &lv) {
 #undef MID_ROWS
 
 // x = M b, the dense end: one warp per row of 16-byte vectors, b staged in
-// shared memory (zero beyond m), FP64 accumulation; a lane's partial sum runs
-// over its vectors in order, then the warp's sum (the same order as the
-// dense kernel of the per-level cycle).
+// shared memory in FP64 (zero beyond m), FP32 entries widened on the integer
+// pipes, FP64 accumulation; a lane's partial sum runs over its vectors in
+// order, then the warp's sum (the same order as the dense kernel of the
+// per-level cycle).
 constexpr int DENSE_LD = 2048;
 
 template <typename TMAT, typename TV>
-__device__ void p_dense(int m, int ld, const TMAT *__restrict__ M, const TV *b, TV *x, TMAT *sb) {
-    for (int j = threadIdx.x; j < ld; j += blockDim.x) sb[j] = j < m ? (TMAT)b[j] : (TMAT)0;
+__device__ void p_dense(int m, int ld, const TMAT *__restrict__ M, const TV *b, TV *x, double *sb) {
+#pragma unroll 8
+    for (int j = threadIdx.x; j < ld; j += blockDim.x) sb[j] = j < m ? fcvt<double>(b[j]) : 0.0;
     __syncthreads();
     using V = typename std::conditional<sizeof(TMAT) == 4, float4, double2>::type;
     constexpr int VW = sizeof(V) / sizeof(TMAT);
     const int lane = threadIdx.x & 31;
     const int nv = ld / VW;
-    const V *bv = reinterpret_cast<const V *>(sb);
+    const double2 *bd = reinterpret_cast<const double2 *>(sb);
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += (gridDim.x * blockDim.x) >> 5) {
         const V *row = reinterpret_cast<const V *>(M + (size_t)i * ld);
         double s = 0.0;
-        constexpr int U = 8;
+        constexpr int U = 8;  // the per-pass kernel takes 16; the lane's order over q is the same
         for (int q0 = lane; q0 < nv; q0 += 32 * U) {
             V a[U];
 #pragma unroll
@@ -204,11 +206,14 @@ __device__ void p_dense(int m, int ld, const TMAT *__restrict__ M, const TV *b, 
             for (int u = 0; u < U; ++u) {
                 const int q = q0 + 32 * u;
                 if (q < nv) {
-                    const V c = bv[q];
-                    if constexpr (VW == 4)
-                        s += (double)a[u].x * c.x + (double)a[u].y * c.y + (double)a[u].z * c.z + (double)a[u].w * c.w;
-                    else
+                    if constexpr (VW == 4) {
+                        const double2 c0 = bd[2 * q], c1 = bd[2 * q + 1];
+                        s += f32_to_f64(a[u].x) * c0.x + f32_to_f64(a[u].y) * c0.y + f32_to_f64(a[u].z) * c1.x +
+                             f32_to_f64(a[u].w) * c1.y;
+                    } else {
+                        const double2 c = bd[q];
                         s += a[u].x * c.x + a[u].y * c.y;
+                    }
                 }
             }
         }
@@ -237,7 +242,7 @@ template <typename TM, typename TMAT>
 __global__ void __launch_bounds__(THREADS) k_mid(const __grid_constant__ MArgs<TM> a, unsigned *bar,
                                                  const int *done, int *err) {
     if (*done) return;  // no kernel writes the flag while this one runs: every CTA returns or none
-    __shared__ __align__(16) TMAT sb[DENSE_LD];
+    __shared__ __align__(16) double sb[DENSE_LD];
     const unsigned nb = gridDim.x;
     auto sync = [&]() -> bool {
         if (grid_barrier(bar, nb)) return true;

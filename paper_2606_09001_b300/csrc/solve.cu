@@ -278,7 +278,9 @@ __global__ void __launch_bounds__(BLOCK) k_coarse(int m, const double *__restric
 // The dense operator of the coarse end of the cycle: x = M b (M m x m, rows
 // padded to ld entries with zeros), one warp per row reading 16-byte vectors
 // with all of a lane's loads of the row in flight together; b is staged into
-// shared memory (zero beyond m); FP64 accumulation.
+// shared memory in FP64 (zero beyond m); FP64 accumulation.  FP32 entries of
+// M are widened on the integer pipes (exact, like any widening), so the FP64
+// pipe runs only the products' FMAs.
 constexpr int DENSE_MAX_LD = 2048;
 
 template <typename TMAT, typename TV>
@@ -287,18 +289,19 @@ __global__ void __launch_bounds__(BLOCK) k_dense_apply(int m, int ld, const TMAT
     pdl_wait();
     pdl_trigger();
     if (*done) return;
-    __shared__ __align__(16) TMAT sb[DENSE_MAX_LD];
-    for (int j = threadIdx.x; j < ld; j += BLOCK) sb[j] = j < m ? (TMAT)b[j] : (TMAT)0;
+    __shared__ __align__(16) double sb[DENSE_MAX_LD];
+#pragma unroll 8
+    for (int j = threadIdx.x; j < ld; j += BLOCK) sb[j] = j < m ? fcvt<double>(b[j]) : 0.0;
     __syncthreads();
     using V = typename std::conditional<sizeof(TMAT) == 4, float4, double2>::type;
     constexpr int VW = sizeof(V) / sizeof(TMAT);
     const int lane = threadIdx.x & 31;
     const int nv = ld / VW;
+    const double2 *bd = reinterpret_cast<const double2 *>(sb);
     for (int i = (blockIdx.x * BLOCK + threadIdx.x) >> 5; i < m; i += (gridDim.x * BLOCK) >> 5) {
         const V *row = reinterpret_cast<const V *>(M + (size_t)i * ld);
-        const V *bv = reinterpret_cast<const V *>(sb);
         double s = 0.0;
-        constexpr int U = 8;
+        constexpr int U = 16;  // 16-byte vectors per lane in flight: a 2048-float row in one round
         for (int q0 = lane; q0 < nv; q0 += 32 * U) {
             V a[U];
 #pragma unroll
@@ -310,11 +313,14 @@ __global__ void __launch_bounds__(BLOCK) k_dense_apply(int m, int ld, const TMAT
             for (int u = 0; u < U; ++u) {
                 const int q = q0 + 32 * u;
                 if (q < nv) {
-                    const V c = bv[q];
-                    if constexpr (VW == 4)
-                        s += (double)a[u].x * c.x + (double)a[u].y * c.y + (double)a[u].z * c.z + (double)a[u].w * c.w;
-                    else
+                    if constexpr (VW == 4) {
+                        const double2 c0 = bd[2 * q], c1 = bd[2 * q + 1];
+                        s += f32_to_f64(a[u].x) * c0.x + f32_to_f64(a[u].y) * c0.y + f32_to_f64(a[u].z) * c1.x +
+                             f32_to_f64(a[u].w) * c1.y;
+                    } else {
+                        const double2 c = bd[q];
                         s += a[u].x * c.x + a[u].y * c.y;
+                    }
                 }
             }
         }
