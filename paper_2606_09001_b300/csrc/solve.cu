@@ -130,6 +130,32 @@ __device__ __forceinline__ TM ld(const T *p, int i) { return fcvt<TM>(__ldg(p + 
 
 #define ROW_LOOP_END }
 
+// sum over k = k0, k0 + VEC, ... < e of v[k] * g(ci[k]), in that order: the
+// indices and values of ROW_UNR terms load before their gathers, so a lane
+// waits on two round trips per ROW_UNR terms instead of two per term.
+constexpr int ROW_UNR = 4;
+
+template <int VEC, typename TM, class G>
+__device__ __forceinline__ TM row_dot(const int *__restrict__ ci, const TM *__restrict__ v, int k0, int e, G g) {
+    TM s = 0;
+    for (int kb = k0; kb < e; kb += VEC * ROW_UNR) {
+        int c[ROW_UNR];
+        TM a[ROW_UNR];
+#pragma unroll
+        for (int u = 0; u < ROW_UNR; ++u) {
+            const int k = kb + u * VEC;
+            if (k < e) {
+                c[u] = __ldg(ci + k);
+                a[u] = __ldg(v + k);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < ROW_UNR; ++u)
+            if (kb + u * VEC < e) s += a[u] * g(c[u]);
+    }
+    return s;
+}
+
 // r = b - A (W b): pre-smoothing from x = 0 fused with the residual.
 template <int VEC, typename TB, typename TM>
 __global__ void __launch_bounds__(BLOCK) k_presmooth(int n, const int *__restrict__ rp, const int *__restrict__ ci,
@@ -140,13 +166,7 @@ __global__ void __launch_bounds__(BLOCK) k_presmooth(int n, const int *__restric
     if (*done) return;
     ROW_LOOP(VEC, n)
     TM s = 0;
-    if (valid) {
-        const int e = rp[i + 1];
-        for (int k = rp[i] + lane_; k < e; k += VEC) {
-            const int j = ci[k];
-            s += v[k] * (ld<TM>(w, j) * ld<TM>(b, j));
-        }
-    }
+    if (valid) s = row_dot<VEC>(ci, v, rp[i] + lane_, rp[i + 1], [&](int j) { return ld<TM>(w, j) * ld<TM>(b, j); });
     s = group_sum<VEC>(s);
     if (valid && lane_ == 0) r[i] = ld<TM>(b, i) - s;
     ROW_LOOP_END
@@ -162,10 +182,7 @@ __global__ void __launch_bounds__(BLOCK) k_spmv(int n, const int *__restrict__ r
     if (*done) return;
     ROW_LOOP(VEC, n)
     TM s = 0;
-    if (valid) {
-        const int e = rp[i + 1];
-        for (int k = rp[i] + lane_; k < e; k += VEC) s += v[k] * ld<TM>(x, ci[k]);
-    }
+    if (valid) s = row_dot<VEC>(ci, v, rp[i] + lane_, rp[i + 1], [&](int j) { return ld<TM>(x, j); });
     s = group_sum<VEC>(s);
     if (valid && lane_ == 0) y[i] = (TY)s;
     ROW_LOOP_END
@@ -182,10 +199,7 @@ __global__ void __launch_bounds__(BLOCK) k_prolong(int n, const int *__restrict_
     if (*done) return;
     ROW_LOOP(VEC, n)
     TM s = 0;
-    if (valid) {
-        const int e = rp[i + 1];
-        for (int k = rp[i] + lane_; k < e; k += VEC) s += v[k] * xc[ci[k]];
-    }
+    if (valid) s = row_dot<VEC>(ci, v, rp[i] + lane_, rp[i + 1], [&](int j) { return xc[j]; });
     s = group_sum<VEC>(s);
     if (valid && lane_ == 0) t[i] = ld<TM>(w, i) * ld<TM>(b, i) + s;
     ROW_LOOP_END
@@ -225,10 +239,7 @@ __global__ void __launch_bounds__(BLOCK) k_postsmooth(int n, const int *__restri
     double acc[2] = {0.0, 0.0};
     ROW_LOOP(VEC, n)
     TM s = 0;
-    if (valid) {
-        const int e = rp[i + 1];
-        for (int k = rp[i] + lane_; k < e; k += VEC) s += v[k] * t[ci[k]];
-    }
+    if (valid) s = row_dot<VEC>(ci, v, rp[i] + lane_, rp[i + 1], [&](int j) { return t[j]; });
     s = group_sum<VEC>(s);
     if (valid && lane_ == 0) {
         const TM bi = ld<TM>(b, i);
