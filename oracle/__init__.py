@@ -25,8 +25,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "amg_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# the same source built with -fopenmp: the solve phase's row loops on every
+# host core, for timing the CPU baseline only (parity uses the serial build)
+_LIB_THREADS = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 OK, MAXIT, BREAKDOWN, NOT_SPD, NAN = 0, 1, 2, 3, 4
 ERR_ARG, ERR_BAD_CSR, ERR_ZERO_DIAG, ERR_STALL, ERR_OOM = -1, -2, -3, -5, -6
@@ -34,15 +37,31 @@ ERR_ARG, ERR_BAD_CSR, ERR_ZERO_DIAG, ERR_STALL, ERR_OOM = -1, -2, -3, -5, -6
 PCG, BICGSTAB, CG, BICGSTAB_NOPREC = 0, 1, 2, 3
 
 
-def build(force: bool = False) -> str:
-    """Compile amg_oracle.c into liboracle.so (gcc, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+def build(force: bool = False, threads: bool = False) -> str:
+    """Compile amg_oracle.c into liboracle.so (gcc, no FMA contraction), or
+    with threads=True into liboracle_omp.so (the same with -fopenmp)."""
+    out = _LIB_THREADS if threads else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                "-shared", "-o", tmp, _SRC, "-lm"]
+        if threads:
+            cmd.insert(1, "-fopenmp")
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
+
+
+def threads_used() -> int:
+    """Threads the threaded build's parallel loops run on (OMP_NUM_THREADS,
+    else every core this process may use)."""
+    env = os.environ.get("OMP_NUM_THREADS", "").split(",")[0].strip()
+    if env.isdigit() and int(env) > 0:
+        return int(env)
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 class _Config(C.Structure):
@@ -62,11 +81,10 @@ _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 
 
-def lib():
-    global _lib
+def lib(threads: bool = False):
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if threads not in _libs:
+            L = C.CDLL(build(threads=threads))
             L.or_config_default.argtypes = [C.POINTER(_Config)]
             L.or_validate.argtypes = [C.c_int, C.c_longlong, _i32p, _i32p, _f64p]
             L.or_spmv.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p, _f64p]
@@ -100,13 +118,16 @@ def lib():
                                        C.POINTER(C.c_longlong)]
             L.or_hier_get.argtypes = [C.c_void_p, C.c_int, C.c_int, _i32p, _i32p, _f64p]
             L.or_hier_get_agg.argtypes = [C.c_void_p, C.c_int, _i32p]
+            L.or_hier_strength_nnz.argtypes = [C.c_void_p, C.c_int]
+            L.or_hier_strength_nnz.restype = C.c_longlong
+            L.or_hier_get_strength.argtypes = [C.c_void_p, C.c_int, _i32p, _i32p]
             L.or_hier_coarse_n.argtypes = [C.c_void_p]
             L.or_vcycle.argtypes = [C.c_void_p, _f64p, _f64p]
             L.or_dense_solve.argtypes = [C.c_void_p, _f64p, _f64p]
             L.or_solve.argtypes = [C.c_void_p, _f64p, _f64p, C.POINTER(_Info)]
             L.or_adjoint.argtypes = [C.c_void_p, _f64p, _f64p, _f64p, _f64p, C.POINTER(_Info)]
-            _lib = L
-    return _lib
+            _libs[threads] = L
+    return _libs[threads]
 
 
 def _csr_args(A):
@@ -210,11 +231,14 @@ class Level:
 class Hierarchy:
     """An oracle AMG hierarchy (owns C memory; freed on close/GC)."""
 
-    def __init__(self, A, config: dict | None = None):
+    def __init__(self, A, config: dict | None = None, threads: bool = False):
+        """threads=True: the threaded build (solve phase on every host core;
+        timing only, its dot products round differently from the serial build)."""
         self._cfg = _make_config(config)
+        self._L = lib(threads)
         rp, ci, v = _csr_args(A)
         st = C.c_int()
-        h = lib().or_setup(C.byref(self._cfg), A.n, A.nnz, rp, ci, v, C.byref(st))
+        h = self._L.or_setup(C.byref(self._cfg), A.n, A.nnz, rp, ci, v, C.byref(st))
         self.status = st.value
         if not h:
             raise OracleError(self.status)
@@ -227,11 +251,12 @@ class Hierarchy:
         value: the numeric re-setup of the cached-setup path (Sec. 2.1)."""
         st = C.c_int()
         v = np.ascontiguousarray(values, dtype=np.float64)
-        h = lib().or_resetup(self._h, v, C.byref(st))
+        h = self._L.or_resetup(self._h, v, C.byref(st))
         if not h:
             raise OracleError(st.value)
         out = Hierarchy.__new__(Hierarchy)
         out._cfg = self._cfg
+        out._L = self._L
         out._h = C.c_void_p(h)
         out.status = st.value
         out.n = self.n
@@ -242,11 +267,12 @@ class Hierarchy:
         transposes every level operator (the adjoint's hierarchy with
         adjoint_reuse)."""
         st = C.c_int()
-        h = lib().or_transposed(self._h, C.byref(st))
+        h = self._L.or_transposed(self._h, C.byref(st))
         if not h:
             raise OracleError(st.value)
         out = Hierarchy.__new__(Hierarchy)
         out._cfg = self._cfg
+        out._L = self._L
         out._h = C.c_void_p(h)
         out.status = st.value
         out.n = self.n
@@ -254,7 +280,7 @@ class Hierarchy:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().or_hier_free(self._h)
+            self._L.or_hier_free(self._h)
             self._h = None
 
     def __del__(self):
@@ -265,15 +291,15 @@ class Hierarchy:
 
     @property
     def nlevels(self) -> int:
-        return lib().or_hier_nlevels(self._h)
+        return self._L.or_hier_nlevels(self._h)
 
     @property
     def symmetric(self) -> bool:
-        return bool(lib().or_hier_symmetric(self._h))
+        return bool(self._L.or_hier_symmetric(self._h))
 
     def dims(self, l):
         n, nnzA, nc, nnzP = C.c_int(), C.c_longlong(), C.c_int(), C.c_longlong()
-        lib().or_hier_dims(self._h, l, C.byref(n), C.byref(nnzA), C.byref(nc), C.byref(nnzP))
+        self._L.or_hier_dims(self._h, l, C.byref(n), C.byref(nnzA), C.byref(nc), C.byref(nnzP))
         return n.value, nnzA.value, nc.value, nnzP.value
 
     def level(self, l) -> Level:
@@ -284,7 +310,7 @@ class Hierarchy:
             rp = np.empty(nrows + 1, np.int32)
             ci = np.empty(max(nnz, 1), np.int32)
             v = np.empty(max(nnz, 1))
-            lib().or_hier_get(self._h, l, which, rp, ci, v)
+            self._L.or_hier_get(self._h, l, which, rp, ci, v)
             return SimpleNamespace(row_ptr=rp, col_idx=ci[:nnz], values=v[:nnz], n=nrows, nnz=nnz)
 
         A = get(0, n, nnzA)
@@ -293,25 +319,37 @@ class Hierarchy:
             P = get(1, n, nnzP)
             R = get(2, nc, nnzP)
             agg = np.empty(n, np.int32)
-            lib().or_hier_get_agg(self._h, l, agg)
-        return Level(A, P, R, agg, lib().or_hier_rho(self._h, l))
+            self._L.or_hier_get_agg(self._h, l, agg)
+        return Level(A, P, R, agg, self._L.or_hier_rho(self._h, l))
+
+    def strength(self, l):
+        """The strength graph (row_ptr, col_idx) level l's aggregation used,
+        as the setup kept it, or None (classical levels, re-setups)."""
+        nnz = self._L.or_hier_strength_nnz(self._h, l)
+        if nnz < 0:
+            return None
+        n = self.dims(l)[0]
+        srp = np.empty(n + 1, np.int32)
+        sci = np.empty(max(nnz, 1), np.int32)
+        self._L.or_hier_get_strength(self._h, l, srp, sci)
+        return srp, sci[:nnz]
 
     def vcycle(self, b):
         x = np.empty(self.n)
-        lib().or_vcycle(self._h, np.ascontiguousarray(b, np.float64), x)
+        self._L.or_vcycle(self._h, np.ascontiguousarray(b, np.float64), x)
         return x
 
     def solve(self, b):
         x = np.empty(self.n)
         info = _Info()
-        lib().or_solve(self._h, np.ascontiguousarray(b, np.float64), x, C.byref(info))
+        self._L.or_solve(self._h, np.ascontiguousarray(b, np.float64), x, C.byref(info))
         return x, Info(info.status, info.iters, info.restarts, info.rel_res_true, info.rel_res_rec)
 
     def adjoint(self, x, g, nnz):
         lam = np.empty(self.n)
         dA = np.empty(nnz)
         info = _Info()
-        lib().or_adjoint(self._h, np.ascontiguousarray(x, np.float64),
+        self._L.or_adjoint(self._h, np.ascontiguousarray(x, np.float64),
                          np.ascontiguousarray(g, np.float64), lam, dA, C.byref(info))
         return lam, dA, Info(info.status, info.iters, info.restarts, info.rel_res_true,
                              info.rel_res_rec)

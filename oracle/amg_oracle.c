@@ -37,6 +37,16 @@
 #define OR_ERR_STALL (-5)
 #define OR_ERR_OOM (-6)
 
+/* The solve phase's row loops run on all host cores in the threaded build
+ * (-fopenmp, liboracle_omp.so, used only to time the CPU baseline); every
+ * such loop writes each entry once, so the split does not change any value.
+ * The parity build compiles them as plain serial loops. */
+#ifdef _OPENMP
+#define OR_PAR _Pragma("omp parallel for schedule(static)")
+#else
+#define OR_PAR
+#endif
+
 #define OR_MAX_LEVELS 32
 #define OR_DENSE_MAX 256
 
@@ -76,6 +86,7 @@ typedef struct or_hier {
     ocsr P[OR_MAX_LEVELS];  /* P[l]: n_l x n_{l+1}, l < nlevels-1 */
     ocsr R[OR_MAX_LEVELS];  /* R[l] = P[l]^T */
     int *agg[OR_MAX_LEVELS];
+    ocsr S[OR_MAX_LEVELS];        /* strength graph the aggregation of level l used (setup only) */
     double *dinv[OR_MAX_LEVELS];  /* smoother weight / d_i, per row */
     double rho[OR_MAX_LEVELS];    /* Gershgorin estimate used for P[l] */
     /* coarsest level: dense factor (row-major), Cholesky L or LU with pivots */
@@ -142,6 +153,7 @@ static double csr_diag(const ocsr *a, int i) {
 
 /* y = A x, each row summed in storage order starting from +0.0. */
 void or_spmv(int nrows, const int *rp, const int *ci, const double *v, const double *x, double *y) {
+    OR_PAR
     for (int i = 0; i < nrows; ++i) {
         double s = 0.0;
         for (int k = rp[i]; k < rp[i + 1]; ++k) s = s + v[k] * x[ci[k]];
@@ -895,7 +907,7 @@ or_hier *or_setup(const or_config *cfg_in, int n, long long nnz, const int *rp, 
         int nc = 0;
         if (!st) st = aggregate(A, &S, root, h->agg[l], &nc);
         free(root);
-        csr_free(&S);
+        h->S[l] = S;  /* kept for the tests' export (or_hier_get_strength) */
         if (st) { *status = st; or_hier_free(h); return NULL; }
         if (nc >= A->nrows) { free(h->agg[l]); h->agg[l] = NULL; break; } /* stalled */
         if ((st = prolongator(A, h->agg[l], nc, &h->P[l], &h->rho[l]))) {
@@ -1064,7 +1076,7 @@ or_hier *or_transposed(const or_hier *f, int *status) {
 void or_hier_free(or_hier *h) {
     if (!h) return;
     for (int l = 0; l < OR_MAX_LEVELS; ++l) {
-        csr_free(&h->A[l]); csr_free(&h->P[l]); csr_free(&h->R[l]);
+        csr_free(&h->A[l]); csr_free(&h->P[l]); csr_free(&h->R[l]); csr_free(&h->S[l]);
         free(h->agg[l]); free(h->dinv[l]);
     }
     free(h->dense); free(h->piv);
@@ -1091,6 +1103,14 @@ void or_hier_get(const or_hier *h, int l, int which, int *rp, int *ci, double *v
 void or_hier_get_agg(const or_hier *h, int l, int *agg) {
     memcpy(agg, h->agg[l], (size_t)h->A[l].nrows * sizeof(int));
 }
+/* The strength graph level l's aggregation used (setup of a smoothed-
+ * aggregation hierarchy; -1 when the level kept none): its entry count, then
+ * its pattern into srp (n_l + 1) and sci. */
+long long or_hier_strength_nnz(const or_hier *h, int l) { return h->S[l].rp ? h->S[l].nnz : -1; }
+void or_hier_get_strength(const or_hier *h, int l, int *srp, int *sci) {
+    memcpy(srp, h->S[l].rp, ((size_t)h->S[l].nrows + 1) * sizeof(int));
+    memcpy(sci, h->S[l].ci, (size_t)h->S[l].nnz * sizeof(int));
+}
 
 /* ------------------------------------------------------------------------ */
 /* V(1,1) cycle                                                             */
@@ -1111,14 +1131,18 @@ static void vcycle(const or_hier *h, int l, const double *b, double *x) {
     double *r = (double *)malloc((size_t)n * sizeof(double));
     double *bc = (double *)malloc((size_t)nc * sizeof(double));
     double *xc = (double *)malloc((size_t)nc * sizeof(double));
+    OR_PAR
     for (int i = 0; i < n; ++i) x[i] = w[i] * b[i];
     spmv(A, x, r);
+    OR_PAR
     for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];
     spmv(R, r, bc);
     vcycle(h, l + 1, bc, xc);
     spmv(P, xc, r);
+    OR_PAR
     for (int i = 0; i < n; ++i) x[i] = x[i] + r[i];
     spmv(A, x, r);
+    OR_PAR
     for (int i = 0; i < n; ++i) x[i] = x[i] + w[i] * (b[i] - r[i]);
     free(r); free(bc); free(xc);
 }
@@ -1129,11 +1153,33 @@ void or_vcycle(const or_hier *h, const double *b, double *x) { vcycle(h, 0, b, x
 /* Krylov solvers                                                           */
 /* ------------------------------------------------------------------------ */
 
+#ifdef _OPENMP
+/* Threaded build (timing only): fixed chunks of OR_CHUNK entries, each summed
+ * in order, then the chunk sums in order -- the same bits for any thread
+ * count, though not the serial build's bits. */
+#define OR_CHUNK 16384
+static double dot(int n, const double *a, const double *b) {
+    int nch = (n + OR_CHUNK - 1) / OR_CHUNK;
+    double *part = (double *)malloc((size_t)(nch > 0 ? nch : 1) * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < nch; ++c) {
+        int i1 = (c + 1) * OR_CHUNK < n ? (c + 1) * OR_CHUNK : n;
+        double s = 0.0;
+        for (int i = c * OR_CHUNK; i < i1; ++i) s = s + a[i] * b[i];
+        part[c] = s;
+    }
+    double s = 0.0;
+    for (int c = 0; c < nch; ++c) s = s + part[c];
+    free(part);
+    return s;
+}
+#else
 static double dot(int n, const double *a, const double *b) {
     double s = 0.0;
     for (int i = 0; i < n; ++i) s = s + a[i] * b[i];
     return s;
 }
+#endif
 
 static void precond(const or_hier *h, int use, const double *r, double *z) {
     if (use) vcycle(h, 0, r, z);
@@ -1143,6 +1189,7 @@ static void precond(const or_hier *h, int use, const double *r, double *z) {
 static double true_residual(const or_hier *h, const double *b, const double *x, double *r) {
     int n = h->A[0].nrows;
     spmv(&h->A[0], x, r);
+    OR_PAR
     for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];
     return sqrt(dot(n, r, r));
 }
@@ -1177,6 +1224,7 @@ static int pcg(const or_hier *h, int use_prec, const double *b, double *x, or_in
             if (!isfinite(pq) || !isfinite(rz)) { status = OR_NAN; break; }
             if (pq <= 0.0) { status = OR_BREAKDOWN; break; }
             double alpha = rz / pq;
+            OR_PAR
             for (int i = 0; i < n; ++i) { x[i] = x[i] + alpha * p[i]; r[i] = r[i] - alpha * q[i]; }
             rn = sqrt(dot(n, r, r));
             if (!isfinite(rn)) { status = OR_NAN; break; }
@@ -1185,6 +1233,7 @@ static int pcg(const or_hier *h, int use_prec, const double *b, double *x, or_in
             double rz_new = dot(n, r, z);
             double beta = rz_new / rz;
             rz = rz_new;
+            OR_PAR
             for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
         }
         if (status) break;
@@ -1229,10 +1278,11 @@ static int bicgstab(const or_hier *h, int use_prec, const double *b, double *x, 
         int conv = 0, breakdown = 0;
         while (iters < h->cfg.max_iter) {
             double rho = dot(n, rh, r);
-            iters++;
             if (!isfinite(rho)) { status = OR_NAN; break; }
             if (rho == 0.0) { breakdown = 1; break; }
+            iters++;  /* an iteration counts once it goes on to its products with A */
             double beta = (rho / rho_old) * (alpha / omega);
+            OR_PAR
             for (int i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
             precond(h, use_prec, p, ph);
             spmv(&h->A[0], ph, v);
@@ -1240,9 +1290,11 @@ static int bicgstab(const or_hier *h, int use_prec, const double *b, double *x, 
             if (!isfinite(rv)) { status = OR_NAN; break; }
             if (rv == 0.0) { breakdown = 1; break; }
             alpha = rho / rv;
+            OR_PAR
             for (int i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
             double sn = sqrt(dot(n, s, s));
             if (sn <= h->cfg.rtol * bn) {
+                OR_PAR
                 for (int i = 0; i < n; ++i) x[i] = x[i] + alpha * ph[i];
                 memcpy(r, s, sz);
                 rn = sn; conv = 1; break;
@@ -1253,6 +1305,7 @@ static int bicgstab(const or_hier *h, int use_prec, const double *b, double *x, 
             if (!isfinite(tt) || !isfinite(ts)) { status = OR_NAN; break; }
             if (tt == 0.0) { breakdown = 1; break; }
             omega = ts / tt;
+            OR_PAR
             for (int i = 0; i < n; ++i) {
                 x[i] = x[i] + alpha * ph[i] + omega * sh[i];
                 r[i] = s[i] - omega * t[i];
@@ -1329,6 +1382,7 @@ int or_adjoint(or_hier *h, const double *x, const double *g, double *lambda, dou
     }
     int st = or_solve(hs, g, lambda, info);
     const ocsr *A = &h->A[0];
+    OR_PAR
     for (int i = 0; i < A->nrows; ++i)
         for (int k = A->rp[i]; k < A->rp[i + 1]; ++k) dA[k] = -(lambda[i] * x[A->ci[k]]);
     return st;

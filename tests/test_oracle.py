@@ -242,6 +242,107 @@ def test_aggregates_partition_and_connected(maker):
         assert set(members.tolist()) <= ball[R[J]]  # radius 2 around its root
 
 
+def _strength_by_definition(A_sp, theta):
+    """S by its definition, written with scipy: j is strong for i (i != j)
+    when a_ij^2 >= theta^2 |a_ii a_jj|, and S is that relation united with
+    its transpose.  Returns a set of (i, j)."""
+    Acoo = A_sp.tocoo()
+    d = A_sp.diagonal()
+    off = Acoo.row != Acoo.col
+    r, c, v = Acoo.row[off], Acoo.col[off], Acoo.data[off]
+    strong = v * v >= (theta * theta) * np.abs(d[r] * d[c])
+    pairs = set(zip(r[strong].tolist(), c[strong].tolist()))
+    return pairs | {(j, i) for (i, j) in pairs}
+
+
+def _pairs(srp, sci):
+    rows = np.repeat(np.arange(srp.shape[0] - 1), np.diff(srp))
+    return set(zip(rows.tolist(), sci.tolist()))
+
+
+def test_strength_threshold_halves_per_level():
+    """Every level's strength graph is the definition evaluated on that
+    level's operator with theta_l = 0.08 * 2^-l (reading: the threshold halves
+    per level), and the level's aggregates are the MIS-2 aggregation of that
+    graph.  On a 3D GRF hierarchy a constant threshold gives other graphs on
+    the coarse levels, so dropping or doubling the halving fails here."""
+    A = M.diffusion3d_grf(N=20).A
+    h = O.Hierarchy(A, {"coarse_max": 8})
+    assert h.nlevels >= 4
+    differs = 0
+    for l in range(min(4, h.nlevels - 1)):
+        lv = h.level(l)
+        Al = lvl_sp(lv.A, lv.A.n)
+        srp, sci = h.strength(l)
+        got = _pairs(srp, sci)
+        assert got == _strength_by_definition(Al, 0.08 * 2.0 ** -l), f"level {l}"
+        if l > 0:
+            differs += got != _strength_by_definition(Al, 0.08)
+            differs += got != _strength_by_definition(Al, 0.08 * 2.0 ** -(l + 1))
+        root, _ = O.mis2(srp, sci)
+        agg, nc = O.aggregate(lv.A, srp, sci, root.astype(np.int32))
+        assert np.array_equal(agg, lv.agg) and nc == h.level(l + 1).A.n, f"level {l}"
+    assert differs >= 2  # the case tells the per-level threshold from its neighbours
+
+
+def _check_phase3(A, srp, sci, root, agg):
+    """Aggregation phases 2-3 by brute force: roots are numbered by index; a
+    non-root adjacent to a root joins it (the root is unique); every other
+    node joins the aggregate of its strong neighbour assigned in phase 2 with
+    the largest |a_ij| (0 when (i, j) is not stored), smallest j on ties.
+    Returns how many phase-3 nodes that rule decides differently from
+    'the first assigned neighbour'."""
+    n = A.n
+    R = np.flatnonzero(root)
+    assert np.array_equal(agg[R], np.arange(R.size))
+    absA = {}
+    for i in range(n):
+        for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            absA[(i, int(A.col_idx[k]))] = abs(A.values[k])
+    snap = np.full(n, -1)
+    snap[R] = np.arange(R.size)
+    for i in range(n):
+        if root[i]:
+            continue
+        nb = [int(j) for j in sci[srp[i]:srp[i + 1]] if root[j]]
+        assert len(nb) <= 1  # independence: at most one adjacent root
+        if nb:
+            snap[i] = snap[nb[0]]
+            assert agg[i] == snap[i]
+    telling = 0
+    for i in range(n):
+        if snap[i] >= 0:
+            continue
+        cand = [int(j) for j in sci[srp[i]:srp[i + 1]] if snap[j] >= 0]
+        assert cand, "maximality leaves every node a phase-2 neighbour"
+        best = min(cand, key=lambda j: (-absA.get((i, j), 0.0), j))
+        assert agg[i] == snap[best], (i, cand, best)
+        telling += snap[cand[0]] != snap[best]
+    return telling
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: M.diffusion_fv(np.exp(np.random.default_rng(17).normal(size=(30, 30)))),
+    lambda: M.diffusion_fv(np.exp(np.random.default_rng(18).normal(size=(9, 9, 9)))),
+])
+def test_aggregation_phase3_joins_largest_coupling(maker):
+    A = maker()
+    srp, sci = O.strength(A, 0.08)
+    root, _ = O.mis2(srp, sci)
+    agg, _ = O.aggregate(A, srp, sci, root.astype(np.int32))
+    assert _check_phase3(A, srp, sci, root, agg) > 0
+
+
+def test_aggregation_phase3_on_a_coarse_level():
+    """The same brute-force rule on the level-1 operator of a 3D GRF
+    hierarchy (distinct Galerkin couplings), with the level's own graph."""
+    h = O.Hierarchy(M.diffusion3d_grf(N=20).A, {"coarse_max": 8})
+    lv = h.level(1)
+    srp, sci = h.strength(1)
+    root, _ = O.mis2(srp, sci)
+    assert _check_phase3(lv.A, srp, sci, root, lv.agg) > 0
+
+
 # --------------------------------------------------------------------------
 # Prolongator, Galerkin, hierarchy
 # --------------------------------------------------------------------------
@@ -421,10 +522,39 @@ def test_paper_example1_iteration_band():
     b = M.rhs_ones(A.n)
     _, info = O.solve(A, b, {"solver": O.BICGSTAB, "rtol": g["tolerance"]})
     assert info.status == O.OK and info.iters <= g["band_amg_max"]
+    _, ic = O.solve(A, b, {"solver": O.BICGSTAB, "rtol": g["tolerance"], "amg_type": 1})
+    assert ic.status == O.OK and ic.iters <= g["band_amg_max_classical"]
     _, info0 = O.solve(A, b, {"solver": O.BICGSTAB_NOPREC, "rtol": g["tolerance"]})
     lo, hi = g["band_unpreconditioned"]
     assert lo <= info0.iters <= hi
     assert info.iters < info0.iters
+
+
+def test_bicgstab_breakdown_restarts_once_then_converges():
+    """rho = r^.r vanishes at iteration 2 of this system (every quantity is a
+    dyadic fraction, so the zero is exact in floating point): alpha = 1/4,
+    omega = 1/2, r_1 = (-1/8, -1/8, 1/4) with r^ = b = (1, 1, 1).  The method
+    restarts once from x_1 with r^ = r_1 and then converges to A^-1 b; the
+    iteration that broke down before its products is not counted."""
+    D = np.array([[3.0, 0.0, 3.0], [0.0, 4.0, -1.0], [1.0, 0.0, 2.0]])
+    A = M.CSR(*_dense_to_csr(D))
+    b = np.ones(3)
+    x, info = O.solve(A, b, {"solver": O.BICGSTAB_NOPREC, "rtol": 1e-12})
+    # without the restart the solve would end in BREAKDOWN at iteration 2
+    assert info.status == O.OK, info
+    assert np.allclose(x, np.linalg.solve(D, b), rtol=0, atol=1e-14)
+    assert info.iters >= 2  # one iteration before the breakdown, at least one after the restart
+
+
+def test_bicgstab_second_breakdown_returns_breakdown():
+    """r^.A b = 0 for b = (1, 1): alpha's denominator vanishes at the first
+    iteration, and again after the one restart (x is still 0, so r^ = r = b);
+    the second breakdown ends the solve with BREAKDOWN, x untouched."""
+    D = np.array([[1.0, -2.0], [0.0, 1.0]])
+    A = M.CSR(*_dense_to_csr(D))
+    x, info = O.solve(A, np.ones(2), {"solver": O.BICGSTAB_NOPREC})
+    assert info.status == O.BREAKDOWN and info.iters == 2
+    assert not x.any()
 
 
 # --------------------------------------------------------------------------
@@ -779,3 +909,20 @@ def test_classical_resetup_keeps_splitting_and_is_galerkin():
     x, info = hr.solve(b)
     assert info.status == 0
     assert np.linalg.norm(to_sp(Anew) @ x - b) <= 1e-8 * np.linalg.norm(b) * 1.0001
+
+
+def test_threaded_build_matches_serial():
+    """The threaded build (timing only: the solve phase's row loops on every
+    host core, dot products in fixed chunks) solves like the serial build, to
+    rounding."""
+    w = M.diffusion3d_grf(N=24)
+    g = np.random.default_rng(2).uniform(-1, 1, w.A.n)
+    h1, h2 = O.Hierarchy(w.A), O.Hierarchy(w.A, threads=True)
+    x1, i1 = h1.solve(w.b)
+    x2, i2 = h2.solve(w.b)
+    assert i1.status == i2.status == O.OK and i1.iters == i2.iters
+    assert np.linalg.norm(x1 - x2) <= 1e-12 * np.linalg.norm(x1)
+    l1, d1, _ = h1.adjoint(x1, g, w.A.nnz)
+    l2, d2, _ = h2.adjoint(x2, g, w.A.nnz)
+    assert np.linalg.norm(l1 - l2) <= 1e-12 * np.linalg.norm(l1)
+    assert O.threads_used() >= 1
