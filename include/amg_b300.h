@@ -297,25 +297,55 @@ int amg_widen_f32(const float *in, double *out, long long n, void *cuda_stream);
  * Computes the same iteration as amg_solve with AMG_SOLVER_CG (x0 = 0; stop at
  * ||b - A x||_2 <= rtol ||b||_2, at most 3 restarts from x while the true
  * residual is above it).  n rows, nnz stored entries; row_ptr/col_idx/values,
- * b and x must be DEVICE memory (host arrays return AMG_ERR_ARG, since
- * staging them would need an allocation); the CSR must satisfy the
+ * b and x must be DEVICE memory of the current device (host arrays, or
+ * memory of another GPU, return AMG_ERR_ARG before any GPU work: staging
+ * them would need an allocation); cuda_stream, when not NULL, must belong to
+ * the current device too (else AMG_ERR_ARG).  The CSR must satisfy the
  * conventions above and is not validated.  info may be NULL (its hierarchy
  * fields are left zero).
  *
  * Work space: the vectors r, p, q, the per-block partial sums and the Krylov
- * scalars live in one fixed __device__ array of about 6.3 MB that every GPU
- * which loads the library keeps until the process exits.  n above
- * AMG_NOALLOC_MAX_N returns AMG_ERR_UNSUPPORTED before any GPU work.  Every
- * call on a device shares that array and it keeps the last call's contents
- * (the call clears what must start at zero), so calls whose GPU work
- * overlaps -- on two streams, or from two host threads -- race and corrupt
- * each other: serialise them.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.
+ * scalars live in one fixed __device__ array of about 6.3 MB.  n above
+ * AMG_NOALLOC_MAX_N returns AMG_ERR_UNSUPPORTED before any GPU work.  The
+ * array belongs to the library's module: with CUDA's lazy module loading
+ * (the default) its device memory is committed when the module first loads
+ * on a device, which happens inside the first call on that device (its
+ * cudaGetSymbolAddress), and is then held until the process exits.  That
+ * first call is therefore the one that may take device memory (and may fail
+ * with AMG_ERR_CUDA when none is left): make one warm-up call on each device
+ * before entering a region that must not allocate, and make it before any
+ * stream capture; later calls take no device memory.  Every call on a device
+ * shares that array and it keeps the last call's contents (the call clears
+ * what must start at zero), so calls whose GPU work overlaps -- on two
+ * streams, or from two host threads -- race and corrupt each other:
+ * serialise them.  The call reads the Krylov scalars back to the host
+ * between iterations, so it waits for all earlier work on cuda_stream and
+ * returns only after its own GPU work has finished.
  * Returns AMG_OK, AMG_MAXIT, AMG_BREAKDOWN, AMG_NAN or a hard error. */
 int amg_cg_solve_noalloc(int n, long long nnz, const int *row_ptr, const int *col_idx, const double *values,
                          const double *b, double *x, double rtol, int max_iter, void *cuda_stream,
                          amg_info *info);
+
+/* Test hook for the bounded device waits.  The paper has no counterpart: it
+ * exists so that tests can run a wait into its limit without faulting or
+ * hanging the GPU.  Arms a one-shot control in h's device state that the next
+ * solve-phase launch doing work consumes:
+ *   AMG_TEST_WITHHOLD_COPY: CTA 0 of the next bulk-copy streaming pass
+ *     expects 16 bytes that no copy delivers, so its first pipeline stage
+ *     never completes; its waits give up after 2^12 polls;
+ *   AMG_TEST_WITHHOLD_BARRIER: the last CTA of the next cooperative coarse
+ *     launch (fuse_coarse = 2) skips its grid-barrier arrivals; the others'
+ *     first waits give up after 2^20 SM clocks;
+ *   0: disarms.
+ * A wait that gives up sets the kernel's error flag and returns; the
+ * amg_solve / amg_adjoint call that ran it returns AMG_ERR_CUDA (amg_last_error
+ * names the wait) and its results are not valid.  The control disarms itself
+ * when consumed; the next call on the handle clears the error flag and the
+ * barrier word and runs normally.  Synchronous on the handle's stream.
+ * Returns AMG_OK or AMG_ERR_ARG (NULL handle, unknown kind). */
+#define AMG_TEST_WITHHOLD_COPY 1
+#define AMG_TEST_WITHHOLD_BARRIER 2
+int amg_test_arm_wait_timeout(amg_handle h, int kind);
 
 /* Releases every resource of the handle.  amg_free(NULL) is a no-op. */
 int amg_free(amg_handle h);

@@ -9,8 +9,10 @@
 // whole hierarchy, so those callers cannot use a handle.  This entry point
 // needs nothing but the caller's arrays: its work vectors (r, p, q), the
 // per-block partial sums and the Krylov scalars live in one file-scope
-// __device__ array of fixed size, which every GPU that loads the library
-// holds until the process exits.
+// __device__ array of fixed size.  Under CUDA's lazy module loading the
+// array's device memory is committed when this file's module first loads on a
+// device -- inside the first call there -- and held until the process exits,
+// so a caller makes one warm-up call before a region that must not allocate.
 //
 // The iteration is the same unpreconditioned CG as amg_solve with
 // AMG_SOLVER_CG: x0 = 0, stop when ||r||_2 <= rtol ||b||_2 on the recursive
@@ -244,13 +246,16 @@ __global__ void na_restart(NaView s) {
     s.sc->first = 1;
 }
 
-bool device_accessible(const void *p) {
+// True when p is device (or managed) memory of device `dev`, the device the
+// kernels run on: memory of another GPU would be dereferenced from this one.
+bool device_accessible(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 int read_scalars(const NaScalars *dev_sc, NaScalars *host, cudaStream_t st) {
@@ -276,19 +281,31 @@ extern "C" int amg_cg_solve_noalloc(int n, long long nnz, const int *row_ptr, co
         amg::set_last_error("amg_cg_solve_noalloc: nnz = %lld exceeds the int32 index range", nnz);
         return AMG_ERR_UNSUPPORTED;
     }
+    int dev = 0;
+    AMG_CUDA_TRY(cudaGetDevice(&dev));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (st) {
+        // a stream of another device would run the kernels there
+        int sdev = -1;
+        AMG_CUDA_TRY(cudaStreamGetDevice(st, &sdev));
+        if (sdev != dev) {
+            amg::set_last_error("amg_cg_solve_noalloc: the stream belongs to device %d, the current device is %d", sdev,
+                                dev);
+            return AMG_ERR_ARG;
+        }
+    }
     const void *ptrs[] = {row_ptr, col_idx, values, b, x};
     for (const void *p : ptrs)
-        if (!device_accessible(p)) {
-            amg::set_last_error("amg_cg_solve_noalloc: every array must be device memory (no staging without allocation)");
+        if (!device_accessible(p, dev)) {
+            amg::set_last_error("amg_cg_solve_noalloc: every array must be device memory of the current device %d "
+                                "(no staging without allocation)", dev);
             return AMG_ERR_ARG;
         }
     double *base = nullptr;
     AMG_TRY(scratch_address(&base));
     const NaView s = carve(base);
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    int sms = 148, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int sms = 148;
+    AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = std::max(1, std::min((n + NA_BLOCK - 1) / NA_BLOCK, std::min(NA_PARTS, sms * 4)));
     const int grid_spmv = std::max(1, std::min((n + NA_BLOCK / 8 - 1) / (NA_BLOCK / 8), std::min(NA_PARTS, sms * 4)));
 
@@ -308,6 +325,7 @@ extern "C" int amg_cg_solve_noalloc(int n, long long nnz, const int *row_ptr, co
     }
     const long long cap = (long long)max_iter * (NA_RESTARTS + 2) + 16;
     long long launched = 0;
+    bool have_true = false;  // h.tr holds ||b - A x||^2 of the final x
     while (status == AMG_OK) {
         for (;;) {
             for (int k = 0; k < 4; ++k) {
@@ -330,7 +348,10 @@ extern "C" int amg_cg_solve_noalloc(int n, long long nnz, const int *row_ptr, co
         na_spmv<true><<<grid_spmv, NA_BLOCK, 0, st>>>(n, row_ptr, col_idx, values, x, b, s);
         AMG_LAUNCH_CHECK();
         AMG_TRY(read_scalars(s.sc, &h, st));
-        if (h.tr <= h.tol2) break;
+        if (h.tr <= h.tol2) {
+            have_true = true;  // x is final: its true residual is already known
+            break;
+        }
         if (restarts >= NA_RESTARTS || h.iters >= max_iter) {
             status = AMG_MAXIT;
             break;
@@ -341,9 +362,11 @@ extern "C" int amg_cg_solve_noalloc(int n, long long nnz, const int *row_ptr, co
     }
     const double rec = h.rr;
     const int iters = h.iters;
-    na_spmv<true><<<grid_spmv, NA_BLOCK, 0, st>>>(n, row_ptr, col_idx, values, x, b, s);
-    AMG_LAUNCH_CHECK();
-    AMG_TRY(read_scalars(s.sc, &h, st));
+    if (!have_true) {
+        na_spmv<true><<<grid_spmv, NA_BLOCK, 0, st>>>(n, row_ptr, col_idx, values, x, b, s);
+        AMG_LAUNCH_CHECK();
+        AMG_TRY(read_scalars(s.sc, &h, st));
+    }
     const double rel_true = sqrt(h.tr / bn2);
     if (status == AMG_OK && !(rel_true <= rtol)) status = AMG_MAXIT;
     if (info) {
