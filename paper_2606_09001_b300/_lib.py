@@ -17,6 +17,7 @@ AMG_MAX_LEVELS = 32
 AMG_DENSE_MAX = 256
 AMG_NOALLOC_MAX_N = 1 << 18
 AMG_BATCH_MAX_RHS = 8
+AMG_TEST_WITHHOLD_COPY, AMG_TEST_WITHHOLD_BARRIER = 1, 2
 
 SOLVERS = {"PCG": 0, "BICGSTAB": 1, "CG": 2, "BICGSTAB_NOPREC": 3}
 SMOOTHERS = {"JACOBI": 0, "L1_JACOBI": 1}
@@ -27,7 +28,7 @@ AMG_TYPES = {"AGGREGATION": 0, "CLASSICAL": 1}
 # Every symbol the header declares.
 EXPORTS = ("amg_config_default", "amg_setup", "amg_resetup", "amg_solve", "amg_adjoint", "amg_vcycle", "amg_get_info",
            "amg_get_level", "amg_get_aggregates", "amg_get_plan", "amg_profile", "amg_profile_summary", "amg_profile_record",
-           "amg_setup_batched", "amg_solve_batched", "amg_batch_level", "amg_cg_solve_noalloc", "amg_narrow_f64", "amg_widen_f32", "amg_free", "amg_status_string", "amg_last_error")
+           "amg_setup_batched", "amg_solve_batched", "amg_batch_level", "amg_cg_solve_noalloc", "amg_test_arm_wait_timeout", "amg_narrow_f64", "amg_widen_f32", "amg_free", "amg_status_string", "amg_last_error")
 
 
 class AmgConfig(C.Structure):
@@ -80,6 +81,7 @@ def load() -> C.CDLL:
         L.amg_solve_batched.argtypes = [vp, i, vp, vp, vp, vp, vp, C.POINTER(AmgInfo)]
         L.amg_batch_level.argtypes = [vp, i, C.POINTER(i), vp, vp, vp]
         L.amg_cg_solve_noalloc.argtypes = [i, ll, vp, vp, vp, vp, vp, C.c_double, i, vp, C.POINTER(AmgInfo)]
+        L.amg_test_arm_wait_timeout.argtypes = [vp, i]
         L.amg_free.argtypes = [vp]
         L.amg_status_string.argtypes = [i]
         L.amg_status_string.restype = C.c_char_p

@@ -1,6 +1,8 @@
 // amg_common.cuh -- internal types and helpers of libamgb300 (not installed).
 #pragma once
 
+#include <cstddef>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -118,9 +120,13 @@ struct DevScalars {
     int flexible;     // PCG uses the Polak-Ribiere beta (mixed-precision V-cycle)
     int max_iter;
     int first;        // PCG: the next beta starts a new recursion (beta = 0)
-    int copy_timeout; // a bulk-copy wait gave up (set by the streaming kernels)
-    int pad;
+    int copy_timeout; // a bounded wait gave up: 1 a bulk-copy wait, 2 a grid-barrier wait
+    int test_ctl;     // one-shot test control read with copy_timeout (amg_test_arm_wait_timeout); 0 normally
 };
+// The solve-phase kernels receive &copy_timeout and read the test control one
+// int further on.
+static_assert(offsetof(DevScalars, test_ctl) == offsetof(DevScalars, copy_timeout) + sizeof(int),
+              "test_ctl must follow copy_timeout");
 
 // ---------------------------------------------------------------------------
 // Hierarchy

@@ -549,6 +549,14 @@ int amg_batch_level(amg_handle h, int level, int *nsys_level, int *sys, int *row
     return AMG_OK;
 }
 
+int amg_test_arm_wait_timeout(amg_handle h, int kind) {
+    if (!h || kind < 0 || kind > AMG_TEST_WITHHOLD_BARRIER) {
+        set_last_error("amg_test_arm_wait_timeout: invalid handle or kind %d", kind);
+        return AMG_ERR_ARG;
+    }
+    return test_arm_wait_timeout(h->W, kind, h->s);
+}
+
 int amg_free(amg_handle h) {
     destroy(h);
     return AMG_OK;

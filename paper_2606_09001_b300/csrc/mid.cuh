@@ -81,25 +81,39 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 // again.  Each CTA waits for the top bit to differ from the one its own add
 // saw.  The add releases the CTA's writes (ordered before it by the CTA
 // barrier), the load that sees the flip acquires everyone's.  A wait gives up
-// after 2^31 SM clocks (about a second) and returns false.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks) {
+// after `limit` SM clocks (2^31, about a second, unless a test shortens it)
+// and returns false.  `skip` (tests only) neither adds nor waits.
+constexpr long long BARRIER_CLOCKS = 1LL << 31;
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, bool skip = false,
+                                             long long limit = BARRIER_CLOCKS) {
     __shared__ int s_ok;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !skip) {
         s_ok = 1;
         const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (nblocks - 1) : 1u;
         const unsigned old = atom_add_release(bar, inc);
         const long long t0 = clock64();
         while (((ld_acquire(bar) ^ old) & 0x80000000u) == 0) {
-            if (clock64() - t0 > (1LL << 31)) {
+            if (clock64() - t0 > limit) {
                 s_ok = 0;
                 break;
             }
         }
+    } else if (threadIdx.x == 0) {
+        s_ok = 1;
     }
     __syncthreads();
     return s_ok != 0;
 }
+
+// The test control read at err[1] (see amg_test_arm_wait_timeout): with
+// TEST_WITHHOLD_BARRIER the last CTA of the next launch that does work skips
+// every grid-barrier arrival, so every other CTA's first wait runs out after
+// TEST_CLOCKS clocks; those CTAs set err[0] |= 2, disarm the control and
+// return, and the skipping CTA runs its phases unsynchronised to the end
+// (results discarded; no wait of its own).
+constexpr int TEST_WITHHOLD_BARRIER = 2;
+constexpr long long TEST_CLOCKS = 1LL << 20;
 
 // Row passes: VEC lanes per row, warps grid-stride over the rows.
 #define MID_ROWS(VEC, n)                                                              \
@@ -241,12 +255,24 @@ __device__ void p_dense(int m, int ld, const TMAT *__restrict__ M, const TV *b, 
 template <typename TM, typename TMAT>
 __global__ void __launch_bounds__(THREADS) k_mid(const __grid_constant__ MArgs<TM> a, unsigned *bar,
                                                  const int *done, int *err) {
-    if (*done) return;  // no kernel writes the flag while this one runs: every CTA returns or none
+    // no kernel writes these flags while this one runs (it is launched without
+    // programmatic overlap): every CTA returns or none.  After a barrier wait
+    // gave up the barrier word is inconsistent until the next call's control
+    // kernel clears it, so later launches of the same call do nothing.
+    if (*done || (*err & 2)) return;
     __shared__ __align__(16) double sb[DENSE_LD];
     const unsigned nb = gridDim.x;
+    // every CTA reads the test control before any CTA can disarm it (that
+    // happens only after a barrier wait has run out)
+    const bool test = __ldcg(err + 1) == TEST_WITHHOLD_BARRIER;
+    const bool skip = test && blockIdx.x == nb - 1 && nb > 1;
+    const long long lim = test ? TEST_CLOCKS : BARRIER_CLOCKS;
     auto sync = [&]() -> bool {
-        if (grid_barrier(bar, nb)) return true;
-        if (threadIdx.x == 0) atomicOr(err, 2);
+        if (grid_barrier(bar, nb, skip, lim)) return true;
+        if (threadIdx.x == 0) {
+            atomicOr(err, 2);
+            atomicExch(err + 1, 0);
+        }
         return false;
     };
     MID_VEC(a.r0vec, (p_spmv<V, TM>(a.r0n, a.r0rp, a.r0ci, a.r0v, a.r0x, a.L[0].b)));

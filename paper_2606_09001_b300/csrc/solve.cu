@@ -1597,7 +1597,7 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &
     AMG_TRY(scr.alloc(&part, (size_t)3 * cap));
     AMG_TRY(scr.alloc(&cnt, 4));
     AMG_TRY(scr.alloc(&tsc, 1));
-    AMG_TRY(scr.alloc(&err, 1));
+    AMG_TRY(scr.alloc(&err, 2));  // the error flag and the (unarmed) test control after it
     k_fill<TG><<<256, 256, 0, s>>>(ncl, (TG)1, x);
     k_fill<TM><<<256, 256, 0, s>>>(nr, (TM)0.5, w);
     k_fill<TM><<<256, 256, 0, s>>>(nr, (TM)1, bm);
@@ -1605,7 +1605,7 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &
     k_fill<double><<<256, 256, 0, s>>>(nr, 0.5, ro);
     AMG_LAUNCH_CHECK();
     AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned), s));
-    AMG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    AMG_CUDA_TRY(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
     constexpr bool same = std::is_same<TM, TG>::value;
     const TM *xm = reinterpret_cast<const TM *>(x);  // the gathered vector as TM (kinds with TG = TM)
     TM *ym = reinterpret_cast<TM *>(y);
@@ -2660,6 +2660,15 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
                                                   : "a bulk-copy wait in a streaming kernel timed out");
         return AMG_ERR_CUDA;
     }
+    return AMG_OK;
+}
+
+int test_arm_wait_timeout(Workspace &W, int kind, cudaStream_t s) {
+    static_assert(stream::TEST_WITHHOLD_COPY == AMG_TEST_WITHHOLD_COPY &&
+                      mid::TEST_WITHHOLD_BARRIER == AMG_TEST_WITHHOLD_BARRIER,
+                  "test control values");
+    AMG_CUDA_TRY(cudaMemcpyAsync(&W.scal->test_ctl, &kind, sizeof(int), cudaMemcpyHostToDevice, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
     return AMG_OK;
 }
 

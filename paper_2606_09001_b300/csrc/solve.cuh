@@ -76,6 +76,9 @@ struct SolveResult {
 // Solves A x = W.b (A = h's finest operator) into W.x with h's configuration.
 int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res);
 
+// Arms the one-shot test control of the bounded waits (AMG_TEST_WITHHOLD_*; 0 disarms).
+int test_arm_wait_timeout(Workspace &W, int kind, cudaStream_t s);
+
 // z = M^-1 r with one V-cycle of h (r, z: device vectors of length n).
 int vcycle_apply(Hierarchy *h, Workspace &W, const double *r, double *z, cudaStream_t s);
 

@@ -89,11 +89,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: gives up after 2^22 polls and reports it.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 22); ++it)
+// Bounded wait: gives up after `limit` polls (2^22 unless a test shortens it)
+// and reports it.
+constexpr uint32_t WAIT_POLLS = 1u << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, uint32_t limit = WAIT_POLLS) {
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try_wait(b, parity)) return true;
     return false;
+}
+
+// The test control the kernels read at err[1] (armed by the host, see
+// amg_test_arm_wait_timeout).  With TEST_WITHHOLD_COPY, CTA 0 of the next
+// streaming launch that does work adds 16 bytes that no copy delivers to its
+// first stage's expected count, so the stage never completes: its consumers'
+// and producer's waits run out after TEST_POLLS polls, set err[0] and leave
+// the loop; by then every copy the CTA issued has landed (the real bytes of
+// both stages arrive microseconds after issue).  CTA 0 disarms the control.
+constexpr int TEST_WITHHOLD_COPY = 1;
+constexpr uint32_t TEST_POLLS = 1u << 12;
+
+// Called by every thread of the CTA after the dependency wait, with c = err[1]
+// as CTA 0 loaded it (0 elsewhere): true in every thread of CTA 0 when the
+// control is armed; thread 0 disarms it.
+__device__ __forceinline__ bool test_withhold(int c, int *err) {
+    if (blockIdx.x != 0) return false;
+    const bool w = __syncthreads_or(c == TEST_WITHHOLD_COPY) != 0;
+    if (w && threadIdx.x == 0) atomicExch(err + 1, 0);
+    return w;
 }
 
 // The row pass.  Op provides: bool done(); TM gather(int j); Pre load(int i)
@@ -154,6 +176,7 @@ __global__ void __launch_bounds__(NT, 2) k_stream(int n, int rt, int cap, int nt
             issue(blockIdx.x + npre * gridDim.x, npre, npre, true);
     pdl_wait();
     pdl_trigger();
+    const int ctl = blockIdx.x == 0 ? __ldcg(err + 1) : 0;  // in flight with the done flag's load
     if (op.done()) {
         // the prefetched copies land before the CTA leaves
         if (tid == 0)
@@ -163,6 +186,8 @@ __global__ void __launch_bounds__(NT, 2) k_stream(int n, int rt, int cap, int nt
             }
         return;
     }
+    const bool wh = test_withhold(ctl, err);
+    const uint32_t lim = wh ? TEST_POLLS : WAIT_POLLS;
     double acc[2] = {0.0, 0.0};
     bool ok = true;
     if (warp == 0) {
@@ -172,10 +197,11 @@ __global__ void __launch_bounds__(NT, 2) k_stream(int n, int rt, int cap, int nt
                 if (t >= ntiles) break;
                 const int st = j % STAGES;
                 if (j < npre) {
+                    if (j == 0 && wh) mbar_expect_tx_only(&full[0], 16);  // bytes no copy delivers
                     mbar_arrive(&full[st]);  // copies already issued
                     continue;
                 }
-                if (!mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1))) {
+                if (!mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1), lim)) {
                     ok = false;
                     break;
                 }
@@ -198,7 +224,7 @@ __global__ void __launch_bounds__(NT, 2) k_stream(int n, int rt, int cap, int nt
             // wait, so their latency overlaps the bulk copy's
             typename Op::Pre pre0{};
             if (rsub < rows && vl == 0) pre0 = op.load(r0 + rsub);
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / STAGES) & 1)))) {  // warp-uniform
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / STAGES) & 1), lim))) {  // warp-uniform
                 ok = false;
                 break;
             }
@@ -396,6 +422,7 @@ __global__ void __launch_bounds__(NT, 2) k_stream_win(int n, int rt, int cap, in
             issue_op(blockIdx.x + npre * gridDim.x, npre, npre);
     pdl_wait();
     pdl_trigger();
+    const int ctl = blockIdx.x == 0 ? __ldcg(err + 1) : 0;  // in flight with the done flag's load
     if (op.done()) {
         // the prefetched copies land before the CTA leaves
         if (tid == 0)
@@ -405,6 +432,8 @@ __global__ void __launch_bounds__(NT, 2) k_stream_win(int n, int rt, int cap, in
             }
         return;
     }
+    const bool wh = test_withhold(ctl, err);
+    const uint32_t lim = wh ? TEST_POLLS : WAIT_POLLS;
     double acc[2] = {0.0, 0.0};
     bool ok = true;
     if (warp == 0) {
@@ -414,13 +443,14 @@ __global__ void __launch_bounds__(NT, 2) k_stream_win(int n, int rt, int cap, in
                 if (t >= ntiles) break;
                 const int st = j % STAGES;
                 if (j >= npre) {
-                    if (!mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1))) {
+                    if (!mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1), lim)) {
                         ok = false;
                         break;
                     }
                     fence_proxy_async();
                     issue_op(t, j, st);
                 }
+                if (j == 0 && wh) mbar_expect_tx_only(&full[0], 16);  // bytes no copy delivers
                 issue_win(t, j, st);
             }
         }
@@ -437,7 +467,7 @@ __global__ void __launch_bounds__(NT, 2) k_stream_win(int n, int rt, int cap, in
             const int rows = min(rt, n - r0);
             typename Op::Pre pre0{};
             if (rsub < rows && vl == 0) pre0 = op.load_rest(r0 + rsub);
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / STAGES) & 1)))) {  // warp-uniform
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / STAGES) & 1), lim))) {  // warp-uniform
                 ok = false;
                 break;
             }
@@ -632,6 +662,7 @@ __global__ void __launch_bounds__(NT, 2) k_stream_ell(int n, int rt, int cap, in
             issue_op(blockIdx.x + npre * gridDim.x, npre, npre);
     pdl_wait();
     pdl_trigger();
+    const int ctl = blockIdx.x == 0 ? __ldcg(err + 1) : 0;  // in flight with the done flag's load
     if (op.done()) {
         // the prefetched copies land before the CTA leaves
         if (tid == 0)
@@ -641,6 +672,8 @@ __global__ void __launch_bounds__(NT, 2) k_stream_ell(int n, int rt, int cap, in
             }
         return;
     }
+    const bool wh = test_withhold(ctl, err);
+    const uint32_t lim = wh ? TEST_POLLS : WAIT_POLLS;
     double acc[2] = {0.0, 0.0};
     bool ok = true;
     if (warp == 0) {
@@ -650,13 +683,14 @@ __global__ void __launch_bounds__(NT, 2) k_stream_ell(int n, int rt, int cap, in
                 if (t >= ntiles) break;
                 const int st = j % STAGES;
                 if (j >= npre) {
-                    if (!mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1))) {
+                    if (!mbar_wait(&empty[st], (uint32_t)(((j / STAGES) - 1) & 1), lim)) {
                         ok = false;
                         break;
                     }
                     fence_proxy_async();
                     issue_op(t, j, st);
                 }
+                if (j == 0 && wh) mbar_expect_tx_only(&full[0], 16);  // bytes no copy delivers
                 issue_win(t, j, st);
             }
         }
@@ -679,7 +713,7 @@ __global__ void __launch_bounds__(NT, 2) k_stream_ell(int n, int rt, int cap, in
                 const int row = r0 + sl * 32 + lane;
                 if (!staged && row < n) pre = op.load_rest(row);
             }
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / STAGES) & 1)))) {  // warp-uniform
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / STAGES) & 1), lim))) {  // warp-uniform
                 ok = false;
                 break;
             }
