@@ -179,12 +179,13 @@ def dist_init():
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_step_time(w, solver: str, budget_s: float, max_steps: int):
+def oracle_step_time(w, solver: str, budget_s: float, max_steps: int, threads: bool = False):
     """Times the oracle's solve + adjoint on the workload (setup excluded);
-    runs as many whole steps as fit in budget_s (at least one)."""
+    runs as many whole steps as fit in budget_s (at least one).  threads: the
+    oracle's threaded build (its solve-phase loops on every host core)."""
     import oracle as O
     cfg = {"solver": {"PCG": 0, "BICGSTAB": 1, "CG": 2, "BICGSTAB_NOPREC": 3}[solver]}
-    h = O.Hierarchy(w.A, cfg)
+    h = O.Hierarchy(w.A, cfg, threads=threads)
     g = np.random.default_rng(7).uniform(-1, 1, w.A.n)
     times = []
     t_start = time.perf_counter()
@@ -199,20 +200,37 @@ def oracle_step_time(w, solver: str, budget_s: float, max_steps: int):
     return statistics.mean(times) * 1e3, len(times), info
 
 
-def oracle_time(workload: str, w, solver: str, budget_s: float, max_steps: int):
+def oracle_time(workload: str, w, solver: str, budget_s: float, max_steps: int, threads: bool = False):
     """oracle_step_time on the workload, or on its smaller sample scaled to the
     workload's rows; returns (ms, steps, info, what was timed)."""
     if workload not in ORACLE_SAMPLE:
-        ms, nsteps, info = oracle_step_time(w, solver, budget_s, max_steps)
+        ms, nsteps, info = oracle_step_time(w, solver, budget_s, max_steps, threads)
         return ms, nsteps, info, "the full workload"
     gen_s, what = ORACLE_SAMPLE[workload]
     ws = gen_s()
-    ms, nsteps, info = oracle_step_time(ws, solver, budget_s, max_steps)
+    ms, nsteps, info = oracle_step_time(ws, solver, budget_s, max_steps, threads)
     scale = w.A.n / ws.A.n
     return ms * scale, nsteps, info, f"{what}, time scaled x{scale:g} by rows"
 
 
-def oracle_batched_time(w, budget_s: float):
+def cpu_baseline(workload: str, w, solver: str, budget_s: float, max_steps: int):
+    """The oracle on the host: the threaded build on every core (the reported
+    value; a third of the budget) and the single-threaded parity build beside
+    it (the rest)."""
+    import oracle as O
+    cores = O.threads_used()
+    ms_t, n_t, info, where = oracle_time(workload, w, solver, budget_s / 3, max_steps, threads=True)
+    ms_1, n_1, _, _ = oracle_time(workload, w, solver, 2 * budget_s / 3, max_steps)
+    return {"value": ms_t, "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": f"{n_t} solve+adjoint step(s) of {where}, setup excluded, FP64, the oracle's solve phase "
+                      f"threaded with OpenMP over rows on {cores} host cores (deterministic fixed-chunk dot "
+                      f"products; {info.iters} iterations per solve)",
+            "nproc": os.cpu_count(),
+            "single_thread": {"value": ms_1, "unit": "ms", "cores": 1,
+                              "sample": f"{n_1} step(s) of the same, the serial parity build"}}
+
+
+def oracle_batched_time(w, budget_s: float, threads: bool = False):
     """Times the oracle solving the batch's (system, RHS) pairs one by one
     (per-system setup excluded), systems in order until budget_s is spent;
     returns the time scaled to the whole batch by rows, and the sample."""
@@ -222,7 +240,7 @@ def oracle_batched_time(w, budget_s: float):
     spent, rows, nsys, its = 0.0, 0, 0, []
     for k in range(len(sides)):
         A = M.poisson2d(int(sides[k]))
-        h = O.Hierarchy(A)
+        h = O.Hierarchy(A, threads=threads)
         t0 = time.perf_counter()
         for r in range(nrhs):
             _, info = h.solve(np.ascontiguousarray(w.b[off[k]:off[k + 1], r]))
@@ -234,9 +252,20 @@ def oracle_batched_time(w, budget_s: float):
         if spent > budget_s:
             break
     ms = spent * 1e3 * (w.A.n / rows)
+    how = f"threaded over rows on {O.threads_used()} host cores" if threads else "single-threaded"
     sample = (f"{nsys} of {len(sides)} systems x {nrhs} RHS solved one by one ({rows} of {w.A.n} rows, setup "
-              f"excluded), single-threaded FP64, {min(its)}-{max(its)} iterations; scaled to the batch by rows")
+              f"excluded), {how} FP64, {min(its)}-{max(its)} iterations; scaled to the batch by rows")
     return ms, sample
+
+
+def cpu_baseline_batched(w, budget_s: float):
+    import oracle as O
+    cores = O.threads_used()
+    ms_t, sample_t = oracle_batched_time(w, budget_s / 3, threads=True)
+    ms_1, sample_1 = oracle_batched_time(w, 2 * budget_s / 3)
+    return {"value": ms_t, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample_t,
+            "nproc": os.cpu_count(),
+            "single_thread": {"value": ms_1, "unit": "ms", "cores": 1, "sample": sample_1}}
 
 
 def run_reference(args):
@@ -244,33 +273,35 @@ def run_reference(args):
     if rank != 0:
         return
     gen, solver, desc = WORKLOADS[args.workload]
+    import oracle as O
+    cores = O.threads_used()
     if args.workload in BATCHED:
         w = gen()
-        ms, sample = oracle_batched_time(w, 60.0)
+        ms, sample = oracle_batched_time(w, 60.0, threads=True)
         out = {
             "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": {"workload": args.workload, "description": desc, "n": w.A.n, "nnz": w.A.nnz, "rtol": 1e-8,
                        "solver": solver},
-            "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }
         print(json.dumps(out), flush=True)
         return
     w = gen()
-    budget = max(30.0, 150.0)
+    budget = 150.0
     total = args.steps + args.warmup
-    ms, nsteps, info, where = oracle_time(args.workload, w, solver, budget, total)
-    sample = (f"{nsteps} of {total} solve+adjoint steps on {where} (setup excluded), "
-              f"single-threaded FP64 oracle, {info.iters} iterations per solve")
+    ms, nsteps, info, where = oracle_time(args.workload, w, solver, budget, total, threads=True)
+    sample = (f"{nsteps} of {total} solve+adjoint steps on {where} (setup excluded), FP64 oracle with its "
+              f"solve phase threaded over rows on {cores} host cores, {info.iters} iterations per solve")
     out = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
         "config": {"workload": args.workload, "description": desc, "n": w.A.n, "nnz": w.A.nnz, "rtol": 1e-8,
                    "solver": solver},
-        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -551,10 +582,7 @@ def run_ours(args):
     # CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ms_cpu, nsteps, info, where = oracle_time(args.workload, w, solver, args.cpu_budget, 4)
-        cpu = {"value": ms_cpu, "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": f"{nsteps} solve+adjoint step(s) of {where}, setup excluded, "
-                         f"single-threaded FP64 ({info.iters} iterations per solve)"}
+        cpu = cpu_baseline(args.workload, w, solver, args.cpu_budget, 4)
 
     info = solvers[primary].info()
     for s in solvers.values():
@@ -746,8 +774,7 @@ def run_batched(args, world, rank, dev, barrier):
                "d2h_bytes_per_step": 8 * n * nrhs + (4 + 8) * nsys * nrhs}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ms_cpu, sample = oracle_batched_time(w, args.cpu_budget)
-        cpu = {"value": ms_cpu, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = cpu_baseline_batched(w, args.cpu_budget)
     info = solvers[primary].info()
     for s in solvers.values():
         s.close()

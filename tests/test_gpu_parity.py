@@ -119,11 +119,14 @@ def test_solve_parity(name, cfg):
     assert info.status == 0 and io.status == 0
     assert info.rel_res_true <= 1e-8
     assert abs(info.iters - io.iters) <= 2, (info.iters, io.iters)
-    # same algorithm, same hierarchy: the iterates agree to rounding
+    # same algorithm, same hierarchy: the iterates agree to rounding, in norm
+    # and entry by entry
     assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
+    assert np.abs(x - xo).max() <= 1e-7 * np.abs(xo).max()
     # against a tight oracle solve (the reference solution)
     xt, _ = O.Hierarchy(A, dict(ocfg(cfg), rtol=1e-13)).solve(b)
-    assert np.linalg.norm(x - xt) <= 1e-6 * np.linalg.norm(xt)
+    assert np.linalg.norm(x - xt) <= 1e-7 * np.linalg.norm(xt)
+    assert np.abs(x - xt).max() <= max(2.0 * np.abs(xo - xt).max(), 1e-7 * np.abs(xt).max())
 
 
 @pytest.mark.parametrize("name", ["poisson2d_64", "grf3d_24", "convdiff_14", "grf3d_33", "poisson2d_181",
@@ -151,14 +154,15 @@ def test_vcycle_mixed_close_to_fp64(name):
 def test_mixed_precision_solve(name, cfg):
     A = SMALL_CASES[name]()
     b = np.random.default_rng(9).uniform(-1, 1, A.n)
-    _, io = O.Hierarchy(A, ocfg(cfg)).solve(b)
+    xo, io = O.Hierarchy(A, ocfg(cfg)).solve(b)
     xt, _ = O.Hierarchy(A, dict(ocfg(cfg), rtol=1e-13)).solve(b)
     s = gpu_solver(A, dict(cfg, precision="MIXED"))
     x, info = s.solve(dev(b))
     x = x.cpu().numpy()
     assert info.status == 0 and info.rel_res_true <= 1e-8
     assert abs(info.iters - io.iters) <= 2, (info.iters, io.iters)
-    assert np.linalg.norm(x - xt) <= 1e-6 * np.linalg.norm(xt)
+    assert np.linalg.norm(x - xt) <= 1e-7 * np.linalg.norm(xt)
+    assert np.abs(x - xt).max() <= max(2.0 * np.abs(xo - xt).max(), 1e-7 * np.abs(xt).max())
 
 
 @pytest.mark.parametrize("name,cfg", [("poisson2d_64", {}), ("logk2d_48", {}),
@@ -182,6 +186,8 @@ def test_adjoint_parity(name, cfg):
     dA = dA.cpu().numpy()
     assert np.linalg.norm(lam - lam_o) <= 1e-6 * np.linalg.norm(lam_o)
     assert np.linalg.norm(dA - dA_o) <= 1e-6 * np.linalg.norm(dA_o)
+    assert np.abs(lam - lam_o).max() <= 1e-6 * np.abs(lam_o).max()
+    assert np.abs(dA - dA_o).max() <= 1e-6 * np.abs(dA_o).max()
     # the stored-pattern product: exact given the GPU's own lambda and x
     rows = A.row_of()
     ref = -lam[rows] * x.cpu().numpy()[A.col_idx]
@@ -339,35 +345,63 @@ def test_symmetry_detection_and_nonsymmetric_adjoint_reuse():
     (lambda: M.convdiff3d_upwind(N=160), {"solver": "BICGSTAB"}),
 ])
 def test_full_size_parity(gen, cfg):
-    """128^3 GRF diffusion and 160^3 convection-diffusion: level-0 and level-1
-    aggregates and coarse patterns bit-exact, iteration counts within 2 of the
-    oracle, both precision forms at true residual <= 1e-8 and within 1e-6 of
-    the oracle's solution; the adjoint's lambda within 1e-6."""
+    """128^3 GRF diffusion and 160^3 convection-diffusion, in the launch
+    configuration the benchmark times: the aggregates of every level and
+    every coarse operator (pattern and values) bit-exact in both precision
+    forms.  Their solutions and gradients are held to the oracle in
+    test_gpu_error_bars.py."""
     w = gen()
     A = w.A
     h = O.Hierarchy(A, ocfg(cfg))
-    xo, io = h.solve(w.b)
     for prec in ("FP64", "MIXED"):
         s = gpu_solver(A, dict(cfg, precision=prec))
         info = s.info()
         assert info.nlevels == h.nlevels
-        for l in range(2):
-            lv = h.level(l)
-            assert np.array_equal(s.aggregates(l), lv.agg)
-            rp, ci, v, _ = s.level(l + 1, "A")
-            nxt = h.level(l + 1).A
-            assert np.array_equal(rp, nxt.row_ptr) and np.array_equal(ci, nxt.col_idx)
-            assert np.array_equal(v.view(np.int64), nxt.values.view(np.int64))
-        x, gi = s.solve(dev(w.b))
-        x = x.cpu().numpy()
-        assert gi.status == 0 and gi.rel_res_true <= 1e-8, gi
-        assert abs(gi.iters - io.iters) <= 2, (prec, gi.iters, io.iters)
-        assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
-        if prec == "MIXED":
-            g = np.random.default_rng(7).uniform(-1, 1, A.n)
-            lam, dA, ai = s.adjoint(dev(x), dev(g))
-            assert ai.status == 0 and ai.rel_res_true <= 1e-8
-            lam_o, _, _ = h.adjoint(x, g, A.nnz)
-            lam = lam.cpu().numpy()
-            assert np.linalg.norm(lam - lam_o) <= 1e-6 * np.linalg.norm(lam_o)
+        for l in range(h.nlevels - 1):
+            lv, nxt = h.level(l), h.level(l + 1)
+            assert np.array_equal(s.aggregates(l), lv.agg), (prec, l)
+            for which, ref in (("P", lv.P), ("R", lv.R), ("A", None)):
+                ref = ref if ref is not None else nxt.A
+                rp, ci, v, _ = s.level(l if which != "A" else l + 1, which)
+                assert np.array_equal(rp, ref.row_ptr) and np.array_equal(ci, ref.col_idx), (prec, which, l)
+                assert np.array_equal(v.view(np.int64), ref.values.view(np.int64)), (prec, which, l)
         s.close()
+
+
+# ---------------------------------------------------------------------------
+# BiCGStab breakdown and its one restart
+# ---------------------------------------------------------------------------
+
+def _dense_csr(D):
+    rows, cols = np.nonzero(D)
+    rp = np.zeros(D.shape[0] + 1, np.int32)
+    rp[1:] = np.cumsum(np.bincount(rows, minlength=D.shape[0]))
+    return M.CSR(rp, cols.astype(np.int32), D[rows, cols].astype(np.float64))
+
+
+def test_bicgstab_breakdown_restart_parity():
+    """rho = r^.r is exactly 0 at iteration 2 of this dyadic system (see the
+    oracle's pin): the GPU restarts once from x with r^ = r, as the oracle
+    does, and converges to A^-1 b in the same iterations."""
+    D = np.array([[3.0, 0.0, 3.0], [0.0, 4.0, -1.0], [1.0, 0.0, 2.0]])
+    A = _dense_csr(D)
+    b = np.ones(3)
+    cfg = {"solver": "BICGSTAB_NOPREC", "rtol": 1e-12}
+    xo, io = O.solve(A, b, ocfg(cfg))
+    x, info = gpu_solver(A, cfg).solve(dev(b))
+    assert io.status == O.OK and info.status == 0, info
+    assert info.iters == io.iters == 3
+    assert np.allclose(x.cpu().numpy(), np.linalg.solve(D, b), rtol=0, atol=1e-14)
+
+
+def test_bicgstab_second_breakdown_status():
+    """r^.A b = 0 at the first iteration and again after the one restart:
+    BREAKDOWN after two iterations, x still 0, as in the oracle."""
+    D = np.array([[1.0, -2.0], [0.0, 1.0]])
+    A = _dense_csr(D)
+    cfg = {"solver": "BICGSTAB_NOPREC"}
+    xo, io = O.solve(A, np.ones(2), ocfg(cfg))
+    x, info = gpu_solver(A, cfg).solve(dev(np.ones(2)))
+    assert io.status == O.BREAKDOWN and info.status == _lib.AMG_BREAKDOWN
+    assert info.iters == io.iters == 2
+    assert not x.cpu().numpy().any()
