@@ -73,7 +73,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--forms", default="mixed,fp64", help="comma list of precision forms to time (first = headline)")
     p.add_argument("--no-trace", action="store_true", help="skip the per-kernel traced pass (profiler captures)")
-    p.add_argument("--layout", default="AUTO", choices=["AUTO", "CSR", "WINDOWED", "SLICED_ELL"],
+    p.add_argument("--layout", default="AUTO", choices=["AUTO", "CSR", "WINDOWED", "SLICED_ELL", "ELL_DIRECT"],
                    help="tile layout of the streaming kernels (default: autotuned per operator)")
     p.add_argument("--amg-type", default="AGGREGATION", choices=["AGGREGATION", "CLASSICAL"],
                    help="AMG family: smoothed aggregation (default) or classical Ruge-Stueben")
@@ -401,14 +401,14 @@ def trace_pass(s, b, x, g, lam, dA, steps, dev, step=None, workload: str = ""):
 
 def plan_summary(s) -> dict:
     """The streaming plans setup chose for the levels that stream:
-    {"L<l>": {op: "<layout>/<rows per tile>x<threads per row>"}}."""
+    {"L<l>": {op: "<layout>/<rows per tile>x<threads per row>/s<stages>"}}."""
     out = {}
     for l in range(s.info().nlevels):
         ops = {}
         for op in ("pre", "post", "P", "R") + (("krylov",) if l == 0 else ()):
             p = s.plan(l, op)
             if p["layout"]:
-                ops[op] = f'{p["layout"]}/{p["rows_per_tile"]}x{p["threads_per_row"]}'
+                ops[op] = f'{p["layout"]}/{p["rows_per_tile"]}x{p["threads_per_row"]}/s{p["stages"]}'
         if ops:
             out[f"L{l}"] = ops
     return out

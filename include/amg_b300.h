@@ -92,6 +92,8 @@ extern "C" {
 #define AMG_LAYOUT_CSR 1        /* CSR row tiles; the vector gathered from global memory */
 #define AMG_LAYOUT_WINDOWED 2   /* CSR row tiles; windows of the vector staged in shared memory */
 #define AMG_LAYOUT_SLICED_ELL 3 /* 32-row slices stored slot-major, one thread per row; windows staged */
+#define AMG_LAYOUT_ELL_DIRECT 4 /* the same slot-major slices read with plain coalesced loads (no staging);
+                                   the vector gathered from global memory */
 
 typedef struct amg_handle_s *amg_handle; /* opaque, owned by the library until amg_free */
 
@@ -202,11 +204,13 @@ int amg_get_aggregates(amg_handle h, int level, int *agg);
 /* The streaming plan chosen at setup for one operator of level l: which = 0
  * A_l W (pre-smoothing), 1 P_l (prolongation), 2 R_l (restriction), 3 A_l
  * (post-smoothing), 4 the FP64 A of the Krylov products (level 0 only).
- * plan[0] = layout (AMG_LAYOUT_CSR, _WINDOWED or _SLICED_ELL; 0 when the
+ * plan[0] = layout (AMG_LAYOUT_CSR, _WINDOWED, _SLICED_ELL or _ELL_DIRECT; 0 when the
  * operator has no streaming plan and runs on the row-vector kernels),
- * plan[1] = rows per tile, plan[2] = threads per row, plan[3] = tiles.
+ * plan[1] = rows per tile, plan[2] = threads per row, plan[3] = tiles,
+ * plan[4] = pipeline stages (tiles in flight per CTA; 1 for _ELL_DIRECT,
+ * which stages nothing; 0 without a plan).
  * Errors: AMG_ERR_ARG (NULL, level or which out of range). */
-int amg_get_plan(amg_handle h, int level, int which, int plan[4]);
+int amg_get_plan(amg_handle h, int level, int which, int plan[5]);
 
 /* Per-kernel tracing of the solve phase.  The paper reports wall-clock times
  * only; this is the library's own instrumentation.  amg_profile(h, 1) clears

@@ -22,7 +22,7 @@ AMG_TEST_WITHHOLD_COPY, AMG_TEST_WITHHOLD_BARRIER = 1, 2
 SOLVERS = {"PCG": 0, "BICGSTAB": 1, "CG": 2, "BICGSTAB_NOPREC": 3}
 SMOOTHERS = {"JACOBI": 0, "L1_JACOBI": 1}
 PRECISIONS = {"FP64": 0, "MIXED": 1}
-LAYOUTS = {"AUTO": 0, "CSR": 1, "WINDOWED": 2, "SLICED_ELL": 3}
+LAYOUTS = {"AUTO": 0, "CSR": 1, "WINDOWED": 2, "SLICED_ELL": 3, "ELL_DIRECT": 4}
 AMG_TYPES = {"AGGREGATION": 0, "CLASSICAL": 1}
 
 # Every symbol the header declares.

@@ -270,18 +270,18 @@ class Solver:
         return agg
 
     PLAN_OPS = {"pre": 0, "P": 1, "R": 2, "post": 3, "krylov": 4}
-    LAYOUT_NAMES = {0: None, 1: "CSR", 2: "WINDOWED", 3: "SLICED_ELL"}
+    LAYOUT_NAMES = {0: None, 1: "CSR", 2: "WINDOWED", 3: "SLICED_ELL", 4: "ELL_DIRECT"}
 
     def plan(self, l: int, op: str) -> dict:
         """The streaming plan setup chose for one operator of level l (op in
         PLAN_OPS): layout name (None: row-vector kernels), rows per tile,
-        threads per row, tiles."""
-        out = (C.c_int * 4)()
+        threads per row, tiles, pipeline stages."""
+        out = (C.c_int * 5)()
         rc = self._L.amg_get_plan(self._h, l, self.PLAN_OPS[op], out)
         if rc < 0:
             raise AMGError(rc, "amg_get_plan")
         return {"layout": self.LAYOUT_NAMES[out[0]], "rows_per_tile": out[1], "threads_per_row": out[2],
-                "tiles": out[3]}
+                "tiles": out[3], "stages": out[4]}
 
 
 class BatchedSolver(Solver):

@@ -143,6 +143,7 @@ struct StreamPlan {
     // gathered vector (start, length pairs; ntiles x 32 ints), 16-bit local
     // column indices, and the window capacity per stage in elements
     int xw = 0;
+    int stages = 2;  // pipeline stages of windowed and sliced-ELL plans (2..4)
     const int *wtab = nullptr;
     const uint16_t *c16 = nullptr;
     // sliced-ELL plans (ell = 1; windowed, rt a multiple of 32): the entries
@@ -152,6 +153,13 @@ struct StreamPlan {
     // slots holds (-1: padding).  Value arrays are laid out in slot order per
     // plan: ev_dst[k] is the copy of CSR values ev_src[k] (vbytes[k] per value).
     int ell = 0;
+    // direct sliced-ELL plans (direct = 1: the slot-major layout read with
+    // plain loads, no tiles): column of every slot as a 16-bit offset from its
+    // row (dcol16, square operators) or an absolute int (dcol32); rt = 32
+    int direct = 0;
+    int maxw = 0;  // widest slice in slots (direct plans)
+    const int16_t *dcol16 = nullptr;
+    const int *dcol32 = nullptr;
     long long ne = 0;
     const int *soff = nullptr;
     const uint16_t *ec = nullptr;
@@ -245,6 +253,9 @@ struct Hierarchy {
     int iter_kernels = 0;
     DevArena arena;
     double setup_ms = 0.0;
+    // the autotuner's timed rounds (ms) of the tile-layout family and the
+    // direct sliced-ELL family (0: not compared); the faster one is in use
+    float plan_family_ms[2] = {0.f, 0.f};
 };
 
 // ---------------------------------------------------------------------------

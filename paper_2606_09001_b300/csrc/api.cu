@@ -36,7 +36,7 @@ int check_config(const amg_config &c) {
     if (c.solver < 0 || c.solver > 3 || (c.smoother != 0 && c.smoother != 1) || !(c.omega > 0.0) ||
         !(c.theta >= 0.0) || c.coarse_max < 1 || c.max_levels < 1 || c.max_levels > AMG_MAX_LEVELS ||
         !(c.rtol > 0.0) || c.max_iter < 1 || c.max_restarts < 0 || (c.precision != 0 && c.precision != 1) ||
-        c.symmetric < -1 || c.symmetric > 1 || c.layout < AMG_LAYOUT_AUTO || c.layout > AMG_LAYOUT_SLICED_ELL ||
+        c.symmetric < -1 || c.symmetric > 1 || c.layout < AMG_LAYOUT_AUTO || c.layout > AMG_LAYOUT_ELL_DIRECT ||
         (c.adjoint_reuse != 0 && c.adjoint_reuse != 1) ||
         (c.amg_type != AMG_TYPE_AGGREGATION && c.amg_type != AMG_TYPE_CLASSICAL) ||
         c.fuse_coarse < 0 || c.fuse_coarse > 2) {
@@ -202,7 +202,7 @@ int amg_setup(const amg_config *cfg, int n, long long nnz, const int *row_ptr, c
         h->H.nnz = nnz;
         if ((rc = build_hierarchy(&h->H, row_ptr, col_idx, values, h->s)) != AMG_OK) break;
         if ((rc = workspace_init(h->W, n)) < 0) break;
-        if ((rc = autotune_plans(&h->H, h->W.scal, h->s)) < 0) break;
+        if ((rc = autotune_plans(&h->H, h->W, h->s)) < 0) break;
         if ((rc = leave(h, cuda_stream, true)) < 0) break;
     } while (0);
     if (rc != AMG_OK) {
@@ -249,7 +249,7 @@ int amg_adjoint(amg_handle h, const double *x, const double *g, double *lambda, 
             if (rc == AMG_OK && reuse) {
                 const auto t0 = clk::now();
                 rc = build_transposed_hierarchy(HT, &h->H, h->s);
-                if (rc == AMG_OK) rc = autotune_plans(HT, h->W.scal, h->s);
+                if (rc == AMG_OK) rc = autotune_plans(HT, h->W, h->s);
                 HT->setup_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
             } else if (rc == AMG_OK) {
                 HT->cfg = h->H.cfg;
@@ -258,7 +258,7 @@ int amg_adjoint(amg_handle h, const double *x, const double *g, double *lambda, 
                 HT->nnz = nnz;
                 const auto t0 = clk::now();
                 rc = build_hierarchy(HT, At.rp, At.ci, At.v, h->s);
-                if (rc == AMG_OK) rc = autotune_plans(HT, h->W.scal, h->s);
+                if (rc == AMG_OK) rc = autotune_plans(HT, h->W, h->s);
                 HT->setup_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
             }
             cudaStreamSynchronize(h->s);
@@ -399,16 +399,23 @@ int amg_widen_f32(const float *in, double *out, long long n, void *cuda_stream) 
     return AMG_OK;
 }
 
-int amg_get_plan(amg_handle h, int level, int which, int plan[4]) {
+int amg_get_plan(amg_handle h, int level, int which, int plan[5]) {
     if (!h || !plan || level < 0 || level >= h->H.nlevels || which < 0 || which > 4 || (which == 4 && level != 0))
         return AMG_ERR_ARG;
     const Level &lv = h->H.L[level];
     const StreamPlan *ps[] = {&lv.sa, &lv.sp, &lv.sr, &lv.sa_post, &lv.sa64};
     const StreamPlan &p = *ps[which];
-    plan[0] = p.rt == 0 ? 0 : p.ell ? AMG_LAYOUT_SLICED_ELL : p.c16 ? AMG_LAYOUT_WINDOWED : AMG_LAYOUT_CSR;
+    plan[0] = p.rt == 0      ? 0
+              : p.direct     ? AMG_LAYOUT_ELL_DIRECT
+              : p.ell        ? AMG_LAYOUT_SLICED_ELL
+              : p.c16        ? AMG_LAYOUT_WINDOWED
+                             : AMG_LAYOUT_CSR;
     plan[1] = p.rt;
     plan[2] = p.vec;
     plan[3] = p.ntiles;
+    // CSR tiles: three stages of 4-byte values at 512 threads, else two
+    const bool v4 = which != 4 && h->H.cfg.precision == AMG_PRECISION_MIXED;
+    plan[4] = p.rt == 0 ? 0 : p.direct ? 1 : (p.ell || p.c16) ? p.stages : (p.nt == 512 && v4 ? 3 : 2);
     return AMG_OK;
 }
 

@@ -1024,23 +1024,27 @@ struct OpFin {
     }
 };
 
+// Resident CTAs per SM of a windowed or sliced-ELL launch (two when they fit:
+// the SM's 228 KB less about 11 KB of static and reserved memory per CTA).
+static int ctas_per_sm(int smem) { return std::max(1, std::min(2, (228 * 1024) / (smem + 11 * 1024))); }
+
 template <typename TM, int VEC, class Op, int NT>
 static int stream_launch_nt(const StreamPlan &pl, int n, const int *rp, const int *ci, const TM *v, const Op &op,
                             int *err, cudaStream_t s) {
     if constexpr (NT == 512) {
         if (pl.c16) {
         using GX = typename Op::GX;
-        const int smem = stream::smem_bytes_win<TM, GX, NT>(pl.rt, pl.cap, pl.xw);
+        const int smem = stream::smem_bytes_win<TM, GX, NT>(pl.rt, pl.cap, pl.xw, pl.stages);
         static int attr_set = 0;
         if (smem > attr_set) {
             AMG_CUDA_TRY(cudaFuncSetAttribute(stream::k_stream_win<TM, VEC, Op, NT>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             attr_set = smem;
         }
-        const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 11 * 1024)));
+        const int per_sm = ctas_per_sm(smem);
         const int grid = std::max(1, std::min(pl.ntiles, per_sm * num_sms()));
         AMG_TRY(launch_k(stream::k_stream_win<TM, VEC, Op, NT>, grid, NT, smem, s, n, pl.rt, pl.cap, pl.xw, pl.ntiles, rp, pl.c16,
-                                                                      v, pl.wtab, op, err));
+                                                                      v, pl.wtab, op, err, pl.stages));
         AMG_LAUNCH_CHECK();
         return AMG_OK;
         }
@@ -1089,12 +1093,16 @@ static int stream_launch_ell(const StreamPlan &pl, int n, const TM *v, const Op 
         return AMG_ERR_ARG;
     }
     using GX = typename Op::GX;
-    // the epilogue's row operands are staged while two CTAs per SM still fit
-    int rows = Op::NROWV > 0 ? 1 : 0;
-    int smem = stream::smem_bytes_ell<TM, GX>(pl.cap, pl.xw, pl.rt, rows ? Op::ROWV_BYTES : 0);
-    if (rows && 2 * (smem + 11 * 1024) > 228 * 1024) {
-        rows = 0;
-        smem = stream::smem_bytes_ell<TM, GX>(pl.cap, pl.xw, pl.rt, 0);
+    // the epilogue's row operands are staged while as many CTAs per SM fit
+    // as without them (and the stage stays within one CTA's 227 KB)
+    int smem = stream::smem_bytes_ell<TM, GX>(pl.cap, pl.xw, pl.rt, 0, pl.stages);
+    int rows = 0;
+    if (Op::NROWV > 0) {
+        const int with = stream::smem_bytes_ell<TM, GX>(pl.cap, pl.xw, pl.rt, Op::ROWV_BYTES, pl.stages);
+        if (ctas_per_sm(with) == ctas_per_sm(smem) && with <= 227 * 1024 - 11 * 1024) {
+            rows = 1;
+            smem = with;
+        }
     }
     static int attr_set = 0;
     if (smem > attr_set) {
@@ -1102,10 +1110,44 @@ static int stream_launch_ell(const StreamPlan &pl, int n, const TM *v, const Op 
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr_set = smem;
     }
-    const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 11 * 1024)));
+    const int per_sm = ctas_per_sm(smem);
     const int grid = std::max(1, std::min(pl.ntiles, per_sm * num_sms()));
     AMG_TRY(launch_k(stream::k_stream_ell<TM, Op, 512>, grid, 512, smem, s, n, pl.rt, pl.cap, pl.xw, pl.ntiles, pl.soff,
-                     pl.ec, ev, pl.wtab, op, rows, err));
+                     pl.ec, ev, pl.wtab, op, rows, err, pl.stages));
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+}
+
+template <typename TM, class Op>
+static int stream_launch_direct(const StreamPlan &pl, int n, const TM *v, const Op &op, cudaStream_t s) {
+    const TM *ev = static_cast<const TM *>(ell_values(pl, v));
+    if (!ev) {
+        set_last_error("streaming pass: the operator's values are not laid out for its direct plan");
+        return AMG_ERR_ARG;
+    }
+    constexpr int NT = stream::DIRECT_THREADS;
+    // one wave of resident blocks (grid-stride over the slices), at most
+    // num_sms() * 8: the reductions' partial sums hold that many
+    auto wave = [](const void *fn) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, 0) != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        return std::min(per_sm, 8) * num_sms();
+    };
+    const int need = (pl.ntiles + NT / 32 - 1) / (NT / 32);
+    auto go = [&](auto kern, const auto *col, int &w) -> int {
+        if (!w) w = wave((const void *)kern);
+        AMG_TRY(launch_k(kern, std::max(1, std::min(need, w)), NT, 0, s, n, pl.ntiles, pl.soff, col, ev, op));
+        return AMG_OK;
+    };
+    static int w16n = 0, w16w = 0, w32n = 0, w32w = 0;
+    const bool wide = pl.maxw > 8;
+    if (pl.dcol16 && !wide) AMG_TRY(go(stream::k_ell_direct<TM, int16_t, Op, false, NT>, pl.dcol16, w16n));
+    else if (pl.dcol16) AMG_TRY(go(stream::k_ell_direct<TM, int16_t, Op, true, NT>, pl.dcol16, w16w));
+    else if (!wide) AMG_TRY(go(stream::k_ell_direct<TM, int, Op, false, NT>, pl.dcol32, w32n));
+    else AMG_TRY(go(stream::k_ell_direct<TM, int, Op, true, NT>, pl.dcol32, w32w));
     AMG_LAUNCH_CHECK();
     return AMG_OK;
 }
@@ -1114,6 +1156,7 @@ static int stream_launch_ell(const StreamPlan &pl, int n, const TM *v, const Op 
 template <typename TM, class Op>
 static int stream_launch(const StreamPlan &pl, int n, const int *rp, const int *ci, const TM *v, const Op &op,
                          int *err, cudaStream_t s) {
+    if (pl.direct) return stream_launch_direct<TM, Op>(pl, n, v, op, s);
     if (pl.ell) return stream_launch_ell<TM, Op>(pl, n, v, op, err, s);
     switch (pl.vec) {
         case 1: return stream_launch_vec<TM, 1, Op>(pl, n, rp, ci, v, op, err, s);
@@ -1420,6 +1463,33 @@ __global__ void k_ell_fill(int n, int nsl, const int *__restrict__ rp, const uin
     }
 }
 
+// One thread per slice row of a direct sliced-ELL plan: the stored entry each
+// slot holds (-1: padding) and its column, as an offset from the row (col16;
+// *bad is set when an offset does not fit 16 bits) or absolute (col32).
+// Padding slots take the row's first column, or column min(r, ncols - 1) for
+// an empty row and the rows past n, so every slot's column is valid.
+__global__ void k_direct_fill(int n, int ncols, int nsl, const int *__restrict__ rp, const int *__restrict__ ci,
+                              const int *__restrict__ soff, int *eperm, int16_t *col16, int *col32, int *bad) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (long long)nsl * 32) return;
+    const int g = (int)(r >> 5), lane = (int)(r & 31);
+    const int s0 = soff[g], wd = (soff[g + 1] - s0) >> 5;
+    const int b = r < n ? rp[r] : 0, len = r < n ? rp[r + 1] - b : 0;
+    const int pad = len > 0 ? ci[b] : (int)min(r, (long long)ncols - 1);
+    for (int u = 0; u < wd; ++u) {
+        const int pos = s0 + u * 32 + lane;
+        const int c = u < len ? ci[b + u] : pad;
+        eperm[pos] = u < len ? b + u : -1;
+        if (col16) {
+            const long long d = (long long)c - r;
+            if (d < -32768 || d > 32767) atomicExch(bad, 1);
+            else col16[pos] = (int16_t)d;
+        } else {
+            col32[pos] = c;
+        }
+    }
+}
+
 // dst = the values of src in slot order (zero in padding slots).
 template <typename T>
 __global__ void k_ell_vals(long long ne, const int *__restrict__ eperm, const T *__restrict__ src, T *dst) {
@@ -1503,6 +1573,75 @@ static bool build_ell(const DevCSR &m, StreamPlan &p, int gx_bytes, Scratch &scr
     return true;
 }
 
+// A direct sliced-ELL plan for operator m (the slot-major layout of 32-row
+// slices, read with plain loads): slice offsets, the slot-to-entry map and
+// the columns -- 16-bit offsets from the row when use16 (square operators,
+// every offset within 16 bits), else absolute -- in `scr`.  Returns false
+// when the offsets do not fit or the slot count overflows.
+static bool build_direct(const DevCSR &m, StreamPlan &p, bool use16, Scratch &scr, cudaStream_t s) {
+    const int n = m.nrows, nsl = (n + 31) / 32;
+    if (use16 && m.ncols != m.nrows) return false;
+    int *wd = nullptr, *soff = nullptr, *bad = nullptr, *eperm = nullptr, *c32 = nullptr;
+    int16_t *c16 = nullptr;
+    if (scr.alloc(&wd, (size_t)nsl) < 0 || scr.alloc(&soff, (size_t)nsl + 1) < 0 || scr.alloc(&bad, 1) < 0) {
+        cudaGetLastError();
+        return false;
+    }
+    k_ell_width<<<(nsl + 255) / 256, 256, 0, s>>>(n, nsl, m.rp, wd);
+    std::vector<int> w((size_t)nsl), so((size_t)nsl + 1);
+    if (cudaMemcpyAsync(w.data(), wd, sizeof(int) * (size_t)nsl, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    long long tot = 0;
+    int maxw = 0;
+    for (int g = 0; g < nsl; ++g) {
+        so[g] = (int)tot;
+        tot += 32LL * w[g];
+        maxw = std::max(maxw, w[g]);
+        if (tot > INT_MAX - 64) return false;
+    }
+    so[nsl] = (int)tot;
+    const size_t ne = (size_t)std::max(1LL, tot);
+    if (scr.alloc(&eperm, ne) < 0 || (use16 ? scr.alloc(&c16, ne) : scr.alloc(&c32, ne)) < 0) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaMemcpyAsync(soff, so.data(), sizeof(int) * so.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const long long rows = (long long)nsl * 32;
+    k_direct_fill<<<(int)((rows + 255) / 256), 256, 0, s>>>(n, m.ncols, nsl, m.rp, m.ci, soff, eperm, c16, c32, bad);
+    int hbad = 1;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (hbad) return false;
+    p = StreamPlan();
+    p.direct = 1;
+    p.maxw = maxw;
+    p.rt = 32;
+    p.vec = 1;
+    p.nt = stream::DIRECT_THREADS;
+    p.ntiles = nsl;
+    p.ne = tot;
+    p.soff = soff;
+    p.eperm = eperm;
+    p.dcol16 = c16;
+    p.dcol32 = c32;
+    return true;
+}
+
+// tune_plan's layout restriction for the tile family: every layout but the
+// direct one (AMG_LAYOUT_AUTO admits all of them)
+constexpr int LAYOUT_TILES = -1;
+
 // What a plan is timed with: the pass it serves, epilogue included, on
 // scratch vectors (y = M x for passes without an epilogue of their own).
 enum TuneKind { TUNE_SPMV, TUNE_PRE, TUNE_POST0, TUNE_POST, TUNE_PROLONG, TUNE_ALPHA };
@@ -1522,11 +1661,12 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &
     std::vector<StreamPlan> cands = plan_candidates(m, pl, sizeof(TM) == 4, s);
     Scratch scr;
     // windowed variants of the 512-thread candidates
+    const bool tiles = layout != AMG_LAYOUT_ELL_DIRECT;
     if (pl.rt > 0) {
         std::vector<int> rp((size_t)m.nrows + 1);
         AMG_CUDA_TRY(cudaMemcpy(rp.data(), m.rp, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost));
         const size_t nbase = cands.size();
-        for (size_t q = 0; q < nbase; ++q) {
+        for (size_t q = 0; q < nbase && tiles; ++q) {
             if (cands[q].nt != 512) continue;
             StreamPlan w = cands[q];
             int worst = 0;
@@ -1536,7 +1676,7 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &
         // sliced-ELL variants: tiles of one or two passes of the 15 consumer
         // warps (a slice each), and of 7 slices for small operators
         for (int rt : {480, 960, 224}) {
-            if ((long long)m.nrows < 2LL * rt) continue;
+            if (!tiles || (long long)m.nrows < 2LL * rt) continue;
             StreamPlan w;
             w.rt = rt;
             w.vec = 1;
@@ -1559,20 +1699,59 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &
             w.ev_bytes[0] = (int)sizeof(TM);
             cands.push_back(w);
         }
+        // the direct sliced-ELL layout: 16-bit column offsets where they fit,
+        // else absolute columns
+        for (bool use16 : {true, false}) {
+            if (layout == LAYOUT_TILES) break;
+            StreamPlan d;
+            if (!build_direct(m, d, use16, scr, s)) continue;
+            TM *ev = nullptr;
+            if (scr.alloc(&ev, (size_t)std::max(1LL, d.ne)) < 0) {
+                cudaGetLastError();
+                break;
+            }
+            if (ell_lay_out(d, vals, ev, (int)sizeof(TM), s) < 0) break;
+            d.nev = 1;
+            d.ev_src[0] = vals;
+            d.ev_dst[0] = ev;
+            d.ev_bytes[0] = (int)sizeof(TM);
+            cands.push_back(d);
+            break;
+        }
+        // the same tiles with a deeper ring: 3 and 4 stages, at two CTAs per
+        // SM where they still fit, else at one (more bytes in flight per SM).
+        // Sized for FP64 gathers, the widest any pass of the plan makes (the
+        // finest level's pre-smoothing reads an FP64 input when no FP32 copy
+        // is given), so every launch stays within one CTA's shared memory.
+        const size_t nring = cands.size();
+        for (size_t q = 0; q < nring; ++q) {
+            if (!cands[q].c16 && !cands[q].ell) continue;
+            for (int st : {3, 4}) {
+                StreamPlan d = cands[q];
+                d.stages = st;
+                const int smem = d.ell ? stream::smem_bytes_ell<TM, double>(d.cap, d.xw, d.rt, 0, st)
+                                       : stream::smem_bytes_win<TM, double>(d.rt, d.cap, d.xw, st);
+                if (smem <= 216 * 1024) cands.push_back(d);
+            }
+        }
     }
     if (layout != AMG_LAYOUT_AUTO) {
-        // only the requested layout (the heuristic CSR plan when none fits)
+        // only the requested layout (LAYOUT_TILES: every tile layout), the
+        // heuristic CSR plan when none fits
         auto kind = [](const StreamPlan &p) {
-            return p.ell ? AMG_LAYOUT_SLICED_ELL : p.c16 ? AMG_LAYOUT_WINDOWED : AMG_LAYOUT_CSR;
+            return p.direct ? AMG_LAYOUT_ELL_DIRECT
+                   : p.ell  ? AMG_LAYOUT_SLICED_ELL
+                   : p.c16  ? AMG_LAYOUT_WINDOWED
+                            : AMG_LAYOUT_CSR;
         };
         std::vector<StreamPlan> keep;
         for (const StreamPlan &c : cands)
-            if (kind(c) == layout) keep.push_back(c);
+            if (layout == LAYOUT_TILES ? kind(c) != AMG_LAYOUT_ELL_DIRECT : kind(c) == layout) keep.push_back(c);
         if (keep.empty() && !cands.empty()) keep.push_back(cands[0]);
         cands.swap(keep);
     }
     if (cands.empty()) return AMG_OK;
-    if (cands.size() == 1 && !cands[0].ell && !cands[0].c16) {
+    if (cands.size() == 1 && !cands[0].ell && !cands[0].c16 && !cands[0].direct) {
         pl = cands[0];
         return AMG_OK;
     }
@@ -1676,7 +1855,7 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &
     }
     if (rc >= 0) {
         const float fastest = *std::min_element(times.begin(), times.end());
-        auto rank = [](const StreamPlan &p) { return p.ell ? 0 : p.c16 ? 1 : 2; };
+        auto rank = [](const StreamPlan &p) { return p.ell ? 0 : p.direct ? 1 : p.c16 ? 2 : 3; };
         int pick = -1;
         for (size_t q = 0; q < cands.size(); ++q)
             if (times[q] <= 1.03f * fastest && (pick < 0 || rank(cands[q]) < rank(cands[pick]))) pick = (int)q;
@@ -1708,6 +1887,29 @@ static int tune_plan(const DevCSR &m, const TM *vals, StreamPlan &pl, DevArena &
         chosen.eperm = eperm;
         chosen.ec = ec;
         chosen.nev = 0;
+    } else if (chosen.direct) {
+        // keep the chosen slice tables (the candidates live in scratch memory)
+        const int nsl = (m.nrows + 31) / 32;
+        const size_t ne = (size_t)std::max(1LL, chosen.ne);
+        int *soff = nullptr, *eperm = nullptr, *c32 = nullptr;
+        int16_t *c16 = nullptr;
+        AMG_TRY(ar.alloc(&soff, (size_t)nsl + 1));
+        AMG_TRY(ar.alloc(&eperm, ne));
+        AMG_CUDA_TRY(cudaMemcpyAsync(soff, chosen.soff, sizeof(int) * ((size_t)nsl + 1), cudaMemcpyDeviceToDevice, s));
+        AMG_CUDA_TRY(cudaMemcpyAsync(eperm, chosen.eperm, sizeof(int) * ne, cudaMemcpyDeviceToDevice, s));
+        if (chosen.dcol16) {
+            AMG_TRY(ar.alloc(&c16, ne));
+            AMG_CUDA_TRY(cudaMemcpyAsync(c16, chosen.dcol16, sizeof(int16_t) * ne, cudaMemcpyDeviceToDevice, s));
+        } else {
+            AMG_TRY(ar.alloc(&c32, ne));
+            AMG_CUDA_TRY(cudaMemcpyAsync(c32, chosen.dcol32, sizeof(int) * ne, cudaMemcpyDeviceToDevice, s));
+        }
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        chosen.soff = soff;
+        chosen.eperm = eperm;
+        chosen.dcol16 = c16;
+        chosen.dcol32 = c32;
+        chosen.nev = 0;
     } else if (chosen.c16) {
         // keep the chosen windows (the candidates live in scratch memory)
         int *wtab = nullptr;
@@ -1737,14 +1939,14 @@ static void for_each_plan(Hierarchy *h, F f) {
 // (nothing for other plans); plans of one layout (the same slice offsets)
 // share a copy.
 static int ell_bind_one(Hierarchy *h, StreamPlan &pl, const void *src, int vbytes, cudaStream_t s) {
-    if (!pl.ell || !src || ell_values(pl, src)) return AMG_OK;
+    if (!(pl.ell || pl.direct) || !src || ell_values(pl, src)) return AMG_OK;
     if (pl.nev == StreamPlan::EV_MAX) {
         set_last_error("sliced-ELL plan: more than %d value arrays", StreamPlan::EV_MAX);
         return AMG_ERR_ARG;
     }
     void *dst = nullptr;
     for_each_plan(h, [&](StreamPlan &q) {
-        if (!dst && q.ell && q.soff == pl.soff) dst = const_cast<void *>(ell_values(q, src));
+        if (!dst && (q.ell || q.direct) && q.soff == pl.soff) dst = const_cast<void *>(ell_values(q, src));
     });
     if (!dst) {
         const size_t ne = (size_t)std::max(1LL, pl.ne);
@@ -1791,7 +1993,7 @@ static int ell_bind(Hierarchy *h, cudaStream_t s) {
 int ell_refresh(Hierarchy *h, cudaStream_t s) {
     int rc = AMG_OK;
     for_each_plan(h, [&](StreamPlan &q) {
-        if (!q.ell) return;
+        if (!q.ell && !q.direct) return;
         for (int k = 0; k < q.nev && rc == AMG_OK; ++k) rc = ell_lay_out(q, q.ev_src[k], q.ev_dst[k], q.ev_bytes[k], s);
     });
     AMG_TRY(rc);
@@ -1799,10 +2001,10 @@ int ell_refresh(Hierarchy *h, cudaStream_t s) {
     return AMG_OK;
 }
 
-// Refines every streaming plan of the hierarchy by timed trial (the autotuner).
-int autotune_plans(Hierarchy *h, DevScalars *, cudaStream_t s) {
+// Refines every streaming plan of the hierarchy by timed trial of each
+// operator's own pass, over the layouts `lay` admits.
+static int tune_all(Hierarchy *h, int lay, cudaStream_t s) {
     const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
-    const int lay = h->cfg.layout;
     for (int l = 0; l < h->nsolve - 1; ++l) {
         Level &lv = h->L[l];
         // pre- and post-smoothing gather different vectors and run different
@@ -2679,6 +2881,96 @@ int vcycle_apply(Hierarchy *h, Workspace &W, const double *r, double *z, cudaStr
     }
     AMG_TRY(set_control(W, s, 0, AMG_OK, 0, h->cfg.max_iter, 1));
     return vcycle(h, W, r, z, FIN_NONE, s);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: plan family by timed trial of whole cycles
+// ---------------------------------------------------------------------------
+
+// Every streaming plan of h (the order of for_each_plan).
+static std::vector<StreamPlan> plans_of(Hierarchy *h) {
+    std::vector<StreamPlan> v;
+    for_each_plan(h, [&](StreamPlan &p) { v.push_back(p); });
+    return v;
+}
+
+static void set_plans(Hierarchy *h, const std::vector<StreamPlan> &v) {
+    size_t k = 0;
+    for_each_plan(h, [&](StreamPlan &p) { p = v[k++]; });
+}
+
+// Best of three trials of four rounds (after two), a round being one V-cycle
+// followed by the finest level's FP64 product -- the passes of one Krylov
+// iteration, in their order -- on constant vectors, with h's current plans.
+// The product's finisher (the true residual's) never stops the scalars, so
+// every round does its full work.
+static int time_rounds(Hierarchy *h, Workspace &W, cudaStream_t s, float *ms_out) {
+    const int n = h->n;
+    const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
+    k_fill<double><<<256, 256, 0, s>>>((size_t)n, 1.0, W.r);
+    k_fill<double><<<256, 256, 0, s>>>((size_t)n, 1.0, W.b);
+    k_fill<float><<<256, 256, 0, s>>>((size_t)n, 1.0f, W.r32);
+    AMG_LAUNCH_CHECK();
+    auto round = [&]() -> int {
+        AMG_TRY(set_control(W, s, 0, AMG_OK, 0, h->cfg.max_iter, 1));
+        if (h->nc > 0) AMG_TRY(vcycle(h, W, W.r, W.z, FIN_NONE, s, mixed ? W.r32 : nullptr));
+        return spmv_fin<SF_TRUE_RES>(h, W, "true_residual", h->nc > 0 ? W.z : W.r, W.t, W.b, s);
+    };
+    cudaEvent_t e0, e1;
+    AMG_CUDA_TRY(cudaEventCreate(&e0));
+    AMG_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int rc = AMG_OK;
+    for (int k = 0; k < 2 && rc >= 0; ++k) rc = round();
+    for (int trial = 0; trial < 3 && rc >= 0; ++trial) {
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < 4 && rc >= 0; ++k) rc = round();
+        cudaEventRecord(e1, s);
+        if (rc >= 0 && cudaEventSynchronize(e1) == cudaSuccess) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best = std::min(best, t);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    AMG_TRY(rc);
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    *ms_out = best;
+    return AMG_OK;
+}
+
+// The autotuner.  With a requested layout, each operator's plan is the
+// fastest of that layout in a timed trial of its own pass.  With
+// AMG_LAYOUT_AUTO the two families are tuned apart -- the tile layouts (CSR,
+// windowed and sliced-ELL tiles through a shared-memory ring) and the direct
+// sliced-ELL layout -- and whole V-cycles with the finest product decide
+// between them: a cycle that interleaves the two families runs slower than
+// either alone (the persistent tile kernels' CTAs wait behind the direct
+// kernels' blocks), which the per-pass trials cannot see.
+int autotune_plans(Hierarchy *h, Workspace &W, cudaStream_t s) {
+    if (h->cfg.layout != AMG_LAYOUT_AUTO) return tune_all(h, h->cfg.layout, s);
+    const std::vector<StreamPlan> base = plans_of(h);
+    AMG_TRY(tune_all(h, LAYOUT_TILES, s));
+    const std::vector<StreamPlan> tiles = plans_of(h);
+    set_plans(h, base);
+    AMG_TRY(tune_all(h, AMG_LAYOUT_ELL_DIRECT, s));
+    const std::vector<StreamPlan> direct = plans_of(h);
+    bool any_direct = false;
+    for (const StreamPlan &p : direct) any_direct |= p.direct != 0;
+    if (!any_direct) {
+        set_plans(h, tiles);
+        return AMG_OK;
+    }
+    float ms_tiles = 0.f, ms_direct = 0.f;
+    set_plans(h, tiles);
+    AMG_TRY(time_rounds(h, W, s, &ms_tiles));
+    set_plans(h, direct);
+    AMG_TRY(time_rounds(h, W, s, &ms_direct));
+    if (ms_tiles <= ms_direct) set_plans(h, tiles);
+    h->plan_family_ms[0] = ms_tiles;
+    h->plan_family_ms[1] = ms_direct;
+    return AMG_OK;
 }
 
 int grad_values(Hierarchy *h, Workspace &W, const double *lambda, const double *x, double *dA, cudaStream_t s) {

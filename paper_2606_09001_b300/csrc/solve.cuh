@@ -63,9 +63,9 @@ struct Workspace {
 
 int workspace_init(Workspace &W, int n);
 
-// Refines the hierarchy's streaming plans by timed trial (needs the workspace's
-// device scalars for the kernels' done flag).
-int autotune_plans(Hierarchy *h, DevScalars *sc, cudaStream_t s);
+// Refines the hierarchy's streaming plans by timed trial (runs whole cycles
+// on the workspace's vectors to choose between plan families).
+int autotune_plans(Hierarchy *h, Workspace &W, cudaStream_t s);
 void workspace_free(Workspace &W);
 
 struct SolveResult {

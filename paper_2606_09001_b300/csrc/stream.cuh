@@ -28,7 +28,7 @@ namespace amg {
 namespace stream {
 
 constexpr int THREADS = 512;  // the default CTA width
-constexpr int MAX_STAGES = 3;
+constexpr int MAX_STAGES = 4;
 constexpr int RT_MAX = 1024;
 constexpr int CAP = 4096;  // stage capacity in stored entries
 // Tile descriptors (entry range, window table row) of a CTA's first META_T
@@ -302,12 +302,16 @@ struct WLayout {
           xwb(align16(xw * (int)sizeof(GX))), stb(rpb + cib + vab + xwb + 16) {}
 };
 
-// Two pipeline stages: consumers no longer wait on gathers, so two tiles in
-// flight per CTA (four per SM) cover the bulk copies' latency.
-constexpr int WIN_STAGES = 2;
+// Pipeline stages of the windowed and sliced-ELL kernels: a plan's own count
+// (2 to MAX_STAGES).  Bytes in flight per SM set the bandwidth a pass
+// reaches, so the autotuner also tries more stages of the same tiles (at one
+// CTA per SM when two no longer fit) and smaller tiles with more stages.
+constexpr int WIN_STAGES = 2;  // the default
 
 template <typename TM, typename GX, int NT = THREADS>
-inline int smem_bytes_win(int rt, int cap, int xw) { return WIN_STAGES * WLayout<TM, GX>(rt, cap, xw).stb; }
+inline int smem_bytes_win(int rt, int cap, int xw, int stages = WIN_STAGES) {
+    return stages * WLayout<TM, GX>(rt, cap, xw).stb;
+}
 
 // Producer side of the windowed kernels: bulk-copies the windows of the
 // gathered vector gx for tile t (the CTA's j-th; its descriptors from the
@@ -357,10 +361,10 @@ template <typename TM, int VEC, class Op, int NT = THREADS>
 __global__ void __launch_bounds__(NT, 2) k_stream_win(int n, int rt, int cap, int xw, int ntiles,
                                                       const int *__restrict__ rp, const uint16_t *__restrict__ c16,
                                                       const TM *__restrict__ v, const int *__restrict__ wtab, Op op,
-                                                      int *err) {
+                                                      int *err, int stages) {
     using GX = typename Op::GX;
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int STAGES = WIN_STAGES;
+    const int STAGES = stages;
     constexpr int CONSUMER_WARPS = NT / 32 - 1;
     __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES];
     const WLayout<TM, GX> L(rt, cap, xw);
@@ -544,8 +548,8 @@ struct ELayout {
 };
 
 template <typename TM, typename GX>
-inline int smem_bytes_ell(int cap, int xw, int rt, int rvbytes) {
-    return WIN_STAGES * ELayout<TM, GX>(cap, xw, rt, rvbytes).stb;
+inline int smem_bytes_ell(int cap, int xw, int rt, int rvbytes, int stages = WIN_STAGES) {
+    return stages * ELayout<TM, GX>(cap, xw, rt, rvbytes).stb;
 }
 
 // One lane's row of a slice with exactly W slots: every value, index and
@@ -569,10 +573,10 @@ template <typename TM, class Op, int NT = THREADS>
 __global__ void __launch_bounds__(NT, 2) k_stream_ell(int n, int rt, int cap, int xw, int ntiles,
                                                       const int *__restrict__ soff, const uint16_t *__restrict__ ec,
                                                       const TM *__restrict__ ev, const int *__restrict__ wtab, Op op,
-                                                      int rows, int *err) {
+                                                      int rows, int *err, int stages) {
     using GX = typename Op::GX;
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int STAGES = WIN_STAGES;
+    const int STAGES = stages;
     constexpr int CONSUMER_WARPS = NT / 32 - 1;
     __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES];
     const ELayout<TM, GX> L(cap, xw, rt, rows ? Op::ROWV_BYTES : 0);
@@ -784,6 +788,116 @@ __global__ void __launch_bounds__(NT, 2) k_stream_ell(int n, int rt, int cap, in
     if (!ok) {
         atomicExch(err, 1);
         for (int k = 0; k < STAGES; ++k) mbar_try_wait(&full[k], 0);
+    }
+    op.template reduce<NT>(acc);
+}
+
+}  // namespace stream
+}  // namespace amg
+
+namespace amg {
+namespace stream {
+
+// ---------------------------------------------------------------------------
+// Direct sliced-ELL variant: no bulk copies
+// ---------------------------------------------------------------------------
+//
+// The sliced-ELL value layout (entry u of row 32g + l at soff[g] + 32u + l)
+// read straight from global memory: a warp takes a 32-row slice, one lane
+// per row, so each slot is one coalesced load of 32 values and one of 32
+// column indices; the gathered vector is read from global memory (L2: the
+// vectors of a pass fit in it), and the epilogue's row operands with
+// coalesced loads issued before the row's.  IDX is int16_t (column minus row,
+// for square operators whose couplings stay within 32767 rows) or int
+// (absolute columns).  Padding slots hold value 0 and a valid column.  With
+// many small independent loads per warp and no producer thread, the pass
+// keeps more memory requests in flight than a tile ring whose copies are
+// small; the autotuner times both.  Each row sums in slot (= CSR) order.
+constexpr int DIRECT_THREADS = 256;
+
+template <typename IDX>
+__device__ __forceinline__ int direct_col(IDX c, int i) {
+    if constexpr (sizeof(IDX) == 2) return i + (int)c;
+    else return (int)c;
+}
+
+template <typename TM, typename IDX, class Op, bool WIDE, int NT = DIRECT_THREADS>
+__global__ void __launch_bounds__(NT) k_ell_direct(int n, int nsl, const int *__restrict__ soff,
+                                                    const IDX *__restrict__ ecol, const TM *__restrict__ ev, Op op) {
+    constexpr int U = 8;  // slots whose loads are in flight together
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * (unsigned)NT) >> 5);
+    int g = (int)((blockIdx.x * (unsigned)NT + threadIdx.x) >> 5);
+    // a slice's first U slots (values, columns): the operator is constant, so
+    // the warp's first slice loads before the dependency wait; without WIDE
+    // (every slice at most U slots wide) each next slice's loads also go out
+    // behind the current slice's gathers
+    TM a[U];
+    IDX c[U];
+    int s0 = 0, wd = 0;
+    auto fetch = [&](int gg, TM (&av)[U], IDX (&cv)[U], int &s0v, int &wdv) {
+        s0v = __ldg(soff + gg);
+        wdv = (__ldg(soff + gg + 1) - s0v) >> 5;  // warp-uniform
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            if (q < wdv) {
+                av[q] = __ldg(ev + s0v + q * 32 + lane);
+                cv[q] = __ldg(ecol + s0v + q * 32 + lane);
+            }
+    };
+    if (g < nsl) fetch(g, a, c, s0, wd);
+    pdl_wait();
+    pdl_trigger();
+    if (op.done()) return;
+    double acc[2] = {0.0, 0.0};
+    while (g < nsl) {
+        const int i = g * 32 + lane;
+        typename Op::Pre pre{};
+        if (i < n) pre = op.load(i);
+        TM x[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            if (q < wd) x[q] = op.gather(direct_col(c[q], i));
+        const int gn = g + nw;
+        TM sum = 0;
+        if constexpr (!WIDE) {
+            TM an[U];
+            IDX cn[U];
+            int s0n = 0, wdn = 0;
+            if (gn < nsl) fetch(gn, an, cn, s0n, wdn);
+#pragma unroll
+            for (int q = 0; q < U; ++q)
+                if (q < wd) sum += a[q] * x[q];
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                a[q] = an[q];
+                c[q] = cn[q];
+            }
+            s0 = s0n;
+            wd = wdn;
+        } else {
+#pragma unroll
+            for (int q = 0; q < U; ++q)
+                if (q < wd) sum += a[q] * x[q];
+            // slots beyond the first U: U at a time, loads first
+            for (int u = U; u < wd; u += U) {
+#pragma unroll
+                for (int q = 0; q < U; ++q)
+                    if (u + q < wd) {
+                        a[q] = __ldg(ev + s0 + (u + q) * 32 + lane);
+                        c[q] = __ldg(ecol + s0 + (u + q) * 32 + lane);
+                    }
+#pragma unroll
+                for (int q = 0; q < U; ++q)
+                    if (u + q < wd) x[q] = op.gather(direct_col(c[q], i));
+#pragma unroll
+                for (int q = 0; q < U; ++q)
+                    if (u + q < wd) sum += a[q] * x[q];
+            }
+            if (gn < nsl) fetch(gn, a, c, s0, wd);
+        }
+        if (i < n) op.finish(i, sum, pre, acc);
+        g = gn;
     }
     op.template reduce<NT>(acc);
 }

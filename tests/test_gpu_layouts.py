@@ -1,5 +1,6 @@
 """GPU parity of each streaming tile layout (amg_config.layout) on its own:
-CSR row tiles, windowed CSR tiles and sliced-ELL tiles, each pinned by the
+CSR row tiles, windowed CSR tiles, sliced-ELL tiles and the direct
+sliced-ELL layout (no staging), each pinned by the
 layout option and checked against the FP64 oracle through the V-cycle, the
 solve, the adjoint and a numeric re-setup.  Matrices have at least 16384
 rows (the streaming kernels' threshold) and ragged last tiles and slices."""
@@ -13,7 +14,7 @@ from paper_2606_09001_b300 import api, matrices as M
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda"
-LAYOUTS = ["CSR", "WINDOWED", "SLICED_ELL"]
+LAYOUTS = ["CSR", "WINDOWED", "SLICED_ELL", "ELL_DIRECT"]
 
 CASES = {
     # n = 35937 = 32 * 1123 + 1: one row in the last slice
@@ -44,7 +45,7 @@ def check_layout(s, layout):
             p = s.plan(l, op)
             if p["rows_per_tile"] > 0 and (l == 0 and op in ("pre", "post", "krylov")):
                 assert p["layout"] == layout, (l, op, p)
-            if p["layout"] == "SLICED_ELL":
+            if p["layout"] in ("SLICED_ELL", "ELL_DIRECT"):
                 assert p["rows_per_tile"] % 32 == 0 and p["threads_per_row"] == 1
 
 
