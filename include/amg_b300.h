@@ -330,6 +330,16 @@ int amg_cg_solve_noalloc(int n, long long nnz, const int *row_ptr, const int *co
                          const double *b, double *x, double rtol, int max_iter, void *cuda_stream,
                          amg_info *info);
 
+/* Average duration (microseconds) of one launch of the finest level's Krylov
+ * product -- q = A p with p.q and alpha for PCG, v = A p^ with r^.v for
+ * BiCGStab -- over reps back-to-back launches
+ * on the handle's stream, chained as in a solve, on the vectors the last
+ * solve left (call it after a solve).  Synchronous; leaves the handle ready
+ * for the next solve.  Errors: AMG_ERR_ARG (NULL, reps < 1, a finisher that
+ * stops on the current vectors), AMG_ERR_UNSUPPORTED (batched handles),
+ * AMG_ERR_CUDA. */
+int amg_profile_product(amg_handle h, int reps, double *us_per_launch);
+
 /* Test hook for the bounded device waits.  The paper has no counterpart: it
  * exists so that tests can run a wait into its limit without faulting or
  * hanging the GPU.  Arms a one-shot control in h's device state that the next

@@ -27,7 +27,7 @@ AMG_TYPES = {"AGGREGATION": 0, "CLASSICAL": 1}
 
 # Every symbol the header declares.
 EXPORTS = ("amg_config_default", "amg_setup", "amg_resetup", "amg_solve", "amg_adjoint", "amg_vcycle", "amg_get_info",
-           "amg_get_level", "amg_get_aggregates", "amg_get_plan", "amg_profile", "amg_profile_summary", "amg_profile_record",
+           "amg_get_level", "amg_get_aggregates", "amg_get_plan", "amg_profile", "amg_profile_summary", "amg_profile_record", "amg_profile_product",
            "amg_setup_batched", "amg_solve_batched", "amg_batch_level", "amg_cg_solve_noalloc", "amg_test_arm_wait_timeout", "amg_narrow_f64", "amg_widen_f32", "amg_free", "amg_status_string", "amg_last_error")
 
 
@@ -82,6 +82,7 @@ def load() -> C.CDLL:
         L.amg_batch_level.argtypes = [vp, i, C.POINTER(i), vp, vp, vp]
         L.amg_cg_solve_noalloc.argtypes = [i, ll, vp, vp, vp, vp, vp, C.c_double, i, vp, C.POINTER(AmgInfo)]
         L.amg_test_arm_wait_timeout.argtypes = [vp, i]
+        L.amg_profile_product.argtypes = [vp, i, C.POINTER(d)]
         L.amg_free.argtypes = [vp]
         L.amg_status_string.argtypes = [i]
         L.amg_status_string.restype = C.c_char_p
@@ -90,7 +91,6 @@ def load() -> C.CDLL:
         for name in EXPORTS:
             if name not in ("amg_status_string", "amg_last_error"):
                 getattr(L, name).restype = C.c_int
-        del d
         _lib = L
         return L
 

@@ -218,6 +218,15 @@ class Solver:
         if rc < 0:
             raise AMGError(rc, "amg_profile")
 
+    def profile_product(self, reps: int = 50) -> float:
+        """Microseconds per launch of the finest level's Krylov product over
+        reps back-to-back launches (call after a solve)."""
+        us = C.c_double()
+        rc = self._L.amg_profile_product(self._h, reps, C.byref(us))
+        if rc < 0:
+            raise AMGError(rc, "amg_profile_product")
+        return us.value
+
     def profile_records(self):
         """(launches, [dict(name, level, launches, ms, bytes), ...]) since the last profile() call."""
         launches, nrec = C.c_longlong(), C.c_int()

@@ -556,6 +556,12 @@ int amg_batch_level(amg_handle h, int level, int *nsys_level, int *sys, int *row
     return AMG_OK;
 }
 
+int amg_profile_product(amg_handle h, int reps, double *us_per_launch) {
+    if (!h || reps < 1 || !us_per_launch) return AMG_ERR_ARG;
+    AMG_TRY(single_only(h, "amg_profile_product"));
+    return time_product(&h->H, h->W, reps, h->s, us_per_launch);
+}
+
 int amg_test_arm_wait_timeout(amg_handle h, int kind) {
     if (!h || kind < 0 || kind > AMG_TEST_WITHHOLD_BARRIER) {
         set_last_error("amg_test_arm_wait_timeout: invalid handle or kind %d", kind);

@@ -2883,6 +2883,45 @@ int vcycle_apply(Hierarchy *h, Workspace &W, const double *r, double *z, cudaStr
     return vcycle(h, W, r, z, FIN_NONE, s);
 }
 
+// Average duration of the finest level's Krylov product with its finisher
+// (PCG: q = A p, p.q, alpha; BiCGStab: v = A p, r^.v) over `reps`
+// back-to-back launches on the handle's stream after two, on the workspace's
+// current vectors (the last solve's).  Launches are chained exactly as in a
+// solve (programmatic dependent launch), so the figure is the kernel's
+// steady-state duration without the per-launch events of a trace.  The
+// scalars' control fields are reset before and after.
+int time_product(Hierarchy *h, Workspace &W, int reps, cudaStream_t s, double *us) {
+    const bool bicg = h->cfg.solver == AMG_SOLVER_BICGSTAB || h->cfg.solver == AMG_SOLVER_BICGSTAB_NOPREC;
+    auto one = [&]() -> int {
+        if (bicg) return spmv_fin<SF_BICG_ALPHA>(h, W, "spmv_rv", W.p, W.v, W.rh, s);
+        return spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s);
+    };
+    AMG_TRY(set_control(W, s, 0, AMG_OK, 0, h->cfg.max_iter, 1));
+    for (int k = 0; k < 2; ++k) AMG_TRY(one());
+    cudaEvent_t e0, e1;
+    AMG_CUDA_TRY(cudaEventCreate(&e0));
+    AMG_CUDA_TRY(cudaEventCreate(&e1));
+    int rc = AMG_OK;
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < reps && rc >= 0; ++k) rc = one();
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (rc >= 0 && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    AMG_TRY(rc);
+    AMG_TRY(read_scalars(W, s));
+    const int stopped = W.scal_h->done;
+    AMG_TRY(set_control(W, s, 1, AMG_OK, 0, h->cfg.max_iter, 1));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (stopped) {
+        set_last_error("product timing: the finisher stopped on the current vectors (run a solve first)");
+        return AMG_ERR_ARG;
+    }
+    *us = 1e3 * (double)ms / std::max(1, reps);
+    return AMG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Autotuner: plan family by timed trial of whole cycles
 // ---------------------------------------------------------------------------

@@ -79,6 +79,9 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res);
 // Arms the one-shot test control of the bounded waits (AMG_TEST_WITHHOLD_*; 0 disarms).
 int test_arm_wait_timeout(Workspace &W, int kind, cudaStream_t s);
 
+// Average duration (us) of the finest Krylov product over reps back-to-back launches.
+int time_product(Hierarchy *h, Workspace &W, int reps, cudaStream_t s, double *us);
+
 // z = M^-1 r with one V-cycle of h (r, z: device vectors of length n).
 int vcycle_apply(Hierarchy *h, Workspace &W, const double *r, double *z, cudaStream_t s);
 

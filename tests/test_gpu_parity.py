@@ -405,3 +405,21 @@ def test_bicgstab_second_breakdown_status():
     assert io.status == O.BREAKDOWN and info.status == _lib.AMG_BREAKDOWN
     assert info.iters == io.iters == 2
     assert not x.cpu().numpy().any()
+
+
+def test_profile_product_leaves_the_handle_ready():
+    """amg_profile_product times the Krylov product on the last solve's
+    vectors and leaves the handle as it found it: the next solve gives the
+    same bits."""
+    A = M.diffusion3d_grf(N=33).A
+    b = dev(np.random.default_rng(4).uniform(-1, 1, A.n))
+    for cfg in ({}, {"precision": "MIXED"}):
+        s = gpu_solver(A, cfg)
+        x1, i1 = s.solve(b)
+        us = s.profile_product(5)
+        assert 0.0 < us < 1e4
+        x2, i2 = s.solve(b)
+        assert torch.equal(x1, x2) and i1.iters == i2.iters
+    s = gpu_solver(M.convdiff3d_upwind(N=14).A, {"solver": "BICGSTAB"})
+    s.solve(dev(np.ones(14 ** 3)))
+    assert s.profile_product(3) > 0.0
