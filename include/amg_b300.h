@@ -345,8 +345,9 @@ int amg_profile_product(amg_handle h, int reps, double *us_per_launch);
  * hanging the GPU.  Arms a one-shot control in h's device state that the next
  * solve-phase launch doing work consumes:
  *   AMG_TEST_WITHHOLD_COPY: CTA 0 of the next bulk-copy streaming pass
- *     expects 16 bytes that no copy delivers, so its first pipeline stage
- *     never completes; its waits give up after 2^12 polls;
+ *     (CSR, windowed or sliced-ELL tiles; the direct layout waits on
+ *     nothing) expects 16 bytes that no copy delivers, so its first
+ *     pipeline stage never completes; its waits give up after 2^12 polls;
  *   AMG_TEST_WITHHOLD_BARRIER: the last CTA of the next cooperative coarse
  *     launch (fuse_coarse = 2) skips its grid-barrier arrivals; the others'
  *     first waits give up after 2^20 SM clocks;

@@ -120,6 +120,7 @@ struct DevScalars {
     int flexible;     // PCG uses the Polak-Ribiere beta (mixed-precision V-cycle)
     int max_iter;
     int first;        // PCG: the next beta starts a new recursion (beta = 0)
+    int trips;        // passes of the device-side iteration loop since the solve began
     int copy_timeout; // a bounded wait gave up: 1 a bulk-copy wait, 2 a grid-barrier wait
     int test_ctl;     // one-shot test control read with copy_timeout (amg_test_arm_wait_timeout); 0 normally
 };
@@ -251,6 +252,14 @@ struct Hierarchy {
     int iter_kind = -1;
     int iter_count = 0;
     int iter_kernels = 0;
+    // The device-side Krylov loop: a graph whose conditional WHILE node repeats
+    // loop_count iterations until the device scalars say the solve is done;
+    // loop_kind: which iteration it holds (-1: none built; -2: conditional
+    // graphs unavailable, the host-polled graph is used).
+    cudaGraph_t loop_graph = nullptr;
+    cudaGraphExec_t loop_exec = nullptr;
+    int loop_kind = -1;
+    int loop_kernels = 0;
     DevArena arena;
     double setup_ms = 0.0;
     // the autotuner's timed rounds (ms) of the tile-layout family and the

@@ -2514,6 +2514,10 @@ void free_hierarchy(Hierarchy *h) {
     if (!h) return;
     if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
     h->iter_exec = nullptr;
+    if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
+    if (h->loop_graph) cudaGraphDestroy(h->loop_graph);
+    h->loop_exec = nullptr;
+    h->loop_graph = nullptr;
     h->arena.free_all();
 }
 

@@ -687,9 +687,20 @@ __global__ void k_set_control(DevScalars *sc, int done, int status, int flexible
     sc->max_iter = max_iter;
     if (reset_iters) {
         sc->iters = 0;
+        sc->trips = 0;
         sc->copy_timeout = 0;
         gbar[0] = 0;
     }
+}
+
+// The condition of the device-side Krylov loop, after each pass of its body:
+// repeat while the solve is running and fewer than cap passes have run (the
+// device sets done at max_iter at the latest; cap only bounds the loop).
+__global__ void k_loop_cond(cudaGraphConditionalHandle hd, DevScalars *sc, int cap) {
+    pdl_wait();
+    pdl_trigger();
+    const int t = ++sc->trips;
+    cudaGraphSetConditional(hd, (sc->done == 0 && t < cap) ? 1u : 0u);
 }
 
 // The next preconditioner application starts a new recursion (beta = 0, p = z).
@@ -2741,6 +2752,65 @@ static int run_iterations(Hierarchy *h, Workspace &W, int kind, int count, cudaS
     return AMG_OK;
 }
 
+// Iterations in one pass of the device-side loop's body.  A pass ends in a
+// one-thread condition kernel; after convergence the rest of a pass's
+// kernels return at once, so two iterations a pass trade that overshoot
+// against the condition launches.
+constexpr int LOOP_ITERS = 2;
+
+// The device-side loop for iteration kind `kind`: a graph holding one
+// conditional WHILE node whose body -- LOOP_ITERS iterations and the
+// condition kernel -- the GPU repeats until the solve is done, so a solve
+// launches it once and synchronises once.  Built on first use per kind;
+// returns false (and marks the hierarchy) where conditional nodes cannot be
+// built, the host-polled graph then being used.
+static bool build_loop(Hierarchy *h, Workspace &W, int kind, int cap, cudaStream_t s) {
+    if (h->loop_kind == kind && h->loop_exec) return true;
+    if (h->loop_kind == -2) return false;
+    if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
+    if (h->loop_graph) cudaGraphDestroy(h->loop_graph);
+    h->loop_exec = nullptr;
+    h->loop_graph = nullptr;
+    h->loop_kind = -2;
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    auto fail = [&]() {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return false;
+    };
+    cudaGraphConditionalHandle hd;
+    if (cudaGraphConditionalHandleCreate(&hd, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) return fail();
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hd;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) return fail();
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail();
+    const long long before = W.prof.launches;
+    int rc = AMG_OK;
+    for (int k = 0; k < LOOP_ITERS && rc >= 0; ++k) rc = iterate(h, W, kind, s);
+    if (rc >= 0) rc = launch_k(k_loop_cond, 1, 1, 0, s, hd, W.scal, cap);
+    cudaGraph_t got = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &got);
+    if (rc < 0 || ce != cudaSuccess) return fail();
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) return fail();
+    h->loop_graph = g;
+    h->loop_exec = ex;
+    h->loop_kind = kind;
+    h->loop_kernels = (int)(W.prof.launches - before) + 1;  // and the condition kernel
+    W.prof.launches = before;
+    return true;
+}
+
 static int read_scalars(Workspace &W, cudaStream_t s) {
     AMG_CUDA_TRY(cudaMemcpyAsync(W.scal_h, W.scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -2801,15 +2871,29 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
         return AMG_OK;
     }
     const int chunk = 4;
+    const int kind = bicg ? (precond ? 3 : 2) : (precond ? 1 : 0);
     long long launched = 0;
     const long long launch_cap = (long long)c.max_iter * (c.max_restarts + 2) + 4 * chunk;
+    const int trip_cap = (int)std::min<long long>(INT_MAX - 1, launch_cap / LOOP_ITERS + 2);
+    // the device-side loop, where conditional graphs build (not while tracing)
+    const bool device_loop = !W.prof.on && build_loop(h, W, kind, trip_cap, s);
+    int trips_seen = 0;
     while (status == AMG_OK) {
         // iterate until the device marks the solve done; the device sets done
         // at max_iter at the latest, launch_cap only guards the host loop
         for (;;) {
-            AMG_TRY(run_iterations(h, W, bicg ? (precond ? 3 : 2) : (precond ? 1 : 0), chunk, s));
-            launched += chunk;
-            AMG_TRY(read_scalars(W, s));
+            if (device_loop) {
+                AMG_CUDA_TRY(cudaGraphLaunch(h->loop_exec, s));
+                launched += launch_cap / 2 + 1;  // one launch runs the loop to its end
+                AMG_TRY(read_scalars(W, s));
+                // kernels launched: the body's (with its condition kernel) per pass
+                W.prof.launches += (long long)h->loop_kernels * std::max(0, W.scal_h->trips - trips_seen);
+                trips_seen = W.scal_h->trips;
+            } else {
+                AMG_TRY(run_iterations(h, W, kind, chunk, s));
+                launched += chunk;
+                AMG_TRY(read_scalars(W, s));
+            }
             if (W.scal_h->done) break;
             if (launched > launch_cap) {
                 set_last_error("solver loop exceeded %lld iterations without finishing", launch_cap);

@@ -60,7 +60,9 @@ def run_timeout_then_clean(A, cfg, kind, what):
 @pytest.mark.parametrize("precision", ["FP64", "MIXED"])
 def test_bulk_copy_wait_runs_out_then_next_solve_is_clean(precision):
     A = M.diffusion3d_grf(N=33).A  # 35,937 rows: the finest level's passes stream
-    s, b, x0 = run_timeout_then_clean(A, {"precision": precision}, _lib.AMG_TEST_WITHHOLD_COPY, "bulk-copy")
+    # sliced-ELL tiles: a bulk-copy ring (the direct layout has no waits)
+    cfg = {"precision": precision, "layout": "SLICED_ELL"}
+    s, b, x0 = run_timeout_then_clean(A, cfg, _lib.AMG_TEST_WITHHOLD_COPY, "bulk-copy")
     xt, _ = O.Hierarchy(A, {"rtol": 1e-13}).solve(b)
     assert np.linalg.norm(x0 - xt) <= 1e-7 * np.linalg.norm(xt)
     s.close()
