@@ -373,6 +373,59 @@ __device__ __forceinline__ float f64_to_f32_rn(double d) {
     return __uint_as_float(sign | (unsigned)(q + up));
 }
 
+// ---------------------------------------------------------------------------
+// Double-FP32 numbers for the batched FP64 product
+// ---------------------------------------------------------------------------
+//
+// On this GPU an FP64 FMA issues at under two per clock per SM, against 128
+// FP32 FMAs.  The batched solve's finest product q = A p does eight FMAs per
+// stored entry (one per right-hand side) and is bound by the FP64 pipe; it
+// runs in double-length FP32 arithmetic instead (Dekker 1971; Shewchuk 1997):
+// A's values and p are split once into an unevaluated sum hi + lo of two
+// binary32 numbers, hi = RN32(d), lo = RN32(d - hi), so hi + lo equals d to
+// within 2^-48 |d|; a product keeps the exact remainder of hi * hi (one FMA)
+// and the two cross terms, and a row sum adds the hi parts with an exact
+// two-sum and the remainders in FP32.  Each q_i is accurate to a few 2^-48 of
+// sum_j |a_ij p_j| (FP64: 2^-53); dot products, norms and vector updates stay
+// FP64.  (The single-system product is not FP64-bound -- one FMA per entry --
+// and stays FP64.)
+struct DF {
+    float hi, lo;
+    DF() = default;
+    __host__ __device__ constexpr DF(int z) : hi((float)z), lo(0.f) {}
+    __host__ __device__ constexpr DF(float h, float l) : hi(h), lo(l) {}
+};
+static_assert(sizeof(DF) == 8, "a DF is two packed binary32 numbers");
+
+// d as hi + lo (hi = RN32(d), lo = RN32(d - hi); the difference is exact in FP64)
+__device__ __forceinline__ DF df_split(double d) {
+    const float h = f64_to_f32_rn(d);
+    return DF(h, f64_to_f32_rn(d - f32_to_f64(h)));
+}
+
+// hi + lo in FP64 (both widenings exact; one rounding in the add)
+__device__ __forceinline__ double df_value(DF a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
+
+// a * x as (t, e): t = RN32(a.hi x.hi), e its exact remainder plus the cross
+// terms a.hi x.lo + a.lo x.hi (the a.lo x.lo term, below 2^-48 |a x|, is dropped)
+__device__ __forceinline__ DF operator*(DF a, DF x) {
+    const float t = __fmul_rn(a.hi, x.hi);
+    float e = __fmaf_rn(a.hi, x.hi, -t);
+    e = __fmaf_rn(a.hi, x.lo, e);
+    e = __fmaf_rn(a.lo, x.hi, e);
+    return DF(t, e);
+}
+
+// s += p: the hi parts by an exact two-sum (Knuth), remainders added in FP32
+__device__ __forceinline__ DF &operator+=(DF &s, DF p) {
+    const float u = __fadd_rn(s.hi, p.hi);
+    const float v = __fsub_rn(u, s.hi);
+    const float w = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(u, v)), __fsub_rn(p.hi, v));
+    s.lo = __fadd_rn(s.lo, __fadd_rn(w, p.lo));
+    s.hi = u;
+    return s;
+}
+
 // Value conversion between the library's floating types, FP32 <-> FP64 on
 // the integer pipes.
 template <typename To, typename From>

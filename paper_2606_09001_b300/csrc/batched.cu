@@ -8,7 +8,11 @@
 // (system, right-hand side) pair carries its own Krylov scalars and stops on
 // its own (a per-pair convergence mask).  The V-cycle runs in FP32 or FP64
 // (the handle's precision); the Krylov vectors, dot products and the
-// coarsest solves are FP64.
+// coarsest solves are FP64.  In the mixed form the finest product q = A p,
+// which does eight FMAs per stored entry and would be bound by the FP64 pipe,
+// runs in double-FP32 arithmetic (A's values and p split into FP32 pairs; see
+// DF), and the flexible beta takes z.(r - r_old) as -alpha z.q with the
+// previous iteration's alpha and q, so no copy of r_old is kept.
 //
 // Finest-level row passes run over "chunks" (at most CH consecutive rows of
 // one system) so that dot products reduce per system deterministically: each
@@ -36,9 +40,13 @@ struct BDev {
     unsigned *ticket = nullptr;   // per system
     double *part = nullptr;       // [chunk][K][2]
     // outer vectors [n][K], FP64
-    double *B = nullptr, *X = nullptr, *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr, *Rold = nullptr;
+    double *B = nullptr, *X = nullptr, *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr;
     // FP32 copy of R for the mixed V-cycle's finest level (null in the FP64 form)
     float *R32 = nullptr;
+    // mixed form: P split into FP32 pairs [n][K] and the finest operator's
+    // values split likewise (the double-FP32 product); null in the FP64 form
+    DF *P2 = nullptr;
+    const DF *adf = nullptr;
     // per pair (system * K + rhs)
     double *bn2 = nullptr, *tol2 = nullptr, *rz = nullptr, *alpha = nullptr, *beta = nullptr, *rr = nullptr,
            *tr = nullptr;
@@ -214,7 +222,7 @@ __global__ void __launch_bounds__(BT) kb_post0(BDev W, const int *rp, const int 
             o = W.Z[e];
         }
         acc[0] += W.R[e] * o;
-        if (flexible) acc[1] += W.Rold[e] * o;
+        if (flexible) acc[1] += W.Q[e] * o;  // q = A p of the previous iteration: r - r_old = -alpha q
     }
     double tot[2];
     if (chunk_reduce<2>(acc, chunk, sys, W, tot) && threadIdx.x < K) {
@@ -223,7 +231,7 @@ __global__ void __launch_bounds__(BT) kb_post0(BDev W, const int *rp, const int 
             if (!isfinite(tot[0])) {
                 deactivate(W, p, AMG_NAN);
             } else {
-                W.beta[p] = W.first[p] ? 0.0 : (flexible ? tot[0] - tot[1] : tot[0]) / W.rz[p];
+                W.beta[p] = W.first[p] ? 0.0 : (flexible ? -W.alpha[p] * tot[1] : tot[0]) / W.rz[p];
                 W.first[p] = 0;
                 W.rz[p] = tot[0];
             }
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(BT) kb_post0(BDev W, const int *rp, const int 
     }
 }
 
-// p = z + beta p (active pairs)
+// p = z + beta p (active pairs), and its FP32 pairs in the mixed form
 __global__ void __launch_bounds__(BT) kb_p(BDev W) {
     const int chunk = blockIdx.x, sys = W.ch_sys[chunk], r0 = W.ch_r0[chunk], rows = W.ch_rows[chunk];
     const int r = threadIdx.x % K, p = sys * K + r;
@@ -239,8 +247,35 @@ __global__ void __launch_bounds__(BT) kb_p(BDev W) {
     const double beta = W.beta[p];
     for (int il = threadIdx.x / K; il < rows; il += BT / K) {
         const size_t e = (size_t)(r0 + il) * K + r;
-        W.P[e] = beta == 0.0 ? W.Z[e] : W.Z[e] + beta * W.P[e];
+        const double pe = beta == 0.0 ? W.Z[e] : W.Z[e] + beta * W.P[e];
+        W.P[e] = pe;
+        if (W.P2) W.P2[e] = df_split(pe);
     }
+}
+
+// one row's q = sum_k a_k p_{col(k)} for right-hand side r in double-FP32
+// (four terms' loads before their products; the sum in CSR order)
+__device__ __forceinline__ DF spmm_row_df(const int *__restrict__ rp, const int *__restrict__ ci,
+                                          const DF *__restrict__ v, const DF *__restrict__ x, int i, int r) {
+    DF s(0);
+    const int e = rp[i + 1];
+    int k = rp[i];
+    const float2 *v2 = reinterpret_cast<const float2 *>(v), *x2 = reinterpret_cast<const float2 *>(x);
+    for (; k + 3 < e; k += 4) {
+        const int j0 = ci[k], j1 = ci[k + 1], j2 = ci[k + 2], j3 = ci[k + 3];
+        const float2 a0 = v2[k], a1 = v2[k + 1], a2 = v2[k + 2], a3 = v2[k + 3];
+        const float2 x0 = x2[(size_t)j0 * K + r], x1 = x2[(size_t)j1 * K + r];
+        const float2 x2_ = x2[(size_t)j2 * K + r], x3 = x2[(size_t)j3 * K + r];
+        s += DF(a0.x, a0.y) * DF(x0.x, x0.y);
+        s += DF(a1.x, a1.y) * DF(x1.x, x1.y);
+        s += DF(a2.x, a2.y) * DF(x2_.x, x2_.y);
+        s += DF(a3.x, a3.y) * DF(x3.x, x3.y);
+    }
+    for (; k < e; ++k) {
+        const float2 a = v2[k], xv = x2[(size_t)ci[k] * K + r];
+        s += DF(a.x, a.y) * DF(xv.x, xv.y);
+    }
+    return s;
 }
 
 // q = A p, p.q per pair -> alpha; or (TRUE_RES) r = b - A x, ||r||^2 per pair
@@ -258,6 +293,10 @@ __global__ void __launch_bounds__(BT) kb_spmv0(BDev W, const int *rp, const int 
             W.R[e] = ri;
             if (W.R32) W.R32[e] = f64_to_f32_rn(ri);
             acc[0] += ri * ri;
+        } else if (W.adf) {  // mixed form: double-FP32 product on p's FP32 pairs
+            const double q = df_value(spmm_row_df(rp, ci, W.adf, W.P2, i, r));
+            W.Q[e] = q;
+            acc[0] += df_value(W.P2[e]) * q;
         } else {
             const double q = spmm_row<double, double>(rp, ci, av, W.P, i, r);
             W.Q[e] = q;
@@ -277,8 +316,8 @@ __global__ void __launch_bounds__(BT) kb_spmv0(BDev W, const int *rp, const int 
     }
 }
 
-// x += alpha p, r_old = r, r -= alpha q (active pairs), ||r||^2 -> convergence
-__global__ void __launch_bounds__(BT) kb_update(BDev W, int max_iter, int flexible) {
+// x += alpha p, r -= alpha q (active pairs), ||r||^2 -> convergence
+__global__ void __launch_bounds__(BT) kb_update(BDev W, int max_iter) {
     const int chunk = blockIdx.x, sys = W.ch_sys[chunk], r0 = W.ch_r0[chunk], rows = W.ch_rows[chunk];
     if (W.sys_nact[sys] == 0) return;
     const int r = threadIdx.x % K, p = sys * K + r;
@@ -289,9 +328,7 @@ __global__ void __launch_bounds__(BT) kb_update(BDev W, int max_iter, int flexib
         const size_t e = (size_t)(r0 + il) * K + r;
         if (a) {
             W.X[e] += alpha * W.P[e];
-            const double ri = W.R[e];
-            if (flexible) W.Rold[e] = ri;
-            const double rn = ri - alpha * W.Q[e];
+            const double rn = W.R[e] - alpha * W.Q[e];
             W.R[e] = rn;
             if (W.R32) W.R32[e] = f64_to_f32_rn(rn);
             acc[0] += rn * rn;
@@ -310,7 +347,7 @@ __global__ void __launch_bounds__(BT) kb_update(BDev W, int max_iter, int flexib
     }
 }
 
-// x = 0, r = b, p = r_old = 0; ||b||^2 per pair; pairs with b = 0 are done at once.
+// x = 0, r = b, p = q = 0; ||b||^2 per pair; pairs with b = 0 are done at once.
 __global__ void __launch_bounds__(BT) kb_init(BDev W, double rtol) {
     const int chunk = blockIdx.x, sys = W.ch_sys[chunk], r0 = W.ch_r0[chunk], rows = W.ch_rows[chunk];
     const int r = threadIdx.x % K;
@@ -322,7 +359,7 @@ __global__ void __launch_bounds__(BT) kb_init(BDev W, double rtol) {
         W.R[e] = bi;
         if (W.R32) W.R32[e] = f64_to_f32_rn(bi);
         W.P[e] = 0.0;
-        W.Rold[e] = 0.0;
+        W.Q[e] = 0.0;  // the flexible beta's first z.q (unused: beta = 0) reads finite values
         W.Z[e] = 0.0;
         acc[0] += bi * bi;
     }
@@ -362,6 +399,11 @@ __global__ void kb_restart(BDev W, int max_iter) {
 // Host side
 // ---------------------------------------------------------------------------
 
+__global__ void k_split_df(long long n, const double *__restrict__ in, DF *out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = df_split(in[i]);
+}
+
 static int workspace_build(Hierarchy *h, BatchWorkspace &W) {
     DevArena &a = W.arena;
     BDev &d = W.d;
@@ -395,9 +437,18 @@ static int workspace_build(Hierarchy *h, BatchWorkspace &W) {
     AMG_CUDA_TRY(cudaMemcpy(d.sys_nch, sys_nch.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
     AMG_CUDA_TRY(cudaMemset(d.ticket, 0, sizeof(unsigned) * ns));
     const size_t nk = (size_t)n * K;
-    double **vecs[] = {&d.B, &d.X, &d.R, &d.Z, &d.P, &d.Q, &d.Rold};
+    double **vecs[] = {&d.B, &d.X, &d.R, &d.Z, &d.P, &d.Q};
     for (double **v : vecs) AMG_TRY(a.alloc(v, nk));
-    if (h->cfg.precision == AMG_PRECISION_MIXED) AMG_TRY(a.alloc(&d.R32, nk));
+    if (h->cfg.precision == AMG_PRECISION_MIXED) {
+        AMG_TRY(a.alloc(&d.R32, nk));
+        AMG_TRY(a.alloc(&d.P2, nk));
+        const DevCSR &A0 = h->L[0].A;
+        DF *adf = nullptr;
+        AMG_TRY(a.alloc(&adf, (size_t)std::max(1LL, A0.nnz)));
+        k_split_df<<<std::max(1, std::min((int)((A0.nnz + 255) / 256), 16 * num_sms())), 256>>>(A0.nnz, A0.v, adf);
+        AMG_LAUNCH_CHECK();
+        d.adf = adf;
+    }
     double **pv[] = {&d.bn2, &d.tol2, &d.rz, &d.alpha, &d.beta, &d.rr, &d.tr};
     for (double **v : pv) AMG_TRY(a.alloc(v, (size_t)d.npairs));
     int **pi[] = {&d.act, &d.first, &d.iters, &d.status};
@@ -537,7 +588,7 @@ static int batch_iteration(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cuda
     const BDev &d = W.d;
     const double nk = (double)d.n * K;
     {
-        ProfScope ps(&prof, s, "b_p", 0, 24.0 * nk);
+        ProfScope ps(&prof, s, "b_p", 0, (mixed ? 32.0 : 24.0) * nk);
         kb_p<<<d.nchunks, BT, 0, s>>>(d);
     }
     {
@@ -545,8 +596,8 @@ static int batch_iteration(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cuda
         kb_spmv0<false><<<d.nchunks, BT, 0, s>>>(d, l0.A.rp, l0.A.ci, l0.A.v);
     }
     {
-        ProfScope ps(&prof, s, "b_update", 0, (mixed ? 64.0 : 56.0) * nk);
-        kb_update<<<d.nchunks, BT, 0, s>>>(d, h->cfg.max_iter, mixed ? 1 : 0);
+        ProfScope ps(&prof, s, "b_update", 0, (mixed ? 52.0 : 48.0) * nk);
+        kb_update<<<d.nchunks, BT, 0, s>>>(d, h->cfg.max_iter);
     }
     AMG_LAUNCH_CHECK();
     return AMG_OK;
