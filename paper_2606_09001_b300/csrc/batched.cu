@@ -67,6 +67,10 @@ struct amg_batch_ws {
     void *lb[AMG_MAX_LEVELS] = {}, *lt[AMG_MAX_LEVELS] = {}, *lx[AMG_MAX_LEVELS] = {};
     cudaGraphExec_t iter_exec = nullptr;
     int iter_kernels = 0;
+    int g = 1;                     // right-hand sides per thread of the V-cycle's row passes (timed trial)
+    int gp = 1;                    // and of the finest Krylov product
+    float g_ms[4] = {0, 0, 0, 0};  // the trials' V-cycle times for G = 1, 2, 4, 8
+    float gp_ms[4] = {0, 0, 0, 0}; // and product times
     amg::DevArena arena;
 };
 
@@ -95,51 +99,190 @@ __device__ __forceinline__ TA spmm_row(const int *__restrict__ rp, const int *__
     return s;
 }
 
-#define ROWS_K(n)                                                                                   \
-    for (long long e_ = (long long)blockIdx.x * BT + threadIdx.x; e_ < (long long)(n) * K;         \
-         e_ += (long long)gridDim.x * BT) {                                                        \
-        const int i = (int)(e_ / K), r = (int)(e_ % K);
+// The V-cycle's row passes give each thread G consecutive right-hand sides
+// of one row (8 / G threads per row, BT * G / 8 rows per block; G chosen per
+// handle by timed trial): the row's indices and values load once for the G
+// columns, and the G gathered entries of a column with 16-byte loads.
+template <int G, typename T>
+__device__ __forceinline__ void ld_g(const T *__restrict__ p, T (&v)[G]) {
+    if constexpr (G * sizeof(T) >= 16) {
+        using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        constexpr int PER = 16 / sizeof(T);
+#pragma unroll
+        for (int q = 0; q < G / PER; ++q) {
+            const V w = __ldg(reinterpret_cast<const V *>(p) + q);
+            const T *u = reinterpret_cast<const T *>(&w);
+#pragma unroll
+            for (int c = 0; c < PER; ++c) v[q * PER + c] = u[c];
+        }
+    } else if constexpr (G == 2 && sizeof(T) == 4) {
+        const float2 w = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = w.x;
+        v[1] = w.y;
+    } else if constexpr (std::is_same<T, DF>::value) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float2 w = __ldg(reinterpret_cast<const float2 *>(p) + g);
+            v[g] = DF(w.x, w.y);
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g) v[g] = __ldg(p + g);
+    }
+}
+
+template <int G, typename T>
+__device__ __forceinline__ void st_g(T *p, const T (&v)[G]) {
+    if constexpr (G * sizeof(T) >= 16) {
+        using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        constexpr int PER = 16 / sizeof(T);
+#pragma unroll
+        for (int q = 0; q < G / PER; ++q) {
+            V w;
+            T *u = reinterpret_cast<T *>(&w);
+#pragma unroll
+            for (int c = 0; c < PER; ++c) u[c] = v[q * PER + c];
+            reinterpret_cast<V *>(p)[q] = w;
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g) p[g] = v[g];
+    }
+}
+
+// s[g] = sum over the row's entries of a_k x[col(k)][r0 + g], in CSR order,
+// four terms at a time as spmm_row groups them
+template <int G, typename TA, typename TX>
+__device__ __forceinline__ void spmm_row_g(const int *__restrict__ rp, const int *__restrict__ ci,
+                                           const TA *__restrict__ v, const TX *__restrict__ x, int i, int r0,
+                                           TA (&s)[G]) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) s[g] = 0;
+    const int e = rp[i + 1];
+    int k = rp[i];
+    for (; k + 3 < e; k += 4) {
+        const int j0 = ci[k], j1 = ci[k + 1], j2 = ci[k + 2], j3 = ci[k + 3];
+        const TA a0 = v[k], a1 = v[k + 1], a2 = v[k + 2], a3 = v[k + 3];
+        TX x0[G], x1[G], x2[G], x3[G];
+        ld_g<G>(x + (size_t)j0 * K + r0, x0);
+        ld_g<G>(x + (size_t)j1 * K + r0, x1);
+        ld_g<G>(x + (size_t)j2 * K + r0, x2);
+        ld_g<G>(x + (size_t)j3 * K + r0, x3);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            s[g] += a0 * fcvt<TA>(x0[g]) + a1 * fcvt<TA>(x1[g]) + a2 * fcvt<TA>(x2[g]) + a3 * fcvt<TA>(x3[g]);
+    }
+    for (; k < e; ++k) {
+        const TA a = v[k];
+        TX xv[G];
+        ld_g<G>(x + (size_t)ci[k] * K + r0, xv);
+#pragma unroll
+        for (int g = 0; g < G; ++g) s[g] += a * fcvt<TA>(xv[g]);
+    }
+}
+
+// s[g] = sum over the row's entries of a_k x[col(k)][r0 + g] in double-FP32,
+// in CSR order (the values' and four columns' loads before their products)
+template <int G>
+__device__ __forceinline__ void spmm_row_df_g(const int *__restrict__ rp, const int *__restrict__ ci,
+                                              const DF *__restrict__ v, const DF *__restrict__ x, int i, int r0,
+                                              DF (&s)[G]) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) s[g] = DF(0);
+    const int e = rp[i + 1];
+    int k = rp[i];
+    const float2 *v2 = reinterpret_cast<const float2 *>(v);
+    for (; k + 3 < e; k += 4) {
+        const int j[4] = {ci[k], ci[k + 1], ci[k + 2], ci[k + 3]};
+        float2 a[4];
+        DF xv[4][G];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a[u] = v2[k + u];
+            ld_g<G>(x + (size_t)j[u] * K + r0, xv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int g = 0; g < G; ++g) s[g] += DF(a[u].x, a[u].y) * xv[u][g];
+    }
+    for (; k < e; ++k) {
+        const float2 a = v2[k];
+        DF xv[G];
+        ld_g<G>(x + (size_t)ci[k] * K + r0, xv);
+#pragma unroll
+        for (int g = 0; g < G; ++g) s[g] += DF(a.x, a.y) * xv[g];
+    }
+}
+
+#define ROWS_G(n)                                                                                      \
+    for (long long e_ = (long long)blockIdx.x * BT + threadIdx.x; e_ < (long long)(n) * (K / G);      \
+         e_ += (long long)gridDim.x * BT) {                                                           \
+        const int i = (int)(e_ / (K / G)), r0 = (int)(e_ % (K / G)) * G;                              \
+        const size_t e0 = (size_t)i * K + r0;
 
 // t = b - (A W) b
-template <typename TB, typename TM>
+template <int G, typename TB, typename TM>
 __global__ void __launch_bounds__(BT) kb_presmooth(int n, const int *rp, const int *ci, const TM *ahat,
                                                    const TB *b, TM *t, const int *nact) {
     if (*nact == 0) return;
-    ROWS_K(n)
-    t[(size_t)i * K + r] = fcvt<TM>(b[(size_t)i * K + r]) - spmm_row<TM, TB>(rp, ci, ahat, b, i, r);
+    ROWS_G(n)
+    TM s[G], o[G];
+    TB bv[G];
+    ld_g<G>(b + e0, bv);
+    spmm_row_g<G, TM, TB>(rp, ci, ahat, b, i, r0, s);
+#pragma unroll
+    for (int g = 0; g < G; ++g) o[g] = fcvt<TM>(bv[g]) - s[g];
+    st_g<G>(t + e0, o);
 }
 }
 
 // y = M x (restriction)
-template <typename TM>
+template <int G, typename TM>
 __global__ void __launch_bounds__(BT) kb_spmm(int n, const int *rp, const int *ci, const TM *v, const TM *x, TM *y,
                                               const int *nact) {
     if (*nact == 0) return;
-    ROWS_K(n)
-    y[(size_t)i * K + r] = spmm_row<TM, TM>(rp, ci, v, x, i, r);
+    ROWS_G(n)
+    TM s[G];
+    spmm_row_g<G, TM, TM>(rp, ci, v, x, i, r0, s);
+    st_g<G>(y + e0, s);
 }
 }
 
 // t = W b + P x_c
-template <typename TB, typename TM>
+template <int G, typename TB, typename TM>
 __global__ void __launch_bounds__(BT) kb_prolong(int n, const int *rp, const int *ci, const TM *pv, const TM *w,
                                                  const TB *b, const TM *xc, TM *t, const int *nact) {
     if (*nact == 0) return;
-    ROWS_K(n)
-    t[(size_t)i * K + r] = w[i] * fcvt<TM>(b[(size_t)i * K + r]) + spmm_row<TM, TM>(rp, ci, pv, xc, i, r);
+    ROWS_G(n)
+    TM s[G], o[G];
+    TB bv[G];
+    ld_g<G>(b + e0, bv);
+    spmm_row_g<G, TM, TM>(rp, ci, pv, xc, i, r0, s);
+    const TM wi = w[i];
+#pragma unroll
+    for (int g = 0; g < G; ++g) o[g] = wi * fcvt<TM>(bv[g]) + s[g];
+    st_g<G>(t + e0, o);
 }
 }
 
 // x = t + W (b - A t) on rows with w > 0 (rows with w = 0 belong to a dense solve)
-template <typename TB, typename TM, typename TO>
+template <int G, typename TB, typename TM, typename TO>
 __global__ void __launch_bounds__(BT) kb_postsmooth(int n, const int *rp, const int *ci, const TM *av, const TM *w,
                                                     const TB *b, const TM *t, TO *x, const int *nact) {
     if (*nact == 0) return;
-    ROWS_K(n)
+    ROWS_G(n)
     const TM wi = w[i];
     if (wi != (TM)0) {
-        const TM s = spmm_row<TM, TM>(rp, ci, av, t, i, r);
-        x[(size_t)i * K + r] = fcvt<TO>(t[(size_t)i * K + r] + wi * (fcvt<TM>(b[(size_t)i * K + r]) - s));
+        TM s[G], tv[G];
+        TB bv[G];
+        TO o[G];
+        ld_g<G>(b + e0, bv);
+        ld_g<G>(t + e0, tv);
+        spmm_row_g<G, TM, TM>(rp, ci, av, t, i, r0, s);
+#pragma unroll
+        for (int g = 0; g < G; ++g) o[g] = fcvt<TO>(tv[g] + wi * (fcvt<TM>(bv[g]) - s[g]));
+        st_g<G>(x + e0, o);
     }
 }
 }
@@ -200,32 +343,82 @@ __device__ __forceinline__ void deactivate(const BDev &W, int p, int status) {
     atomicSub(W.nact, 1);
 }
 
+// chunk_reduce for threads that hold G right-hand sides each (acc[q][g] for
+// right-hand side r0 + g): per right-hand side, the block's values are added
+// in row-slot order.
+template <int NV, int G>
+__device__ bool chunk_reduce_g(double (&acc)[NV][G], int chunk, int sys, const BDev &W, double (&tot)[NV]) {
+    constexpr int SLOTS = BT / (K / G);
+    __shared__ double sh[NV][K][SLOTS];
+    __shared__ bool s_last;
+    const int slot = threadIdx.x / (K / G), r0 = (threadIdx.x % (K / G)) * G;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+#pragma unroll
+        for (int g = 0; g < G; ++g) sh[q][r0 + g][slot] = acc[q][g];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        for (int q = 0; q < NV; ++q) {
+            double a = 0.0;
+            for (int t = 0; t < SLOTS; ++t) a += sh[q][threadIdx.x][t];
+            W.part[((size_t)chunk * K + threadIdx.x) * 2 + q] = a;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&W.ticket[sys], 1u) == (unsigned)W.sys_nch[sys] - 1;
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    if (threadIdx.x < K) {
+        const int c0 = W.sys_ch0[sys], nc = W.sys_nch[sys];
+        for (int q = 0; q < NV; ++q) {
+            double a = 0.0;
+            for (int c = c0; c < c0 + nc; ++c) a += __ldcg(&W.part[((size_t)c * K + threadIdx.x) * 2 + q]);
+            tot[q] = a;
+        }
+    }
+    if (threadIdx.x == 0) W.ticket[sys] = 0u;
+    return true;
+}
+
 // Finest level, chunked: z = t + W (b - A t) (rows with w = 0 keep the dense
-// solve's z), r.z and r_old.z per pair -> beta.
-template <typename TM>
+// solve's z), r.z and, flexible, z.q per pair -> beta.  G right-hand sides
+// per thread.
+template <int G, typename TM>
 __global__ void __launch_bounds__(BT) kb_post0(BDev W, const int *rp, const int *ci, const TM *av,
                                                const TM *w, const TM *t, int flexible) {
-    const int chunk = blockIdx.x, sys = W.ch_sys[chunk], r0 = W.ch_r0[chunk], rows = W.ch_rows[chunk];
+    const int chunk = blockIdx.x, sys = W.ch_sys[chunk], r0c = W.ch_r0[chunk], rows = W.ch_rows[chunk];
     if (W.sys_nact[sys] == 0) return;
-    const int r = threadIdx.x % K;
-    double acc[2] = {0.0, 0.0};
-    for (int il = threadIdx.x / K; il < rows; il += BT / K) {
-        const int i = r0 + il;
-        const size_t e = (size_t)i * K + r;
+    const int r0 = (threadIdx.x % (K / G)) * G;
+    double acc[2][G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[0][g] = acc[1][g] = 0.0;
+    for (int il = threadIdx.x / (K / G); il < rows; il += BT / (K / G)) {
+        const int i = r0c + il;
+        const size_t e0 = (size_t)i * K + r0;
         const TM wi = w[i];
-        double o;
+        double rv[G], o[G], qv[G];
+        ld_g<G>(W.R + e0, rv);
         if (wi != (TM)0) {
-            const TM s = spmm_row<TM, TM>(rp, ci, av, t, i, r);
-            o = fcvt<double>(t[e] + wi * (fcvt<TM>(W.R[e]) - s));
-            W.Z[e] = o;
+            TM s[G], tv[G];
+            ld_g<G>(t + e0, tv);
+            spmm_row_g<G, TM, TM>(rp, ci, av, t, i, r0, s);
+#pragma unroll
+            for (int g = 0; g < G; ++g) o[g] = fcvt<double>(tv[g] + wi * (fcvt<TM>(rv[g]) - s[g]));
+            st_g<G>(W.Z + e0, o);
         } else {
-            o = W.Z[e];
+            ld_g<G>(W.Z + e0, o);
         }
-        acc[0] += W.R[e] * o;
-        if (flexible) acc[1] += W.Q[e] * o;  // q = A p of the previous iteration: r - r_old = -alpha q
+        if (flexible) ld_g<G>(W.Q + e0, qv);  // q = A p of the previous iteration: r - r_old = -alpha q
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            acc[0][g] += rv[g] * o[g];
+            if (flexible) acc[1][g] += qv[g] * o[g];
+        }
     }
     double tot[2];
-    if (chunk_reduce<2>(acc, chunk, sys, W, tot) && threadIdx.x < K) {
+    if (chunk_reduce_g<2, G>(acc, chunk, sys, W, tot) && threadIdx.x < K) {
         const int p = sys * K + threadIdx.x;
         if (W.act[p]) {
             if (!isfinite(tot[0])) {
@@ -278,33 +471,58 @@ __device__ __forceinline__ DF spmm_row_df(const int *__restrict__ rp, const int 
     return s;
 }
 
-// q = A p, p.q per pair -> alpha; or (TRUE_RES) r = b - A x, ||r||^2 per pair
-template <bool TRUE_RES>
+// q = A p, p.q per pair -> alpha; or (TRUE_RES) r = b - A x, ||r||^2 per pair.
+// G right-hand sides per thread; in the mixed form the product runs in
+// double-FP32 on p's FP32 pairs (the true residual stays FP64).
+template <bool TRUE_RES, int G>
 __global__ void __launch_bounds__(BT) kb_spmv0(BDev W, const int *rp, const int *ci, const double *av) {
-    const int chunk = blockIdx.x, sys = W.ch_sys[chunk], r0 = W.ch_r0[chunk], rows = W.ch_rows[chunk];
+    const int chunk = blockIdx.x, sys = W.ch_sys[chunk], r0c = W.ch_r0[chunk], rows = W.ch_rows[chunk];
     if (!TRUE_RES && W.sys_nact[sys] == 0) return;
-    const int r = threadIdx.x % K;
-    double acc[1] = {0.0};
-    for (int il = threadIdx.x / K; il < rows; il += BT / K) {
-        const int i = r0 + il;
-        const size_t e = (size_t)i * K + r;
+    const int r0 = (threadIdx.x % (K / G)) * G;
+    double acc[1][G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[0][g] = 0.0;
+    for (int il = threadIdx.x / (K / G); il < rows; il += BT / (K / G)) {
+        const int i = r0c + il;
+        const size_t e0 = (size_t)i * K + r0;
         if (TRUE_RES) {
-            const double ri = W.B[e] - spmm_row<double, double>(rp, ci, av, W.X, i, r);
-            W.R[e] = ri;
-            if (W.R32) W.R32[e] = f64_to_f32_rn(ri);
-            acc[0] += ri * ri;
+            double sv[G], bv[G], rv[G];
+            ld_g<G>(W.B + e0, bv);
+            spmm_row_g<G, double, double>(rp, ci, av, W.X, i, r0, sv);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                rv[g] = bv[g] - sv[g];
+                acc[0][g] += rv[g] * rv[g];
+            }
+            st_g<G>(W.R + e0, rv);
+            if (W.R32) {
+                float rf[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) rf[g] = f64_to_f32_rn(rv[g]);
+                st_g<G>(W.R32 + e0, rf);
+            }
         } else if (W.adf) {  // mixed form: double-FP32 product on p's FP32 pairs
-            const double q = df_value(spmm_row_df(rp, ci, W.adf, W.P2, i, r));
-            W.Q[e] = q;
-            acc[0] += df_value(W.P2[e]) * q;
+            DF sd[G], pv[G];
+            ld_g<G>(W.P2 + e0, pv);
+            spmm_row_df_g<G>(rp, ci, W.adf, W.P2, i, r0, sd);
+            double q[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                q[g] = df_value(sd[g]);
+                acc[0][g] += df_value(pv[g]) * q[g];
+            }
+            st_g<G>(W.Q + e0, q);
         } else {
-            const double q = spmm_row<double, double>(rp, ci, av, W.P, i, r);
-            W.Q[e] = q;
-            acc[0] += W.P[e] * q;
+            double sv[G], pv[G];
+            ld_g<G>(W.P + e0, pv);
+            spmm_row_g<G, double, double>(rp, ci, av, W.P, i, r0, sv);
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[0][g] += pv[g] * sv[g];
+            st_g<G>(W.Q + e0, sv);
         }
     }
     double tot[1];
-    if (chunk_reduce<1>(acc, chunk, sys, W, tot) && threadIdx.x < K) {
+    if (chunk_reduce_g<1, G>(acc, chunk, sys, W, tot) && threadIdx.x < K) {
         const int p = sys * K + threadIdx.x;
         if (TRUE_RES) {
             W.tr[p] = tot[0];
@@ -313,6 +531,17 @@ __global__ void __launch_bounds__(BT) kb_spmv0(BDev W, const int *rp, const int 
             else if (tot[0] <= 0.0) deactivate(W, p, AMG_BREAKDOWN);
             else W.alpha[p] = W.rz[p] / tot[0];
         }
+    }
+}
+
+// The finest product at the handle's G.
+template <bool TRUE_RES>
+static void launch_spmv0(const BDev &d, int g, const int *rp, const int *ci, const double *av, cudaStream_t s) {
+    switch (g) {
+        case 8: kb_spmv0<TRUE_RES, 8><<<d.nchunks, BT, 0, s>>>(d, rp, ci, av); break;
+        case 4: kb_spmv0<TRUE_RES, 4><<<d.nchunks, BT, 0, s>>>(d, rp, ci, av); break;
+        case 2: kb_spmv0<TRUE_RES, 2><<<d.nchunks, BT, 0, s>>>(d, rp, ci, av); break;
+        default: kb_spmv0<TRUE_RES, 1><<<d.nchunks, BT, 0, s>>>(d, rp, ci, av); break;
     }
 }
 
@@ -473,11 +702,14 @@ static int workspace_build(Hierarchy *h, BatchWorkspace &W) {
     return AMG_OK;
 }
 
+static int tune_g(Hierarchy *h, BatchWorkspace &W);
+
 int batch_create(Hierarchy *h, BatchWorkspace **out) {
     *out = nullptr;
     BatchWorkspace *W = new (std::nothrow) BatchWorkspace();
     if (!W) return AMG_ERR_OOM;
-    const int rc = workspace_build(h, *W);
+    int rc = workspace_build(h, *W);
+    if (rc == AMG_OK) rc = tune_g(h, *W);
     if (rc < 0) {
         batch_destroy(W);
         return rc;
@@ -493,12 +725,13 @@ void batch_destroy(BatchWorkspace *W) {
     delete W;
 }
 
-static int rows_grid(long long n) {
-    const long long g = (n * K + BT - 1) / BT;
+// blocks for n rows at G right-hand sides per thread
+static int rows_grid(long long n, int G) {
+    const long long g = (n * (K / G) + BT - 1) / BT;
     return (int)std::max(1LL, std::min(g, (long long)num_sms() * 16));
 }
 
-template <typename TM>
+template <int G, typename TM>
 static int batch_vcycle(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cudaStream_t s) {
     const int L = h->nlevels;
     constexpr bool mixed = sizeof(TM) == 4;
@@ -531,15 +764,15 @@ static int batch_vcycle(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cudaStr
             // the input is vb bytes wide on every level (the finest: FP64 R, or its FP32 copy in the mixed form)
             ProfScope ps(&prof, s, "b_presmooth", l, lv.A.nnz * (4.0 + vb) + (double)n * K * 2.0 * vb);
             if (l == 0 && mixed)  // the FP32 copy of R: no conversion per gathered entry
-                kb_presmooth<float, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Ah(lv), d.R32, T(0), na);
+                kb_presmooth<G, float, TM><<<rows_grid(n, G), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Ah(lv), d.R32, T(0), na);
             else if (l == 0)
-                kb_presmooth<double, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Ah(lv), d.R, T(0), na);
+                kb_presmooth<G, double, TM><<<rows_grid(n, G), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Ah(lv), d.R, T(0), na);
             else
-                kb_presmooth<TM, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Ah(lv), Bv(l), T(l), na);
+                kb_presmooth<G, TM, TM><<<rows_grid(n, G), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Ah(lv), Bv(l), T(l), na);
         }
         {
             ProfScope ps(&prof, s, "b_restrict", l, lv.R.nnz * (4.0 + vb) + (double)(n + nc) * K * vb);
-            kb_spmm<TM><<<rows_grid(nc), BT, 0, s>>>(nc, lv.R.rp, lv.R.ci, Av(lv.R), T(l), Bv(l + 1), na);
+            kb_spmm<G, TM><<<rows_grid(nc, G), BT, 0, s>>>(nc, lv.R.rp, lv.R.ci, Av(lv.R), T(l), Bv(l + 1), na);
         }
         AMG_LAUNCH_CHECK();
         AMG_TRY(dense(l + 1));
@@ -551,19 +784,19 @@ static int batch_vcycle(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cudaStr
         {
             ProfScope ps(&prof, s, "b_prolong", l, lv.P.nnz * (4.0 + vb) + (double)n * vb + (double)(2 * n + nc) * K * vb);
             if (l == 0 && mixed)
-                kb_prolong<float, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), d.R32, Xv(1),
+                kb_prolong<G, float, TM><<<rows_grid(n, G), BT, 0, s>>>(n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), d.R32, Xv(1),
                                                                   T(0), na);
             else if (l == 0)
-                kb_prolong<double, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), d.R, Xv(1),
+                kb_prolong<G, double, TM><<<rows_grid(n, G), BT, 0, s>>>(n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), d.R, Xv(1),
                                                                    T(0), na);
             else
-                kb_prolong<TM, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), Bv(l),
+                kb_prolong<G, TM, TM><<<rows_grid(n, G), BT, 0, s>>>(n, lv.P.rp, lv.P.ci, Av(lv.P), Wv(lv), Bv(l),
                                                                Xv(l + 1), T(l), na);
         }
         AMG_LAUNCH_CHECK();
         if (l > 0) {
             ProfScope ps(&prof, s, "b_postsmooth", l, lv.A.nnz * (4.0 + vb) + (double)n * vb + (double)n * K * 3.0 * vb);
-            kb_postsmooth<TM, TM, TM><<<rows_grid(n), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), Bv(l), T(l),
+            kb_postsmooth<G, TM, TM, TM><<<rows_grid(n, G), BT, 0, s>>>(n, lv.A.rp, lv.A.ci, Av(lv.A), Wv(lv), Bv(l), T(l),
                                                                   Xv(l), na);
             AMG_LAUNCH_CHECK();
         }
@@ -574,16 +807,110 @@ static int batch_vcycle(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cudaStr
         const double nk = (double)l0.A.nrows * K;
         ProfScope ps(&prof, s, "b_postsmooth_rz", 0,
                      L > 1 ? l0.A.nnz * (4.0 + vb) + l0.A.nrows * vb + nk * (vb + 8.0 * (mixed ? 4.0 : 3.0)) : nk * 16.0);
-        kb_post0<TM><<<d.nchunks, BT, 0, s>>>(d, l0.A.rp, l0.A.ci, Av(l0.A), Wv(l0), T(0), mixed ? 1 : 0);
+        kb_post0<G, TM><<<d.nchunks, BT, 0, s>>>(d, l0.A.rp, l0.A.ci, Av(l0.A), Wv(l0), T(0), mixed ? 1 : 0);
         AMG_LAUNCH_CHECK();
     }
     return AMG_OK;
 }
 
+// One batched V-cycle at the handle's G.
+static int vcycle_g(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cudaStream_t s) {
+    const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
+    switch (W.g) {
+        case 8: return mixed ? batch_vcycle<8, float>(h, W, prof, s) : batch_vcycle<8, double>(h, W, prof, s);
+        case 4: return mixed ? batch_vcycle<4, float>(h, W, prof, s) : batch_vcycle<4, double>(h, W, prof, s);
+        case 2: return mixed ? batch_vcycle<2, float>(h, W, prof, s) : batch_vcycle<2, double>(h, W, prof, s);
+        default: return mixed ? batch_vcycle<1, float>(h, W, prof, s) : batch_vcycle<1, double>(h, W, prof, s);
+    }
+}
+
+// The autotuner of the batched V-cycle: right-hand sides per thread G in
+// {1, 2, 4, 8} (threads per row 8 / G, rows per block BT G / 8), each timed
+// as the best of three trials of two whole V-cycles (after one) with every
+// system active; the fastest is kept.
+static int tune_g(Hierarchy *h, BatchWorkspace &W) {
+    BDev &d = W.d;
+    cudaStream_t s = nullptr;
+    AMG_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    // every system active (the kernels skip inactive ones), the vectors zero
+    AMG_CUDA_TRY(cudaMemsetAsync(d.nact, 0x01, sizeof(int), s));
+    AMG_CUDA_TRY(cudaMemsetAsync(d.sys_nact, 0x01, sizeof(int) * d.nsys, s));
+    AMG_CUDA_TRY(cudaMemsetAsync(d.R, 0, sizeof(double) * (size_t)d.n * K, s));
+    if (d.R32) AMG_CUDA_TRY(cudaMemsetAsync(d.R32, 0, sizeof(float) * (size_t)d.n * K, s));
+    AMG_CUDA_TRY(cudaMemsetAsync(d.Q, 0, sizeof(double) * (size_t)d.n * K, s));
+    AMG_CUDA_TRY(cudaMemsetAsync(d.P, 0, sizeof(double) * (size_t)d.n * K, s));
+    if (d.P2) AMG_CUDA_TRY(cudaMemsetAsync(d.P2, 0, sizeof(DF) * (size_t)d.n * K, s));
+    AMG_CUDA_TRY(cudaMemsetAsync(d.act, 0, sizeof(int) * d.npairs, s));
+    Profiler prof;
+    cudaEvent_t e0, e1;
+    AMG_CUDA_TRY(cudaEventCreate(&e0));
+    AMG_CUDA_TRY(cudaEventCreate(&e1));
+    int best = 1, rc = AMG_OK;
+    float best_ms = 1e30f;
+    const int gs[4] = {1, 2, 4, 8};
+    const Level &l0 = h->L[0];
+    // the finest product first, in the form the solve runs (the systems
+    // count as active while every pair is marked stopped, so the kernel does
+    // its full work and its finisher changes nothing)
+    int bestp = 1;
+    float bestp_ms = 1e30f;
+    for (int q = 0; q < 4 && rc >= 0; ++q) {
+        launch_spmv0<false>(d, gs[q], l0.A.rp, l0.A.ci, l0.A.v, s);
+        float t_best = 1e30f;
+        for (int trial = 0; trial < 3; ++trial) {
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < 2; ++k) launch_spmv0<false>(d, gs[q], l0.A.rp, l0.A.ci, l0.A.v, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = AMG_ERR_CUDA;
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            t_best = std::min(t_best, t);
+        }
+        W.gp_ms[q] = t_best;
+        if (t_best < bestp_ms) {
+            bestp_ms = t_best;
+            bestp = gs[q];
+        }
+    }
+    W.gp = bestp;
+    for (int q = 0; q < 4 && rc >= 0; ++q) {
+        W.g = gs[q];
+        rc = vcycle_g(h, W, prof, s);
+        float t_best = 1e30f;
+        for (int trial = 0; trial < 3 && rc >= 0; ++trial) {
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < 2 && rc >= 0; ++k) rc = vcycle_g(h, W, prof, s);
+            cudaEventRecord(e1, s);
+            if (rc >= 0 && cudaEventSynchronize(e1) == cudaSuccess) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                t_best = std::min(t_best, t);
+            }
+        }
+        W.g_ms[q] = t_best;
+        if (t_best < best_ms) {
+            best_ms = t_best;
+            best = gs[q];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    W.g = best;
+    cudaMemsetAsync(d.nact, 0, sizeof(int), s);
+    cudaMemsetAsync(d.sys_nact, 0, sizeof(int) * d.nsys, s);
+    const cudaError_t se = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    AMG_TRY(rc);
+    AMG_CUDA_TRY(se);
+    return AMG_OK;
+}
+
 static int batch_iteration(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cudaStream_t s) {
     const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
-    if (mixed) AMG_TRY(batch_vcycle<float>(h, W, prof, s));
-    else AMG_TRY(batch_vcycle<double>(h, W, prof, s));
+    AMG_TRY(vcycle_g(h, W, prof, s));
     const Level &l0 = h->L[0];
     const BDev &d = W.d;
     const double nk = (double)d.n * K;
@@ -593,7 +920,7 @@ static int batch_iteration(Hierarchy *h, BatchWorkspace &W, Profiler &prof, cuda
     }
     {
         ProfScope ps(&prof, s, "b_spmv_pq", 0, l0.A.nnz * 12.0 + 4.0 * (d.n + 1) + 24.0 * nk);
-        kb_spmv0<false><<<d.nchunks, BT, 0, s>>>(d, l0.A.rp, l0.A.ci, l0.A.v);
+        launch_spmv0<false>(d, W.gp, l0.A.rp, l0.A.ci, l0.A.v, s);
     }
     {
         ProfScope ps(&prof, s, "b_update", 0, (mixed ? 52.0 : 48.0) * nk);
@@ -696,7 +1023,7 @@ int batch_solve(Hierarchy *h, BatchWorkspace *Wp, Profiler &prof, int nrhs, cons
         // true residuals; restart the pairs still above the tolerance
         {
             ProfScope ps(&prof, s, "b_true_residual", 0, l0.A.nnz * 12.0 + 4.0 * (d.n + 1) + 24.0 * d.n * K);
-            kb_spmv0<true><<<d.nchunks, BT, 0, s>>>(d, l0.A.rp, l0.A.ci, l0.A.v);
+            launch_spmv0<true>(d, W.gp, l0.A.rp, l0.A.ci, l0.A.v, s);
         }
         AMG_LAUNCH_CHECK();
         if (restarts >= c.max_restarts) break;
