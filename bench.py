@@ -73,12 +73,15 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--forms", default="mixed,fp64", help="comma list of precision forms to time (first = headline)")
     p.add_argument("--no-trace", action="store_true", help="skip the per-kernel traced pass (profiler captures)")
-    p.add_argument("--layout", default="AUTO", choices=["AUTO", "CSR", "WINDOWED", "SLICED_ELL", "ELL_DIRECT"],
+    p.add_argument("--layout", default="AUTO", choices=["AUTO", "CSR", "WINDOWED", "SLICED_ELL", "ELL_DIRECT", "TILES"],
                    help="tile layout of the streaming kernels (default: autotuned per operator)")
     p.add_argument("--amg-type", default="AGGREGATION", choices=["AGGREGATION", "CLASSICAL"],
                    help="AMG family: smoothed aggregation (default) or classical Ruge-Stueben")
     p.add_argument("--adjoint-reuse", action="store_true",
                    help="nonsymmetric adjoint on A's hierarchy transposed instead of a setup of A^T")
+    p.add_argument("--host-loop", action="store_true",
+                   help="Krylov iterations in host-polled graphs instead of the device-side conditional loop "
+                        "(profilers cannot see kernels inside graphs with conditional nodes)")
     p.add_argument("--fuse-coarse", type=int, default=1, choices=[0, 1, 2],
                    help="coarse levels below the streaming threshold: 1 single-cluster tail where they fit "
                         "(default), 2 one cooperative whole-GPU launch, 0 one launch per pass")
@@ -470,7 +473,8 @@ def run_ours(args):
     for form in form_list:
         s = api.Solver(rp, ci, vals, {"solver": solver, "precision": form.upper() if form == "mixed" else "FP64",
                                       "layout": args.layout, "adjoint_reuse": int(args.adjoint_reuse),
-                                      "amg_type": args.amg_type, "fuse_coarse": args.fuse_coarse})
+                                      "amg_type": args.amg_type, "fuse_coarse": args.fuse_coarse,
+                                      "device_loop": 0 if args.host_loop else 1})
         solvers[form] = s
         setup_ms = s.info().setup_ms  # the cold setup (re-setups below overwrite the handle's figure)
         # the first adjoint (a nonsymmetric A's builds the hierarchy of A^T), timed apart

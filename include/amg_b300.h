@@ -94,6 +94,7 @@ extern "C" {
 #define AMG_LAYOUT_SLICED_ELL 3 /* 32-row slices stored slot-major, one thread per row; windows staged */
 #define AMG_LAYOUT_ELL_DIRECT 4 /* the same slot-major slices read with plain coalesced loads (no staging);
                                    the vector gathered from global memory */
+#define AMG_LAYOUT_TILES 5      /* the timed trial over the tile layouts (CSR, windowed, sliced-ELL) only */
 
 typedef struct amg_handle_s *amg_handle; /* opaque, owned by the library until amg_free */
 
@@ -121,6 +122,10 @@ typedef struct {
                          entries per level), else one launch per pass; 2 one cooperative whole-GPU
                          launch for the run of them with the dense end of the cycle, a grid barrier
                          between passes (same bits as one launch per pass); 0 one launch per pass */
+    int device_loop;  /* 1 (default): the Krylov iterations run as one CUDA graph whose conditional
+                         node repeats them on the GPU until the solve is done (one host
+                         synchronisation per solve); 0: graphs of four iterations polled by the host
+                         (for profilers that cannot see inside graphs with conditional nodes) */
 } amg_config;
 
 typedef struct {

@@ -22,7 +22,7 @@ AMG_TEST_WITHHOLD_COPY, AMG_TEST_WITHHOLD_BARRIER = 1, 2
 SOLVERS = {"PCG": 0, "BICGSTAB": 1, "CG": 2, "BICGSTAB_NOPREC": 3}
 SMOOTHERS = {"JACOBI": 0, "L1_JACOBI": 1}
 PRECISIONS = {"FP64": 0, "MIXED": 1}
-LAYOUTS = {"AUTO": 0, "CSR": 1, "WINDOWED": 2, "SLICED_ELL": 3, "ELL_DIRECT": 4}
+LAYOUTS = {"AUTO": 0, "CSR": 1, "WINDOWED": 2, "SLICED_ELL": 3, "ELL_DIRECT": 4, "TILES": 5}
 AMG_TYPES = {"AGGREGATION": 0, "CLASSICAL": 1}
 
 # Every symbol the header declares.
@@ -35,7 +35,8 @@ class AmgConfig(C.Structure):
     _fields_ = [("solver", C.c_int), ("smoother", C.c_int), ("omega", C.c_double), ("theta", C.c_double),
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int),
                 ("max_restarts", C.c_int), ("precision", C.c_int), ("symmetric", C.c_int), ("layout", C.c_int),
-                ("adjoint_reuse", C.c_int), ("amg_type", C.c_int), ("fuse_coarse", C.c_int)]
+                ("adjoint_reuse", C.c_int), ("amg_type", C.c_int), ("fuse_coarse", C.c_int),
+                ("device_loop", C.c_int)]
 
 
 class AmgInfo(C.Structure):

@@ -36,10 +36,10 @@ int check_config(const amg_config &c) {
     if (c.solver < 0 || c.solver > 3 || (c.smoother != 0 && c.smoother != 1) || !(c.omega > 0.0) ||
         !(c.theta >= 0.0) || c.coarse_max < 1 || c.max_levels < 1 || c.max_levels > AMG_MAX_LEVELS ||
         !(c.rtol > 0.0) || c.max_iter < 1 || c.max_restarts < 0 || (c.precision != 0 && c.precision != 1) ||
-        c.symmetric < -1 || c.symmetric > 1 || c.layout < AMG_LAYOUT_AUTO || c.layout > AMG_LAYOUT_ELL_DIRECT ||
+        c.symmetric < -1 || c.symmetric > 1 || c.layout < AMG_LAYOUT_AUTO || c.layout > AMG_LAYOUT_TILES ||
         (c.adjoint_reuse != 0 && c.adjoint_reuse != 1) ||
         (c.amg_type != AMG_TYPE_AGGREGATION && c.amg_type != AMG_TYPE_CLASSICAL) ||
-        c.fuse_coarse < 0 || c.fuse_coarse > 2) {
+        c.fuse_coarse < 0 || c.fuse_coarse > 2 || (c.device_loop != 0 && c.device_loop != 1)) {
         set_last_error("invalid amg_config");
         return AMG_ERR_ARG;
     }
@@ -169,6 +169,7 @@ int amg_config_default(amg_config *c) {
     c->adjoint_reuse = 0;
     c->amg_type = AMG_TYPE_AGGREGATION;
     c->fuse_coarse = 1;
+    c->device_loop = 1;
     return AMG_OK;
 }
 

@@ -2876,7 +2876,7 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
     const long long launch_cap = (long long)c.max_iter * (c.max_restarts + 2) + 4 * chunk;
     const int trip_cap = (int)std::min<long long>(INT_MAX - 1, launch_cap / LOOP_ITERS + 2);
     // the device-side loop, where conditional graphs build (not while tracing)
-    const bool device_loop = !W.prof.on && build_loop(h, W, kind, trip_cap, s);
+    const bool device_loop = c.device_loop && !W.prof.on && build_loop(h, W, kind, trip_cap, s);
     int trips_seen = 0;
     while (status == AMG_OK) {
         // iterate until the device marks the solve done; the device sets done
@@ -3072,6 +3072,7 @@ static int time_rounds(Hierarchy *h, Workspace &W, cudaStream_t s, float *ms_out
 // either alone (the persistent tile kernels' CTAs wait behind the direct
 // kernels' blocks), which the per-pass trials cannot see.
 int autotune_plans(Hierarchy *h, Workspace &W, cudaStream_t s) {
+    if (h->cfg.layout == AMG_LAYOUT_TILES) return tune_all(h, LAYOUT_TILES, s);
     if (h->cfg.layout != AMG_LAYOUT_AUTO) return tune_all(h, h->cfg.layout, s);
     const std::vector<StreamPlan> base = plans_of(h);
     AMG_TRY(tune_all(h, LAYOUT_TILES, s));

@@ -423,3 +423,19 @@ def test_profile_product_leaves_the_handle_ready():
     s = gpu_solver(M.convdiff3d_upwind(N=14).A, {"solver": "BICGSTAB"})
     s.solve(dev(np.ones(14 ** 3)))
     assert s.profile_product(3) > 0.0
+
+
+@pytest.mark.parametrize("cfg", [{}, {"precision": "MIXED"}, {"solver": "BICGSTAB"}, {"solver": "CG"}])
+def test_device_loop_matches_host_polled_loop(cfg):
+    """The device-side Krylov loop (a conditional graph node) and the
+    host-polled graphs run the same iterations: same bits, same counts."""
+    A = M.diffusion3d_grf(N=24).A if cfg.get("solver") != "BICGSTAB" else M.convdiff3d_upwind(N=14).A
+    b = dev(np.random.default_rng(6).uniform(-1, 1, A.n))
+    out = []
+    for loop in (1, 0):
+        s = gpu_solver(A, dict(cfg, device_loop=loop, max_iter=2000))
+        x, info = s.solve(b)
+        assert info.status == 0
+        out.append((x, info.iters))
+        s.close()
+    assert torch.equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
