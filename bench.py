@@ -217,20 +217,22 @@ def oracle_time(workload: str, w, solver: str, budget_s: float, max_steps: int, 
 
 
 def cpu_baseline(workload: str, w, solver: str, budget_s: float, max_steps: int):
-    """The oracle on the host: the threaded build on every core (the reported
-    value; a third of the budget) and the single-threaded parity build beside
-    it (the rest)."""
+    """The oracle on the host: the threaded build on every core (a third of
+    the budget) and the single-threaded parity build (the rest); the faster
+    is the reported baseline, the other is given beside it."""
     import oracle as O
     cores = O.threads_used()
     ms_t, n_t, info, where = oracle_time(workload, w, solver, budget_s / 3, max_steps, threads=True)
     ms_1, n_1, _, _ = oracle_time(workload, w, solver, 2 * budget_s / 3, max_steps)
-    return {"value": ms_t, "unit": "ms", "cores": cores, "kind": "oracle",
-            "sample": f"{n_t} solve+adjoint step(s) of {where}, setup excluded, FP64, the oracle's solve phase "
-                      f"threaded with OpenMP over rows on {cores} host cores (deterministic fixed-chunk dot "
-                      f"products; {info.iters} iterations per solve)",
-            "nproc": os.cpu_count(),
-            "single_thread": {"value": ms_1, "unit": "ms", "cores": 1,
-                              "sample": f"{n_1} step(s) of the same, the serial parity build"}}
+    threaded = {"value": ms_t, "unit": "ms", "cores": cores,
+                "sample": f"{n_t} solve+adjoint step(s) of {where}, setup excluded, FP64, the oracle's solve phase "
+                          f"threaded with OpenMP over rows on {cores} host cores (deterministic fixed-chunk dot "
+                          f"products; {info.iters} iterations per solve)"}
+    single = {"value": ms_1, "unit": "ms", "cores": 1,
+              "sample": f"{n_1} solve+adjoint step(s) of {where}, setup excluded, FP64, the serial parity build"}
+    # the faster of the two is the baseline (threads do not pay on tiny problems)
+    best, other = (threaded, single) if ms_t <= ms_1 else (single, threaded)
+    return dict(best, kind="oracle", nproc=os.cpu_count(), other=other)
 
 
 def oracle_batched_time(w, budget_s: float, threads: bool = False):
@@ -266,9 +268,10 @@ def cpu_baseline_batched(w, budget_s: float):
     cores = O.threads_used()
     ms_t, sample_t = oracle_batched_time(w, budget_s / 3, threads=True)
     ms_1, sample_1 = oracle_batched_time(w, 2 * budget_s / 3)
-    return {"value": ms_t, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample_t,
-            "nproc": os.cpu_count(),
-            "single_thread": {"value": ms_1, "unit": "ms", "cores": 1, "sample": sample_1}}
+    threaded = {"value": ms_t, "unit": "ms", "cores": cores, "sample": sample_t}
+    single = {"value": ms_1, "unit": "ms", "cores": 1, "sample": sample_1}
+    best, other = (threaded, single) if ms_t <= ms_1 else (single, threaded)
+    return dict(best, kind="oracle", nproc=os.cpu_count(), other=other)
 
 
 def run_reference(args):

@@ -265,6 +265,11 @@ struct Hierarchy {
     // the autotuner's timed rounds (ms) of the tile-layout family and the
     // direct sliced-ELL family (0: not compared); the faster one is in use
     float plan_family_ms[2] = {0.f, 0.f};
+    // mixed form only: 1 when the cycle runs in FP64 after all -- a
+    // hierarchy the single-cluster tail runs whole has no DRAM traffic to
+    // halve, and the autotuner keeps whichever precision's cycle was faster
+    int cycle64 = 0;
+    float cycle_ms[2] = {0.f, 0.f};  // the trial's rounds with the FP32 and the FP64 cycle
 };
 
 // ---------------------------------------------------------------------------

@@ -2610,7 +2610,8 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
 // level's pre-smoothing and prolongation in place of converting b0.
 static int vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z0, int fin, cudaStream_t s,
                   const float *b032 = nullptr) {
-    if (h->cfg.precision == AMG_PRECISION_MIXED) return launch_vcycle<float>(h, W, b0, z0, fin, s, b032);
+    if (h->cfg.precision == AMG_PRECISION_MIXED && !h->cycle64)
+        return launch_vcycle<float>(h, W, b0, z0, fin, s, b032);
     return launch_vcycle<double>(h, W, b0, z0, fin, s, nullptr);
 }
 
@@ -3063,15 +3064,38 @@ static int time_rounds(Hierarchy *h, Workspace &W, cudaStream_t s, float *ms_out
     return AMG_OK;
 }
 
-// The autotuner.  With a requested layout, each operator's plan is the
-// fastest of that layout in a timed trial of its own pass.  With
-// AMG_LAYOUT_AUTO the two families are tuned apart -- the tile layouts (CSR,
-// windowed and sliced-ELL tiles through a shared-memory ring) and the direct
-// sliced-ELL layout -- and whole V-cycles with the finest product decide
-// between them: a cycle that interleaves the two families runs slower than
-// either alone (the persistent tile kernels' CTAs wait behind the direct
-// kernels' blocks), which the per-pass trials cannot see.
+// The mixed form on a hierarchy whose whole cycle is one cluster launch (the
+// tail from level 0): its operators sit in shared memory and L2, so the FP32
+// cycle saves no DRAM traffic and only adds conversions; the rounds are timed
+// with the FP32 and the FP64 cycle and the faster is kept.
+static int tune_cycle_precision(Hierarchy *h, Workspace &W, cudaStream_t s) {
+    h->cycle64 = 0;
+    if (h->cfg.precision != AMG_PRECISION_MIXED || h->tail_start != 0 || h->nc == 0) return AMG_OK;
+    AMG_TRY(time_rounds(h, W, s, &h->cycle_ms[0]));
+    h->cycle64 = 1;
+    AMG_TRY(time_rounds(h, W, s, &h->cycle_ms[1]));
+    h->cycle64 = h->cycle_ms[1] < h->cycle_ms[0] ? 1 : 0;
+    return AMG_OK;
+}
+
+static int autotune_layouts(Hierarchy *h, Workspace &W, cudaStream_t s);
+
+// The autotuner: the streaming plans (autotune_layouts), then, for the mixed
+// form of a tail-only hierarchy, the cycle's precision.
 int autotune_plans(Hierarchy *h, Workspace &W, cudaStream_t s) {
+    AMG_TRY(autotune_layouts(h, W, s));
+    return tune_cycle_precision(h, W, s);
+}
+
+// With a requested layout, each operator's plan is the fastest of that
+// layout in a timed trial of its own pass.  With AMG_LAYOUT_AUTO the two
+// families are tuned apart -- the tile layouts (CSR, windowed and sliced-ELL
+// tiles through a shared-memory ring) and the direct sliced-ELL layout -- and
+// whole V-cycles with the finest product decide between them: a cycle that
+// interleaves the two families runs slower than either alone (the persistent
+// tile kernels' CTAs wait behind the direct kernels' blocks), which the
+// per-pass trials cannot see.
+static int autotune_layouts(Hierarchy *h, Workspace &W, cudaStream_t s) {
     if (h->cfg.layout == AMG_LAYOUT_TILES) return tune_all(h, LAYOUT_TILES, s);
     if (h->cfg.layout != AMG_LAYOUT_AUTO) return tune_all(h, h->cfg.layout, s);
     const std::vector<StreamPlan> base = plans_of(h);
