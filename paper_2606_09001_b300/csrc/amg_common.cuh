@@ -121,7 +121,8 @@ struct DevScalars {
     int max_iter;
     int first;        // PCG: the next beta starts a new recursion (beta = 0)
     int trips;        // passes of the device-side iteration loop since the solve began
-    int copy_timeout; // a bounded wait gave up: 1 a bulk-copy wait, 2 a grid-barrier wait
+    int copy_timeout; // a bounded wait gave up: 1 a bulk-copy wait, 2 a grid-barrier wait,
+                      // 4 a wait for another CTA's slice in the whole-solve cluster launch
     int test_ctl;     // one-shot test control read with copy_timeout (amg_test_arm_wait_timeout); 0 normally
 };
 // The solve-phase kernels receive &copy_timeout and read the test control one
@@ -270,6 +271,13 @@ struct Hierarchy {
     // halve, and the autotuner keeps whichever precision's cycle was faster
     int cycle64 = 0;
     float cycle_ms[2] = {0.f, 0.f};  // the trial's rounds with the FP32 and the FP64 cycle
+    // Whole PCG solves in one cluster launch (cpcg.cuh), where every level's
+    // operators fit the cluster's shared memory: CTAs of the cluster (0: not
+    // used), the kernel's parameter table (FP32 cycle in the mixed form, FP64
+    // otherwise) and its dynamic shared memory.
+    int cpcg_cta = 0;
+    std::vector<unsigned char> cpcg_args;
+    int cpcg_smem = 0;
 };
 
 // ---------------------------------------------------------------------------

@@ -14,6 +14,7 @@
 #include "stream.cuh"
 #include "tail.cuh"
 #include "mid.cuh"
+#include "cpcg.cuh"
 
 namespace amg {
 
@@ -2263,6 +2264,8 @@ static int tail_cluster_size(int smem) {
     return 0;
 }
 
+static int cpcg_prepare(Hierarchy *h);
+
 // Chooses the first level of the fused tail: every level from it down is
 // small -- no streaming plan, fewer than 16384 rows and at most 400K stored
 // entries, a few MB that one cluster of 16 SMs reads faster than a
@@ -2292,7 +2295,7 @@ int tail_prepare(Hierarchy *h, cudaStream_t) {
             h->tail_smem64 = s64;
             h->tail_smem32 = s32;
             h->tail_start = t;
-            return AMG_OK;
+            return cpcg_prepare(h);
         }
     }
     return AMG_OK;
@@ -2320,6 +2323,315 @@ static int launch_tail(Hierarchy *h, Workspace &W, const double *b0, double *z0,
         return AMG_ERR_CUDA;
     }
     AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, tail::k_tail<TM>, args, b0, z0, qprev, fin, W.scal));
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Whole PCG solves in one cluster (cpcg.cuh)
+// ---------------------------------------------------------------------------
+
+constexpr int CPCG_SMEM_MAX = 220 * 1024;
+
+// A level's row split: `cta` slices of about equal stored entries of A (of
+// rows for the dense level), inner bounds rounded to multiples of 4.
+static void cpcg_split(int n, const std::vector<int> *rp, int cta, int *r0) {
+    r0[0] = 0;
+    const long long tot = rp ? (long long)(*rp)[n] : n;
+    for (int c = 1; c < cta; ++c) {
+        const long long t = tot * c / cta;
+        int r = rp ? (int)(std::lower_bound(rp->begin(), rp->begin() + n + 1, (int)t) - rp->begin()) : (int)t;
+        r = (r + 2) / 4 * 4;
+        r0[c] = std::min(std::max(r, r0[c - 1]), n);
+    }
+    for (int c = cta; c <= cpcg::MAX_CTAS; ++c) r0[c] = n;
+}
+
+// Fills an operator's entry bounds per slice and its lanes per row (the
+// fused tail's rule: as many lanes as the mean row length asks, while the
+// largest slice's rows still fill the CTA's threads).
+template <typename TV>
+static void cpcg_op(cpcg::COp<TV> &op, const DevCSR *m, const TV *v, const std::vector<int> *rp, const int *r0,
+                    int cta, int ncols) {
+    op.rp = m ? m->rp : nullptr;
+    op.ci = m ? m->ci : nullptr;
+    op.v = v;
+    op.ncols = ncols;
+    op.copy = 3;
+    const int n = r0[cta];
+    for (int c = 0; c <= cpcg::MAX_CTAS; ++c) op.e0[c] = rp ? (*rp)[r0[std::min(c, cta)]] : 0;
+    const long long nnz = rp ? (long long)(*rp)[n] : (long long)n * ncols;
+    int rows_max = 1;
+    for (int c = 0; c < cta; ++c) rows_max = std::max(rows_max, r0[c + 1] - r0[c]);
+    const double mean = n > 0 ? (double)nnz / n : 1.0;
+    int by_rows = 1;
+    while (by_rows < 32 && (long long)(by_rows * 2) * rows_max <= cpcg::THREADS) by_rows <<= 1;
+    int by_nnz = 1;
+    while (by_nnz < 32 && by_nnz < mean) by_nnz <<= 1;
+    op.vec = std::max(1, std::min(by_rows, by_nnz));
+}
+
+// Largest slice of an operator over the CTAs: bytes of row pointers,
+// indices and values, each region 16-byte aligned.
+template <typename TV>
+static void cpcg_slice_max(const cpcg::COp<TV> &op, const int *r0, int cta, long long &rpb, long long &cib,
+                           long long &vb) {
+    rpb = cib = vb = 0;
+    for (int c = 0; c < cta; ++c) {
+        const int a = r0[c], z = r0[c + 1];
+        if (a >= z) continue;
+        long long e0, e1;
+        if (op.ci) {
+            rpb = std::max(rpb, (tail::align_hi<int>(z + 1) - tail::align_lo<int>(a)) * 4);
+            e0 = op.e0[c];
+            e1 = op.e0[c + 1];
+            if (e1 > e0) cib = std::max(cib, (tail::align_hi<int>(e1) - tail::align_lo<int>(e0)) * 4);
+        } else {
+            e0 = (long long)a * op.ncols;
+            e1 = (long long)z * op.ncols;
+        }
+        if (e1 > e0) vb = std::max(vb, (tail::align_hi<TV>(e1) - tail::align_lo<TV>(e0)) * (long long)sizeof(TV));
+    }
+}
+
+static long long round16(long long b) { return (b + 15) / 16 * 16; }
+
+// The parameter table of the whole-solve cluster kernel with `cta` CTAs and
+// its dynamic shared memory, or *smem_bytes = -1 where the operators and
+// vectors do not all fit.  Shared memory: the two staging buffers (a whole
+// vector of the largest level, FP64 for the outer product), the CTA's FP64
+// slices of x, r, p, q, z, each smoothed level's slices of w and b, then the
+// operator slices.
+//
+// collapsed = 1 takes the hierarchy as the V-cycle runs it, levels 0 ..
+// nsolve-1 with the dense operator of the collapsed coarse end (its FP32
+// copy in the mixed form); collapsed = 0 takes every level, 0 .. nlevels-1,
+// with the coarsest level's dense inverse -- the same preconditioner up to
+// rounding, the collapse being exact.
+template <typename TM>
+static int build_cpcg_table(Hierarchy *h, int cta, int collapsed, std::vector<unsigned char> &out,
+                            int *smem_bytes) {
+    const bool mixed = sizeof(TM) == 4;
+    *smem_bytes = -1;
+    const int nl = collapsed ? h->nsolve : h->nlevels;
+    const bool dense32 = collapsed && mixed && h->nsolve < h->nlevels && h->cinv32;
+    if (nl < 2 || nl > cpcg::MAX_LEVELS) return AMG_OK;
+    cpcg::CArgs<TM> a;
+    memset(&a, 0, sizeof(a));
+    a.nlev = nl;
+    a.cta = cta;
+    std::vector<std::vector<int>> rpA(nl), rpP(nl), rpR(nl);
+    for (int k = 0; k < nl; ++k) {
+        cpcg::CLevel<TM> &d = a.L[k];
+        d.w_off = d.b_off = -1;
+        if (k < nl - 1) {
+            const Level &lv = h->L[k];
+            d.n = lv.A.nrows;
+            AMG_TRY(host_rp(lv.A, rpA[k]));
+            AMG_TRY(host_rp(lv.P, rpP[k]));
+            AMG_TRY(host_rp(lv.R, rpR[k]));
+            cpcg_split(d.n, &rpA[k], cta, d.r0);
+            d.w = (const TM *)(mixed ? (const void *)lv.w32 : (const void *)lv.w);
+        } else {
+            d.n = collapsed ? h->nc : h->L[k].A.nrows;
+            cpcg_split(d.n, nullptr, cta, d.r0);
+        }
+    }
+    for (int k = 0; k < nl - 1; ++k) {
+        const Level &lv = h->L[k];
+        cpcg::CLevel<TM> &d = a.L[k];
+        auto vals = [&](const DevCSR &m) { return (const TM *)(mixed ? (const void *)m.v32 : (const void *)m.v); };
+        cpcg_op(d.A, &lv.A, vals(lv.A), &rpA[k], d.r0, cta, lv.A.ncols);
+        cpcg_op(d.P, &lv.P, vals(lv.P), &rpP[k], d.r0, cta, lv.P.ncols);
+        cpcg_op(d.R, &lv.R, vals(lv.R), &rpR[k], a.L[k + 1].r0, cta, lv.R.ncols);
+    }
+    cpcg_op(a.K, &h->L[0].A, (const double *)h->L[0].A.v, &rpA[0], a.L[0].r0, cta, h->L[0].A.ncols);
+    const int nd = a.L[nl - 1].n;
+    cpcg_op(a.C, (const DevCSR *)nullptr, (const double *)(collapsed ? h->cinv : h->cinv_last), nullptr,
+            a.L[nl - 1].r0, cta, nd);
+    cpcg_op(a.C32, (const DevCSR *)nullptr, (const float *)h->cinv32, nullptr, a.L[nl - 1].r0, cta, nd);
+    a.c32 = dense32 ? 1 : 0;
+    a.C.copy = dense32 ? 0 : 3;
+    a.C32.copy = dense32 ? 3 : 0;
+    // the outer operator shares A_0's row pointers and indices (and in the
+    // FP64 form its values)
+    a.K.copy = mixed ? 2 : 0;
+
+    long long vec_bytes = 8LL * h->n;
+    for (int k = 0; k < nl; ++k) vec_bytes = std::max<long long>(vec_bytes, (long long)a.L[k].n * sizeof(TM));
+    const long long bufb = round16(vec_bytes);
+    long long off = 0;
+    a.buf_bytes = (int)bufb;
+    a.buf_off[0] = 0;
+    a.buf_off[1] = (int)bufb;
+    off = 2 * bufb;
+    auto slice_rows = [&](int k) {
+        int m = 0;
+        for (int c = 0; c < cta; ++c) m = std::max(m, a.L[k].r0[c + 1] - a.L[k].r0[c]);
+        return m;
+    };
+    const long long kb = round16(8LL * slice_rows(0));
+    int *koffs[5] = {&a.x_off, &a.r_off, &a.p_off, &a.q_off, &a.z_off};
+    for (int *o : koffs) {
+        *o = (int)off;
+        off += kb;
+    }
+    for (int k = 0; k < nl - 1; ++k) {
+        const long long vb = round16((long long)sizeof(TM) * slice_rows(k));
+        a.L[k].w_off = (int)off;
+        off += vb;
+        if (k > 0) {
+            a.L[k].b_off = (int)off;
+            off += vb;
+        }
+    }
+    auto place = [&](auto &op, const int *r0) {
+        long long rpb, cib, vb;
+        if (!op.copy) return;
+        cpcg_slice_max(op, r0, cta, rpb, cib, vb);
+        if (op.copy & 1) {
+            op.rp_off = (int)off;
+            op.ci_off = (int)(off + rpb);
+            off += rpb + cib;
+        }
+        if (op.copy & 2) {
+            op.v_off = (int)off;
+            off += vb;
+        }
+    };
+    for (int k = 0; k < nl - 1; ++k) {
+        place(a.L[k].A, a.L[k].r0);
+        place(a.L[k].P, a.L[k].r0);
+        place(a.L[k].R, a.L[k + 1].r0);
+    }
+    place(a.C, a.L[nl - 1].r0);
+    place(a.C32, a.L[nl - 1].r0);
+    a.K.rp_off = a.L[0].A.rp_off;
+    a.K.ci_off = a.L[0].A.ci_off;
+    if (mixed) place(a.K, a.L[0].r0);
+    else a.K.v_off = a.L[0].A.v_off;  // the FP64 cycle's A_0 itself
+    if (off > CPCG_SMEM_MAX) return AMG_OK;
+    for (int c = 0; c < cta; ++c) {
+        long long tx = 0;
+        for (int k = 0; k < nl - 1; ++k) {
+            const cpcg::CLevel<TM> &d = a.L[k], &nx = a.L[k + 1];
+            tx += cpcg::slice_copy(d.A, d.r0[c], d.r0[c + 1], c, nullptr, nullptr, false);
+            tx += cpcg::slice_copy(d.P, d.r0[c], d.r0[c + 1], c, nullptr, nullptr, false);
+            tx += cpcg::slice_copy(d.R, nx.r0[c], nx.r0[c + 1], c, nullptr, nullptr, false);
+        }
+        tx += cpcg::slice_copy(a.K, a.L[0].r0[c], a.L[0].r0[c + 1], c, nullptr, nullptr, false);
+        tx += cpcg::slice_copy(a.C, a.L[nl - 1].r0[c], a.L[nl - 1].r0[c + 1], c, nullptr, nullptr, false);
+        tx += cpcg::slice_copy(a.C32, a.L[nl - 1].r0[c], a.L[nl - 1].r0[c + 1], c, nullptr, nullptr, false);
+        a.tx[c] = (unsigned)tx;
+    }
+    out.resize(sizeof(a));
+    memcpy(out.data(), &a, sizeof(a));
+    *smem_bytes = (int)off;
+    return AMG_OK;
+}
+
+// Whether k_cpcg<TM> schedules a cluster of `cta` CTAs with smem bytes of
+// dynamic shared memory (the kernel's limit only grows, as the tail's).
+template <typename TM>
+static bool cpcg_fits(int cta, int smem) {
+    static int limit = 0;
+    const void *fn = (const void *)cpcg::k_cpcg<TM>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
+    if (smem > limit) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        limit = smem;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cta);
+    cfg.blockDim = dim3(cpcg::THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cta;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) == cudaSuccess && nclusters > 0) return true;
+    cudaGetLastError();
+    return false;
+}
+
+// Prepares whole-solve cluster launches for a hierarchy whose whole cycle
+// already runs in the single-cluster tail: the hierarchy as collapsed (fewer
+// phases a cycle), else every level with the coarsest inverse, on the
+// largest cluster (16, then 8 CTAs) whose shared memory holds every operator
+// slice and vector.
+static int cpcg_prepare(Hierarchy *h) {
+    h->cpcg_cta = 0;
+    if (h->tail_start != 0 || h->nsys > 0) return AMG_OK;
+    const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
+    for (int collapsed : {1, 0}) {
+        if (!collapsed && h->nsolve == h->nlevels) break;
+        for (int cs : {16, 8}) {
+            std::vector<unsigned char> args;
+            int smem = -1;
+            if (mixed) AMG_TRY(build_cpcg_table<float>(h, cs, collapsed, args, &smem));
+            else AMG_TRY(build_cpcg_table<double>(h, cs, collapsed, args, &smem));
+            if (smem < 0) continue;
+            if (mixed ? cpcg_fits<float>(cs, smem) : cpcg_fits<double>(cs, smem)) {
+                h->cpcg_cta = cs;
+                h->cpcg_args = args;
+                h->cpcg_smem = smem;
+                return AMG_OK;
+            }
+        }
+    }
+    return AMG_OK;
+}
+
+// Bytes one whole-solve launch moves to and from global memory: the operator
+// slices every CTA bulk-copies once (the table's transaction counts), x, r,
+// p, q read and x, r, p, q, z (and r's FP32 copy) written.
+static double cpcg_bytes(const Hierarchy *h) {
+    const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
+    const unsigned *tx = mixed ? ((const cpcg::CArgs<float> *)h->cpcg_args.data())->tx
+                               : ((const cpcg::CArgs<double> *)h->cpcg_args.data())->tx;
+    double by = 0.0;
+    for (int c = 0; c < h->cpcg_cta; ++c) by += tx[c];
+    return by + (72.0 + (mixed ? 4.0 : 0.0)) * h->n;
+}
+
+// One launch that iterates the PCG solve to its end (the scalars say why).
+static int launch_cpcg(Hierarchy *h, Workspace &W, cudaStream_t s) {
+    const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->cpcg_cta);
+    cfg.blockDim = dim3(cpcg::THREADS);
+    cfg.dynamicSmemBytes = h->cpcg_smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = h->cpcg_cta;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    TRACE("cluster_pcg", 0, cpcg_bytes(h));
+    if (mixed) {
+        if (!cpcg_fits<float>(h->cpcg_cta, h->cpcg_smem)) {
+            set_last_error("whole-solve cluster: %d bytes of shared memory refused", h->cpcg_smem);
+            return AMG_ERR_CUDA;
+        }
+        const auto &args = *(const cpcg::CArgs<float> *)h->cpcg_args.data();
+        AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<float>, args, W.x, W.r, W.p, W.q, W.z, W.r32, W.scal));
+    } else {
+        if (!cpcg_fits<double>(h->cpcg_cta, h->cpcg_smem)) {
+            set_last_error("whole-solve cluster: %d bytes of shared memory refused", h->cpcg_smem);
+            return AMG_ERR_CUDA;
+        }
+        const auto &args = *(const cpcg::CArgs<double> *)h->cpcg_args.data();
+        AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<double>, args, W.x, W.r, W.p, W.q, W.z,
+                                        (float *)nullptr, W.scal));
+    }
     return AMG_OK;
 }
 
@@ -2876,14 +3188,21 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
     long long launched = 0;
     const long long launch_cap = (long long)c.max_iter * (c.max_restarts + 2) + 4 * chunk;
     const int trip_cap = (int)std::min<long long>(INT_MAX - 1, launch_cap / LOOP_ITERS + 2);
-    // the device-side loop, where conditional graphs build (not while tracing)
-    const bool device_loop = c.device_loop && !W.prof.on && build_loop(h, W, kind, trip_cap, s);
+    // PCG on a hierarchy that fits one cluster: each pass of the loop below
+    // is one whole-solve launch; else the device-side loop, where conditional
+    // graphs build (not while tracing)
+    const bool cluster = c.device_loop && kind == 1 && h->cpcg_cta > 0;
+    const bool device_loop = !cluster && c.device_loop && !W.prof.on && build_loop(h, W, kind, trip_cap, s);
     int trips_seen = 0;
     while (status == AMG_OK) {
         // iterate until the device marks the solve done; the device sets done
         // at max_iter at the latest, launch_cap only guards the host loop
         for (;;) {
-            if (device_loop) {
+            if (cluster) {
+                AMG_TRY(launch_cpcg(h, W, s));
+                launched += launch_cap / 2 + 1;  // one launch runs the solve to its end
+                AMG_TRY(read_scalars(W, s));
+            } else if (device_loop) {
                 AMG_CUDA_TRY(cudaGraphLaunch(h->loop_exec, s));
                 launched += launch_cap / 2 + 1;  // one launch runs the loop to its end
                 AMG_TRY(read_scalars(W, s));
@@ -2943,7 +3262,8 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
     if (status == AMG_OK && !(res->rel_res_true <= c.rtol)) res->status = AMG_MAXIT;
     W.prof.collect();
     if (W.scal_h->copy_timeout) {
-        set_last_error(W.scal_h->copy_timeout & 2 ? "a grid-barrier wait of the fused coarse levels timed out"
+        set_last_error(W.scal_h->copy_timeout & 4   ? "a distributed-shared-memory wait of the whole-solve cluster launch timed out"
+                       : W.scal_h->copy_timeout & 2 ? "a grid-barrier wait of the fused coarse levels timed out"
                                                   : "a bulk-copy wait in a streaming kernel timed out");
         return AMG_ERR_CUDA;
     }
