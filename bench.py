@@ -138,6 +138,13 @@ class ClockSampler:
                     ts = None
                 self.samples.append([ts] + parts[1:])
 
+    def wait_first(self, timeout: float = 5.0):
+        """Returns once nvidia-smi has delivered its first sample (its start-up
+        queries the driver heavily), or after timeout seconds."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.samples and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+
     @staticmethod
     def now():
         import datetime
@@ -507,7 +514,7 @@ def run_ours(args):
                 pass
             sampler = ClockSampler(uuid)
             sampler.start()
-            time.sleep(0.25)
+            sampler.wait_first()
         barrier()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -735,7 +742,7 @@ def run_batched(args, world, rank, dev, barrier):
                 pass
             sampler = ClockSampler(uuid)
             sampler.start()
-            time.sleep(0.25)
+            sampler.wait_first()
         barrier()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -184,11 +184,12 @@ __device__ __forceinline__ uint32_t mapa(uint32_t a, uint32_t rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
     return r;
 }
-// A 16-byte store into another CTA's shared memory that completes its bytes
-// on that CTA's mbarrier (both addresses shared::cluster).
-__device__ __forceinline__ void st_async16(uint32_t dst, int4 v, uint32_t bar) {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(dst),
-                 "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(bar)
+// A bulk copy of `bytes` (a multiple of 16) from this CTA's shared memory to
+// another CTA's (dst and bar shared::cluster), completing on that CTA's
+// mbarrier.
+__device__ __forceinline__ void bulk_s2peer(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "r"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
 __device__ __forceinline__ void st_async8(uint32_t dst, double v, uint32_t bar) {
@@ -229,34 +230,34 @@ __device__ __forceinline__ uint32_t incoming(const int *r0, int size, int c, int
     return by;
 }
 
-// The CTA's NV partial sums (one per thread) into tot[0..NV-1] (shared),
-// summed warp by warp in a fixed order; poison makes tot[0] a NaN.
+// The CTA's NV partial sums (acc, one per thread) into tot[0..NV-1]
+// (shared).  Every thread's partials go to part (NV x THREADS); warp q then
+// adds value q's in a fixed order (lane l: threads l, l+32, ..., then a
+// shuffle tree), the values in parallel on different warps: FP64 adds are
+// slow, so few warps should issue them.  *poison (read after the barrier)
+// makes tot[0] a NaN.
 template <int NV>
-__device__ __forceinline__ void cta_sum(const double (&acc)[NV], double (*red)[THREADS / 32], double *tot,
-                                        bool poison = false) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+__device__ __forceinline__ void cta_sum(const double (&acc)[NV], double *part, double *tot, const int *poison) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        const double v = warp_sum(acc[q]);
-        if (lane == 0) red[q][wid] = v;
-    }
+    for (int q = 0; q < NV; ++q) part[q * THREADS + threadIdx.x] = acc[q];
     __syncthreads();
-    if (threadIdx.x < NV) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (wid < NV) {
         double v = 0.0;
-        for (int w = 0; w < THREADS / 32; ++w) v += red[threadIdx.x][w];
-        tot[threadIdx.x] = poison && threadIdx.x == 0 ? __longlong_as_double(0x7ff8000000000000ll) : v;
+        for (int k = lane; k < THREADS; k += 32) v += part[wid * THREADS + k];
+        v = warp_sum(v);
+        if (lane == 0) tot[wid] = *poison && wid == 0 ? __longlong_as_double(0x7ff8000000000000ll) : v;
     }
     __syncthreads();
 }
 
-template <int NV>
-__device__ __forceinline__ void sum_slots(const double *slots, int C, double (&out)[NV]) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) out[q] = 0.0;
-    for (int d = 0; d < C; ++d)
-#pragma unroll
-        for (int q = 0; q < NV; ++q) out[q] += slots[d * NV + q];
-}
+// The Krylov scalars, kept in shared memory: thread 0 alone updates them
+// (from the reduction slots), the other threads read them after a barrier.
+struct KScal {
+    double rz, alpha, beta, pq, rr;
+    int iters, first, status, stop;
+    int have_rr;  // an update preceded this V-cycle: its ||r||^2 is reduced with r.z
+};
 
 // x, r, p, q, z: the solve's FP64 vectors in global memory (x and r the
 // current iterate and residual; p and q the previous iteration's, read when
@@ -270,30 +271,41 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
                                                      float *__restrict__ gr32, DevScalars *sc) {
     extern __shared__ __align__(128) unsigned char smem[];
     // bar: the operator slices' bulk copies; xbar[k]: staging buffer k's
-    // incoming slices; rbar: the three reductions' incoming partials
-    __shared__ __align__(8) uint64_t bar, xbar[2], rbar[3];
-    __shared__ double red[2][THREADS / 32];
-    __shared__ double tot[2];
-    __shared__ __align__(16) double slot_rz[MAX_CTAS * 2], slot_pq[MAX_CTAS], slot_rr[MAX_CTAS];
+    // incoming slices; rbar: the two reductions' incoming partials
+    __shared__ __align__(8) uint64_t bar, xbar[2], rbar[2];
+    __shared__ double part[3 * THREADS];
+    __shared__ double tot[3], sums[3];
+    __shared__ __align__(16) double slot_rz[MAX_CTAS * 3], slot_pq[MAX_CTAS];
+    __shared__ KScal S;
+    __shared__ int bad;  // 1: the bulk copies did not land; 2: an exchange wait ran out
     cg::cluster_group cl = cg::this_cluster();
     pdl_wait();
     pdl_trigger();
     if (sc->done) return;  // uniform: every thread of every CTA reads the same word before any barrier
     const int c = (int)cl.block_rank(), C = a.cta, nl = a.nlev;
     const int tid = threadIdx.x;
-    // scalars, identical in every thread
-    double rz = sc->rz, alpha = sc->alpha, beta = sc->beta, pq = sc->pq, rr = sc->rr;
     const double tol2 = sc->tol2;
-    int iters = sc->iters, first = sc->first;
-    const int max_iter = sc->max_iter, flexible = sc->flexible;
-    int status = AMG_OK;
+    const int max_iter = sc->max_iter, flexible = sc->flexible, first0 = sc->first;
+    if (tid == 0) {
+        S.rz = sc->rz;
+        S.alpha = sc->alpha;
+        S.beta = sc->beta;
+        S.pq = sc->pq;
+        S.rr = sc->rr;
+        S.iters = sc->iters;
+        S.first = first0;
+        S.status = AMG_OK;
+        S.stop = 0;
+        S.have_rr = 0;
+        bad = 0;
+    }
 
     // bulk copies of the CTA's operator slices (warp 0), one mbarrier
     if (tid < 32) {
         if (tid == 0) {
             stream::mbar_init(&bar, 1);
             for (int k = 0; k < 2; ++k) stream::mbar_init(&xbar[k], 1);
-            for (int k = 0; k < 3; ++k) stream::mbar_init(&rbar[k], 1);
+            for (int k = 0; k < 2; ++k) stream::mbar_init(&rbar[k], 1);
             stream::fence_mbar_init();
             stream::mbar_expect_tx(&bar, a.tx[c]);
         }
@@ -323,8 +335,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
     for (int i = r0 + tid; i < r1; i += THREADS) {
         X[i - r0] = gx[i];
         R[i - r0] = gr[i];
-        P[i - r0] = first ? 0.0 : gp[i];
-        Q[i - r0] = first ? 0.0 : gq[i];
+        P[i - r0] = first0 ? 0.0 : gp[i];
+        Q[i - r0] = first0 ? 0.0 : gq[i];
     }
     for (int k = 0; k < nl - 1; ++k) {
         const CLevel<TM> &lv = a.L[k];
@@ -335,44 +347,50 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
     cl.sync();
     auto buf = [&](int k) { return smem + a.buf_off[k]; };
     uint32_t xpar = 0, rpar = 0;  // phase parities of xbar[k] (bit k) and rbar[k] (bit k)
-    bool ok = true;               // every exchange wait so far completed
     int cur = 0;
+    double rr_part = 0.0;         // the thread's share of the last update's ||r||^2
 
     // Sends this CTA's rows [q0, q1) of the vector in buf(nb) to every other
-    // CTA, then waits for theirs.  The caller has armed xbar[nb] with the
-    // incoming bytes and written its rows (visible to the CTA after the
-    // barrier here).
+    // CTA -- one bulk copy a peer -- then waits for theirs.  The caller has
+    // armed xbar[nb] with the incoming bytes and written its rows (made
+    // visible to the copies by the proxy fence and the barrier here).
     auto exchange = [&](int nb, int q0, int q1, int size) {
+        stream::fence_proxy_async();
         __syncthreads();
-        const int b0 = slice_b0(q0, size), units = (slice_b1(q0, q1, size) - b0) >> 4;
-        const uint32_t src = stream::smem_u32(buf(nb) + b0), xb = stream::smem_u32(&xbar[nb]);
-        for (int p = tid; p < units * MAX_CTAS; p += THREADS) {
-            const int d = p & (MAX_CTAS - 1), k = p / MAX_CTAS;
-            if (d == c || d >= C) continue;
-            const int4 v = reinterpret_cast<const int4 *>(buf(nb) + b0)[k];
-            st_async16(mapa(src + 16u * k, (uint32_t)d), v, mapa(xb, (uint32_t)d));
+        const int b0 = slice_b0(q0, size), bytes = slice_b1(q0, q1, size) - b0;
+        if (tid < C && tid != c && bytes > 0) {
+            const uint32_t src = stream::smem_u32(buf(nb) + b0);
+            bulk_s2peer(mapa(src, (uint32_t)tid), src, (uint32_t)bytes,
+                        mapa(stream::smem_u32(&xbar[nb]), (uint32_t)tid));
         }
-        ok = wait_cluster(&xbar[nb], (xpar >> nb) & 1u) && ok;
+        if (!wait_cluster(&xbar[nb], (xpar >> nb) & 1u)) atomicOr(&bad, 2);
         xpar ^= 1u << nb;
         cur = nb;
     };
-    // Puts the CTA's NV totals (tot) into slot c of every CTA's slots, waits
-    // for the others' and returns the sums in rank order.
-    auto reduce = [&](int j, double *slots, auto &out) {
-        constexpr int NV = sizeof(out) / sizeof(double);
+    // Puts the CTA's nv totals (tot) into slot c of every CTA's slots; warp 0
+    // waits for the others' and adds them in a fixed order (a shuffle tree
+    // over the ranks, the same bits in every CTA) into sums[0..nv-1], read by
+    // thread 0 after the warp's sync.
+    auto reduce = [&](int j, double *slots, int nv) {
         const uint32_t sb = stream::smem_u32(slots), rb = stream::smem_u32(&rbar[j]);
-        if (tid < C && tid != c) {
-#pragma unroll
-            for (int q = 0; q < NV; ++q)
-                st_async8(mapa(sb + 8u * (c * NV + q), (uint32_t)tid), tot[q], mapa(rb, (uint32_t)tid));
+        if (tid < C && tid != c)
+            for (int q = 0; q < nv; ++q)
+                st_async8(mapa(sb + 8u * (c * nv + q), (uint32_t)tid), tot[q], mapa(rb, (uint32_t)tid));
+        if (tid < 32) {
+            if (tid == 0)
+                for (int q = 0; q < nv; ++q) slots[c * nv + q] = tot[q];
+            if (!wait_cluster(&rbar[j], (rpar >> j) & 1u)) atomicOr(&bad, 2);
+            __syncwarp();
+            const int d = tid & (MAX_CTAS - 1);
+            for (int q0 = 0; q0 < nv; q0 += 2) {
+                const int q = q0 + (tid >> 4);
+                double v = q < nv && d < C ? slots[d * nv + q] : 0.0;
+                v = group_sum<MAX_CTAS>(v);
+                if (d == 0 && q < nv) sums[q] = v;
+            }
+            __syncwarp();
         }
-        if (tid == 0)
-#pragma unroll
-            for (int q = 0; q < NV; ++q) slots[c * NV + q] = tot[q];
-        __syncthreads();
-        ok = wait_cluster(&rbar[j], (rpar >> j) & 1u) && ok;
         rpar ^= 1u << j;
-        sum_slots<NV>(slots, C, out);
     };
     auto arm_vec = [&](int nb, const int *split, int size) {
         if (tid == 0) stream::mbar_expect_tx(&xbar[nb], incoming(split, size, c, C));
@@ -390,7 +408,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
         exchange(0, r0, r1, (int)sizeof(TM));
     }
     const bool loaded = __syncthreads_and(stream::mbar_wait(&bar, 0)) != 0;
-    if (!loaded && tid == 0) atomicOr(&sc->copy_timeout, 1);
+    if (!loaded && tid == 0) {
+        atomicOr(&sc->copy_timeout, 1);
+        atomicOr(&bad, 1);
+    }
 
     for (;;) {
         // V-cycle, down: pre-smoothing with the residual, restriction
@@ -481,8 +502,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
                                      [&](int i, TM s) { ys[i] = ts[i] + wk[i - s0] * (bof(i) - s); });
                 exchange(nb, s0, s1, (int)sizeof(TM));
             } else {
-                arm_red(0, 2);
-                double acc[2] = {0.0, 0.0};
+                // r.z, z.q and the last update's ||r||^2 in one reduction
+                arm_red(0, 3);
+                double acc[3] = {0.0, 0.0, rr_part};
                 if (loaded)
                     rows<TM, TM, TM>(lv.A, s0, s1, c, smem, ts, [&](int i, TM s) {
                         const double zi = fcvt<double>(ts[i] + wk[i - s0] * (bof(i) - s));
@@ -490,17 +512,35 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
                         acc[0] += R[i - s0] * zi;
                         acc[1] += Q[i - s0] * zi;  // z.q: the flexible beta's z.(r - r_old) = -alpha z.q
                     });
-                cta_sum<2>(acc, red, tot, !(ok && loaded));  // a NaN ends the solve everywhere
-                double sums[2];
-                reduce(0, slot_rz, sums);
-                if (!isfinite(sums[0])) {
-                    status = AMG_NAN;
-                    stop = true;
-                } else {
-                    beta = first ? 0.0 : (flexible ? -alpha * sums[1] : sums[0]) / rz;
-                    first = 0;
-                    rz = sums[0];
+                cta_sum<3>(acc, part, tot, &bad);  // a NaN ends the solve everywhere
+                reduce(0, slot_rz, 3);
+                if (tid == 0) {
+                    // the last update's convergence test, then beta: an update
+                    // that converged costs one V-cycle more, not an iteration
+                    if (S.have_rr) {
+                        S.rr = sums[2];
+                        if (!isfinite(sums[2])) {
+                            S.status = AMG_NAN;
+                            S.stop = 1;
+                        } else if (sums[2] <= tol2) {
+                            S.stop = 1;
+                        } else if (S.iters >= max_iter) {
+                            S.status = AMG_MAXIT;
+                            S.stop = 1;
+                        }
+                    }
+                    if (S.stop) {
+                    } else if (!isfinite(sums[0])) {
+                        S.status = AMG_NAN;
+                        S.stop = 1;
+                    } else {
+                        S.beta = S.first ? 0.0 : (flexible ? -S.alpha * sums[1] : sums[0]) / S.rz;
+                        S.first = 0;
+                        S.rz = sums[0];
+                    }
                 }
+                __syncthreads();
+                stop = S.stop != 0;
             }
         }
         if (stop) break;
@@ -509,6 +549,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
             const int nb = cur ^ 1;
             arm_vec(nb, a.L[0].r0, 8);
             double *ps = reinterpret_cast<double *>(buf(nb));
+            const double beta = S.beta;
             for (int i = r0 + tid; i < r1; i += THREADS) {
                 const double pv = beta == 0.0 ? Z[i - r0] : Z[i - r0] + beta * P[i - r0];
                 P[i - r0] = pv;
@@ -525,53 +566,43 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
                 Q[i - r0] = s;
                 acc[0] += P[i - r0] * s;
             });
-            cta_sum<1>(acc, red, tot);
-            double sums[1];
-            reduce(1, slot_pq, sums);
-            if (!isfinite(sums[0])) {
-                status = AMG_NAN;
-                break;
+            cta_sum<1>(acc, part, tot, &bad);
+            reduce(1, slot_pq, 1);
+            if (tid == 0) {
+                if (!isfinite(sums[0]) || sums[0] <= 0.0) {
+                    S.status = isfinite(sums[0]) ? AMG_BREAKDOWN : AMG_NAN;
+                    S.stop = 1;
+                } else {
+                    S.pq = sums[0];
+                    S.alpha = S.rz / sums[0];
+                }
             }
-            if (sums[0] <= 0.0) {
-                status = AMG_BREAKDOWN;
-                break;
-            }
-            pq = sums[0];
-            alpha = rz / pq;
+            __syncthreads();
+            if (S.stop) break;
         }
         // x += alpha p, r -= alpha q, r.r; the next pre-smoothing gathers W r
         {
             const int nb = cur ^ 1;
             arm_vec(nb, a.L[0].r0, (int)sizeof(TM));
-            arm_red(2, 1);
             TM *ys = reinterpret_cast<TM *>(buf(nb));
             const TM *w0 = reinterpret_cast<const TM *>(smem + a.L[0].w_off);
-            double acc[1] = {0.0};
+            const double alpha = S.alpha;
+            rr_part = 0.0;
             for (int i = r0 + tid; i < r1; i += THREADS) {
                 X[i - r0] += alpha * P[i - r0];
                 const double rn = R[i - r0] - alpha * Q[i - r0];
                 R[i - r0] = rn;
-                acc[0] += rn * rn;
+                rr_part += rn * rn;
                 ys[i] = w0[i - r0] * fcvt<TM>(rn);
             }
-            cta_sum<1>(acc, red, tot);
-            double sums[1];
-            reduce(2, slot_rr, sums);
+            if (tid == 0) {
+                S.iters += 1;
+                S.have_rr = 1;
+            }
             exchange(nb, r0, r1, (int)sizeof(TM));
-            rr = sums[0];
-            iters += 1;
-            if (!isfinite(rr)) {
-                status = AMG_NAN;
-                break;
-            }
-            if (rr <= tol2) break;
-            if (iters >= max_iter) {
-                status = AMG_MAXIT;
-                break;
-            }
         }
     }
-    if (!ok && tid == 0) atomicOr(&sc->copy_timeout, 4);
+    if ((bad & 2) && tid == 0) atomicOr(&sc->copy_timeout, 4);
     // the state back to global memory for the true residual and a restart
     for (int i = r0 + tid; i < r1; i += THREADS) {
         gx[i] = X[i - r0];
@@ -582,14 +613,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
         if (gr32) gr32[i] = f64_to_f32_rn(R[i - r0]);
     }
     if (c == 0 && tid == 0) {
-        sc->rz = rz;
-        sc->alpha = alpha;
-        sc->beta = beta;
-        sc->pq = pq;
-        sc->rr = rr;
-        sc->iters = iters;
-        sc->first = first;
-        sc->status = status;
+        sc->rz = S.rz;
+        sc->alpha = S.alpha;
+        sc->beta = S.beta;
+        sc->pq = S.pq;
+        sc->rr = S.rr;
+        sc->iters = S.iters;
+        sc->first = S.first;
+        sc->status = S.status;
         sc->done = 1;
     }
     if (!loaded) stream::mbar_wait(&bar, 0);  // a bounded chance for late copies to land before exit

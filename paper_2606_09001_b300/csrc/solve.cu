@@ -2330,7 +2330,9 @@ static int launch_tail(Hierarchy *h, Workspace &W, const double *b0, double *z0,
 // Whole PCG solves in one cluster (cpcg.cuh)
 // ---------------------------------------------------------------------------
 
-constexpr int CPCG_SMEM_MAX = 220 * 1024;
+// Dynamic shared memory of one whole-solve CTA: the SM's 227 KB less the
+// kernel's static part (the reductions' partials, about 13 KB).
+constexpr int CPCG_SMEM_MAX = 214 * 1024;
 
 // A level's row split: `cta` slices of about equal stored entries of A (of
 // rows for the dense level), inner bounds rounded to multiples of 4.
@@ -3171,18 +3173,14 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
                              W.counter, precond ? 0 : 1));
     }
     AMG_LAUNCH_CHECK();
-    AMG_TRY(read_scalars(W, s));
-    int status = W.scal_h->status;
+    // The start's scalars (||b||^2, a failure) are read with the first
+    // iterations': the start leaves done set for b = 0 or a non-finite b, so
+    // those iterations return at once.
+    int status = AMG_OK;
     int restarts = 0, bd_restarts = 0;
-    const double bn2 = W.scal_h->bn2;
-    if (bn2 == 0.0 && status == AMG_OK) {
-        res->status = AMG_OK;
-        res->iters = 0;
-        res->restarts = 0;
-        res->rel_res_true = res->rel_res_rec = 0.0;
-        W.prof.collect();
-        return AMG_OK;
-    }
+    bool first_read = true;
+    // W.scal_h holds the scalars of a true residual of the current x
+    bool fresh = false;
     const int chunk = 4;
     const int kind = bicg ? (precond ? 3 : 2) : (precond ? 1 : 0);
     long long launched = 0;
@@ -3214,6 +3212,18 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
                 launched += chunk;
                 AMG_TRY(read_scalars(W, s));
             }
+            if (first_read) {
+                first_read = false;
+                if (W.scal_h->bn2 == 0.0 && W.scal_h->status == AMG_OK) {
+                    // b = 0: x = 0 exactly
+                    res->status = AMG_OK;
+                    res->iters = 0;
+                    res->restarts = 0;
+                    res->rel_res_true = res->rel_res_rec = 0.0;
+                    W.prof.collect();
+                    return AMG_OK;
+                }
+            }
             if (W.scal_h->done) break;
             if (launched > launch_cap) {
                 set_last_error("solver loop exceeded %lld iterations without finishing", launch_cap);
@@ -3234,6 +3244,7 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
         if (status != AMG_OK) break;
         // converged on the recursive residual: check the true residual
         AMG_TRY(true_residual(h, W, s));
+        fresh = true;
         const double tr = W.scal_h->tr;
         if (tr <= W.scal_h->tol2) break;
         if (restarts >= c.max_restarts || W.scal_h->iters >= c.max_iter) {
@@ -3241,6 +3252,7 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
             break;
         }
         restarts++;
+        fresh = false;
         // r already holds b - A x; restart the recursion from the current x
         if (bicg) {
             AMG_TRY(bicg_restart(h, W, s));
@@ -3251,10 +3263,11 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
             AMG_LAUNCH_CHECK();
         }
     }
-    AMG_TRY(read_scalars(W, s));
+    if (!fresh) AMG_TRY(read_scalars(W, s));
     const double rec = W.scal_h->rr;
     res->iters = W.scal_h->iters;
-    AMG_TRY(true_residual(h, W, s));
+    if (!fresh) AMG_TRY(true_residual(h, W, s));
+    const double bn2 = W.scal_h->bn2;
     res->status = status;
     res->restarts = restarts;
     res->rel_res_true = sqrt(W.scal_h->tr / bn2);
