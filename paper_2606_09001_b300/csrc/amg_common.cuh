@@ -124,6 +124,7 @@ struct DevScalars {
     int copy_timeout; // a bounded wait gave up: 1 a bulk-copy wait, 2 a grid-barrier wait,
                       // 4 a wait for another CTA's slice in the whole-solve cluster launch
     int test_ctl;     // one-shot test control read with copy_timeout (amg_test_arm_wait_timeout); 0 normally
+    int tr_fresh;     // 1: the whole-solve cluster launch ended with tr and r = b - A x of the final x
 };
 // The solve-phase kernels receive &copy_timeout and read the test control one
 // int further on.

@@ -50,6 +50,10 @@ namespace cg = cooperative_groups;
 constexpr int THREADS = 512;
 constexpr int MAX_LEVELS = 8;
 constexpr int MAX_CTAS = 16;
+// The last warp arms the mbarriers and issues the sends: the row passes of
+// the small levels leave it idle, so the bookkeeping stays off the path of
+// the warps that hold rows.
+constexpr int AUX_WARP = THREADS / 32 - 1;
 
 // One operator's slices: CSR (ci != null) or the dense coarsest operator
 // (row-major, ncols entries a row).  The shared-memory offsets are the same
@@ -197,6 +201,15 @@ __device__ __forceinline__ void st_async8(uint32_t dst, double v, uint32_t bar) 
                  "l"(__double_as_longlong(v)), "r"(bar)
                  : "memory");
 }
+// Arrives on an mbarrier and adds `bytes` to its expected transaction count,
+// without ordering the thread's earlier memory operations (the arrival
+// publishes nothing).
+__device__ __forceinline__ void arm_relaxed(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.relaxed.cta.shared::cta.b64 _, [%0], %1;" ::"r"(stream::smem_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+
 // Bounded wait for an mbarrier phase whose bytes other CTAs of the cluster
 // wrote (acquire at cluster scope).
 constexpr uint32_t WAIT_POLLS = 1u << 22;
@@ -234,17 +247,18 @@ __device__ __forceinline__ uint32_t incoming(const int *r0, int size, int c, int
 // (shared).  Every thread's partials go to part (NV x THREADS); warp q then
 // adds value q's in a fixed order (lane l: threads l, l+32, ..., then a
 // shuffle tree), the values in parallel on different warps: FP64 adds are
-// slow, so few warps should issue them.  *poison (read after the barrier)
-// makes tot[0] a NaN.
+// slow, so few warps should issue them.  Only threads below np hold
+// partials.  *poison (read after the barrier) makes tot[0] a NaN.
 template <int NV>
-__device__ __forceinline__ void cta_sum(const double (&acc)[NV], double *part, double *tot, const int *poison) {
+__device__ __forceinline__ void cta_sum(const double (&acc)[NV], double *part, double *tot, const int *poison,
+                                        int np) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) part[q * THREADS + threadIdx.x] = acc[q];
     __syncthreads();
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (wid < NV) {
         double v = 0.0;
-        for (int k = lane; k < THREADS; k += 32) v += part[wid * THREADS + k];
+        for (int k = lane; k < np; k += 32) v += part[wid * THREADS + k];
         v = warp_sum(v);
         if (lane == 0) tot[wid] = *poison && wid == 0 ? __longlong_as_double(0x7ff8000000000000ll) : v;
     }
@@ -259,13 +273,16 @@ struct KScal {
     int have_rr;  // an update preceded this V-cycle: its ||r||^2 is reduced with r.z
 };
 
-// x, r, p, q, z: the solve's FP64 vectors in global memory (x and r the
-// current iterate and residual; p and q the previous iteration's, read when
-// the recursion continues); r32: the FP32 copy of r (mixed form), or null.
-// The kernel reads and writes the scalars in sc as the per-iteration kernels
-// do, and leaves done = 1.
+// b: the right-hand side; x, r, p, q, z: the solve's FP64 vectors in global
+// memory (x and r the current iterate and residual; p and q the previous
+// iteration's, read when the recursion continues); r32: the FP32 copy of r
+// (mixed form), or null.  The kernel reads and writes the scalars in sc as
+// the per-iteration kernels do and leaves done = 1; when the iterations end
+// converged or at the cap it also leaves r = b - A x and tr = ||r||^2 of the
+// final x (tr_fresh = 1), the true residual the host checks.
 template <typename TM>
-__global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CArgs<TM> a, double *__restrict__ gx,
+__global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CArgs<TM> ga, const double *__restrict__ gb,
+                                                     double *__restrict__ gx,
                                                      double *__restrict__ gr, double *__restrict__ gp,
                                                      double *__restrict__ gq, double *__restrict__ gz,
                                                      float *__restrict__ gr32, DevScalars *sc) {
@@ -278,10 +295,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
     __shared__ __align__(16) double slot_rz[MAX_CTAS * 3], slot_pq[MAX_CTAS];
     __shared__ KScal S;
     __shared__ int bad;  // 1: the bulk copies did not land; 2: an exchange wait ran out
+    // the table, copied to shared memory: the phases index it by level and
+    // rank, which the constant cache serves slowly
+    __shared__ __align__(16) CArgs<TM> a;
     cg::cluster_group cl = cg::this_cluster();
     pdl_wait();
     pdl_trigger();
     if (sc->done) return;  // uniform: every thread of every CTA reads the same word before any barrier
+    {
+        static_assert(sizeof(CArgs<TM>) % 4 == 0, "table copied in words");
+        const int *src = reinterpret_cast<const int *>(&ga);
+        int *dst = reinterpret_cast<int *>(&a);
+        for (int k = threadIdx.x; k < (int)(sizeof(CArgs<TM>) / 4); k += THREADS) dst[k] = src[k];
+        __syncthreads();
+    }
     const int c = (int)cl.block_rank(), C = a.cta, nl = a.nlev;
     const int tid = threadIdx.x;
     const double tol2 = sc->tol2;
@@ -358,10 +385,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
         stream::fence_proxy_async();
         __syncthreads();
         const int b0 = slice_b0(q0, size), bytes = slice_b1(q0, q1, size) - b0;
-        if (tid < C && tid != c && bytes > 0) {
+        const int d = tid - AUX_WARP * 32;
+        if (d >= 0 && d < C && d != c && bytes > 0) {
             const uint32_t src = stream::smem_u32(buf(nb) + b0);
-            bulk_s2peer(mapa(src, (uint32_t)tid), src, (uint32_t)bytes,
-                        mapa(stream::smem_u32(&xbar[nb]), (uint32_t)tid));
+            bulk_s2peer(mapa(src, (uint32_t)d), src, (uint32_t)bytes, mapa(stream::smem_u32(&xbar[nb]), (uint32_t)d));
         }
         if (!wait_cluster(&xbar[nb], (xpar >> nb) & 1u)) atomicOr(&bad, 2);
         xpar ^= 1u << nb;
@@ -373,9 +400,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
     // thread 0 after the warp's sync.
     auto reduce = [&](int j, double *slots, int nv) {
         const uint32_t sb = stream::smem_u32(slots), rb = stream::smem_u32(&rbar[j]);
-        if (tid < C && tid != c)
+        const int d = tid - AUX_WARP * 32;
+        if (d >= 0 && d < C && d != c)
             for (int q = 0; q < nv; ++q)
-                st_async8(mapa(sb + 8u * (c * nv + q), (uint32_t)tid), tot[q], mapa(rb, (uint32_t)tid));
+                st_async8(mapa(sb + 8u * (c * nv + q), (uint32_t)d), tot[q], mapa(rb, (uint32_t)d));
         if (tid < 32) {
             if (tid == 0)
                 for (int q = 0; q < nv; ++q) slots[c * nv + q] = tot[q];
@@ -393,10 +421,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
         rpar ^= 1u << j;
     };
     auto arm_vec = [&](int nb, const int *split, int size) {
-        if (tid == 0) stream::mbar_expect_tx(&xbar[nb], incoming(split, size, c, C));
+        if (tid == AUX_WARP * 32) arm_relaxed(&xbar[nb], incoming(split, size, c, C));
     };
     auto arm_red = [&](int j, int nv) {
-        if (tid == 0) stream::mbar_expect_tx(&rbar[j], (uint32_t)(8 * nv * (C - 1)));
+        if (tid == AUX_WARP * 32) arm_relaxed(&rbar[j], (uint32_t)(8 * nv * (C - 1)));
     };
 
     // the first pre-smoothing gathers W b with b = r
@@ -512,7 +540,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
                         acc[0] += R[i - s0] * zi;
                         acc[1] += Q[i - s0] * zi;  // z.q: the flexible beta's z.(r - r_old) = -alpha z.q
                     });
-                cta_sum<3>(acc, part, tot, &bad);  // a NaN ends the solve everywhere
+                // partials sit in the rows' lane-0 threads and the update's
+                // threads: below rows x lanes
+                cta_sum<3>(acc, part, tot, &bad, min(THREADS, (s1 - s0) * lv.A.vec));  // a NaN ends the solve everywhere
                 reduce(0, slot_rz, 3);
                 if (tid == 0) {
                     // the last update's convergence test, then beta: an update
@@ -566,7 +596,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
                 Q[i - r0] = s;
                 acc[0] += P[i - r0] * s;
             });
-            cta_sum<1>(acc, part, tot, &bad);
+            cta_sum<1>(acc, part, tot, &bad, min(THREADS, (r1 - r0) * a.K.vec));
             reduce(1, slot_pq, 1);
             if (tid == 0) {
                 if (!isfinite(sums[0]) || sums[0] <= 0.0) {
@@ -602,6 +632,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
             exchange(nb, r0, r1, (int)sizeof(TM));
         }
     }
+    // the true residual of the final x: x to every CTA, then r = b - A x
+    // (the FP64 operator) and ||r||^2
+    const bool true_res = S.status == AMG_OK || S.status == AMG_MAXIT;
+    if (true_res) {
+        {
+            const int nb = cur ^ 1;
+            arm_vec(nb, a.L[0].r0, 8);
+            double *xs = reinterpret_cast<double *>(buf(nb));
+            for (int i = r0 + tid; i < r1; i += THREADS) xs[i] = X[i - r0];
+            exchange(nb, r0, r1, 8);
+        }
+        arm_red(1, 1);
+        const double *xs = reinterpret_cast<const double *>(buf(cur));
+        double acc[1] = {0.0};
+        if (loaded)
+            rows<double, double, double>(a.K, r0, r1, c, smem, xs, [&](int i, double s) {
+                const double ri = gb[i] - s;
+                R[i - r0] = ri;
+                acc[0] += ri * ri;
+            });
+        cta_sum<1>(acc, part, tot, &bad, min(THREADS, (r1 - r0) * a.K.vec));
+        reduce(1, slot_pq, 1);
+        __syncthreads();  // R's new entries, for the write-back below
+    }
     if ((bad & 2) && tid == 0) atomicOr(&sc->copy_timeout, 4);
     // the state back to global memory for the true residual and a restart
     for (int i = r0 + tid; i < r1; i += THREADS) {
@@ -621,6 +675,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
         sc->iters = S.iters;
         sc->first = S.first;
         sc->status = S.status;
+        if (true_res) sc->tr = sums[0];
+        sc->tr_fresh = true_res ? 1 : 0;
         sc->done = 1;
     }
     if (!loaded) stream::mbar_wait(&bar, 0);  // a bounded chance for late copies to land before exit

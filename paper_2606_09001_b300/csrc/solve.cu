@@ -686,6 +686,7 @@ __global__ void k_set_control(DevScalars *sc, int done, int status, int flexible
     sc->status = status;
     sc->flexible = flexible;
     sc->max_iter = max_iter;
+    sc->tr_fresh = 0;
     if (reset_iters) {
         sc->iters = 0;
         sc->trips = 0;
@@ -2331,8 +2332,8 @@ static int launch_tail(Hierarchy *h, Workspace &W, const double *b0, double *z0,
 // ---------------------------------------------------------------------------
 
 // Dynamic shared memory of one whole-solve CTA: the SM's 227 KB less the
-// kernel's static part (the reductions' partials, about 13 KB).
-constexpr int CPCG_SMEM_MAX = 214 * 1024;
+// kernel's static part (the reductions' partials and the table, about 18 KB).
+constexpr int CPCG_SMEM_MAX = 208 * 1024;
 
 // A level's row split: `cta` slices of about equal stored entries of A (of
 // rows for the dense level), inner bounds rounded to multiples of 4.
@@ -2624,15 +2625,16 @@ static int launch_cpcg(Hierarchy *h, Workspace &W, cudaStream_t s) {
             return AMG_ERR_CUDA;
         }
         const auto &args = *(const cpcg::CArgs<float> *)h->cpcg_args.data();
-        AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<float>, args, W.x, W.r, W.p, W.q, W.z, W.r32, W.scal));
+        AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<float>, args, (const double *)W.b, W.x, W.r, W.p, W.q, W.z,
+                                        W.r32, W.scal));
     } else {
         if (!cpcg_fits<double>(h->cpcg_cta, h->cpcg_smem)) {
             set_last_error("whole-solve cluster: %d bytes of shared memory refused", h->cpcg_smem);
             return AMG_ERR_CUDA;
         }
         const auto &args = *(const cpcg::CArgs<double> *)h->cpcg_args.data();
-        AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<double>, args, W.x, W.r, W.p, W.q, W.z,
-                                        (float *)nullptr, W.scal));
+        AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<double>, args, (const double *)W.b, W.x, W.r, W.p, W.q,
+                                        W.z, (float *)nullptr, W.scal));
     }
     return AMG_OK;
 }
@@ -3241,9 +3243,14 @@ int krylov_solve(Hierarchy *h, Workspace &W, cudaStream_t s, SolveResult *res) {
             if (W.scal_h->done) break;
             continue;
         }
-        if (status != AMG_OK) break;
+        // the cluster launch ends with the true residual of its final x
+        const bool tr_done = cluster && W.scal_h->tr_fresh;
+        if (status != AMG_OK) {
+            fresh = tr_done;
+            break;
+        }
         // converged on the recursive residual: check the true residual
-        AMG_TRY(true_residual(h, W, s));
+        if (!tr_done) AMG_TRY(true_residual(h, W, s));
         fresh = true;
         const double tr = W.scal_h->tr;
         if (tr <= W.scal_h->tol2) break;
