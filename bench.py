@@ -42,6 +42,10 @@ WORKLOADS = {
     # name: (generator, solver, description)
     "diffusion3d_grf_128": (lambda: M.diffusion3d_grf(N=128), "PCG",
                             "3D 7-point variable-coefficient diffusion, 128^3 cells, log k GRF (sigma 1, ell 0.1)"),
+    # the same kernels on 1.4M rows (each pass still larger than L2): the size the
+    # per-kernel ncu counters are captured on, scaled to 128^3 by stored entries
+    "diffusion3d_grf_112": (lambda: M.diffusion3d_grf(N=112), "PCG",
+                            "3D 7-point variable-coefficient diffusion, 112^3 cells, log k GRF (sigma 1, ell 0.1)"),
     "poisson2d_64": (lambda: M.poisson2d_64(), "PCG", "2D 5-point Poisson, 64x64"),
     "diffusion2d_logk_512": (lambda: M.diffusion2d_logk(N=512), "PCG", "2D diffusion, 512x512 cells, log k ~ N(0,1)"),
     "convdiff3d_upwind_160": (lambda: M.convdiff3d_upwind(N=160), "BICGSTAB",
