@@ -434,14 +434,16 @@ def trace_pass(s, b, x, g, lam, dA, steps, dev, step=None, workload: str = ""):
 
 def plan_summary(s) -> dict:
     """The streaming plans setup chose for the levels that stream:
-    {"L<l>": {op: "<layout>/<rows per tile>x<threads per row>/s<stages>"}}."""
+    {"L<l>": {op: "<layout>/<rows per tile>x<threads per row>/s<stages>[/df]"}}
+    (/df: the product runs in double-FP32 arithmetic)."""
     out = {}
     for l in range(s.info().nlevels):
         ops = {}
         for op in ("pre", "post", "P", "R") + (("krylov",) if l == 0 else ()):
             p = s.plan(l, op)
             if p["layout"]:
-                ops[op] = f'{p["layout"]}/{p["rows_per_tile"]}x{p["threads_per_row"]}/s{p["stages"]}'
+                ops[op] = (f'{p["layout"]}/{p["rows_per_tile"]}x{p["threads_per_row"]}/s{p["stages"]}'
+                           + ("/df" if p.get("df") else ""))
         if ops:
             out[f"L{l}"] = ops
     return out

@@ -126,6 +126,11 @@ typedef struct {
                          node repeats them on the GPU until the solve is done (one host
                          synchronisation per solve); 0: graphs of four iterations polled by the host
                          (for profilers that cannot see inside graphs with conditional nodes) */
+    int outer_product; /* arithmetic of the mixed form's Krylov product q = A p on a streamed finest
+                         level: -1 (default) chosen at setup by timing both on the chosen plan; 0 FP64;
+                         1 double-FP32 (A's values and p as pairs of binary32 numbers, each product and
+                         row sum accurate to a few 2^-48 of sum_j |a_ij p_j|; q, dot products, norms,
+                         updates and the true residual stay FP64).  Ignored in the FP64 form */
 } amg_config;
 
 typedef struct {
@@ -208,14 +213,18 @@ int amg_get_aggregates(amg_handle h, int level, int *agg);
 
 /* The streaming plan chosen at setup for one operator of level l: which = 0
  * A_l W (pre-smoothing), 1 P_l (prolongation), 2 R_l (restriction), 3 A_l
- * (post-smoothing), 4 the FP64 A of the Krylov products (level 0 only).
+ * (post-smoothing), 4 the A of the Krylov products (level 0 only).
  * plan[0] = layout (AMG_LAYOUT_CSR, _WINDOWED, _SLICED_ELL or _ELL_DIRECT; 0 when the
  * operator has no streaming plan and runs on the row-vector kernels),
  * plan[1] = rows per tile, plan[2] = threads per row, plan[3] = tiles,
  * plan[4] = pipeline stages (tiles in flight per CTA; 1 for _ELL_DIRECT,
- * which stages nothing; 0 without a plan).
+ * which stages nothing; 0 without a plan), plan[5] = 1 when the operator's
+ * product runs in double-FP32 arithmetic (which = 4 in the mixed form, where
+ * setup found it faster than FP64: A's values and p as pairs of binary32
+ * numbers, each product and row sum accurate to a few 2^-48 of
+ * sum_j |a_ij p_j|), else 0.
  * Errors: AMG_ERR_ARG (NULL, level or which out of range). */
-int amg_get_plan(amg_handle h, int level, int which, int plan[5]);
+int amg_get_plan(amg_handle h, int level, int which, int plan[6]);
 
 /* Per-kernel tracing of the solve phase.  The paper reports wall-clock times
  * only; this is the library's own instrumentation.  amg_profile(h, 1) clears

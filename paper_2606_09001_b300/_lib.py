@@ -36,7 +36,7 @@ class AmgConfig(C.Structure):
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int),
                 ("max_restarts", C.c_int), ("precision", C.c_int), ("symmetric", C.c_int), ("layout", C.c_int),
                 ("adjoint_reuse", C.c_int), ("amg_type", C.c_int), ("fuse_coarse", C.c_int),
-                ("device_loop", C.c_int)]
+                ("device_loop", C.c_int), ("outer_product", C.c_int)]
 
 
 class AmgInfo(C.Structure):

@@ -284,13 +284,14 @@ class Solver:
     def plan(self, l: int, op: str) -> dict:
         """The streaming plan setup chose for one operator of level l (op in
         PLAN_OPS): layout name (None: row-vector kernels), rows per tile,
-        threads per row, tiles, pipeline stages."""
-        out = (C.c_int * 5)()
+        threads per row, tiles, pipeline stages, and whether the product runs
+        in double-FP32 arithmetic (the mixed form's Krylov product)."""
+        out = (C.c_int * 6)()
         rc = self._L.amg_get_plan(self._h, l, self.PLAN_OPS[op], out)
         if rc < 0:
             raise AMGError(rc, "amg_get_plan")
         return {"layout": self.LAYOUT_NAMES[out[0]], "rows_per_tile": out[1], "threads_per_row": out[2],
-                "tiles": out[3], "stages": out[4]}
+                "tiles": out[3], "stages": out[4], "df": bool(out[5])}
 
 
 class BatchedSolver(Solver):

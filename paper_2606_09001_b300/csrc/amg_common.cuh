@@ -91,6 +91,8 @@ struct Scratch {
 // Sparse matrices
 // ---------------------------------------------------------------------------
 
+struct DF;
+
 struct DevCSR {
     int nrows = 0, ncols = 0;
     long long nnz = 0;
@@ -98,6 +100,7 @@ struct DevCSR {
     int *ci = nullptr;
     double *v = nullptr;
     float *v32 = nullptr;  // FP32 copy (mixed precision), or null
+    DF *vdf = nullptr;     // double-FP32 copy (the finest level of the mixed form), or null
 };
 
 // ---------------------------------------------------------------------------
@@ -279,6 +282,11 @@ struct Hierarchy {
     int cpcg_cta = 0;
     std::vector<unsigned char> cpcg_args;
     int cpcg_smem = 0;
+    // mixed form: 1 when the outer product q = A p runs in double-FP32
+    // arithmetic (A's values and p split into FP32 pairs), chosen at setup by
+    // timing it against the FP64 product on the same plan; the two timings (us)
+    int krylov_df = 0;
+    float krylov_us[2] = {0.f, 0.f};
 };
 
 // ---------------------------------------------------------------------------
@@ -401,15 +409,27 @@ __device__ __forceinline__ float f64_to_f32_rn(double d) {
 // and the two cross terms, and a row sum adds the hi parts with an exact
 // two-sum and the remainders in FP32.  Each q_i is accurate to a few 2^-48 of
 // sum_j |a_ij p_j| (FP64: 2^-53); dot products, norms and vector updates stay
-// FP64.  (The single-system product is not FP64-bound -- one FMA per entry --
-// and stays FP64.)
-struct DF {
+// FP64.  The single-system product does one FMA per entry; on a 7-point
+// operator that still keeps the FP64 pipe busier than DRAM, so the mixed form
+// times it both ways at setup and keeps the faster.
+struct __align__(8) DF {
     float hi, lo;
     DF() = default;
     __host__ __device__ constexpr DF(int z) : hi((float)z), lo(0.f) {}
     __host__ __device__ constexpr DF(float h, float l) : hi(h), lo(l) {}
 };
 static_assert(sizeof(DF) == 8, "a DF is two packed binary32 numbers");
+
+// Read-only-path loads for the value types the streaming kernels take: the
+// built-in types through __ldg, a DF as one 8-byte load.
+template <typename T>
+__device__ __forceinline__ T ldgv(const T *p) {
+    return __ldg(p);
+}
+__device__ __forceinline__ DF ldgv(const DF *p) {
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return DF(v.x, v.y);
+}
 
 // d as hi + lo (hi = RN32(d), lo = RN32(d - hi); the difference is exact in FP64)
 __device__ __forceinline__ DF df_split(double d) {

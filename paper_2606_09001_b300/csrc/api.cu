@@ -39,7 +39,8 @@ int check_config(const amg_config &c) {
         c.symmetric < -1 || c.symmetric > 1 || c.layout < AMG_LAYOUT_AUTO || c.layout > AMG_LAYOUT_TILES ||
         (c.adjoint_reuse != 0 && c.adjoint_reuse != 1) ||
         (c.amg_type != AMG_TYPE_AGGREGATION && c.amg_type != AMG_TYPE_CLASSICAL) ||
-        c.fuse_coarse < 0 || c.fuse_coarse > 2 || (c.device_loop != 0 && c.device_loop != 1)) {
+        c.fuse_coarse < 0 || c.fuse_coarse > 2 || (c.device_loop != 0 && c.device_loop != 1) ||
+        c.outer_product < -1 || c.outer_product > 1) {
         set_last_error("invalid amg_config");
         return AMG_ERR_ARG;
     }
@@ -170,6 +171,7 @@ int amg_config_default(amg_config *c) {
     c->amg_type = AMG_TYPE_AGGREGATION;
     c->fuse_coarse = 1;
     c->device_loop = 1;
+    c->outer_product = -1;
     return AMG_OK;
 }
 
@@ -400,7 +402,7 @@ int amg_widen_f32(const float *in, double *out, long long n, void *cuda_stream) 
     return AMG_OK;
 }
 
-int amg_get_plan(amg_handle h, int level, int which, int plan[5]) {
+int amg_get_plan(amg_handle h, int level, int which, int plan[6]) {
     if (!h || !plan || level < 0 || level >= h->H.nlevels || which < 0 || which > 4 || (which == 4 && level != 0))
         return AMG_ERR_ARG;
     const Level &lv = h->H.L[level];
@@ -417,6 +419,7 @@ int amg_get_plan(amg_handle h, int level, int which, int plan[5]) {
     // CSR tiles: three stages of 4-byte values at 512 threads, else two
     const bool v4 = which != 4 && h->H.cfg.precision == AMG_PRECISION_MIXED;
     plan[4] = p.rt == 0 ? 0 : p.direct ? 1 : (p.ell || p.c16) ? p.stages : (p.nt == 512 && v4 ? 3 : 2);
+    plan[5] = which == 4 && h->H.krylov_df ? 1 : 0;
     return AMG_OK;
 }
 

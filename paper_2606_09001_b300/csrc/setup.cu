@@ -160,6 +160,13 @@ __global__ void k_fill_double(double *a, long long n, double v) {
         a[i] = v;
 }
 
+// d[k] = v[k] as an unevaluated FP32 pair hi + lo (the double-FP32 copy of the
+// finest operator for the mixed form's outer product).
+__global__ void k_to_df(const double *__restrict__ v, DF *__restrict__ d, long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        d[k] = df_split(v[k]);
+}
+
 __global__ void k_to_f32(const double *in, float *out, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = __double2float_rn(in[i]);
@@ -1309,6 +1316,10 @@ static int finish_build(Hierarchy *h, bool precond, cudaStream_t s) {
                 AMG_TRY(ar.alloc(&Lv.R.v32, (size_t)std::max(1LL, Lv.R.nnz)));
                 k_to_f32<<<grid_for(Lv.R.nnz), 256, 0, s>>>(Lv.R.v, Lv.R.v32, Lv.R.nnz);
             }
+            if (k == 0) {
+                AMG_TRY(ar.alloc(&Lv.A.vdf, (size_t)std::max(1LL, Lv.A.nnz)));
+                k_to_df<<<grid_for(Lv.A.nnz), 256, 0, s>>>(Lv.A.v, Lv.A.vdf, Lv.A.nnz);
+            }
             AMG_LAUNCH_CHECK();
             AMG_TRY(ar.alloc(&Lv.t32, (size_t)nl));
             if (k > 0) {
@@ -2011,6 +2022,7 @@ static int refresh_derived(Hierarchy *h, cudaStream_t s) {
         if (Lv.ahat) k_scale_cols<<<grid_for(nl), 256, 0, s>>>(nl, Lv.A.rp, Lv.A.ci, Lv.A.v, Lv.w, Lv.ahat, Lv.ahat32);
         if (mixed) {
             k_to_f32<<<grid_for(Lv.A.nnz), 256, 0, s>>>(Lv.A.v, Lv.A.v32, Lv.A.nnz);
+            if (Lv.A.vdf) k_to_df<<<grid_for(Lv.A.nnz), 256, 0, s>>>(Lv.A.v, Lv.A.vdf, Lv.A.nnz);
             k_to_f32<<<grid_for(nl), 256, 0, s>>>(Lv.w, Lv.w32, nl);
             if (!last) {
                 k_to_f32<<<grid_for(Lv.P.nnz), 256, 0, s>>>(Lv.P.v, Lv.P.v32, Lv.P.nnz);

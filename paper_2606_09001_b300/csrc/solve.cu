@@ -381,28 +381,38 @@ __global__ void __launch_bounds__(BLOCK) k_pcg_init(int n, const double *__restr
 }
 
 // p = z + beta p
-__global__ void __launch_bounds__(BLOCK) k_pcg_p(int n, const double *__restrict__ z, double *p, const DevScalars *sc) {
+__global__ void __launch_bounds__(BLOCK) k_pcg_p(int n, const double *__restrict__ z, double *p, DF *p2,
+                                                 const DevScalars *sc) {
     pdl_wait();
     pdl_trigger();
     if (sc->done) return;
     const double beta = sc->beta;
     // pairs of entries as 16-byte accesses (the workspace vectors are
-    // allocation-aligned), then the odd last entry
+    // allocation-aligned), then the odd last entry; p2 (when given) takes p
+    // split into FP32 pairs for the double-FP32 product
     const int n2 = n >> 1, g0 = blockIdx.x * BLOCK + threadIdx.x, gs = gridDim.x * BLOCK;
     const double2 *z2 = reinterpret_cast<const double2 *>(z);
-    double2 *p2 = reinterpret_cast<double2 *>(p);
-    if (beta == 0.0) {  // first step after a (re)start: p = z exactly
-        for (int i = g0; i < n2; i += gs) p2[i] = z2[i];
-        if ((n & 1) && g0 == 0) p[n - 1] = z[n - 1];
-    } else {
-        for (int i = g0; i < n2; i += gs) {
-            const double2 zv = z2[i];
-            double2 pv = p2[i];
+    double2 *pp2 = reinterpret_cast<double2 *>(p);
+    for (int i = g0; i < n2; i += gs) {
+        const double2 zv = z2[i];
+        double2 pv;
+        if (beta == 0.0) {  // first step after a (re)start: p = z exactly
+            pv = zv;
+        } else {
+            pv = pp2[i];
             pv.x = zv.x + beta * pv.x;
             pv.y = zv.y + beta * pv.y;
-            p2[i] = pv;
         }
-        if ((n & 1) && g0 == 0) p[n - 1] = z[n - 1] + beta * p[n - 1];
+        pp2[i] = pv;
+        if (p2) {
+            const DF a = df_split(pv.x), b = df_split(pv.y);
+            reinterpret_cast<float4 *>(p2)[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        }
+    }
+    if ((n & 1) && g0 == 0) {
+        const double pv = beta == 0.0 ? z[n - 1] : z[n - 1] + beta * p[n - 1];
+        p[n - 1] = pv;
+        if (p2) p2[n - 1] = df_split(pv);
     }
 }
 
@@ -797,6 +807,7 @@ int workspace_init(Workspace &W, int n) {
     double **vecs[] = {&W.b, &W.x, &W.r, &W.z, &W.p, &W.q, &W.rh, &W.v, &W.ph, &W.s, &W.sh, &W.t, &W.aux};
     for (double **pp : vecs) AMG_TRY(a.alloc(pp, (size_t)n));
     AMG_TRY(a.alloc(&W.r32, (size_t)n));
+    AMG_TRY(a.alloc(&W.p2, (size_t)n));
     AMG_TRY(a.alloc(&W.scal, 1));
     W.part_cap = num_sms() * 8;
     AMG_TRY(a.alloc(&W.part, (size_t)3 * W.part_cap));
@@ -1034,6 +1045,42 @@ struct OpFin {
     __device__ void reduce(double (&acc)[2]) const {
         double tot[2];
         if (reduce_last<2, NT>(acc, part, cap, counter, tot) && threadIdx.x == 0) finish_spmv<SF>(sc, tot);
+    }
+};
+
+// q = A p in double-FP32 arithmetic with p.q -> alpha (the mixed form's
+// outer product where the setup found it faster): A's values and the gathered
+// p are FP32 pairs (p2, written with p), each row's sum is a double-FP32
+// number converted to FP64 once, and q, p.q and alpha are FP64 as in OpFin.
+struct OpFinDF {
+    DevScalars *sc;
+    const double *p;
+    const DF *p2;
+    double *y;
+    double *part;
+    int cap;
+    unsigned *counter;
+    struct Pre {
+        double d;
+    };
+    __device__ bool done() const { return sc->done != 0; }
+    __device__ DF gather(int j) const { return p2[j]; }
+    using GX = DF;
+    __device__ const GX *gsrc() const { return p2; }
+    __device__ Pre load(int i) const { return Pre{__ldg(p + i)}; }
+    static constexpr bool SELF = false;
+    static constexpr int NROWV = 0, ROWV_BYTES = 0;
+    __device__ Pre load_rest(int i) const { return load(i); }
+    __device__ void put_self(Pre &, GX) const {}
+    __device__ void finish(int i, DF s, const Pre &pr, double (&acc)[2]) const {
+        const double q = df_value(s);
+        y[i] = q;
+        acc[0] += pr.d * q;
+    }
+    template <int NT>
+    __device__ void reduce(double (&acc)[2]) const {
+        double tot[2];
+        if (reduce_last<2, NT>(acc, part, cap, counter, tot) && threadIdx.x == 0) finish_spmv<SF_PCG_ALPHA>(sc, tot);
     }
 };
 
@@ -1999,6 +2046,7 @@ static int ell_bind(Hierarchy *h, cudaStream_t s) {
         }
     }
     AMG_TRY(ell_bind_one(h, h->L[0].sa64, h->L[0].A.v, 8, s));
+    if (mixed && h->L[0].A.vdf) AMG_TRY(ell_bind_one(h, h->L[0].sa64, h->L[0].A.vdf, 8, s));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
     return AMG_OK;
 }
@@ -2939,6 +2987,17 @@ static int spmv_fin(Hierarchy *h, Workspace &W, const char *name, const double *
                     cudaStream_t s, float *y32 = nullptr) {
     const int n = h->n, cap = W.part_cap;
     const Level &l0 = h->L[0];
+    if constexpr (SF == SF_PCG_ALPHA) {
+        if (h->krylov_df && x == W.p) {
+            // the operation's algorithmic bytes, as for the FP64 product (this
+            // launch also reads p itself for p.q beside the split copy it gathers)
+            TRACE(name, 0, csr_bytes(l0.A, 8) + 16.0 * n);
+            const OpFinDF op{W.scal, W.p, W.p2, y, W.part, cap, W.counter};
+            if (l0.sa64.direct) AMG_TRY(stream_launch_direct<DF>(l0.sa64, n, l0.A.vdf, op, s));
+            else AMG_TRY(stream_launch_ell<DF>(l0.sa64, n, l0.A.vdf, op, &W.scal->copy_timeout, s));
+            return AMG_OK;
+        }
+    }
     TRACE(name, 0, csr_bytes(l0.A, 8) + 16.0 * n + (SF == SF_PCG_ALPHA ? 0.0 : 8.0 * n));
     if (l0.sa64.rt) {
         AMG_TRY(stream_launch<double>(l0.sa64, n, l0.A.rp, l0.A.ci, l0.A.v,
@@ -2958,7 +3017,8 @@ static int pcg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
     AMG_TRY(vcycle(h, W, W.r, W.z, FIN_PCG_BETA, s, mixed ? W.r32 : nullptr));
     {
         TRACE("pcg_p", 0, 24.0 * n);
-        AMG_TRY(launch_k(k_pcg_p, stream_grid(n, cap), BLOCK, 0, s, n, W.z, W.p, W.scal));
+        AMG_TRY(launch_k(k_pcg_p, stream_grid(n, cap), BLOCK, 0, s, n, W.z, W.p, h->krylov_df ? W.p2 : nullptr,
+                         W.scal));
     }
     AMG_TRY(spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s));
     {
@@ -2975,7 +3035,8 @@ static int cg_iteration(Hierarchy *h, Workspace &W, cudaStream_t s) {
     const int n = h->n, cap = W.part_cap;
     {
         TRACE("pcg_p", 0, 24.0 * n);
-        AMG_TRY(launch_k(k_pcg_p, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.p, W.scal));
+        AMG_TRY(launch_k(k_pcg_p, stream_grid(n, cap), BLOCK, 0, s, n, W.r, W.p, h->krylov_df ? W.p2 : nullptr,
+                         W.scal));
     }
     AMG_TRY(spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s));
     {
@@ -3420,10 +3481,64 @@ static int tune_cycle_precision(Hierarchy *h, Workspace &W, cudaStream_t s) {
 
 static int autotune_layouts(Hierarchy *h, Workspace &W, cudaStream_t s);
 
-// The autotuner: the streaming plans (autotune_layouts), then, for the mixed
-// form of a tail-only hierarchy, the cycle's precision.
+// The mixed form's outer product q = A p: its plan launched in FP64 and in
+// double-FP32 arithmetic (same plan and operands), the faster kept.  Each
+// launch starts from reset scalars, so a p.Ap <= 0 on the constant vector
+// stops none of the others.
+static int tune_krylov_df(Hierarchy *h, Workspace &W, cudaStream_t s) {
+    h->krylov_df = 0;
+    const Level &l0 = h->L[0];
+    if (h->cfg.precision != AMG_PRECISION_MIXED || h->cfg.outer_product == 0 || !l0.A.vdf ||
+        !(l0.sa64.ell || l0.sa64.direct) || !ell_values(l0.sa64, l0.A.vdf))
+        return AMG_OK;
+    if (h->cfg.outer_product == 1) {
+        h->krylov_df = 1;
+        return AMG_OK;
+    }
+    const int n = h->n;
+    k_fill<double><<<256, 256, 0, s>>>((size_t)n, 1.0, W.p);
+    k_fill<DF><<<256, 256, 0, s>>>((size_t)n, DF(1.f, 0.f), W.p2);
+    AMG_LAUNCH_CHECK();
+    cudaEvent_t e0, e1;
+    AMG_CUDA_TRY(cudaEventCreate(&e0));
+    AMG_CUDA_TRY(cudaEventCreate(&e1));
+    float best[2] = {1e30f, 1e30f};
+    int rc = AMG_OK;
+    for (int df = 0; df < 2 && rc >= 0; ++df) {
+        h->krylov_df = df;
+        auto one = [&]() -> int {
+            AMG_TRY(set_control(W, s, 0, AMG_OK, 0, h->cfg.max_iter, 1));
+            return spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s);
+        };
+        for (int k = 0; k < 2 && rc >= 0; ++k) rc = one();
+        for (int trial = 0; trial < 3 && rc >= 0; ++trial) {
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < 10 && rc >= 0; ++k) rc = one();
+            cudaEventRecord(e1, s);
+            if (rc >= 0 && cudaEventSynchronize(e1) == cudaSuccess) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                best[df] = std::min(best[df], t);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    AMG_TRY(rc);
+    AMG_TRY(set_control(W, s, 1, AMG_OK, 0, h->cfg.max_iter, 1));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    h->krylov_us[0] = 100.f * best[0];  // ms for 10 launches -> us per launch
+    h->krylov_us[1] = 100.f * best[1];
+    h->krylov_df = best[1] < 0.97f * best[0] ? 1 : 0;
+    return AMG_OK;
+}
+
+// The autotuner: the streaming plans (autotune_layouts), then, in the mixed
+// form, the outer product's arithmetic and, for a tail-only hierarchy, the
+// cycle's precision.
 int autotune_plans(Hierarchy *h, Workspace &W, cudaStream_t s) {
     AMG_TRY(autotune_layouts(h, W, s));
+    AMG_TRY(tune_krylov_df(h, W, s));
     return tune_cycle_precision(h, W, s);
 }
 

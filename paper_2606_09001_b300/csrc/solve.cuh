@@ -51,6 +51,7 @@ struct Workspace {
     double *rh = nullptr, *v = nullptr, *ph = nullptr, *s = nullptr, *sh = nullptr, *t = nullptr;
     double *aux = nullptr;                                 // adjoint: forward solution x
     float *r32 = nullptr;                                  // mixed PCG: FP32 copy of r (the V-cycle's input)
+    DF *p2 = nullptr;                                      // mixed PCG: p split into FP32 pairs (double-FP32 product)
     DevScalars *scal = nullptr;                            // device
     DevScalars *scal_h = nullptr;                          // pinned host mirror
     double *part = nullptr;                                // per-block partial sums (3 x part_cap)

@@ -770,7 +770,7 @@ __global__ void __launch_bounds__(NT, 2) k_stream_ell(int n, int rt, int cap, in
                     }
                 }
                 if (row < n) {
-                    if (Op::SELF) op.put_self(pre, dl0 >= 0 ? xs[dl0 + rl] : __ldg(op.gsrc() + row));
+                    if (Op::SELF) op.put_self(pre, dl0 >= 0 ? xs[dl0 + rl] : ldgv(op.gsrc() + row));
                     op.finish(row, sum, pre, acc);
                 }
                 sl += CONSUMER_WARPS;
@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(NT) k_ell_direct(int n, int nsl, const int *__
 #pragma unroll
         for (int q = 0; q < U; ++q)
             if (q < wdv) {
-                av[q] = __ldg(ev + s0v + q * 32 + lane);
+                av[q] = ldgv(ev + s0v + q * 32 + lane);
                 cv[q] = __ldg(ecol + s0v + q * 32 + lane);
             }
     };
@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(NT) k_ell_direct(int n, int nsl, const int *__
 #pragma unroll
                 for (int q = 0; q < U; ++q)
                     if (u + q < wd) {
-                        a[q] = __ldg(ev + s0 + (u + q) * 32 + lane);
+                        a[q] = ldgv(ev + s0 + (u + q) * 32 + lane);
                         c[q] = __ldg(ecol + s0 + (u + q) * 32 + lane);
                     }
 #pragma unroll

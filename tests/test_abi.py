@@ -40,7 +40,7 @@ def test_config_defaults_and_status_strings():
     assert c.solver == 0 and c.omega == pytest.approx(2 / 3) and c.theta == 0.08
     assert c.coarse_max == 64 and c.rtol == 1e-8 and c.precision == 0 and c.symmetric == -1
     assert c.layout == 0 and c.adjoint_reuse == 0 and c.amg_type == 0 and c.fuse_coarse == 1
-    assert c.device_loop == 1
+    assert c.device_loop == 1 and c.outer_product == -1
     assert L.amg_config_default(None) == _lib.AMG_ERR_ARG
     for code in (0, 1, 2, 3, 4, -1, -2, -3, -4, -5, -6, -7):
         assert _lib.status_string(code) != "unknown status"
