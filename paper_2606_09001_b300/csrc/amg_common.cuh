@@ -284,9 +284,13 @@ struct Hierarchy {
     int cpcg_smem = 0;
     // mixed form: 1 when the outer product q = A p runs in double-FP32
     // arithmetic (A's values and p split into FP32 pairs), chosen at setup by
-    // timing it against the FP64 product on the same plan; the two timings (us)
+    // timing; krylov_us: a PCG iteration with the cycle's plan family's FP64
+    // product and with the kept variant (us)
     int krylov_df = 0;
     float krylov_us[2] = {0.f, 0.f};
+    // the direct family's plan of the Krylov product, kept when the tile
+    // family wins the cycle (a candidate for the product alone), else rt = 0
+    StreamPlan alt_sa64;
 };
 
 // ---------------------------------------------------------------------------

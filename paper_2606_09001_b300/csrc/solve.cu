@@ -3482,54 +3482,84 @@ static int tune_cycle_precision(Hierarchy *h, Workspace &W, cudaStream_t s) {
 static int autotune_layouts(Hierarchy *h, Workspace &W, cudaStream_t s);
 
 // The mixed form's outer product q = A p: its plan launched in FP64 and in
-// double-FP32 arithmetic (same plan and operands), the faster kept.  Each
-// launch starts from reset scalars, so a p.Ap <= 0 on the constant vector
-// stops none of the others.
+// double-FP32 arithmetic, and, when the tile family won the cycle, the direct
+// family's plan of the product both ways too.  Whole PCG iterations decide
+// (the cycle, p = z + beta p -- which also writes the split p for the
+// double-FP32 product -- the product and the update, launched as the solve
+// launches them): a faster product alone measured slower iterations when it
+// added the split's writes or put direct blocks between the cycle's tile
+// rings.  The chosen plan in FP64 is kept unless another is 3 % faster.  Each
+// iteration starts from reset scalars, so a finisher that stops on the
+// constant vectors (p.Ap <= 0) stops none of the others.
 static int tune_krylov_df(Hierarchy *h, Workspace &W, cudaStream_t s) {
     h->krylov_df = 0;
-    const Level &l0 = h->L[0];
-    if (h->cfg.precision != AMG_PRECISION_MIXED || h->cfg.outer_product == 0 || !l0.A.vdf ||
-        !(l0.sa64.ell || l0.sa64.direct) || !ell_values(l0.sa64, l0.A.vdf))
+    Level &l0 = h->L[0];
+    const StreamPlan alt = h->alt_sa64;
+    h->alt_sa64 = StreamPlan{};
+    auto df_ok = [&](const StreamPlan &p) { return (p.ell || p.direct) && l0.A.vdf && ell_values(p, l0.A.vdf); };
+    // the double-FP32 product serves PCG and CG (BiCGStab's products stay FP64)
+    const bool cg = h->cfg.solver == AMG_SOLVER_CG;
+    if (h->cfg.precision != AMG_PRECISION_MIXED || h->cfg.outer_product == 0 || !df_ok(l0.sa64) ||
+        !(cg || h->cfg.solver == AMG_SOLVER_PCG))
         return AMG_OK;
     if (h->cfg.outer_product == 1) {
         h->krylov_df = 1;
         return AMG_OK;
     }
+    struct Cand {
+        StreamPlan plan;
+        int df;
+    };
+    std::vector<Cand> cands = {{l0.sa64, 0}, {l0.sa64, 1}};
+    if (alt.direct && ell_values(alt, l0.A.v)) {
+        cands.push_back({alt, 0});
+        if (df_ok(alt)) cands.push_back({alt, 1});
+    }
     const int n = h->n;
-    k_fill<double><<<256, 256, 0, s>>>((size_t)n, 1.0, W.p);
+    for (double *v : {W.p, W.q, W.r, W.b}) k_fill<double><<<256, 256, 0, s>>>((size_t)n, 1.0, v);
+    k_fill<double><<<256, 256, 0, s>>>((size_t)n, 0.0, W.x);
+    k_fill<float><<<256, 256, 0, s>>>((size_t)n, 1.0f, W.r32);
     k_fill<DF><<<256, 256, 0, s>>>((size_t)n, DF(1.f, 0.f), W.p2);
     AMG_LAUNCH_CHECK();
     cudaEvent_t e0, e1;
     AMG_CUDA_TRY(cudaEventCreate(&e0));
     AMG_CUDA_TRY(cudaEventCreate(&e1));
-    float best[2] = {1e30f, 1e30f};
+    std::vector<float> best(cands.size(), 1e30f);
+    const StreamPlan chosen = l0.sa64;
     int rc = AMG_OK;
-    for (int df = 0; df < 2 && rc >= 0; ++df) {
-        h->krylov_df = df;
+    for (size_t q = 0; q < cands.size() && rc >= 0; ++q) {
+        l0.sa64 = cands[q].plan;
+        h->krylov_df = cands[q].df;
         auto one = [&]() -> int {
-            AMG_TRY(set_control(W, s, 0, AMG_OK, 0, h->cfg.max_iter, 1));
-            return spmv_fin<SF_PCG_ALPHA>(h, W, "spmv_pq", W.p, W.q, W.p, s);
+            AMG_TRY(set_control(W, s, 0, AMG_OK, cg ? 0 : 1, h->cfg.max_iter, 1));
+            return cg ? cg_iteration(h, W, s) : pcg_iteration(h, W, s);
         };
         for (int k = 0; k < 2 && rc >= 0; ++k) rc = one();
         for (int trial = 0; trial < 3 && rc >= 0; ++trial) {
             cudaEventRecord(e0, s);
-            for (int k = 0; k < 10 && rc >= 0; ++k) rc = one();
+            for (int k = 0; k < 4 && rc >= 0; ++k) rc = one();
             cudaEventRecord(e1, s);
             if (rc >= 0 && cudaEventSynchronize(e1) == cudaSuccess) {
                 float t = 0.f;
                 cudaEventElapsedTime(&t, e0, e1);
-                best[df] = std::min(best[df], t);
+                best[q] = std::min(best[q], t);
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    l0.sa64 = chosen;
+    h->krylov_df = 0;
     AMG_TRY(rc);
     AMG_TRY(set_control(W, s, 1, AMG_OK, 0, h->cfg.max_iter, 1));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
-    h->krylov_us[0] = 100.f * best[0];  // ms for 10 launches -> us per launch
-    h->krylov_us[1] = 100.f * best[1];
-    h->krylov_df = best[1] < 0.97f * best[0] ? 1 : 0;
+    size_t pick = 0;
+    for (size_t q = 1; q < cands.size(); ++q)
+        if (best[q] < 0.97f * best[0] && best[q] < best[pick]) pick = q;
+    l0.sa64 = cands[pick].plan;
+    h->krylov_df = cands[pick].df;
+    h->krylov_us[0] = 250.f * best[0];  // ms for 4 iterations -> us per iteration
+    h->krylov_us[1] = 250.f * best[pick];
     return AMG_OK;
 }
 
@@ -3570,7 +3600,11 @@ static int autotune_layouts(Hierarchy *h, Workspace &W, cudaStream_t s) {
     AMG_TRY(time_rounds(h, W, s, &ms_tiles));
     set_plans(h, direct);
     AMG_TRY(time_rounds(h, W, s, &ms_direct));
-    if (ms_tiles <= ms_direct) set_plans(h, tiles);
+    if (ms_tiles <= ms_direct) {
+        set_plans(h, tiles);
+        h->alt_sa64 = direct[4];  // level 0's Krylov plan (the order of for_each_plan)
+        if (!h->alt_sa64.direct) h->alt_sa64 = StreamPlan{};
+    }
     h->plan_family_ms[0] = ms_tiles;
     h->plan_family_ms[1] = ms_direct;
     return AMG_OK;
