@@ -282,6 +282,12 @@ struct Hierarchy {
     int cpcg_cta = 0;
     std::vector<unsigned char> cpcg_args;
     int cpcg_smem = 0;
+    // The same kernel running one V-cycle from the tail's first level when
+    // that level is not the finest (vmode): CTAs (0: the tail kernel is used),
+    // table (FP32 cycle in the mixed form) and dynamic shared memory.
+    int vtail_cta = 0;
+    std::vector<unsigned char> vtail_args;
+    int vtail_smem = 0;
     // mixed form: 1 when the outer product q = A p runs in double-FP32
     // arithmetic (A's values and p split into FP32 pairs), chosen at setup by
     // timing; krylov_us: a PCG iteration with the cycle's plan family's FP64

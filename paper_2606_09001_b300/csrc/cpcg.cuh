@@ -27,6 +27,12 @@
 // peer's output of the phase before, which the peer sends after it has read
 // the buffer, so a phase never overwrites what a slower CTA still gathers.
 //
+// V-cycle mode (vmode = 1): the same phases from a coarse level t down and
+// back, for a hierarchy whose levels above t stream: level t's right-hand
+// side comes from global memory (written by the restriction above) and its
+// result goes back there (read by the prolongation above); no reduction and
+// no data-dependent branch, so every CTA runs the same phases.
+//
 // Reductions.  A CTA's partial dot products go into a slot per CTA in every
 // CTA's shared memory the same way; each CTA adds the slots in rank order,
 // so every CTA holds the same bits and takes the same decision (beta, alpha,
@@ -83,6 +89,12 @@ struct CLevel {
 template <typename TM>
 struct CArgs {
     int nlev;                  // levels 0 .. nlev-1; the last one is the dense coarsest
+    // 1: one V-cycle from a coarse level t (table level 0) -- its right-hand
+    // side vb and result vx in global memory, the levels above it run as
+    // separate passes -- instead of a whole PCG solve
+    int vmode;
+    const TM *vb;
+    TM *vx;
     int cta;
     int buf_off[2], buf_bytes; // the two staging buffers
     int x_off, r_off, p_off, q_off, z_off;  // the CTA's level-0 slices of the FP64 Krylov vectors
@@ -299,9 +311,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
     // rank, which the constant cache serves slowly
     __shared__ __align__(16) CArgs<TM> a;
     cg::cluster_group cl = cg::this_cluster();
-    pdl_wait();
-    pdl_trigger();
-    if (sc->done) return;  // uniform: every thread of every CTA reads the same word before any barrier
+    // What depends on no earlier kernel -- the table, the mbarriers, the bulk
+    // copies of the operator slices and the smoother weights, all written at
+    // setup -- is issued before the wait on the preceding kernel (launched
+    // with programmatic stream serialisation, this overlaps its end).
     {
         static_assert(sizeof(CArgs<TM>) % 4 == 0, "table copied in words");
         const int *src = reinterpret_cast<const int *>(&ga);
@@ -311,21 +324,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
     }
     const int c = (int)cl.block_rank(), C = a.cta, nl = a.nlev;
     const int tid = threadIdx.x;
-    const double tol2 = sc->tol2;
-    const int max_iter = sc->max_iter, flexible = sc->flexible, first0 = sc->first;
-    if (tid == 0) {
-        S.rz = sc->rz;
-        S.alpha = sc->alpha;
-        S.beta = sc->beta;
-        S.pq = sc->pq;
-        S.rr = sc->rr;
-        S.iters = sc->iters;
-        S.first = first0;
-        S.status = AMG_OK;
-        S.stop = 0;
-        S.have_rr = 0;
-        bad = 0;
-    }
 
     // bulk copies of the CTA's operator slices (warp 0), one mbarrier
     if (tid < 32) {
@@ -354,21 +352,50 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
             }
         }
     }
+    for (int k = 0; k < nl - 1; ++k) {
+        const CLevel<TM> &lv = a.L[k];
+        TM *w = reinterpret_cast<TM *>(smem + lv.w_off);
+        for (int i = lv.r0[c] + tid; i < lv.r0[c + 1]; i += THREADS) w[i - lv.r0[c]] = lv.w[i];
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (sc->done) {
+        // uniform (every thread of every CTA reads the same word, before any
+        // cluster barrier); the copies land before the shared memory is released
+        stream::mbar_wait(&bar, 0);
+        return;
+    }
+    const double tol2 = sc->tol2;
+    const int max_iter = sc->max_iter, flexible = sc->flexible, first0 = sc->first;
+    if (tid == 0) {
+        S.rz = sc->rz;
+        S.alpha = sc->alpha;
+        S.beta = sc->beta;
+        S.pq = sc->pq;
+        S.rr = sc->rr;
+        S.iters = sc->iters;
+        S.first = first0;
+        S.status = AMG_OK;
+        S.stop = 0;
+        S.have_rr = 0;
+        bad = 0;
+    }
+
     // the CTA's slices of the vectors
     const int r0 = a.L[0].r0[c], r1 = a.L[0].r0[c + 1];
     double *X = reinterpret_cast<double *>(smem + a.x_off), *R = reinterpret_cast<double *>(smem + a.r_off);
     double *P = reinterpret_cast<double *>(smem + a.p_off), *Q = reinterpret_cast<double *>(smem + a.q_off);
     double *Z = reinterpret_cast<double *>(smem + a.z_off);
-    for (int i = r0 + tid; i < r1; i += THREADS) {
-        X[i - r0] = gx[i];
-        R[i - r0] = gr[i];
-        P[i - r0] = first0 ? 0.0 : gp[i];
-        Q[i - r0] = first0 ? 0.0 : gq[i];
-    }
-    for (int k = 0; k < nl - 1; ++k) {
-        const CLevel<TM> &lv = a.L[k];
-        TM *w = reinterpret_cast<TM *>(smem + lv.w_off);
-        for (int i = lv.r0[c] + tid; i < lv.r0[c + 1]; i += THREADS) w[i - lv.r0[c]] = lv.w[i];
+    if (a.vmode) {
+        TM *b0 = reinterpret_cast<TM *>(smem + a.L[0].b_off);
+        for (int i = r0 + tid; i < r1; i += THREADS) b0[i - r0] = a.vb[i];
+    } else {
+        for (int i = r0 + tid; i < r1; i += THREADS) {
+            X[i - r0] = gx[i];
+            R[i - r0] = gr[i];
+            P[i - r0] = first0 ? 0.0 : gp[i];
+            Q[i - r0] = first0 ? 0.0 : gq[i];
+        }
     }
     // every CTA has started and initialised its mbarriers: remote stores may begin
     cl.sync();
@@ -427,12 +454,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
         if (tid == AUX_WARP * 32) arm_relaxed(&rbar[j], (uint32_t)(8 * nv * (C - 1)));
     };
 
-    // the first pre-smoothing gathers W b with b = r
+    // the first pre-smoothing gathers W b with b = r (a V-cycle: level t's b)
     {
         arm_vec(0, a.L[0].r0, (int)sizeof(TM));
         TM *ys = reinterpret_cast<TM *>(buf(0));
         const TM *w0 = reinterpret_cast<const TM *>(smem + a.L[0].w_off);
-        for (int i = r0 + tid; i < r1; i += THREADS) ys[i] = w0[i - r0] * fcvt<TM>(R[i - r0]);
+        const TM *b0 = reinterpret_cast<const TM *>(smem + a.L[0].b_off);
+        for (int i = r0 + tid; i < r1; i += THREADS)
+            ys[i] = w0[i - r0] * (a.vmode ? b0[i - r0] : fcvt<TM>(R[i - r0]));
         exchange(0, r0, r1, (int)sizeof(TM));
     }
     const bool loaded = __syncthreads_and(stream::mbar_wait(&bar, 0)) != 0;
@@ -455,7 +484,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
                 TM *ys = reinterpret_cast<TM *>(buf(nb));
                 if (loaded)
                     rows<TM, TM, TM>(lv.A, s0, s1, c, smem, xs, [&](int i, TM s) {
-                        const TM bi = k == 0 ? fcvt<TM>(R[i - s0]) : bk[i - s0];
+                        const TM bi = k == 0 && !a.vmode ? fcvt<TM>(R[i - s0]) : bk[i - s0];
                         ys[i] = bi - s;
                     });
                 exchange(nb, s0, s1, (int)sizeof(TM));
@@ -507,7 +536,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
             const int s0 = lv.r0[c], s1 = lv.r0[c + 1];
             const TM *wk = reinterpret_cast<const TM *>(smem + lv.w_off);
             const TM *bk = reinterpret_cast<const TM *>(smem + lv.b_off);
-            auto bof = [&](int i) { return k == 0 ? fcvt<TM>(R[i - s0]) : bk[i - s0]; };
+            auto bof = [&](int i) { return k == 0 && !a.vmode ? fcvt<TM>(R[i - s0]) : bk[i - s0]; };
             {
                 // t = W b + P x_next
                 const int nb = cur ^ 1;
@@ -529,6 +558,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
                     rows<TM, TM, TM>(lv.A, s0, s1, c, smem, ts,
                                      [&](int i, TM s) { ys[i] = ts[i] + wk[i - s0] * (bof(i) - s); });
                 exchange(nb, s0, s1, (int)sizeof(TM));
+            } else if (a.vmode) {
+                // the cycle's result, read by the prolongation of the level above
+                if (loaded)
+                    rows<TM, TM, TM>(lv.A, s0, s1, c, smem, ts,
+                                     [&](int i, TM s) { a.vx[i] = ts[i] + wk[i - s0] * (bof(i) - s); });
             } else {
                 // r.z, z.q and the last update's ||r||^2 in one reduction
                 arm_red(0, 3);
@@ -573,7 +607,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
                 stop = S.stop != 0;
             }
         }
-        if (stop) break;
+        if (stop || a.vmode) break;
         // p = z + beta p
         {
             const int nb = cur ^ 1;
@@ -634,7 +668,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
     }
     // the true residual of the final x: x to every CTA, then r = b - A x
     // (the FP64 operator) and ||r||^2
-    const bool true_res = S.status == AMG_OK || S.status == AMG_MAXIT;
+    const bool true_res = !a.vmode && (S.status == AMG_OK || S.status == AMG_MAXIT);
     if (true_res) {
         {
             const int nb = cur ^ 1;
@@ -658,15 +692,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
     }
     if ((bad & 2) && tid == 0) atomicOr(&sc->copy_timeout, 4);
     // the state back to global memory for the true residual and a restart
-    for (int i = r0 + tid; i < r1; i += THREADS) {
-        gx[i] = X[i - r0];
-        gr[i] = R[i - r0];
-        gp[i] = P[i - r0];
-        gq[i] = Q[i - r0];
-        gz[i] = Z[i - r0];
-        if (gr32) gr32[i] = f64_to_f32_rn(R[i - r0]);
-    }
-    if (c == 0 && tid == 0) {
+    if (!a.vmode)
+        for (int i = r0 + tid; i < r1; i += THREADS) {
+            gx[i] = X[i - r0];
+            gr[i] = R[i - r0];
+            gp[i] = P[i - r0];
+            gq[i] = Q[i - r0];
+            gz[i] = Z[i - r0];
+            if (gr32) gr32[i] = f64_to_f32_rn(R[i - r0]);
+        }
+    if (c == 0 && tid == 0 && !a.vmode) {
         sc->rz = S.rz;
         sc->alpha = S.alpha;
         sc->beta = S.beta;

@@ -2314,6 +2314,7 @@ static int tail_cluster_size(int smem) {
 }
 
 static int cpcg_prepare(Hierarchy *h);
+static int vtail_prepare(Hierarchy *h);
 
 // Chooses the first level of the fused tail: every level from it down is
 // small -- no streaming plan, fewer than 16384 rows and at most 400K stored
@@ -2344,6 +2345,7 @@ int tail_prepare(Hierarchy *h, cudaStream_t) {
             h->tail_smem64 = s64;
             h->tail_smem32 = s32;
             h->tail_start = t;
+            AMG_TRY(vtail_prepare(h));
             return cpcg_prepare(h);
         }
     }
@@ -2458,24 +2460,34 @@ static long long round16(long long b) { return (b + 15) / 16 * 16; }
 // copy in the mixed form); collapsed = 0 takes every level, 0 .. nlevels-1,
 // with the coarsest level's dense inverse -- the same preconditioner up to
 // rounding, the collapse being exact.
+//
+// vmode = 1 builds the table of one V-cycle from level t (the kernel's level
+// 0; no Krylov vectors or outer product), with level t's b and x in global
+// memory.
 template <typename TM>
-static int build_cpcg_table(Hierarchy *h, int cta, int collapsed, std::vector<unsigned char> &out,
+static int build_cpcg_table(Hierarchy *h, int cta, int collapsed, int t, int vmode, std::vector<unsigned char> &out,
                             int *smem_bytes) {
     const bool mixed = sizeof(TM) == 4;
     *smem_bytes = -1;
-    const int nl = collapsed ? h->nsolve : h->nlevels;
+    const int nl = (collapsed ? h->nsolve : h->nlevels) - t;
     const bool dense32 = collapsed && mixed && h->nsolve < h->nlevels && h->cinv32;
     if (nl < 2 || nl > cpcg::MAX_LEVELS) return AMG_OK;
     cpcg::CArgs<TM> a;
     memset(&a, 0, sizeof(a));
     a.nlev = nl;
     a.cta = cta;
+    a.vmode = vmode;
+    if (vmode) {
+        const Level &lt = h->L[t];
+        a.vb = (const TM *)(mixed ? (const void *)lt.b32 : (const void *)lt.b);
+        a.vx = (TM *)(mixed ? (void *)lt.x32 : (void *)lt.x);
+    }
     std::vector<std::vector<int>> rpA(nl), rpP(nl), rpR(nl);
     for (int k = 0; k < nl; ++k) {
         cpcg::CLevel<TM> &d = a.L[k];
         d.w_off = d.b_off = -1;
         if (k < nl - 1) {
-            const Level &lv = h->L[k];
+            const Level &lv = h->L[t + k];
             d.n = lv.A.nrows;
             AMG_TRY(host_rp(lv.A, rpA[k]));
             AMG_TRY(host_rp(lv.P, rpP[k]));
@@ -2483,19 +2495,19 @@ static int build_cpcg_table(Hierarchy *h, int cta, int collapsed, std::vector<un
             cpcg_split(d.n, &rpA[k], cta, d.r0);
             d.w = (const TM *)(mixed ? (const void *)lv.w32 : (const void *)lv.w);
         } else {
-            d.n = collapsed ? h->nc : h->L[k].A.nrows;
+            d.n = collapsed ? h->nc : h->L[t + k].A.nrows;
             cpcg_split(d.n, nullptr, cta, d.r0);
         }
     }
     for (int k = 0; k < nl - 1; ++k) {
-        const Level &lv = h->L[k];
+        const Level &lv = h->L[t + k];
         cpcg::CLevel<TM> &d = a.L[k];
         auto vals = [&](const DevCSR &m) { return (const TM *)(mixed ? (const void *)m.v32 : (const void *)m.v); };
         cpcg_op(d.A, &lv.A, vals(lv.A), &rpA[k], d.r0, cta, lv.A.ncols);
         cpcg_op(d.P, &lv.P, vals(lv.P), &rpP[k], d.r0, cta, lv.P.ncols);
         cpcg_op(d.R, &lv.R, vals(lv.R), &rpR[k], a.L[k + 1].r0, cta, lv.R.ncols);
     }
-    cpcg_op(a.K, &h->L[0].A, (const double *)h->L[0].A.v, &rpA[0], a.L[0].r0, cta, h->L[0].A.ncols);
+    if (!vmode) cpcg_op(a.K, &h->L[0].A, (const double *)h->L[0].A.v, &rpA[0], a.L[0].r0, cta, h->L[0].A.ncols);
     const int nd = a.L[nl - 1].n;
     cpcg_op(a.C, (const DevCSR *)nullptr, (const double *)(collapsed ? h->cinv : h->cinv_last), nullptr,
             a.L[nl - 1].r0, cta, nd);
@@ -2505,9 +2517,9 @@ static int build_cpcg_table(Hierarchy *h, int cta, int collapsed, std::vector<un
     a.C32.copy = dense32 ? 3 : 0;
     // the outer operator shares A_0's row pointers and indices (and in the
     // FP64 form its values)
-    a.K.copy = mixed ? 2 : 0;
+    a.K.copy = mixed && !vmode ? 2 : 0;
 
-    long long vec_bytes = 8LL * h->n;
+    long long vec_bytes = vmode ? 0 : 8LL * h->n;
     for (int k = 0; k < nl; ++k) vec_bytes = std::max<long long>(vec_bytes, (long long)a.L[k].n * sizeof(TM));
     const long long bufb = round16(vec_bytes);
     long long off = 0;
@@ -2520,7 +2532,7 @@ static int build_cpcg_table(Hierarchy *h, int cta, int collapsed, std::vector<un
         for (int c = 0; c < cta; ++c) m = std::max(m, a.L[k].r0[c + 1] - a.L[k].r0[c]);
         return m;
     };
-    const long long kb = round16(8LL * slice_rows(0));
+    const long long kb = vmode ? 0 : round16(8LL * slice_rows(0));
     int *koffs[5] = {&a.x_off, &a.r_off, &a.p_off, &a.q_off, &a.z_off};
     for (int *o : koffs) {
         *o = (int)off;
@@ -2530,7 +2542,7 @@ static int build_cpcg_table(Hierarchy *h, int cta, int collapsed, std::vector<un
         const long long vb = round16((long long)sizeof(TM) * slice_rows(k));
         a.L[k].w_off = (int)off;
         off += vb;
-        if (k > 0) {
+        if (k > 0 || vmode) {
             a.L[k].b_off = (int)off;
             off += vb;
         }
@@ -2556,10 +2568,12 @@ static int build_cpcg_table(Hierarchy *h, int cta, int collapsed, std::vector<un
     }
     place(a.C, a.L[nl - 1].r0);
     place(a.C32, a.L[nl - 1].r0);
-    a.K.rp_off = a.L[0].A.rp_off;
-    a.K.ci_off = a.L[0].A.ci_off;
-    if (mixed) place(a.K, a.L[0].r0);
-    else a.K.v_off = a.L[0].A.v_off;  // the FP64 cycle's A_0 itself
+    if (!vmode) {
+        a.K.rp_off = a.L[0].A.rp_off;
+        a.K.ci_off = a.L[0].A.ci_off;
+        if (mixed) place(a.K, a.L[0].r0);
+        else a.K.v_off = a.L[0].A.v_off;  // the FP64 cycle's A_0 itself
+    }
     if (off > CPCG_SMEM_MAX) return AMG_OK;
     for (int c = 0; c < cta; ++c) {
         long long tx = 0;
@@ -2625,8 +2639,8 @@ static int cpcg_prepare(Hierarchy *h) {
         for (int cs : {16, 8}) {
             std::vector<unsigned char> args;
             int smem = -1;
-            if (mixed) AMG_TRY(build_cpcg_table<float>(h, cs, collapsed, args, &smem));
-            else AMG_TRY(build_cpcg_table<double>(h, cs, collapsed, args, &smem));
+            if (mixed) AMG_TRY(build_cpcg_table<float>(h, cs, collapsed, 0, 0, args, &smem));
+            else AMG_TRY(build_cpcg_table<double>(h, cs, collapsed, 0, 0, args, &smem));
             if (smem < 0) continue;
             if (mixed ? cpcg_fits<float>(cs, smem) : cpcg_fits<double>(cs, smem)) {
                 h->cpcg_cta = cs;
@@ -2636,6 +2650,62 @@ static int cpcg_prepare(Hierarchy *h) {
             }
         }
     }
+    return AMG_OK;
+}
+
+// Prepares one-V-cycle cluster launches from the tail's first level when it is
+// a coarse level (the finest level streams): collapsed first, on 16 then 8
+// CTAs, as for the whole solve.
+static int vtail_prepare(Hierarchy *h) {
+    h->vtail_cta = 0;
+    const int t = h->tail_start;
+    if (t <= 0 || h->nsys > 0) return AMG_OK;
+    const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
+    for (int collapsed : {1, 0}) {
+        if (!collapsed && h->nsolve == h->nlevels) break;
+        if (collapsed && h->nsolve - t < 2) continue;
+        for (int cs : {16, 8}) {
+            std::vector<unsigned char> args;
+            int smem = -1;
+            if (mixed) AMG_TRY(build_cpcg_table<float>(h, cs, collapsed, t, 1, args, &smem));
+            else AMG_TRY(build_cpcg_table<double>(h, cs, collapsed, t, 1, args, &smem));
+            if (smem < 0) continue;
+            if (mixed ? cpcg_fits<float>(cs, smem) : cpcg_fits<double>(cs, smem)) {
+                h->vtail_cta = cs;
+                h->vtail_args = args;
+                h->vtail_smem = smem;
+                return AMG_OK;
+            }
+        }
+    }
+    return AMG_OK;
+}
+
+// One V-cycle from the tail's first level as one cluster launch.
+template <typename TM>
+static int launch_vtail(Hierarchy *h, Workspace &W, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->vtail_cta);
+    cfg.blockDim = dim3(cpcg::THREADS);
+    cfg.dynamicSmemBytes = h->vtail_smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = h->vtail_cta;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    if (!cpcg_fits<TM>(h->vtail_cta, h->vtail_smem)) {
+        set_last_error("V-cycle cluster: %d bytes of shared memory refused", h->vtail_smem);
+        return AMG_ERR_CUDA;
+    }
+    const auto &args = *(const cpcg::CArgs<TM> *)h->vtail_args.data();
+    AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<TM>, args, (const double *)nullptr, (double *)nullptr,
+                                    (double *)nullptr, (double *)nullptr, (double *)nullptr, (double *)nullptr,
+                                    (float *)nullptr, W.scal));
     return AMG_OK;
 }
 
@@ -2659,13 +2729,15 @@ static int launch_cpcg(Hierarchy *h, Workspace &W, cudaStream_t s) {
     cfg.blockDim = dim3(cpcg::THREADS);
     cfg.dynamicSmemBytes = h->cpcg_smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = h->cpcg_cta;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     TRACE("cluster_pcg", 0, cpcg_bytes(h));
     if (mixed) {
         if (!cpcg_fits<float>(h->cpcg_cta, h->cpcg_smem)) {
@@ -2884,7 +2956,12 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
     }
     if (h->tail_start > 0) {
         TRACE("tail", tl, tail_bytes(h, vb));
-        AMG_TRY(launch_tail<TM>(h, W, nullptr, nullptr, nullptr, 0, s));
+        // the cluster kernel's V-cycle where its table fits (built for the
+        // form's cycle type), else the tail kernel
+        if (h->vtail_cta && (sizeof(TM) == 4) == (h->cfg.precision == AMG_PRECISION_MIXED))
+            AMG_TRY(launch_vtail<TM>(h, W, s));
+        else
+            AMG_TRY(launch_tail<TM>(h, W, nullptr, nullptr, nullptr, 0, s));
     } else if (mm > 0) {
         TRACE("mid", mm, mid_bytes(h, mm, vb));
         AMG_TRY(launch_mid<TM>(h, W, mm, s));
