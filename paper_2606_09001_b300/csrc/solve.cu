@@ -2955,13 +2955,15 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         AMG_LAUNCH_CHECK();
     }
     if (h->tail_start > 0) {
-        TRACE("tail", tl, tail_bytes(h, vb));
         // the cluster kernel's V-cycle where its table fits (built for the
         // form's cycle type), else the tail kernel
-        if (h->vtail_cta && (sizeof(TM) == 4) == (h->cfg.precision == AMG_PRECISION_MIXED))
+        if (h->vtail_cta && (sizeof(TM) == 4) == (h->cfg.precision == AMG_PRECISION_MIXED)) {
+            TRACE("cluster_cycle", tl, tail_bytes(h, vb));
             AMG_TRY(launch_vtail<TM>(h, W, s));
-        else
+        } else {
+            TRACE("tail", tl, tail_bytes(h, vb));
             AMG_TRY(launch_tail<TM>(h, W, nullptr, nullptr, nullptr, 0, s));
+        }
     } else if (mm > 0) {
         TRACE("mid", mm, mid_bytes(h, mm, vb));
         AMG_TRY(launch_mid<TM>(h, W, mm, s));

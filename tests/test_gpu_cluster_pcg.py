@@ -162,3 +162,43 @@ def test_cluster_solve_not_taken(case):
     assert "cluster_pcg" not in launched(s, lambda: s.solve(dev(b)))
     x, info = s.solve(dev(b))
     assert info.status == 0 and info.rel_res_true <= 1e-8
+
+
+# tails that start below the finest level: 32,761 rows (streamed) -> 4,648 ->
+# dense 427; the cluster kernel runs the cycle from level 1 (V-cycle mode)
+CYCLE_CASES = {
+    "logk2d_181": lambda: M.diffusion2d_logk(N=181).A,
+    "poisson2d_181": lambda: M.poisson2d(181),
+}
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+@pytest.mark.parametrize("name", list(CYCLE_CASES))
+def test_cluster_cycle_from_a_coarse_level(name, precision):
+    A = CYCLE_CASES[name]()
+    rng = np.random.default_rng(21)
+    r = rng.uniform(-1, 1, A.n)
+    s = solver(A, {"precision": precision})
+    names = launched(s, lambda: s.vcycle(dev(r)))
+    assert "cluster_cycle" in names and "tail" not in names, names
+    z = s.vcycle(dev(r)).cpu().numpy()
+    zo = O.Hierarchy(A).vcycle(r)
+    tol = 1e-12 if precision == "FP64" else 1e-5
+    assert np.linalg.norm(z - zo) <= tol * np.linalg.norm(zo)
+    # the per-pass cycle of the same hierarchy (fuse_coarse = 0)
+    p = solver(A, {"precision": precision, "fuse_coarse": 0})
+    zp = p.vcycle(dev(r)).cpu().numpy()
+    assert np.linalg.norm(z - zp) <= tol * np.linalg.norm(zp)
+    # solve and adjoint against the oracle
+    b, g = rng.uniform(-1, 1, A.n), rng.uniform(-1, 1, A.n)
+    ho = O.Hierarchy(A, {"rtol": 1e-13})
+    xt, _ = ho.solve(b)
+    lam_t, _, _ = ho.adjoint(xt, g, A.nnz)
+    x, info = s.solve(dev(b))
+    assert info.status == 0 and info.rel_res_true <= 1e-8
+    lam, _, ainfo = s.adjoint(x, dev(g))
+    assert ainfo.status == 0
+    x, lam = x.cpu().numpy(), lam.cpu().numpy()
+    assert np.linalg.norm(x - xt) <= 1e-7 * np.linalg.norm(xt)
+    assert np.abs(x - xt).max() <= 1e-7 * np.abs(xt).max()
+    assert np.linalg.norm(lam - lam_t) <= 1e-7 * np.linalg.norm(lam_t)
