@@ -302,6 +302,34 @@ __global__ void __launch_bounds__(BT) kb_dense(const int *r0s, const int *ms, co
     }
 }
 
+// Adds n values v(0), ..., v(n-1) with one warp in a fixed order (lane-strided
+// partial sums, then a shuffle tree); every lane returns the total.  FP64
+// adds are slow on this GPU, so the block's warps share a reduction's pairs
+// rather than a few threads adding long serial chains.
+template <class F>
+__device__ __forceinline__ double warp_sum_n(int n, F v) {
+    double a = 0.0;
+    for (int t = threadIdx.x & 31; t < n; t += 32) a += v(t);
+    return warp_sum(a);
+}
+
+// The system's totals from its chunks' partials, in its last chunk: one warp
+// per (value, right-hand side) pair; tot[q] valid in threads tid < K for
+// right-hand side tid.
+template <int NV>
+__device__ __forceinline__ void system_totals(int sys, const BDev &W, double (&tot)[NV]) {
+    __shared__ double s_tot[NV][K];
+    const int c0 = W.sys_ch0[sys], nc = W.sys_nch[sys];
+    for (int pr = threadIdx.x >> 5; pr < NV * K; pr += BT / 32) {
+        const int q = pr / K, r = pr % K;
+        const double a = warp_sum_n(nc, [&](int c) { return __ldcg(&W.part[((size_t)(c0 + c) * K + r) * 2 + q]); });
+        if ((threadIdx.x & 31) == 0) s_tot[q][r] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < K)
+        for (int q = 0; q < NV; ++q) tot[q] = s_tot[q][threadIdx.x];
+}
+
 // Block reduction of acc[NV] per right-hand side (thread r = tid % K), the
 // chunk's partials, and in the last chunk of the system the per-system totals
 // (returned in tot[q], valid in threads tid < K for right-hand side tid).
@@ -311,12 +339,11 @@ __device__ bool chunk_reduce(double (&acc)[NV], int chunk, int sys, const BDev &
     __shared__ bool s_last;
     for (int q = 0; q < NV; ++q) sh[q][threadIdx.x] = acc[q];
     __syncthreads();
-    if (threadIdx.x < K) {
-        for (int q = 0; q < NV; ++q) {
-            double a = 0.0;
-            for (int t = threadIdx.x; t < BT; t += K) a += sh[q][t];
-            W.part[((size_t)chunk * K + threadIdx.x) * 2 + q] = a;
-        }
+    // one warp per (value, right-hand side) pair: entries r, r + K, ...
+    for (int pr = threadIdx.x >> 5; pr < NV * K; pr += BT / 32) {
+        const int q = pr / K, r = pr % K;
+        const double a = warp_sum_n(BT / K, [&](int u) { return sh[q][r + K * u]; });
+        if ((threadIdx.x & 31) == 0) W.part[((size_t)chunk * K + r) * 2 + q] = a;
     }
     __threadfence();
     __syncthreads();
@@ -324,14 +351,7 @@ __device__ bool chunk_reduce(double (&acc)[NV], int chunk, int sys, const BDev &
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
-    if (threadIdx.x < K) {
-        const int c0 = W.sys_ch0[sys], nc = W.sys_nch[sys];
-        for (int q = 0; q < NV; ++q) {
-            double a = 0.0;
-            for (int c = c0; c < c0 + nc; ++c) a += __ldcg(&W.part[((size_t)c * K + threadIdx.x) * 2 + q]);
-            tot[q] = a;
-        }
-    }
+    system_totals<NV>(sys, W, tot);
     if (threadIdx.x == 0) W.ticket[sys] = 0u;
     return true;
 }
@@ -345,7 +365,7 @@ __device__ __forceinline__ void deactivate(const BDev &W, int p, int status) {
 
 // chunk_reduce for threads that hold G right-hand sides each (acc[q][g] for
 // right-hand side r0 + g): per right-hand side, the block's values are added
-// in row-slot order.
+// over the row slots by one warp.
 template <int NV, int G>
 __device__ bool chunk_reduce_g(double (&acc)[NV][G], int chunk, int sys, const BDev &W, double (&tot)[NV]) {
     constexpr int SLOTS = BT / (K / G);
@@ -357,12 +377,11 @@ __device__ bool chunk_reduce_g(double (&acc)[NV][G], int chunk, int sys, const B
 #pragma unroll
         for (int g = 0; g < G; ++g) sh[q][r0 + g][slot] = acc[q][g];
     __syncthreads();
-    if (threadIdx.x < K) {
-        for (int q = 0; q < NV; ++q) {
-            double a = 0.0;
-            for (int t = 0; t < SLOTS; ++t) a += sh[q][threadIdx.x][t];
-            W.part[((size_t)chunk * K + threadIdx.x) * 2 + q] = a;
-        }
+    // one warp per (value, right-hand side) pair, over its slots
+    for (int pr = threadIdx.x >> 5; pr < NV * K; pr += BT / 32) {
+        const int q = pr / K, r = pr % K;
+        const double a = warp_sum_n(SLOTS, [&](int t) { return sh[q][r][t]; });
+        if ((threadIdx.x & 31) == 0) W.part[((size_t)chunk * K + r) * 2 + q] = a;
     }
     __threadfence();
     __syncthreads();
@@ -370,14 +389,7 @@ __device__ bool chunk_reduce_g(double (&acc)[NV][G], int chunk, int sys, const B
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
-    if (threadIdx.x < K) {
-        const int c0 = W.sys_ch0[sys], nc = W.sys_nch[sys];
-        for (int q = 0; q < NV; ++q) {
-            double a = 0.0;
-            for (int c = c0; c < c0 + nc; ++c) a += __ldcg(&W.part[((size_t)c * K + threadIdx.x) * 2 + q]);
-            tot[q] = a;
-        }
-    }
+    system_totals<NV>(sys, W, tot);
     if (threadIdx.x == 0) W.ticket[sys] = 0u;
     return true;
 }
@@ -480,8 +492,12 @@ __global__ void __launch_bounds__(BT) kb_spmv0(BDev W, const int *rp, const int 
     if (!TRUE_RES && W.sys_nact[sys] == 0) return;
     const int r0 = (threadIdx.x % (K / G)) * G;
     double acc[1][G];
+    DF accdf[G];  // the mixed form's p.q partials, double-FP32 (one FP64 conversion a thread)
 #pragma unroll
-    for (int g = 0; g < G; ++g) acc[0][g] = 0.0;
+    for (int g = 0; g < G; ++g) {
+        acc[0][g] = 0.0;
+        accdf[g] = DF(0);
+    }
     for (int il = threadIdx.x / (K / G); il < rows; il += BT / (K / G)) {
         const int i = r0c + il;
         const size_t e0 = (size_t)i * K + r0;
@@ -509,7 +525,7 @@ __global__ void __launch_bounds__(BT) kb_spmv0(BDev W, const int *rp, const int 
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 q[g] = df_value(sd[g]);
-                acc[0][g] += df_value(pv[g]) * q[g];
+                accdf[g] += pv[g] * sd[g];
             }
             st_g<G>(W.Q + e0, q);
         } else {
@@ -521,6 +537,9 @@ __global__ void __launch_bounds__(BT) kb_spmv0(BDev W, const int *rp, const int 
             st_g<G>(W.Q + e0, sv);
         }
     }
+    if (!TRUE_RES && W.adf)
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[0][g] = df_value(accdf[g]);
     double tot[1];
     if (chunk_reduce_g<1, G>(acc, chunk, sys, W, tot) && threadIdx.x < K) {
         const int p = sys * K + threadIdx.x;
