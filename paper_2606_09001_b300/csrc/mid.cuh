@@ -188,27 +188,33 @@ __device__ void p_post(const MLevel<TM> &lv) {
 
 #undef MID_ROWS
 
-// x = M b, the dense end: one warp per row of 16-byte vectors, b staged in
-// shared memory in FP64 (zero beyond m), FP32 entries widened on the integer
-// pipes, FP64 accumulation; a lane's partial sum runs over its vectors in
-// order, then the warp's sum (the same order as the dense kernel of the
-// per-level cycle).
+// x = M b, the dense end of the cycle (M m x m, rows padded to ld entries
+// with zeros): one warp per row reading 16-byte vectors, U of a lane's loads
+// of the row in flight together; b is staged in sb (DENSE_LD doubles of
+// shared memory; zero beyond m).  The mixed cycle (FP32 entries, FP32
+// vectors) sums in FP32, two chains a lane, like its other passes and like
+// the cluster kernel's FP32 coarse end; otherwise b is staged and summed in
+// FP64, FP32 entries widened on the integer pipes (exact, like any widening)
+// so that the FP64 pipe runs only the products' FMAs.  A lane's partial sums
+// run over its vectors in order whatever U, then the warp's sum: the
+// per-level cycle's kernel and the cooperative mid kernel give the same bits.
 constexpr int DENSE_LD = 2048;
 
-template <typename TMAT, typename TV>
-__device__ void p_dense(int m, int ld, const TMAT *__restrict__ M, const TV *b, TV *x, double *sb) {
+template <int U, typename TMAT, typename TV>
+__device__ void dense_rows(int m, int ld, const TMAT *__restrict__ M, const TV *b, TV *x, void *sbuf) {
+    constexpr bool F32 = std::is_same<TMAT, float>::value && std::is_same<TV, float>::value;
+    using TS = typename std::conditional<F32, float, double>::type;
+    TS *sb = reinterpret_cast<TS *>(sbuf);
 #pragma unroll 8
-    for (int j = threadIdx.x; j < ld; j += blockDim.x) sb[j] = j < m ? fcvt<double>(b[j]) : 0.0;
+    for (int j = threadIdx.x; j < ld; j += blockDim.x) sb[j] = j < m ? fcvt<TS>(b[j]) : TS(0);
     __syncthreads();
     using V = typename std::conditional<sizeof(TMAT) == 4, float4, double2>::type;
     constexpr int VW = sizeof(V) / sizeof(TMAT);
     const int lane = threadIdx.x & 31;
     const int nv = ld / VW;
-    const double2 *bd = reinterpret_cast<const double2 *>(sb);
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += (gridDim.x * blockDim.x) >> 5) {
         const V *row = reinterpret_cast<const V *>(M + (size_t)i * ld);
-        double s = 0.0;
-        constexpr int U = 8;  // the per-pass kernel takes 16; the lane's order over q is the same
+        TS s = 0, s1 = 0;
         for (int q0 = lane; q0 < nv; q0 += 32 * U) {
             V a[U];
 #pragma unroll
@@ -220,19 +226,26 @@ __device__ void p_dense(int m, int ld, const TMAT *__restrict__ M, const TV *b, 
             for (int u = 0; u < U; ++u) {
                 const int q = q0 + 32 * u;
                 if (q < nv) {
-                    if constexpr (VW == 4) {
+                    if constexpr (F32) {
+                        const float4 c = reinterpret_cast<const float4 *>(sb)[q];
+                        s = fmaf(a[u].x, c.x, s);
+                        s1 = fmaf(a[u].y, c.y, s1);
+                        s = fmaf(a[u].z, c.z, s);
+                        s1 = fmaf(a[u].w, c.w, s1);
+                    } else if constexpr (VW == 4) {
+                        const double2 *bd = reinterpret_cast<const double2 *>(sb);
                         const double2 c0 = bd[2 * q], c1 = bd[2 * q + 1];
                         s += f32_to_f64(a[u].x) * c0.x + f32_to_f64(a[u].y) * c0.y + f32_to_f64(a[u].z) * c1.x +
                              f32_to_f64(a[u].w) * c1.y;
                     } else {
-                        const double2 c = bd[q];
+                        const double2 c = reinterpret_cast<const double2 *>(sb)[q];
                         s += a[u].x * c.x + a[u].y * c.y;
                     }
                 }
             }
         }
-        s = warp_sum(s);
-        if (lane == 0) x[i] = (TV)s;
+        s = group_sum<32>(s + s1);
+        if (lane == 0) x[i] = fcvt<TV>(s);
     }
 }
 
@@ -285,7 +298,7 @@ __global__ void __launch_bounds__(THREADS) k_mid(const __grid_constant__ MArgs<T
         MID_VEC(lv.vec_r, (p_spmv<V, TM>(lv.nc, lv.rrp, lv.rci, lv.rv, lv.t, bn)));
     }
     if (!sync()) return;
-    p_dense<TMAT, TM>(a.dm, a.dld, reinterpret_cast<const TMAT *>(a.M), a.db, a.dx, sb);
+    dense_rows<8, TMAT, TM>(a.dm, a.dld, reinterpret_cast<const TMAT *>(a.M), a.db, a.dx, sb);
     for (int k = a.nlev - 1; k >= 0; --k) {
         const MLevel<TM> &lv = a.L[k];
         const TM *xn = k + 1 < a.nlev ? a.L[k + 1].x : a.dx;

@@ -287,58 +287,17 @@ __global__ void __launch_bounds__(BLOCK) k_coarse(int m, const double *__restric
     }
 }
 
-// The dense operator of the coarse end of the cycle: x = M b (M m x m, rows
-// padded to ld entries with zeros), one warp per row reading 16-byte vectors
-// with all of a lane's loads of the row in flight together; b is staged into
-// shared memory in FP64 (zero beyond m); FP64 accumulation.  FP32 entries of
-// M are widened on the integer pipes (exact, like any widening), so the FP64
-// pipe runs only the products' FMAs.
-constexpr int DENSE_MAX_LD = 2048;
-
+// The dense operator of the coarse end of the cycle, x = M b (dense_rows:
+// one warp per row, 16 16-byte loads of a lane in flight, a 2048-float row in
+// one round).
 template <typename TMAT, typename TV>
 __global__ void __launch_bounds__(BLOCK) k_dense_apply(int m, int ld, const TMAT *__restrict__ M,
                                                        const TV *__restrict__ b, TV *__restrict__ x, const int *done) {
     pdl_wait();
     pdl_trigger();
     if (*done) return;
-    __shared__ __align__(16) double sb[DENSE_MAX_LD];
-#pragma unroll 8
-    for (int j = threadIdx.x; j < ld; j += BLOCK) sb[j] = j < m ? fcvt<double>(b[j]) : 0.0;
-    __syncthreads();
-    using V = typename std::conditional<sizeof(TMAT) == 4, float4, double2>::type;
-    constexpr int VW = sizeof(V) / sizeof(TMAT);
-    const int lane = threadIdx.x & 31;
-    const int nv = ld / VW;
-    const double2 *bd = reinterpret_cast<const double2 *>(sb);
-    for (int i = (blockIdx.x * BLOCK + threadIdx.x) >> 5; i < m; i += (gridDim.x * BLOCK) >> 5) {
-        const V *row = reinterpret_cast<const V *>(M + (size_t)i * ld);
-        double s = 0.0;
-        constexpr int U = 16;  // 16-byte vectors per lane in flight: a 2048-float row in one round
-        for (int q0 = lane; q0 < nv; q0 += 32 * U) {
-            V a[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int q = q0 + 32 * u;
-                if (q < nv) a[u] = __ldg(row + q);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int q = q0 + 32 * u;
-                if (q < nv) {
-                    if constexpr (VW == 4) {
-                        const double2 c0 = bd[2 * q], c1 = bd[2 * q + 1];
-                        s += f32_to_f64(a[u].x) * c0.x + f32_to_f64(a[u].y) * c0.y + f32_to_f64(a[u].z) * c1.x +
-                             f32_to_f64(a[u].w) * c1.y;
-                    } else {
-                        const double2 c = bd[q];
-                        s += a[u].x * c.x + a[u].y * c.y;
-                    }
-                }
-            }
-        }
-        s = warp_sum(s);
-        if (lane == 0) x[i] = (TV)s;
-    }
+    __shared__ __align__(16) double sb[mid::DENSE_LD];
+    mid::dense_rows<16, TMAT, TV>(m, ld, M, b, x, sb);
 }
 
 // ---------------------------------------------------------------------------
@@ -2594,20 +2553,29 @@ static int build_cpcg_table(Hierarchy *h, int cta, int collapsed, int t, int vmo
     return AMG_OK;
 }
 
-// Whether k_cpcg<TM> schedules a cluster of `cta` CTAs with smem bytes of
-// dynamic shared memory (the kernel's limit only grows, as the tail's).
+// Raises k_cpcg<TM>'s dynamic shared-memory limit to at least smem (the
+// limit belongs to the kernel and only grows, as the tail's) and allows
+// 16-CTA clusters.
 template <typename TM>
-static bool cpcg_fits(int cta, int smem) {
+static bool cpcg_smem_limit(int smem) {
     static int limit = 0;
     const void *fn = (const void *)cpcg::k_cpcg<TM>;
+    if (smem <= limit) return true;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
-    if (smem > limit) {
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        limit = smem;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
     }
+    limit = smem;
+    return true;
+}
+
+// Whether k_cpcg<TM> schedules a cluster of `cta` CTAs with smem bytes of
+// dynamic shared memory (checked once, at setup).
+template <typename TM>
+static bool cpcg_fits(int cta, int smem) {
+    const void *fn = (const void *)cpcg::k_cpcg<TM>;
+    if (!cpcg_smem_limit<TM>(smem)) return false;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cta);
     cfg.blockDim = dim3(cpcg::THREADS);
@@ -2698,7 +2666,7 @@ static int launch_vtail(Hierarchy *h, Workspace &W, cudaStream_t s) {
     at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 2;
-    if (!cpcg_fits<TM>(h->vtail_cta, h->vtail_smem)) {
+    if (!cpcg_smem_limit<TM>(h->vtail_smem)) {
         set_last_error("V-cycle cluster: %d bytes of shared memory refused", h->vtail_smem);
         return AMG_ERR_CUDA;
     }
@@ -2740,7 +2708,7 @@ static int launch_cpcg(Hierarchy *h, Workspace &W, cudaStream_t s) {
     cfg.numAttrs = 2;
     TRACE("cluster_pcg", 0, cpcg_bytes(h));
     if (mixed) {
-        if (!cpcg_fits<float>(h->cpcg_cta, h->cpcg_smem)) {
+        if (!cpcg_smem_limit<float>(h->cpcg_smem)) {
             set_last_error("whole-solve cluster: %d bytes of shared memory refused", h->cpcg_smem);
             return AMG_ERR_CUDA;
         }
@@ -2748,7 +2716,7 @@ static int launch_cpcg(Hierarchy *h, Workspace &W, cudaStream_t s) {
         AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<float>, args, (const double *)W.b, W.x, W.r, W.p, W.q, W.z,
                                         W.r32, W.scal));
     } else {
-        if (!cpcg_fits<double>(h->cpcg_cta, h->cpcg_smem)) {
+        if (!cpcg_smem_limit<double>(h->cpcg_smem)) {
             set_last_error("whole-solve cluster: %d bytes of shared memory refused", h->cpcg_smem);
             return AMG_ERR_CUDA;
         }
