@@ -700,20 +700,32 @@ __global__ void __launch_bounds__(NT, 2) k_stream_ell(int n, int rt, int cap, in
         }
     } else {
         const int cw = warp - 1;
+        // the entry range of the warp's first slice of tile t, loaded a tile
+        // ahead (the table is constant) so that its latency overlaps the
+        // tile before instead of the stage wait alone
+        auto first_range = [&](int t, int &a, int &b) {
+            const int g0 = t * spt;
+            if (cw < min(spt, nsl_all - g0)) {
+                a = __ldg(soff + g0 + cw);
+                b = __ldg(soff + g0 + cw + 1);
+            }
+        };
+        int nb0 = 0, nb1 = 0;
+        if ((int)blockIdx.x < ntiles) first_range(blockIdx.x, nb0, nb1);
         for (int j = 0;; ++j) {
             const int t = blockIdx.x + j * gridDim.x;
             if (t >= ntiles) break;
             const int st = j % STAGES;
             const int r0 = t * rt, g0 = t * spt;
             const int nsl = min(spt, nsl_all - g0);
-            // the warp's first slice: its entry range and the rows' epilogue
-            // operands, loaded before the stage wait so the latencies overlap
+            // the warp's first slice: its entry range (loaded during the tile
+            // before) and the rows' epilogue operands, loaded before the stage
+            // wait so the latencies overlap; then the next tile's range
             int sl = cw;
-            int sb0 = 0, sb1 = 0;
+            int sb0 = nb0, sb1 = nb1;
+            if (t + (int)gridDim.x < ntiles) first_range(t + gridDim.x, nb0, nb1);
             typename Op::Pre pre{};
             if (sl < nsl) {
-                sb0 = __ldg(soff + g0 + sl);
-                sb1 = __ldg(soff + g0 + sl + 1);
                 const int row = r0 + sl * 32 + lane;
                 if (!staged && row < n) pre = op.load_rest(row);
             }
