@@ -331,14 +331,15 @@ int amg_widen_f32(const float *in, double *out, long long n, void *cuda_stream);
  * cudaGetSymbolAddress), and is then held until the process exits.  That
  * first call is therefore the one that may take device memory (and may fail
  * with AMG_ERR_CUDA when none is left): make one warm-up call on each device
- * before entering a region that must not allocate, and make it before any
- * stream capture; later calls take no device memory.  Every call on a device
+ * before entering a region that must not allocate; later calls take no
+ * device memory.  Every call on a device
  * shares that array and it keeps the last call's contents (the call clears
  * what must start at zero), so calls whose GPU work overlaps -- on two
  * streams, or from two host threads -- race and corrupt each other:
  * serialise them.  The call reads the Krylov scalars back to the host
  * between iterations, so it waits for all earlier work on cuda_stream and
- * returns only after its own GPU work has finished.
+ * returns only after its own GPU work has finished: it is synchronous, and a
+ * stream that is capturing into a CUDA graph cannot record it.
  * Returns AMG_OK, AMG_MAXIT, AMG_BREAKDOWN, AMG_NAN or a hard error. */
 int amg_cg_solve_noalloc(int n, long long nnz, const int *row_ptr, const int *col_idx, const double *values,
                          const double *b, double *x, double rtol, int max_iter, void *cuda_stream,
