@@ -214,16 +214,30 @@ __global__ void __launch_bounds__(NT, 2) k_stream(int n, int rt, int cap, int nt
         const int ct = tid - 32;
         constexpr int ROWS_PER_PASS = CONSUMER_WARPS * 32 / VEC;
         const int rsub = ct / VEC, vl = ct % VEC;
+        // the first pass's epilogue operands of tile t (written by
+        // predecessors, so after the dependency wait): loaded a tile ahead,
+        // so that their latency overlaps the tile before, where the registers
+        // allow it (up to 512 threads), else before the stage wait
+        constexpr bool AHEAD = NT <= 512;
+        typename Op::Pre pnext{};
+        if constexpr (AHEAD) {
+            if ((int)blockIdx.x < ntiles && rsub < min(rt, n - (int)blockIdx.x * rt) && vl == 0)
+                pnext = op.load(blockIdx.x * rt + rsub);
+        }
         for (int j = 0;; ++j) {
             const int t = blockIdx.x + j * gridDim.x;
             if (t >= ntiles) break;
             const int st = j % STAGES;
             const int r0 = t * rt;
             const int rows = min(rt, n - r0);
-            // the first pass's epilogue operands are loaded before the stage
-            // wait, so their latency overlaps the bulk copy's
             typename Op::Pre pre0{};
-            if (rsub < rows && vl == 0) pre0 = op.load(r0 + rsub);
+            if constexpr (AHEAD) {
+                pre0 = pnext;
+                const int tn = t + gridDim.x;
+                if (tn < ntiles && rsub < min(rt, n - tn * rt) && vl == 0) pnext = op.load(tn * rt + rsub);
+            } else if (rsub < rows && vl == 0) {
+                pre0 = op.load(r0 + rsub);
+            }
             if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / STAGES) & 1), lim))) {  // warp-uniform
                 ok = false;
                 break;
