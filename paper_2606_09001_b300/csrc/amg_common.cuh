@@ -288,6 +288,7 @@ struct Hierarchy {
     int vtail_cta = 0;
     std::vector<unsigned char> vtail_args;
     int vtail_smem = 0;
+    int vtail_restricts = 0;  // the V-cycle table computes its first level's right-hand side (R_{t-1} t_{t-1})
     // mixed form: 1 when the outer product q = A p runs in double-FP32
     // arithmetic (A's values and p split into FP32 pairs), chosen at setup by
     // timing; krylov_us: a PCG iteration with the cycle's plan family's FP64

@@ -29,9 +29,11 @@
 //
 // V-cycle mode (vmode = 1): the same phases from a coarse level t down and
 // back, for a hierarchy whose levels above t stream: level t's right-hand
-// side comes from global memory (written by the restriction above) and its
-// result goes back there (read by the prolongation above); no reduction and
-// no data-dependent branch, so every CTA runs the same phases.
+// side is computed here from level t-1's residual (the restriction R_{t-1},
+// read from global memory: one launch fewer a cycle) or read from global
+// memory, and the result goes back there (read by the prolongation above);
+// no reduction and no data-dependent branch, so every CTA runs the same
+// phases.
 //
 // Reductions.  A CTA's partial dot products go into a slot per CTA in every
 // CTA's shared memory the same way; each CTA adds the slots in rank order,
@@ -95,6 +97,12 @@ struct CArgs {
     int vmode;
     const TM *vb;
     TM *vx;
+    // V-cycle mode, where vr_rp is set: level t's right-hand side computed
+    // here as R_{t-1} t_{t-1} (R's rows are level t's, split as level t; R
+    // and t_{t-1} are read from global memory), in place of the restriction
+    // pass above and the read of vb
+    const int *vr_rp, *vr_ci;
+    const TM *vr_v, *vr_x;
     int cta;
     int buf_off[2], buf_bytes; // the two staging buffers
     int x_off, r_off, p_off, q_off, z_off;  // the CTA's level-0 slices of the FP64 Krylov vectors
@@ -386,7 +394,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
     double *X = reinterpret_cast<double *>(smem + a.x_off), *R = reinterpret_cast<double *>(smem + a.r_off);
     double *P = reinterpret_cast<double *>(smem + a.p_off), *Q = reinterpret_cast<double *>(smem + a.q_off);
     double *Z = reinterpret_cast<double *>(smem + a.z_off);
-    if (a.vmode) {
+    if (a.vmode && a.vr_rp) {
+        // b_t = R_{t-1} t_{t-1} on the CTA's rows, four lanes a row
+        constexpr int G = 4;
+        TM *b0 = reinterpret_cast<TM *>(smem + a.L[0].b_off);
+        const int g = tid & (G - 1);
+        for (int base = r0; base < r1; base += THREADS / G) {
+            const int i = base + tid / G;
+            TM s = 0;
+            if (i < r1) {
+                const int e = __ldg(a.vr_rp + i + 1);
+                for (int k = __ldg(a.vr_rp + i) + g; k < e; k += G) s += __ldg(a.vr_v + k) * __ldg(a.vr_x + __ldg(a.vr_ci + k));
+            }
+            s = group_sum<G>(s);
+            if (i < r1 && g == 0) b0[i - r0] = s;
+        }
+    } else if (a.vmode) {
         TM *b0 = reinterpret_cast<TM *>(smem + a.L[0].b_off);
         for (int i = r0 + tid; i < r1; i += THREADS) b0[i - r0] = a.vb[i];
     } else {

@@ -2423,6 +2423,16 @@ static long long round16(long long b) { return (b + 15) / 16 * 16; }
 // vmode = 1 builds the table of one V-cycle from level t (the kernel's level
 // 0; no Krylov vectors or outer product), with level t's b and x in global
 // memory.
+// Whether the V-cycle cluster launch from level t computes level t's
+// right-hand side itself (R_{t-1} t_{t-1}): when R_{t-1} does not stream
+// (its rows are level t's, fewer than 16384) and is small enough for the
+// cluster's SMs to read in about a microsecond.
+static bool vtail_folds_restriction(const Hierarchy *h, int t) {
+    if (t < 1) return false;
+    const Level &lp = h->L[t - 1];
+    return !lp.sr.rt && lp.R.nnz <= 400000;
+}
+
 template <typename TM>
 static int build_cpcg_table(Hierarchy *h, int cta, int collapsed, int t, int vmode, std::vector<unsigned char> &out,
                             int *smem_bytes) {
@@ -2440,6 +2450,13 @@ static int build_cpcg_table(Hierarchy *h, int cta, int collapsed, int t, int vmo
         const Level &lt = h->L[t];
         a.vb = (const TM *)(mixed ? (const void *)lt.b32 : (const void *)lt.b);
         a.vx = (TM *)(mixed ? (void *)lt.x32 : (void *)lt.x);
+        if (vtail_folds_restriction(h, t)) {
+            const Level &lp = h->L[t - 1];
+            a.vr_rp = lp.R.rp;
+            a.vr_ci = lp.R.ci;
+            a.vr_v = (const TM *)(mixed ? (const void *)lp.R.v32 : (const void *)lp.R.v);
+            a.vr_x = (const TM *)(mixed ? (const void *)lp.t32 : (const void *)lp.t);
+        }
     }
     std::vector<std::vector<int>> rpA(nl), rpP(nl), rpR(nl);
     for (int k = 0; k < nl; ++k) {
@@ -2626,6 +2643,7 @@ static int cpcg_prepare(Hierarchy *h) {
 // CTAs, as for the whole solve.
 static int vtail_prepare(Hierarchy *h) {
     h->vtail_cta = 0;
+    h->vtail_restricts = 0;
     const int t = h->tail_start;
     if (t <= 0 || h->nsys > 0) return AMG_OK;
     const bool mixed = h->cfg.precision == AMG_PRECISION_MIXED;
@@ -2642,6 +2660,7 @@ static int vtail_prepare(Hierarchy *h) {
                 h->vtail_cta = cs;
                 h->vtail_args = args;
                 h->vtail_smem = smem;
+                h->vtail_restricts = vtail_folds_restriction(h, t) ? 1 : 0;  // as the table was built
                 return AMG_OK;
             }
         }
@@ -2876,6 +2895,12 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
     const int mm = mid_level(h);  // first level of the cooperative coarse launch, or -1
     // first level handled by the fused tail or the cooperative launch
     const int tl = h->tail_start >= 0 ? h->tail_start : (mm > 0 ? mm : L - 1);
+    // the cluster kernel's V-cycle where its table fits (built for the form's
+    // cycle type), else the tail kernel; the cluster V-cycle restricts into
+    // its first level itself when its table says so
+    const bool vt = h->tail_start > 0 && h->vtail_cta &&
+                    (sizeof(TM) == 4) == (h->cfg.precision == AMG_PRECISION_MIXED);
+    const bool vt_restricts = vt && h->vtail_restricts;
     if (h->tail_start == 0) {
         TRACE("tail", 0, tail_bytes(h, vb));
         return launch_tail<TM>(h, W, b0, z0, qprev, fin == FIN_PCG_BETA, s);
@@ -2912,7 +2937,8 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
             }
         }
         const int nc = lv.R.nrows;
-        if (l != mm - 1 || lv.sr.rt) {  // the cooperative launch restricts into its first level itself
+        // the cooperative launch and the cluster V-cycle restrict into their first level themselves
+        if ((l != mm - 1 || lv.sr.rt) && !(vt_restricts && l == tl - 1)) {
             TRACE("restrict", l, csr_bytes(lv.R, vb) + (double)vb * (n + nc));
             if (lv.sr.rt)
                 AMG_TRY(stream_launch<TM>(lv.sr, nc, lv.R.rp, lv.R.ci, Av(lv.R), OpSpmv<TM>{done, Tv(lv), Bv(nx)}, err, s));
@@ -2923,10 +2949,10 @@ static int launch_vcycle(Hierarchy *h, Workspace &W, const double *b0, double *z
         AMG_LAUNCH_CHECK();
     }
     if (h->tail_start > 0) {
-        // the cluster kernel's V-cycle where its table fits (built for the
-        // form's cycle type), else the tail kernel
-        if (h->vtail_cta && (sizeof(TM) == 4) == (h->cfg.precision == AMG_PRECISION_MIXED)) {
-            TRACE("cluster_cycle", tl, tail_bytes(h, vb));
+        if (vt) {
+            const Level &lp = h->L[tl - 1];
+            TRACE("cluster_cycle", tl,
+                  tail_bytes(h, vb) + (vt_restricts ? csr_bytes(lp.R, vb) + (double)vb * lp.A.nrows : 0.0));
             AMG_TRY(launch_vtail<TM>(h, W, s));
         } else {
             TRACE("tail", tl, tail_bytes(h, vb));

@@ -35,11 +35,14 @@ def solver(A, cfg=None):
     return api.Solver(dev(A.row_ptr), dev(A.col_idx), dev(A.values), cfg or {})
 
 
-def launched(s, fn):
+def launched(s, fn, levels=False):
+    """Names of the traced launches of fn() (with levels: (name, level) pairs)."""
     s.profile(True)
     fn()
     _, recs = s.profile_records()
     s.profile(False)
+    if levels:
+        return {(r["name"], r["level"]) for r in recs if r["launches"] > 0}
     return {r["name"] for r in recs if r["launches"] > 0}
 
 
@@ -179,8 +182,13 @@ def test_cluster_cycle_from_a_coarse_level(name, precision):
     rng = np.random.default_rng(21)
     r = rng.uniform(-1, 1, A.n)
     s = solver(A, {"precision": precision})
-    names = launched(s, lambda: s.vcycle(dev(r)))
+    runs = launched(s, lambda: s.vcycle(dev(r)), levels=True)
+    names = {n for n, _ in runs}
     assert "cluster_cycle" in names and "tail" not in names, names
+    # the launch restricts into its first level t itself: no restriction pass
+    # from level t-1 runs
+    (t,) = [lv for n, lv in runs if n == "cluster_cycle"]
+    assert t >= 1 and ("restrict", t - 1) not in runs and ("presmooth", t - 1) in runs, runs
     z = s.vcycle(dev(r)).cpu().numpy()
     zo = O.Hierarchy(A).vcycle(r)
     tol = 1e-12 if precision == "FP64" else 1e-5
