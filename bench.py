@@ -50,6 +50,10 @@ WORKLOADS = {
     "diffusion2d_logk_512": (lambda: M.diffusion2d_logk(N=512), "PCG", "2D diffusion, 512x512 cells, log k ~ N(0,1)"),
     "convdiff3d_upwind_160": (lambda: M.convdiff3d_upwind(N=160), "BICGSTAB",
                               "3D upwind convection-diffusion, 160^3, cell Peclet 10"),
+    # the same kernels on 2.1M rows (each pass still larger than L2): the size the
+    # per-kernel ncu counters of the 160^3 case are captured on, scaled by stored entries
+    "convdiff3d_upwind_128": (lambda: M.convdiff3d_upwind(N=128), "BICGSTAB",
+                              "3D upwind convection-diffusion, 128^3, cell Peclet 10"),
     "batched_poisson2d_256x8": (lambda: M.batched_poisson2d(), "PCG",
                                 "256 independent 2D 5-point Poisson systems, sides U{32..256}, 8 RHS each, "
                                 "block-diagonal CSR; one step = all 2048 (system, RHS) solves"),
