@@ -27,13 +27,16 @@
 // peer's output of the phase before, which the peer sends after it has read
 // the buffer, so a phase never overwrites what a slower CTA still gathers.
 //
-// V-cycle mode (vmode = 1): the same phases from a coarse level t down and
-// back, for a hierarchy whose levels above t stream: level t's right-hand
-// side is computed here from level t-1's residual (the restriction R_{t-1},
-// read from global memory: one launch fewer a cycle) or read from global
-// memory, and the result goes back there (read by the prolongation above);
-// no reduction and no data-dependent branch, so every CTA runs the same
-// phases.
+// V-cycle mode (k_cpcg<TM, true>, for a table built with vmode = 1): the
+// same phases from a coarse level t down and back, for a hierarchy whose
+// levels above t stream: level t's right-hand side is computed here from
+// level t-1's residual (the restriction R_{t-1}, read from global memory:
+// one launch fewer a cycle) or read from global memory, and the result goes
+// back there (read by the prolongation above); no reduction and no
+// data-dependent branch, so every CTA runs the same phases.  The mode is a
+// template parameter: the V-cycle instance carries none of the Krylov code
+// (71 registers a thread instead of 114-124, 4 KB of static shared memory
+// instead of 17 KB).
 //
 // Reductions.  A CTA's partial dot products go into a slot per CTA in every
 // CTA's shared memory the same way; each CTA adds the slots in rank order,
@@ -93,7 +96,8 @@ struct CArgs {
     int nlev;                  // levels 0 .. nlev-1; the last one is the dense coarsest
     // 1: one V-cycle from a coarse level t (table level 0) -- its right-hand
     // side vb and result vx in global memory, the levels above it run as
-    // separate passes -- instead of a whole PCG solve
+    // separate passes -- instead of a whole PCG solve; launched as
+    // k_cpcg<TM, true>
     int vmode;
     const TM *vb;
     TM *vx;
@@ -300,7 +304,7 @@ struct KScal {
 // the per-iteration kernels do and leaves done = 1; when the iterations end
 // converged or at the cap it also leaves r = b - A x and tr = ||r||^2 of the
 // final x (tr_fresh = 1), the true residual the host checks.
-template <typename TM>
+template <typename TM, bool VM>
 __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CArgs<TM> ga, const double *__restrict__ gb,
                                                      double *__restrict__ gx,
                                                      double *__restrict__ gr, double *__restrict__ gp,
@@ -394,7 +398,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
     double *X = reinterpret_cast<double *>(smem + a.x_off), *R = reinterpret_cast<double *>(smem + a.r_off);
     double *P = reinterpret_cast<double *>(smem + a.p_off), *Q = reinterpret_cast<double *>(smem + a.q_off);
     double *Z = reinterpret_cast<double *>(smem + a.z_off);
-    if (a.vmode && a.vr_rp) {
+    if (VM && a.vr_rp) {
         // b_t = R_{t-1} t_{t-1} on the CTA's rows, four lanes a row
         constexpr int G = 4;
         TM *b0 = reinterpret_cast<TM *>(smem + a.L[0].b_off);
@@ -409,7 +413,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
             s = group_sum<G>(s);
             if (i < r1 && g == 0) b0[i - r0] = s;
         }
-    } else if (a.vmode) {
+    } else if (VM) {
         TM *b0 = reinterpret_cast<TM *>(smem + a.L[0].b_off);
         for (int i = r0 + tid; i < r1; i += THREADS) b0[i - r0] = a.vb[i];
     } else {
@@ -484,7 +488,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
         const TM *w0 = reinterpret_cast<const TM *>(smem + a.L[0].w_off);
         const TM *b0 = reinterpret_cast<const TM *>(smem + a.L[0].b_off);
         for (int i = r0 + tid; i < r1; i += THREADS)
-            ys[i] = w0[i - r0] * (a.vmode ? b0[i - r0] : fcvt<TM>(R[i - r0]));
+            ys[i] = w0[i - r0] * (VM ? b0[i - r0] : fcvt<TM>(R[i - r0]));
         exchange(0, r0, r1, (int)sizeof(TM));
     }
     const bool loaded = __syncthreads_and(stream::mbar_wait(&bar, 0)) != 0;
@@ -507,7 +511,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
                 TM *ys = reinterpret_cast<TM *>(buf(nb));
                 if (loaded)
                     rows<TM, TM, TM>(lv.A, s0, s1, c, smem, xs, [&](int i, TM s) {
-                        const TM bi = k == 0 && !a.vmode ? fcvt<TM>(R[i - s0]) : bk[i - s0];
+                        const TM bi = k == 0 && !VM ? fcvt<TM>(R[i - s0]) : bk[i - s0];
                         ys[i] = bi - s;
                     });
                 exchange(nb, s0, s1, (int)sizeof(TM));
@@ -559,7 +563,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
             const int s0 = lv.r0[c], s1 = lv.r0[c + 1];
             const TM *wk = reinterpret_cast<const TM *>(smem + lv.w_off);
             const TM *bk = reinterpret_cast<const TM *>(smem + lv.b_off);
-            auto bof = [&](int i) { return k == 0 && !a.vmode ? fcvt<TM>(R[i - s0]) : bk[i - s0]; };
+            auto bof = [&](int i) { return k == 0 && !VM ? fcvt<TM>(R[i - s0]) : bk[i - s0]; };
             {
                 // t = W b + P x_next
                 const int nb = cur ^ 1;
@@ -581,7 +585,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
                     rows<TM, TM, TM>(lv.A, s0, s1, c, smem, ts,
                                      [&](int i, TM s) { ys[i] = ts[i] + wk[i - s0] * (bof(i) - s); });
                 exchange(nb, s0, s1, (int)sizeof(TM));
-            } else if (a.vmode) {
+            } else if (VM) {
                 // the cycle's result, read by the prolongation of the level above
                 if (loaded)
                     rows<TM, TM, TM>(lv.A, s0, s1, c, smem, ts,
@@ -630,7 +634,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
                 stop = S.stop != 0;
             }
         }
-        if (stop || a.vmode) break;
+        if (stop || VM) break;
         // p = z + beta p
         {
             const int nb = cur ^ 1;
@@ -691,7 +695,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
     }
     // the true residual of the final x: x to every CTA, then r = b - A x
     // (the FP64 operator) and ||r||^2
-    const bool true_res = !a.vmode && (S.status == AMG_OK || S.status == AMG_MAXIT);
+    const bool true_res = !VM && (S.status == AMG_OK || S.status == AMG_MAXIT);
     if (true_res) {
         {
             const int nb = cur ^ 1;
@@ -715,7 +719,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
     }
     if ((bad & 2) && tid == 0) atomicOr(&sc->copy_timeout, 4);
     // the state back to global memory for the true residual and a restart
-    if (!a.vmode)
+    if (!VM)
         for (int i = r0 + tid; i < r1; i += THREADS) {
             gx[i] = X[i - r0];
             gr[i] = R[i - r0];
@@ -724,7 +728,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cpcg(const __grid_constant__ CAr
             gz[i] = Z[i - r0];
             if (gr32) gr32[i] = f64_to_f32_rn(R[i - r0]);
         }
-    if (c == 0 && tid == 0 && !a.vmode) {
+    if (c == 0 && tid == 0 && !VM) {
         sc->rz = S.rz;
         sc->alpha = S.alpha;
         sc->beta = S.beta;

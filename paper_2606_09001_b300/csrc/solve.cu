@@ -2570,13 +2570,13 @@ static int build_cpcg_table(Hierarchy *h, int cta, int collapsed, int t, int vmo
     return AMG_OK;
 }
 
-// Raises k_cpcg<TM>'s dynamic shared-memory limit to at least smem (the
+// Raises k_cpcg<TM, VM>'s dynamic shared-memory limit to at least smem (the
 // limit belongs to the kernel and only grows, as the tail's) and allows
 // 16-CTA clusters.
-template <typename TM>
+template <typename TM, bool VM>
 static bool cpcg_smem_limit(int smem) {
     static int limit = 0;
-    const void *fn = (const void *)cpcg::k_cpcg<TM>;
+    const void *fn = (const void *)cpcg::k_cpcg<TM, VM>;
     if (smem <= limit) return true;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
@@ -2587,12 +2587,12 @@ static bool cpcg_smem_limit(int smem) {
     return true;
 }
 
-// Whether k_cpcg<TM> schedules a cluster of `cta` CTAs with smem bytes of
-// dynamic shared memory (checked once, at setup).
-template <typename TM>
+// Whether k_cpcg<TM, VM> schedules a cluster of `cta` CTAs with smem bytes
+// of dynamic shared memory (checked once, at setup).
+template <typename TM, bool VM>
 static bool cpcg_fits(int cta, int smem) {
-    const void *fn = (const void *)cpcg::k_cpcg<TM>;
-    if (!cpcg_smem_limit<TM>(smem)) return false;
+    const void *fn = (const void *)cpcg::k_cpcg<TM, VM>;
+    if (!cpcg_smem_limit<TM, VM>(smem)) return false;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cta);
     cfg.blockDim = dim3(cpcg::THREADS);
@@ -2627,7 +2627,7 @@ static int cpcg_prepare(Hierarchy *h) {
             if (mixed) AMG_TRY(build_cpcg_table<float>(h, cs, collapsed, 0, 0, args, &smem));
             else AMG_TRY(build_cpcg_table<double>(h, cs, collapsed, 0, 0, args, &smem));
             if (smem < 0) continue;
-            if (mixed ? cpcg_fits<float>(cs, smem) : cpcg_fits<double>(cs, smem)) {
+            if (mixed ? cpcg_fits<float, false>(cs, smem) : cpcg_fits<double, false>(cs, smem)) {
                 h->cpcg_cta = cs;
                 h->cpcg_args = args;
                 h->cpcg_smem = smem;
@@ -2656,7 +2656,7 @@ static int vtail_prepare(Hierarchy *h) {
             if (mixed) AMG_TRY(build_cpcg_table<float>(h, cs, collapsed, t, 1, args, &smem));
             else AMG_TRY(build_cpcg_table<double>(h, cs, collapsed, t, 1, args, &smem));
             if (smem < 0) continue;
-            if (mixed ? cpcg_fits<float>(cs, smem) : cpcg_fits<double>(cs, smem)) {
+            if (mixed ? cpcg_fits<float, true>(cs, smem) : cpcg_fits<double, true>(cs, smem)) {
                 h->vtail_cta = cs;
                 h->vtail_args = args;
                 h->vtail_smem = smem;
@@ -2685,12 +2685,12 @@ static int launch_vtail(Hierarchy *h, Workspace &W, cudaStream_t s) {
     at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 2;
-    if (!cpcg_smem_limit<TM>(h->vtail_smem)) {
+    if (!cpcg_smem_limit<TM, true>(h->vtail_smem)) {
         set_last_error("V-cycle cluster: %d bytes of shared memory refused", h->vtail_smem);
         return AMG_ERR_CUDA;
     }
     const auto &args = *(const cpcg::CArgs<TM> *)h->vtail_args.data();
-    AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<TM>, args, (const double *)nullptr, (double *)nullptr,
+    AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<TM, true>, args, (const double *)nullptr, (double *)nullptr,
                                     (double *)nullptr, (double *)nullptr, (double *)nullptr, (double *)nullptr,
                                     (float *)nullptr, W.scal));
     return AMG_OK;
@@ -2727,20 +2727,20 @@ static int launch_cpcg(Hierarchy *h, Workspace &W, cudaStream_t s) {
     cfg.numAttrs = 2;
     TRACE("cluster_pcg", 0, cpcg_bytes(h));
     if (mixed) {
-        if (!cpcg_smem_limit<float>(h->cpcg_smem)) {
+        if (!cpcg_smem_limit<float, false>(h->cpcg_smem)) {
             set_last_error("whole-solve cluster: %d bytes of shared memory refused", h->cpcg_smem);
             return AMG_ERR_CUDA;
         }
         const auto &args = *(const cpcg::CArgs<float> *)h->cpcg_args.data();
-        AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<float>, args, (const double *)W.b, W.x, W.r, W.p, W.q, W.z,
+        AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<float, false>, args, (const double *)W.b, W.x, W.r, W.p, W.q, W.z,
                                         W.r32, W.scal));
     } else {
-        if (!cpcg_smem_limit<double>(h->cpcg_smem)) {
+        if (!cpcg_smem_limit<double, false>(h->cpcg_smem)) {
             set_last_error("whole-solve cluster: %d bytes of shared memory refused", h->cpcg_smem);
             return AMG_ERR_CUDA;
         }
         const auto &args = *(const cpcg::CArgs<double> *)h->cpcg_args.data();
-        AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<double>, args, (const double *)W.b, W.x, W.r, W.p, W.q,
+        AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpcg::k_cpcg<double, false>, args, (const double *)W.b, W.x, W.r, W.p, W.q,
                                         W.z, (float *)nullptr, W.scal));
     }
     return AMG_OK;
